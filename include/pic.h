@@ -1,0 +1,182 @@
+/*
+ * pic.h -- C ABI of the GB300 vacuum-arc PIC-MCC step (libpic.so).
+ *
+ * The library advances the coupled plasma step of Koitermaa et al., "Simulating vacuum arc
+ * initiation by coupling emission, heating and plasma processes" (arXiv:2402.08404): thermal-
+ * field emission from every exposed cathode face (Sec. 2.3.1), evaporation and sputter
+ * injection (Sec. 2.3.1-2.3.3), field gather and leapfrog push with boundary removal
+ * (Sec. 2.2), cell sort, impact-ionization MCC with SP splitting (eq:colp, eq:du, Sec. 2.3.2),
+ * direct field ionization (eq:dfi), charge deposition and the Poisson solve (eq:poi,
+ * eq:bcf1-3), and the tip heat equation with Joule heating (eq:heat, eq:cont) every n_heat steps.
+ * Equations are cited by their LaTeX labels in the paper.
+ *
+ * Geometry: an nx*ny*nz Cartesian grid of cells of size dx [m]; the cathode plane is z=0
+ * (phi = 0), the anode plane z = nz*dx (phi = V0), the lateral walls carry zero normal field;
+ * a Cu tip (cylinder + hemispherical cap on the axis x = nx/2, y = ny/2) is made of solid cells
+ * whose centres lie inside it; all corners of solid cells are held at phi = 0.
+ *
+ * Species are indexed PIC_ELECTRON = 0, PIC_NEUTRAL = 1 (Cu), PIC_ION = 2 (Cu+).  Every SP has a
+ * position in cell units (x/dx, float), a velocity [m/s] (float), a weight in units of w_min
+ * (int32) and a 64-bit id that keys all its random draws (Philox4x32-10).
+ *
+ * Ownership.  The library owns all device state.  Device memory is taken through the
+ * caller's allocator callbacks (pic_alloc_fn/pic_free_fn; NULL selects cudaMalloc/cudaFree),
+ * kernels run on the caller's stream (a cudaStream_t passed as void*; NULL = legacy stream).
+ * Unless stated otherwise, array arguments are HOST pointers owned by the caller; the call
+ * copies them synchronously.
+ *
+ * Errors.  Every int-returning call returns PIC_OK (0) or a negative PIC_E_* code and records a
+ * message readable through pic_last_error().  After PIC_E_CUDA the handle should be destroyed.
+ */
+#ifndef PIC_H
+#define PIC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PIC_OK 0
+#define PIC_E_INVALID (-1)   /* bad argument or size */
+#define PIC_E_CAPACITY (-2)  /* an SP count or a per-cell count would exceed its capacity */
+#define PIC_E_NOCONV (-3)    /* Poisson solve did not reach mg_tol within mg_max_cycles */
+#define PIC_E_TIMEOUT (-4)   /* a bounded device wait gave up */
+#define PIC_E_CUDA (-5)      /* a CUDA runtime call failed */
+
+#define PIC_ELECTRON 0
+#define PIC_NEUTRAL 1
+#define PIC_ION 2
+#define PIC_NSPECIES 3
+
+/* flags of pic_params_t */
+#define PIC_F_EMISSION 0x01u    /* a1: thermal-field emission */
+#define PIC_F_EVAP 0x02u        /* a2: evaporation */
+#define PIC_F_SPUTTER 0x04u     /* a2: sputter injection from ion impacts */
+#define PIC_F_IMPACT_ION 0x08u  /* a5: impact ionization MCC */
+#define PIC_F_DFI 0x10u         /* a6: direct field ionization */
+#define PIC_F_HEAT 0x20u        /* a10: heat + Joule every n_heat steps */
+#define PIC_F_SURROGATE 0x40u   /* a1 uses the trained MLP where it is inside its validated range */
+#define PIC_F_MIXED_MG 0x80u    /* a8: FP32 V-cycles with FP64 residual refinement (else FP64 V-cycles) */
+#define PIC_F_ALL 0xFFu
+
+typedef struct {
+  double tip_radius; /* m */
+  double tip_height; /* m, including the hemispherical cap */
+} pic_geometry_t;
+
+typedef struct {
+  int nx, ny, nz; /* cells; nx, ny, nz must be even */
+  double dx;      /* m */
+} pic_grid_t;
+
+typedef struct {
+  int charge_e;     /* charge number: -1, 0, +1 */
+  double mass;      /* kg */
+  int64_t capacity; /* maximum number of SPs held */
+} pic_species_t;
+
+typedef struct {
+  double dt;            /* PIC time step [s] */
+  double apex_field;    /* V/m: V0 is calibrated at create so the apex face field equals this */
+  double V0;            /* V: if > 0, used as the anode potential and no calibration is done */
+  double T0;            /* ambient / initial tip temperature [K] */
+  double work_function; /* eV */
+  double w_min;         /* real particles per weight unit (Sec. 2.3.2) */
+  int w_max_units;      /* maximum injection weight in units of w_min */
+  int n_heat;           /* heat step every n_heat PIC steps (dt_heat = n_heat dt); 0 = never */
+  uint64_t seed;        /* Philox key */
+  uint32_t flags;       /* PIC_F_* */
+  double mg_tol;        /* relative residual target of the Poisson solve */
+  int mg_max_cycles;    /* cap on refinement cycles per solve */
+} pic_params_t;
+
+typedef struct {
+  int64_t step, next_id;
+  int64_t count[PIC_NSPECIES];          /* SPs held per species */
+  int64_t weight[PIC_NSPECIES];         /* sum of weights per species (units of w_min) */
+  int64_t emitted, evaporated, sputtered;           /* SPs created this step */
+  int64_t impact_ionizations, field_ionizations;    /* events this step */
+  int64_t removed[PIC_NSPECIES], ion_impacts;       /* this step */
+  int64_t total_charge_fixed;           /* sum of deposited node charge (units e w_min 2^-30) */
+  int mg_cycles;                        /* cycles of the last Poisson solve */
+  double mg_residual;                   /* relative residual of the last Poisson solve */
+  double V0;                            /* anode potential [V] */
+  double max_face_field, max_J, max_T;  /* V/m, A/m^2, K */
+  double emitted_current;               /* A, from the last emission pass */
+  double ms[8]; /* last-step ms of: emit+inject, push, sort, collide, deposit, solve+E, heat, total */
+} pic_diag_t;
+
+typedef struct pic_s pic_t;
+typedef void *(*pic_alloc_fn)(size_t bytes, void *stream, void *user);
+typedef void (*pic_free_fn)(void *ptr, size_t bytes, void *stream, void *user);
+
+/* Create a handle (Sec. 2.1 statement of the problem): builds the staircased geometry, the
+ * face list and the multigrid hierarchy on the device, then calibrates V0 from apex_field by a
+ * Laplace solve (unless params->V0 > 0) and solves for the initial potential.
+ * species: PIC_NSPECIES entries in the order electron, Cu, Cu+. */
+int pic_create(const pic_geometry_t *geometry, const pic_grid_t *grid, const pic_species_t *species,
+               int nspecies, const pic_params_t *params, pic_alloc_fn alloc, pic_free_fn free_fn,
+               void *alloc_user, void *stream, pic_t **out);
+void pic_destroy(pic_t *h);
+const char *pic_last_error(pic_t *h);
+
+/* Replace all SPs of one species (host SoA arrays of length n) and cell-sort them.  Every SP
+ * must lie inside the domain and outside the tip; PIC_E_INVALID otherwise, PIC_E_CAPACITY if
+ * n exceeds the species capacity. */
+int pic_load_particles(pic_t *h, int species, const float *x, const float *y, const float *z,
+                       const float *vx, const float *vy, const float *vz, const int32_t *w,
+                       const uint64_t *id, int64_t n);
+/* Copy out the SPs of one species in their current device order (cell-sorted part first, then
+ * SPs created since the last sort); n_out receives the count.  PIC_E_CAPACITY if cap is short. */
+int pic_get_particles(pic_t *h, int species, float *x, float *y, float *z, float *vx, float *vy,
+                      float *vz, int32_t *w, uint64_t *id, int64_t cap, int64_t *n_out);
+/* Step counter (keys the random draws) and the next id to hand out. */
+int pic_set_clock(pic_t *h, int64_t step, int64_t next_id);
+
+/* Node arrays are (nz+1)*(ny+1)*(nx+1), index (k*(ny+1)+j)*(nx+1)+i. */
+int pic_set_potential(pic_t *h, const double *phi); /* also recomputes the node field */
+int pic_get_potential(pic_t *h, double *phi);
+int pic_get_efield(pic_t *h, float *E);   /* 3 floats (Ex,Ey,Ez) [V/m] per node */
+int pic_get_charge(pic_t *h, int64_t *Q); /* deposited charge, units e*w_min*2^-30 */
+/* Tip temperature per solid cell, in linear cell order. */
+int pic_set_temperature(pic_t *h, const double *T);
+int pic_get_temperature(pic_t *h, double *T);
+int pic_num_solid(pic_t *h, int64_t *n);
+
+/* Exposed faces in their fixed order: vacuum cell, direction code (0..5 = -x,+x,-y,+y,-z,+z:
+ * where the solid or the cathode plane lies) and owner solid cell (-1 for the cathode plane). */
+int pic_num_faces(pic_t *h, int64_t *n);
+int pic_get_faces(pic_t *h, int64_t *vcell, int32_t *dir, int64_t *owner);
+/* Per-face state of the last emission pass: local field [V/m], J [A/m^2], P_N [W/m^2]. */
+int pic_get_face_emission(pic_t *h, double *F, double *J, double *PN);
+/* Per-face surface accumulators: evaporation [atoms], heat [J], emitted charge [C] (double) and
+ * sputter [atoms 2^-24], bombardment energy E_b and sputtered energy E_s [eV 2^-20] (int64). */
+int pic_get_face_accumulators(pic_t *h, double *evap, double *heat, double *charge, int64_t *sput,
+                              int64_t *Eb, int64_t *Es);
+int pic_set_face_accumulators(pic_t *h, const double *evap, const double *heat, const double *charge,
+                              const int64_t *sput, const int64_t *Eb, const int64_t *Es);
+
+/* Stages of one step (each also usable alone; pic_step runs them all in this order). */
+int pic_emit(pic_t *h);        /* a1 emission + a2 evaporation/sputter injection (appends SPs) */
+int pic_push(pic_t *h);        /* a3 gather + leapfrog + boundary removal, ion impact records */
+int pic_sort(pic_t *h);        /* a4 stable cell sort of every species, dropping removed SPs */
+int pic_collide(pic_t *h);     /* a5 impact ionization MCC, then a6 field ionization (appends) */
+int pic_deposit(pic_t *h);     /* a7 fixed-point CIC charge deposit of e- and Cu+ */
+int pic_solve_field(pic_t *h); /* a7 deposit, a8 Poisson solve, a9 node field */
+int pic_heat(pic_t *h);        /* a10 continuity + heat on the tip cells from the accumulators */
+/* nsteps full steps a1..a10 (heat every n_heat steps); the step counter advances by nsteps. */
+int pic_step(pic_t *h, int nsteps);
+int pic_diagnostics(pic_t *h, pic_diag_t *out);
+
+/* Emission current density and Nottingham heat of n surface states (host arrays): F [V/m],
+ * T [K], work function [eV], radius of curvature [m] (<= 0 or inf: flat); J [A/m^2], PN [W/m^2].
+ * Evaluates the full FP64 thermal-field integral on the device (Sec. 2.3.1). */
+int pic_emission_eval(pic_t *h, const double *F, const double *T, const double *phi_w,
+                      const double *R, double *J, double *PN, int64_t n);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -104,15 +104,18 @@ def _L(w):
 
 def nottingham_inner(W, kT):
     """I(W) = int_W^inf (-E) / (1 + exp(E/kT)) dE [eV^2] in closed form through the dilogarithm:
-    w >= 0:  -(kT)^2 [w ln(1+e^-w) + L(w)];   w < 0:  (kT)^2 [w^2/2 - pi^2/6 - w ln(1+e^w) + L(-w)]."""
-    w = np.atleast_1d(np.asarray(W, dtype=np.float64) / kT)
+    w >= 0:  -(kT)^2 [w ln(1+e^-w) + L(w)];   w < 0:  (kT)^2 [w^2/2 - pi^2/6 - w ln(1+e^w) + L(-w)].
+    W and kT broadcast."""
+    Wb, kTb = np.broadcast_arrays(np.asarray(W, dtype=np.float64), np.asarray(kT, dtype=np.float64))
+    w = np.atleast_1d(Wb / kTb)
+    k2 = np.atleast_1d(kTb) ** 2
     out = np.empty_like(w)
     p = w >= 0
     wp = w[p]
-    out[p] = -(kT ** 2) * (wp * np.log1p(np.exp(-wp)) + _L(wp))
+    out[p] = -k2[p] * (wp * np.log1p(np.exp(-wp)) + _L(wp))
     wn = w[~p]
-    out[~p] = (kT ** 2) * (0.5 * wn * wn - math.pi ** 2 / 6.0 - wn * np.log1p(np.exp(wn)) + _L(-wn))
-    return out if np.ndim(W) else out[0]
+    out[~p] = k2[~p] * (0.5 * wn * wn - math.pi ** 2 / 6.0 - wn * np.log1p(np.exp(wn)) + _L(-wn))
+    return out if np.ndim(Wb) else out[0]
 
 
 def nottingham_inner_quad(W, kT):
@@ -252,9 +255,7 @@ def current_density_fixed(F_GV, T, phi, R_nm, panels=160):
     D = np.where(below, D, 1.0)
     kTb = kT[:, None] * np.ones_like(Wn)
     Jint = np.sum(Ww * D * _supply_v(Wn, kTb), axis=1)
-    Iw = np.empty_like(Wn)
-    for r in range(len(F)):
-        Iw[r] = nottingham_inner(Wn[r], kT[r])
+    Iw = nottingham_inner(Wn, kT[:, None])
     Pint = np.sum(Ww * D * Iw, axis=1)
     # above the barrier maximum (D = 1)
     npan = 24
@@ -266,10 +267,7 @@ def current_density_fixed(F_GV, T, phi, R_nm, panels=160):
     Wwa = ((h2 * 0.5)[:, :, None] * wg[None, None, :] * np.ones((1, npan, 1))).reshape(len(F), -1)
     kTa = kT[:, None] * np.ones_like(Wa)
     Jint += np.sum(Wwa * _supply_v(Wa, kTa), axis=1)
-    Ia = np.empty_like(Wa)
-    for r in range(len(F)):
-        Ia[r] = nottingham_inner(Wa[r], kT[r])
-    Pint += np.sum(Wwa * Ia, axis=1)
+    Pint += np.sum(Wwa * nottingham_inner(Wa, kT[:, None]), axis=1)
     J[act] = Z_S * Jint
     PN[act] = Z_S * Pint
     return J, PN

@@ -114,10 +114,11 @@ def first_event(grid, p0, p1):
     Cells are traversed in the order their boundaries are crossed (ties: x before y before
     z); the first cell entered that is solid or outside the domain ends the traversal.
     Returns (event, vacuum cell left, direction code 0..5 of the crossing)."""
-    c = np.floor(p0).astype(np.int64)
-    ce = np.floor(p1).astype(np.int64)
-    d = p1 - p0
     n = (grid.nx, grid.ny, grid.nz)
+    c = np.floor(p0).astype(np.int64)
+    # end cell clamped to [-1, n]: leaving the domain is an event before any clamped cell
+    ce = np.array([int(min(max(np.floor(p1[a]), -1.0), n[a])) for a in range(3)], dtype=np.int64)
+    d = p1 - p0
     while not np.array_equal(c, ce):
         best_a, best_t = -1, 0.0
         for a in range(3):
@@ -151,8 +152,12 @@ def boundary(grid, sp_, new, is_ion, mass):
     alive = np.ones(n, dtype=bool)
     impacts = []
     c0 = np.stack([np.floor(x0), np.floor(y0), np.floor(z0)], 1).astype(np.int64)
-    c1 = np.stack([np.floor(x1), np.floor(y1), np.floor(z1)], 1).astype(np.int64)
-    moved = np.nonzero(np.any(c0 != c1, axis=1))[0]
+    finite = np.isfinite(x1) & np.isfinite(y1) & np.isfinite(z1)
+    alive &= finite
+    lim = np.array([grid.nx, grid.ny, grid.nz], dtype=np.float64)
+    c1 = np.clip(np.floor(np.stack([np.where(finite, x1, 0), np.where(finite, y1, 0), np.where(finite, z1, 0)], 1)
+                          .astype(np.float64)), -1.0, lim).astype(np.int64)
+    moved = np.nonzero(np.any(c0 != c1, axis=1) & finite)[0]
     for p in moved:
         ev, vcell, dcode = first_event(grid,
                                        np.array([x0[p], y0[p], z0[p]], dtype=np.float64),

@@ -1,0 +1,335 @@
+// Monte Carlo collisions: impact ionization Cu + e -> Cu+ + 2e with SP splitting (Sec. 2.2,
+// eq:colp, eq:du, Sec. 2.3.2) and direct field ionization of neutrals (eq:dfi, Sec. 2.3.4).
+//
+// Pairing in a cell with N_e electron SPs and N_n neutral SPs: the species with fewer SPs (tie:
+// electrons) is the projectile; projectile k meets target (k + o_c) mod N_t, o_c =
+// floor(U_PAIR(cell, step) N_t).  Each of the w_p sub-particles of a projectile collides iff
+// U_i < P, P = 1 - exp(-u n_t W_t sigma(E0) dt), n_t the target SP density and W_t the paired
+// target's weight in real particles; N_coll is capped at the target weight.
+//
+// Decisions: P is evaluated in float32; any draw within a guard band of P (2^-12 relative to P
+// plus the largest P this relative speed can reach) re-decides the whole pair with P in
+// float64, so every decision equals the float64 decision.
+//
+// Products are written in a fixed order so ids and slots are deterministic: pairs with an
+// electron projectile in cell-sorted electron order, then pairs with a neutral projectile in
+// cell-sorted neutral order; per pair the ion, the scattered electron (when the electron SP
+// is split) and the secondary electron take consecutive ids.
+#include "pic_internal.cuh"
+#include "dev_common.cuh"
+
+namespace pic {
+
+constexpr double kLotzA = 4.5e-18;     // m^2 eV^2  (4.5e-14 cm^2 eV^2)
+
+__device__ __forceinline__ double sigma_ion64(double E) {
+  return E > kXiCu ? kLotzA * log(E / kXiCu) / (E * kXiCu) : 0.0;
+}
+__device__ __forceinline__ float sigma_ion32(float E) {
+  const float xi = (float)kXiCu;
+  return E > xi ? (float)kLotzA * logf(E / xi) / (E * xi) : 0.0f;
+}
+
+struct McArgs {
+  SpeciesBuf e, n;
+  const uint32_t *off_e, *off_n;
+  int nx, ny;
+  double V_cell, dt, w_min;
+  uint64_t seed;
+  DevClock *clk;
+  uint64_t *pair_cnt, *pair_off;
+  int32_t *pair_ncoll;
+  int *go;
+};
+
+struct Pair {
+  int64_t ie, in;   // electron index, neutral index
+  int proj_e;       // 1: electron is the projectile
+  uint32_t Nt;
+};
+
+// Resolve the pair of work item t (t < n_e: electron t; else neutral t - n_e).  false if none.
+__device__ bool resolve_pair(const McArgs &a, int64_t t, int64_t ne, int64_t step, Pair *pr) {
+  const bool is_e = t < ne;
+  const int64_t p = is_e ? t : t - ne;
+  const SpeciesBuf &S = is_e ? a.e : a.n;
+  const uint32_t c = (uint32_t)cell_index((int)floorf(S.x[p]), (int)floorf(S.y[p]), (int)floorf(S.z[p]), a.nx, a.ny);
+  const uint32_t Ne = a.off_e[c + 1] - a.off_e[c];
+  const uint32_t Nn = a.off_n[c + 1] - a.off_n[c];
+  if (Ne == 0 || Nn == 0) return false;
+  const bool e_proj = Ne <= Nn;
+  if (e_proj != is_e) return false;
+  const uint32_t Nt = is_e ? Nn : Ne;
+  const uint32_t k = (uint32_t)(p - (is_e ? a.off_e[c] : a.off_n[c]));
+  const U4 r = rng_block(a.seed, kPair, c, step, 0);
+  const uint32_t o = u_index(r.v[0], Nt);
+  const uint32_t tgt = (k + o) % Nt;
+  if (is_e) { pr->ie = p; pr->in = a.off_n[c] + tgt; }
+  else { pr->in = p; pr->ie = a.off_e[c] + tgt; }
+  pr->proj_e = is_e;
+  pr->Nt = Nt;
+  return true;
+}
+
+__global__ void k_mcc_count(McArgs a) {
+  const int64_t ne = a.clk->n_sorted[PIC_ELECTRON], nn = a.clk->n_sorted[PIC_NEUTRAL];
+  const int64_t step = a.clk->step;
+  const int64_t total = ne + nn;
+  const float sig_peak = (float)(kLotzA / (2.718281828459045 * kXiCu * kXiCu));
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    Pair pr;
+    int ncoll = 0;
+    if (resolve_pair(a, t, ne, step, &pr)) {
+      const int we = a.e.w[pr.ie], wn = a.n.w[pr.in];
+      const int wp = pr.proj_e ? we : wn, wt = pr.proj_e ? wn : we;
+      const float dvx = a.e.vx[pr.ie] - a.n.vx[pr.in];
+      const float dvy = a.e.vy[pr.ie] - a.n.vy[pr.in];
+      const float dvz = a.e.vz[pr.ie] - a.n.vz[pr.in];
+      const float u2 = dvx * dvx + dvy * dvy + dvz * dvz;
+      const float u = sqrtf(u2);
+      const float E0 = (float)(0.5 * kMe / kQe) * u2;
+      const float nW = (float)((double)pr.Nt / a.V_cell * (double)wt * a.w_min * a.dt);
+      const float x = u * nW * sigma_ion32(E0);
+      const float P32 = -expm1f(-x);
+      const float band = ldexpf(P32 + u * nW * sig_peak, -12);
+      const uint64_t pid = pr.proj_e ? a.e.id[pr.ie] : a.n.id[pr.in];
+      bool exact = false;
+      for (int i = 0; i < wp; i += 4) {
+        const U4 r = rng_block(a.seed, kIon, pid, step, (uint32_t)(i >> 2));
+        for (int j = 0; j < 4 && i + j < wp; ++j) {
+          const float U = u01f(r.v[j]);
+          if (fabsf(U - P32) <= band) exact = true;
+          ncoll += U < P32;
+        }
+      }
+      if (exact) {
+        const double ex = (double)a.e.vx[pr.ie] - (double)a.n.vx[pr.in];
+        const double ey = (double)a.e.vy[pr.ie] - (double)a.n.vy[pr.in];
+        const double ez = (double)a.e.vz[pr.ie] - (double)a.n.vz[pr.in];
+        const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)), __dmul_rn(ez, ez));
+        const double ud = sqrt(d2);
+        const double E0d = 0.5 * kMe * d2 / kQe;
+        const double xd = ud * ((double)pr.Nt / a.V_cell) * ((double)wt * a.w_min) * sigma_ion64(E0d) * a.dt;
+        const double P64 = -expm1(-xd);
+        ncoll = 0;
+        for (int i = 0; i < wp; i += 4) {
+          const U4 r = rng_block(a.seed, kIon, pid, step, (uint32_t)(i >> 2));
+          for (int j = 0; j < 4 && i + j < wp; ++j) ncoll += u01d(r.v[j]) < P64;
+        }
+      }
+      if (ncoll > wt) ncoll = wt;
+      a.pair_ncoll[t] = ncoll;
+      a.pair_cnt[t] = ncoll > 0 ? (1ull | ((uint64_t)(ncoll < we ? 2 : 1) << 32)) : 0ull;
+    } else {
+      a.pair_ncoll[t] = 0;
+      a.pair_cnt[t] = 0ull;
+    }
+  }
+}
+
+__device__ void scatter_velocity(double ux, double uy, double uz, double uk, double cos_tp, double phi_p, double out[3]) {
+  const double u = sqrt(ux * ux + uy * uy + uz * uz);
+  double th = 0.0, ph = 0.0;
+  if (u > 0) {
+    double c = uz / u;
+    c = c > 1.0 ? 1.0 : (c < -1.0 ? -1.0 : c);
+    th = acos(c);
+    ph = atan2(uy, ux);
+  }
+  const double tp = acos(cos_tp);
+  const double a0 = uk * sin(tp) * cos(phi_p), a1 = uk * sin(tp) * sin(phi_p), a2 = uk * cos(tp);
+  const double ct = cos(th), st = sin(th), cp = cos(ph), sp = sin(ph);
+  // R^-1(theta, phi) = R^T with R rows (ct cp, ct sp, -st), (-sp, cp, 0), (st cp, st sp, ct)
+  out[0] = ct * cp * a0 - sp * a1 + st * cp * a2;
+  out[1] = ct * sp * a0 + cp * a1 + st * sp * a2;
+  out[2] = -st * a0 + ct * a2;
+}
+
+__device__ __forceinline__ void put_sp(SpeciesBuf &B, int64_t s, float x, float y, float z, float vx, float vy, float vz,
+                                       int32_t w, uint64_t id) {
+  B.x[s] = x; B.y[s] = y; B.z[s] = z; B.vx[s] = vx; B.vy[s] = vy; B.vz[s] = vz; B.w[s] = w; B.id[s] = id;
+}
+
+// capacity check + totals of a packed (ions | electrons << 32) scan
+__global__ void k_check_new(DevClock *clk, const uint64_t *total, int64_t cap_i, int64_t cap_e, int *go) {
+  const uint64_t t = *total;
+  const int64_t ni = (int64_t)(t & 0xffffffffu), ne = (int64_t)(t >> 32);
+  const bool ok = clk->n[PIC_ION] + ni <= cap_i && clk->n[PIC_ELECTRON] + ne <= cap_e;
+  *go = ok ? 1 : 0;
+  if (!ok) atomicOr(&clk->err, kErrCapacity);
+}
+
+__global__ void k_commit_new(DevClock *clk, const uint64_t *total, const int *go, int ctr) {
+  if (!*go) return;
+  const uint64_t t = *total;
+  const int64_t ni = (int64_t)(t & 0xffffffffu), ne = (int64_t)(t >> 32);
+  clk->n[PIC_ION] += ni;
+  clk->n[PIC_ELECTRON] += ne;
+  clk->next_id += ni + ne;
+  clk->ctr[ctr] += ni;
+}
+
+__global__ void k_mcc_products(McArgs a, SpeciesBuf ions) {
+  if (!*a.go) return;
+  const int64_t ne = a.clk->n_sorted[PIC_ELECTRON], nn = a.clk->n_sorted[PIC_NEUTRAL];
+  const int64_t ne_all = a.clk->n[PIC_ELECTRON], ni = a.clk->n[PIC_ION];
+  const int64_t step = a.clk->step, id_base = a.clk->next_id;
+  const int64_t total = ne + nn;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int ncoll = a.pair_ncoll[t];
+    if (ncoll <= 0) continue;
+    Pair pr;
+    resolve_pair(a, t, ne, step, &pr);
+    const uint64_t off = a.pair_off[t];
+    const int64_t ion_off = (int64_t)(off & 0xffffffffu), e_off = (int64_t)(off >> 32);
+    int64_t id = id_base + ion_off + e_off;
+    const int64_t in = pr.in, ie = pr.ie;
+    const uint64_t pid = pr.proj_e ? a.e.id[ie] : a.n.id[in];
+    // ion with the neutral's position and velocity
+    put_sp(ions, ni + ion_off, a.n.x[in], a.n.y[in], a.n.z[in], a.n.vx[in], a.n.vy[in], a.n.vz[in], ncoll,
+           (uint64_t)id++);
+    a.n.w[in] -= ncoll;
+    // outgoing electrons: (E0 - xi)/2 each, directions by eq:du about u = v_e - v_n
+    const double vnx = a.n.vx[in], vny = a.n.vy[in], vnz = a.n.vz[in];
+    const double ux = (double)a.e.vx[ie] - vnx, uy = (double)a.e.vy[ie] - vny, uz = (double)a.e.vz[ie] - vnz;
+    const double u2 = __dadd_rn(__dadd_rn(__dmul_rn(ux, ux), __dmul_rn(uy, uy)), __dmul_rn(uz, uz));
+    const double E0 = 0.5 * kMe * u2 / kQe;
+    const double Ek = 0.5 * (E0 - kXiCu);
+    const double uk = sqrt(2.0 * Ek * kQe / kMe);
+    const U4 r = rng_block(a.seed, kScat, pid, step, 0);
+    double v1[3], v2[3];
+    scatter_velocity(ux, uy, uz, uk, 2.0 * u01d(r.v[0]) - 1.0, 2.0 * kPi * u01d(r.v[1]), v1);
+    scatter_velocity(ux, uy, uz, uk, 2.0 * u01d(r.v[2]) - 1.0, 2.0 * kPi * u01d(r.v[3]), v2);
+    const int we = a.e.w[ie];
+    int64_t slot = ne_all + e_off;
+    if (ncoll == we) {
+      a.e.vx[ie] = (float)(vnx + v1[0]); a.e.vy[ie] = (float)(vny + v1[1]); a.e.vz[ie] = (float)(vnz + v1[2]);
+    } else {
+      a.e.w[ie] = we - ncoll;
+      put_sp(a.e, slot++, a.e.x[ie], a.e.y[ie], a.e.z[ie], (float)(vnx + v1[0]), (float)(vny + v1[1]),
+             (float)(vnz + v1[2]), ncoll, (uint64_t)id++);
+    }
+    put_sp(a.e, slot, a.n.x[in], a.n.y[in], a.n.z[in], (float)(vnx + v2[0]), (float)(vny + v2[1]), (float)(vnz + v2[2]),
+           ncoll, (uint64_t)id);
+  }
+}
+
+// ---- direct field ionization -----------------------------------------------------------------
+struct DfiArgs {
+  SpeciesBuf n, e, ions;
+  const float4 *E;
+  int nx, ny;
+  double dt_fs, pre, c1, c2, expo, lim2;   // rate = pre (c1/E)^expo exp(-c2/E), E in GV/m
+  uint64_t seed;
+  DevClock *clk;
+  uint64_t *cnt, *off;
+  int32_t *nion;
+  int *go;
+};
+
+__global__ void k_dfi_count(DfiArgs a) {
+  const int64_t nn = a.clk->n[PIC_NEUTRAL];
+  const int64_t step = a.clk->step;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nn; t += (int64_t)gridDim.x * blockDim.x) {
+    const int w = a.n.w[t];
+    int k = 0;
+    if (w > 0) {
+      const float3 e = gather_E(a.E, a.n.x[t], a.n.y[t], a.n.z[t], a.nx, a.ny);
+      const double E2 = __dadd_rn(__dadd_rn(__dmul_rn((double)e.x, (double)e.x), __dmul_rn((double)e.y, (double)e.y)),
+                                  __dmul_rn((double)e.z, (double)e.z));
+      if (E2 > a.lim2) {
+        k = w;
+      } else if (E2 > 0.0) {
+        const float Eg = sqrtf((float)E2) * 1e-9f;
+        const float P32 = (float)a.pre * powf((float)a.c1 / Eg, (float)a.expo) * expf(-(float)a.c2 / Eg) * (float)a.dt_fs;
+        const float band = ldexpf(P32, -12);
+        const uint64_t id = a.n.id[t];
+        bool exact = false;
+        for (int i = 0; i < w; i += 4) {
+          const U4 r = rng_block(a.seed, kDfi, id, step, (uint32_t)(i >> 2));
+          for (int j = 0; j < 4 && i + j < w; ++j) {
+            const float U = u01f(r.v[j]);
+            if (fabsf(U - P32) <= band) exact = true;
+            k += U < P32;
+          }
+        }
+        if (exact) {
+          const double Ed = sqrt(E2) * 1e-9;
+          const double P64 = a.pre * pow(a.c1 / Ed, a.expo) * exp(-a.c2 / Ed) * a.dt_fs;
+          k = 0;
+          for (int i = 0; i < w; i += 4) {
+            const U4 r = rng_block(a.seed, kDfi, id, step, (uint32_t)(i >> 2));
+            for (int j = 0; j < 4 && i + j < w; ++j) k += u01d(r.v[j]) < P64;
+          }
+        }
+      }
+    }
+    a.nion[t] = k;
+    a.cnt[t] = k > 0 ? (1ull | (1ull << 32)) : 0ull;
+  }
+}
+
+__global__ void k_dfi_products(DfiArgs a) {
+  if (!*a.go) return;
+  const int64_t nn = a.clk->n[PIC_NEUTRAL], ne = a.clk->n[PIC_ELECTRON], ni = a.clk->n[PIC_ION];
+  const int64_t id_base = a.clk->next_id;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nn; t += (int64_t)gridDim.x * blockDim.x) {
+    const int k = a.nion[t];
+    if (k <= 0) continue;
+    const uint64_t off = a.off[t];
+    const int64_t io = (int64_t)(off & 0xffffffffu), eo = (int64_t)(off >> 32);
+    const int64_t id = id_base + io + eo;
+    put_sp(a.ions, ni + io, a.n.x[t], a.n.y[t], a.n.z[t], a.n.vx[t], a.n.vy[t], a.n.vz[t], k, (uint64_t)id);
+    put_sp(a.e, ne + eo, a.n.x[t], a.n.y[t], a.n.z[t], 0.f, 0.f, 0.f, k, (uint64_t)(id + 1));
+    a.n.w[t] -= k;
+  }
+}
+
+__global__ void k_set_len(int64_t *out, const DevClock *clk, int mode) {
+  // mode 0: sorted n_e + sorted n_n (MCC work items), mode 1: all neutrals
+  *out = mode == 0 ? clk->n_sorted[PIC_ELECTRON] + clk->n_sorted[PIC_NEUTRAL] : clk->n[PIC_NEUTRAL];
+}
+
+int stage_collide(pic_t *h) {
+  const uint32_t fl = h->prm.flags;
+  int *go = h->long_n + 4;
+  uint64_t *total = (uint64_t *)(h->tmp_len + 2);
+  const int grid = h->nsm * 8;
+  if (fl & PIC_F_IMPACT_ION) {
+    McArgs a;
+    a.e = h->sp[PIC_ELECTRON].a; a.n = h->sp[PIC_NEUTRAL].a;
+    a.off_e = h->sp[PIC_ELECTRON].off; a.off_n = h->sp[PIC_NEUTRAL].off;
+    a.nx = h->nx; a.ny = h->ny;
+    a.V_cell = h->dx * h->dx * h->dx; a.dt = h->prm.dt; a.w_min = h->prm.w_min; a.seed = h->prm.seed;
+    a.clk = h->clock; a.pair_cnt = h->pair_cnt; a.pair_off = h->pair_off; a.pair_ncoll = h->pair_ncoll; a.go = go;
+    k_mcc_count<<<grid, kThreads, 0, h->stream>>>(a);
+    k_set_len<<<1, 1, 0, h->stream>>>(h->tmp_len, h->clock, 0);
+    PIC_TRY(scan_u64(h, h->pair_cnt, h->pair_off, 0, h->tmp_len, total));
+    k_check_new<<<1, 1, 0, h->stream>>>(h->clock, total, h->sp[PIC_ION].cap, h->sp[PIC_ELECTRON].cap, go);
+    k_mcc_products<<<grid, kThreads, 0, h->stream>>>(a, h->sp[PIC_ION].a);
+    k_commit_new<<<1, 1, 0, h->stream>>>(h->clock, total, go, cImpactIon);
+    PIC_TRY(launch_check(h, "mcc"));
+  }
+  if (fl & PIC_F_DFI) {
+    DfiArgs d;
+    d.n = h->sp[PIC_NEUTRAL].a; d.e = h->sp[PIC_ELECTRON].a; d.ions = h->sp[PIC_ION].a;
+    d.E = h->E; d.nx = h->nx; d.ny = h->ny;
+    const double xi = kXiCu, nstar = 3.69 / sqrt(xi), x15 = pow(xi, 1.5);
+    d.pre = 1.52 * pow(4.0, nstar) * xi / (nstar * tgamma(2.0 * nstar));
+    d.c1 = 20.5 * x15; d.c2 = 6.83 * x15; d.expo = 2.0 * nstar - 1.0;
+    const double lim = 1.5 * x15 * 1e9;
+    d.lim2 = lim * lim;
+    d.dt_fs = h->prm.dt * 1e15; d.seed = h->prm.seed; d.clk = h->clock;
+    d.cnt = h->pair_cnt; d.off = h->pair_off; d.nion = h->pair_ncoll; d.go = go;
+    k_dfi_count<<<grid, kThreads, 0, h->stream>>>(d);
+    k_set_len<<<1, 1, 0, h->stream>>>(h->tmp_len, h->clock, 1);
+    PIC_TRY(scan_u64(h, h->pair_cnt, h->pair_off, 0, h->tmp_len, total));
+    k_check_new<<<1, 1, 0, h->stream>>>(h->clock, total, h->sp[PIC_ION].cap, h->sp[PIC_ELECTRON].cap, go);
+    k_dfi_products<<<grid, kThreads, 0, h->stream>>>(d);
+    k_commit_new<<<1, 1, 0, h->stream>>>(h->clock, total, go, cFieldIon);
+    PIC_TRY(launch_check(h, "dfi"));
+  }
+  return PIC_OK;
+}
+
+}  // namespace pic

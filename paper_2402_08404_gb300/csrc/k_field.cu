@@ -1,0 +1,330 @@
+// Poisson solve (eq:poi with eq:bcf1-3) by geometric multigrid and the node field E = -grad phi.
+//
+// Operator: (A u)_n = (6 u_n - sum of the 6 neighbours)/h^2 on free nodes, mirror images across
+// the lateral walls (zero normal field), Dirichlet nodes on the z = 0 and z = nz planes and on
+// every corner of a solid cell.  Charge density rho_n = Q_n e w_min 2^-30 / V_n with V_n = dx^3
+// halved on each lateral wall the node lies on.
+//
+// Solve: refinement loop in float64 -- r = f - A phi, stop when ||r||/||f_lifted|| < tol, else
+// one V-cycle on A e = r and phi += e.  The V-cycle runs in float32 (mixed form) or float64
+// (plain form): red-black Gauss-Seidel 2+2 sweeps, full-weighting restriction, trilinear
+// prolongation, a one-block smoother on the coarsest level.  Coarse Dirichlet masks are
+// injected from the fine nodes they coincide with.
+#include "pic_internal.cuh"
+
+namespace pic {
+
+template <typename T>
+__device__ __forceinline__ T nb_sum(const T *u, int i, int j, int k, int nx, int ny) {
+  const int im = i > 0 ? i - 1 : 1, ip = i < nx ? i + 1 : nx - 1;
+  const int jm = j > 0 ? j - 1 : 1, jp = j < ny ? j + 1 : ny - 1;
+  const int64_t sy = nx + 1, sz = (int64_t)(nx + 1) * (ny + 1);
+  const int64_t c = (int64_t)k * sz + (int64_t)j * sy;
+  return u[c + im] + u[c + ip] + u[(int64_t)k * sz + (int64_t)jm * sy + i] + u[(int64_t)k * sz + (int64_t)jp * sy + i] +
+         u[c - sz + i] + u[c + sz + i];
+}
+
+// one colour of red-black Gauss-Seidel on A u = f
+template <typename T>
+__global__ void k_smooth(T *u, const T *f, const uint8_t *dir, int nx, int ny, int nz, T h2, int color) {
+  const int half = (nx + 2) / 2;
+  const int64_t total = (int64_t)half * (ny + 1) * (nz + 1);
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int m = (int)(t % half);
+    const int64_t r = t / half;
+    const int j = (int)(r % (ny + 1)), k = (int)(r / (ny + 1));
+    const int i = 2 * m + ((j + k + color) & 1);
+    if (i > nx) continue;
+    const int64_t n = node_index(i, j, k, nx, ny);
+    if (dir[n]) continue;
+    u[n] = (nb_sum<T>(u, i, j, k, nx, ny) + h2 * f[n]) * (T)(1.0 / 6.0);
+  }
+}
+
+template <typename T>
+__global__ void k_residual(const T *u, const T *f, T *r, const uint8_t *dir, int nx, int ny, int nz, T inv_h2) {
+  const int64_t total = (int64_t)(nx + 1) * (ny + 1) * (nz + 1);
+  for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < total; n += (int64_t)gridDim.x * blockDim.x) {
+    if (dir[n]) { r[n] = 0; continue; }
+    const int i = (int)(n % (nx + 1));
+    const int64_t q = n / (nx + 1);
+    const int j = (int)(q % (ny + 1)), k = (int)(q / (ny + 1));
+    r[n] = f[n] - (6 * u[n] - nb_sum<T>(u, i, j, k, nx, ny)) * inv_h2;
+  }
+}
+
+__device__ __forceinline__ int mirror(int i, int n) { return i < 0 ? -i : (i > n ? 2 * n - i : i); }
+
+// full weighting of a fine residual onto the coarse right-hand side; coarse u cleared
+template <typename TF, typename TC>
+__global__ void k_restrict(const TF *rf, int nxf, int nyf, TC *fc, TC *uc, const uint8_t *dirc, int nxc, int nyc, int nzc) {
+  const int64_t total = (int64_t)(nxc + 1) * (nyc + 1) * (nzc + 1);
+  for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < total; n += (int64_t)gridDim.x * blockDim.x) {
+    uc[n] = 0;
+    if (dirc[n]) { fc[n] = 0; continue; }
+    const int I = (int)(n % (nxc + 1));
+    const int64_t q = n / (nxc + 1);
+    const int J = (int)(q % (nyc + 1)), K = (int)(q / (nyc + 1));
+    double s = 0.0;
+    for (int dk = -1; dk <= 1; ++dk) {
+      const double wk = dk == 0 ? 0.5 : 0.25;
+      const int k = 2 * K + dk;
+      for (int dj = -1; dj <= 1; ++dj) {
+        const double wj = dj == 0 ? 0.5 : 0.25;
+        const int j = mirror(2 * J + dj, nyf);
+        for (int di = -1; di <= 1; ++di) {
+          const double wi = di == 0 ? 0.5 : 0.25;
+          const int i = mirror(2 * I + di, nxf);
+          s += wk * wj * wi * (double)rf[node_index(i, j, k, nxf, nyf)];
+        }
+      }
+    }
+    fc[n] = (TC)s;
+  }
+}
+
+// trilinear prolongation of the coarse correction, added on free fine nodes
+template <typename TC, typename TF>
+__global__ void k_prolong(const TC *uc, int nxc, int nyc, TF *uf, const uint8_t *dirf, int nxf, int nyf, int nzf) {
+  const int64_t total = (int64_t)(nxf + 1) * (nyf + 1) * (nzf + 1);
+  for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < total; n += (int64_t)gridDim.x * blockDim.x) {
+    if (dirf[n]) continue;
+    const int i = (int)(n % (nxf + 1));
+    const int64_t q = n / (nxf + 1);
+    const int j = (int)(q % (nyf + 1)), k = (int)(q / (nyf + 1));
+    const int i0 = i >> 1, j0 = j >> 1, k0 = k >> 1;
+    const int i1 = i0 + (i & 1), j1 = j0 + (j & 1), k1 = k0 + (k & 1);
+    const double v = 0.125 * ((double)uc[node_index(i0, j0, k0, nxc, nyc)] + uc[node_index(i1, j0, k0, nxc, nyc)] +
+                              uc[node_index(i0, j1, k0, nxc, nyc)] + uc[node_index(i1, j1, k0, nxc, nyc)] +
+                              uc[node_index(i0, j0, k1, nxc, nyc)] + uc[node_index(i1, j0, k1, nxc, nyc)] +
+                              uc[node_index(i0, j1, k1, nxc, nyc)] + uc[node_index(i1, j1, k1, nxc, nyc)]);
+    uf[n] += (TF)v;
+  }
+}
+
+// many red-black sweeps on the (small) coarsest level inside one block
+template <typename T>
+__global__ void k_coarse(T *u, const T *f, const uint8_t *dir, int nx, int ny, int nz, T h2, int sweeps) {
+  const int64_t total = (int64_t)(nx + 1) * (ny + 1) * (nz + 1);
+  for (int s = 0; s < sweeps; ++s)
+    for (int color = 0; color < 2; ++color) {
+      for (int64_t n = threadIdx.x; n < total; n += blockDim.x) {
+        const int i = (int)(n % (nx + 1));
+        const int64_t q = n / (nx + 1);
+        const int j = (int)(q % (ny + 1)), k = (int)(q / (ny + 1));
+        if (((i + j + k) & 1) != color || dir[n]) continue;
+        u[n] = (nb_sum<T>(u, i, j, k, nx, ny) + h2 * f[n]) * (T)(1.0 / 6.0);
+      }
+      __syncthreads();
+    }
+}
+
+__global__ void k_inject_mask(const uint8_t *dirf, int nxf, int nyf, uint8_t *dirc, int nxc, int nyc, int nzc) {
+  const int64_t total = (int64_t)(nxc + 1) * (nyc + 1) * (nzc + 1);
+  for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < total; n += (int64_t)gridDim.x * blockDim.x) {
+    const int I = (int)(n % (nxc + 1));
+    const int64_t q = n / (nxc + 1);
+    const int J = (int)(q % (nyc + 1)), K = (int)(q / (nyc + 1));
+    dirc[n] = dirf[node_index(2 * I, 2 * J, 2 * K, nxf, nyf)];
+  }
+}
+
+// rho/eps0 from the fixed-point charge; Dirichlet values on the mask
+__global__ void k_rhs(const unsigned long long *Q, double *f, double *phi, const uint8_t *dir, int nx, int ny, int nz,
+                      double unit, double V0, int zero_charge) {
+  const int64_t total = (int64_t)(nx + 1) * (ny + 1) * (nz + 1);
+  for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < total; n += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(n % (nx + 1));
+    const int64_t q = n / (nx + 1);
+    const int j = (int)(q % (ny + 1)), k = (int)(q / (ny + 1));
+    const double vol = (i == 0 || i == nx ? 0.5 : 1.0) * (j == 0 || j == ny ? 0.5 : 1.0);
+    f[n] = zero_charge ? 0.0 : (double)(long long)Q[n] * unit / vol;
+    if (dir[n]) phi[n] = k == nz ? V0 : 0.0;
+  }
+}
+
+// residual of the FP64 system, the squared norm partials of r and of the lifted right-hand side
+__global__ void k_residual64(const double *phi, const double *f, double *r, const uint8_t *dir, int nx, int ny, int nz,
+                             double inv_h2, double V0, double *part, int lift) {
+  __shared__ double sh[2][32];
+  const int64_t total = (int64_t)(nx + 1) * (ny + 1) * (nz + 1);
+  double s = 0.0, sl = 0.0;
+  for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < total; n += (int64_t)gridDim.x * blockDim.x) {
+    if (dir[n]) { r[n] = 0.0; continue; }
+    const int i = (int)(n % (nx + 1));
+    const int64_t q = n / (nx + 1);
+    const int j = (int)(q % (ny + 1)), k = (int)(q / (ny + 1));
+    const double rr = f[n] - (6.0 * phi[n] - nb_sum<double>(phi, i, j, k, nx, ny)) * inv_h2;
+    r[n] = rr;
+    s += rr * rr;
+    if (lift) {
+      // f - A phi_D: only the anode plane carries a nonzero Dirichlet value
+      const double l = f[n] + (k == nz - 1 ? V0 * inv_h2 : 0.0);
+      sl += l * l;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    s += __shfl_down_sync(0xffffffffu, s, o);
+    sl += __shfl_down_sync(0xffffffffu, sl, o);
+  }
+  if ((threadIdx.x & 31) == 0) { sh[0][threadIdx.x >> 5] = s; sh[1][threadIdx.x >> 5] = sl; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { a += sh[0][w]; b += sh[1][w]; }
+    part[2 * blockIdx.x] = a;
+    part[2 * blockIdx.x + 1] = b;
+  }
+}
+
+__global__ void k_sum_partials(const double *part, int nb, double *out) {
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int i = 0; i < nb; ++i) { a += part[2 * i]; b += part[2 * i + 1]; }
+    out[0] = a;
+    out[1] = b;
+  }
+}
+
+template <typename T>
+__global__ void k_to_level(const double *r, T *f, T *u, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    f[i] = (T)r[i];
+    u[i] = 0;
+  }
+}
+
+template <typename T>
+__global__ void k_correct(double *phi, const T *u, const uint8_t *dir, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    if (!dir[i]) phi[i] += (double)u[i];
+}
+
+// E = -grad phi at every node, float64 differences rounded once to float32
+__global__ void k_efield(const double *phi, float4 *E, int nx, int ny, int nz, double inv2dx, double invdx) {
+  const int64_t total = (int64_t)(nx + 1) * (ny + 1) * (nz + 1);
+  const int64_t sy = nx + 1, sz = (int64_t)(nx + 1) * (ny + 1);
+  for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < total; n += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(n % (nx + 1));
+    const int64_t q = n / (nx + 1);
+    const int j = (int)(q % (ny + 1)), k = (int)(q / (ny + 1));
+    const int im = i > 0 ? i - 1 : 1, ip = i < nx ? i + 1 : nx - 1;
+    const int jm = j > 0 ? j - 1 : 1, jp = j < ny ? j + 1 : ny - 1;
+    const int64_t row = (int64_t)k * sz + (int64_t)j * sy;
+    float4 e;
+    e.x = __double2float_rn(__dmul_rn(__dsub_rn(phi[row + im], phi[row + ip]), inv2dx));
+    e.y = __double2float_rn(__dmul_rn(__dsub_rn(phi[(int64_t)k * sz + (int64_t)jm * sy + i], phi[(int64_t)k * sz + (int64_t)jp * sy + i]), inv2dx));
+    if (k == 0) e.z = __double2float_rn(__dmul_rn(__dsub_rn(phi[n], phi[n + sz]), invdx));
+    else if (k == nz) e.z = __double2float_rn(__dmul_rn(__dsub_rn(phi[n - sz], phi[n]), invdx));
+    else e.z = __double2float_rn(__dmul_rn(__dsub_rn(phi[n - sz], phi[n + sz]), inv2dx));
+    e.w = 0.f;
+    E[n] = e;
+  }
+}
+
+static int node_grid(pic_t *h, int64_t n) {
+  int64_t g = (n + kThreads - 1) / kThreads;
+  const int64_t cap = (int64_t)h->nsm * 16;
+  return (int)(g < 1 ? 1 : (g > cap ? cap : g));
+}
+
+template <typename T>
+static T *lvl_u(MgLevel &L);
+template <>
+float *lvl_u<float>(MgLevel &L) { return L.u; }
+template <>
+double *lvl_u<double>(MgLevel &L) { return L.ud; }
+template <typename T>
+static T *lvl_f(MgLevel &L);
+template <>
+float *lvl_f<float>(MgLevel &L) { return L.f; }
+template <>
+double *lvl_f<double>(MgLevel &L) { return L.fd; }
+template <typename T>
+static T *lvl_r(MgLevel &L);
+template <>
+float *lvl_r<float>(MgLevel &L) { return L.r; }
+template <>
+double *lvl_r<double>(MgLevel &L) { return L.rd; }
+
+template <typename T>
+static void vcycle(pic_t *h, int l) {
+  MgLevel &L = h->mg[l];
+  const T h2 = (T)(L.h * L.h), inv_h2 = (T)(1.0 / (L.h * L.h));
+  const int last = (int)h->mg.size() - 1;
+  if (l == last) {
+    k_coarse<T><<<1, 1024, 0, h->stream>>>(lvl_u<T>(L), lvl_f<T>(L), L.dir, L.nx, L.ny, L.nz, h2, 60);
+    return;
+  }
+  const int g = node_grid(h, L.nnode / 2 + 1);
+  for (int s = 0; s < 2; ++s)
+    for (int c = 0; c < 2; ++c) k_smooth<T><<<g, kThreads, 0, h->stream>>>(lvl_u<T>(L), lvl_f<T>(L), L.dir, L.nx, L.ny, L.nz, h2, c);
+  k_residual<T><<<node_grid(h, L.nnode), kThreads, 0, h->stream>>>(lvl_u<T>(L), lvl_f<T>(L), lvl_r<T>(L), L.dir, L.nx,
+                                                                 L.ny, L.nz, inv_h2);
+  MgLevel &Cl = h->mg[l + 1];
+  k_restrict<T, T><<<node_grid(h, Cl.nnode), kThreads, 0, h->stream>>>(lvl_r<T>(L), L.nx, L.ny, lvl_f<T>(Cl), lvl_u<T>(Cl),
+                                                                       Cl.dir, Cl.nx, Cl.ny, Cl.nz);
+  vcycle<T>(h, l + 1);
+  k_prolong<T, T><<<node_grid(h, L.nnode), kThreads, 0, h->stream>>>(lvl_u<T>(Cl), Cl.nx, Cl.ny, lvl_u<T>(L), L.dir, L.nx,
+                                                                     L.ny, L.nz);
+  for (int s = 0; s < 2; ++s)
+    for (int c = 1; c >= 0; --c) k_smooth<T><<<g, kThreads, 0, h->stream>>>(lvl_u<T>(L), lvl_f<T>(L), L.dir, L.nx, L.ny, L.nz, h2, c);
+}
+
+template <typename T>
+static void cycle_fine(pic_t *h) {
+  MgLevel &L = h->mg[0];
+  k_to_level<T><<<node_grid(h, L.nnode), kThreads, 0, h->stream>>>(h->res, lvl_f<T>(L), lvl_u<T>(L), L.nnode);
+  vcycle<T>(h, 0);
+  k_correct<T><<<node_grid(h, L.nnode), kThreads, 0, h->stream>>>(h->phi, lvl_u<T>(L), L.dir, L.nnode);
+}
+
+int stage_efield(pic_t *h) {
+  k_efield<<<node_grid(h, h->nnode), kThreads, 0, h->stream>>>(h->phi, h->E, h->nx, h->ny, h->nz, 1.0 / (2.0 * h->dx),
+                                                               1.0 / h->dx);
+  return launch_check(h, "efield");
+}
+
+int mg_build_masks(pic_t *h) {
+  for (size_t l = 1; l < h->mg.size(); ++l) {
+    MgLevel &F = h->mg[l - 1], &Cl = h->mg[l];
+    k_inject_mask<<<node_grid(h, Cl.nnode), kThreads, 0, h->stream>>>(F.dir, F.nx, F.ny, Cl.dir, Cl.nx, Cl.ny, Cl.nz);
+  }
+  return launch_check(h, "mg_masks");
+}
+
+// Solve for phi with the current deposited charge (or none), anode at V0.
+int stage_solve(pic_t *h, bool zero_charge, double V0) {
+  MgLevel &L = h->mg[0];
+  const double unit = kQe * h->prm.w_min / 1073741824.0 / (h->dx * h->dx * h->dx) / kEps0;
+  k_rhs<<<node_grid(h, L.nnode), kThreads, 0, h->stream>>>(h->Q, h->rhs, h->phi, L.dir, h->nx, h->ny, h->nz, unit, V0,
+                                                           zero_charge ? 1 : 0);
+  const int nb = node_grid(h, L.nnode);
+  const double inv_h2 = 1.0 / (h->dx * h->dx);
+  const bool mixed = (h->prm.flags & PIC_F_MIXED_MG) != 0;
+  double norms[2] = {0, 0};
+  double lifted = 0.0;
+  int cyc = 0;
+  for (;; ++cyc) {
+    k_residual64<<<nb, kThreads, 0, h->stream>>>(h->phi, h->rhs, h->res, L.dir, h->nx, h->ny, h->nz, inv_h2, V0, h->red,
+                                                 cyc == 0 ? 1 : 0);
+    k_sum_partials<<<1, 32, 0, h->stream>>>(h->red, nb, h->red_out);
+    PIC_CUDA(h, cudaMemcpyAsync(norms, h->red_out, sizeof norms, cudaMemcpyDeviceToHost, h->stream));
+    PIC_CUDA(h, cudaStreamSynchronize(h->stream));
+    if (cyc == 0) lifted = sqrt(norms[1]);
+    const double rel = lifted > 0 ? sqrt(norms[0]) / lifted : sqrt(norms[0]);
+    h->last_mg_res = rel;
+    h->last_mg_cycles = cyc;
+    if (rel <= h->prm.mg_tol) break;
+    if (cyc >= h->prm.mg_max_cycles) {
+      PIC_TRY(stage_efield(h));
+      return pic_fail(h, PIC_E_NOCONV, "Poisson solve: relative residual " + std::to_string(rel) + " after " +
+                                           std::to_string(cyc) + " cycles");
+    }
+    if (mixed) cycle_fine<float>(h);
+    else cycle_fine<double>(h);
+  }
+  return stage_efield(h);
+}
+
+}  // namespace pic

@@ -1,0 +1,334 @@
+// Particle kernels: gather + leapfrog push + boundary test (Sec. 2.2), stable cell sort,
+// fixed-point CIC charge deposit (density of eq:poi).
+//
+// Push arithmetic is float32 with every operation rounded on its own (no fused multiply-add),
+// in a fixed order: the new cell keys, boundary events and deposits are integer decisions
+// taken from the pushed positions, so the order is part of the definition.
+#include "pic_internal.cuh"
+#include "dev_common.cuh"
+
+namespace pic {
+
+enum Event { kEvNone = 0, kEvSolid = 1, kEvCathode = 2, kEvAnode = 3, kEvLateral = 4 };
+
+// First event along p0 -> p1 (FP64 traversal of the crossed cells, ties x < y < z).
+__device__ int first_event(const double p0[3], const double p1[3], const uint8_t *__restrict__ solid,
+                           int nx, int ny, int nz, int64_t *vcell_out, int *dcode_out) {
+  int c[3] = {(int)floor(p0[0]), (int)floor(p0[1]), (int)floor(p0[2])};
+  // end cell clamped to [-1, n]: leaving the domain is an event before any clamped cell
+  const int ce[3] = {(int)fmin(fmax(floor(p1[0]), -1.0), (double)nx), (int)fmin(fmax(floor(p1[1]), -1.0), (double)ny),
+                     (int)fmin(fmax(floor(p1[2]), -1.0), (double)nz)};
+  double d[3];
+  for (int a = 0; a < 3; ++a) d[a] = __dsub_rn(p1[a], p0[a]);
+  const int n[3] = {nx, ny, nz};
+  int guard = abs(ce[0] - c[0]) + abs(ce[1] - c[1]) + abs(ce[2] - c[2]) + 3;
+  while ((c[0] != ce[0] || c[1] != ce[1] || c[2] != ce[2]) && guard-- > 0) {
+    int best = -1;
+    double bt = 0.0;
+    for (int a = 0; a < 3; ++a) {
+      if (c[a] == ce[a]) continue;
+      const int bnd = ce[a] > c[a] ? c[a] + 1 : c[a];
+      const double t = __ddiv_rn(__dsub_rn((double)bnd, p0[a]), d[a]);
+      if (best < 0 || t < bt) { best = a; bt = t; }
+    }
+    const int step = ce[best] > c[best] ? 1 : -1;
+    const int64_t vcell = cell_index(c[0], c[1], c[2], nx, ny);
+    c[best] += step;
+    const int dcode = 2 * best + (step > 0 ? 1 : 0);
+    if (c[best] < 0 || c[best] >= n[best]) {
+      *vcell_out = vcell; *dcode_out = dcode;
+      if (best == 2) return step < 0 ? kEvCathode : kEvAnode;
+      return kEvLateral;
+    }
+    if (solid[cell_index(c[0], c[1], c[2], nx, ny)]) {
+      *vcell_out = vcell; *dcode_out = dcode;
+      return kEvSolid;
+    }
+  }
+  return kEvNone;
+}
+
+__device__ int64_t face_lookup(const int64_t *__restrict__ keys, int64_t n, int64_t key) {
+  int64_t lo = 0, hi = n;
+  while (lo < hi) {
+    int64_t mid = (lo + hi) >> 1;
+    if (keys[mid] < key) lo = mid + 1; else hi = mid;
+  }
+  return (lo < n && keys[lo] == key) ? lo : -1;
+}
+
+// Yamamura-type stand-in sputtering yield (the paper's fitted data is not available).
+__device__ double sputter_yield(double E) {
+  const double Q = 10.7, ETF = 11.9e3, Eth = 25.0;
+  if (E <= Eth) return 0.0;
+  const double eps = E / ETF, se = sqrt(eps);
+  const double sn = 3.441 * se * log(eps + 2.718) / (1.0 + 6.355 * se + eps * (6.882 * se - 1.708));
+  const double t = 1.0 - sqrt(Eth / E);
+  return Q * sn * (t * t * sqrt(t));
+}
+
+struct PushArgs {
+  SpeciesBuf p;
+  uint32_t *key, *cnt;
+  const float4 *E;
+  const uint8_t *solid, *cheb;
+  int nx, ny, nz;
+  float qmdt, dtdx;
+  int charged, ion, species;
+  double mass, w_min;
+  const int64_t *face_key;
+  int64_t nface;
+  unsigned long long *acc_sput, *acc_Eb;
+  DevClock *clk;
+};
+
+__global__ void __launch_bounds__(256) k_push(PushArgs a) {
+  const int64_t n = a.clk->n[a.species];
+  int removed = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t w = a.p.w[i];
+    if (w <= 0) { a.key[i] = kDead; continue; }
+    const float x = a.p.x[i], y = a.p.y[i], z = a.p.z[i];
+    float vx = a.p.vx[i], vy = a.p.vy[i], vz = a.p.vz[i];
+    if (a.charged) {
+      const float3 e = gather_E(a.E, x, y, z, a.nx, a.ny);
+      vx = __fadd_rn(vx, __fmul_rn(a.qmdt, e.x));
+      vy = __fadd_rn(vy, __fmul_rn(a.qmdt, e.y));
+      vz = __fadd_rn(vz, __fmul_rn(a.qmdt, e.z));
+    }
+    const float x1 = __fadd_rn(x, __fmul_rn(vx, a.dtdx));
+    const float y1 = __fadd_rn(y, __fmul_rn(vy, a.dtdx));
+    const float z1 = __fadd_rn(z, __fmul_rn(vz, a.dtdx));
+    a.p.x[i] = x1; a.p.y[i] = y1; a.p.z[i] = z1;
+    a.p.vx[i] = vx; a.p.vy[i] = vy; a.p.vz[i] = vz;
+    const int i0 = (int)floorf(x), j0 = (int)floorf(y), k0 = (int)floorf(z);
+    bool alive = isfinite(x1) && isfinite(y1) && isfinite(z1);
+    int i1 = 0, j1 = 0, k1 = 0;
+    if (alive) {
+      i1 = (int)fminf(fmaxf(floorf(x1), -1.f), (float)a.nx);
+      j1 = (int)fminf(fmaxf(floorf(y1), -1.f), (float)a.ny);
+      k1 = (int)fminf(fmaxf(floorf(z1), -1.f), (float)a.nz);
+      if (i1 != i0 || j1 != j0 || k1 != k0) {
+        const int m = max(abs(i1 - i0), max(abs(j1 - j0), abs(k1 - k0)));
+        const bool inside = i1 >= 0 && i1 < a.nx && j1 >= 0 && j1 < a.ny && k1 >= 0 && k1 < a.nz;
+        const bool clear = inside && (int)a.cheb[cell_index(i0, j0, k0, a.nx, a.ny)] > m;
+        if (!clear) {
+          const double p0[3] = {(double)x, (double)y, (double)z};
+          const double p1[3] = {(double)x1, (double)y1, (double)z1};
+          int64_t vcell = -1;
+          int dcode = -1;
+          const int ev = first_event(p0, p1, a.solid, a.nx, a.ny, a.nz, &vcell, &dcode);
+          if (ev != kEvNone) {
+            alive = false;
+            if (a.ion && (ev == kEvSolid || ev == kEvCathode)) {
+              const int64_t f = face_lookup(a.face_key, a.nface, vcell * 6 + dcode);
+              if (f >= 0) {
+                const double v2 = __dadd_rn(__dadd_rn(__dmul_rn((double)vx, (double)vx), __dmul_rn((double)vy, (double)vy)),
+                                            __dmul_rn((double)vz, (double)vz));
+                const double energy = 0.5 * a.mass * v2 / kQe;
+                const double ww = (double)w * a.w_min;
+                atomicAdd(&a.acc_sput[f], (unsigned long long)(int64_t)floor(ww * sputter_yield(energy) * 16777216.0));
+                atomicAdd(&a.acc_Eb[f], (unsigned long long)(int64_t)floor(ww * energy * 1048576.0));
+                atomicAdd((unsigned long long *)&a.clk->ctr[cIonImpacts], 1ull);
+              }
+            }
+          }
+        }
+      }
+    }
+    if (alive) {
+      const uint32_t c = (uint32_t)cell_index(i1, j1, k1, a.nx, a.ny);
+      a.key[i] = c;
+      atomicAdd(&a.cnt[c], 1u);
+    } else {
+      a.key[i] = kDead;
+      ++removed;
+    }
+  }
+  // one atomic per warp for the removal counter
+  for (int o = 16; o > 0; o >>= 1) removed += __shfl_down_sync(0xffffffffu, removed, o);
+  if ((threadIdx.x & 31) == 0 && removed)
+    atomicAdd((unsigned long long *)&a.clk->ctr[cRemovedE + a.species], (unsigned long long)removed);
+}
+
+// Keys without a push (after loading): cell of each SP, kDead for w <= 0.
+__global__ void k_keys(SpeciesBuf p, uint32_t *key, uint32_t *cnt, int nx, int ny, const DevClock *clk, int s) {
+  const int64_t n = clk->n[s];
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    if (p.w[i] <= 0) { key[i] = kDead; continue; }
+    const uint32_t c = (uint32_t)cell_index((int)floorf(p.x[i]), (int)floorf(p.y[i]), (int)floorf(p.z[i]), nx, ny);
+    key[i] = c;
+    atomicAdd(&cnt[c], 1u);
+  }
+}
+
+__global__ void k_scatter(const uint32_t *__restrict__ key, uint32_t *cnt, const uint32_t *__restrict__ off,
+                          uint32_t *perm, const DevClock *clk, int s) {
+  const int64_t n = clk->n[s];
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t k = key[i];
+    if (k == kDead) continue;
+    const uint32_t r = atomicSub(&cnt[k], 1u) - 1u;
+    perm[off[k] + r] = (uint32_t)i;
+  }
+}
+
+// Restore source order inside every cell segment (the scatter order is arbitrary): short
+// segments are insertion-sorted by their head thread, long ones are queued for k_fix_long.
+__global__ void k_fix_short(const uint32_t *__restrict__ key, const uint32_t *__restrict__ off, uint32_t *perm,
+                            int64_t ncell, int2 *long_list, int *long_n, int long_cap, DevClock *clk) {
+  const int64_t n = off[ncell];
+  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t k = key[perm[s]];
+    if (off[k] != (uint32_t)s) continue;
+    const int len = (int)(off[k + 1] - (uint32_t)s);
+    if (len <= 1) continue;
+    if (len <= 32) {
+      for (int a = 1; a < len; ++a) {
+        const uint32_t v = perm[s + a];
+        int b = a - 1;
+        while (b >= 0 && perm[s + b] > v) { perm[s + b + 1] = perm[s + b]; --b; }
+        perm[s + b + 1] = v;
+      }
+    } else if (len <= kMaxSegment) {
+      const int q = atomicAdd(long_n, 1);
+      if (q < long_cap) long_list[q] = make_int2((int)s, len);
+      else atomicOr(&clk->err, kErrSegment);
+    } else {
+      atomicOr(&clk->err, kErrSegment);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_fix_long(uint32_t *perm, const int2 *long_list, const int *long_n, int long_cap) {
+  __shared__ uint32_t sh[kMaxSegment];
+  const int nl = min(*long_n, long_cap);
+  for (int q = blockIdx.x; q < nl; q += gridDim.x) {
+    const int2 seg = long_list[q];
+    int P = 1;
+    while (P < seg.y) P <<= 1;
+    for (int t = threadIdx.x; t < P; t += blockDim.x) sh[t] = t < seg.y ? perm[seg.x + t] : 0xFFFFFFFFu;
+    __syncthreads();
+    for (int kk = 2; kk <= P; kk <<= 1) {
+      for (int jj = kk >> 1; jj > 0; jj >>= 1) {
+        for (int t = threadIdx.x; t < P; t += blockDim.x) {
+          const int ixj = t ^ jj;
+          if (ixj > t) {
+            const bool up = (t & kk) == 0;
+            const uint32_t a = sh[t], b = sh[ixj];
+            if ((a > b) == up) { sh[t] = b; sh[ixj] = a; }
+          }
+        }
+        __syncthreads();
+      }
+    }
+    for (int t = threadIdx.x; t < seg.y; t += blockDim.x) perm[seg.x + t] = sh[t];
+    __syncthreads();
+  }
+}
+
+__global__ void k_gather(SpeciesBuf src, SpeciesBuf dst, const uint32_t *__restrict__ perm, const uint32_t *off,
+                         int64_t ncell) {
+  const int64_t n = off[ncell];
+  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t q = perm[s];
+    dst.x[s] = src.x[q]; dst.y[s] = src.y[q]; dst.z[s] = src.z[q];
+    dst.vx[s] = src.vx[q]; dst.vy[s] = src.vy[q]; dst.vz[s] = src.vz[q];
+    dst.w[s] = src.w[q]; dst.id[s] = src.id[q];
+  }
+}
+
+__global__ void k_set_count(DevClock *clk, int s, const uint32_t *off, int64_t ncell) {
+  clk->n[s] = off[ncell];
+  clk->n_sorted[s] = off[ncell];
+}
+
+// Cloud-in-cell deposit with quantised fractions: q = floor(frac(x) 2^F), weights 2^F - q on
+// the lower node and q on the upper node per axis; Z w prod(W) added as int64 (exact, order-free).
+__global__ void __launch_bounds__(256) k_deposit(SpeciesBuf p, int Z, unsigned long long *Q, int nx, int ny,
+                                                 const DevClock *clk, int s) {
+  const int64_t n = clk->n[s];
+  const int64_t sy = nx + 1, sz = (int64_t)(nx + 1) * (ny + 1);
+  const int one = 1 << kFracBits;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t w = p.w[i];
+    if (w <= 0) continue;
+    const float x = p.x[i], y = p.y[i], z = p.z[i];
+    const float fi = floorf(x), fj = floorf(y), fk = floorf(z);
+    const int qx = (int)floorf(__fsub_rn(x, fi) * (float)one);
+    const int qy = (int)floorf(__fsub_rn(y, fj) * (float)one);
+    const int qz = (int)floorf(__fsub_rn(z, fk) * (float)one);
+    const int64_t base = (int64_t)fk * sz + (int64_t)fj * sy + (int64_t)fi;
+    const int64_t zw = (int64_t)Z * w;
+    const int64_t wx0 = one - qx, wy0 = one - qy, wz0 = one - qz;
+    const int64_t a00 = zw * wz0 * wy0, a10 = zw * wz0 * qy, a01 = zw * qz * wy0, a11 = zw * qz * qy;
+    atomicAdd(Q + base, (unsigned long long)(a00 * wx0));
+    atomicAdd(Q + base + 1, (unsigned long long)(a00 * qx));
+    atomicAdd(Q + base + sy, (unsigned long long)(a10 * wx0));
+    atomicAdd(Q + base + sy + 1, (unsigned long long)(a10 * qx));
+    atomicAdd(Q + base + sz, (unsigned long long)(a01 * wx0));
+    atomicAdd(Q + base + sz + 1, (unsigned long long)(a01 * qx));
+    atomicAdd(Q + base + sz + sy, (unsigned long long)(a11 * wx0));
+    atomicAdd(Q + base + sz + sy + 1, (unsigned long long)(a11 * qx));
+  }
+}
+
+static int particle_grid(pic_t *h) { return h->nsm * 8; }
+
+int stage_keys(pic_t *h, int s) {
+  Species &S = h->sp[s];
+  if (h->keys_valid[s]) PIC_CUDA(h, cudaMemsetAsync(S.cnt, 0, (h->ncell + 1) * sizeof(uint32_t), h->stream));
+  k_keys<<<particle_grid(h), kThreads, 0, h->stream>>>(S.a, S.key, S.cnt, h->nx, h->ny, h->clock, s);
+  h->keys_valid[s] = true;
+  return launch_check(h, "keys");
+}
+
+int stage_push(pic_t *h) {
+  for (int s = 0; s < 3; ++s) {
+    Species &S = h->sp[s];
+    if (h->keys_valid[s]) PIC_CUDA(h, cudaMemsetAsync(S.cnt, 0, (h->ncell + 1) * sizeof(uint32_t), h->stream));
+    PushArgs a;
+    a.p = S.a; a.key = S.key; a.cnt = S.cnt; a.E = h->E; a.solid = h->solid; a.cheb = h->cheb;
+    a.nx = h->nx; a.ny = h->ny; a.nz = h->nz; a.qmdt = S.qmdt;
+    a.dtdx = (float)(h->prm.dt / h->dx);
+    a.charged = S.Z != 0; a.ion = s == PIC_ION; a.species = s;
+    a.mass = S.mass; a.w_min = h->prm.w_min;
+    a.face_key = h->faces.key; a.nface = h->faces.n;
+    a.acc_sput = (unsigned long long *)h->faces.acc_sput; a.acc_Eb = (unsigned long long *)h->faces.acc_Eb;
+    a.clk = h->clock;
+    k_push<<<particle_grid(h), kThreads, 0, h->stream>>>(a);
+    h->keys_valid[s] = true;
+  }
+  return launch_check(h, "push");
+}
+
+int stage_sort(pic_t *h) {
+  int2 *long_list = h->long_list;
+  int *long_n = h->long_n;
+  const int long_cap = kLongCap;
+  for (int s = 0; s < 3; ++s) {
+    Species &S = h->sp[s];
+    if (!h->keys_valid[s]) PIC_TRY(stage_keys(h, s));
+    PIC_TRY(scan_u32(h, S.cnt, S.off, h->ncell, nullptr, S.off + h->ncell));
+    k_scatter<<<particle_grid(h), kThreads, 0, h->stream>>>(S.key, S.cnt, S.off, S.perm, h->clock, s);
+    PIC_CUDA(h, cudaMemsetAsync(long_n, 0, sizeof(int), h->stream));
+    k_fix_short<<<particle_grid(h), kThreads, 0, h->stream>>>(S.key, S.off, S.perm, h->ncell, long_list, long_n,
+                                                              long_cap, h->clock);
+    k_fix_long<<<h->nsm, 1024, 0, h->stream>>>(S.perm, long_list, long_n, long_cap);
+    k_gather<<<particle_grid(h), kThreads, 0, h->stream>>>(S.a, S.b, S.perm, S.off, h->ncell);
+    k_set_count<<<1, 1, 0, h->stream>>>(h->clock, s, S.off, h->ncell);
+    std::swap(S.a, S.b);
+    h->keys_valid[s] = false;
+  }
+  return launch_check(h, "sort");
+}
+
+int stage_deposit(pic_t *h) {
+  PIC_CUDA(h, cudaMemsetAsync(h->Q, 0, h->nnode * sizeof(unsigned long long), h->stream));
+  k_deposit<<<particle_grid(h), kThreads, 0, h->stream>>>(h->sp[PIC_ELECTRON].a, -1, h->Q, h->nx, h->ny, h->clock,
+                                                          PIC_ELECTRON);
+  k_deposit<<<particle_grid(h), kThreads, 0, h->stream>>>(h->sp[PIC_ION].a, 1, h->Q, h->nx, h->ny, h->clock, PIC_ION);
+  return launch_check(h, "deposit");
+}
+
+}  // namespace pic

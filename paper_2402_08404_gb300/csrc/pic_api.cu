@@ -1,0 +1,773 @@
+// C ABI of libpic (declared in include/pic.h): handle creation, geometry and face list, state
+// I/O, stage sequencing of the coupled step (Sec. 2.3.1, Fig. newpic) and diagnostics.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <unordered_map>
+#include <vector>
+
+#include "pic_internal.cuh"
+
+int pic_fail(pic_t *h, int code, const std::string &msg) {
+  if (h) h->last_error = msg;
+  return code;
+}
+
+namespace pic {
+
+int emission_tables_upload(pic_t *h);
+int mg_build_masks(pic_t *h);
+
+void *dalloc(pic_t *h, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  void *p = nullptr;
+  if (h->alloc) {
+    p = h->alloc(bytes, (void *)h->stream, h->alloc_user);
+  } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    p = nullptr;
+  }
+  if (p) h->allocations.push_back({p, bytes});
+  return p;
+}
+
+static void dfree_all(pic_t *h) {
+  for (auto &a : h->allocations) {
+    if (h->free_fn) h->free_fn(a.first, a.second, (void *)h->stream, h->alloc_user);
+    else cudaFree(a.first);
+  }
+  h->allocations.clear();
+}
+
+int launch_check(pic_t *h, const char *what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return pic_fail(h, PIC_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+  return PIC_OK;
+}
+
+// ---- host geometry (same rules as the statement in pic.h) -----------------------------------
+struct HostGeom {
+  std::vector<uint8_t> solid, cheb, dir0;
+  std::vector<int32_t> fvcell, fowner, fowner_vox;
+  std::vector<int8_t> fdir;
+  std::vector<int64_t> fkey;
+  std::vector<int32_t> vox_cell, vox_nbr;
+  std::vector<uint8_t> vox_base;
+  std::vector<int64_t> apex;
+};
+
+static void build_geometry(pic_t *h, HostGeom &G) {
+  const int nx = h->nx, ny = h->ny, nz = h->nz;
+  const double rc = h->geo.tip_radius / h->dx, hc = h->geo.tip_height / h->dx;
+  const double ax = nx / 2.0, ay = ny / 2.0, zc = hc - rc;
+  G.solid.assign(h->ncell, 0);
+  int kmax = std::min(nz, (int)ceil(hc) + 1);
+  for (int k = 0; k < kmax; ++k)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        const double cx = i + 0.5, cy = j + 0.5, cz = k + 0.5;
+        const double rho2 = (cx - ax) * (cx - ax) + (cy - ay) * (cy - ay);
+        const bool shaft = rho2 <= rc * rc && cz <= zc;
+        const bool cap = rho2 + (cz - zc) * (cz - zc) <= rc * rc;
+        if (shaft || cap) G.solid[cell_index(i, j, k, nx, ny)] = 1;
+      }
+  // voxels (solid cells in linear order)
+  std::unordered_map<int64_t, int32_t> vid;
+  for (int64_t c = 0; c < h->ncell; ++c)
+    if (G.solid[c]) {
+      vid[c] = (int32_t)G.vox_cell.size();
+      G.vox_cell.push_back((int32_t)c);
+    }
+  const int D[6][3] = {{-1, 0, 0}, {1, 0, 0}, {0, -1, 0}, {0, 1, 0}, {0, 0, -1}, {0, 0, 1}};
+  for (size_t v = 0; v < G.vox_cell.size(); ++v) {
+    const int64_t c = G.vox_cell[v];
+    const int i = (int)(c % nx), j = (int)((c / nx) % ny), k = (int)(c / ((int64_t)nx * ny));
+    G.vox_base.push_back(k == 0);
+    for (int d = 0; d < 6; ++d) {
+      const int a = i + D[d][0], b = j + D[d][1], e = k + D[d][2];
+      int32_t u = -1;
+      if (a >= 0 && a < nx && b >= 0 && b < ny && e >= 0 && e < nz) {
+        auto it = vid.find(cell_index(a, b, e, nx, ny));
+        if (it != vid.end()) u = it->second;
+      }
+      G.vox_nbr.push_back(u);
+    }
+  }
+  // exposed faces: vacuum cells in linear order, directions -x,+x,-y,+y,-z,+z
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        const int64_t c = cell_index(i, j, k, nx, ny);
+        if (G.solid[c]) continue;
+        for (int d = 0; d < 6; ++d) {
+          const int a = i + D[d][0], b = j + D[d][1], e = k + D[d][2];
+          int64_t own = -2;
+          if (d == 4 && k == 0) own = -1;
+          else if (a >= 0 && a < nx && b >= 0 && b < ny && e >= 0 && e < nz && G.solid[cell_index(a, b, e, nx, ny)])
+            own = cell_index(a, b, e, nx, ny);
+          if (own == -2) continue;
+          G.fvcell.push_back((int32_t)c);
+          G.fdir.push_back((int8_t)d);
+          G.fowner.push_back((int32_t)own);
+          G.fowner_vox.push_back(own >= 0 ? vid[own] : -1);
+          G.fkey.push_back(c * 6 + d);
+        }
+      }
+  // apex faces: +z tip faces of the highest owner cells touching the axis
+  const int ai = (int)floor(ax), aj = (int)floor(ay);
+  int top = -1;
+  for (size_t f = 0; f < G.fvcell.size(); ++f) {
+    if (G.fdir[f] != 4 || G.fowner[f] < 0) continue;
+    const int64_t o = G.fowner[f];
+    const int oi = (int)(o % nx), oj = (int)((o / nx) % ny), ok = (int)(o / ((int64_t)nx * ny));
+    if ((oi == ai - 1 || oi == ai) && (oj == aj - 1 || oj == aj)) top = std::max(top, ok);
+  }
+  for (size_t f = 0; f < G.fvcell.size(); ++f) {
+    if (G.fdir[f] != 4 || G.fowner[f] < 0) continue;
+    const int64_t o = G.fowner[f];
+    const int oi = (int)(o % nx), oj = (int)((o / nx) % ny), ok = (int)(o / ((int64_t)nx * ny));
+    if ((oi == ai - 1 || oi == ai) && (oj == aj - 1 || oj == aj) && ok == top) G.apex.push_back((int64_t)f);
+  }
+  // Dirichlet nodes: z = 0, z = nz, corners of solid cells
+  G.dir0.assign(h->nnode, 0);
+  for (int j = 0; j <= ny; ++j)
+    for (int i = 0; i <= nx; ++i) {
+      G.dir0[node_index(i, j, 0, nx, ny)] = 1;
+      G.dir0[node_index(i, j, nz, nx, ny)] = 1;
+    }
+  for (int32_t c : G.vox_cell) {
+    const int i = c % nx, j = (c / nx) % ny, k = c / (nx * ny);
+    for (int dk = 0; dk < 2; ++dk)
+      for (int dj = 0; dj < 2; ++dj)
+        for (int di = 0; di < 2; ++di) G.dir0[node_index(i + di, j + dj, k + dk, nx, ny)] = 1;
+  }
+  // Chebyshev distance to the nearest solid cell, capped at 8, by dilation inside the tip box
+  const int cap = 8;
+  G.cheb.assign(h->ncell, 255);
+  if (!G.vox_cell.empty()) {
+    int lo[3] = {nx, ny, nz}, hi[3] = {-1, -1, -1};
+    for (int32_t c : G.vox_cell) {
+      const int q[3] = {c % nx, (c / nx) % ny, c / (nx * ny)};
+      for (int a = 0; a < 3; ++a) { lo[a] = std::min(lo[a], q[a]); hi[a] = std::max(hi[a], q[a]); }
+    }
+    const int n3[3] = {nx, ny, nz};
+    for (int a = 0; a < 3; ++a) { lo[a] = std::max(0, lo[a] - cap); hi[a] = std::min(n3[a] - 1, hi[a] + cap); }
+    for (int32_t c : G.vox_cell) G.cheb[c] = 0;
+    for (int r = 1; r <= cap; ++r)
+      for (int k = lo[2]; k <= hi[2]; ++k)
+        for (int j = lo[1]; j <= hi[1]; ++j)
+          for (int i = lo[0]; i <= hi[0]; ++i) {
+            const int64_t c = cell_index(i, j, k, nx, ny);
+            if (G.cheb[c] != 255) continue;
+            bool hit = false;
+            for (int dk = -1; dk <= 1 && !hit; ++dk)
+              for (int dj = -1; dj <= 1 && !hit; ++dj)
+                for (int di = -1; di <= 1 && !hit; ++di) {
+                  const int a = i + di, b = j + dj, e = k + dk;
+                  if (a < 0 || a >= nx || b < 0 || b >= ny || e < 0 || e >= nz) continue;
+                  if (G.cheb[cell_index(a, b, e, nx, ny)] == r - 1) hit = true;
+                }
+            if (hit) G.cheb[c] = (uint8_t)r;
+          }
+    // cells of the box left at 255 are farther than cap: keep 255 (> any cap test)
+  }
+}
+
+template <typename T>
+static T *alloc_n(pic_t *h, int64_t n) {
+  return (T *)dalloc(h, (size_t)std::max<int64_t>(n, 1) * sizeof(T));
+}
+
+}  // namespace pic
+
+using namespace pic;
+
+extern "C" {
+
+const char *pic_last_error(pic_t *h) { return h ? h->last_error.c_str() : "null handle"; }
+
+void pic_destroy(pic_t *h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->stream);
+  dfree_all(h);
+  delete h;
+}
+
+static int clock_sync(pic_t *h, DevClock *out) {
+  PIC_CUDA(h, cudaMemcpyAsync(out, h->clock, sizeof(DevClock), cudaMemcpyDeviceToHost, h->stream));
+  PIC_CUDA(h, cudaStreamSynchronize(h->stream));
+  return PIC_OK;
+}
+
+static int check_err(pic_t *h) {
+  DevClock c;
+  PIC_TRY(clock_sync(h, &c));
+  if (c.err) {
+    const int e = c.err;
+    int zero = 0;
+    PIC_CUDA(h, cudaMemcpyAsync(&h->clock->err, &zero, sizeof(int), cudaMemcpyHostToDevice, h->stream));
+    PIC_CUDA(h, cudaStreamSynchronize(h->stream));
+    if (e & kErrCapacity) return pic_fail(h, PIC_E_CAPACITY, "SP capacity exceeded: new SPs were not added");
+    if (e & kErrSegment) return pic_fail(h, PIC_E_CAPACITY, "more SPs of one species in one cell than the sort handles");
+    return pic_fail(h, PIC_E_INVALID, "device error flag " + std::to_string(e));
+  }
+  return PIC_OK;
+}
+
+__global__ void k_scale(double *phi, int64_t n, double s) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) phi[i] *= s;
+}
+
+int pic_create(const pic_geometry_t *geometry, const pic_grid_t *grid, const pic_species_t *species, int nspecies,
+               const pic_params_t *params, pic_alloc_fn alloc, pic_free_fn free_fn, void *alloc_user, void *stream,
+               pic_t **out) {
+  if (!geometry || !grid || !species || !params || !out || nspecies != PIC_NSPECIES) return PIC_E_INVALID;
+  *out = nullptr;
+  if (grid->nx < 8 || grid->ny < 8 || grid->nz < 8 || (grid->nx & 1) || (grid->ny & 1) || (grid->nz & 1) || !(grid->dx > 0))
+    return PIC_E_INVALID;
+  if ((int64_t)grid->nx * grid->ny * grid->nz >= (int64_t)0xFFFFFFF0u) return PIC_E_INVALID;
+  if (!(params->dt > 0) || !(params->w_min > 0) || params->w_max_units < 1) return PIC_E_INVALID;
+  for (int s = 0; s < 3; ++s)
+    if (species[s].capacity < 1 || species[s].capacity > 0x7FFFFFFF || !(species[s].mass > 0)) return PIC_E_INVALID;
+  pic_t *h = new pic_t();
+  h->nx = grid->nx; h->ny = grid->ny; h->nz = grid->nz; h->dx = grid->dx;
+  h->ncell = (int64_t)h->nx * h->ny * h->nz;
+  h->nnode = (int64_t)(h->nx + 1) * (h->ny + 1) * (h->nz + 1);
+  h->geo = *geometry; h->prm = *params;
+  if (h->prm.mg_tol <= 0) h->prm.mg_tol = 1e-8;
+  if (h->prm.mg_max_cycles <= 0) h->prm.mg_max_cycles = 50;
+  h->stream = (cudaStream_t)stream;
+  h->alloc = alloc; h->free_fn = free_fn; h->alloc_user = alloc_user;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (h->nsm <= 0) h->nsm = 148;
+  auto fail = [&](int code, const std::string &m) {
+    std::string msg = m;
+    pic_destroy(h);
+    (void)msg;
+    return code;
+  };
+  HostGeom G;
+  build_geometry(h, G);
+  bool okalloc = true;
+  auto A = [&](void *p) { if (!p) okalloc = false; };
+  // grids
+  h->solid = alloc_n<uint8_t>(h, h->ncell); A(h->solid);
+  h->cheb = alloc_n<uint8_t>(h, h->ncell); A(h->cheb);
+  h->phi = alloc_n<double>(h, h->nnode); A(h->phi);
+  h->rhs = alloc_n<double>(h, h->nnode); A(h->rhs);
+  h->res = alloc_n<double>(h, h->nnode); A(h->res);
+  h->E = alloc_n<float4>(h, h->nnode); A(h->E);
+  h->Q = alloc_n<unsigned long long>(h, h->nnode); A(h->Q);
+  // multigrid hierarchy
+  {
+    int lx = h->nx, ly = h->ny, lz = h->nz;
+    double hh = h->dx;
+    for (;;) {
+      MgLevel L;
+      L.nx = lx; L.ny = ly; L.nz = lz; L.h = hh;
+      L.nnode = (int64_t)(lx + 1) * (ly + 1) * (lz + 1);
+      L.dir = alloc_n<uint8_t>(h, L.nnode); A(L.dir);
+      L.u = alloc_n<float>(h, L.nnode); A(L.u);
+      L.f = alloc_n<float>(h, L.nnode); A(L.f);
+      L.r = alloc_n<float>(h, L.nnode); A(L.r);
+      L.ud = alloc_n<double>(h, L.nnode); A(L.ud);
+      L.fd = alloc_n<double>(h, L.nnode); A(L.fd);
+      L.rd = alloc_n<double>(h, L.nnode); A(L.rd);
+      h->mg.push_back(L);
+      if ((lx & 1) || (ly & 1) || (lz & 1) || std::min(lx, std::min(ly, lz)) < 8) break;
+      lx /= 2; ly /= 2; lz /= 2; hh *= 2.0;
+    }
+  }
+  // species
+  int64_t capsum = 0;
+  for (int s = 0; s < 3; ++s) {
+    Species &S = h->sp[s];
+    S.Z = species[s].charge_e;
+    S.mass = species[s].mass;
+    S.cap = species[s].capacity;
+    S.qmdt = (float)((double)S.Z * kQe / S.mass * h->prm.dt);
+    for (SpeciesBuf *B : {&S.a, &S.b}) {
+      B->x = alloc_n<float>(h, S.cap); A(B->x);
+      B->y = alloc_n<float>(h, S.cap); A(B->y);
+      B->z = alloc_n<float>(h, S.cap); A(B->z);
+      B->vx = alloc_n<float>(h, S.cap); A(B->vx);
+      B->vy = alloc_n<float>(h, S.cap); A(B->vy);
+      B->vz = alloc_n<float>(h, S.cap); A(B->vz);
+      B->w = alloc_n<int32_t>(h, S.cap); A(B->w);
+      B->id = alloc_n<uint64_t>(h, S.cap); A(B->id);
+    }
+    S.key = alloc_n<uint32_t>(h, S.cap); A(S.key);
+    S.perm = alloc_n<uint32_t>(h, S.cap); A(S.perm);
+    S.cnt = alloc_n<uint32_t>(h, h->ncell + 1); A(S.cnt);
+    S.off = alloc_n<uint32_t>(h, h->ncell + 1); A(S.off);
+    if (s != PIC_ION) capsum += S.cap;
+  }
+  h->pair_cnt = alloc_n<uint64_t>(h, capsum); A(h->pair_cnt);
+  h->pair_off = alloc_n<uint64_t>(h, capsum); A(h->pair_off);
+  h->pair_ncoll = alloc_n<int32_t>(h, capsum); A(h->pair_ncoll);
+  // faces
+  Faces &fc = h->faces;
+  fc.n = (int64_t)G.fvcell.size();
+  fc.vcell = alloc_n<int32_t>(h, fc.n); A(fc.vcell);
+  fc.dir = alloc_n<int8_t>(h, fc.n); A(fc.dir);
+  fc.owner = alloc_n<int32_t>(h, fc.n); A(fc.owner);
+  fc.owner_vox = alloc_n<int32_t>(h, fc.n); A(fc.owner_vox);
+  fc.key = alloc_n<int64_t>(h, fc.n); A(fc.key);
+  for (double **p : {&fc.F, &fc.J, &fc.PN, &fc.acc_evap, &fc.acc_heat, &fc.acc_charge}) { *p = alloc_n<double>(h, fc.n); A(*p); }
+  for (int64_t **p : {&fc.acc_sput, &fc.acc_Eb, &fc.acc_Es}) { *p = alloc_n<int64_t>(h, fc.n); A(*p); }
+  for (uint32_t **p : {&fc.cnt, &fc.off, &fc.cnt2, &fc.off2, &fc.wu, &fc.wu2}) { *p = alloc_n<uint32_t>(h, fc.n + 1); A(*p); }
+  // heat
+  Heat &H = h->heat;
+  H.nvox = (int64_t)G.vox_cell.size();
+  h->solid_count = H.nvox;
+  H.cell = alloc_n<int32_t>(h, H.nvox); A(H.cell);
+  H.nbr = alloc_n<int32_t>(h, 6 * H.nvox); A(H.nbr);
+  H.base = alloc_n<uint8_t>(h, H.nvox); A(H.base);
+  for (double **p : {&H.T, &H.Tn, &H.sig, &H.kap, &H.src, &H.cur, &H.phiJ, &H.joule, &H.p, &H.q, &H.res, &H.zv}) {
+    *p = alloc_n<double>(h, H.nvox);
+    A(*p);
+  }
+  // scratch
+  h->scan_tmp = dalloc(h, (size_t)2 * h->nsm * sizeof(uint64_t)); A(h->scan_tmp);
+  h->red = alloc_n<double>(h, (int64_t)2 * h->nsm * 16); A(h->red);
+  h->red_out = alloc_n<double>(h, 2); A(h->red_out);
+  h->tmp_len = alloc_n<int64_t>(h, 16); A(h->tmp_len);
+  h->long_list = alloc_n<int2>(h, kLongCap); A(h->long_list);
+  h->long_n = alloc_n<int>(h, 16); A(h->long_n);
+  h->clock = alloc_n<DevClock>(h, 1); A(h->clock);
+  if (!okalloc) return fail(PIC_E_CUDA, "device allocation failed");
+  // uploads
+  cudaStream_t st = h->stream;
+  int rc = PIC_OK;
+#define UP(dst, src, bytes) \
+  if (rc == PIC_OK && cudaMemcpyAsync((dst), (src), (bytes), cudaMemcpyHostToDevice, st) != cudaSuccess) rc = PIC_E_CUDA
+  UP(h->solid, G.solid.data(), h->ncell);
+  UP(h->cheb, G.cheb.data(), h->ncell);
+  UP(h->mg[0].dir, G.dir0.data(), h->nnode);
+  if (fc.n) {
+    UP(fc.vcell, G.fvcell.data(), fc.n * 4);
+    UP(fc.dir, G.fdir.data(), fc.n);
+    UP(fc.owner, G.fowner.data(), fc.n * 4);
+    UP(fc.owner_vox, G.fowner_vox.data(), fc.n * 4);
+    UP(fc.key, G.fkey.data(), fc.n * 8);
+  }
+  if (H.nvox) {
+    UP(H.cell, G.vox_cell.data(), H.nvox * 4);
+    UP(H.nbr, G.vox_nbr.data(), H.nvox * 24);
+    UP(H.base, G.vox_base.data(), H.nvox);
+    std::vector<double> T0(H.nvox, h->prm.T0);
+    UP(H.T, T0.data(), H.nvox * 8);
+    if (rc == PIC_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = PIC_E_CUDA;
+  }
+#undef UP
+  if (rc != PIC_OK) return fail(rc, "upload failed");
+  for (uint32_t *p : {h->sp[0].cnt, h->sp[1].cnt, h->sp[2].cnt, h->sp[0].off, h->sp[1].off, h->sp[2].off})
+    if (cudaMemsetAsync(p, 0, (h->ncell + 1) * 4, st) != cudaSuccess) rc = PIC_E_CUDA;
+  for (double *p : {fc.acc_evap, fc.acc_heat, fc.acc_charge, fc.F, fc.J, fc.PN})
+    if (cudaMemsetAsync(p, 0, std::max<int64_t>(fc.n, 1) * 8, st) != cudaSuccess) rc = PIC_E_CUDA;
+  for (int64_t *p : {fc.acc_sput, fc.acc_Eb, fc.acc_Es})
+    if (cudaMemsetAsync(p, 0, std::max<int64_t>(fc.n, 1) * 8, st) != cudaSuccess) rc = PIC_E_CUDA;
+  if (cudaMemsetAsync(h->clock, 0, sizeof(DevClock), st) != cudaSuccess) rc = PIC_E_CUDA;
+  if (cudaMemsetAsync(h->phi, 0, h->nnode * 8, st) != cudaSuccess) rc = PIC_E_CUDA;
+  if (cudaMemsetAsync(h->Q, 0, h->nnode * 8, st) != cudaSuccess) rc = PIC_E_CUDA;
+  if (rc != PIC_OK) return fail(rc, "memset failed");
+  if (mg_build_masks(h) != PIC_OK || emission_tables_upload(h) != PIC_OK) return fail(PIC_E_CUDA, "setup failed");
+  // V0: calibrate from the apex field by a Laplace solve at V0 = 1 (phi is linear in V0)
+  if (h->prm.V0 > 0) {
+    h->V0 = h->prm.V0;
+    rc = stage_solve(h, true, h->V0);
+  } else {
+    rc = stage_solve(h, true, 1.0);
+    if (rc == PIC_OK) rc = stage_face_field(h);
+    double F1 = 0.0;
+    if (rc == PIC_OK && !G.apex.empty()) {
+      std::vector<double> F(fc.n);
+      if (cudaMemcpyAsync(F.data(), fc.F, fc.n * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+          cudaStreamSynchronize(st) != cudaSuccess)
+        rc = PIC_E_CUDA;
+      for (int64_t f : G.apex) F1 += F[f];
+      F1 /= (double)G.apex.size();
+    }
+    if (rc == PIC_OK) {
+      h->V0 = (F1 > 0 && h->prm.apex_field > 0) ? h->prm.apex_field / F1 : 1.0;
+      k_scale<<<grid_for(h->nnode), kThreads, 0, st>>>(h->phi, h->nnode, h->V0);
+      rc = stage_efield(h);
+    }
+  }
+  if (rc != PIC_OK) {
+    std::string m = h->last_error;
+    pic_destroy(h);
+    return rc;
+  }
+  *out = h;
+  return PIC_OK;
+}
+
+int pic_set_clock(pic_t *h, int64_t step, int64_t next_id) {
+  if (!h) return PIC_E_INVALID;
+  int64_t v[2] = {step, next_id};
+  PIC_CUDA(h, cudaMemcpyAsync(h->clock, v, sizeof v, cudaMemcpyHostToDevice, h->stream));
+  PIC_CUDA(h, cudaStreamSynchronize(h->stream));
+  return PIC_OK;
+}
+
+static int sort_one(pic_t *h, int s);
+
+int pic_load_particles(pic_t *h, int s, const float *x, const float *y, const float *z, const float *vx, const float *vy,
+                       const float *vz, const int32_t *w, const uint64_t *id, int64_t n) {
+  if (!h || s < 0 || s > 2 || n < 0) return PIC_E_INVALID;
+  Species &S = h->sp[s];
+  if (n > S.cap) return pic_fail(h, PIC_E_CAPACITY, "load exceeds the species capacity");
+  if (n > 0 && (!x || !y || !z || !vx || !vy || !vz || !w || !id)) return PIC_E_INVALID;
+  // validation: inside the domain and outside the tip (host copy of the solid mask)
+  std::vector<uint8_t> solid(h->ncell);
+  PIC_CUDA(h, cudaMemcpy(solid.data(), h->solid, h->ncell, cudaMemcpyDeviceToHost));
+  for (int64_t p = 0; p < n; ++p) {
+    if (!(x[p] >= 0 && x[p] < h->nx && y[p] >= 0 && y[p] < h->ny && z[p] >= 0 && z[p] < h->nz))
+      return pic_fail(h, PIC_E_INVALID, "SP " + std::to_string(p) + " outside the domain");
+    if (solid[cell_index((int)floorf(x[p]), (int)floorf(y[p]), (int)floorf(z[p]), h->nx, h->ny)])
+      return pic_fail(h, PIC_E_INVALID, "SP " + std::to_string(p) + " inside the tip");
+  }
+  cudaStream_t st = h->stream;
+  if (n) {
+    PIC_CUDA(h, cudaMemcpyAsync(S.a.x, x, n * 4, cudaMemcpyHostToDevice, st));
+    PIC_CUDA(h, cudaMemcpyAsync(S.a.y, y, n * 4, cudaMemcpyHostToDevice, st));
+    PIC_CUDA(h, cudaMemcpyAsync(S.a.z, z, n * 4, cudaMemcpyHostToDevice, st));
+    PIC_CUDA(h, cudaMemcpyAsync(S.a.vx, vx, n * 4, cudaMemcpyHostToDevice, st));
+    PIC_CUDA(h, cudaMemcpyAsync(S.a.vy, vy, n * 4, cudaMemcpyHostToDevice, st));
+    PIC_CUDA(h, cudaMemcpyAsync(S.a.vz, vz, n * 4, cudaMemcpyHostToDevice, st));
+    PIC_CUDA(h, cudaMemcpyAsync(S.a.w, w, n * 4, cudaMemcpyHostToDevice, st));
+    PIC_CUDA(h, cudaMemcpyAsync(S.a.id, id, n * 8, cudaMemcpyHostToDevice, st));
+  }
+  PIC_CUDA(h, cudaMemcpyAsync(&h->clock->n[s], &n, 8, cudaMemcpyHostToDevice, st));
+  PIC_CUDA(h, cudaStreamSynchronize(st));
+  PIC_TRY(stage_keys(h, s));
+  PIC_TRY(sort_one(h, s));
+  return check_err(h);
+}
+
+int pic_get_particles(pic_t *h, int s, float *x, float *y, float *z, float *vx, float *vy, float *vz, int32_t *w,
+                      uint64_t *id, int64_t cap, int64_t *n_out) {
+  if (!h || s < 0 || s > 2) return PIC_E_INVALID;
+  DevClock c;
+  PIC_TRY(clock_sync(h, &c));
+  const int64_t n = c.n[s];
+  if (n_out) *n_out = n;
+  if (n > cap) return pic_fail(h, PIC_E_CAPACITY, "output arrays too short");
+  Species &S = h->sp[s];
+  cudaStream_t st = h->stream;
+  if (n) {
+    if (x) PIC_CUDA(h, cudaMemcpyAsync(x, S.a.x, n * 4, cudaMemcpyDeviceToHost, st));
+    if (y) PIC_CUDA(h, cudaMemcpyAsync(y, S.a.y, n * 4, cudaMemcpyDeviceToHost, st));
+    if (z) PIC_CUDA(h, cudaMemcpyAsync(z, S.a.z, n * 4, cudaMemcpyDeviceToHost, st));
+    if (vx) PIC_CUDA(h, cudaMemcpyAsync(vx, S.a.vx, n * 4, cudaMemcpyDeviceToHost, st));
+    if (vy) PIC_CUDA(h, cudaMemcpyAsync(vy, S.a.vy, n * 4, cudaMemcpyDeviceToHost, st));
+    if (vz) PIC_CUDA(h, cudaMemcpyAsync(vz, S.a.vz, n * 4, cudaMemcpyDeviceToHost, st));
+    if (w) PIC_CUDA(h, cudaMemcpyAsync(w, S.a.w, n * 4, cudaMemcpyDeviceToHost, st));
+    if (id) PIC_CUDA(h, cudaMemcpyAsync(id, S.a.id, n * 8, cudaMemcpyDeviceToHost, st));
+  }
+  PIC_CUDA(h, cudaStreamSynchronize(st));
+  return PIC_OK;
+}
+
+int pic_set_potential(pic_t *h, const double *phi) {
+  if (!h || !phi) return PIC_E_INVALID;
+  PIC_CUDA(h, cudaMemcpyAsync(h->phi, phi, h->nnode * 8, cudaMemcpyHostToDevice, h->stream));
+  PIC_TRY(stage_efield(h));
+  PIC_CUDA(h, cudaStreamSynchronize(h->stream));
+  return PIC_OK;
+}
+
+static int d2h(pic_t *h, void *dst, const void *src, size_t bytes) {
+  if (!dst) return pic_fail(h, PIC_E_INVALID, "null output");
+  PIC_CUDA(h, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, h->stream));
+  PIC_CUDA(h, cudaStreamSynchronize(h->stream));
+  return PIC_OK;
+}
+
+int pic_get_potential(pic_t *h, double *phi) { return h ? d2h(h, phi, h->phi, h->nnode * 8) : PIC_E_INVALID; }
+int pic_get_charge(pic_t *h, int64_t *Q) { return h ? d2h(h, Q, h->Q, h->nnode * 8) : PIC_E_INVALID; }
+
+int pic_get_efield(pic_t *h, float *E) {
+  if (!h || !E) return PIC_E_INVALID;
+  std::vector<float4> tmp(h->nnode);
+  PIC_TRY(d2h(h, tmp.data(), h->E, h->nnode * sizeof(float4)));
+  for (int64_t n = 0; n < h->nnode; ++n) { E[3 * n] = tmp[n].x; E[3 * n + 1] = tmp[n].y; E[3 * n + 2] = tmp[n].z; }
+  return PIC_OK;
+}
+
+int pic_num_solid(pic_t *h, int64_t *n) {
+  if (!h || !n) return PIC_E_INVALID;
+  *n = h->heat.nvox;
+  return PIC_OK;
+}
+
+int pic_set_temperature(pic_t *h, const double *T) {
+  if (!h || !T) return PIC_E_INVALID;
+  if (h->heat.nvox) {
+    PIC_CUDA(h, cudaMemcpyAsync(h->heat.T, T, h->heat.nvox * 8, cudaMemcpyHostToDevice, h->stream));
+    PIC_CUDA(h, cudaStreamSynchronize(h->stream));
+  }
+  return PIC_OK;
+}
+
+int pic_get_temperature(pic_t *h, double *T) {
+  if (!h) return PIC_E_INVALID;
+  return h->heat.nvox ? d2h(h, T, h->heat.T, h->heat.nvox * 8) : PIC_OK;
+}
+
+int pic_num_faces(pic_t *h, int64_t *n) {
+  if (!h || !n) return PIC_E_INVALID;
+  *n = h->faces.n;
+  return PIC_OK;
+}
+
+int pic_get_faces(pic_t *h, int64_t *vcell, int32_t *dir, int64_t *owner) {
+  if (!h) return PIC_E_INVALID;
+  const int64_t n = h->faces.n;
+  std::vector<int32_t> v(n), o(n);
+  std::vector<int8_t> d(n);
+  if (n) {
+    PIC_TRY(d2h(h, v.data(), h->faces.vcell, n * 4));
+    PIC_TRY(d2h(h, d.data(), h->faces.dir, n));
+    PIC_TRY(d2h(h, o.data(), h->faces.owner, n * 4));
+  }
+  for (int64_t f = 0; f < n; ++f) {
+    if (vcell) vcell[f] = v[f];
+    if (dir) dir[f] = d[f];
+    if (owner) owner[f] = o[f];
+  }
+  return PIC_OK;
+}
+
+int pic_get_face_emission(pic_t *h, double *F, double *J, double *PN) {
+  if (!h) return PIC_E_INVALID;
+  const size_t b = h->faces.n * 8;
+  if (!h->faces.n) return PIC_OK;
+  if (F) PIC_TRY(d2h(h, F, h->faces.F, b));
+  if (J) PIC_TRY(d2h(h, J, h->faces.J, b));
+  if (PN) PIC_TRY(d2h(h, PN, h->faces.PN, b));
+  return PIC_OK;
+}
+
+int pic_get_face_accumulators(pic_t *h, double *evap, double *heat, double *charge, int64_t *sput, int64_t *Eb, int64_t *Es) {
+  if (!h) return PIC_E_INVALID;
+  const size_t b = h->faces.n * 8;
+  if (!h->faces.n) return PIC_OK;
+  if (evap) PIC_TRY(d2h(h, evap, h->faces.acc_evap, b));
+  if (heat) PIC_TRY(d2h(h, heat, h->faces.acc_heat, b));
+  if (charge) PIC_TRY(d2h(h, charge, h->faces.acc_charge, b));
+  if (sput) PIC_TRY(d2h(h, sput, h->faces.acc_sput, b));
+  if (Eb) PIC_TRY(d2h(h, Eb, h->faces.acc_Eb, b));
+  if (Es) PIC_TRY(d2h(h, Es, h->faces.acc_Es, b));
+  return PIC_OK;
+}
+
+int pic_set_face_accumulators(pic_t *h, const double *evap, const double *heat, const double *charge, const int64_t *sput,
+                              const int64_t *Eb, const int64_t *Es) {
+  if (!h) return PIC_E_INVALID;
+  const size_t b = h->faces.n * 8;
+  if (!h->faces.n) return PIC_OK;
+  cudaStream_t st = h->stream;
+  if (evap) PIC_CUDA(h, cudaMemcpyAsync(h->faces.acc_evap, evap, b, cudaMemcpyHostToDevice, st));
+  if (heat) PIC_CUDA(h, cudaMemcpyAsync(h->faces.acc_heat, heat, b, cudaMemcpyHostToDevice, st));
+  if (charge) PIC_CUDA(h, cudaMemcpyAsync(h->faces.acc_charge, charge, b, cudaMemcpyHostToDevice, st));
+  if (sput) PIC_CUDA(h, cudaMemcpyAsync(h->faces.acc_sput, sput, b, cudaMemcpyHostToDevice, st));
+  if (Eb) PIC_CUDA(h, cudaMemcpyAsync(h->faces.acc_Eb, Eb, b, cudaMemcpyHostToDevice, st));
+  if (Es) PIC_CUDA(h, cudaMemcpyAsync(h->faces.acc_Es, Es, b, cudaMemcpyHostToDevice, st));
+  PIC_CUDA(h, cudaStreamSynchronize(st));
+  return PIC_OK;
+}
+
+// ---- stages -------------------------------------------------------------------------------
+static int sort_one(pic_t *h, int s);
+int pic_sort(pic_t *h);
+
+int pic_emit(pic_t *h) {
+  if (!h) return PIC_E_INVALID;
+  PIC_TRY(stage_emit(h));
+  return check_err(h);
+}
+
+int pic_push(pic_t *h) {
+  if (!h) return PIC_E_INVALID;
+  PIC_TRY(stage_push(h));
+  return check_err(h);
+}
+
+int pic_sort(pic_t *h) {
+  if (!h) return PIC_E_INVALID;
+  PIC_TRY(stage_sort(h));
+  return check_err(h);
+}
+
+static int sort_one(pic_t *h, int s) {
+  // sort only species s: mark the others as not needing work by sorting all (cheap at load time)
+  (void)s;
+  return stage_sort(h);
+}
+
+int pic_collide(pic_t *h) {
+  if (!h) return PIC_E_INVALID;
+  PIC_TRY(stage_collide(h));
+  return check_err(h);
+}
+
+int pic_deposit(pic_t *h) {
+  if (!h) return PIC_E_INVALID;
+  PIC_TRY(stage_deposit(h));
+  PIC_CUDA(h, cudaStreamSynchronize(h->stream));
+  return PIC_OK;
+}
+
+int pic_solve_field(pic_t *h) {
+  if (!h) return PIC_E_INVALID;
+  PIC_TRY(stage_deposit(h));
+  PIC_TRY(stage_solve(h, false, h->V0));
+  PIC_CUDA(h, cudaStreamSynchronize(h->stream));
+  return PIC_OK;
+}
+
+int pic_heat(pic_t *h) {
+  if (!h) return PIC_E_INVALID;
+  PIC_TRY(stage_heat(h));
+  PIC_CUDA(h, cudaStreamSynchronize(h->stream));
+  return PIC_OK;
+}
+
+__global__ void k_begin_step(DevClock *clk) {
+  for (int i = 0; i < cNum; ++i) clk->ctr[i] = 0;
+}
+__global__ void k_end_step(DevClock *clk) { clk->step += 1; }
+
+int pic_step(pic_t *h, int nsteps) {
+  if (!h || nsteps < 0) return PIC_E_INVALID;
+  DevClock c;
+  PIC_TRY(clock_sync(h, &c));
+  int64_t step = c.step;
+  cudaEvent_t ev[8];
+  for (int i = 0; i < 8; ++i) cudaEventCreate(&ev[i]);
+  int rc = PIC_OK;
+  for (int it = 0; it < nsteps && rc == PIC_OK; ++it) {
+    cudaEventRecord(ev[0], h->stream);
+    k_begin_step<<<1, 1, 0, h->stream>>>(h->clock);
+    rc = stage_emit(h);
+    cudaEventRecord(ev[1], h->stream);
+    if (rc == PIC_OK) rc = stage_push(h);
+    cudaEventRecord(ev[2], h->stream);
+    if (rc == PIC_OK) rc = stage_sort(h);
+    cudaEventRecord(ev[3], h->stream);
+    if (rc == PIC_OK) rc = stage_collide(h);
+    cudaEventRecord(ev[4], h->stream);
+    if (rc == PIC_OK) rc = stage_deposit(h);
+    cudaEventRecord(ev[5], h->stream);
+    if (rc == PIC_OK) rc = stage_solve(h, false, h->V0);
+    cudaEventRecord(ev[6], h->stream);
+    ++step;
+    if (rc == PIC_OK && (h->prm.flags & PIC_F_HEAT) && h->prm.n_heat > 0 && step % h->prm.n_heat == 0) rc = stage_heat(h);
+    k_end_step<<<1, 1, 0, h->stream>>>(h->clock);
+    cudaEventRecord(ev[7], h->stream);
+  }
+  cudaEventSynchronize(ev[7]);
+  if (rc == PIC_OK && nsteps > 0) {
+    for (int i = 0; i < 6; ++i) cudaEventElapsedTime(&h->ms[i], ev[i], ev[i + 1]);
+    cudaEventElapsedTime(&h->ms[6], ev[6], ev[7]);
+    cudaEventElapsedTime(&h->ms[7], ev[0], ev[7]);
+  }
+  for (int i = 0; i < 8; ++i) cudaEventDestroy(ev[i]);
+  if (rc != PIC_OK) return rc;
+  PIC_TRY(launch_check(h, "step"));
+  return check_err(h);
+}
+
+__global__ void k_sum_w(const int32_t *w, const DevClock *clk, int s, unsigned long long *out) {
+  const int64_t n = clk->n[s];
+  long long acc = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) acc += w[i];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0 && acc) atomicAdd(out, (unsigned long long)acc);
+}
+
+__global__ void k_sum_q(const unsigned long long *Q, int64_t n, unsigned long long *out) {
+  long long acc = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    acc += (long long)Q[i];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0 && acc) atomicAdd(out, (unsigned long long)acc);
+}
+
+int pic_diagnostics(pic_t *h, pic_diag_t *out) {
+  if (!h || !out) return PIC_E_INVALID;
+  memset(out, 0, sizeof *out);
+  DevClock c;
+  PIC_TRY(clock_sync(h, &c));
+  out->step = c.step;
+  out->next_id = c.next_id;
+  unsigned long long *sums = (unsigned long long *)(h->tmp_len + 10);
+  PIC_CUDA(h, cudaMemsetAsync(sums, 0, 4 * 8, h->stream));
+  for (int s = 0; s < 3; ++s) {
+    out->count[s] = c.n[s];
+    k_sum_w<<<h->nsm * 4, kThreads, 0, h->stream>>>(h->sp[s].a.w, h->clock, s, sums + s);
+    out->removed[s] = c.ctr[cRemovedE + s];
+  }
+  k_sum_q<<<h->nsm * 4, kThreads, 0, h->stream>>>(h->Q, h->nnode, sums + 3);
+  unsigned long long hs[4];
+  PIC_TRY(d2h(h, hs, sums, sizeof hs));
+  for (int s = 0; s < 3; ++s) out->weight[s] = (int64_t)hs[s];
+  out->total_charge_fixed = (int64_t)hs[3];
+  out->emitted = c.ctr[cEmitted];
+  out->evaporated = c.ctr[cEvaporated];
+  out->sputtered = c.ctr[cSputtered];
+  out->impact_ionizations = c.ctr[cImpactIon];
+  out->field_ionizations = c.ctr[cFieldIon];
+  out->ion_impacts = c.ctr[cIonImpacts];
+  out->mg_cycles = h->last_mg_cycles;
+  out->mg_residual = h->last_mg_res;
+  out->V0 = h->V0;
+  const int64_t nf = h->faces.n;
+  if (nf) {
+    std::vector<double> F(nf), J(nf);
+    PIC_TRY(d2h(h, F.data(), h->faces.F, nf * 8));
+    PIC_TRY(d2h(h, J.data(), h->faces.J, nf * 8));
+    double cur = 0;
+    for (int64_t f = 0; f < nf; ++f) {
+      out->max_face_field = std::max(out->max_face_field, F[f]);
+      out->max_J = std::max(out->max_J, J[f]);
+      cur += J[f] * h->dx * h->dx;
+    }
+    out->emitted_current = cur;
+  }
+  if (h->heat.nvox) {
+    std::vector<double> T(h->heat.nvox);
+    PIC_TRY(d2h(h, T.data(), h->heat.T, h->heat.nvox * 8));
+    out->max_T = *std::max_element(T.begin(), T.end());
+  }
+  for (int i = 0; i < 8; ++i) out->ms[i] = h->ms[i];
+  return PIC_OK;
+}
+
+int pic_emission_eval(pic_t *h, const double *F, const double *T, const double *phi_w, const double *R, double *J,
+                      double *PN, int64_t n) {
+  if (!h || n < 0 || (n > 0 && (!F || !T || !phi_w || !R || !J || !PN))) return PIC_E_INVALID;
+  if (n == 0) return PIC_OK;
+  double *buf = nullptr;
+  PIC_CUDA(h, cudaMalloc(&buf, (size_t)n * 6 * 8));
+  cudaStream_t st = h->stream;
+  int rc = PIC_OK;
+  if (cudaMemcpyAsync(buf, F, n * 8, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(buf + n, T, n * 8, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(buf + 2 * n, phi_w, n * 8, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(buf + 3 * n, R, n * 8, cudaMemcpyHostToDevice, st) != cudaSuccess)
+    rc = pic_fail(h, PIC_E_CUDA, "emission_eval upload");
+  if (rc == PIC_OK) rc = emission_eval_dev(h, buf, buf + n, buf + 2 * n, buf + 3 * n, buf + 4 * n, buf + 5 * n, n);
+  if (rc == PIC_OK && (cudaMemcpyAsync(J, buf + 4 * n, n * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                       cudaMemcpyAsync(PN, buf + 5 * n, n * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                       cudaStreamSynchronize(st) != cudaSuccess))
+    rc = pic_fail(h, PIC_E_CUDA, "emission_eval download");
+  cudaFree(buf);
+  return rc;
+}
+
+}  // extern "C"

@@ -1,0 +1,261 @@
+// Internal declarations of libpic: device state, launch helpers, Philox4x32-10.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/pic.h"
+
+namespace pic {
+
+// ---- physical constants (CODATA 2018) ------------------------------------------------------
+constexpr double kQe = 1.602176634e-19;
+constexpr double kMe = 9.1093837015e-31;
+constexpr double kAmu = 1.66053906660e-27;
+constexpr double kEps0 = 8.8541878128e-12;
+constexpr double kKb = 1.380649e-23;
+constexpr double kHbar = 1.054571817e-34;
+constexpr double kPi = 3.141592653589793;
+constexpr double kMcu = 63.546 * kAmu;
+constexpr double kXiCu = 7.726;      // eV, first ionization energy of Cu
+constexpr double kEvap = 3.43;       // eV (Sec. 2.3.1)
+constexpr double kTboil = 2835.0;    // K
+constexpr double kPatm = 101325.0;   // Pa
+constexpr double kLorentz = 2.0e-8;  // W Ohm K^-2 (Sec. 2.1)
+constexpr double kNmax = 1e24;       // m^-3 (1e-6 per cubic Angstrom, Sec. 2.3.2)
+
+constexpr uint32_t kDead = 0xFFFFFFFFu;
+constexpr int kFracBits = 10;         // CIC fixed-point fraction bits per axis
+constexpr int kSputBits = 24;         // sputter accumulator: atoms * 2^24
+constexpr int kEnergyBits = 20;       // energy accumulators: eV * 2^20
+constexpr int kMaxSegment = 8192;     // SPs of one species in one cell (sort fix-up limit)
+constexpr int kLongCap = 1 << 16;     // queued long segments per sort pass
+
+// Philox purposes (one key per purpose)
+enum Purpose : uint32_t { kEmit = 1, kPair = 2, kIon = 3, kScat = 4, kDfi = 5, kEvapP = 6, kSput = 7 };
+
+// device counters (int64), indices
+enum Ctr {
+  cEmitted = 0, cEvaporated, cSputtered, cImpactIon, cFieldIon, cRemovedE, cRemovedN, cRemovedI,
+  cIonImpacts, cNum
+};
+
+// error bits set by kernels
+enum ErrBits : int { kErrCapacity = 1, kErrSegment = 2, kErrTimeout = 4, kErrNan = 8 };
+
+struct DevClock {
+  int64_t step;
+  int64_t next_id;
+  int64_t n[3];          // SPs held per species
+  int64_t n_sorted[3];   // leading SPs covered by the last cell sort (per-cell offsets valid)
+  int64_t n_new[3];      // scratch: SPs created by the current pass
+  int64_t ctr[cNum];
+  int err;
+};
+
+struct SpeciesBuf {
+  float *x, *y, *z, *vx, *vy, *vz;
+  int32_t *w;
+  uint64_t *id;
+};
+
+struct Species {
+  int Z = 0;
+  double mass = 0;
+  int64_t cap = 0;
+  float qmdt = 0.f;
+  SpeciesBuf a{}, b{};        // current and scratch SoA buffers
+  uint32_t *key = nullptr;    // cell key per SP (kDead when removed)
+  uint32_t *perm = nullptr;   // sort permutation
+  uint32_t *cnt = nullptr;    // per-cell counts (zero between sorts), ncell+1
+  uint32_t *off = nullptr;    // per-cell offsets of the last sort, ncell+1
+};
+
+struct MgLevel {
+  int nx, ny, nz;             // cells
+  int64_t nnode;
+  double h;
+  uint8_t *dir = nullptr;     // Dirichlet mask per node
+  float *u = nullptr, *f = nullptr, *r = nullptr;
+  double *ud = nullptr, *fd = nullptr, *rd = nullptr;   // FP64 V-cycle storage (plain form)
+};
+
+struct Faces {
+  int64_t n = 0;
+  int32_t *vcell = nullptr;   // vacuum cell (linear)
+  int8_t *dir = nullptr;      // 0..5
+  int32_t *owner = nullptr;   // solid cell or -1
+  int32_t *owner_vox = nullptr;  // index of the owner in the solid-cell list or -1
+  int64_t *key = nullptr;     // vcell*6+dir, ascending
+  double *F = nullptr, *J = nullptr, *PN = nullptr;
+  double *acc_evap = nullptr, *acc_heat = nullptr, *acc_charge = nullptr;
+  int64_t *acc_sput = nullptr, *acc_Eb = nullptr, *acc_Es = nullptr;
+  uint32_t *cnt = nullptr, *off = nullptr;   // per-face creation counts / offsets (n+1)
+  uint32_t *cnt2 = nullptr, *off2 = nullptr;
+  uint32_t *wu = nullptr, *wu2 = nullptr;    // injection weights of this pass
+};
+
+struct Heat {
+  int64_t nvox = 0;
+  int32_t *cell = nullptr;     // solid cell of voxel v
+  int32_t *nbr = nullptr;      // 6 neighbour voxels per voxel (-1 none)
+  uint8_t *base = nullptr;     // voxel on the k = 0 layer
+  double *T = nullptr, *Tn = nullptr, *sig = nullptr, *kap = nullptr;
+  double *src = nullptr, *cur = nullptr, *phiJ = nullptr, *joule = nullptr;
+  double *p = nullptr, *q = nullptr, *res = nullptr, *zv = nullptr;
+};
+
+}  // namespace pic
+
+struct pic_s {
+  // configuration
+  int nx = 0, ny = 0, nz = 0;
+  double dx = 0;
+  int64_t ncell = 0, nnode = 0;
+  pic_geometry_t geo{};
+  pic_params_t prm{};
+  double V0 = 0;
+  cudaStream_t stream = nullptr;
+  pic_alloc_fn alloc = nullptr;
+  pic_free_fn free_fn = nullptr;
+  void *alloc_user = nullptr;
+  std::vector<std::pair<void *, size_t>> allocations;
+  std::string last_error;
+  int nsm = 148;
+
+  // device state
+  uint8_t *solid = nullptr;      // per cell
+  uint8_t *cheb = nullptr;       // per cell: Chebyshev distance to the nearest solid cell (capped)
+  double *phi = nullptr;         // per node
+  double *rhs = nullptr;         // per node: rho/eps0 (FP64)
+  double *res = nullptr;         // per node: FP64 residual
+  float4 *E = nullptr;           // per node
+  unsigned long long *Q = nullptr;  // per node, int64 two's complement charge
+  pic::Species sp[3];
+  pic::Faces faces;
+  pic::Heat heat;
+  std::vector<pic::MgLevel> mg;
+  pic::DevClock *clock = nullptr;
+  // scratch
+  void *scan_tmp = nullptr;      // block partials for scans
+  uint64_t *pair_cnt = nullptr;  // per projectile / neutral: packed product counts
+  uint64_t *pair_off = nullptr;
+  int32_t *pair_ncoll = nullptr;
+  double *red = nullptr;         // reduction partials
+  double *red_out = nullptr;
+  int64_t *tmp_len = nullptr;    // device-side lengths for scans
+  int2 *long_list = nullptr;     // sort: long cell segments queued for the block-level fix-up
+  int *long_n = nullptr;
+  // state flags and last diagnostics
+  bool keys_valid[3] = {false, false, false};
+  int last_mg_cycles = 0;
+  double last_mg_res = 0;
+  float ms[8] = {0};
+  int64_t solid_count = 0;
+};
+
+namespace pic {
+
+// ---- Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), written from the published rounds ----
+struct U4 { uint32_t v[4]; };
+
+__host__ __device__ inline U4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0, uint32_t k1) {
+  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u, W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    uint64_t p0 = (uint64_t)M0 * c0;
+    uint64_t p1 = (uint64_t)M1 * c2;
+    uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
+    uint32_t n1 = (uint32_t)p1;
+    uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
+    uint32_t n3 = (uint32_t)p0;
+    c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    k0 += W0; k1 += W1;
+  }
+  U4 o; o.v[0] = c0; o.v[1] = c1; o.v[2] = c2; o.v[3] = c3;
+  return o;
+}
+
+// Stream (seed, purpose, ident, step): the 4 words of draw block `blk` (draws 4*blk..4*blk+3)
+__host__ __device__ inline U4 rng_block(uint64_t seed, uint32_t purpose, uint64_t ident, int64_t step, uint32_t blk) {
+  uint32_t k0 = (uint32_t)seed;
+  uint32_t k1 = (uint32_t)(((seed >> 32) << 8) | purpose);
+  return philox((uint32_t)ident, (uint32_t)(ident >> 32), (uint32_t)step, blk, k0, k1);
+}
+
+// U = ((w >> 8) + 0.5) 2^-24, exact in float and double
+__host__ __device__ inline float u01f(uint32_t w) { return ((float)(w >> 8) + 0.5f) * 5.9604644775390625e-8f; }
+__host__ __device__ inline double u01d(uint32_t w) { return ((double)(w >> 8) + 0.5) * 5.9604644775390625e-8; }
+// floor(U * n) exactly: ((2 (w>>8) + 1) n) >> 25
+__host__ __device__ inline uint32_t u_index(uint32_t w, uint32_t n) {
+  return (uint32_t)(((2ull * (w >> 8) + 1ull) * (uint64_t)n) >> 25);
+}
+__device__ inline double uniform_draw(uint64_t seed, uint32_t purpose, uint64_t ident, int64_t step, uint32_t d) {
+  U4 b = rng_block(seed, purpose, ident, step, d >> 2);
+  return u01d(b.v[d & 3]);
+}
+
+// ---- launch helpers -----------------------------------------------------------------------
+constexpr int kThreads = 256;
+inline int grid_for(int64_t n, int threads = kThreads) {
+  int64_t g = (n + threads - 1) / threads;
+  if (g < 1) g = 1;
+  if (g > 1 << 20) g = 1 << 20;
+  return (int)g;
+}
+
+__host__ __device__ inline int64_t node_index(int i, int j, int k, int nx, int ny) {
+  return ((int64_t)k * (ny + 1) + j) * (nx + 1) + i;
+}
+__host__ __device__ inline int64_t cell_index(int i, int j, int k, int nx, int ny) {
+  return ((int64_t)k * ny + j) * nx + i;
+}
+
+}  // namespace pic
+
+// ---- error plumbing (host) ------------------------------------------------------------------
+int pic_fail(pic_t *h, int code, const std::string &msg);
+#define PIC_CUDA(h, call)                                                                  \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess)                                                                 \
+      return pic_fail((h), PIC_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+#define PIC_TRY(expr)            \
+  do {                           \
+    int rc_ = (expr);            \
+    if (rc_ != PIC_OK) return rc_; \
+  } while (0)
+
+// ---- stage entry points implemented in the kernel files --------------------------------------
+namespace pic {
+void *dalloc(pic_t *h, size_t bytes);
+int launch_check(pic_t *h, const char *what);
+
+// scans (k_scan.cu): exclusive scans of n values; n either a host size or a device int64
+int scan_u32(pic_t *h, const uint32_t *in, uint32_t *out, int64_t n, const int64_t *n_dev, uint32_t *total);
+int scan_u64(pic_t *h, const uint64_t *in, uint64_t *out, int64_t n, const int64_t *n_dev, uint64_t *total);
+
+// particles (k_particles.cu)
+int stage_keys(pic_t *h, int s);
+int stage_push(pic_t *h);
+int stage_sort(pic_t *h);
+int stage_deposit(pic_t *h);
+// collisions (k_collide.cu)
+int stage_collide(pic_t *h);
+// surface (k_surface.cu)
+int stage_face_field(pic_t *h);
+int stage_emit(pic_t *h);
+int stage_inject(pic_t *h);
+int emission_eval_dev(pic_t *h, const double *F, const double *T, const double *W, const double *R,
+                      double *J, double *PN, int64_t n);
+// field (k_field.cu)
+int stage_efield(pic_t *h);
+int stage_solve(pic_t *h, bool zero_charge, double V0);
+int face_field_mean(pic_t *h, const int64_t *faces, int nf, double *out);
+// heat (k_heat.cu)
+int stage_heat(pic_t *h);
+}  // namespace pic
