@@ -98,8 +98,15 @@ def supply(W, kT):
 
 
 def _L(w):
-    """L(w) = int_w^inf ln(1 + e^-t) dt = -Li2(-e^-w), for w >= 0 (scipy: Li2(z) = spence(1 - z))."""
-    return -ss.spence(1.0 + np.exp(-np.asarray(w, dtype=np.float64)))
+    """L(w) = int_w^inf ln(1 + e^-t) dt = -Li2(-e^-w) = sum_k (-1)^(k+1) x^k / k^2, x = e^-w, w >= 0.
+    The power series is used for x <= 1/2 (spence(1 + x) would lose x when 1 + x rounds to 1);
+    scipy's spence (Li2(z) = spence(1 - z)) for 1/2 < x <= 1."""
+    w = np.asarray(w, dtype=np.float64)
+    x = np.exp(-w)
+    k = np.arange(1, 61, dtype=np.float64)
+    xs = np.minimum(x, 0.5)
+    series = np.sum(((-1.0) ** (k + 1)) * xs[..., None] ** k / (k * k), axis=-1)
+    return np.where(x <= 0.5, series, -ss.spence(1.0 + x))
 
 
 def nottingham_inner(W, kT):
@@ -195,9 +202,12 @@ def _bisect(fun, lo, hi, iters=200):
 
 
 def current_density_fixed(F_GV, T, phi, R_nm, panels=160):
-    """Vectorised (J, P_N) for arrays of faces: 8-point Gauss-Legendre on `panels` equal panels
-    over [W_lo, U_m], 48-point Gauss-Legendre in the Chebyshev-type angle for G(W), and
-    24 panels of 8 points over [U_m, U_m + 60 kT] for the part above the barrier."""
+    """Vectorised (J, P_N) for arrays of faces: 8-point Gauss-Legendre on the panels between
+    breakpoints over [W_lo, U_m] -- `panels` equal panels, refined by geometric breakpoints
+    toward the Fermi level (steps kT 2^j) and toward the barrier top (steps min(kT, hbar omega/2)
+    2^j, omega the curvature frequency of the top) --, 48-point Gauss-Legendre in the
+    Chebyshev-type angle for G(W), and 24 panels of 8 points over [U_m, U_m + 60 kT] for the
+    part above the barrier."""
     F = np.atleast_1d(np.asarray(F_GV, dtype=np.float64))
     T = np.broadcast_to(np.asarray(T, dtype=np.float64), F.shape)
     phi = np.broadcast_to(np.asarray(phi, dtype=np.float64), F.shape)
@@ -216,14 +226,24 @@ def current_density_fixed(F_GV, T, phi, R_nm, panels=160):
     xm = _bisect(lambda x: _slope_v(x, F, R), np.full_like(F, 1e-9), hi)
     Um = _barrier_v(xm, F, phi, R)
     top = np.maximum(Um, W_LO)
-    # below the barrier maximum
+    # below the barrier maximum: breakpoints (equal + graded), 8-point rule on every panel
     xg, wg = _GL8
-    edges = np.linspace(0.0, 1.0, panels + 1)
-    h = (top - W_LO)[:, None] / panels
-    Wn = (W_LO + (top - W_LO)[:, None] * edges[None, :-1])[:, :, None] + h[:, :, None] * (0.5 * (xg + 1.0))[None, None, :]
+    d = 1e-4 * xm
+    d2U = (_slope_v(xm + d, F, R) - _slope_v(xm - d, F, R)) / (2 * d)
+    hw = np.sqrt(8.0 * np.abs(d2U)) / G_CONST                  # hbar omega at the top [eV]
+    steps = 2.0 ** np.arange(40) - 1.0
+    span = (top - W_LO)[:, None]
+    bp = np.concatenate([
+        W_LO + span * np.linspace(0.0, 1.0, panels + 1)[None, :],
+        top[:, None] - np.minimum(kT, 0.5 * hw)[:, None] * steps[None, :],
+        kT[:, None] * steps[None, :],
+        -kT[:, None] * steps[None, :]], axis=1)
+    bp = np.sort(np.clip(bp, W_LO, top[:, None]), axis=1)
+    a_, b_ = bp[:, :-1], bp[:, 1:]
+    h = 0.5 * (b_ - a_)
+    Wn = (0.5 * (a_ + b_))[:, :, None] + h[:, :, None] * xg[None, None, :]
     Wn = Wn.reshape(len(F), -1)
-    Ww = (h * 0.5)[:, :, None] * wg[None, None, :] * np.ones((1, panels, 1))
-    Ww = Ww.reshape(len(F), -1)
+    Ww = (h[:, :, None] * wg[None, None, :]).reshape(len(F), -1)
     Fb, phib, Rb, xmb = (a[:, None] * np.ones_like(Wn) for a in (F, phi, R, xm))
     below = Wn < Um[:, None]
     # x1 in (0, xm]

@@ -130,8 +130,28 @@ def test_deposit_bit_exact_and_conserving(pic):
 
 
 def test_collisions_match_oracle(pic):
-    # strong field near the apex so that field ionization fires, plus impact ionization
-    cfg, g, sim, pop, phi = _pushed_case(pic, n_sp=30000, seed=5, V0=140.0)
+    # energetic electrons mixed with the neutrals (impact ionization) and a strong applied
+    # field (field ionization near the apex); w_min = 1 raises the per-pair probabilities
+    n_sp = 30000
+    cfg = small_cfg(n_sp=n_sp, w_min=1.0)
+    g = grid_of(cfg)
+    V0 = 420.0
+    sim = make(pic, cfg, V0=V0)
+    pop = synth.plasma(cfg, seed=5)
+    rng = np.random.default_rng(6)
+    ne = len(pop["e"]["x"])
+    src = rng.integers(0, len(pop["n"]["x"]), ne)
+    for c in ("x", "y", "z"):
+        pop["e"][c] = pop["n"][c][src].copy()             # electrons on neutral positions
+    speed = np.sqrt(2 * rng.uniform(20.0, 300.0, ne) * OC.E_CHARGE / OC.M_E)
+    u = rng.normal(size=(ne, 3))
+    u /= np.linalg.norm(u, axis=1)[:, None]
+    for a, c in enumerate(("vx", "vy", "vz")):
+        pop["e"][c] = (speed * u[:, a]).astype(np.float32)
+    phi = field.solve_poisson(g, V0)
+    sim.set_potential(phi)
+    load(sim, pop)
+    sim.set_clock(3, n_sp)
     E = field.efield(g, phi)
     st = sorted_pop(g, pop)
     offs = {k: P.stable_sort(g, st[k])[1] for k in "eni"}
@@ -142,8 +162,8 @@ def test_collisions_match_oracle(pic):
     ref = {"e": P.concat(P.concat(st["e"], ne), ne2), "n": st["n"], "i": P.concat(P.concat(st["i"], ni), ni2)}
     sim.collide()
     d = sim.diagnostics()
+    assert ev > 20 and ev2 > 20, (ev, ev2)
     assert d["impact_ionizations"] == ev and d["field_ionizations"] == ev2
-    assert ev + ev2 > 0
     assert d["next_id"] == ids.next_id
     for s, (k, _, _) in enumerate(SPECIES):
         got = sim.get_particles(s)
@@ -161,9 +181,13 @@ def test_emission_integral_matches_oracle(pic):
     R = np.where(np.arange(400) % 5 == 0, -1.0, R)          # some flat faces
     J, PN = sim.emission_eval(F * 1e9, T, W, np.where(R > 0, R * 1e-9, -1.0))
     Jr, Pr = em.current_density_fixed(F, T, W, np.where(R > 0, R, np.inf))
+    assert np.all(np.isfinite(J)) and np.all(np.isfinite(PN)), np.nonzero(~(np.isfinite(J) & np.isfinite(PN)))
     ok = Jr > 1e-200
-    assert np.all(np.abs(J[ok] / Jr[ok] - 1) <= 1e-8)
-    assert np.all(np.abs(PN - Pr) <= 1e-6 * (np.abs(Pr) + np.abs(Jr) * 1.0) + 1e-30)
+    bad = np.nonzero(ok & ~(np.abs(J / np.where(ok, Jr, 1.0) - 1) <= 1e-8))[0]
+    assert len(bad) == 0, (bad[:5], F[bad[:5]], T[bad[:5]], W[bad[:5]], R[bad[:5]], J[bad[:5]], Jr[bad[:5]])
+    tol = 1e-6 * (np.abs(Pr) + np.abs(Jr) * 1.0) + 1e-30
+    bad = np.nonzero(~(np.abs(PN - Pr) <= tol))[0]
+    assert len(bad) == 0, (bad[:5], F[bad[:5]], T[bad[:5]], W[bad[:5]], R[bad[:5]], PN[bad[:5]], Pr[bad[:5]])
     sim.close()
 
 
@@ -198,7 +222,8 @@ def test_emission_and_injection_match_oracle(pic):
     F_got, J_got, P_got = sim.face_emission()
     assert np.array_equal(F_got, Fv)
     ok = J > 1e-200
-    assert np.all(np.abs(J_got[ok] / J[ok] - 1) <= 1e-8)
+    bad = np.nonzero(ok & ~(np.abs(J_got / np.where(ok, J, 1.0) - 1) <= 1e-8))[0]
+    assert len(bad) == 0, (bad[:5], Fv[bad[:5]], J_got[bad[:5]], J[bad[:5]])
     N, new_e = OS.emit(st, J)
     st.acc_heat += PN * g.dx * g.dx * cfg["dt"]
     new_ev, new_sp = OS.inject(st)

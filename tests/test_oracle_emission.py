@@ -63,9 +63,12 @@ def test_gamow_exponent_at_fermi_level_matches_forbes_v():
 
 
 def test_nottingham_inner_closed_form_matches_definition():
+    # relative agreement everywhere, including far above E_F where I(W) ~ -(kT)^2 (w+1) e^-w
     for kT in (0.02585, 0.3):
-        for W in (-6.0, -1.0, -0.05, 0.0, 0.02, 0.7, 3.0):
-            assert em.nottingham_inner(W, kT) == pytest.approx(em.nottingham_inner_quad(W, kT), rel=1e-9, abs=1e-14)
+        for W in (-6.0, -1.0, -0.05, 0.0, 0.02, 0.7, 3.0, 6.0):
+            assert em.nottingham_inner(W, kT) == pytest.approx(em.nottingham_inner_quad(W, kT), rel=1e-9)
+    w = 60.0
+    assert em._L(np.array([w]))[0] == pytest.approx(math.exp(-w) * (1 - math.exp(-w) / 4), rel=1e-12)
 
 
 @pytest.mark.slow
@@ -84,7 +87,8 @@ def test_flat_limit_and_monotonicity():
 @pytest.mark.slow
 def test_fixed_rule_matches_adaptive_quadrature():
     cases = [(8.0, 300.0, 4.5, math.inf), (10.0, 2000.0, 4.3, 5.0), (2.0, 3500.0, 4.8, 3.0),
-             (13.0, 800.0, 4.1, 15.0), (1.2, 4000.0, 4.9, 1.0)]
+             (13.0, 800.0, 4.1, 15.0), (1.2, 4000.0, 4.9, 1.0), (0.0609, 3300.0, 4.5, 2.0),
+             (0.17, 3300.0, 4.5, 2.0), (1.955, 614.0, 4.37, 2.67), (0.1, 3000.0, 4.5, math.inf)]
     F, T, W, R = (np.array(c) for c in zip(*cases))
     J, PN = em.current_density_fixed(F, T, W, R)
     for r, c in enumerate(cases):
