@@ -105,7 +105,10 @@ typedef struct {
   double V0;                            /* anode potential [V] */
   double max_face_field, max_J, max_T;  /* V/m, A/m^2, K */
   double emitted_current;               /* A, from the last emission pass */
-  double ms[8]; /* last-step ms of: emit+inject, push, sort, collide, deposit, solve+E, heat, total */
+  double ms[8]; /* ms of the last pic_step call, summed over its steps: emit+inject, push, sort,
+                   collide, deposit, solve+E, heat, total (CUDA events on the library stream) */
+  int64_t kernel_launches;  /* kernels launched by the library since create */
+  int64_t emission_evals;   /* transmission evaluations of the emission integral this step */
 } pic_diag_t;
 
 typedef struct pic_s pic_t;

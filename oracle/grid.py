@@ -50,26 +50,33 @@ class Grid:
 
     # -- faces ---------------------------------------------------------------------------
     def _faces(self):
+        """Vacuum cells in linear order, per cell the directions 0..5 in order (array form of the
+        double loop: a face exists toward a solid neighbour, or toward z < 0 from a k = 0 cell)."""
         nx, ny, nz = self.nx, self.ny, self.nz
-        vcell, fdir, owner = [], [], []
         solid = self.solid
-        for k in range(nz):
-            for j in range(ny):
-                for i in range(nx):
-                    if solid[k, j, i]:
-                        continue
-                    for d in range(6):
-                        ni, nj, nk = i + DIRS[d, 0], j + DIRS[d, 1], k + DIRS[d, 2]
-                        if d == 4 and k == 0:
-                            vcell.append(self.cell_index(i, j, k)); fdir.append(d); owner.append(-1)
-                            continue
-                        if 0 <= ni < nx and 0 <= nj < ny and 0 <= nk < nz and solid[nk, nj, ni]:
-                            vcell.append(self.cell_index(i, j, k)); fdir.append(d)
-                            owner.append(self.cell_index(ni, nj, nk))
-        self.face_vcell = np.array(vcell, dtype=np.int64)
-        self.face_dir = np.array(fdir, dtype=np.int64)
-        self.face_owner = np.array(owner, dtype=np.int64)
-        self.nface = len(vcell)
+        vac = ~solid
+        has = np.zeros((nz, ny, nx, 6), dtype=bool)
+        own = np.full((nz, ny, nx, 6), -1, dtype=np.int64)
+        cidx = np.arange(self.ncell, dtype=np.int64).reshape(nz, ny, nx)
+        for d in range(6):
+            di, dj, dk = DIRS[d]
+            nb_solid = np.zeros_like(solid)
+            nb_idx = np.full(solid.shape, -1, dtype=np.int64)
+            src = (slice(max(dk, 0), nz + min(dk, 0)), slice(max(dj, 0), ny + min(dj, 0)), slice(max(di, 0), nx + min(di, 0)))
+            dst = (slice(max(-dk, 0), nz + min(-dk, 0)), slice(max(-dj, 0), ny + min(-dj, 0)), slice(max(-di, 0), nx + min(-di, 0)))
+            nb_solid[dst] = solid[src]
+            nb_idx[dst] = cidx[src]
+            has[..., d] = vac & nb_solid
+            own[..., d] = np.where(nb_solid, nb_idx, -1)
+            if d == 4:
+                has[0, :, :, 4] = vac[0]            # cathode plane under a vacuum cell
+                own[0, :, :, 4] = -1
+        flat = has.reshape(-1, 6)
+        cells, dirs = np.nonzero(flat)
+        self.face_vcell = cells.astype(np.int64)
+        self.face_dir = dirs.astype(np.int64)
+        self.face_owner = own.reshape(-1, 6)[cells, dirs]
+        self.nface = len(cells)
         self.face_key = self.face_vcell * 6 + self.face_dir     # ascending by construction
 
     def face_cell_ijk(self, f):

@@ -34,6 +34,7 @@ struct Consts {
 struct Tables {
   const double *x16, *w16;   // Gauss-Legendre on [-1,1]
   const double *x32, *w32;
+  const double *c32, *s32;   // cos and sin of the angles pi/2 (x32 + 1)
 };
 
 struct Barrier {
@@ -145,10 +146,8 @@ __host__ __device__ inline double transmission(const Barrier &b, const Consts &C
   const double m = 0.5 * (x1 + x2), h = 0.5 * (x2 - x1);
   double s = 0.0;
   for (int i = 0; i < 32; ++i) {
-    const double th = 1.5707963267948966 * (T.x32[i] + 1.0);
-    const double st = sin(th), ct = cos(th);
-    const double x = m - h * ct;
-    s += T.w32[i] * sqrt(fmax(U(b, x) - W, 0.0)) * st;
+    const double x = m - h * T.c32[i];
+    s += T.w32[i] * sqrt(fmax(U(b, x) - W, 0.0)) * T.s32[i];
   }
   const double G = C.g * 1.5707963267948966 * h * s;
   return G > 700.0 ? exp(-G) : 1.0 / (1.0 + exp(G));
@@ -174,7 +173,7 @@ __host__ __device__ inline Acc panel_below(const Barrier &br, const Consts &C, c
 
 // (J [A/m^2], PN [W/m^2]); F in V/nm, T in K, phi in eV, R in nm (R <= 0 or not finite: flat)
 __host__ __device__ inline void current_density(const Consts &C, const Tables &T, double F, double Temp, double phi,
-                                                double R, double *J_out, double *P_out) {
+                                                double R, double *J_out, double *P_out, int *n_eval = nullptr) {
   if (!(F > 0.0)) { *J_out = 0.0; *P_out = 0.0; return; }
   Barrier b;
   b.F = F; b.phi = phi; b.Q = C.Q;
@@ -215,6 +214,7 @@ __host__ __device__ inline void current_density(const Consts &C, const Tables &T
         const double nxt = side == 0 ? fmin(pos + w, M) : fmax(pos - w, M);
         const Acc r = side == 0 ? panel_below(b, C, T, pos, nxt, kT, xm) : panel_below(b, C, T, nxt, pos, kT, xm);
         J += r.J; P += r.P;
+        if (n_eval) *n_eval += 16;
         pos = nxt;
         if (pos == M) break;
         w *= 2.0;
@@ -230,6 +230,7 @@ __host__ __device__ inline void current_density(const Consts &C, const Tables &T
         const double nxt = fmax(pos - w, Wcut);
         const Acc r = panel_below(b, C, T, nxt, pos, kT, xm);
         J += r.J; P += r.P;
+        if (n_eval) *n_eval += 16;
         pos = nxt;
         if (pos == Wcut) break;
         if (it >= 1 && fabs(r.J) <= 1e-18 * fabs(J) && fabs(r.P) <= 1e-18 * fabs(P)) break;

@@ -253,33 +253,40 @@ static void vcycle(pic_t *h, int l) {
   const T h2 = (T)(L.h * L.h), inv_h2 = (T)(1.0 / (L.h * L.h));
   const int last = (int)h->mg.size() - 1;
   if (l == last) {
+    ++h->nlaunch;
     k_coarse<T><<<1, 1024, 0, h->stream>>>(lvl_u<T>(L), lvl_f<T>(L), L.dir, L.nx, L.ny, L.nz, h2, 60);
     return;
   }
   const int g = node_grid(h, L.nnode / 2 + 1);
   for (int s = 0; s < 2; ++s)
-    for (int c = 0; c < 2; ++c) k_smooth<T><<<g, kThreads, 0, h->stream>>>(lvl_u<T>(L), lvl_f<T>(L), L.dir, L.nx, L.ny, L.nz, h2, c);
+    for (int c = 0; c < 2; ++c) { ++h->nlaunch; k_smooth<T><<<g, kThreads, 0, h->stream>>>(lvl_u<T>(L), lvl_f<T>(L), L.dir, L.nx, L.ny, L.nz, h2, c); }
+  ++h->nlaunch;
   k_residual<T><<<node_grid(h, L.nnode), kThreads, 0, h->stream>>>(lvl_u<T>(L), lvl_f<T>(L), lvl_r<T>(L), L.dir, L.nx,
                                                                  L.ny, L.nz, inv_h2);
   MgLevel &Cl = h->mg[l + 1];
+  ++h->nlaunch;
   k_restrict<T, T><<<node_grid(h, Cl.nnode), kThreads, 0, h->stream>>>(lvl_r<T>(L), L.nx, L.ny, lvl_f<T>(Cl), lvl_u<T>(Cl),
                                                                        Cl.dir, Cl.nx, Cl.ny, Cl.nz);
   vcycle<T>(h, l + 1);
+  ++h->nlaunch;
   k_prolong<T, T><<<node_grid(h, L.nnode), kThreads, 0, h->stream>>>(lvl_u<T>(Cl), Cl.nx, Cl.ny, lvl_u<T>(L), L.dir, L.nx,
                                                                      L.ny, L.nz);
   for (int s = 0; s < 2; ++s)
-    for (int c = 1; c >= 0; --c) k_smooth<T><<<g, kThreads, 0, h->stream>>>(lvl_u<T>(L), lvl_f<T>(L), L.dir, L.nx, L.ny, L.nz, h2, c);
+    for (int c = 1; c >= 0; --c) { ++h->nlaunch; k_smooth<T><<<g, kThreads, 0, h->stream>>>(lvl_u<T>(L), lvl_f<T>(L), L.dir, L.nx, L.ny, L.nz, h2, c); }
 }
 
 template <typename T>
 static void cycle_fine(pic_t *h) {
   MgLevel &L = h->mg[0];
+  ++h->nlaunch;
   k_to_level<T><<<node_grid(h, L.nnode), kThreads, 0, h->stream>>>(h->res, lvl_f<T>(L), lvl_u<T>(L), L.nnode);
   vcycle<T>(h, 0);
+  ++h->nlaunch;
   k_correct<T><<<node_grid(h, L.nnode), kThreads, 0, h->stream>>>(h->phi, lvl_u<T>(L), L.dir, L.nnode);
 }
 
 int stage_efield(pic_t *h) {
+  ++h->nlaunch;
   k_efield<<<node_grid(h, h->nnode), kThreads, 0, h->stream>>>(h->phi, h->E, h->nx, h->ny, h->nz, 1.0 / (2.0 * h->dx),
                                                                1.0 / h->dx);
   return launch_check(h, "efield");
@@ -288,6 +295,7 @@ int stage_efield(pic_t *h) {
 int mg_build_masks(pic_t *h) {
   for (size_t l = 1; l < h->mg.size(); ++l) {
     MgLevel &F = h->mg[l - 1], &Cl = h->mg[l];
+    ++h->nlaunch;
     k_inject_mask<<<node_grid(h, Cl.nnode), kThreads, 0, h->stream>>>(F.dir, F.nx, F.ny, Cl.dir, Cl.nx, Cl.ny, Cl.nz);
   }
   return launch_check(h, "mg_masks");
@@ -297,6 +305,7 @@ int mg_build_masks(pic_t *h) {
 int stage_solve(pic_t *h, bool zero_charge, double V0) {
   MgLevel &L = h->mg[0];
   const double unit = kQe * h->prm.w_min / 1073741824.0 / (h->dx * h->dx * h->dx) / kEps0;
+  ++h->nlaunch;
   k_rhs<<<node_grid(h, L.nnode), kThreads, 0, h->stream>>>(h->Q, h->rhs, h->phi, L.dir, h->nx, h->ny, h->nz, unit, V0,
                                                            zero_charge ? 1 : 0);
   const int nb = node_grid(h, L.nnode);
@@ -306,8 +315,10 @@ int stage_solve(pic_t *h, bool zero_charge, double V0) {
   double lifted = 0.0;
   int cyc = 0;
   for (;; ++cyc) {
+    ++h->nlaunch;
     k_residual64<<<nb, kThreads, 0, h->stream>>>(h->phi, h->rhs, h->res, L.dir, h->nx, h->ny, h->nz, inv_h2, V0, h->red,
                                                  cyc == 0 ? 1 : 0);
+    ++h->nlaunch;
     k_sum_partials<<<1, 32, 0, h->stream>>>(h->red, nb, h->red_out);
     PIC_CUDA(h, cudaMemcpyAsync(norms, h->red_out, sizeof norms, cudaMemcpyDeviceToHost, h->stream));
     PIC_CUDA(h, cudaStreamSynchronize(h->stream));

@@ -146,6 +146,7 @@ int stage_heat(pic_t *h) {
   PIC_CUDA(h, cudaMemsetAsync(H.src, 0, H.nvox * sizeof(double), h->stream));
   PIC_CUDA(h, cudaMemsetAsync(H.cur, 0, H.nvox * sizeof(double), h->stream));
   Faces &fc = h->faces;
+  ++h->nlaunch;
   k_heat_sources<<<grid_for(fc.n), kThreads, 0, h->stream>>>(fc.owner_vox, fc.n, fc.acc_heat, fc.acc_charge,
                                                              (const long long *)fc.acc_Eb, (const long long *)fc.acc_Es,
                                                              dth, H.src, H.cur);
@@ -157,6 +158,7 @@ int stage_heat(pic_t *h) {
   a.T_amb = h->prm.T0;
   int *status = h->long_n + 7;
   a.status = status;
+  ++h->nlaunch;
   k_heat_solve<<<1, 1024, 0, h->stream>>>(a);
   PIC_CUDA(h, cudaMemsetAsync(fc.acc_heat, 0, fc.n * sizeof(double), h->stream));
   PIC_CUDA(h, cudaMemsetAsync(fc.acc_charge, 0, fc.n * sizeof(double), h->stream));

@@ -278,6 +278,7 @@ static int particle_grid(pic_t *h) { return h->nsm * 8; }
 int stage_keys(pic_t *h, int s) {
   Species &S = h->sp[s];
   if (h->keys_valid[s]) PIC_CUDA(h, cudaMemsetAsync(S.cnt, 0, (h->ncell + 1) * sizeof(uint32_t), h->stream));
+  ++h->nlaunch;
   k_keys<<<particle_grid(h), kThreads, 0, h->stream>>>(S.a, S.key, S.cnt, h->nx, h->ny, h->clock, s);
   h->keys_valid[s] = true;
   return launch_check(h, "keys");
@@ -296,6 +297,7 @@ int stage_push(pic_t *h) {
     a.face_key = h->faces.key; a.nface = h->faces.n;
     a.acc_sput = (unsigned long long *)h->faces.acc_sput; a.acc_Eb = (unsigned long long *)h->faces.acc_Eb;
     a.clk = h->clock;
+    ++h->nlaunch;
     k_push<<<particle_grid(h), kThreads, 0, h->stream>>>(a);
     h->keys_valid[s] = true;
   }
@@ -310,12 +312,17 @@ int stage_sort(pic_t *h) {
     Species &S = h->sp[s];
     if (!h->keys_valid[s]) PIC_TRY(stage_keys(h, s));
     PIC_TRY(scan_u32(h, S.cnt, S.off, h->ncell, nullptr, S.off + h->ncell));
+    ++h->nlaunch;
     k_scatter<<<particle_grid(h), kThreads, 0, h->stream>>>(S.key, S.cnt, S.off, S.perm, h->clock, s);
     PIC_CUDA(h, cudaMemsetAsync(long_n, 0, sizeof(int), h->stream));
+    ++h->nlaunch;
     k_fix_short<<<particle_grid(h), kThreads, 0, h->stream>>>(S.key, S.off, S.perm, h->ncell, long_list, long_n,
                                                               long_cap, h->clock);
+    ++h->nlaunch;
     k_fix_long<<<h->nsm, 1024, 0, h->stream>>>(S.perm, long_list, long_n, long_cap);
+    ++h->nlaunch;
     k_gather<<<particle_grid(h), kThreads, 0, h->stream>>>(S.a, S.b, S.perm, S.off, h->ncell);
+    ++h->nlaunch;
     k_set_count<<<1, 1, 0, h->stream>>>(h->clock, s, S.off, h->ncell);
     std::swap(S.a, S.b);
     h->keys_valid[s] = false;
@@ -325,8 +332,10 @@ int stage_sort(pic_t *h) {
 
 int stage_deposit(pic_t *h) {
   PIC_CUDA(h, cudaMemsetAsync(h->Q, 0, h->nnode * sizeof(unsigned long long), h->stream));
+  ++h->nlaunch;
   k_deposit<<<particle_grid(h), kThreads, 0, h->stream>>>(h->sp[PIC_ELECTRON].a, -1, h->Q, h->nx, h->ny, h->clock,
                                                           PIC_ELECTRON);
+  ++h->nlaunch;
   k_deposit<<<particle_grid(h), kThreads, 0, h->stream>>>(h->sp[PIC_ION].a, 1, h->Q, h->nx, h->ny, h->clock, PIC_ION);
   return launch_check(h, "deposit");
 }

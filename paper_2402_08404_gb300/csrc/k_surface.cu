@@ -9,7 +9,7 @@
 
 namespace pic {
 
-__constant__ double c_gl16x[16], c_gl16w[16], c_gl32x[32], c_gl32w[32];
+__constant__ double c_gl16x[16], c_gl16w[16], c_gl32x[32], c_gl32w[32], c_gl32c[32], c_gl32s[32];
 __constant__ gtf::Consts c_gtf;
 
 struct FaceGeom {
@@ -62,7 +62,7 @@ __global__ void k_face_field(const int32_t *vcell, const int8_t *dir, int64_t nf
 
 __device__ __forceinline__ gtf::Tables dev_tables() {
   gtf::Tables t;
-  t.x16 = c_gl16x; t.w16 = c_gl16w; t.x32 = c_gl32x; t.w32 = c_gl32w;
+  t.x16 = c_gl16x; t.w16 = c_gl16w; t.x32 = c_gl32x; t.w32 = c_gl32w; t.c32 = c_gl32c; t.s32 = c_gl32s;
   return t;
 }
 
@@ -86,7 +86,7 @@ struct EmitArgs {
   double *J, *PN, *acc_heat, *acc_charge;
   uint32_t *cnt;
   uint64_t seed;
-  const DevClock *clk;
+  DevClock *clk;
 };
 
 __global__ void k_emit_count(EmitArgs a) {
@@ -97,7 +97,9 @@ __global__ void k_emit_count(EmitArgs a) {
     const double T = v >= 0 ? a.Tvox[v] : a.T0;
     const double R = v >= 0 ? a.R_nm : -1.0;
     double J, P;
-    gtf::current_density(c_gtf, tb, a.F[f] * 1e-9, T, a.phi_w, R, &J, &P);
+    int nev = 0;
+    gtf::current_density(c_gtf, tb, a.F[f] * 1e-9, T, a.phi_w, R, &J, &P, &nev);
+    atomicAdd((unsigned long long *)&a.clk->ctr[cWevals], (unsigned long long)nev);
     a.J[f] = J;
     a.PN[f] = P;
     a.acc_heat[f] += P * a.A * a.dt;
@@ -281,6 +283,7 @@ __global__ void k_inject_write(InjWrite a) {
 static int face_grid(pic_t *h) { return grid_for(h->faces.n, 128); }
 
 int stage_face_field(pic_t *h) {
+  ++h->nlaunch;
   k_face_field<<<grid_for(h->faces.n), kThreads, 0, h->stream>>>(h->faces.vcell, h->faces.dir, h->faces.n, h->phi, h->nx,
                                                                  h->ny, h->dx, h->faces.F);
   return launch_check(h, "face_field");
@@ -300,12 +303,20 @@ int emission_tables_upload(pic_t *h) {
   PIC_CUDA(h, cudaMemcpyToSymbol(c_gl16w, w16, sizeof w16));
   PIC_CUDA(h, cudaMemcpyToSymbol(c_gl32x, x32, sizeof x32));
   PIC_CUDA(h, cudaMemcpyToSymbol(c_gl32w, w32, sizeof w32));
+  double c32[32], s32[32];
+  for (int i = 0; i < 32; ++i) {
+    c32[i] = cos(0.5 * kPi * (x32[i] + 1.0));
+    s32[i] = sin(0.5 * kPi * (x32[i] + 1.0));
+  }
+  PIC_CUDA(h, cudaMemcpyToSymbol(c_gl32c, c32, sizeof c32));
+  PIC_CUDA(h, cudaMemcpyToSymbol(c_gl32s, s32, sizeof s32));
   PIC_CUDA(h, cudaMemcpyToSymbol(c_gtf, &C, sizeof C));
   return PIC_OK;
 }
 
 int emission_eval_dev(pic_t *h, const double *F, const double *T, const double *W, const double *R, double *J,
                       double *PN, int64_t n) {
+  ++h->nlaunch;
   k_emission_eval<<<grid_for(n, 64), 64, 0, h->stream>>>(F, T, W, R, J, PN, n);
   return launch_check(h, "emission_eval");
 }
@@ -323,11 +334,15 @@ int stage_emit(pic_t *h) {
     a.R_nm = h->geo.tip_radius * 1e9; a.A = A; a.dt = h->prm.dt; a.w_min = h->prm.w_min;
     a.J = fc.J; a.PN = fc.PN; a.acc_heat = fc.acc_heat; a.acc_charge = fc.acc_charge; a.cnt = fc.cnt;
     a.seed = h->prm.seed; a.clk = h->clock;
+    ++h->nlaunch;
     k_emit_count<<<face_grid(h), 128, 0, h->stream>>>(a);
     PIC_TRY(scan_u32(h, fc.cnt, fc.off, fc.n, nullptr, tot1));
+    ++h->nlaunch;
     k_check_face_new<<<1, 1, 0, h->stream>>>(h->clock, tot1, nullptr, PIC_ELECTRON, h->sp[PIC_ELECTRON].cap, go);
+    ++h->nlaunch;
     k_emit_write<<<grid_for(fc.n), kThreads, 0, h->stream>>>(h->sp[PIC_ELECTRON].a, fc.vcell, fc.dir, fc.n, fc.cnt,
                                                              fc.off, h->nx, h->ny, h->prm.seed, h->clock, go);
+    ++h->nlaunch;
     k_commit_face_new<<<1, 1, 0, h->stream>>>(h->clock, tot1, nullptr, PIC_ELECTRON, go, cEmitted, cEmitted);
     PIC_TRY(launch_check(h, "emit"));
   }
@@ -348,9 +363,11 @@ int stage_inject(pic_t *h) {
   a.acc_evap = fc.acc_evap; a.acc_heat = fc.acc_heat; a.acc_sput = (long long *)fc.acc_sput;
   a.cnt = fc.cnt; a.wu = fc.wu; a.cnt2 = fc.cnt2; a.wu2 = fc.wu2;
   a.evap = (fl & PIC_F_EVAP) != 0; a.sput = (fl & PIC_F_SPUTTER) != 0;
+  ++h->nlaunch;
   k_inject_count<<<grid_for(fc.n), kThreads, 0, h->stream>>>(a);
   PIC_TRY(scan_u32(h, fc.cnt, fc.off, fc.n, nullptr, tot1));
   PIC_TRY(scan_u32(h, fc.cnt2, fc.off2, fc.n, nullptr, tot2));
+  ++h->nlaunch;
   k_check_face_new<<<1, 1, 0, h->stream>>>(h->clock, tot1, tot2, PIC_NEUTRAL, h->sp[PIC_NEUTRAL].cap, go);
   InjWrite w;
   w.n = h->sp[PIC_NEUTRAL].a; w.vcell = fc.vcell; w.owner_vox = fc.owner_vox; w.dir = fc.dir; w.nface = fc.n;
@@ -358,7 +375,9 @@ int stage_inject(pic_t *h) {
   w.cnt = fc.cnt; w.off = fc.off; w.wu = fc.wu; w.cnt2 = fc.cnt2; w.off2 = fc.off2; w.wu2 = fc.wu2; w.total1 = tot1;
   w.acc_Es = (unsigned long long *)fc.acc_Es; w.nx = h->nx; w.ny = h->ny; w.seed = h->prm.seed; w.clk = h->clock;
   w.go = go;
+  ++h->nlaunch;
   k_inject_write<<<grid_for(fc.n), kThreads, 0, h->stream>>>(w);
+  ++h->nlaunch;
   k_commit_face_new<<<1, 1, 0, h->stream>>>(h->clock, tot1, tot2, PIC_NEUTRAL, go, cEvaporated, cSputtered);
   return launch_check(h, "inject");
 }

@@ -250,6 +250,7 @@ int pic_create(const pic_geometry_t *geometry, const pic_grid_t *grid, const pic
   };
   HostGeom G;
   build_geometry(h, G);
+  h->solid_host = G.solid;
   bool okalloc = true;
   auto A = [&](void *p) { if (!p) okalloc = false; };
   // grids
@@ -422,8 +423,7 @@ int pic_load_particles(pic_t *h, int s, const float *x, const float *y, const fl
   if (n > S.cap) return pic_fail(h, PIC_E_CAPACITY, "load exceeds the species capacity");
   if (n > 0 && (!x || !y || !z || !vx || !vy || !vz || !w || !id)) return PIC_E_INVALID;
   // validation: inside the domain and outside the tip (host copy of the solid mask)
-  std::vector<uint8_t> solid(h->ncell);
-  PIC_CUDA(h, cudaMemcpy(solid.data(), h->solid, h->ncell, cudaMemcpyDeviceToHost));
+  const std::vector<uint8_t> &solid = h->solid_host;
   for (int64_t p = 0; p < n; ++p) {
     if (!(x[p] >= 0 && x[p] < h->nx && y[p] >= 0 && y[p] < h->ny && z[p] >= 0 && z[p] < h->nz))
       return pic_fail(h, PIC_E_INVALID, "SP " + std::to_string(p) + " outside the domain");
@@ -649,9 +649,11 @@ int pic_step(pic_t *h, int nsteps) {
   int64_t step = c.step;
   cudaEvent_t ev[8];
   for (int i = 0; i < 8; ++i) cudaEventCreate(&ev[i]);
+  float acc_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   int rc = PIC_OK;
   for (int it = 0; it < nsteps && rc == PIC_OK; ++it) {
     cudaEventRecord(ev[0], h->stream);
+    ++h->nlaunch;
     k_begin_step<<<1, 1, 0, h->stream>>>(h->clock);
     rc = stage_emit(h);
     cudaEventRecord(ev[1], h->stream);
@@ -667,15 +669,21 @@ int pic_step(pic_t *h, int nsteps) {
     cudaEventRecord(ev[6], h->stream);
     ++step;
     if (rc == PIC_OK && (h->prm.flags & PIC_F_HEAT) && h->prm.n_heat > 0 && step % h->prm.n_heat == 0) rc = stage_heat(h);
+    ++h->nlaunch;
     k_end_step<<<1, 1, 0, h->stream>>>(h->clock);
     cudaEventRecord(ev[7], h->stream);
+    // per-stage times summed over the steps of this call (events on the library stream)
+    cudaEventSynchronize(ev[7]);
+    float t;
+    for (int i = 0; i < 7; ++i) {
+      cudaEventElapsedTime(&t, ev[i], ev[i + 1]);
+      acc_ms[i] += t;
+    }
+    cudaEventElapsedTime(&t, ev[0], ev[7]);
+    acc_ms[7] += t;
   }
-  cudaEventSynchronize(ev[7]);
-  if (rc == PIC_OK && nsteps > 0) {
-    for (int i = 0; i < 6; ++i) cudaEventElapsedTime(&h->ms[i], ev[i], ev[i + 1]);
-    cudaEventElapsedTime(&h->ms[6], ev[6], ev[7]);
-    cudaEventElapsedTime(&h->ms[7], ev[0], ev[7]);
-  }
+  if (rc == PIC_OK && nsteps > 0)
+    for (int i = 0; i < 8; ++i) h->ms[i] = acc_ms[i];
   for (int i = 0; i < 8; ++i) cudaEventDestroy(ev[i]);
   if (rc != PIC_OK) return rc;
   PIC_TRY(launch_check(h, "step"));
@@ -709,9 +717,11 @@ int pic_diagnostics(pic_t *h, pic_diag_t *out) {
   PIC_CUDA(h, cudaMemsetAsync(sums, 0, 4 * 8, h->stream));
   for (int s = 0; s < 3; ++s) {
     out->count[s] = c.n[s];
+    ++h->nlaunch;
     k_sum_w<<<h->nsm * 4, kThreads, 0, h->stream>>>(h->sp[s].a.w, h->clock, s, sums + s);
     out->removed[s] = c.ctr[cRemovedE + s];
   }
+  ++h->nlaunch;
   k_sum_q<<<h->nsm * 4, kThreads, 0, h->stream>>>(h->Q, h->nnode, sums + 3);
   unsigned long long hs[4];
   PIC_TRY(d2h(h, hs, sums, sizeof hs));
@@ -745,6 +755,8 @@ int pic_diagnostics(pic_t *h, pic_diag_t *out) {
     out->max_T = *std::max_element(T.begin(), T.end());
   }
   for (int i = 0; i < 8; ++i) out->ms[i] = h->ms[i];
+  out->kernel_launches = h->nlaunch;
+  out->emission_evals = c.ctr[cWevals];
   return PIC_OK;
 }
 

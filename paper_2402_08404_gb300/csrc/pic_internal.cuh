@@ -40,7 +40,7 @@ enum Purpose : uint32_t { kEmit = 1, kPair = 2, kIon = 3, kScat = 4, kDfi = 5, k
 // device counters (int64), indices
 enum Ctr {
   cEmitted = 0, cEvaporated, cSputtered, cImpactIon, cFieldIon, cRemovedE, cRemovedN, cRemovedI,
-  cIonImpacts, cNum
+  cIonImpacts, cWevals, cNum
 };
 
 // error bits set by kernels
@@ -155,6 +155,8 @@ struct pic_s {
   double last_mg_res = 0;
   float ms[8] = {0};
   int64_t solid_count = 0;
+  int64_t nlaunch = 0;           // kernels launched by the library since create
+  std::vector<uint8_t> solid_host;  // host copy of the solid-cell mask (load validation)
 };
 
 namespace pic {

@@ -54,7 +54,7 @@ class Diag(C.Structure):
                 ("ion_impacts", C.c_int64), ("total_charge_fixed", C.c_int64), ("mg_cycles", C.c_int),
                 ("mg_residual", C.c_double), ("V0", C.c_double), ("max_face_field", C.c_double),
                 ("max_J", C.c_double), ("max_T", C.c_double), ("emitted_current", C.c_double),
-                ("ms", C.c_double * 8)]
+                ("ms", C.c_double * 8), ("kernel_launches", C.c_int64), ("emission_evals", C.c_int64)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)

@@ -11,9 +11,11 @@ a pre-seeded population around the tip:
     half on the ions' positions with the ions' weights (a locally neutral cloud) and a 2 eV
     Maxwellian;
   * mix 40 % e- / 40 % Cu / 20 % Cu+ by SP count, weights uniform integers 1..8 (units of w_min);
-  * w_min = 0.01 real particles per weight unit, which puts the near-tip neutral density
-    near 1e26 m^-3 on these grids (w_min = 1 would give a space charge far above the
-    barrier-suppression field and ionize every neutral in the first step);
+  * w_min = 0.01 real particles per weight unit on the 1 nm grid and 1e-5 on the 0.5 nm
+    grids: the net space charge of the seeded beam then stays below about 0.5 GV/m, well
+    under the applied field (w_min = 1e-4 on the 0.5 nm grid screens the apex down to
+    ~1 GV/m; 0.01 gives fields far above the barrier-suppression limit and ionizes every
+    neutral in the first step);
   * ids 0..N-1 in the order electrons, neutrals, ions.
 
 Points closer than one cell to the tip surface are redrawn, so no SP starts in a solid cell.
@@ -34,10 +36,10 @@ CONFIGS = {
                   w_max_units=1024, n_heat=1000, seed=1),
     "production": dict(nx=256, ny=256, nz=512, dx=0.5e-9, tip_radius=5e-9, tip_height=60e-9,
                        apex_field=10e9, n_sp=20_000_000, dt=5e-17, steps=10_000, T0=300.0,
-                       work_function=4.5, w_min=0.01, w_max_units=1024, n_heat=1000, seed=1),
+                       work_function=4.5, w_min=1e-5, w_max_units=1024, n_heat=1000, seed=1),
     "large": dict(nx=512, ny=512, nz=1024, dx=0.5e-9, tip_radius=10e-9, tip_height=100e-9,
                   apex_field=12e9, n_sp=200_000_000, dt=5e-17, steps=5000, T0=300.0,
-                  work_function=4.5, w_min=0.01, w_max_units=1024, n_heat=1000, seed=1),
+                  work_function=4.5, w_min=1e-5, w_max_units=1024, n_heat=1000, seed=1),
 }
 
 
