@@ -179,6 +179,21 @@ int pic_diagnostics(pic_t *h, pic_diag_t *out);
 int pic_emission_eval(pic_t *h, const double *F, const double *T, const double *phi_w,
                       const double *R, double *J, double *PN, int64_t n);
 
+/* Allocation-free form of pic_emission_eval, for callers that cannot take device memory: a
+ * process whose device memory is fully reserved by another framework's pool, or a latency-bound
+ * loop that cannot afford the device-wide synchronisation of cudaFree.  The paper has no
+ * counterpart; this is a property of the library only.  Same arguments, units and results as
+ * pic_emission_eval, for at most PIC_NOALLOC_MAX_TUPLES tuples per call (PIC_E_INVALID above
+ * that, with a message).  The inputs and outputs are staged through one fixed device array
+ * built into the library (1.5 MiB, held on every GPU that loads it until exit); no cudaMalloc,
+ * cudaFree or allocating routine is called.  The first call on a device looks the array's
+ * address up (cudaGetSymbolAddress) with that device current: make it before any stream
+ * capture starts there.  All calls share the array, so calls whose work overlaps on the GPU
+ * race and must be serialised by the caller. */
+#define PIC_NOALLOC_MAX_TUPLES 32768
+int pic_emission_eval_noalloc(pic_t *h, const double *F, const double *T, const double *phi_w,
+                              const double *R, double *J, double *PN, int64_t n);
+
 #ifdef __cplusplus
 }
 #endif

@@ -93,6 +93,7 @@ def lib():
         L.pic_set_face_accumulators.argtypes = [vp] * 7
         L.pic_diagnostics.argtypes = [vp, C.POINTER(Diag)]
         L.pic_emission_eval.argtypes = [vp] * 7 + [i64]
+        L.pic_emission_eval_noalloc.argtypes = [vp] * 7 + [i64]
         _lib = L
     return _lib
 
@@ -289,6 +290,16 @@ class Pic:
             v = getattr(d, name)
             out[name] = list(v) if isinstance(v, C.Array) else v
         return out
+
+    def emission_eval_noalloc(self, F, T, W, R):
+        """pic_emission_eval_noalloc: the same evaluation staged through the library's fixed
+        device array (no device allocation; at most PIC_NOALLOC_MAX_TUPLES tuples per call)."""
+        F, T, W, R = (np.ascontiguousarray(np.broadcast_to(a, np.shape(F)), dtype=np.float64) for a in (F, T, W, R))
+        J = np.zeros(F.size)
+        P = np.zeros(F.size)
+        self._check(lib().pic_emission_eval_noalloc(self.h, _ptr(F), _ptr(T), _ptr(W), _ptr(R), _ptr(J), _ptr(P),
+                                                    F.size))
+        return J, P
 
     def emission_eval(self, F, T, W, R):
         F, T, W, R = (np.ascontiguousarray(np.broadcast_to(a, np.shape(F)), dtype=np.float64) for a in (F, T, W, R))
