@@ -144,7 +144,9 @@ def inject(st):
         if Ninj >= 1:
             wu = surface.injection_weight_units(ncell, Ninj, wmin, prm["w_max_units"])
             nsp = int(math.floor(lam / (wu * wmin)))
-            st.acc_sput[f] -= int(nsp * wu * wmin) << surface.SPUT_FRAC_BITS
+            # the accumulator counts real atoms in 2^-24 units: remove the nsp*wu*w_min atoms
+            # the new SPs carry (Sec. 2.3.3), rounded down to the accumulator's resolution
+            st.acc_sput[f] -= int(math.floor(nsp * wu * wmin * 2.0 ** surface.SPUT_FRAC_BITS))
             for j in range(nsp):
                 u = philox.uniform(prm["seed"], philox.SPUT, f, n, 8 * j + np.arange(5))
                 pos, axis, sign, t = face_point(g, f, u[0], u[1])

@@ -42,3 +42,34 @@ def test_two_steps_keep_the_books():
     assert np.all(np.isfinite(st.T)) and np.any(st.T != CFG["T0"])
     # hot tip (2900 K) evaporates
     assert st.count["evaporated"] >= 0 and np.any(st.acc_evap > 0)
+
+
+def test_sputter_injection_conserves_atoms():
+    """Sputtered atoms handed to new SPs leave the face accumulator: before = after + injected
+    atoms, to the accumulator's 2^-24 resolution, for weights with fractional w_min * w."""
+    from oracle import surface
+    cfg = dict(CFG, w_min=0.37)
+    g = Grid(cfg["nx"], cfg["ny"], cfg["nz"], cfg["dx"], cfg["tip_radius"], cfg["tip_height"])
+    prm = dict(cfg, V0=1.0, next_id=0)
+    pop = synth.plasma(dict(cfg, n_sp=200), seed=3)
+    st = S.State(g, prm, pop, np.zeros((g.nz + 1, g.ny + 1, g.nx + 1)))
+    rng = np.random.default_rng(4)
+    atoms = np.where(rng.random(g.nface) < 0.2, rng.uniform(0.0, 6.0, g.nface), 0.0)
+    st.acc_sput[:] = np.floor(atoms * 2.0 ** surface.SPUT_FRAC_BITS).astype(np.int64)
+    before = st.acc_sput.copy()
+    _, new_sp = S.inject(st)
+    wmin = cfg["w_min"]
+    injected = np.zeros(g.nface)
+    frac = 2.0 ** surface.SPUT_FRAC_BITS
+    n_sp = P.count(new_sp)
+    assert n_sp > 0
+    # attribute each new SP to its face through the removed amount: per face the drop equals
+    # floor(nsp * wu * w_min * 2^24) with nsp * wu * w_min <= the atoms that were there
+    drop = before - st.acc_sput
+    assert np.all(drop >= 0)
+    assert np.all(st.acc_sput >= 0)
+    moved = drop > 0
+    assert moved.sum() > 0
+    assert abs(drop.sum() / frac - float(new_sp["w"].astype(np.float64).sum()) * wmin) <= moved.sum() / frac
+    # what stays behind is less than one SP of the chosen weight plus one atom
+    assert np.all(st.acc_sput[moved] / frac < before[moved] / frac)
