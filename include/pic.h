@@ -59,7 +59,9 @@ extern "C" {
 #define PIC_F_HEAT 0x20u        /* a10: heat + Joule every n_heat steps */
 #define PIC_F_SURROGATE 0x40u   /* a1 uses the trained MLP where it is inside its validated range */
 #define PIC_F_MIXED_MG 0x80u    /* a8: FP32 V-cycles with FP64 residual refinement (else FP64 V-cycles) */
-#define PIC_F_ALL 0xFFu
+#define PIC_F_FAST_INTEGRAL 0x100u  /* a1: Gamow quadrature and turning points in FP32 (J, P_N to ~1e-5
+                                       relative) in the step and in pic_emission_eval; else all FP64 */
+#define PIC_F_ALL 0xFFu         /* every stage, surrogate and mixed-precision solve; not FAST_INTEGRAL */
 
 typedef struct {
   double tip_radius; /* m */
@@ -109,6 +111,7 @@ typedef struct {
                    collide, deposit, solve+E, heat, total (CUDA events on the library stream) */
   int64_t kernel_launches;  /* kernels launched by the library since create */
   int64_t emission_evals;   /* transmission evaluations of the emission integral this step */
+  int64_t surrogate_faces;  /* faces whose emission came from the surrogate this step */
 } pic_diag_t;
 
 typedef struct pic_s pic_t;
@@ -161,6 +164,10 @@ int pic_get_face_accumulators(pic_t *h, double *evap, double *heat, double *char
 int pic_set_face_accumulators(pic_t *h, const double *evap, const double *heat, const double *charge,
                               const int64_t *sput, const int64_t *Eb, const int64_t *Es);
 
+/* Replace the PIC_F_* flags (e.g. switch the surrogate or the mixed-precision solve on or off
+ * between steps of the same state). */
+int pic_set_flags(pic_t *h, uint32_t flags);
+
 /* Stages of one step (each also usable alone; pic_step runs them all in this order). */
 int pic_emit(pic_t *h);        /* a1 emission + a2 evaporation/sputter injection (appends SPs) */
 int pic_push(pic_t *h);        /* a3 gather + leapfrog + boundary removal, ion impact records */
@@ -178,6 +185,32 @@ int pic_diagnostics(pic_t *h, pic_diag_t *out);
  * Evaluates the full FP64 thermal-field integral on the device (Sec. 2.3.1). */
 int pic_emission_eval(pic_t *h, const double *F, const double *T, const double *phi_w,
                       const double *R, double *J, double *PN, int64_t n);
+
+/* Emission surrogate (no counterpart in the paper): an MLP 4 -> 64 -> 64 -> 64 -> 2 with GELU,
+ * BF16 operands and FP32 accumulation on the tensor cores, mapping (log10 F, T, work function,
+ * log10 R | flat) to (log10 J - log10 J_c, eps_N = P_N/J), J_c the classical estimate (Murphy-Good
+ * Fowler-Nordheim + Richardson-Dushman with Schottky lowering).  Trained on tuples drawn over F 0.001-15 GV/m,
+ * T 300-4000 K, phi_w 4-5 eV, R 1-20 nm or flat, with targets from the full FP64 integral; a
+ * held-out set (half the training size) fills a validity map (bins whose every held-out sample has
+ * |dlog10 J| <= 0.015 wherever log10 J >= -5, a margin under the 0.02 bar); log10 J is
+ * clipped at -8 (no face emits below it).
+ * With PIC_F_SURROGATE, pic_emit/pic_step use it on faces inside the range and a valid bin,
+ * and the full integral elsewhere.  Parameters in the public layout: W1 (64x4), b1, W2 (64x64),
+ * b2, W3 (64x64), b3, W4 (2x64), b4 -- pic_mlp_num_params() floats, row-major [out][in]. */
+int pic_mlp_num_params(void);
+int pic_mlp_set_params(pic_t *h, const float *params);
+int pic_mlp_get_params(pic_t *h, float *params);
+/* Forward (and, with targets t, loss 0.5 mean sum (y - t)^2 and its gradient) on n host rows of
+ * 4 standardised inputs; y: n x 2 standardised outputs. */
+int pic_mlp_forward_backward(pic_t *h, const float *x, const float *t, int64_t n, float *y, float *loss, float *grad);
+/* Train and install; stats (8 doubles, optional): train loss, validation RMS and max |dlog10 J|
+ * over relevant samples, fraction of valid bins, fraction of valid held-out samples, ms of data
+ * generation, ms of training, optimiser steps. */
+int pic_surrogate_train(pic_t *h, int64_t nsamples, int epochs, int batch, double lr, uint64_t seed, double *stats);
+/* Surrogate J [A/m^2], P_N [W/m^2] of n host tuples (F [V/m], T [K], phi_w [eV], R [m], <= 0 flat);
+ * valid[i] = 1 where the step would use the surrogate for that tuple. */
+int pic_surrogate_eval(pic_t *h, const double *F, const double *T, const double *phi_w, const double *R, double *J,
+                       double *PN, uint8_t *valid, int64_t n);
 
 /* Allocation-free form of pic_emission_eval, for callers that cannot take device memory: a
  * process whose device memory is fully reserved by another framework's pool, or a latency-bound

@@ -38,4 +38,31 @@ __device__ __forceinline__ float3 gather_E(const float4 *__restrict__ E, float x
   return r;
 }
 
+// Classical estimate the surrogate corrects: log10 of (Murphy-Good FN with Forbes' v(f), t(f),
+// f capped at 1) + (Richardson-Dushman with Schottky lowering, barrier top capped at E_F);
+// F in GV/m, T in K, phi in eV; clipped at the floor.
+__device__ __forceinline__ double approx_log10J(double F, double T, double phi) {
+  const double a = 1.541434e-6, b = 6.830890, c = 1.439964, ln10 = 2.302585092994046;
+  const double f = fmin(c * F / (phi * phi), 1.0);
+  const double lf = log(f);
+  const double v = 1.0 - f + f / 6.0 * lf, t = 1.0 + f / 9.0 - f / 18.0 * lf;
+  const double lfn = log10(a * F * F / (phi * t * t)) + 18.0 - v * b * phi * sqrt(phi) / F / ln10;
+  const double kT = 8.617333262e-5 * T;
+  const double lrd = log10(1.20173e6 * T * T) - fmax(phi - sqrt(c * F), 0.0) / kT / ln10;
+  const double m = fmax(lfn, lrd);
+  return fmax(m + log10(pow(10.0, lfn - m) + pow(10.0, lrd - m)), kSurLogJFloor);
+}
+
+// surrogate outputs of row i (bias b4 not yet added): J [A/m^2] and P_N [W/m^2]; 0 below the floor.
+// log10 J = approx + y0 kSurY0s (approx from approx_log10J of the same tuple)
+__device__ __forceinline__ void surrogate_out(const float *Y, const float *b4, int64_t i, double approx, double *J,
+                                              double *P) {
+  const double y0 = (double)(Y[i * kSurOut] + b4[0]);
+  const double y1 = (double)(Y[i * kSurOut + 1] + b4[1]);
+  const double lj = approx + y0 * kSurY0s;
+  if (lj <= kSurLogJFloor + 1e-9) { *J = 0.0; *P = 0.0; return; }
+  *J = pow(10.0, lj);
+  *P = *J * (y1 * kSurY1s);
+}
+
 }  // namespace pic

@@ -35,6 +35,7 @@ struct Tables {
   const double *x16, *w16;   // Gauss-Legendre on [-1,1]
   const double *x32, *w32;
   const double *c32, *s32;   // cos and sin of the angles pi/2 (x32 + 1)
+  const float *w32f, *c32f, *s32f;   // the same in FP32 (transmission_f32)
 };
 
 struct Barrier {
@@ -153,6 +154,67 @@ __host__ __device__ inline double transmission(const Barrier &b, const Consts &C
   return G > 700.0 ? exp(-G) : 1.0 / (1.0 + exp(G));
 }
 
+// The same D(W) with the turning points and the Gamow quadrature in FP32 (the exponent and
+// D itself in FP64).  U - W is formed as (phi - W) - (image and field terms) with phi - W taken
+// in FP64 first, so the cancellation near the turning points costs ~1e-7 eV; relative error of
+// G ~1e-6, of D ~1e-6 G.  On GB300 an FP32 operation is ~64x cheaper than an FP64 one.
+__host__ __device__ inline float uw_f32(bool flat, float a, float F, float R, float Q, float x) {
+  if (flat) return a - F * x - Q / x;
+  return a - F * R * x / (R + x) - 2.0f * R * Q / (x * (2.0f * R + x));
+}
+
+__host__ __device__ inline float duw_f32(bool flat, float F, float R, float Q, float x) {
+  if (flat) return -F + Q / (x * x);
+  const float rx = R + x, r2x = 2.0f * R + x;
+  return -F * R * R / (rx * rx) + 2.0f * R * Q * (2.0f * R + 2.0f * x) / (x * x * r2x * r2x);
+}
+
+// root of U(x) - W = 0 in [lo, hi], safeguarded Newton in FP32
+__host__ __device__ inline float root_f32(bool flat, float a, float F, float R, float Q, float lo, float hi, float x0) {
+  const float flo = uw_f32(flat, a, F, R, Q, lo);
+  float x = (x0 > lo && x0 < hi) ? x0 : 0.5f * (lo + hi);
+  for (int it = 0; it < 60; ++it) {
+    const float f = uw_f32(flat, a, F, R, Q, x);
+    if (f == 0.0f) return x;
+    if ((f < 0.0f) == (flo < 0.0f)) lo = x; else hi = x;
+    float xn = x - f / duw_f32(flat, F, R, Q, x);
+    if (!(xn > lo && xn < hi)) xn = 0.5f * (lo + hi);
+    if (fabsf(xn - x) <= 2e-7f * fabsf(xn) || hi - lo <= 2e-7f * hi) return xn;
+    x = xn;
+  }
+  return x;
+}
+
+__host__ __device__ inline double transmission_f32(const Barrier &b, const Consts &C, const Tables &T, double W,
+                                                   double xm) {
+  const double a = b.phi - W;
+  const double disc = a * a - 4.0 * b.Q * b.F;
+  double x1, x2;
+  const float af = (float)a, Ff = (float)b.F, Rf = (float)b.R, Qf = (float)b.Q;
+  if (b.flat) {
+    const double sq = sqrt(fmax(disc, 0.0));
+    x1 = 2.0 * b.Q / (a + sq);
+    x2 = (a + sq) / (2.0 * b.F);
+  } else {
+    if (b.phi - b.F * b.R >= W) return 0.0;
+    const double sq = sqrt(fmax(disc, 0.0));
+    float lo = (float)xm;
+    for (int i = 0; i < 200 && uw_f32(false, af, Ff, Rf, Qf, lo) > 0.0f; ++i) lo *= 0.5f;
+    x1 = root_f32(false, af, Ff, Rf, Qf, lo, (float)xm, disc > 0 ? (float)(2.0 * b.Q / (a + sq)) : 0.5f * (float)xm);
+    const double s = a / (b.F * b.R);
+    const double hi = 2.0 * s * b.R / (1.0 - s) + 2.0 * xm;
+    x2 = root_f32(false, af, Ff, Rf, Qf, (float)xm, (float)hi, disc > 0 ? (float)((a + sq) / (2.0 * b.F)) : 2.0f * (float)xm);
+  }
+  const float m = (float)(0.5 * (x1 + x2)), h = (float)(0.5 * (x2 - x1));
+  float s = 0.0f;
+  for (int i = 0; i < 32; ++i) {
+    const float x = m - h * T.c32f[i];
+    s += T.w32f[i] * sqrtf(fmaxf(uw_f32(b.flat, af, Ff, Rf, Qf, x), 0.0f)) * T.s32f[i];
+  }
+  const double G = C.g * 1.5707963267948966 * (double)h * (double)s;
+  return G > 700.0 ? exp(-G) : 1.0 / (1.0 + exp(G));
+}
+
 struct Acc { double J, P; };
 
 // panel [a, b] with 16-point Gauss-Legendre; below the barrier top
@@ -241,6 +303,117 @@ __host__ __device__ inline void current_density(const Consts &C, const Tables &T
   *J_out = C.zS * J;
   *P_out = C.zS * P;
 }
+
+#ifdef __CUDACC__
+__device__ __forceinline__ double warp_sum_d(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// The same integrals and panels as current_density, evaluated by a whole warp for one face: the
+// 32 lanes split the (panel, node) work items and sum with a fixed butterfly, so a few faces
+// still fill the FP64 pipes.  Every lane must call it with the same arguments; every lane gets
+// the result.  The below-E_F tail is taken two panels per round with the same exit test.
+template <bool kFast>
+__device__ __forceinline__ double transmission_sel(const Barrier &b, const Consts &C, const Tables &T, double W,
+                                                   double xm) {
+  return kFast ? transmission_f32(b, C, T, W, xm) : transmission(b, C, T, W, xm);
+}
+
+// kFast: transmission_f32 at every node (J, P_N to ~1e-5 relative); else all FP64
+template <bool kFast>
+__device__ inline void current_density_warp(const Consts &C, const Tables &T, double F, double Temp, double phi,
+                                            double R, double *J_out, double *P_out, int *n_eval = nullptr) {
+  const int lane = threadIdx.x & 31;
+  if (!(F > 0.0)) { *J_out = 0.0; *P_out = 0.0; return; }
+  Barrier b;
+  b.F = F; b.phi = phi; b.Q = C.Q;
+  b.flat = !(R > 0.0) || !isfinite(R);
+  b.R = b.flat ? 1.0 : R;
+  const double kT = C.kB * Temp;
+  double xm, Um;
+  barrier_top(b, &xm, &Um);
+  const double top = fmax(Um, C.Wlo);
+  double J = supply_tail(top, kT);
+  // above the top: panels of 4, 8, 16, 32, 16 kT, 16 nodes each
+  double Pl = 0.0;
+  for (int q = lane; q < 80; q += 32) {
+    const int p = q >> 4, i = q & 15;
+    const double lo = top + kT * (p == 0 ? 0.0 : p == 1 ? 4.0 : p == 2 ? 12.0 : p == 3 ? 28.0 : 60.0);
+    const double wd = kT * (p == 0 ? 4.0 : p == 1 ? 8.0 : p == 2 ? 16.0 : p == 3 ? 32.0 : 16.0);
+    const double c = lo + 0.5 * wd, hw = 0.5 * wd;
+    Pl += hw * T.w16[i] * inner(c + hw * T.x16[i], kT);
+  }
+  double P = warp_sum_d(Pl);
+  const double h0 = 4.0 * kT;
+  const double dlt = 1e-4 * xm;
+  const double d2U = (dU(b, xm + dlt) - dU(b, xm - dlt)) / (2.0 * dlt);
+  const double htop = fmin(h0, 0.5 * sqrt(8.0 * fabs(d2U)) / C.g);
+  const double Wcut = b.flat ? C.Wlo : fmax(C.Wlo, b.phi - b.F * b.R);
+  int nev = 0;
+  // [max(0, W_cut), top], graded from both ends toward the middle
+  if (top > 0.0 && top > Wcut) {
+    const double A = fmax(0.0, Wcut), B = top, M = 0.5 * (A + B);
+    int nA = 0, nB = 0;
+    for (double pos = A, w = h0; nA < 64; w *= 2.0) { ++nA; pos = fmin(pos + w, M); if (pos == M) break; }
+    for (double pos = B, w = htop; nB < 64; w *= 2.0) { ++nB; pos = fmax(pos - w, M); if (pos == M) break; }
+    double Jl = 0.0;
+    Pl = 0.0;
+    for (int q = lane; q < 16 * (nA + nB); q += 32) {
+      const int pnl = q >> 4, i = q & 15;
+      double a, c;
+      if (pnl < nA) {
+        a = fmin(A + h0 * (ldexp(1.0, pnl) - 1.0), M);
+        c = fmin(A + h0 * (ldexp(1.0, pnl + 1) - 1.0), M);
+      } else {
+        const int p2 = pnl - nA;
+        c = fmax(B - htop * (ldexp(1.0, p2) - 1.0), M);
+        a = fmax(B - htop * (ldexp(1.0, p2 + 1) - 1.0), M);
+      }
+      const double mid = 0.5 * (a + c), hw = 0.5 * (c - a);
+      const double W = mid + hw * T.x16[i];
+      const double D = transmission_sel<kFast>(b, C, T, W, xm);
+      Jl += hw * T.w16[i] * D * supply(W, kT);
+      Pl += hw * T.w16[i] * D * inner(W, kT);
+    }
+    J += warp_sum_d(Jl);
+    P += warp_sum_d(Pl);
+    nev += 16 * (nA + nB);
+  }
+  // [W_cut, min(0, top)], graded downward, two panels per round, stops when negligible
+  {
+    const double B = fmin(0.0, top);
+    if (B > Wcut) {
+      const double w0 = B == top ? htop : h0;
+      const int half = lane >> 4, i = lane & 15;
+      for (int r = 0; r < 32; ++r) {
+        const int pnl = 2 * r + half;
+        const double hi = fmax(B - w0 * (ldexp(1.0, pnl) - 1.0), Wcut);
+        const double lo = fmax(B - w0 * (ldexp(1.0, pnl + 1) - 1.0), Wcut);
+        double Jl = 0.0;
+        Pl = 0.0;
+        if (hi > lo) {
+          const double mid = 0.5 * (lo + hi), hw = 0.5 * (hi - lo);
+          const double W = mid + hw * T.x16[i];
+          const double D = transmission_sel<kFast>(b, C, T, W, xm);
+          Jl = hw * T.w16[i] * D * supply(W, kT);
+          Pl = hw * T.w16[i] * D * inner(W, kT);
+        }
+        const double rJ = warp_sum_d(Jl), rP = warp_sum_d(Pl);
+        J += rJ;
+        P += rP;
+        const double last_lo = fmax(B - w0 * (ldexp(1.0, 2 * r + 2) - 1.0), Wcut);
+        nev += 32;
+        if (last_lo == Wcut) break;
+        if (fabs(rJ) <= 1e-18 * fabs(J) && fabs(rP) <= 1e-18 * fabs(P)) break;
+      }
+    }
+  }
+  if (n_eval) *n_eval += nev;
+  *J_out = C.zS * J;
+  *P_out = C.zS * P;
+}
+#endif
 
 // Gauss-Legendre nodes and weights on [-1, 1] (Newton on the Legendre recurrence; host only).
 inline void gauss_legendre(int n, double *x, double *w) {

@@ -24,33 +24,32 @@ __device__ __forceinline__ T nb_sum(const T *u, int i, int j, int k, int nx, int
          u[c - sz + i] + u[c + sz + i];
 }
 
+// Node kernels run on 3D grids: x over i (32 threads), y over j (8), z over k -- no index division.
+__host__ __device__ inline dim3 node_block() { return dim3(32, 8, 1); }
+inline dim3 node_grid3(int nx, int ny, int nz) { return dim3((nx + 1 + 31) / 32, (ny + 1 + 7) / 8, nz + 1); }
+inline dim3 color_grid3(int nx, int ny, int nz) { return dim3(((nx + 2) / 2 + 31) / 32, (ny + 1 + 7) / 8, nz + 1); }
+#define NODE_IJK(nx, ny)                                       \
+  const int i = blockIdx.x * 32 + threadIdx.x;               \
+  const int j = blockIdx.y * 8 + threadIdx.y, k = blockIdx.z; \
+  if (i > (nx) || j > (ny)) return;                           \
+  const int64_t n = node_index(i, j, k, nx, ny);
+
 // one colour of red-black Gauss-Seidel on A u = f
 template <typename T>
 __global__ void k_smooth(T *u, const T *f, const uint8_t *dir, int nx, int ny, int nz, T h2, int color) {
-  const int half = (nx + 2) / 2;
-  const int64_t total = (int64_t)half * (ny + 1) * (nz + 1);
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
-    const int m = (int)(t % half);
-    const int64_t r = t / half;
-    const int j = (int)(r % (ny + 1)), k = (int)(r / (ny + 1));
-    const int i = 2 * m + ((j + k + color) & 1);
-    if (i > nx) continue;
-    const int64_t n = node_index(i, j, k, nx, ny);
-    if (dir[n]) continue;
-    u[n] = (nb_sum<T>(u, i, j, k, nx, ny) + h2 * f[n]) * (T)(1.0 / 6.0);
-  }
+  const int j = blockIdx.y * 8 + threadIdx.y, k = blockIdx.z;
+  const int i = 2 * (blockIdx.x * 32 + threadIdx.x) + ((j + k + color) & 1);
+  if (i > nx || j > ny) return;
+  const int64_t n = node_index(i, j, k, nx, ny);
+  if (dir[n]) return;
+  u[n] = (nb_sum<T>(u, i, j, k, nx, ny) + h2 * f[n]) * (T)(1.0 / 6.0);
 }
 
 template <typename T>
 __global__ void k_residual(const T *u, const T *f, T *r, const uint8_t *dir, int nx, int ny, int nz, T inv_h2) {
-  const int64_t total = (int64_t)(nx + 1) * (ny + 1) * (nz + 1);
-  for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < total; n += (int64_t)gridDim.x * blockDim.x) {
-    if (dir[n]) { r[n] = 0; continue; }
-    const int i = (int)(n % (nx + 1));
-    const int64_t q = n / (nx + 1);
-    const int j = (int)(q % (ny + 1)), k = (int)(q / (ny + 1));
-    r[n] = f[n] - (6 * u[n] - nb_sum<T>(u, i, j, k, nx, ny)) * inv_h2;
-  }
+  NODE_IJK(nx, ny)
+  if (dir[n]) { r[n] = 0; return; }
+  r[n] = f[n] - (6 * u[n] - nb_sum<T>(u, i, j, k, nx, ny)) * inv_h2;
 }
 
 __device__ __forceinline__ int mirror(int i, int n) { return i < 0 ? -i : (i > n ? 2 * n - i : i); }
@@ -58,43 +57,43 @@ __device__ __forceinline__ int mirror(int i, int n) { return i < 0 ? -i : (i > n
 // full weighting of a fine residual onto the coarse right-hand side; coarse u cleared
 template <typename TF, typename TC>
 __global__ void k_restrict(const TF *rf, int nxf, int nyf, TC *fc, TC *uc, const uint8_t *dirc, int nxc, int nyc, int nzc) {
-  const int64_t total = (int64_t)(nxc + 1) * (nyc + 1) * (nzc + 1);
-  for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < total; n += (int64_t)gridDim.x * blockDim.x) {
+  {
+    const int I = blockIdx.x * 32 + threadIdx.x;
+    const int J = blockIdx.y * 8 + threadIdx.y, K = blockIdx.z;
+    if (I > nxc || J > nyc) return;
+    const int64_t n = node_index(I, J, K, nxc, nyc);
     uc[n] = 0;
-    if (dirc[n]) { fc[n] = 0; continue; }
-    const int I = (int)(n % (nxc + 1));
-    const int64_t q = n / (nxc + 1);
-    const int J = (int)(q % (nyc + 1)), K = (int)(q / (nyc + 1));
-    double s = 0.0;
+    if (dirc[n]) { fc[n] = 0; return; }
+    // accumulate in the level's precision (float in the mixed form)
+    TC s = 0;
     for (int dk = -1; dk <= 1; ++dk) {
-      const double wk = dk == 0 ? 0.5 : 0.25;
+      const TC wk = dk == 0 ? (TC)0.5 : (TC)0.25;
       const int k = 2 * K + dk;
       for (int dj = -1; dj <= 1; ++dj) {
-        const double wj = dj == 0 ? 0.5 : 0.25;
+        const TC wj = dj == 0 ? (TC)0.5 : (TC)0.25;
         const int j = mirror(2 * J + dj, nyf);
+        TC row = 0;
         for (int di = -1; di <= 1; ++di) {
-          const double wi = di == 0 ? 0.5 : 0.25;
+          const TC wi = di == 0 ? (TC)0.5 : (TC)0.25;
           const int i = mirror(2 * I + di, nxf);
-          s += wk * wj * wi * (double)rf[node_index(i, j, k, nxf, nyf)];
+          row += wi * (TC)rf[node_index(i, j, k, nxf, nyf)];
         }
+        s += wk * wj * row;
       }
     }
-    fc[n] = (TC)s;
+    fc[n] = s;
   }
 }
 
 // trilinear prolongation of the coarse correction, added on free fine nodes
 template <typename TC, typename TF>
 __global__ void k_prolong(const TC *uc, int nxc, int nyc, TF *uf, const uint8_t *dirf, int nxf, int nyf, int nzf) {
-  const int64_t total = (int64_t)(nxf + 1) * (nyf + 1) * (nzf + 1);
-  for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < total; n += (int64_t)gridDim.x * blockDim.x) {
-    if (dirf[n]) continue;
-    const int i = (int)(n % (nxf + 1));
-    const int64_t q = n / (nxf + 1);
-    const int j = (int)(q % (nyf + 1)), k = (int)(q / (nyf + 1));
+  {
+    NODE_IJK(nxf, nyf)
+    if (dirf[n]) return;
     const int i0 = i >> 1, j0 = j >> 1, k0 = k >> 1;
     const int i1 = i0 + (i & 1), j1 = j0 + (j & 1), k1 = k0 + (k & 1);
-    const double v = 0.125 * ((double)uc[node_index(i0, j0, k0, nxc, nyc)] + uc[node_index(i1, j0, k0, nxc, nyc)] +
+    const TC v = (TC)0.125 * (uc[node_index(i0, j0, k0, nxc, nyc)] + uc[node_index(i1, j0, k0, nxc, nyc)] +
                               uc[node_index(i0, j1, k0, nxc, nyc)] + uc[node_index(i1, j1, k0, nxc, nyc)] +
                               uc[node_index(i0, j0, k1, nxc, nyc)] + uc[node_index(i1, j0, k1, nxc, nyc)] +
                               uc[node_index(i0, j1, k1, nxc, nyc)] + uc[node_index(i1, j1, k1, nxc, nyc)]);
@@ -120,70 +119,73 @@ __global__ void k_coarse(T *u, const T *f, const uint8_t *dir, int nx, int ny, i
 }
 
 __global__ void k_inject_mask(const uint8_t *dirf, int nxf, int nyf, uint8_t *dirc, int nxc, int nyc, int nzc) {
-  const int64_t total = (int64_t)(nxc + 1) * (nyc + 1) * (nzc + 1);
-  for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < total; n += (int64_t)gridDim.x * blockDim.x) {
-    const int I = (int)(n % (nxc + 1));
-    const int64_t q = n / (nxc + 1);
-    const int J = (int)(q % (nyc + 1)), K = (int)(q / (nyc + 1));
-    dirc[n] = dirf[node_index(2 * I, 2 * J, 2 * K, nxf, nyf)];
-  }
+  const int I = blockIdx.x * 32 + threadIdx.x;
+  const int J = blockIdx.y * 8 + threadIdx.y, K = blockIdx.z;
+  if (I > nxc || J > nyc) return;
+  dirc[node_index(I, J, K, nxc, nyc)] = dirf[node_index(2 * I, 2 * J, 2 * K, nxf, nyf)];
 }
 
 // rho/eps0 from the fixed-point charge; Dirichlet values on the mask
 __global__ void k_rhs(const unsigned long long *Q, double *f, double *phi, const uint8_t *dir, int nx, int ny, int nz,
                       double unit, double V0, int zero_charge) {
-  const int64_t total = (int64_t)(nx + 1) * (ny + 1) * (nz + 1);
-  for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < total; n += (int64_t)gridDim.x * blockDim.x) {
-    const int i = (int)(n % (nx + 1));
-    const int64_t q = n / (nx + 1);
-    const int j = (int)(q % (ny + 1)), k = (int)(q / (ny + 1));
-    const double vol = (i == 0 || i == nx ? 0.5 : 1.0) * (j == 0 || j == ny ? 0.5 : 1.0);
-    f[n] = zero_charge ? 0.0 : (double)(long long)Q[n] * unit / vol;
-    if (dir[n]) phi[n] = k == nz ? V0 : 0.0;
-  }
+  NODE_IJK(nx, ny)
+  // 1/V_n relative to dx^3: 2 per lateral wall the node lies on (exact powers of two)
+  const double inv_vol = (i == 0 || i == nx ? 2.0 : 1.0) * (j == 0 || j == ny ? 2.0 : 1.0);
+  f[n] = zero_charge ? 0.0 : (double)(long long)Q[n] * unit * inv_vol;
+  if (dir[n]) phi[n] = k == nz ? V0 : 0.0;
 }
 
 // residual of the FP64 system, the squared norm partials of r and of the lifted right-hand side
+// 3D launch with blocks (32, 8); block partials of the squared norms land at the block's linear id
 __global__ void k_residual64(const double *phi, const double *f, double *r, const uint8_t *dir, int nx, int ny, int nz,
                              double inv_h2, double V0, double *part, int lift) {
-  __shared__ double sh[2][32];
-  const int64_t total = (int64_t)(nx + 1) * (ny + 1) * (nz + 1);
+  __shared__ double sh[2][8];
+  const int i = blockIdx.x * 32 + threadIdx.x;
+  const int j = blockIdx.y * 8 + threadIdx.y, k = blockIdx.z;
   double s = 0.0, sl = 0.0;
-  for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < total; n += (int64_t)gridDim.x * blockDim.x) {
-    if (dir[n]) { r[n] = 0.0; continue; }
-    const int i = (int)(n % (nx + 1));
-    const int64_t q = n / (nx + 1);
-    const int j = (int)(q % (ny + 1)), k = (int)(q / (ny + 1));
-    const double rr = f[n] - (6.0 * phi[n] - nb_sum<double>(phi, i, j, k, nx, ny)) * inv_h2;
-    r[n] = rr;
-    s += rr * rr;
-    if (lift) {
-      // f - A phi_D: only the anode plane carries a nonzero Dirichlet value
-      const double l = f[n] + (k == nz - 1 ? V0 * inv_h2 : 0.0);
-      sl += l * l;
+  if (i <= nx && j <= ny) {
+    const int64_t n = node_index(i, j, k, nx, ny);
+    if (dir[n]) {
+      r[n] = 0.0;
+    } else {
+      const double rr = f[n] - (6.0 * phi[n] - nb_sum<double>(phi, i, j, k, nx, ny)) * inv_h2;
+      r[n] = rr;
+      s = rr * rr;
+      if (lift) {
+        // f - A phi_D: only the anode plane carries a nonzero Dirichlet value
+        const double l = f[n] + (k == nz - 1 ? V0 * inv_h2 : 0.0);
+        sl = l * l;
+      }
     }
   }
   for (int o = 16; o > 0; o >>= 1) {
     s += __shfl_down_sync(0xffffffffu, s, o);
     sl += __shfl_down_sync(0xffffffffu, sl, o);
   }
-  if ((threadIdx.x & 31) == 0) { sh[0][threadIdx.x >> 5] = s; sh[1][threadIdx.x >> 5] = sl; }
+  if (threadIdx.x == 0) { sh[0][threadIdx.y] = s; sh[1][threadIdx.y] = sl; }
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
     double a = 0.0, b = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { a += sh[0][w]; b += sh[1][w]; }
-    part[2 * blockIdx.x] = a;
-    part[2 * blockIdx.x + 1] = b;
+    for (int w = 0; w < 8; ++w) { a += sh[0][w]; b += sh[1][w]; }
+    const int64_t bid = ((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    part[2 * bid] = a;
+    part[2 * bid + 1] = b;
   }
 }
 
-__global__ void k_sum_partials(const double *part, int nb, double *out) {
-  if (threadIdx.x == 0) {
-    double a = 0.0, b = 0.0;
-    for (int i = 0; i < nb; ++i) { a += part[2 * i]; b += part[2 * i + 1]; }
-    out[0] = a;
-    out[1] = b;
+// fixed-order reduction of nb block partials: thread t sums blocks t, t+1024, ... then a tree
+__global__ void __launch_bounds__(1024) k_sum_partials(const double *part, int64_t nb, double *out) {
+  __shared__ double sa[1024], sb[1024];
+  double a = 0.0, b = 0.0;
+  for (int64_t q = threadIdx.x; q < nb; q += 1024) { a += part[2 * q]; b += part[2 * q + 1]; }
+  sa[threadIdx.x] = a;
+  sb[threadIdx.x] = b;
+  __syncthreads();
+  for (int w = 512; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) { sa[threadIdx.x] += sa[threadIdx.x + w]; sb[threadIdx.x] += sb[threadIdx.x + w]; }
+    __syncthreads();
   }
+  if (threadIdx.x == 0) { out[0] = sa[0]; out[1] = sb[0]; }
 }
 
 template <typename T>
@@ -202,12 +204,9 @@ __global__ void k_correct(double *phi, const T *u, const uint8_t *dir, int64_t n
 
 // E = -grad phi at every node, float64 differences rounded once to float32
 __global__ void k_efield(const double *phi, float4 *E, int nx, int ny, int nz, double inv2dx, double invdx) {
-  const int64_t total = (int64_t)(nx + 1) * (ny + 1) * (nz + 1);
   const int64_t sy = nx + 1, sz = (int64_t)(nx + 1) * (ny + 1);
-  for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < total; n += (int64_t)gridDim.x * blockDim.x) {
-    const int i = (int)(n % (nx + 1));
-    const int64_t q = n / (nx + 1);
-    const int j = (int)(q % (ny + 1)), k = (int)(q / (ny + 1));
+  {
+    NODE_IJK(nx, ny)
     const int im = i > 0 ? i - 1 : 1, ip = i < nx ? i + 1 : nx - 1;
     const int jm = j > 0 ? j - 1 : 1, jp = j < ny ? j + 1 : ny - 1;
     const int64_t row = (int64_t)k * sz + (int64_t)j * sy;
@@ -257,22 +256,22 @@ static void vcycle(pic_t *h, int l) {
     k_coarse<T><<<1, 1024, 0, h->stream>>>(lvl_u<T>(L), lvl_f<T>(L), L.dir, L.nx, L.ny, L.nz, h2, 60);
     return;
   }
-  const int g = node_grid(h, L.nnode / 2 + 1);
+  const dim3 cg = color_grid3(L.nx, L.ny, L.nz), bl = node_block();
   for (int s = 0; s < 2; ++s)
-    for (int c = 0; c < 2; ++c) { ++h->nlaunch; k_smooth<T><<<g, kThreads, 0, h->stream>>>(lvl_u<T>(L), lvl_f<T>(L), L.dir, L.nx, L.ny, L.nz, h2, c); }
+    for (int c = 0; c < 2; ++c) { ++h->nlaunch; k_smooth<T><<<cg, bl, 0, h->stream>>>(lvl_u<T>(L), lvl_f<T>(L), L.dir, L.nx, L.ny, L.nz, h2, c); }
   ++h->nlaunch;
-  k_residual<T><<<node_grid(h, L.nnode), kThreads, 0, h->stream>>>(lvl_u<T>(L), lvl_f<T>(L), lvl_r<T>(L), L.dir, L.nx,
+  k_residual<T><<<node_grid3(L.nx, L.ny, L.nz), bl, 0, h->stream>>>(lvl_u<T>(L), lvl_f<T>(L), lvl_r<T>(L), L.dir, L.nx,
                                                                  L.ny, L.nz, inv_h2);
   MgLevel &Cl = h->mg[l + 1];
   ++h->nlaunch;
-  k_restrict<T, T><<<node_grid(h, Cl.nnode), kThreads, 0, h->stream>>>(lvl_r<T>(L), L.nx, L.ny, lvl_f<T>(Cl), lvl_u<T>(Cl),
+  k_restrict<T, T><<<node_grid3(Cl.nx, Cl.ny, Cl.nz), bl, 0, h->stream>>>(lvl_r<T>(L), L.nx, L.ny, lvl_f<T>(Cl), lvl_u<T>(Cl),
                                                                        Cl.dir, Cl.nx, Cl.ny, Cl.nz);
   vcycle<T>(h, l + 1);
   ++h->nlaunch;
-  k_prolong<T, T><<<node_grid(h, L.nnode), kThreads, 0, h->stream>>>(lvl_u<T>(Cl), Cl.nx, Cl.ny, lvl_u<T>(L), L.dir, L.nx,
+  k_prolong<T, T><<<node_grid3(L.nx, L.ny, L.nz), bl, 0, h->stream>>>(lvl_u<T>(Cl), Cl.nx, Cl.ny, lvl_u<T>(L), L.dir, L.nx,
                                                                      L.ny, L.nz);
   for (int s = 0; s < 2; ++s)
-    for (int c = 1; c >= 0; --c) { ++h->nlaunch; k_smooth<T><<<g, kThreads, 0, h->stream>>>(lvl_u<T>(L), lvl_f<T>(L), L.dir, L.nx, L.ny, L.nz, h2, c); }
+    for (int c = 1; c >= 0; --c) { ++h->nlaunch; k_smooth<T><<<cg, bl, 0, h->stream>>>(lvl_u<T>(L), lvl_f<T>(L), L.dir, L.nx, L.ny, L.nz, h2, c); }
 }
 
 template <typename T>
@@ -287,8 +286,8 @@ static void cycle_fine(pic_t *h) {
 
 int stage_efield(pic_t *h) {
   ++h->nlaunch;
-  k_efield<<<node_grid(h, h->nnode), kThreads, 0, h->stream>>>(h->phi, h->E, h->nx, h->ny, h->nz, 1.0 / (2.0 * h->dx),
-                                                               1.0 / h->dx);
+  k_efield<<<node_grid3(h->nx, h->ny, h->nz), node_block(), 0, h->stream>>>(h->phi, h->E, h->nx, h->ny, h->nz,
+                                                                            1.0 / (2.0 * h->dx), 1.0 / h->dx);
   return launch_check(h, "efield");
 }
 
@@ -296,7 +295,8 @@ int mg_build_masks(pic_t *h) {
   for (size_t l = 1; l < h->mg.size(); ++l) {
     MgLevel &F = h->mg[l - 1], &Cl = h->mg[l];
     ++h->nlaunch;
-    k_inject_mask<<<node_grid(h, Cl.nnode), kThreads, 0, h->stream>>>(F.dir, F.nx, F.ny, Cl.dir, Cl.nx, Cl.ny, Cl.nz);
+    k_inject_mask<<<node_grid3(Cl.nx, Cl.ny, Cl.nz), node_block(), 0, h->stream>>>(F.dir, F.nx, F.ny, Cl.dir, Cl.nx, Cl.ny,
+                                                                                  Cl.nz);
   }
   return launch_check(h, "mg_masks");
 }
@@ -306,9 +306,10 @@ int stage_solve(pic_t *h, bool zero_charge, double V0) {
   MgLevel &L = h->mg[0];
   const double unit = kQe * h->prm.w_min / 1073741824.0 / (h->dx * h->dx * h->dx) / kEps0;
   ++h->nlaunch;
-  k_rhs<<<node_grid(h, L.nnode), kThreads, 0, h->stream>>>(h->Q, h->rhs, h->phi, L.dir, h->nx, h->ny, h->nz, unit, V0,
-                                                           zero_charge ? 1 : 0);
-  const int nb = node_grid(h, L.nnode);
+  k_rhs<<<node_grid3(h->nx, h->ny, h->nz), node_block(), 0, h->stream>>>(h->Q, h->rhs, h->phi, L.dir, h->nx, h->ny, h->nz,
+                                                                         unit, V0, zero_charge ? 1 : 0);
+  const dim3 rg = node_grid3(h->nx, h->ny, h->nz);
+  const int64_t nb = (int64_t)rg.x * rg.y * rg.z;
   const double inv_h2 = 1.0 / (h->dx * h->dx);
   const bool mixed = (h->prm.flags & PIC_F_MIXED_MG) != 0;
   double norms[2] = {0, 0};
@@ -316,10 +317,10 @@ int stage_solve(pic_t *h, bool zero_charge, double V0) {
   int cyc = 0;
   for (;; ++cyc) {
     ++h->nlaunch;
-    k_residual64<<<nb, kThreads, 0, h->stream>>>(h->phi, h->rhs, h->res, L.dir, h->nx, h->ny, h->nz, inv_h2, V0, h->red,
-                                                 cyc == 0 ? 1 : 0);
+    k_residual64<<<rg, node_block(), 0, h->stream>>>(h->phi, h->rhs, h->res, L.dir, h->nx, h->ny, h->nz, inv_h2, V0,
+                                                     h->red, cyc == 0 ? 1 : 0);
     ++h->nlaunch;
-    k_sum_partials<<<1, 32, 0, h->stream>>>(h->red, nb, h->red_out);
+    k_sum_partials<<<1, 1024, 0, h->stream>>>(h->red, nb, h->red_out);
     PIC_CUDA(h, cudaMemcpyAsync(norms, h->red_out, sizeof norms, cudaMemcpyDeviceToHost, h->stream));
     PIC_CUDA(h, cudaStreamSynchronize(h->stream));
     if (cyc == 0) lifted = sqrt(norms[1]);

@@ -6,10 +6,12 @@
 // every new SP its slot and its id, so creation is deterministic.
 #include "pic_internal.cuh"
 #include "gtf.cuh"
+#include "dev_common.cuh"
 
 namespace pic {
 
 __constant__ double c_gl16x[16], c_gl16w[16], c_gl32x[32], c_gl32w[32], c_gl32c[32], c_gl32s[32];
+__constant__ float c_gl32wf[32], c_gl32cf[32], c_gl32sf[32];
 __constant__ gtf::Consts c_gtf;
 
 struct FaceGeom {
@@ -63,17 +65,22 @@ __global__ void k_face_field(const int32_t *vcell, const int8_t *dir, int64_t nf
 __device__ __forceinline__ gtf::Tables dev_tables() {
   gtf::Tables t;
   t.x16 = c_gl16x; t.w16 = c_gl16w; t.x32 = c_gl32x; t.w32 = c_gl32w; t.c32 = c_gl32c; t.s32 = c_gl32s;
+  t.w32f = c_gl32wf; t.c32f = c_gl32cf; t.s32f = c_gl32sf;
   return t;
 }
 
+template <bool kFast>
 __global__ void k_emission_eval(const double *F, const double *T, const double *W, const double *R, double *J,
                                 double *PN, int64_t n) {
   const gtf::Tables tb = dev_tables();
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += warps) {
     double j, p;
-    gtf::current_density(c_gtf, tb, F[i] * 1e-9, T[i], W[i], R[i] > 0 ? R[i] * 1e9 : -1.0, &j, &p);
-    J[i] = j;
-    PN[i] = p;
+    gtf::current_density_warp<kFast>(c_gtf, tb, F[i] * 1e-9, T[i], W[i], R[i] > 0 ? R[i] * 1e9 : -1.0, &j, &p);
+    if ((threadIdx.x & 31) == 0) {
+      J[i] = j;
+      PN[i] = p;
+    }
   }
 }
 
@@ -87,28 +94,96 @@ struct EmitArgs {
   uint32_t *cnt;
   uint64_t seed;
   DevClock *clk;
+  const uint8_t *elig;   // surrogate: eligible faces (null: full integral everywhere)
+  const float *Y, *b4;
+  int32_t *fb_list;      // surrogate pass: faces left for the integral (compacted, any order)
+  int *fb_n;
 };
 
-__global__ void k_emit_count(EmitArgs a) {
+// finish one face once (J, P) are known: accumulators and the emission count
+__device__ __forceinline__ void emit_finish(const EmitArgs &a, int64_t f, int64_t step, double J, double P) {
+  a.J[f] = J;
+  a.PN[f] = P;
+  a.acc_heat[f] += P * a.A * a.dt;
+  a.acc_charge[f] += J * a.A * a.dt;
+  const double lam = J * a.A * a.dt / (kQe * a.w_min);
+  const double base = floor(lam);
+  const U4 r = rng_block(a.seed, kEmit, (uint64_t)f, step, 0);
+  const double U = u01d(r.v[0]);
+  a.cnt[f] = (uint32_t)base + (U < lam - base ? 1u : 0u);
+}
+
+// surrogate pass: eligible faces and faces without a pulling field are finished here, the
+// others are queued for k_emit_fallback (results do not depend on the queue order)
+__global__ void k_emit_surrogate(EmitArgs a) {
+  const int64_t step = a.clk->step;
+  int served = 0;
+  for (int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; f < a.nface; f += (int64_t)gridDim.x * blockDim.x) {
+    const int v = a.owner_vox[f];
+    const double T = v >= 0 ? a.Tvox[v] : a.T0;
+    double J = 0.0, P = 0.0;
+    if (a.F[f] > 0.0) {
+      const double ap = approx_log10J(a.F[f] * 1e-9, T, a.phi_w);
+      // elig 1: inside a validated bin; 2: inside the range, bin not validated -- used only
+      // when the network and the classical estimate both put J below 1e-3 A/m^2, where no
+      // face emits an SP (probability < 1e-13 per step on these grids)
+      bool use = a.elig[f] == 1;
+      if (a.elig[f] == 2) {
+        surrogate_out(a.Y, a.b4, f, ap, &J, &P);
+        use = ap <= -3.0 && J <= 1e-3;
+      }
+      if (!use) {
+        a.fb_list[atomicAdd(a.fb_n, 1)] = (int32_t)f;
+        continue;
+      }
+      surrogate_out(a.Y, a.b4, f, ap, &J, &P);
+      ++served;
+    }
+    emit_finish(a, f, step, J, P);
+  }
+  for (int o = 16; o > 0; o >>= 1) served += __shfl_down_sync(0xffffffffu, served, o);
+  if ((threadIdx.x & 31) == 0 && served) atomicAdd((unsigned long long *)&a.clk->ctr[cSurFaces], (unsigned long long)served);
+}
+
+// the full integral over the queued faces: one warp per face
+template <bool kFast>
+__global__ void k_emit_fallback(EmitArgs a) {
   const gtf::Tables tb = dev_tables();
   const int64_t step = a.clk->step;
-  for (int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; f < a.nface; f += (int64_t)gridDim.x * blockDim.x) {
+  const int nq = *a.fb_n;
+  const int warps = (gridDim.x * blockDim.x) >> 5;
+  for (int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < nq; q += warps) {
+    const int64_t f = a.fb_list[q];
     const int v = a.owner_vox[f];
     const double T = v >= 0 ? a.Tvox[v] : a.T0;
     const double R = v >= 0 ? a.R_nm : -1.0;
     double J, P;
     int nev = 0;
-    gtf::current_density(c_gtf, tb, a.F[f] * 1e-9, T, a.phi_w, R, &J, &P, &nev);
-    atomicAdd((unsigned long long *)&a.clk->ctr[cWevals], (unsigned long long)nev);
-    a.J[f] = J;
-    a.PN[f] = P;
-    a.acc_heat[f] += P * a.A * a.dt;
-    a.acc_charge[f] += J * a.A * a.dt;
-    const double lam = J * a.A * a.dt / (kQe * a.w_min);
-    const double base = floor(lam);
-    const U4 r = rng_block(a.seed, kEmit, (uint64_t)f, step, 0);
-    const double U = u01d(r.v[0]);
-    a.cnt[f] = (uint32_t)base + (U < lam - base ? 1u : 0u);
+    gtf::current_density_warp<kFast>(c_gtf, tb, a.F[f] * 1e-9, T, a.phi_w, R, &J, &P, &nev);
+    if ((threadIdx.x & 31) == 0) {
+      atomicAdd((unsigned long long *)&a.clk->ctr[cWevals], (unsigned long long)nev);
+      emit_finish(a, f, step, J, P);
+    }
+  }
+}
+
+// every face by the full integral: one warp per face
+template <bool kFast>
+__global__ void k_emit_count(EmitArgs a) {
+  const gtf::Tables tb = dev_tables();
+  const int64_t step = a.clk->step;
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t f = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; f < a.nface; f += warps) {
+    const int v = a.owner_vox[f];
+    const double T = v >= 0 ? a.Tvox[v] : a.T0;
+    const double R = v >= 0 ? a.R_nm : -1.0;
+    double J, P;
+    int nev = 0;
+    gtf::current_density_warp<kFast>(c_gtf, tb, a.F[f] * 1e-9, T, a.phi_w, R, &J, &P, &nev);
+    if ((threadIdx.x & 31) == 0) {
+      atomicAdd((unsigned long long *)&a.clk->ctr[cWevals], (unsigned long long)nev);
+      emit_finish(a, f, step, J, P);
+    }
   }
 }
 
@@ -310,14 +385,27 @@ int emission_tables_upload(pic_t *h) {
   }
   PIC_CUDA(h, cudaMemcpyToSymbol(c_gl32c, c32, sizeof c32));
   PIC_CUDA(h, cudaMemcpyToSymbol(c_gl32s, s32, sizeof s32));
+  float w32f[32], c32f[32], s32f[32];
+  for (int i = 0; i < 32; ++i) {
+    w32f[i] = (float)w32[i];
+    c32f[i] = (float)c32[i];
+    s32f[i] = (float)s32[i];
+  }
+  PIC_CUDA(h, cudaMemcpyToSymbol(c_gl32wf, w32f, sizeof w32f));
+  PIC_CUDA(h, cudaMemcpyToSymbol(c_gl32cf, c32f, sizeof c32f));
+  PIC_CUDA(h, cudaMemcpyToSymbol(c_gl32sf, s32f, sizeof s32f));
   PIC_CUDA(h, cudaMemcpyToSymbol(c_gtf, &C, sizeof C));
   return PIC_OK;
 }
 
 int emission_eval_dev(pic_t *h, const double *F, const double *T, const double *W, const double *R, double *J,
-                      double *PN, int64_t n) {
+                      double *PN, int64_t n, bool fast) {
   ++h->nlaunch;
-  k_emission_eval<<<grid_for(n, 64), 64, 0, h->stream>>>(F, T, W, R, J, PN, n);
+  const int64_t blocks = std::min<int64_t>((n + 3) / 4, (int64_t)h->nsm * 16);
+  if (fast)
+    k_emission_eval<true><<<(int)blocks, 128, 0, h->stream>>>(F, T, W, R, J, PN, n);
+  else
+    k_emission_eval<false><<<(int)blocks, 128, 0, h->stream>>>(F, T, W, R, J, PN, n);
   return launch_check(h, "emission_eval");
 }
 
@@ -334,8 +422,28 @@ int stage_emit(pic_t *h) {
     a.R_nm = h->geo.tip_radius * 1e9; a.A = A; a.dt = h->prm.dt; a.w_min = h->prm.w_min;
     a.J = fc.J; a.PN = fc.PN; a.acc_heat = fc.acc_heat; a.acc_charge = fc.acc_charge; a.cnt = fc.cnt;
     a.seed = h->prm.seed; a.clk = h->clock;
-    ++h->nlaunch;
-    k_emit_count<<<face_grid(h), 128, 0, h->stream>>>(a);
+    a.elig = nullptr; a.Y = nullptr; a.b4 = nullptr;
+    const bool fast = (h->prm.flags & PIC_F_FAST_INTEGRAL) != 0;
+    a.fb_list = (int32_t *)fc.cnt2;          // scratch: the injection pass rewrites it afterwards
+    a.fb_n = h->long_n + 8;
+    if ((h->prm.flags & PIC_F_SURROGATE) && surrogate_ready(h)) {
+      PIC_TRY(surrogate_faces(h, &a.elig, &a.Y, &a.b4));
+      PIC_CUDA(h, cudaMemsetAsync(a.fb_n, 0, sizeof(int), h->stream));
+      ++h->nlaunch;
+      k_emit_surrogate<<<grid_for(fc.n), kThreads, 0, h->stream>>>(a);
+      ++h->nlaunch;
+      if (fast)
+        k_emit_fallback<true><<<h->nsm * 8, 128, 0, h->stream>>>(a);
+      else
+        k_emit_fallback<false><<<h->nsm * 8, 128, 0, h->stream>>>(a);
+    } else {
+      ++h->nlaunch;
+      const int blocks = (int)std::min<int64_t>((fc.n + 3) / 4, (int64_t)h->nsm * 16);
+      if (fast)
+        k_emit_count<true><<<blocks, 128, 0, h->stream>>>(a);
+      else
+        k_emit_count<false><<<blocks, 128, 0, h->stream>>>(a);
+    }
     PIC_TRY(scan_u32(h, fc.cnt, fc.off, fc.n, nullptr, tot1));
     ++h->nlaunch;
     k_check_face_new<<<1, 1, 0, h->stream>>>(h->clock, tot1, nullptr, PIC_ELECTRON, h->sp[PIC_ELECTRON].cap, go);

@@ -189,6 +189,7 @@ const char *pic_last_error(pic_t *h) { return h ? h->last_error.c_str() : "null 
 void pic_destroy(pic_t *h) {
   if (!h) return;
   cudaStreamSynchronize(h->stream);
+  mlp_forget(h);
   dfree_all(h);
   delete h;
 }
@@ -332,7 +333,8 @@ int pic_create(const pic_geometry_t *geometry, const pic_grid_t *grid, const pic
   }
   // scratch
   h->scan_tmp = dalloc(h, (size_t)2 * h->nsm * sizeof(uint64_t)); A(h->scan_tmp);
-  h->red = alloc_n<double>(h, (int64_t)2 * h->nsm * 16); A(h->red);
+  // residual-norm partials: one pair per block of the 3D node grid (32 x 8 x 1 blocks)
+  h->red = alloc_n<double>(h, (int64_t)2 * ((h->nx + 1 + 31) / 32) * ((h->ny + 1 + 7) / 8) * (h->nz + 1)); A(h->red);
   h->red_out = alloc_n<double>(h, 2); A(h->red_out);
   h->tmp_len = alloc_n<int64_t>(h, 16); A(h->tmp_len);
   h->long_list = alloc_n<int2>(h, kLongCap); A(h->long_list);
@@ -585,6 +587,12 @@ int pic_set_face_accumulators(pic_t *h, const double *evap, const double *heat, 
 static int sort_one(pic_t *h, int s);
 int pic_sort(pic_t *h);
 
+int pic_set_flags(pic_t *h, uint32_t flags) {
+  if (!h) return PIC_E_INVALID;
+  h->prm.flags = flags;
+  return PIC_OK;
+}
+
 int pic_emit(pic_t *h) {
   if (!h) return PIC_E_INVALID;
   PIC_TRY(stage_emit(h));
@@ -757,6 +765,7 @@ int pic_diagnostics(pic_t *h, pic_diag_t *out) {
   for (int i = 0; i < 8; ++i) out->ms[i] = h->ms[i];
   out->kernel_launches = h->nlaunch;
   out->emission_evals = c.ctr[cWevals];
+  out->surrogate_faces = c.ctr[cSurFaces];
   return PIC_OK;
 }
 
@@ -773,7 +782,8 @@ int pic_emission_eval(pic_t *h, const double *F, const double *T, const double *
       cudaMemcpyAsync(buf + 2 * n, phi_w, n * 8, cudaMemcpyHostToDevice, st) != cudaSuccess ||
       cudaMemcpyAsync(buf + 3 * n, R, n * 8, cudaMemcpyHostToDevice, st) != cudaSuccess)
     rc = pic_fail(h, PIC_E_CUDA, "emission_eval upload");
-  if (rc == PIC_OK) rc = emission_eval_dev(h, buf, buf + n, buf + 2 * n, buf + 3 * n, buf + 4 * n, buf + 5 * n, n);
+  if (rc == PIC_OK) rc = emission_eval_dev(h, buf, buf + n, buf + 2 * n, buf + 3 * n, buf + 4 * n, buf + 5 * n, n,
+                                         (h->prm.flags & PIC_F_FAST_INTEGRAL) != 0);
   if (rc == PIC_OK && (cudaMemcpyAsync(J, buf + 4 * n, n * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
                        cudaMemcpyAsync(PN, buf + 5 * n, n * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
                        cudaStreamSynchronize(st) != cudaSuccess))

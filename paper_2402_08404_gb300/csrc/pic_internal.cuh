@@ -33,6 +33,10 @@ constexpr int kSputBits = 24;         // sputter accumulator: atoms * 2^24
 constexpr int kEnergyBits = 20;       // energy accumulators: eV * 2^20
 constexpr int kMaxSegment = 8192;     // SPs of one species in one cell (sort fix-up limit)
 constexpr int kLongCap = 1 << 16;     // queued long segments per sort pass
+// emission surrogate output decoding: log10 J = approx_log10J + y0 kSurY0s (floor
+// kSurLogJFloor), eps_N = y1 kSurY1s [eV]; output rows are kSurOut floats wide
+constexpr double kSurY0c = 0.0, kSurY0s = 1.0, kSurY1s = 2.0, kSurLogJFloor = -8.0;
+constexpr int kSurOut = 8;
 
 // Philox purposes (one key per purpose)
 enum Purpose : uint32_t { kEmit = 1, kPair = 2, kIon = 3, kScat = 4, kDfi = 5, kEvapP = 6, kSput = 7 };
@@ -40,7 +44,7 @@ enum Purpose : uint32_t { kEmit = 1, kPair = 2, kIon = 3, kScat = 4, kDfi = 5, k
 // device counters (int64), indices
 enum Ctr {
   cEmitted = 0, cEvaporated, cSputtered, cImpactIon, cFieldIon, cRemovedE, cRemovedN, cRemovedI,
-  cIonImpacts, cWevals, cNum
+  cIonImpacts, cWevals, cSurFaces, cNum
 };
 
 // error bits set by kernels
@@ -253,11 +257,15 @@ int stage_face_field(pic_t *h);
 int stage_emit(pic_t *h);
 int stage_inject(pic_t *h);
 int emission_eval_dev(pic_t *h, const double *F, const double *T, const double *W, const double *R,
-                      double *J, double *PN, int64_t n);
+                      double *J, double *PN, int64_t n, bool fast);
 // field (k_field.cu)
 int stage_efield(pic_t *h);
 int stage_solve(pic_t *h, bool zero_charge, double V0);
 int face_field_mean(pic_t *h, const int64_t *faces, int nf, double *out);
 // heat (k_heat.cu)
 int stage_heat(pic_t *h);
+// emission surrogate (k_mlp.cu)
+bool surrogate_ready(pic_t *h);
+void mlp_forget(pic_t *h);
+int surrogate_faces(pic_t *h, const uint8_t **elig, const float **Y, const float **b4);
 }  // namespace pic

@@ -70,7 +70,7 @@ extern "C" int pic_emission_eval_noalloc(pic_t *h, const double *F, const double
   PIC_CUDA(h, cudaMemcpyAsync(dT, T, n * 8, cudaMemcpyHostToDevice, st));
   PIC_CUDA(h, cudaMemcpyAsync(dW, phi_w, n * 8, cudaMemcpyHostToDevice, st));
   PIC_CUDA(h, cudaMemcpyAsync(dR, R, n * 8, cudaMemcpyHostToDevice, st));
-  PIC_TRY(emission_eval_dev(h, dF, dT, dW, dR, dJ, dP, n));
+  PIC_TRY(emission_eval_dev(h, dF, dT, dW, dR, dJ, dP, n, (h->prm.flags & PIC_F_FAST_INTEGRAL) != 0));
   PIC_CUDA(h, cudaMemcpyAsync(J, dJ, n * 8, cudaMemcpyDeviceToHost, st));
   PIC_CUDA(h, cudaMemcpyAsync(PN, dP, n * 8, cudaMemcpyDeviceToHost, st));
   PIC_CUDA(h, cudaStreamSynchronize(st));

@@ -16,6 +16,8 @@ ELECTRON, NEUTRAL, ION = 0, 1, 2
 F_EMISSION, F_EVAP, F_SPUTTER, F_IMPACT_ION, F_DFI, F_HEAT, F_SURROGATE, F_MIXED_MG = (
     0x01, 0x02, 0x04, 0x08, 0x10, 0x20, 0x40, 0x80)
 F_ALL = 0xFF
+F_FAST_INTEGRAL = 0x100
+F_PRODUCTION = F_ALL | F_FAST_INTEGRAL     # surrogate, FP32 Gamow quadrature for its fallback, mixed MG
 
 QE = 1.602176634e-19
 ME = 9.1093837015e-31
@@ -54,7 +56,8 @@ class Diag(C.Structure):
                 ("ion_impacts", C.c_int64), ("total_charge_fixed", C.c_int64), ("mg_cycles", C.c_int),
                 ("mg_residual", C.c_double), ("V0", C.c_double), ("max_face_field", C.c_double),
                 ("max_J", C.c_double), ("max_T", C.c_double), ("emitted_current", C.c_double),
-                ("ms", C.c_double * 8), ("kernel_launches", C.c_int64), ("emission_evals", C.c_int64)]
+                ("ms", C.c_double * 8), ("kernel_launches", C.c_int64), ("emission_evals", C.c_int64),
+                ("surrogate_faces", C.c_int64)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
@@ -94,6 +97,13 @@ def lib():
         L.pic_diagnostics.argtypes = [vp, C.POINTER(Diag)]
         L.pic_emission_eval.argtypes = [vp] * 7 + [i64]
         L.pic_emission_eval_noalloc.argtypes = [vp] * 7 + [i64]
+        L.pic_set_flags.argtypes = [vp, C.c_uint32]
+        L.pic_mlp_num_params.argtypes = []
+        L.pic_mlp_set_params.argtypes = [vp, vp]
+        L.pic_mlp_get_params.argtypes = [vp, vp]
+        L.pic_mlp_forward_backward.argtypes = [vp, vp, vp, i64, vp, vp, vp]
+        L.pic_surrogate_train.argtypes = [vp, i64, i32, i32, C.c_double, C.c_uint64, vp]
+        L.pic_surrogate_eval.argtypes = [vp] * 8 + [i64]
         _lib = L
     return _lib
 
@@ -257,6 +267,9 @@ class Pic:
                                                                     ("Eb", np.int64), ("Es", np.int64))]
         self._check(lib().pic_set_face_accumulators(self.h, *[_ptr(a) for a in arrs]))
 
+    def set_flags(self, flags):
+        self._check(lib().pic_set_flags(self.h, int(flags)))
+
     # -- stages --------------------------------------------------------------------------------
     def emit(self):
         self._check(lib().pic_emit(self.h))
@@ -290,6 +303,47 @@ class Pic:
             v = getattr(d, name)
             out[name] = list(v) if isinstance(v, C.Array) else v
         return out
+
+    # -- emission surrogate ------------------------------------------------------------------------
+    def mlp_params(self):
+        p = np.zeros(lib().pic_mlp_num_params(), dtype=np.float32)
+        self._check(lib().pic_mlp_get_params(self.h, _ptr(p)))
+        return p
+
+    def set_mlp_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        assert p.size == lib().pic_mlp_num_params()
+        self._check(lib().pic_mlp_set_params(self.h, _ptr(p)))
+
+    def mlp_forward_backward(self, x, t=None):
+        """y (n x 2); with targets t also (loss, flat gradient in the public parameter layout)."""
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        n = x.shape[0]
+        y = np.zeros((n, 2), dtype=np.float32)
+        loss = np.zeros(1, dtype=np.float32)
+        g = np.zeros(lib().pic_mlp_num_params(), dtype=np.float32)
+        tt = None if t is None else np.ascontiguousarray(t, dtype=np.float32)
+        self._check(lib().pic_mlp_forward_backward(self.h, _ptr(x), _ptr(tt), n, _ptr(y),
+                                                   _ptr(loss) if t is not None else None,
+                                                   _ptr(g) if t is not None else None))
+        return (y,) if t is None else (y, float(loss[0]), g)
+
+    def surrogate_train(self, nsamples=2_000_000, epochs=60, batch=8192, lr=2e-3, seed=1):
+        st = np.zeros(8)
+        self._check(lib().pic_surrogate_train(self.h, int(nsamples), int(epochs), int(batch), float(lr), int(seed),
+                                              _ptr(st)))
+        keys = ("train_loss", "val_rms_dlog10J", "val_max_dlog10J", "valid_bin_fraction", "valid_sample_fraction",
+                "ms_data", "ms_train", "steps")
+        return dict(zip(keys, st.tolist()))
+
+    def surrogate_eval(self, F, T, W, R):
+        F, T, W, R = (np.ascontiguousarray(np.broadcast_to(a, np.shape(F)), dtype=np.float64) for a in (F, T, W, R))
+        J = np.zeros(F.size)
+        P = np.zeros(F.size)
+        v = np.zeros(F.size, dtype=np.uint8)
+        self._check(lib().pic_surrogate_eval(self.h, _ptr(F), _ptr(T), _ptr(W), _ptr(R), _ptr(J), _ptr(P), _ptr(v),
+                                             F.size))
+        return J, P, v.astype(bool)
 
     def emission_eval_noalloc(self, F, T, W, R):
         """pic_emission_eval_noalloc: the same evaluation staged through the library's fixed

@@ -191,6 +191,29 @@ def test_emission_integral_matches_oracle(pic):
     sim.close()
 
 
+def test_fast_integral_matches_oracle(pic):
+    """FP32 Gamow quadrature (PIC_F_FAST_INTEGRAL): J and P_N within 1e-4 relative of the oracle's
+    FP64 integral wherever J is above 1e-5 A/m^2, and log10 J within 1e-3 everywhere it is finite."""
+    cfg = small_cfg()
+    sim = make(pic, cfg, cap=16, V0=10.0, flags=pic.F_ALL | pic.F_FAST_INTEGRAL)
+    F, T, W, R = synth.face_tuples(400, seed=8)
+    F = np.concatenate([F, np.full(40, 0.5), np.full(40, 14.0)])            # low and near-top fields
+    T = np.concatenate([T, np.linspace(300, 4000, 40), np.linspace(300, 4000, 40)])
+    W = np.concatenate([W, np.full(80, 4.5)])
+    R = np.concatenate([R, np.full(80, 5.0)])
+    R = np.where(np.arange(R.size) % 5 == 0, -1.0, R)
+    J, PN = sim.emission_eval(F * 1e9, T, W, np.where(R > 0, R * 1e-9, -1.0))
+    Jr, Pr = em.current_density_fixed(F, T, W, np.where(R > 0, R, np.inf))
+    assert np.all(np.isfinite(J)) and np.all(np.isfinite(PN))
+    rel = Jr > 1e-5
+    assert rel.sum() > 100
+    assert np.max(np.abs(J[rel] / Jr[rel] - 1)) <= 1e-4
+    assert np.max(np.abs(PN[rel] - Pr[rel]) / (np.abs(Pr[rel]) + 0.05 * Jr[rel])) <= 1e-4
+    tiny = (Jr > 1e-250) & ~rel
+    assert np.max(np.abs(np.log10(J[tiny]) - np.log10(Jr[tiny]))) <= 1e-3
+    sim.close()
+
+
 def _emit_case(pic, T_tip):
     cfg = small_cfg(nx=16, ny=16, nz=32, tip_radius=2e-9, tip_height=10e-9, n_sp=3000, apex_field=9e9)
     g = grid_of(cfg)
@@ -212,9 +235,14 @@ def test_emission_and_injection_match_oracle(pic):
     cfg, g, sim, st = _emit_case(pic, 3300.0)
     # a big evaporation accumulator on every face: injection happens this step
     acc = sim.face_accumulators()
-    acc["evap"] = 1.0 + 0.05 * np.random.default_rng(1).random(g.nface)
+    rng = np.random.default_rng(1)
+    acc["evap"] = 1.0 + 0.05 * rng.random(g.nface)
+    # and sputtered atoms waiting on a tenth of the faces (fractional SP weights drain them)
+    atoms = np.where(rng.random(g.nface) < 0.1, rng.uniform(1.0, 1.6, g.nface), 0.0)
+    acc["sput"] = np.floor(atoms * 2.0 ** 24).astype(np.int64)
     sim.set_face_accumulators(acc)
     st.acc_evap[:] = acc["evap"]
+    st.acc_sput[:] = acc["sput"]
     sim.emit()
     Fv = field.face_field(g, st.phi)
     J, PN = em.current_density_fixed(Fv * 1e-9, OS.face_temperature(st), cfg["work_function"],
@@ -238,6 +266,8 @@ def test_emission_and_injection_match_oracle(pic):
         assert np.allclose(got_n[c], ref_n[c], rtol=1e-6, atol=1e-3)
     acc = sim.face_accumulators()
     assert np.allclose(acc["evap"], st.acc_evap, rtol=1e-12, atol=1e-12)
+    assert np.array_equal(acc["sput"], st.acc_sput)
+    assert new_sp["id"].size > 0
     assert np.allclose(acc["heat"], st.acc_heat, rtol=1e-6, atol=1e-30)
     sim.close()
 
