@@ -186,22 +186,25 @@ int pic_diagnostics(pic_t *h, pic_diag_t *out);
 int pic_emission_eval(pic_t *h, const double *F, const double *T, const double *phi_w,
                       const double *R, double *J, double *PN, int64_t n);
 
-/* Emission surrogate (no counterpart in the paper): an MLP 4 -> 64 -> 64 -> 64 -> 2 with GELU,
- * BF16 operands and FP32 accumulation on the tensor cores, mapping (log10 F, T, work function,
- * log10 R | flat) to (log10 J - log10 J_c, eps_N = P_N/J), J_c the classical estimate (Murphy-Good
- * Fowler-Nordheim + Richardson-Dushman with Schottky lowering).  Trained on tuples drawn over F 0.001-15 GV/m,
+/* Emission surrogate (no counterpart in the paper): an MLP 7 -> 128 -> 128 -> 128 -> 2 with GELU.
+ * The two 128 x 128 hidden layers run with BF16 operands and FP32 accumulation on the tensor
+ * cores; the input and output layers are FP32.  Features (each standardised): log10 F, T, work
+ * function, log10 R (flat: 3), 1/R (flat: 0), min(phi^1.5/F, 20), 1000/T.  Outputs: (log10 J -
+ * log10 J_c, eps_N = P_N/J), J_c the classical estimate (Murphy-Good Fowler-Nordheim +
+ * Richardson-Dushman with Schottky lowering).  Trained on tuples drawn over F 0.001-15 GV/m,
  * T 300-4000 K, phi_w 4-5 eV, R 1-20 nm or flat, with targets from the full FP64 integral; a
  * held-out set (half the training size) fills a validity map (bins whose every held-out sample has
  * |dlog10 J| <= 0.015 wherever log10 J >= -5, a margin under the 0.02 bar); log10 J is
  * clipped at -8 (no face emits below it).
- * With PIC_F_SURROGATE, pic_emit/pic_step use it on faces inside the range and a valid bin,
- * and the full integral elsewhere.  Parameters in the public layout: W1 (64x4), b1, W2 (64x64),
- * b2, W3 (64x64), b3, W4 (2x64), b4 -- pic_mlp_num_params() floats, row-major [out][in]. */
+ * With PIC_F_SURROGATE, pic_emit/pic_step use it on faces inside the range and a valid bin (and
+ * on in-range faces of unvalidated bins where both it and J_c put J below 1e-3 A/m^2), and the
+ * full integral elsewhere.  Parameters: W1 (128x7), b1, W2 (128x128), b2, W3 (128x128), b3,
+ * W4 (2x128), b4 -- pic_mlp_num_params() floats, row-major [out][in]. */
 int pic_mlp_num_params(void);
 int pic_mlp_set_params(pic_t *h, const float *params);
 int pic_mlp_get_params(pic_t *h, float *params);
 /* Forward (and, with targets t, loss 0.5 mean sum (y - t)^2 and its gradient) on n host rows of
- * 4 standardised inputs; y: n x 2 standardised outputs. */
+ * 7 standardised features; y: n x 2 standardised outputs. */
 int pic_mlp_forward_backward(pic_t *h, const float *x, const float *t, int64_t n, float *y, float *loss, float *grad);
 /* Train and install; stats (8 doubles, optional): train loss, validation RMS and max |dlog10 J|
  * over relevant samples, fraction of valid bins, fraction of valid held-out samples, ms of data

@@ -1,7 +1,7 @@
 """FP64 emission-surrogate MLP (test infrastructure only; the paper has no counterpart).
 
-Inputs x = (log10 F[GV/m], T/1000 K, phi_w [eV], log10 R[nm]) standardised as (x - mu)/s;
-layers 4 -> 64 -> 64 -> 64 -> 2 with GELU(z) = z/2 (1 + erf(z/sqrt 2)) on the hidden layers;
+Inputs x: 7 standardised features of (F, T, phi_w, R); layers 7 -> 128 -> 128 -> 128 -> 2 with
+GELU(z) = z/2 (1 + erf(z/sqrt 2)) on the hidden layers;
 outputs (log10 J [A/m^2], eps_N = P_N/J [eV]) standardised by (y - ym)/ys.
 Loss: mean over the batch of the sum over the two outputs of (y_hat - y)^2 / 2.
 """
@@ -10,7 +10,7 @@ import math
 import numpy as np
 import scipy.special as ss
 
-SIZES = (4, 64, 64, 64, 2)
+SIZES = (7, 128, 128, 128, 2)
 
 
 def gelu(z):

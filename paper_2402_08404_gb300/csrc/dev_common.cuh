@@ -53,12 +53,11 @@ __device__ __forceinline__ double approx_log10J(double F, double T, double phi) 
   return fmax(m + log10(pow(10.0, lfn - m) + pow(10.0, lrd - m)), kSurLogJFloor);
 }
 
-// surrogate outputs of row i (bias b4 not yet added): J [A/m^2] and P_N [W/m^2]; 0 below the floor.
+// surrogate outputs of row i: J [A/m^2] and P_N [W/m^2]; 0 below the floor.
 // log10 J = approx + y0 kSurY0s (approx from approx_log10J of the same tuple)
-__device__ __forceinline__ void surrogate_out(const float *Y, const float *b4, int64_t i, double approx, double *J,
-                                              double *P) {
-  const double y0 = (double)(Y[i * kSurOut] + b4[0]);
-  const double y1 = (double)(Y[i * kSurOut + 1] + b4[1]);
+__device__ __forceinline__ void surrogate_out(const float *Y, int64_t i, double approx, double *J, double *P) {
+  const double y0 = (double)Y[i * kSurOut];
+  const double y1 = (double)Y[i * kSurOut + 1];
   const double lj = approx + y0 * kSurY0s;
   if (lj <= kSurLogJFloor + 1e-9) { *J = 0.0; *P = 0.0; return; }
   *J = pow(10.0, lj);

@@ -135,25 +135,33 @@ __global__ void k_rhs(const unsigned long long *Q, double *f, double *phi, const
   if (dir[n]) phi[n] = k == nz ? V0 : 0.0;
 }
 
-// residual of the FP64 system, the squared norm partials of r and of the lifted right-hand side
-// 3D launch with blocks (32, 8); block partials of the squared norms land at the block's linear id
-__global__ void k_residual64(const double *phi, const double *f, double *r, const uint8_t *dir, int nx, int ny, int nz,
-                             double inv_h2, double V0, double *part, int lift) {
-  __shared__ double sh[2][8];
+// Residual of the FP64 system r = f - A phi, handed straight to the finest V-cycle level as its
+// right-hand side (rounded to the level's type T) with a zero initial correction.  The squared
+// norms of h^2 r and of h^2 times the lifted right-hand side (f - A phi_D: only the plane below
+// the anode carries a nonzero Dirichlet term) are accumulated in FP32 -- they only decide
+// convergence -- so the FP64 pipe (1/64 of the FP32 rate on this part) runs just the stencil.
+// 3D launch with blocks (32, 8); block partials land at the block's linear id.
+template <typename T>
+__global__ void k_residual64(const double *phi, const double *f, T *fl, T *ul, const uint8_t *dir, int nx, int ny,
+                             int nz, double inv_h2, float h2f, float V0f, double *part, int lift) {
+  __shared__ float sh[2][8];
   const int i = blockIdx.x * 32 + threadIdx.x;
   const int j = blockIdx.y * 8 + threadIdx.y, k = blockIdx.z;
-  double s = 0.0, sl = 0.0;
+  float s = 0.f, sl = 0.f;
   if (i <= nx && j <= ny) {
     const int64_t n = node_index(i, j, k, nx, ny);
+    ul[n] = 0;
     if (dir[n]) {
-      r[n] = 0.0;
+      fl[n] = 0;
     } else {
-      const double rr = f[n] - (6.0 * phi[n] - nb_sum<double>(phi, i, j, k, nx, ny)) * inv_h2;
-      r[n] = rr;
-      s = rr * rr;
+      const double fn = f[n];
+      const double t = fma(6.0, phi[n], -nb_sum<double>(phi, i, j, k, nx, ny));
+      const double rr = fma(-t, inv_h2, fn);
+      fl[n] = (T)rr;
+      const float rs = (float)rr * h2f;
+      s = rs * rs;
       if (lift) {
-        // f - A phi_D: only the anode plane carries a nonzero Dirichlet value
-        const double l = f[n] + (k == nz - 1 ? V0 * inv_h2 : 0.0);
+        const float l = (float)fn * h2f + (k == nz - 1 ? V0f : 0.f);
         sl = l * l;
       }
     }
@@ -165,11 +173,11 @@ __global__ void k_residual64(const double *phi, const double *f, double *r, cons
   if (threadIdx.x == 0) { sh[0][threadIdx.y] = s; sh[1][threadIdx.y] = sl; }
   __syncthreads();
   if (threadIdx.x == 0 && threadIdx.y == 0) {
-    double a = 0.0, b = 0.0;
+    float a = 0.f, b = 0.f;
     for (int w = 0; w < 8; ++w) { a += sh[0][w]; b += sh[1][w]; }
     const int64_t bid = ((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-    part[2 * bid] = a;
-    part[2 * bid + 1] = b;
+    part[2 * bid] = (double)a;
+    part[2 * bid + 1] = (double)b;
   }
 }
 
@@ -186,14 +194,6 @@ __global__ void __launch_bounds__(1024) k_sum_partials(const double *part, int64
     __syncthreads();
   }
   if (threadIdx.x == 0) { out[0] = sa[0]; out[1] = sb[0]; }
-}
-
-template <typename T>
-__global__ void k_to_level(const double *r, T *f, T *u, int64_t n) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    f[i] = (T)r[i];
-    u[i] = 0;
-  }
 }
 
 template <typename T>
@@ -274,11 +274,10 @@ static void vcycle(pic_t *h, int l) {
     for (int c = 1; c >= 0; --c) { ++h->nlaunch; k_smooth<T><<<cg, bl, 0, h->stream>>>(lvl_u<T>(L), lvl_f<T>(L), L.dir, L.nx, L.ny, L.nz, h2, c); }
 }
 
+// one V-cycle on A e = r (r already on the finest level, e = 0 there) and phi += e
 template <typename T>
 static void cycle_fine(pic_t *h) {
   MgLevel &L = h->mg[0];
-  ++h->nlaunch;
-  k_to_level<T><<<node_grid(h, L.nnode), kThreads, 0, h->stream>>>(h->res, lvl_f<T>(L), lvl_u<T>(L), L.nnode);
   vcycle<T>(h, 0);
   ++h->nlaunch;
   k_correct<T><<<node_grid(h, L.nnode), kThreads, 0, h->stream>>>(h->phi, lvl_u<T>(L), L.dir, L.nnode);
@@ -315,10 +314,15 @@ int stage_solve(pic_t *h, bool zero_charge, double V0) {
   double norms[2] = {0, 0};
   double lifted = 0.0;
   int cyc = 0;
+  const float h2f = (float)(h->dx * h->dx), V0f = (float)V0;
   for (;; ++cyc) {
     ++h->nlaunch;
-    k_residual64<<<rg, node_block(), 0, h->stream>>>(h->phi, h->rhs, h->res, L.dir, h->nx, h->ny, h->nz, inv_h2, V0,
-                                                     h->red, cyc == 0 ? 1 : 0);
+    if (mixed)
+      k_residual64<float><<<rg, node_block(), 0, h->stream>>>(h->phi, h->rhs, L.f, L.u, L.dir, h->nx, h->ny, h->nz,
+                                                              inv_h2, h2f, V0f, h->red, cyc == 0 ? 1 : 0);
+    else
+      k_residual64<double><<<rg, node_block(), 0, h->stream>>>(h->phi, h->rhs, L.fd, L.ud, L.dir, h->nx, h->ny,
+                                                               h->nz, inv_h2, h2f, V0f, h->red, cyc == 0 ? 1 : 0);
     ++h->nlaunch;
     k_sum_partials<<<1, 1024, 0, h->stream>>>(h->red, nb, h->red_out);
     PIC_CUDA(h, cudaMemcpyAsync(norms, h->red_out, sizeof norms, cudaMemcpyDeviceToHost, h->stream));

@@ -1,13 +1,15 @@
-// Emission surrogate (no counterpart in the paper): an MLP 4 -> 64 -> 64 -> 64 -> 2 with GELU
-// (exact erf form) mapping (log10 F, T, work function, log10 R | flat) to (log10 J, eps_N =
-// P_N / J in eV), trained on the full FP64 emission integral and used per face in the step
-// wherever its inputs lie in the trained range and a held-out validation bin shows
-// |delta log10 J| <= 0.02; elsewhere the step falls back to the full integral.
+// Emission surrogate (no counterpart in the paper): an MLP 7 -> 128 -> 128 -> 128 -> 2 with GELU
+// (exact erf form) mapping features of (F, T, work function, R | flat) to (log10 J - a classical
+// estimate, eps_N = P_N / J in eV), trained on the full FP64 emission integral and used per face
+// in the step wherever its inputs lie in the trained range and a held-out validation bin shows
+// |delta log10 J| <= 0.015; elsewhere the step falls back to the full integral.
 //
-// Arithmetic: BF16 operands, FP32 accumulation on the tensor cores (mma.sync m16n8k16), FP32
-// master weights, Adam.  Weight gradients reduce over the batch with a fixed split order, so
-// training is deterministic.  Layer-1 inputs are padded from 4 to 16 columns and the output
-// layer from 2 to 8 rows (zero pads keep zero gradients).
+// Arithmetic: the two 128 x 128 hidden layers run on the tensor cores (mma.sync m16n8k16, BF16
+// operands, FP32 accumulation); the input layer (7 features) and the output layer (2 values)
+// are FP32 on the CUDA cores, so the features and the last activations keep FP32 precision
+// (in BF16 a feature step of 2^-9 moves log10 J by up to ~0.04 in the field-emission regime).
+// FP32 master weights, Adam.  Weight gradients reduce over the batch with a fixed split order,
+// so training is deterministic.
 #include <cuda_bf16.h>
 #include <math.h>
 #include <string.h>
@@ -22,12 +24,14 @@
 
 namespace pic {
 
-// ---- layout ---------------------------------------------------------------------------------
-constexpr int kH = 64, kIn = 16, kOut = 8;
+// ---- layout (public = master, row-major [out][in]) -------------------------------------------
+constexpr int kH = 128, kIn = 7, kXld = 8, kOut = kSurOut;
 constexpr int kOffW1 = 0, kOffB1 = kOffW1 + kH * kIn, kOffW2 = kOffB1 + kH, kOffB2 = kOffW2 + kH * kH,
               kOffW3 = kOffB2 + kH, kOffB3 = kOffW3 + kH * kH, kOffW4 = kOffB3 + kH, kOffB4 = kOffW4 + kOut * kH,
               kNParam = kOffB4 + kOut;
-constexpr int kPublicParams = 64 * 4 + 64 + 64 * 64 + 64 + 64 * 64 + 64 + 2 * 64 + 2;   // 8770
+static_assert(kNParam == 34306, "parameter count");
+static_assert(kOffB1 == kOffW1 + kH * kIn && kOffB4 == kOffW4 + kOut * kH, "bias follows its weights");
+static_assert(kH * kIn + kH <= 1024, "one thread per layer-1 gradient entry");
 
 // input / output standardisation (fixed by the trained ranges)
 constexpr double kF_lo = 0.001, kF_hi = 15.0;      // GV/m
@@ -37,24 +41,24 @@ constexpr double kW_lo = 4.0, kW_hi = 5.0;         // eV
 constexpr double kR_lo = 1.0, kR_hi = 20.0;        // nm
 constexpr double kLogFlat = 3.0;                    // log10 R used for a flat surface
 constexpr double kLogJFloor = kSurLogJFloor;       // log10 J below this carries no emission
-constexpr double kY0c = kSurY0c, kY0s = kSurY0s, kY1s = kSurY1s;
+constexpr double kY0s = kSurY0s, kY1s = kSurY1s;
 constexpr int kBinF = 40, kBinT = 12, kBinW = 4, kBinR = 5, kNBin = kBinF * kBinT * kBinW * kBinR;
+constexpr int kSplitMax = 64;
 
 struct MlpState {
   bool ready = false, trained = false;
   float *master = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr;
-  __nv_bfloat16 *w1 = nullptr, *w2 = nullptr, *w3 = nullptr, *w4 = nullptr;   // BF16 operand copies
+  __nv_bfloat16 *w2 = nullptr, *w3 = nullptr;   // BF16 operand copies of the hidden layers
   int64_t cap_rows = 0;
-  __nv_bfloat16 *X = nullptr;                    // rows x 16
-  float *Z1 = nullptr, *Z2 = nullptr, *Z3 = nullptr, *Y = nullptr;
-  __nv_bfloat16 *A1 = nullptr, *A2 = nullptr, *A3 = nullptr;
-  float *dY = nullptr, *dZ = nullptr;            // rows x 8, rows x 64
-  __nv_bfloat16 *dYb = nullptr, *dZb = nullptr, *dAb = nullptr;
-  float *dA = nullptr, *part = nullptr;          // split-K partials
+  float *X = nullptr;                            // rows x kXld features (FP32)
+  float *Z1 = nullptr, *Z2 = nullptr, *Z3 = nullptr, *A3 = nullptr, *Y = nullptr;
+  __nv_bfloat16 *A1 = nullptr, *A2 = nullptr;
+  float *dY = nullptr, *dZ = nullptr, *dA = nullptr;   // rows x 2, rows x kH, rows x kH
+  __nv_bfloat16 *dZb = nullptr;
+  float *part = nullptr;                         // split partials
   float *loss = nullptr;
   uint8_t *binok = nullptr;
   uint8_t *elig = nullptr;                       // per face (step)
-  int adam_t = 0;
 };
 
 static std::vector<std::pair<pic_t *, MlpState *>> &mlp_table() {
@@ -181,68 +185,126 @@ static void gemm(pic_t *h, MlpState &S, const __nv_bfloat16 *A, int64_t sam, int
   }
 }
 
-// ---- elementwise -----------------------------------------------------------------------------
+// ---- FP32 layers and elementwise ---------------------------------------------------------------
 __device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.f + erff(z * 0.70710678118654752f)); }
 __device__ __forceinline__ float gelu_grad_f(float z) {
   return 0.5f * (1.f + erff(z * 0.70710678118654752f)) + z * expf(-0.5f * z * z) * 0.3989422804014327f;
 }
 
-// Z += b (per column); A = bf16(gelu(Z))
-__global__ void k_bias_gelu(float *Z, const float *b, __nv_bfloat16 *A, int64_t rows) {
+// input layer: Z1 = W1 x + b1 (FP32), A1 = bf16(gelu(Z1))
+__global__ void k_layer1(const float *X, const float *W1, const float *b1, float *Z1, __nv_bfloat16 *A1, int64_t rows) {
+  __shared__ float w[kH * kIn + kH];
+  for (int e = threadIdx.x; e < kH * kIn + kH; e += blockDim.x) w[e] = W1[e];   // W1 then b1 (contiguous)
+  __syncthreads();
+  const int64_t n = rows * kH;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / kH;
+    const int o = (int)(e - r * kH);
+    float z = w[kH * kIn + o];
+    for (int c = 0; c < kIn; ++c) z += w[o * kIn + c] * X[r * kXld + c];
+    Z1[e] = z;
+    A1[e] = __float2bfloat16(gelu_f(z));
+  }
+}
+
+// Z += b (per column); A = bf16(gelu(Z)); Af = gelu(Z) in FP32 when given
+__global__ void k_bias_gelu(float *Z, const float *b, __nv_bfloat16 *A, float *Af, int64_t rows) {
   const int64_t n = rows * kH;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
     const float z = Z[e] + b[e % kH];
     Z[e] = z;
-    A[e] = __float2bfloat16(gelu_f(z));
+    const float a = gelu_f(z);
+    if (A) A[e] = __float2bfloat16(a);
+    if (Af) Af[e] = a;
   }
 }
 
-// Y += b4; dY = (Y - T)/rows on the 2 outputs; loss partial sums
-__global__ void k_out_loss(float *Y, const float *b4, const float *Tg, float *dY, __nv_bfloat16 *dYb, int64_t rows,
-                           float *loss) {
+// output layer: one warp per row, Y = W4 A3 + b4 (FP32)
+__global__ void k_layer4(const float *A3, const float *W4, const float *b4, float *Y, int64_t rows) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < rows; r += warps) {
+    float y0 = 0.f, y1 = 0.f;
+    for (int k = lane; k < kH; k += 32) {
+      const float a = A3[r * kH + k];
+      y0 += W4[k] * a;
+      y1 += W4[kH + k] * a;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      y0 += __shfl_xor_sync(0xffffffffu, y0, o);
+      y1 += __shfl_xor_sync(0xffffffffu, y1, o);
+    }
+    if (lane == 0) {
+      Y[r * kOut] = y0 + b4[0];
+      Y[r * kOut + 1] = y1 + b4[1];
+    }
+  }
+}
+
+// dY = (Y - T)/rows; loss partial sums (0.5 sum of squares) per block
+__global__ void k_out_loss(const float *Y, const float *Tg, float *dY, int64_t rows, float *loss) {
   __shared__ float sh[32];
   float acc = 0.f;
   for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += (int64_t)gridDim.x * blockDim.x) {
     for (int o = 0; o < kOut; ++o) {
-      float y = Y[r * kOut + o] + b4[o];
-      Y[r * kOut + o] = y;
-      float d = 0.f;
-      if (o < 2 && Tg) {
-        const float diff = y - Tg[r * 2 + o];
-        acc += 0.5f * diff * diff;
-        d = diff / (float)rows;
-      }
-      if (dY) {
-        dY[r * kOut + o] = d;
-        dYb[r * 16 + o] = __float2bfloat16(d);
-        dYb[r * 16 + 8 + o] = __float2bfloat16(0.f);
-      }
+      const float diff = Y[r * kOut + o] - Tg[r * 2 + o];
+      acc += 0.5f * diff * diff;
+      dY[r * kOut + o] = diff / (float)rows;
     }
   }
-  if (loss) {
-    for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      float s = 0.f;
-      for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += sh[i];
-      loss[blockIdx.x] = s;
-    }
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float s = 0.f;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += sh[i];
+    loss[blockIdx.x] = s;
   }
 }
 
-// dZ = dA * gelu'(Z) (fp32 and bf16 copies)
-__global__ void k_gelu_bwd(const float *dA, const float *Z, float *dZ, __nv_bfloat16 *dZb, int64_t rows) {
+// dA3 = dY W4 then dZ3 = dA3 gelu'(Z3) (FP32 and BF16 copies)
+__global__ void k_layer4_bwd(const float *dY, const float *W4, const float *Z3, float *dZ, __nv_bfloat16 *dZb,
+                             int64_t rows) {
   const int64_t n = rows * kH;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
-    const float d = dA[e] * gelu_grad_f(Z[e]);
+    const int64_t r = e / kH;
+    const int k = (int)(e - r * kH);
+    const float da = dY[r * kOut] * W4[k] + dY[r * kOut + 1] * W4[kH + k];
+    const float d = da * gelu_grad_f(Z3[e]);
     dZ[e] = d;
     dZb[e] = __float2bfloat16(d);
   }
 }
 
+// dZ = dA * gelu'(Z) (FP32, and BF16 when given)
+__global__ void k_gelu_bwd(const float *dA, const float *Z, float *dZ, __nv_bfloat16 *dZb, int64_t rows) {
+  const int64_t n = rows * kH;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const float d = dA[e] * gelu_grad_f(Z[e]);
+    dZ[e] = d;
+    if (dZb) dZb[e] = __float2bfloat16(d);
+  }
+}
+
+// Weight gradient of an FP32 layer, G[o][c] = sum_r D[r ldd + o] X[r ldx + c] (o < O, c < C), and
+// with bias_out also sum_r D[r ldd + o]: block z sums its chunk of rows into partial z (one
+// thread per (o, c) pair, O*C + O <= blockDim), k_reduce_splits adds the partials in order.
+__global__ void k_wgrad32(const float *D, int ldd, const float *X, int ldx, int O, int C, int64_t rows, int chunks,
+                          float *part) {
+  const int t = threadIdx.x;
+  const int nout = O * C + O;
+  const int64_t per = (rows + chunks - 1) / chunks;
+  const int64_t r0 = (int64_t)blockIdx.x * per, r1 = std::min<int64_t>(rows, r0 + per);
+  if (t >= nout) return;
+  const bool bias = t >= O * C;
+  const int o = bias ? t - O * C : t / C, c = bias ? 0 : t - (t / C) * C;
+  float s = 0.f;
+  for (int64_t r = r0; r < r1; ++r) s += D[r * ldd + o] * (bias ? 1.f : X[r * ldx + c]);
+  part[(int64_t)blockIdx.x * nout + t] = s;
+}
+
 // column sums of a rows x cols fp32 matrix (one block per column, fixed order)
-__global__ void k_colsum(const float *X, int64_t rows, int cols, int ld, float *out) {
+__global__ void k_colsum(const float *X, int64_t rows, int ld, float *out) {
   __shared__ float sh[32];
   const int c = blockIdx.x;
   float s = 0.f;
@@ -255,7 +317,6 @@ __global__ void k_colsum(const float *X, int64_t rows, int cols, int ld, float *
     for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += sh[i];
     out[c] = t;
   }
-  (void)cols;
 }
 
 __global__ void k_adam(float *p, const float *g, float *m, float *v, int n, float lr, float b1t, float b2t) {
@@ -272,13 +333,17 @@ __global__ void k_to_bf16(const float *src, __nv_bfloat16 *dst, int n) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) dst[i] = __float2bfloat16(src[i]);
 }
 
-// standardised inputs -> padded bf16 rows
-__device__ __forceinline__ void features(double F_GV, double T, double W, double R_nm, float x[4]) {
+// standardised features of one tuple: log10 F, T, phi_w, log10 R (flat: 3), 1/R (flat: 0),
+// phi^1.5/F (the field-emission exponent scale, capped at 20), 1000/T
+__device__ __forceinline__ void features(double F_GV, double T, double W, double R_nm, float x[kIn]) {
+  const bool flat = !(R_nm > 0) || !isfinite(R_nm);
   x[0] = (float)((log10(F_GV) - (-0.912)) / 2.09);
   x[1] = (float)((T * 1e-3 - 2.15) / 1.85);
   x[2] = (float)((W - 4.5) / 0.5);
-  const double lr = (R_nm > 0 && isfinite(R_nm)) ? log10(R_nm) : kLogFlat;
-  x[3] = (float)((lr - 1.15) / 1.0);
+  x[3] = (float)((flat ? kLogFlat : log10(R_nm)) - 1.15);
+  x[4] = (float)(flat ? -1.0 : 2.0 / R_nm - 1.0);
+  x[5] = (float)(fmin(W * sqrt(W) / F_GV, 20.0) / 10.0 - 1.0);
+  x[6] = (float)(1000.0 / T - 1.5);
 }
 
 __device__ __forceinline__ bool in_range(double F_GV, double T, double W, double R_nm) {
@@ -287,24 +352,26 @@ __device__ __forceinline__ bool in_range(double F_GV, double T, double W, double
          (flat || (R_nm >= kR_lo && R_nm <= kR_hi));
 }
 
-__device__ __forceinline__ int bin_of(double F_GV, double T, double W, double R_nm) {
+__host__ __device__ inline int bin_of(double F_GV, double T, double W, double R_nm) {
   const bool flat = !(R_nm > 0) || !isfinite(R_nm);
   int bf = (int)((log10(F_GV) - log10(kF_lo)) / (log10(kF_hi) - log10(kF_lo)) * kBinF);
   int bt = (int)((T - kT_lo) / (kT_hi - kT_lo) * kBinT);
   int bw = (int)((W - kW_lo) / (kW_hi - kW_lo) * kBinW);
   int br = flat ? kBinR - 1 : (int)(log10(R_nm) / log10(kR_hi) * (kBinR - 1));
-  bf = min(max(bf, 0), kBinF - 1); bt = min(max(bt, 0), kBinT - 1); bw = min(max(bw, 0), kBinW - 1);
-  br = min(max(br, 0), kBinR - 1);
+  bf = bf < 0 ? 0 : (bf > kBinF - 1 ? kBinF - 1 : bf);
+  bt = bt < 0 ? 0 : (bt > kBinT - 1 ? kBinT - 1 : bt);
+  bw = bw < 0 ? 0 : (bw > kBinW - 1 ? kBinW - 1 : bw);
+  br = br < 0 ? 0 : (br > kBinR - 1 ? kBinR - 1 : br);
   return ((bf * kBinT + bt) * kBinW + bw) * kBinR + br;
 }
 
-// SI inputs (V/m, K, eV, m or <= 0 flat) -> padded bf16 feature rows
+// SI inputs (V/m, K, eV, m or <= 0 flat) -> feature rows
 __global__ void k_features_rows(const double *F, const double *T, const double *W, const double *R, int64_t n,
-                                __nv_bfloat16 *X) {
+                                float *X) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    float x[4];
+    float x[kIn];
     features(F[i] * 1e-9, T[i], W[i], R[i] > 0 ? R[i] * 1e9 : -1.0, x);
-    for (int c = 0; c < kIn; ++c) X[i * kIn + c] = __float2bfloat16(c < 4 ? x[c] : 0.f);
+    for (int c = 0; c < kXld; ++c) X[i * kXld + c] = c < kIn ? x[c] : 0.f;
   }
 }
 
@@ -343,14 +410,12 @@ static int ensure(pic_t *h, MlpState &S, int64_t rows) {
     S.grad = (float *)dalloc(h, kNParam * 4);
     S.m = (float *)dalloc(h, kNParam * 4);
     S.v = (float *)dalloc(h, kNParam * 4);
-    S.w1 = (__nv_bfloat16 *)dalloc(h, kH * kIn * 2);
     S.w2 = (__nv_bfloat16 *)dalloc(h, kH * kH * 2);
     S.w3 = (__nv_bfloat16 *)dalloc(h, kH * kH * 2);
-    S.w4 = (__nv_bfloat16 *)dalloc(h, kOut * kH * 2);
-    S.part = (float *)dalloc(h, (size_t)64 * 64 * 64 * 4);
+    S.part = (float *)dalloc(h, (size_t)kSplitMax * kH * kH * 4);
     S.loss = (float *)dalloc(h, 4096 * 4);
     S.binok = (uint8_t *)dalloc(h, kNBin);
-    if (!S.master || !S.grad || !S.m || !S.v || !S.w1 || !S.w2 || !S.w3 || !S.w4 || !S.part || !S.loss || !S.binok)
+    if (!S.master || !S.grad || !S.m || !S.v || !S.w2 || !S.w3 || !S.part || !S.loss || !S.binok)
       return pic_fail(h, PIC_E_CUDA, "surrogate allocation failed");
     PIC_CUDA(h, cudaMemsetAsync(S.master, 0, kNParam * 4, h->stream));
     PIC_CUDA(h, cudaMemsetAsync(S.binok, 0, kNBin, h->stream));
@@ -358,20 +423,18 @@ static int ensure(pic_t *h, MlpState &S, int64_t rows) {
   }
   if (rows > S.cap_rows) {
     const int64_t r = std::max<int64_t>(rows, 1024);
-    S.X = (__nv_bfloat16 *)dalloc(h, r * kIn * 2);
+    S.X = (float *)dalloc(h, r * kXld * 4);
     S.Z1 = (float *)dalloc(h, r * kH * 4); S.Z2 = (float *)dalloc(h, r * kH * 4); S.Z3 = (float *)dalloc(h, r * kH * 4);
+    S.A3 = (float *)dalloc(h, r * kH * 4);
     S.Y = (float *)dalloc(h, r * kOut * 4);
     S.A1 = (__nv_bfloat16 *)dalloc(h, r * kH * 2); S.A2 = (__nv_bfloat16 *)dalloc(h, r * kH * 2);
-    S.A3 = (__nv_bfloat16 *)dalloc(h, r * kH * 2);
     S.dY = (float *)dalloc(h, r * kOut * 4);
-    S.dYb = (__nv_bfloat16 *)dalloc(h, r * 16 * 2);
     S.dZ = (float *)dalloc(h, r * kH * 4);
     S.dA = (float *)dalloc(h, r * kH * 4);
     S.dZb = (__nv_bfloat16 *)dalloc(h, r * kH * 2);
-    S.dAb = (__nv_bfloat16 *)dalloc(h, r * kH * 2);
     S.elig = (uint8_t *)dalloc(h, r);
-    if (!S.X || !S.Z1 || !S.Z2 || !S.Z3 || !S.Y || !S.A1 || !S.A2 || !S.A3 || !S.dY || !S.dYb || !S.dZ || !S.dA ||
-        !S.dZb || !S.dAb || !S.elig)
+    if (!S.X || !S.Z1 || !S.Z2 || !S.Z3 || !S.A3 || !S.Y || !S.A1 || !S.A2 || !S.dY || !S.dZ || !S.dA || !S.dZb ||
+        !S.elig)
       return pic_fail(h, PIC_E_CUDA, "surrogate allocation failed");
     S.cap_rows = r;
   }
@@ -379,108 +442,84 @@ static int ensure(pic_t *h, MlpState &S, int64_t rows) {
 }
 
 static void refresh_bf16(pic_t *h, MlpState &S) {
-  h->nlaunch += 4;
-  k_to_bf16<<<8, 256, 0, h->stream>>>(S.master + kOffW1, S.w1, kH * kIn);
-  k_to_bf16<<<16, 256, 0, h->stream>>>(S.master + kOffW2, S.w2, kH * kH);
-  k_to_bf16<<<16, 256, 0, h->stream>>>(S.master + kOffW3, S.w3, kH * kH);
-  k_to_bf16<<<4, 256, 0, h->stream>>>(S.master + kOffW4, S.w4, kOut * kH);
+  h->nlaunch += 2;
+  k_to_bf16<<<32, 256, 0, h->stream>>>(S.master + kOffW2, S.w2, kH * kH);
+  k_to_bf16<<<32, 256, 0, h->stream>>>(S.master + kOffW3, S.w3, kH * kH);
 }
 
 static int eg(int64_t n) { return (int)std::min<int64_t>((n + 255) / 256, 4096); }
 
-// forward of rows [X] -> Y (fp32 rows x 8); keeps Z1..Z3, A1..A3
-static void forward(pic_t *h, MlpState &S, const __nv_bfloat16 *X, int64_t rows) {
+// forward of feature rows X -> Y (rows x 2, bias included); keeps Z1..Z3, A1, A2, A3
+static void forward(pic_t *h, MlpState &S, const float *X, int64_t rows) {
   const int M = (int)rows;
-  gemm(h, S, X, kIn, 1, S.w1, 1, kIn, S.Z1, kH, 1, M, kH, kIn, 1);
   ++h->nlaunch;
-  k_bias_gelu<<<eg(rows * kH), 256, 0, h->stream>>>(S.Z1, S.master + kOffB1, S.A1, rows);
+  k_layer1<<<eg(rows * kH), 256, 0, h->stream>>>(X, S.master + kOffW1, S.master + kOffB1, S.Z1, S.A1, rows);
   gemm(h, S, S.A1, kH, 1, S.w2, 1, kH, S.Z2, kH, 1, M, kH, kH, 1);
   ++h->nlaunch;
-  k_bias_gelu<<<eg(rows * kH), 256, 0, h->stream>>>(S.Z2, S.master + kOffB2, S.A2, rows);
+  k_bias_gelu<<<eg(rows * kH), 256, 0, h->stream>>>(S.Z2, S.master + kOffB2, S.A2, nullptr, rows);
   gemm(h, S, S.A2, kH, 1, S.w3, 1, kH, S.Z3, kH, 1, M, kH, kH, 1);
   ++h->nlaunch;
-  k_bias_gelu<<<eg(rows * kH), 256, 0, h->stream>>>(S.Z3, S.master + kOffB3, S.A3, rows);
-  gemm(h, S, S.A3, kH, 1, S.w4, 1, kH, S.Y, kOut, 1, M, kOut, kH, 1);
+  k_bias_gelu<<<eg(rows * kH), 256, 0, h->stream>>>(S.Z3, S.master + kOffB3, nullptr, S.A3, rows);
+  ++h->nlaunch;
+  k_layer4<<<eg(rows * 32), 256, 0, h->stream>>>(S.A3, S.master + kOffW4, S.master + kOffB4, S.Y, rows);
 }
 
-// loss and gradients (into S.grad) for targets Tg (rows x 2, fp32); returns loss via S.loss partials
-static int backward(pic_t *h, MlpState &S, const __nv_bfloat16 *X, const float *Tg, int64_t rows, int nloss_blocks) {
+// FP32 weight and bias gradient of a small layer into S.grad: the layouts keep b right after W
+// (offB = offW + O C), so the partials [W | b] reduce straight into place
+static void wgrad32(pic_t *h, MlpState &S, const float *D, int ldd, const float *X, int ldx, int O, int C, int64_t rows,
+                    int offW) {
+  const int nout = O * C + O;
+  const int chunks = (int)std::min<int64_t>(kSplitMax, std::max<int64_t>(1, rows / 256));
+  ++h->nlaunch;
+  k_wgrad32<<<chunks, (nout + 31) / 32 * 32, 0, h->stream>>>(D, ldd, X, ldx, O, C, rows, chunks, S.part);
+  ++h->nlaunch;
+  k_reduce_splits<<<std::max(1, (nout + 255) / 256), 256, 0, h->stream>>>(S.part, chunks, 1, nout, S.grad + offW, 0, 1);
+}
+
+// loss and gradients (into S.grad) for targets Tg (rows x 2, fp32); loss partials in S.loss
+static int backward(pic_t *h, MlpState &S, const float *X, const float *Tg, int64_t rows, int nloss_blocks) {
   const int M = (int)rows;
   ++h->nlaunch;
-  k_out_loss<<<nloss_blocks, 256, 0, h->stream>>>(S.Y, S.master + kOffB4, Tg, S.dY, S.dYb, rows, S.loss);
-  const int splits = (int)std::min<int64_t>(64, std::max<int64_t>(1, rows / 512));
-  // layer 4: dW4 = dY^T A3, db4 = colsum dY, dA3 = dY W4
-  gemm(h, S, S.dYb, 1, 16, S.A3, kH, 1, S.grad + kOffW4, kH, 1, kOut, kH, M, splits);
+  k_out_loss<<<nloss_blocks, 256, 0, h->stream>>>(S.Y, Tg, S.dY, rows, S.loss);
+  const int splits = (int)std::min<int64_t>(16, std::max<int64_t>(1, rows / 512));
+  // layer 4 (FP32): dW4 = dY^T A3, db4; dZ3 = (dY W4) gelu'(Z3)
+  wgrad32(h, S, S.dY, kOut, S.A3, kH, kOut, kH, rows, kOffW4);
   ++h->nlaunch;
-  k_colsum<<<kOut, 256, 0, h->stream>>>(S.dY, rows, kOut, kOut, S.grad + kOffB4);
-  gemm(h, S, S.dYb, 16, 1, S.w4, kH, 1, S.dA, kH, 1, M, kH, kOut, 1);
-  // layer 3
-  ++h->nlaunch;
-  k_gelu_bwd<<<eg(rows * kH), 256, 0, h->stream>>>(S.dA, S.Z3, S.dZ, S.dZb, rows);
+  k_layer4_bwd<<<eg(rows * kH), 256, 0, h->stream>>>(S.dY, S.master + kOffW4, S.Z3, S.dZ, S.dZb, rows);
+  // layer 3 (tensor cores): dW3 = dZ3^T A2, db3, dA2 = dZ3 W3
   gemm(h, S, S.dZb, 1, kH, S.A2, kH, 1, S.grad + kOffW3, kH, 1, kH, kH, M, splits);
   ++h->nlaunch;
-  k_colsum<<<kH, 256, 0, h->stream>>>(S.dZ, rows, kH, kH, S.grad + kOffB3);
+  k_colsum<<<kH, 256, 0, h->stream>>>(S.dZ, rows, kH, S.grad + kOffB3);
   gemm(h, S, S.dZb, kH, 1, S.w3, kH, 1, S.dA, kH, 1, M, kH, kH, 1);
-  // layer 2
   ++h->nlaunch;
   k_gelu_bwd<<<eg(rows * kH), 256, 0, h->stream>>>(S.dA, S.Z2, S.dZ, S.dZb, rows);
+  // layer 2 (tensor cores): dW2 = dZ2^T A1, db2, dA1 = dZ2 W2
   gemm(h, S, S.dZb, 1, kH, S.A1, kH, 1, S.grad + kOffW2, kH, 1, kH, kH, M, splits);
   ++h->nlaunch;
-  k_colsum<<<kH, 256, 0, h->stream>>>(S.dZ, rows, kH, kH, S.grad + kOffB2);
+  k_colsum<<<kH, 256, 0, h->stream>>>(S.dZ, rows, kH, S.grad + kOffB2);
   gemm(h, S, S.dZb, kH, 1, S.w2, kH, 1, S.dA, kH, 1, M, kH, kH, 1);
-  // layer 1
   ++h->nlaunch;
-  k_gelu_bwd<<<eg(rows * kH), 256, 0, h->stream>>>(S.dA, S.Z1, S.dZ, S.dZb, rows);
-  gemm(h, S, S.dZb, 1, kH, X, kIn, 1, S.grad + kOffW1, kIn, 1, kH, kIn, M, splits);
-  ++h->nlaunch;
-  k_colsum<<<kH, 256, 0, h->stream>>>(S.dZ, rows, kH, kH, S.grad + kOffB1);
+  k_gelu_bwd<<<eg(rows * kH), 256, 0, h->stream>>>(S.dA, S.Z1, S.dZ, nullptr, rows);
+  // layer 1 (FP32): dW1 = dZ1^T X, db1
+  wgrad32(h, S, S.dZ, kH, X, kXld, kH, kIn, rows, kOffW1);
   return launch_check(h, "mlp backward");
-}
-
-// public <-> padded parameter layouts
-static void to_padded(const float *pub, std::vector<float> &pad) {
-  pad.assign(kNParam, 0.f);
-  int q = 0;
-  for (int o = 0; o < kH; ++o)
-    for (int i = 0; i < 4; ++i) pad[kOffW1 + o * kIn + i] = pub[q++];
-  for (int o = 0; o < kH; ++o) pad[kOffB1 + o] = pub[q++];
-  for (int e = 0; e < kH * kH; ++e) pad[kOffW2 + e] = pub[q++];
-  for (int o = 0; o < kH; ++o) pad[kOffB2 + o] = pub[q++];
-  for (int e = 0; e < kH * kH; ++e) pad[kOffW3 + e] = pub[q++];
-  for (int o = 0; o < kH; ++o) pad[kOffB3 + o] = pub[q++];
-  for (int o = 0; o < 2; ++o)
-    for (int i = 0; i < kH; ++i) pad[kOffW4 + o * kH + i] = pub[q++];
-  for (int o = 0; o < 2; ++o) pad[kOffB4 + o] = pub[q++];
-}
-
-static void from_padded(const std::vector<float> &pad, float *pub) {
-  int q = 0;
-  for (int o = 0; o < kH; ++o)
-    for (int i = 0; i < 4; ++i) pub[q++] = pad[kOffW1 + o * kIn + i];
-  for (int o = 0; o < kH; ++o) pub[q++] = pad[kOffB1 + o];
-  for (int e = 0; e < kH * kH; ++e) pub[q++] = pad[kOffW2 + e];
-  for (int o = 0; o < kH; ++o) pub[q++] = pad[kOffB2 + o];
-  for (int e = 0; e < kH * kH; ++e) pub[q++] = pad[kOffW3 + e];
-  for (int o = 0; o < kH; ++o) pub[q++] = pad[kOffB3 + o];
-  for (int o = 0; o < 2; ++o)
-    for (int i = 0; i < kH; ++i) pub[q++] = pad[kOffW4 + o * kH + i];
-  for (int o = 0; o < 2; ++o) pub[q++] = pad[kOffB4 + o];
 }
 
 // ---- step integration ---------------------------------------------------------------------------
 __global__ void k_face_rows(const double *Fface, const int32_t *owner_vox, const double *Tvox, double T0, double phi_w,
-                            double R_nm, int64_t nface, const uint8_t *binok, __nv_bfloat16 *X, uint8_t *elig) {
+                            double R_nm, int64_t nface, const uint8_t *binok, float *X, uint8_t *elig) {
   for (int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; f < nface; f += (int64_t)gridDim.x * blockDim.x) {
     const int v = owner_vox[f];
     const double T = v >= 0 ? Tvox[v] : T0;
     const double R = v >= 0 ? R_nm : -1.0;
     const double F = Fface[f] * 1e-9;
     const bool inr = F > 0 && in_range(F, T, phi_w, R);
-    float x[4] = {0, 0, 0, 0};
+    float x[kIn] = {};
     if (inr) features(F, T, phi_w, R, x);
-    for (int c = 0; c < kIn; ++c) X[f * kIn + c] = __float2bfloat16(c < 4 ? x[c] : 0.f);
-    // 1: inside the range and a validated bin; 2: inside the range only; 0: outside
-    elig[f] = inr ? (binok[bin_of(F, T, phi_w, R)] ? 1 : 2) : 0;
+    for (int c = 0; c < kXld; ++c) X[f * kXld + c] = c < kIn ? x[c] : 0.f;
+    // 1: inside the range and a validated bin; 2: inside the range only; 3: a pulling field
+    // below the trained range (F < kF_lo); 0: otherwise
+    elig[f] = inr ? (binok[bin_of(F, T, phi_w, R)] ? 1 : 2) : (F > 0 && F < kF_lo ? 3 : 0);
   }
 }
 
@@ -488,11 +527,11 @@ __global__ void k_face_rows(const double *Fface, const int32_t *owner_vox, const
 
 namespace pic {
 
-__global__ void k_surrogate_apply(const float *Y, const float *b4, const uint8_t *elig, const double *F, const double *T,
+__global__ void k_surrogate_apply(const float *Y, const uint8_t *elig, const double *F, const double *T,
                                   const double *W, int64_t n, double *J, double *P, uint8_t *valid) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     double j = 0, p = 0;
-    surrogate_out(Y, b4, i, approx_log10J(F[i] * 1e-9, T[i], W[i]), &j, &p);
+    surrogate_out(Y, i, approx_log10J(F[i] * 1e-9, T[i], W[i]), &j, &p);
     J[i] = j;
     P[i] = p;
     if (valid) valid[i] = elig ? elig[i] : 1;
@@ -508,7 +547,7 @@ __global__ void k_rows_eligible(const double *F, const double *T, const double *
 }
 
 // Surrogate forward for the step's faces: fills J, PN of eligible faces and the eligibility flag.
-int surrogate_faces(pic_t *h, const uint8_t **elig_out, const float **Y_out, const float **b4_out) {
+int surrogate_faces(pic_t *h, const uint8_t **elig_out, const float **Y_out) {
   MlpState &S = mlp_of(h);
   if (!S.trained) return pic_fail(h, PIC_E_INVALID, "surrogate not trained");
   PIC_TRY(ensure(h, S, h->faces.n));
@@ -519,7 +558,6 @@ int surrogate_faces(pic_t *h, const uint8_t **elig_out, const float **Y_out, con
   forward(h, S, S.X, h->faces.n);
   *elig_out = S.elig;
   *Y_out = S.Y;
-  *b4_out = S.master + kOffB4;
   return launch_check(h, "surrogate faces");
 }
 
@@ -531,15 +569,13 @@ using namespace pic;
 
 extern "C" {
 
-int pic_mlp_num_params(void) { return kPublicParams; }
+int pic_mlp_num_params(void) { return kNParam; }
 
 int pic_mlp_set_params(pic_t *h, const float *params) {
   if (!h || !params) return PIC_E_INVALID;
   MlpState &S = mlp_of(h);
   PIC_TRY(ensure(h, S, 1024));
-  std::vector<float> pad;
-  to_padded(params, pad);
-  PIC_CUDA(h, cudaMemcpyAsync(S.master, pad.data(), kNParam * 4, cudaMemcpyHostToDevice, h->stream));
+  PIC_CUDA(h, cudaMemcpyAsync(S.master, params, kNParam * 4, cudaMemcpyHostToDevice, h->stream));
   refresh_bf16(h, S);
   PIC_CUDA(h, cudaStreamSynchronize(h->stream));
   return launch_check(h, "mlp set");
@@ -549,32 +585,26 @@ int pic_mlp_get_params(pic_t *h, float *params) {
   if (!h || !params) return PIC_E_INVALID;
   MlpState &S = mlp_of(h);
   PIC_TRY(ensure(h, S, 1024));
-  std::vector<float> pad(kNParam);
-  PIC_CUDA(h, cudaMemcpyAsync(pad.data(), S.master, kNParam * 4, cudaMemcpyDeviceToHost, h->stream));
+  PIC_CUDA(h, cudaMemcpyAsync(params, S.master, kNParam * 4, cudaMemcpyDeviceToHost, h->stream));
   PIC_CUDA(h, cudaStreamSynchronize(h->stream));
-  from_padded(pad, params);
   return PIC_OK;
 }
 
-// x: n x 4 standardised inputs (host, float); y: n x 2 outputs; optional t (n x 2 targets): then
-// loss (mean over rows of sum 0.5 (y - t)^2) and grad (public layout) are returned too.
+// x: n x 7 standardised features (host, float); y: n x 2 outputs; optional t (n x 2 targets):
+// then loss (mean over rows of sum 0.5 (y - t)^2) and grad (parameter layout) are returned too.
 int pic_mlp_forward_backward(pic_t *h, const float *x, const float *t, int64_t n, float *y, float *loss, float *grad) {
   if (!h || !x || n <= 0 || n > (1 << 22)) return PIC_E_INVALID;
   MlpState &S = mlp_of(h);
   PIC_TRY(ensure(h, S, n));
-  std::vector<__nv_bfloat16> X(n * kIn);
+  std::vector<float> X(n * kXld, 0.f);
   for (int64_t i = 0; i < n; ++i)
-    for (int c = 0; c < kIn; ++c) X[i * kIn + c] = __float2bfloat16(c < 4 ? x[i * 4 + c] : 0.f);
-  PIC_CUDA(h, cudaMemcpyAsync(S.X, X.data(), n * kIn * 2, cudaMemcpyHostToDevice, h->stream));
+    for (int c = 0; c < kIn; ++c) X[i * kXld + c] = x[i * kIn + c];
+  PIC_CUDA(h, cudaMemcpyAsync(S.X, X.data(), n * kXld * 4, cudaMemcpyHostToDevice, h->stream));
   forward(h, S, S.X, n);
-  float *Tg = nullptr;
   if (t) {
-    Tg = S.dZ;   // scratch for targets (rows x 2 fits in rows x 64)
+    float *Tg = S.dA;   // scratch for targets (rows x 2 fits in rows x kH)
     PIC_CUDA(h, cudaMemcpyAsync(Tg, t, n * 2 * 4, cudaMemcpyHostToDevice, h->stream));
     PIC_TRY(backward(h, S, S.X, Tg, n, 64));
-  } else {
-    ++h->nlaunch;
-    k_out_loss<<<64, 256, 0, h->stream>>>(S.Y, S.master + kOffB4, nullptr, nullptr, nullptr, n, nullptr);
   }
   std::vector<float> Yh(n * kOut);
   PIC_CUDA(h, cudaMemcpyAsync(Yh.data(), S.Y, n * kOut * 4, cudaMemcpyDeviceToHost, h->stream));
@@ -590,7 +620,7 @@ int pic_mlp_forward_backward(pic_t *h, const float *x, const float *t, int64_t n
     double l = 0;
     for (float v : lp) l += v;
     if (loss) *loss = (float)(l / n);
-    if (grad) from_padded(g, grad);
+    if (grad) memcpy(grad, g.data(), kNParam * 4);
   }
   return launch_check(h, "mlp fwd/bwd");
 }
@@ -611,7 +641,7 @@ int pic_surrogate_train(pic_t *h, int64_t nsamples, int epochs, int batch, doubl
   cudaEventRecord(e0, st);
   // data: tuples, FP64 integral, standardised features and targets
   double *buf = (double *)dalloc(h, (size_t)ntot * 6 * 8);
-  __nv_bfloat16 *Xall = (__nv_bfloat16 *)dalloc(h, (size_t)ntot * kIn * 2);
+  float *Xall = (float *)dalloc(h, (size_t)ntot * kXld * 4);
   float *Tall = (float *)dalloc(h, (size_t)ntot * 2 * 4);
   if (!buf || !Xall || !Tall) return pic_fail(h, PIC_E_CUDA, "surrogate data allocation failed");
   double *F = buf, *T = buf + ntot, *W = buf + 2 * ntot, *R = buf + 3 * ntot, *J = buf + 4 * ntot, *P = buf + 5 * ntot;
@@ -626,7 +656,7 @@ int pic_surrogate_train(pic_t *h, int64_t nsamples, int epochs, int batch, doubl
   k_targets<<<grid_for(ntot), kThreads, 0, st>>>(F, T, W, J, P, ntot, Tall, approx);
   cudaEventRecord(e1, st);
   // init: He-normal weights from a fixed host generator, zero biases
-  std::vector<float> pub(kPublicParams, 0.f);
+  std::vector<float> pub(kNParam, 0.f);
   {
     uint64_t s = seed * 6364136223846793005ull + 1442695040888963407ull;
     auto nrm = [&]() {
@@ -638,16 +668,14 @@ int pic_surrogate_train(pic_t *h, int64_t nsamples, int epochs, int batch, doubl
       return sqrt(-2.0 * log(u1)) * cos(2.0 * 3.141592653589793 * u2);
     };
     int q = 0;
-    const int fan[4] = {4, 64, 64, 64}, outs[4] = {64, 64, 64, 2};
+    const int fan[4] = {kIn, kH, kH, kH}, outs[4] = {kH, kH, kH, kOut};
     for (int l = 0; l < 4; ++l) {
       const double sd = sqrt(2.0 / fan[l]);
       for (int e = 0; e < outs[l] * fan[l]; ++e) pub[q++] = (float)(sd * nrm());
       for (int e = 0; e < outs[l]; ++e) pub[q++] = 0.f;
     }
   }
-  std::vector<float> pad;
-  to_padded(pub.data(), pad);
-  PIC_CUDA(h, cudaMemcpyAsync(S.master, pad.data(), kNParam * 4, cudaMemcpyHostToDevice, st));
+  PIC_CUDA(h, cudaMemcpyAsync(S.master, pub.data(), kNParam * 4, cudaMemcpyHostToDevice, st));
   PIC_CUDA(h, cudaMemsetAsync(S.m, 0, kNParam * 4, st));
   PIC_CUDA(h, cudaMemsetAsync(S.v, 0, kNParam * 4, st));
   refresh_bf16(h, S);
@@ -658,7 +686,7 @@ int pic_surrogate_train(pic_t *h, int64_t nsamples, int epochs, int batch, doubl
   for (int ep = 0; ep < epochs; ++ep) {
     for (int64_t b = 0; b < steps_per_epoch; ++b, ++step) {
       const int64_t r0 = ((b + (int64_t)ep * 7919) % steps_per_epoch) * batch;
-      const __nv_bfloat16 *Xb = Xall + r0 * kIn;
+      const float *Xb = Xall + r0 * kXld;
       const float *Tb = Tall + r0 * 2;
       forward(h, S, Xb, batch);
       PIC_TRY(backward(h, S, Xb, Tb, batch, 16));
@@ -681,10 +709,8 @@ int pic_surrogate_train(pic_t *h, int64_t nsamples, int epochs, int batch, doubl
   cudaEventRecord(e2, st);
   PIC_TRY(launch_check(h, "surrogate train"));
   // validation on the held-out tuples: per-bin max |dlog10 J| where either side is relevant
-  const __nv_bfloat16 *Xv = Xall + nsamples * kIn;
+  const float *Xv = Xall + nsamples * kXld;
   forward(h, S, Xv, nval);
-  ++h->nlaunch;
-  k_out_loss<<<64, 256, 0, st>>>(S.Y, S.master + kOffB4, nullptr, nullptr, nullptr, nval, nullptr);
   std::vector<float> Yv(nval * kOut), Tv(nval * 2);
   std::vector<double> hF(nval), hT(nval), hW(nval), hR(nval), hA(nval);
   PIC_CUDA(h, cudaMemcpyAsync(hA.data(), approx + nsamples, nval * 8, cudaMemcpyDeviceToHost, st));
@@ -770,7 +796,7 @@ int pic_surrogate_eval(pic_t *h, const double *F, const double *T, const double 
     k_features_rows<<<grid_for(n), kThreads, 0, st>>>(dF, dT, dW, dR, n, S.X);
     forward(h, S, S.X, n);
     ++h->nlaunch;
-    k_surrogate_apply<<<grid_for(n), kThreads, 0, st>>>(S.Y, S.master + kOffB4, el, dF, dT, dW, n, dJ, dP, el);
+    k_surrogate_apply<<<grid_for(n), kThreads, 0, st>>>(S.Y, el, dF, dT, dW, n, dJ, dP, el);
     if (cudaMemcpyAsync(J, dJ, n * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaMemcpyAsync(PN, dP, n * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         (valid && cudaMemcpyAsync(valid, el, n, cudaMemcpyDeviceToHost, st) != cudaSuccess) ||

@@ -95,7 +95,7 @@ struct EmitArgs {
   uint64_t seed;
   DevClock *clk;
   const uint8_t *elig;   // surrogate: eligible faces (null: full integral everywhere)
-  const float *Y, *b4;
+  const float *Y;
   int32_t *fb_list;      // surrogate pass: faces left for the integral (compacted, any order)
   int *fb_n;
 };
@@ -124,19 +124,29 @@ __global__ void k_emit_surrogate(EmitArgs a) {
     double J = 0.0, P = 0.0;
     if (a.F[f] > 0.0) {
       const double ap = approx_log10J(a.F[f] * 1e-9, T, a.phi_w);
-      // elig 1: inside a validated bin; 2: inside the range, bin not validated -- used only
+      // elig 1: inside a validated bin.  2: inside the range, bin not validated -- used only
       // when the network and the classical estimate both put J below 1e-3 A/m^2, where no
-      // face emits an SP (probability < 1e-13 per step on these grids)
-      bool use = a.elig[f] == 1;
-      if (a.elig[f] == 2) {
-        surrogate_out(a.Y, a.b4, f, ap, &J, &P);
+      // face emits an SP (probability < 1e-13 per step on these grids).  3: field below the
+      // trained range -- tunnelling is nil there and Richardson-Dushman with flat Schottky
+      // lowering bounds the current from above (a curved barrier's top is higher), so a bound
+      // below 1e-3 A/m^2 means J = P_N = 0 for the step.
+      const int e = a.elig[f];
+      bool use = e == 1;
+      if (e == 2) {
+        surrogate_out(a.Y, f, ap, &J, &P);
         use = ap <= -3.0 && J <= 1e-3;
+      } else if (e == 3 && ap <= -3.0) {
+        J = 0.0;
+        P = 0.0;
+        emit_finish(a, f, step, J, P);
+        ++served;
+        continue;
       }
       if (!use) {
         a.fb_list[atomicAdd(a.fb_n, 1)] = (int32_t)f;
         continue;
       }
-      surrogate_out(a.Y, a.b4, f, ap, &J, &P);
+      surrogate_out(a.Y, f, ap, &J, &P);
       ++served;
     }
     emit_finish(a, f, step, J, P);
@@ -422,12 +432,12 @@ int stage_emit(pic_t *h) {
     a.R_nm = h->geo.tip_radius * 1e9; a.A = A; a.dt = h->prm.dt; a.w_min = h->prm.w_min;
     a.J = fc.J; a.PN = fc.PN; a.acc_heat = fc.acc_heat; a.acc_charge = fc.acc_charge; a.cnt = fc.cnt;
     a.seed = h->prm.seed; a.clk = h->clock;
-    a.elig = nullptr; a.Y = nullptr; a.b4 = nullptr;
+    a.elig = nullptr; a.Y = nullptr;
     const bool fast = (h->prm.flags & PIC_F_FAST_INTEGRAL) != 0;
     a.fb_list = (int32_t *)fc.cnt2;          // scratch: the injection pass rewrites it afterwards
     a.fb_n = h->long_n + 8;
     if ((h->prm.flags & PIC_F_SURROGATE) && surrogate_ready(h)) {
-      PIC_TRY(surrogate_faces(h, &a.elig, &a.Y, &a.b4));
+      PIC_TRY(surrogate_faces(h, &a.elig, &a.Y));
       PIC_CUDA(h, cudaMemsetAsync(a.fb_n, 0, sizeof(int), h->stream));
       ++h->nlaunch;
       k_emit_surrogate<<<grid_for(fc.n), kThreads, 0, h->stream>>>(a);

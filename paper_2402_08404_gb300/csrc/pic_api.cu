@@ -259,7 +259,6 @@ int pic_create(const pic_geometry_t *geometry, const pic_grid_t *grid, const pic
   h->cheb = alloc_n<uint8_t>(h, h->ncell); A(h->cheb);
   h->phi = alloc_n<double>(h, h->nnode); A(h->phi);
   h->rhs = alloc_n<double>(h, h->nnode); A(h->rhs);
-  h->res = alloc_n<double>(h, h->nnode); A(h->res);
   h->E = alloc_n<float4>(h, h->nnode); A(h->E);
   h->Q = alloc_n<unsigned long long>(h, h->nnode); A(h->Q);
   // multigrid hierarchy

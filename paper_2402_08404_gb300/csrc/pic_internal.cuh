@@ -34,9 +34,9 @@ constexpr int kEnergyBits = 20;       // energy accumulators: eV * 2^20
 constexpr int kMaxSegment = 8192;     // SPs of one species in one cell (sort fix-up limit)
 constexpr int kLongCap = 1 << 16;     // queued long segments per sort pass
 // emission surrogate output decoding: log10 J = approx_log10J + y0 kSurY0s (floor
-// kSurLogJFloor), eps_N = y1 kSurY1s [eV]; output rows are kSurOut floats wide
+// kSurLogJFloor), eps_N = y1 kSurY1s [eV]; output rows are kSurOut floats (y0, y1)
 constexpr double kSurY0c = 0.0, kSurY0s = 1.0, kSurY1s = 2.0, kSurLogJFloor = -8.0;
-constexpr int kSurOut = 8;
+constexpr int kSurOut = 2;
 
 // Philox purposes (one key per purpose)
 enum Purpose : uint32_t { kEmit = 1, kPair = 2, kIon = 3, kScat = 4, kDfi = 5, kEvapP = 6, kSput = 7 };
@@ -135,7 +135,6 @@ struct pic_s {
   uint8_t *cheb = nullptr;       // per cell: Chebyshev distance to the nearest solid cell (capped)
   double *phi = nullptr;         // per node
   double *rhs = nullptr;         // per node: rho/eps0 (FP64)
-  double *res = nullptr;         // per node: FP64 residual
   float4 *E = nullptr;           // per node
   unsigned long long *Q = nullptr;  // per node, int64 two's complement charge
   pic::Species sp[3];
@@ -267,5 +266,5 @@ int stage_heat(pic_t *h);
 // emission surrogate (k_mlp.cu)
 bool surrogate_ready(pic_t *h);
 void mlp_forget(pic_t *h);
-int surrogate_faces(pic_t *h, const uint8_t **elig, const float **Y, const float **b4);
+int surrogate_faces(pic_t *h, const uint8_t **elig, const float **Y);
 }  // namespace pic

@@ -107,7 +107,7 @@ def test_joule_heat_of_uniform_current_and_energy_balance():
 def test_mlp_gradients_match_finite_differences():
     rng = np.random.default_rng(0)
     params = mlp.init_params(rng)
-    x = rng.normal(size=(7, 4))
+    x = rng.normal(size=(7, mlp.SIZES[0]))
     y = rng.normal(size=(7, 2))
     loss, grads = mlp.loss_and_grad(params, x, y)
     h = 1e-6
