@@ -10,10 +10,18 @@
 // (plain form): red-black Gauss-Seidel 2+2 sweeps, full-weighting restriction, trilinear
 // prolongation, a one-block smoother on the coarsest level.  Coarse Dirichlet masks are
 // injected from the fine nodes they coincide with.
+//
+// Layout: phi, the right-hand side, E and the fixed-point charge are node arrays in natural
+// order.  The V-cycle levels keep their two colours apart: node (i, j, k) of colour
+// c = (i + j + k) & 1 lives at c * nper + ((k (ny + 1) + j) Xh + (i >> 1)), Xh = (nx + 2) / 2.
+// A colour sweep then reads the other colour and writes its own as contiguous rows, and its
+// 6 neighbours of (i, j, k) sit at slots (i -+ 1) >> 1 of its own row and i >> 1 of the four
+// rows around it, all in the other colour.
 #include "pic_internal.cuh"
 
 namespace pic {
 
+// ---- natural-order helpers (phi, rhs) ---------------------------------------------------------
 template <typename T>
 __device__ __forceinline__ T nb_sum(const T *u, int i, int j, int k, int nx, int ny) {
   const int im = i > 0 ? i - 1 : 1, ip = i < nx ? i + 1 : nx - 1;
@@ -27,97 +35,192 @@ __device__ __forceinline__ T nb_sum(const T *u, int i, int j, int k, int nx, int
 // Node kernels run on 3D grids: x over i (32 threads), y over j (8), z over k -- no index division.
 __host__ __device__ inline dim3 node_block() { return dim3(32, 8, 1); }
 inline dim3 node_grid3(int nx, int ny, int nz) { return dim3((nx + 1 + 31) / 32, (ny + 1 + 7) / 8, nz + 1); }
-inline dim3 color_grid3(int nx, int ny, int nz) { return dim3(((nx + 2) / 2 + 31) / 32, (ny + 1 + 7) / 8, nz + 1); }
 #define NODE_IJK(nx, ny)                                       \
   const int i = blockIdx.x * 32 + threadIdx.x;               \
   const int j = blockIdx.y * 8 + threadIdx.y, k = blockIdx.z; \
   if (i > (nx) || j > (ny)) return;                           \
   const int64_t n = node_index(i, j, k, nx, ny);
 
-// one colour of red-black Gauss-Seidel on A u = f
-template <typename T>
-__global__ void k_smooth(T *u, const T *f, const uint8_t *dir, int nx, int ny, int nz, T h2, int color) {
-  const int j = blockIdx.y * 8 + threadIdx.y, k = blockIdx.z;
-  const int i = 2 * (blockIdx.x * 32 + threadIdx.x) + ((j + k + color) & 1);
-  if (i > nx || j > ny) return;
-  const int64_t n = node_index(i, j, k, nx, ny);
-  if (dir[n]) return;
-  u[n] = (nb_sum<T>(u, i, j, k, nx, ny) + h2 * f[n]) * (T)(1.0 / 6.0);
+// ---- split-colour level geometry -------------------------------------------------------------
+struct Lv {
+  int nx, ny, nz, Xh;
+  int64_t nper;
+};
+
+inline Lv lv_of(const MgLevel &L) { return Lv{L.nx, L.ny, L.nz, L.Xh, L.nper}; }
+
+__host__ __device__ __forceinline__ int64_t srow(const Lv &L, int j, int k) {
+  return ((int64_t)k * (L.ny + 1) + j) * L.Xh;
 }
 
+// split index of node (i, j, k)
+__host__ __device__ __forceinline__ int64_t sidx(const Lv &L, int i, int j, int k) {
+  return (int64_t)((i + j + k) & 1) * L.nper + srow(L, j, k) + (i >> 1);
+}
+
+// planes per thread in the level sweeps
+constexpr int kKZ = 4;
+
+// slot grid: x over slots (32), y over j (8), z over groups of kKZ planes (x colours)
+inline dim3 slot_grid(const Lv &L, int colours) {
+  return dim3((L.Xh + 31) / 32, (L.ny + 1 + 7) / 8, ((L.nz + kKZ) / kKZ) * colours);
+}
+
+// sum of the 6 neighbours of colour-c node i in row (j, k), read from the other colour uo
 template <typename T>
-__global__ void k_residual(const T *u, const T *f, T *r, const uint8_t *dir, int nx, int ny, int nz, T inv_h2) {
-  NODE_IJK(nx, ny)
-  if (dir[n]) { r[n] = 0; return; }
-  r[n] = f[n] - (6 * u[n] - nb_sum<T>(u, i, j, k, nx, ny)) * inv_h2;
+__device__ __forceinline__ T nb_sum_s(const T *uo, const Lv &L, int i, int t, int j, int k) {
+  const int im = i > 0 ? i - 1 : 1, ip = i < L.nx ? i + 1 : L.nx - 1;
+  const int jm = j > 0 ? j - 1 : 1, jp = j < L.ny ? j + 1 : L.ny - 1;
+  const int64_t row = srow(L, j, k);
+  return uo[row + (im >> 1)] + uo[row + (ip >> 1)] + uo[srow(L, jm, k) + t] + uo[srow(L, jp, k) + t] +
+         uo[srow(L, j, k - 1) + t] + uo[srow(L, j, k + 1) + t];
+}
+
+// The fine-level sweeps are bound by memory latency, not bandwidth, when a thread waits for its
+// mask before loading the stencil: each thread therefore takes kKZ planes (k0 .. k0 + kKZ - 1)
+// and issues every load of all of them (mask, right-hand side, neighbours) before the first
+// store.  Within one colour pass no value read is written, so the order is free.
+
+// one colour of red-black Gauss-Seidel on A u = f (grid z: plane groups of kKZ)
+template <typename T>
+__global__ void k_smooth(T *u, const T *f, const uint8_t *dirs, Lv L, T h2, int c) {
+  const int t = blockIdx.x * 32 + threadIdx.x;
+  const int j = blockIdx.y * 8 + threadIdx.y, k0 = blockIdx.z * kKZ;
+  if (t >= L.Xh || j > L.ny) return;
+  const T *uo = u + (int64_t)(c ^ 1) * L.nper;
+  T v[kKZ];
+  int64_t m[kKZ];
+  bool ok[kKZ];
+#pragma unroll
+  for (int q = 0; q < kKZ; ++q) {
+    const int k = k0 + q;
+    const int i = 2 * t + ((j + k + c) & 1);
+    ok[q] = k > 0 && k < L.nz && i <= L.nx;   // the k = 0 and k = nz planes are Dirichlet
+    m[q] = (int64_t)c * L.nper + srow(L, j, k) + t;
+    v[q] = 0;
+    if (ok[q]) {
+      ok[q] = !dirs[m[q]];
+      v[q] = nb_sum_s<T>(uo, L, i, t, j, k) + h2 * f[m[q]];
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < kKZ; ++q)
+    if (ok[q]) u[m[q]] = v[q] * (T)(1.0 / 6.0);
+}
+
+// r = f - A u at every node (grid z: plane groups of kKZ x 2 colours)
+template <typename T>
+__global__ void k_residual(const T *u, const T *f, T *r, const uint8_t *dirs, Lv L, T inv_h2) {
+  const int t = blockIdx.x * 32 + threadIdx.x;
+  const int j = blockIdx.y * 8 + threadIdx.y, k0 = (blockIdx.z >> 1) * kKZ, c = blockIdx.z & 1;
+  if (t >= L.Xh || j > L.ny) return;
+  const T *uo = u + (int64_t)(c ^ 1) * L.nper;
+  T v[kKZ];
+  int64_t m[kKZ];
+  bool ok[kKZ];
+#pragma unroll
+  for (int q = 0; q < kKZ; ++q) {
+    const int k = k0 + q;
+    const int i = 2 * t + ((j + k + c) & 1);
+    ok[q] = k <= L.nz && i <= L.nx;
+    m[q] = (int64_t)c * L.nper + srow(L, j, k) + t;
+    v[q] = 0;
+    if (ok[q] && k > 0 && k < L.nz) {
+      const bool d = dirs[m[q]];
+      const T rr = f[m[q]] - (6 * u[m[q]] - nb_sum_s<T>(uo, L, i, t, j, k)) * inv_h2;
+      v[q] = d ? (T)0 : rr;
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < kKZ; ++q)
+    if (ok[q]) r[m[q]] = v[q];
 }
 
 __device__ __forceinline__ int mirror(int i, int n) { return i < 0 ? -i : (i > n ? 2 * n - i : i); }
 
 // full weighting of a fine residual onto the coarse right-hand side; coarse u cleared
 template <typename TF, typename TC>
-__global__ void k_restrict(const TF *rf, int nxf, int nyf, TC *fc, TC *uc, const uint8_t *dirc, int nxc, int nyc, int nzc) {
-  {
-    const int I = blockIdx.x * 32 + threadIdx.x;
-    const int J = blockIdx.y * 8 + threadIdx.y, K = blockIdx.z;
-    if (I > nxc || J > nyc) return;
-    const int64_t n = node_index(I, J, K, nxc, nyc);
-    uc[n] = 0;
-    if (dirc[n]) { fc[n] = 0; return; }
-    // accumulate in the level's precision (float in the mixed form)
-    TC s = 0;
-    for (int dk = -1; dk <= 1; ++dk) {
-      const TC wk = dk == 0 ? (TC)0.5 : (TC)0.25;
-      const int k = 2 * K + dk;
-      for (int dj = -1; dj <= 1; ++dj) {
-        const TC wj = dj == 0 ? (TC)0.5 : (TC)0.25;
-        const int j = mirror(2 * J + dj, nyf);
-        TC row = 0;
-        for (int di = -1; di <= 1; ++di) {
-          const TC wi = di == 0 ? (TC)0.5 : (TC)0.25;
-          const int i = mirror(2 * I + di, nxf);
-          row += wi * (TC)rf[node_index(i, j, k, nxf, nyf)];
-        }
-        s += wk * wj * row;
+__global__ void k_restrict(const TF *rf, Lv Fl, TC *fc, TC *uc, const uint8_t *dirsc, Lv Cl) {
+  const int I = blockIdx.x * 32 + threadIdx.x;
+  const int J = blockIdx.y * 8 + threadIdx.y, K = blockIdx.z;
+  if (I > Cl.nx || J > Cl.ny) return;
+  const int64_t n = sidx(Cl, I, J, K);
+  uc[n] = 0;
+  if (dirsc[n]) { fc[n] = 0; return; }
+  // accumulate in the level's precision (float in the mixed form)
+  TC s = 0;
+  for (int dk = -1; dk <= 1; ++dk) {
+    const TC wk = dk == 0 ? (TC)0.5 : (TC)0.25;
+    const int k = 2 * K + dk;
+    for (int dj = -1; dj <= 1; ++dj) {
+      const TC wj = dj == 0 ? (TC)0.5 : (TC)0.25;
+      const int j = mirror(2 * J + dj, Fl.ny);
+      TC row = 0;
+      for (int di = -1; di <= 1; ++di) {
+        const TC wi = di == 0 ? (TC)0.5 : (TC)0.25;
+        const int i = mirror(2 * I + di, Fl.nx);
+        row += wi * (TC)rf[sidx(Fl, i, j, k)];
       }
+      s += wk * wj * row;
     }
-    fc[n] = s;
   }
+  fc[n] = s;
 }
 
-// trilinear prolongation of the coarse correction, added on free fine nodes
+// trilinear prolongation of the coarse correction, added on free fine nodes (fine slot grid,
+// z: plane groups of kKZ x 2 colours; all loads before the stores)
 template <typename TC, typename TF>
-__global__ void k_prolong(const TC *uc, int nxc, int nyc, TF *uf, const uint8_t *dirf, int nxf, int nyf, int nzf) {
-  {
-    NODE_IJK(nxf, nyf)
-    if (dirf[n]) return;
-    const int i0 = i >> 1, j0 = j >> 1, k0 = k >> 1;
-    const int i1 = i0 + (i & 1), j1 = j0 + (j & 1), k1 = k0 + (k & 1);
-    const TC v = (TC)0.125 * (uc[node_index(i0, j0, k0, nxc, nyc)] + uc[node_index(i1, j0, k0, nxc, nyc)] +
-                              uc[node_index(i0, j1, k0, nxc, nyc)] + uc[node_index(i1, j1, k0, nxc, nyc)] +
-                              uc[node_index(i0, j0, k1, nxc, nyc)] + uc[node_index(i1, j0, k1, nxc, nyc)] +
-                              uc[node_index(i0, j1, k1, nxc, nyc)] + uc[node_index(i1, j1, k1, nxc, nyc)]);
-    uf[n] += (TF)v;
+__global__ void k_prolong(const TC *uc, Lv Cl, TF *uf, const uint8_t *dirsf, Lv Fl) {
+  const int t = blockIdx.x * 32 + threadIdx.x;
+  const int j = blockIdx.y * 8 + threadIdx.y, kb = (blockIdx.z >> 1) * kKZ, c = blockIdx.z & 1;
+  if (t >= Fl.Xh || j > Fl.ny) return;
+  TF v[kKZ];
+  int64_t m[kKZ];
+  bool ok[kKZ];
+#pragma unroll
+  for (int q = 0; q < kKZ; ++q) {
+    const int k = kb + q;
+    const int i = 2 * t + ((j + k + c) & 1);
+    ok[q] = k > 0 && k < Fl.nz && i <= Fl.nx;
+    m[q] = (int64_t)c * Fl.nper + srow(Fl, j, k) + t;
+    v[q] = 0;
+    if (ok[q]) {
+      ok[q] = !dirsf[m[q]];
+      const int i0 = i >> 1, j0 = j >> 1, k0 = k >> 1;
+      const int i1 = i0 + (i & 1), j1 = j0 + (j & 1), k1 = k0 + (k & 1);
+      const TC s = (TC)0.125 * (uc[sidx(Cl, i0, j0, k0)] + uc[sidx(Cl, i1, j0, k0)] + uc[sidx(Cl, i0, j1, k0)] +
+                                uc[sidx(Cl, i1, j1, k0)] + uc[sidx(Cl, i0, j0, k1)] + uc[sidx(Cl, i1, j0, k1)] +
+                                uc[sidx(Cl, i0, j1, k1)] + uc[sidx(Cl, i1, j1, k1)]);
+      v[q] = uf[m[q]] + (TF)s;
+    }
   }
+#pragma unroll
+  for (int q = 0; q < kKZ; ++q)
+    if (ok[q]) uf[m[q]] = v[q];
 }
 
 // many red-black sweeps on the (small) coarsest level inside one block
 template <typename T>
-__global__ void k_coarse(T *u, const T *f, const uint8_t *dir, int nx, int ny, int nz, T h2, int sweeps) {
-  const int64_t total = (int64_t)(nx + 1) * (ny + 1) * (nz + 1);
+__global__ void k_coarse(T *u, const T *f, const uint8_t *dirs, Lv L, T h2, int sweeps) {
+  const int64_t rows = (int64_t)(L.ny + 1) * (L.nz + 1);
+  const int64_t slots = rows * L.Xh;
   for (int s = 0; s < sweeps; ++s)
-    for (int color = 0; color < 2; ++color) {
-      for (int64_t n = threadIdx.x; n < total; n += blockDim.x) {
-        const int i = (int)(n % (nx + 1));
-        const int64_t q = n / (nx + 1);
-        const int j = (int)(q % (ny + 1)), k = (int)(q / (ny + 1));
-        if (((i + j + k) & 1) != color || dir[n]) continue;
-        u[n] = (nb_sum<T>(u, i, j, k, nx, ny) + h2 * f[n]) * (T)(1.0 / 6.0);
+    for (int c = 0; c < 2; ++c) {
+      const T *uo = u + (int64_t)(c ^ 1) * L.nper;
+      for (int64_t q = threadIdx.x; q < slots; q += blockDim.x) {
+        const int t = (int)(q % L.Xh);
+        const int64_t rw = q / L.Xh;
+        const int j = (int)(rw % (L.ny + 1)), k = (int)(rw / (L.ny + 1));
+        const int i = 2 * t + ((j + k + c) & 1);
+        const int64_t n = (int64_t)c * L.nper + q;
+        if (i > L.nx || dirs[n]) continue;
+        u[n] = (nb_sum_s<T>(uo, L, i, t, j, k) + h2 * f[n]) * (T)(1.0 / 6.0);
       }
       __syncthreads();
     }
 }
 
+// coarse natural mask from the fine nodes it coincides with
 __global__ void k_inject_mask(const uint8_t *dirf, int nxf, int nyf, uint8_t *dirc, int nxc, int nyc, int nzc) {
   const int I = blockIdx.x * 32 + threadIdx.x;
   const int J = blockIdx.y * 8 + threadIdx.y, K = blockIdx.z;
@@ -125,6 +228,13 @@ __global__ void k_inject_mask(const uint8_t *dirf, int nxf, int nyf, uint8_t *di
   dirc[node_index(I, J, K, nxc, nyc)] = dirf[node_index(2 * I, 2 * J, 2 * K, nxf, nyf)];
 }
 
+// split-colour copy of a level's natural mask (slots without a node stay 1: never updated)
+__global__ void k_split_mask(const uint8_t *dir, uint8_t *dirs, Lv L) {
+  NODE_IJK(L.nx, L.ny)
+  dirs[sidx(L, i, j, k)] = dir[n];
+}
+
+// ---- fine level <-> FP64 refinement ---------------------------------------------------------------
 // rho/eps0 from the fixed-point charge; Dirichlet values on the mask
 __global__ void k_rhs(const unsigned long long *Q, double *f, double *phi, const uint8_t *dir, int nx, int ny, int nz,
                       double unit, double V0, int zero_charge) {
@@ -136,28 +246,31 @@ __global__ void k_rhs(const unsigned long long *Q, double *f, double *phi, const
 }
 
 // Residual of the FP64 system r = f - A phi, handed straight to the finest V-cycle level as its
-// right-hand side (rounded to the level's type T) with a zero initial correction.  The squared
-// norms of h^2 r and of h^2 times the lifted right-hand side (f - A phi_D: only the plane below
-// the anode carries a nonzero Dirichlet term) are accumulated in FP32 -- they only decide
-// convergence -- so the FP64 pipe (1/64 of the FP32 rate on this part) runs just the stencil.
-// 3D launch with blocks (32, 8); block partials land at the block's linear id.
+// right-hand side (rounded to the level's type T, split-colour layout) with a zero initial
+// correction.  The squared norms of h^2 r and of h^2 times the lifted right-hand side (f - A
+// phi_D: only the plane below the anode carries a nonzero Dirichlet term) are accumulated in
+// FP32 -- they only decide convergence -- so the FP64 pipe (1/64 of the FP32 rate on this
+// part) runs just the stencil.  3D launch with blocks (32, 8); block partials land at the
+// block's linear id.
 template <typename T>
-__global__ void k_residual64(const double *phi, const double *f, T *fl, T *ul, const uint8_t *dir, int nx, int ny,
-                             int nz, double inv_h2, float h2f, float V0f, double *part, int lift) {
+__global__ void k_residual64(const double *phi, const double *f, T *fl, T *ul, const uint8_t *dir, Lv L,
+                             double inv_h2, float h2f, float V0f, double *part, int lift) {
   __shared__ float sh[2][8];
+  const int nx = L.nx, ny = L.ny, nz = L.nz;
   const int i = blockIdx.x * 32 + threadIdx.x;
   const int j = blockIdx.y * 8 + threadIdx.y, k = blockIdx.z;
   float s = 0.f, sl = 0.f;
   if (i <= nx && j <= ny) {
     const int64_t n = node_index(i, j, k, nx, ny);
-    ul[n] = 0;
+    const int64_t m = sidx(L, i, j, k);
+    ul[m] = 0;
     if (dir[n]) {
-      fl[n] = 0;
+      fl[m] = 0;
     } else {
       const double fn = f[n];
       const double t = fma(6.0, phi[n], -nb_sum<double>(phi, i, j, k, nx, ny));
       const double rr = fma(-t, inv_h2, fn);
-      fl[n] = (T)rr;
+      fl[m] = (T)rr;
       const float rs = (float)rr * h2f;
       s = rs * rs;
       if (lift) {
@@ -181,25 +294,59 @@ __global__ void k_residual64(const double *phi, const double *f, T *fl, T *ul, c
   }
 }
 
-// fixed-order reduction of nb block partials: thread t sums blocks t, t+1024, ... then a tree
-__global__ void __launch_bounds__(1024) k_sum_partials(const double *part, int64_t nb, double *out) {
-  __shared__ double sa[1024], sb[1024];
+// Fixed-order two-stage reduction of nb (a, b) block partials: block q of stage 1 sums the
+// contiguous chunk q (thread t takes every 256th entry, then a tree), stage 2 one block the chunks.
+constexpr int kSumChunks = 128;
+__global__ void __launch_bounds__(256) k_sum_stage1(const double *part, int64_t nb, double *mid) {
+  __shared__ double sa[256], sb[256];
+  const int64_t per = (nb + kSumChunks - 1) / kSumChunks;
+  const int64_t q0 = (int64_t)blockIdx.x * per, q1 = q0 + per < nb ? q0 + per : nb;
   double a = 0.0, b = 0.0;
-  for (int64_t q = threadIdx.x; q < nb; q += 1024) { a += part[2 * q]; b += part[2 * q + 1]; }
+  for (int64_t q = q0 + threadIdx.x; q < q1; q += 256) { a += part[2 * q]; b += part[2 * q + 1]; }
   sa[threadIdx.x] = a;
   sb[threadIdx.x] = b;
   __syncthreads();
-  for (int w = 512; w > 0; w >>= 1) {
+  for (int w = 128; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) { sa[threadIdx.x] += sa[threadIdx.x + w]; sb[threadIdx.x] += sb[threadIdx.x + w]; }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) { mid[2 * blockIdx.x] = sa[0]; mid[2 * blockIdx.x + 1] = sb[0]; }
+}
+
+__global__ void __launch_bounds__(kSumChunks) k_sum_stage2(const double *mid, double *out) {
+  __shared__ double sa[kSumChunks], sb[kSumChunks];
+  sa[threadIdx.x] = mid[2 * threadIdx.x];
+  sb[threadIdx.x] = mid[2 * threadIdx.x + 1];
+  __syncthreads();
+  for (int w = kSumChunks / 2; w > 0; w >>= 1) {
     if ((int)threadIdx.x < w) { sa[threadIdx.x] += sa[threadIdx.x + w]; sb[threadIdx.x] += sb[threadIdx.x + w]; }
     __syncthreads();
   }
   if (threadIdx.x == 0) { out[0] = sa[0]; out[1] = sb[0]; }
 }
 
+// phi += e on free nodes (e in the finest level's split layout; z: plane groups of kKZ)
 template <typename T>
-__global__ void k_correct(double *phi, const T *u, const uint8_t *dir, int64_t n) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    if (!dir[i]) phi[i] += (double)u[i];
+__global__ void k_correct(double *phi, const T *u, const uint8_t *dir, Lv L) {
+  const int i = blockIdx.x * 32 + threadIdx.x;
+  const int j = blockIdx.y * 8 + threadIdx.y, k0 = blockIdx.z * kKZ;
+  if (i > L.nx || j > L.ny) return;
+  double v[kKZ];
+  bool ok[kKZ];
+#pragma unroll
+  for (int q = 0; q < kKZ; ++q) {
+    const int k = k0 + q;
+    ok[q] = k > 0 && k < L.nz;
+    v[q] = 0;
+    if (ok[q]) {
+      const int64_t n = node_index(i, j, k, L.nx, L.ny);
+      ok[q] = !dir[n];
+      v[q] = phi[n] + (double)u[sidx(L, i, j, k)];
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < kKZ; ++q)
+    if (ok[q]) phi[node_index(i, j, k0 + q, L.nx, L.ny)] = v[q];
 }
 
 // E = -grad phi at every node, float64 differences rounded once to float32
@@ -219,12 +366,6 @@ __global__ void k_efield(const double *phi, float4 *E, int nx, int ny, int nz, d
     e.w = 0.f;
     E[n] = e;
   }
-}
-
-static int node_grid(pic_t *h, int64_t n) {
-  int64_t g = (n + kThreads - 1) / kThreads;
-  const int64_t cap = (int64_t)h->nsm * 16;
-  return (int)(g < 1 ? 1 : (g > cap ? cap : g));
 }
 
 template <typename T>
@@ -249,29 +390,29 @@ double *lvl_r<double>(MgLevel &L) { return L.rd; }
 template <typename T>
 static void vcycle(pic_t *h, int l) {
   MgLevel &L = h->mg[l];
+  const Lv lv = lv_of(L);
   const T h2 = (T)(L.h * L.h), inv_h2 = (T)(1.0 / (L.h * L.h));
   const int last = (int)h->mg.size() - 1;
   if (l == last) {
     ++h->nlaunch;
-    k_coarse<T><<<1, 1024, 0, h->stream>>>(lvl_u<T>(L), lvl_f<T>(L), L.dir, L.nx, L.ny, L.nz, h2, 60);
+    k_coarse<T><<<1, 1024, 0, h->stream>>>(lvl_u<T>(L), lvl_f<T>(L), L.dirs, lv, h2, 60);
     return;
   }
-  const dim3 cg = color_grid3(L.nx, L.ny, L.nz), bl = node_block();
+  const dim3 sg = slot_grid(lv, 1), sg2 = slot_grid(lv, 2), bl = node_block();
   for (int s = 0; s < 2; ++s)
-    for (int c = 0; c < 2; ++c) { ++h->nlaunch; k_smooth<T><<<cg, bl, 0, h->stream>>>(lvl_u<T>(L), lvl_f<T>(L), L.dir, L.nx, L.ny, L.nz, h2, c); }
+    for (int c = 0; c < 2; ++c) { ++h->nlaunch; k_smooth<T><<<sg, bl, 0, h->stream>>>(lvl_u<T>(L), lvl_f<T>(L), L.dirs, lv, h2, c); }
   ++h->nlaunch;
-  k_residual<T><<<node_grid3(L.nx, L.ny, L.nz), bl, 0, h->stream>>>(lvl_u<T>(L), lvl_f<T>(L), lvl_r<T>(L), L.dir, L.nx,
-                                                                 L.ny, L.nz, inv_h2);
+  k_residual<T><<<sg2, bl, 0, h->stream>>>(lvl_u<T>(L), lvl_f<T>(L), lvl_r<T>(L), L.dirs, lv, inv_h2);
   MgLevel &Cl = h->mg[l + 1];
+  const Lv cv = lv_of(Cl);
   ++h->nlaunch;
-  k_restrict<T, T><<<node_grid3(Cl.nx, Cl.ny, Cl.nz), bl, 0, h->stream>>>(lvl_r<T>(L), L.nx, L.ny, lvl_f<T>(Cl), lvl_u<T>(Cl),
-                                                                       Cl.dir, Cl.nx, Cl.ny, Cl.nz);
+  k_restrict<T, T><<<node_grid3(Cl.nx, Cl.ny, Cl.nz), bl, 0, h->stream>>>(lvl_r<T>(L), lv, lvl_f<T>(Cl), lvl_u<T>(Cl),
+                                                                       Cl.dirs, cv);
   vcycle<T>(h, l + 1);
   ++h->nlaunch;
-  k_prolong<T, T><<<node_grid3(L.nx, L.ny, L.nz), bl, 0, h->stream>>>(lvl_u<T>(Cl), Cl.nx, Cl.ny, lvl_u<T>(L), L.dir, L.nx,
-                                                                     L.ny, L.nz);
+  k_prolong<T, T><<<sg2, bl, 0, h->stream>>>(lvl_u<T>(Cl), cv, lvl_u<T>(L), L.dirs, lv);
   for (int s = 0; s < 2; ++s)
-    for (int c = 1; c >= 0; --c) { ++h->nlaunch; k_smooth<T><<<cg, bl, 0, h->stream>>>(lvl_u<T>(L), lvl_f<T>(L), L.dir, L.nx, L.ny, L.nz, h2, c); }
+    for (int c = 1; c >= 0; --c) { ++h->nlaunch; k_smooth<T><<<sg, bl, 0, h->stream>>>(lvl_u<T>(L), lvl_f<T>(L), L.dirs, lv, h2, c); }
 }
 
 // one V-cycle on A e = r (r already on the finest level, e = 0 there) and phi += e
@@ -280,7 +421,8 @@ static void cycle_fine(pic_t *h) {
   MgLevel &L = h->mg[0];
   vcycle<T>(h, 0);
   ++h->nlaunch;
-  k_correct<T><<<node_grid(h, L.nnode), kThreads, 0, h->stream>>>(h->phi, lvl_u<T>(L), L.dir, L.nnode);
+  const dim3 g((L.nx + 1 + 31) / 32, (L.ny + 1 + 7) / 8, (L.nz + 1 + kKZ - 1) / kKZ);
+  k_correct<T><<<g, node_block(), 0, h->stream>>>(h->phi, lvl_u<T>(L), L.dir, lv_of(L));
 }
 
 int stage_efield(pic_t *h) {
@@ -297,12 +439,19 @@ int mg_build_masks(pic_t *h) {
     k_inject_mask<<<node_grid3(Cl.nx, Cl.ny, Cl.nz), node_block(), 0, h->stream>>>(F.dir, F.nx, F.ny, Cl.dir, Cl.nx, Cl.ny,
                                                                                   Cl.nz);
   }
+  for (size_t l = 0; l < h->mg.size(); ++l) {
+    MgLevel &L = h->mg[l];
+    PIC_CUDA(h, cudaMemsetAsync(L.dirs, 1, (size_t)2 * L.nper, h->stream));
+    ++h->nlaunch;
+    k_split_mask<<<node_grid3(L.nx, L.ny, L.nz), node_block(), 0, h->stream>>>(L.dir, L.dirs, lv_of(L));
+  }
   return launch_check(h, "mg_masks");
 }
 
 // Solve for phi with the current deposited charge (or none), anode at V0.
 int stage_solve(pic_t *h, bool zero_charge, double V0) {
   MgLevel &L = h->mg[0];
+  const Lv lv = lv_of(L);
   const double unit = kQe * h->prm.w_min / 1073741824.0 / (h->dx * h->dx * h->dx) / kEps0;
   ++h->nlaunch;
   k_rhs<<<node_grid3(h->nx, h->ny, h->nz), node_block(), 0, h->stream>>>(h->Q, h->rhs, h->phi, L.dir, h->nx, h->ny, h->nz,
@@ -318,13 +467,14 @@ int stage_solve(pic_t *h, bool zero_charge, double V0) {
   for (;; ++cyc) {
     ++h->nlaunch;
     if (mixed)
-      k_residual64<float><<<rg, node_block(), 0, h->stream>>>(h->phi, h->rhs, L.f, L.u, L.dir, h->nx, h->ny, h->nz,
-                                                              inv_h2, h2f, V0f, h->red, cyc == 0 ? 1 : 0);
+      k_residual64<float><<<rg, node_block(), 0, h->stream>>>(h->phi, h->rhs, L.f, L.u, L.dir, lv, inv_h2, h2f, V0f,
+                                                              h->red, cyc == 0 ? 1 : 0);
     else
-      k_residual64<double><<<rg, node_block(), 0, h->stream>>>(h->phi, h->rhs, L.fd, L.ud, L.dir, h->nx, h->ny,
-                                                               h->nz, inv_h2, h2f, V0f, h->red, cyc == 0 ? 1 : 0);
-    ++h->nlaunch;
-    k_sum_partials<<<1, 1024, 0, h->stream>>>(h->red, nb, h->red_out);
+      k_residual64<double><<<rg, node_block(), 0, h->stream>>>(h->phi, h->rhs, L.fd, L.ud, L.dir, lv, inv_h2, h2f,
+                                                               V0f, h->red, cyc == 0 ? 1 : 0);
+    h->nlaunch += 2;
+    k_sum_stage1<<<kSumChunks, 256, 0, h->stream>>>(h->red, nb, h->red_mid);
+    k_sum_stage2<<<1, kSumChunks, 0, h->stream>>>(h->red_mid, h->red_out);
     PIC_CUDA(h, cudaMemcpyAsync(norms, h->red_out, sizeof norms, cudaMemcpyDeviceToHost, h->stream));
     PIC_CUDA(h, cudaStreamSynchronize(h->stream));
     if (cyc == 0) lifted = sqrt(norms[1]);

@@ -82,7 +82,34 @@ struct PushArgs {
   DevClock *clk;
 };
 
-__global__ void __launch_bounds__(256) k_push(PushArgs a) {
+// The rare path of the push (an SP whose move may reach a solid cell or leave the domain): the
+// FP64 cell traversal and, for an ion that hits the tip or the cathode, the sputter and
+// bombardment accumulators of the face it hits.  Kept out of line so that the common path
+// of k_push needs few registers.  Returns true when the SP is removed.
+__device__ __noinline__ bool crosser_event(const PushArgs &a, float x, float y, float z, float x1, float y1, float z1,
+                                          float vx, float vy, float vz, int32_t w) {
+  const double p0[3] = {(double)x, (double)y, (double)z};
+  const double p1[3] = {(double)x1, (double)y1, (double)z1};
+  int64_t vcell = -1;
+  int dcode = -1;
+  const int ev = first_event(p0, p1, a.solid, a.nx, a.ny, a.nz, &vcell, &dcode);
+  if (ev == kEvNone) return false;
+  if (a.ion && (ev == kEvSolid || ev == kEvCathode)) {
+    const int64_t f = face_lookup(a.face_key, a.nface, vcell * 6 + dcode);
+    if (f >= 0) {
+      const double v2 = __dadd_rn(__dadd_rn(__dmul_rn((double)vx, (double)vx), __dmul_rn((double)vy, (double)vy)),
+                                  __dmul_rn((double)vz, (double)vz));
+      const double energy = 0.5 * a.mass * v2 / kQe;
+      const double ww = (double)w * a.w_min;
+      atomicAdd(&a.acc_sput[f], (unsigned long long)(int64_t)floor(ww * sputter_yield(energy) * 16777216.0));
+      atomicAdd(&a.acc_Eb[f], (unsigned long long)(int64_t)floor(ww * energy * 1048576.0));
+      atomicAdd((unsigned long long *)&a.clk->ctr[cIonImpacts], 1ull);
+    }
+  }
+  return true;
+}
+
+__global__ void __launch_bounds__(256, 4) k_push(PushArgs a) {
   const int64_t n = a.clk->n[a.species];
   int removed = 0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -112,28 +139,7 @@ __global__ void __launch_bounds__(256) k_push(PushArgs a) {
         const int m = max(abs(i1 - i0), max(abs(j1 - j0), abs(k1 - k0)));
         const bool inside = i1 >= 0 && i1 < a.nx && j1 >= 0 && j1 < a.ny && k1 >= 0 && k1 < a.nz;
         const bool clear = inside && (int)a.cheb[cell_index(i0, j0, k0, a.nx, a.ny)] > m;
-        if (!clear) {
-          const double p0[3] = {(double)x, (double)y, (double)z};
-          const double p1[3] = {(double)x1, (double)y1, (double)z1};
-          int64_t vcell = -1;
-          int dcode = -1;
-          const int ev = first_event(p0, p1, a.solid, a.nx, a.ny, a.nz, &vcell, &dcode);
-          if (ev != kEvNone) {
-            alive = false;
-            if (a.ion && (ev == kEvSolid || ev == kEvCathode)) {
-              const int64_t f = face_lookup(a.face_key, a.nface, vcell * 6 + dcode);
-              if (f >= 0) {
-                const double v2 = __dadd_rn(__dadd_rn(__dmul_rn((double)vx, (double)vx), __dmul_rn((double)vy, (double)vy)),
-                                            __dmul_rn((double)vz, (double)vz));
-                const double energy = 0.5 * a.mass * v2 / kQe;
-                const double ww = (double)w * a.w_min;
-                atomicAdd(&a.acc_sput[f], (unsigned long long)(int64_t)floor(ww * sputter_yield(energy) * 16777216.0));
-                atomicAdd(&a.acc_Eb[f], (unsigned long long)(int64_t)floor(ww * energy * 1048576.0));
-                atomicAdd((unsigned long long *)&a.clk->ctr[cIonImpacts], 1ull);
-              }
-            }
-          }
-        }
+        if (!clear) alive = !crosser_event(a, x, y, z, x1, y1, z1, vx, vy, vz, w);
       }
     }
     if (alive) {
@@ -162,34 +168,73 @@ __global__ void k_keys(SpeciesBuf p, uint32_t *key, uint32_t *cnt, int nx, int n
   }
 }
 
+// Counting-sort scatter.  Each warp takes 32 consecutive SPs; lanes with the same cell key form
+// a group (__match_any_sync) whose leader reserves the group's places with one atomic, and the
+// group fills them in input order.  The input is the previous step's sorted order (SPs rarely
+// change cell), so most cells get all their SPs from one group and come out already in stable
+// order; the fix-up below only sorts segments that did not.
 __global__ void k_scatter(const uint32_t *__restrict__ key, uint32_t *cnt, const uint32_t *__restrict__ off,
-                          uint32_t *perm, const DevClock *clk, int s) {
+                          uint32_t *perm, uint32_t *skey, const DevClock *clk, int s) {
   const int64_t n = clk->n[s];
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const uint32_t k = key[i];
-    if (k == kDead) continue;
-    const uint32_t r = atomicSub(&cnt[k], 1u) - 1u;
-    perm[off[k] + r] = (uint32_t)i;
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; i0 < n; i0 += warps * 32) {
+    const int64_t i = i0 + lane;
+    const uint32_t k = i < n ? key[i] : kDead;
+    const unsigned grp = __match_any_sync(0xffffffffu, k);
+    const int leader = __ffs(grp) - 1;
+    const int size = __popc(grp), rank = __popc(grp & ((1u << lane) - 1u));
+    uint32_t base = 0;
+    if (lane == leader && k != kDead) base = atomicSub(&cnt[k], (uint32_t)size) - (uint32_t)size;
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (k != kDead) {
+      const uint32_t pos = off[k] + base + (uint32_t)rank;
+      perm[pos] = (uint32_t)i;
+      skey[pos] = k;
+    }
   }
 }
 
-// Restore source order inside every cell segment (the scatter order is arbitrary): short
-// segments are insertion-sorted by their head thread, long ones are queued for k_fix_long.
-__global__ void k_fix_short(const uint32_t *__restrict__ key, const uint32_t *__restrict__ off, uint32_t *perm,
-                            int64_t ncell, int2 *long_list, int *long_n, int long_cap, DevClock *clk) {
+// Restore source order inside every cell segment that the scatter left unsorted.  Segment heads
+// come from the sorted keys (a position whose key differs from its left neighbour's); the
+// length is found by reading on in the keys (off[] only past 32).  Unsorted segments of up to
+// 4 SPs are sorted in registers by their head thread; 5 to 32 are queued for k_fix_mid (one
+// warp each), longer ones for k_fix_long (one block each).
+__global__ void k_fix_short(const uint32_t *__restrict__ skey, const uint32_t *__restrict__ off, uint32_t *perm,
+                            int64_t ncell, int2 *mid_list, int *mid_n, int mid_cap, int2 *long_list, int *long_n,
+                            int long_cap, DevClock *clk) {
   const int64_t n = off[ncell];
   for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
-    const uint32_t k = key[perm[s]];
-    if (off[k] != (uint32_t)s) continue;
-    const int len = (int)(off[k + 1] - (uint32_t)s);
+    const uint32_t k = skey[s];
+    if (s > 0 && skey[s - 1] == k) continue;
+    int len = 1;
+    while (len <= 32 && s + len < n && skey[s + len] == k) ++len;
+    if (len > 32) len = (int)(off[k + 1] - (uint32_t)s);
     if (len <= 1) continue;
-    if (len <= 32) {
-      for (int a = 1; a < len; ++a) {
+    if (len <= 4) {
+      uint32_t v[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) v[a] = a < len ? perm[s + a] : 0xFFFFFFFFu;
+      if (v[0] < v[1] && (len < 3 || v[1] < v[2]) && (len < 4 || v[2] < v[3])) continue;   // already in order
+      // sorting network for 4 (pads sort last)
+#define PIC_CSWAP(a, b) { const uint32_t lo = min(v[a], v[b]), hi = max(v[a], v[b]); v[a] = lo; v[b] = hi; }
+      PIC_CSWAP(0, 1) PIC_CSWAP(2, 3) PIC_CSWAP(0, 2) PIC_CSWAP(1, 3) PIC_CSWAP(1, 2)
+#undef PIC_CSWAP
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+        if (a < len) perm[s + a] = v[a];
+    } else if (len <= 32) {
+      bool sorted = true;
+      uint32_t prev = perm[s];
+      for (int a = 1; a < len && sorted; ++a) {
         const uint32_t v = perm[s + a];
-        int b = a - 1;
-        while (b >= 0 && perm[s + b] > v) { perm[s + b + 1] = perm[s + b]; --b; }
-        perm[s + b + 1] = v;
+        sorted = prev < v;
+        prev = v;
       }
+      if (sorted) continue;
+      const int q = atomicAdd(mid_n, 1);
+      if (q < mid_cap) mid_list[q] = make_int2((int)s, len);
+      else atomicOr(&clk->err, kErrSegment);
     } else if (len <= kMaxSegment) {
       const int q = atomicAdd(long_n, 1);
       if (q < long_cap) long_list[q] = make_int2((int)s, len);
@@ -197,6 +242,25 @@ __global__ void k_fix_short(const uint32_t *__restrict__ key, const uint32_t *__
     } else {
       atomicOr(&clk->err, kErrSegment);
     }
+  }
+}
+
+// one warp per queued segment of 5..32 SPs: lane l holds element l, its rank is the number of
+// smaller elements (the original indices are distinct), and it stores itself at that rank
+__global__ void k_fix_mid(uint32_t *perm, const int2 *mid_list, const int *mid_n, int mid_cap) {
+  const int lane = threadIdx.x & 31;
+  const int nq = min(*mid_n, mid_cap);
+  const int warps = (gridDim.x * blockDim.x) >> 5;
+  for (int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < nq; q += warps) {
+    const int2 seg = mid_list[q];
+    const uint32_t v = lane < seg.y ? perm[seg.x + lane] : 0xFFFFFFFFu;
+    int rank = 0;
+    for (int m = 0; m < 32; ++m) {
+      const uint32_t o = __shfl_sync(0xffffffffu, v, m);
+      rank += o < v ? 1 : 0;
+    }
+    __syncwarp();
+    if (lane < seg.y) perm[seg.x + rank] = v;
   }
 }
 
@@ -227,14 +291,37 @@ __global__ void __launch_bounds__(1024) k_fix_long(uint32_t *perm, const int2 *l
   }
 }
 
+// dst[s] = src[perm[s]] for every field; each thread takes kGatherItems positions spaced by the
+// grid stride and issues all of their loads before the stores
+constexpr int kGatherItems = 4;
 __global__ void k_gather(SpeciesBuf src, SpeciesBuf dst, const uint32_t *__restrict__ perm, const uint32_t *off,
                          int64_t ncell) {
   const int64_t n = off[ncell];
-  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
-    const uint32_t q = perm[s];
-    dst.x[s] = src.x[q]; dst.y[s] = src.y[q]; dst.z[s] = src.z[q];
-    dst.vx[s] = src.vx[q]; dst.vy[s] = src.vy[q]; dst.vz[s] = src.vz[q];
-    dst.w[s] = src.w[q]; dst.id[s] = src.id[q];
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t s0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s0 < n; s0 += stride * kGatherItems) {
+    uint32_t q[kGatherItems];
+#pragma unroll
+    for (int u = 0; u < kGatherItems; ++u) q[u] = s0 + u * stride < n ? perm[s0 + u * stride] : 0u;
+    float x[kGatherItems], y[kGatherItems], z[kGatherItems], vx[kGatherItems], vy[kGatherItems], vz[kGatherItems];
+    int32_t w[kGatherItems];
+    uint64_t id[kGatherItems];
+#pragma unroll
+    for (int u = 0; u < kGatherItems; ++u) {
+      if (s0 + u * stride < n) {
+        x[u] = src.x[q[u]]; y[u] = src.y[q[u]]; z[u] = src.z[q[u]];
+        vx[u] = src.vx[q[u]]; vy[u] = src.vy[q[u]]; vz[u] = src.vz[q[u]];
+        w[u] = src.w[q[u]]; id[u] = src.id[q[u]];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kGatherItems; ++u) {
+      const int64_t s = s0 + u * stride;
+      if (s < n) {
+        dst.x[s] = x[u]; dst.y[s] = y[u]; dst.z[s] = z[u];
+        dst.vx[s] = vx[u]; dst.vy[s] = vy[u]; dst.vz[s] = vz[u];
+        dst.w[s] = w[u]; dst.id[s] = id[u];
+      }
+    }
   }
 }
 
@@ -313,11 +400,14 @@ int stage_sort(pic_t *h) {
     if (!h->keys_valid[s]) PIC_TRY(stage_keys(h, s));
     PIC_TRY(scan_u32(h, S.cnt, S.off, h->ncell, nullptr, S.off + h->ncell));
     ++h->nlaunch;
-    k_scatter<<<particle_grid(h), kThreads, 0, h->stream>>>(S.key, S.cnt, S.off, S.perm, h->clock, s);
-    PIC_CUDA(h, cudaMemsetAsync(long_n, 0, sizeof(int), h->stream));
+    k_scatter<<<particle_grid(h), kThreads, 0, h->stream>>>(S.key, S.cnt, S.off, S.perm, S.skey, h->clock, s);
+    PIC_CUDA(h, cudaMemsetAsync(long_n, 0, 2 * sizeof(int), h->stream));   // long_n[0]: long, [1]: mid
     ++h->nlaunch;
-    k_fix_short<<<particle_grid(h), kThreads, 0, h->stream>>>(S.key, S.off, S.perm, h->ncell, long_list, long_n,
+    k_fix_short<<<particle_grid(h), kThreads, 0, h->stream>>>(S.skey, S.off, S.perm, h->ncell, h->mid_list,
+                                                              long_n + 1, (int)h->mid_cap, long_list, long_n,
                                                               long_cap, h->clock);
+    ++h->nlaunch;
+    k_fix_mid<<<particle_grid(h), kThreads, 0, h->stream>>>(S.perm, h->mid_list, long_n + 1, (int)h->mid_cap);
     ++h->nlaunch;
     k_fix_long<<<h->nsm, 1024, 0, h->stream>>>(S.perm, long_list, long_n, long_cap);
     ++h->nlaunch;

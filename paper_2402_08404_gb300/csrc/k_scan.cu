@@ -52,12 +52,18 @@ __device__ T block_incl_scan(T v, T *sh, T *tot) {
   return v;
 }
 
+// elements per thread in the chunk scan; block chunks start on multiples of it (aligned vectors)
+constexpr int kItems = 16;
+__device__ __forceinline__ int64_t scan_chunk(int64_t n, int nb) {
+  return ((n + nb - 1) / nb + kItems - 1) / kItems * kItems;
+}
+
 template <typename T>
 __global__ void k_scan_partial(const T *__restrict__ in, int64_t n_host, const int64_t *n_dev, T *partial) {
   __shared__ T sh[33];
   const int64_t n = n_dev ? *n_dev : n_host;
   const int nb = gridDim.x;
-  const int64_t chunk = (n + nb - 1) / nb;
+  const int64_t chunk = scan_chunk(n, nb);
   const int64_t lo = (int64_t)blockIdx.x * chunk;
   const int64_t hi = lo + chunk < n ? lo + chunk : n;
   T s = 0;
@@ -81,22 +87,53 @@ __global__ void k_scan_top(T *partial, int nb, T *total) {
   if (threadIdx.x == 0 && total) *total = carry;
 }
 
+// per-block chunk scan: each thread scans kItems consecutive elements in registers (16-byte
+// vector loads and stores when the run is whole), the block scans the thread totals
 template <typename T>
 __global__ void k_scan_apply(const T *__restrict__ in, T *__restrict__ out, int64_t n_host, const int64_t *n_dev,
                              const T *__restrict__ partial) {
+  static_assert((kItems * sizeof(T)) % 16 == 0, "whole vectors per thread");
+  constexpr int kVec = kItems * (int)sizeof(T) / 16;
   __shared__ T sh[33];
   const int64_t n = n_dev ? *n_dev : n_host;
   const int nb = gridDim.x;
-  const int64_t chunk = (n + nb - 1) / nb;
+  const int64_t chunk = scan_chunk(n, nb);
   const int64_t lo = (int64_t)blockIdx.x * chunk;
   const int64_t hi = lo + chunk < n ? lo + chunk : n;
   T carry = partial[blockIdx.x];
-  for (int64_t base = lo; base < hi; base += blockDim.x) {
-    const int64_t i = base + threadIdx.x;
-    T v = i < hi ? in[i] : T(0);
+  for (int64_t base = lo; base < hi; base += (int64_t)blockDim.x * kItems) {
+    const int64_t i0 = base + (int64_t)threadIdx.x * kItems;
+    const bool whole = i0 + kItems <= hi;
+    union { uint4 q[kVec]; T e[kItems]; } v;
+    if (whole) {
+      const uint4 *src = reinterpret_cast<const uint4 *>(in + i0);
+#pragma unroll
+      for (int q = 0; q < kVec; ++q) v.q[q] = src[q];
+    } else {
+#pragma unroll
+      for (int q = 0; q < kItems; ++q) v.e[q] = i0 + q < hi ? in[i0 + q] : T(0);
+    }
+    T s = 0;
+#pragma unroll
+    for (int q = 0; q < kItems; ++q) s += v.e[q];
     T tot;
-    T inc = block_incl_scan<T>(v, sh, &tot);
-    if (i < hi) out[i] = carry + inc - v;
+    const T inc = block_incl_scan<T>(s, sh, &tot);
+    T run = carry + inc - s;
+#pragma unroll
+    for (int q = 0; q < kItems; ++q) {
+      const T x = v.e[q];
+      v.e[q] = run;
+      run += x;
+    }
+    if (whole) {
+      uint4 *dst = reinterpret_cast<uint4 *>(out + i0);
+#pragma unroll
+      for (int q = 0; q < kVec; ++q) dst[q] = v.q[q];
+    } else {
+#pragma unroll
+      for (int q = 0; q < kItems; ++q)
+        if (i0 + q < hi) out[i0 + q] = v.e[q];
+    }
     carry += tot;
   }
 }

@@ -269,13 +269,17 @@ int pic_create(const pic_geometry_t *geometry, const pic_grid_t *grid, const pic
       MgLevel L;
       L.nx = lx; L.ny = ly; L.nz = lz; L.h = hh;
       L.nnode = (int64_t)(lx + 1) * (ly + 1) * (lz + 1);
+      L.Xh = (lx + 2) / 2;
+      L.nper = (int64_t)(lz + 1) * (ly + 1) * L.Xh;
+      const int64_t ns = 2 * L.nper;
       L.dir = alloc_n<uint8_t>(h, L.nnode); A(L.dir);
-      L.u = alloc_n<float>(h, L.nnode); A(L.u);
-      L.f = alloc_n<float>(h, L.nnode); A(L.f);
-      L.r = alloc_n<float>(h, L.nnode); A(L.r);
-      L.ud = alloc_n<double>(h, L.nnode); A(L.ud);
-      L.fd = alloc_n<double>(h, L.nnode); A(L.fd);
-      L.rd = alloc_n<double>(h, L.nnode); A(L.rd);
+      L.dirs = alloc_n<uint8_t>(h, ns); A(L.dirs);
+      L.u = alloc_n<float>(h, ns); A(L.u);
+      L.f = alloc_n<float>(h, ns); A(L.f);
+      L.r = alloc_n<float>(h, ns); A(L.r);
+      L.ud = alloc_n<double>(h, ns); A(L.ud);
+      L.fd = alloc_n<double>(h, ns); A(L.fd);
+      L.rd = alloc_n<double>(h, ns); A(L.rd);
       h->mg.push_back(L);
       if ((lx & 1) || (ly & 1) || (lz & 1) || std::min(lx, std::min(ly, lz)) < 8) break;
       lx /= 2; ly /= 2; lz /= 2; hh *= 2.0;
@@ -301,6 +305,7 @@ int pic_create(const pic_geometry_t *geometry, const pic_grid_t *grid, const pic
     }
     S.key = alloc_n<uint32_t>(h, S.cap); A(S.key);
     S.perm = alloc_n<uint32_t>(h, S.cap); A(S.perm);
+    S.skey = alloc_n<uint32_t>(h, S.cap); A(S.skey);
     S.cnt = alloc_n<uint32_t>(h, h->ncell + 1); A(S.cnt);
     S.off = alloc_n<uint32_t>(h, h->ncell + 1); A(S.off);
     if (s != PIC_ION) capsum += S.cap;
@@ -335,8 +340,15 @@ int pic_create(const pic_geometry_t *geometry, const pic_grid_t *grid, const pic
   // residual-norm partials: one pair per block of the 3D node grid (32 x 8 x 1 blocks)
   h->red = alloc_n<double>(h, (int64_t)2 * ((h->nx + 1 + 31) / 32) * ((h->ny + 1 + 7) / 8) * (h->nz + 1)); A(h->red);
   h->red_out = alloc_n<double>(h, 2); A(h->red_out);
+  h->red_mid = alloc_n<double>(h, 2 * 128); A(h->red_mid);
   h->tmp_len = alloc_n<int64_t>(h, 16); A(h->tmp_len);
   h->long_list = alloc_n<int2>(h, kLongCap); A(h->long_list);
+  {
+    int64_t mc = 0;
+    for (int s = 0; s < 3; ++s) mc = std::max<int64_t>(mc, h->sp[s].cap);
+    h->mid_cap = std::min<int64_t>(mc / 5 + 1024, INT32_MAX);   // a queued segment holds >= 5 SPs
+    h->mid_list = alloc_n<int2>(h, h->mid_cap); A(h->mid_list);
+  }
   h->long_n = alloc_n<int>(h, 16); A(h->long_n);
   h->clock = alloc_n<DevClock>(h, 1); A(h->clock);
   if (!okalloc) return fail(PIC_E_CUDA, "device allocation failed");

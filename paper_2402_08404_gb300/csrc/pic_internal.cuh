@@ -74,6 +74,7 @@ struct Species {
   SpeciesBuf a{}, b{};        // current and scratch SoA buffers
   uint32_t *key = nullptr;    // cell key per SP (kDead when removed)
   uint32_t *perm = nullptr;   // sort permutation
+  uint32_t *skey = nullptr;   // cell key at each sorted position (written by the scatter)
   uint32_t *cnt = nullptr;    // per-cell counts (zero between sorts), ncell+1
   uint32_t *off = nullptr;    // per-cell offsets of the last sort, ncell+1
 };
@@ -81,9 +82,12 @@ struct Species {
 struct MgLevel {
   int nx, ny, nz;             // cells
   int64_t nnode;
+  int Xh;                     // slots per row and colour, (nx + 2) / 2
+  int64_t nper;               // slots per colour, (nz + 1) (ny + 1) Xh
   double h;
-  uint8_t *dir = nullptr;     // Dirichlet mask per node
-  float *u = nullptr, *f = nullptr, *r = nullptr;
+  uint8_t *dir = nullptr;     // Dirichlet mask per node (natural order)
+  uint8_t *dirs = nullptr;    // the same in the split-colour layout (2 nper; unused slots 1)
+  float *u = nullptr, *f = nullptr, *r = nullptr;        // split-colour, 2 nper each
   double *ud = nullptr, *fd = nullptr, *rd = nullptr;   // FP64 V-cycle storage (plain form)
 };
 
@@ -149,8 +153,11 @@ struct pic_s {
   int32_t *pair_ncoll = nullptr;
   double *red = nullptr;         // reduction partials
   double *red_out = nullptr;
+  double *red_mid = nullptr;     // first-stage sums of the partials (2 x 128)
   int64_t *tmp_len = nullptr;    // device-side lengths for scans
   int2 *long_list = nullptr;     // sort: long cell segments queued for the block-level fix-up
+  int2 *mid_list = nullptr;      // sort: 5..32-SP cell segments queued for the warp-level fix-up
+  int64_t mid_cap = 0;
   int *long_n = nullptr;
   // state flags and last diagnostics
   bool keys_valid[3] = {false, false, false};
