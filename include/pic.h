@@ -141,8 +141,13 @@ int pic_get_particles(pic_t *h, int species, float *x, float *y, float *z, float
 /* Step counter (keys the random draws) and the next id to hand out. */
 int pic_set_clock(pic_t *h, int64_t step, int64_t next_id);
 
-/* Node arrays are (nz+1)*(ny+1)*(nx+1), index (k*(ny+1)+j)*(nx+1)+i. */
-int pic_set_potential(pic_t *h, const double *phi); /* also recomputes the node field */
+/* Node arrays are (nz+1)*(ny+1)*(nx+1), index (k*(ny+1)+j)*(nx+1)+i.
+ * The library holds the potential in fixed point, steps of 2^-40 V (~9.1e-13 V), so that the
+ * Poisson stencil and the node differences of E are exact integer sums; pic_set_potential rounds
+ * each value to that grid (half to even) and recomputes the node field; it returns PIC_E_INVALID
+ * for a value that is not finite or not inside (-8192, 8192) V.  pic_get_potential returns the
+ * held values exactly. */
+int pic_set_potential(pic_t *h, const double *phi);
 int pic_get_potential(pic_t *h, double *phi);
 int pic_get_efield(pic_t *h, float *E);   /* 3 floats (Ex,Ey,Ez) [V/m] per node */
 int pic_get_charge(pic_t *h, int64_t *Q); /* deposited charge, units e*w_min*2^-30 */

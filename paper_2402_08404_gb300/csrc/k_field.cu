@@ -11,8 +11,8 @@
 // prolongation, a one-block smoother on the coarsest level.  Coarse Dirichlet masks are
 // injected from the fine nodes they coincide with.
 //
-// Layout: phi, the right-hand side, E and the fixed-point charge are node arrays in natural
-// order.  The V-cycle levels keep their two colours apart: node (i, j, k) of colour
+// Layout: phi (fixed point, 2^-40 V), the right-hand side, E and the fixed-point charge are
+// node arrays in natural order.  The V-cycle levels keep their two colours apart: node (i, j, k) of colour
 // c = (i + j + k) & 1 lives at c * nper + ((k (ny + 1) + j) Xh + (i >> 1)), Xh = (nx + 2) / 2.
 // A colour sweep then reads the other colour and writes its own as contiguous rows, and its
 // 6 neighbours of (i, j, k) sit at slots (i -+ 1) >> 1 of its own row and i >> 1 of the four
@@ -235,26 +235,37 @@ __global__ void k_split_mask(const uint8_t *dir, uint8_t *dirs, Lv L) {
 }
 
 // ---- fine level <-> FP64 refinement ---------------------------------------------------------------
-// rho/eps0 from the fixed-point charge; Dirichlet values on the mask
-__global__ void k_rhs(const unsigned long long *Q, double *f, double *phi, const uint8_t *dir, int nx, int ny, int nz,
-                      double unit, double V0, int zero_charge) {
+// rho/eps0 from the fixed-point charge; Dirichlet values on the mask (V0 in fixed point)
+__global__ void k_rhs(const unsigned long long *Q, double *f, long long *phi, const uint8_t *dir, int nx, int ny, int nz,
+                      double unit, long long V0fx, int zero_charge) {
   NODE_IJK(nx, ny)
-  // 1/V_n relative to dx^3: 2 per lateral wall the node lies on (exact powers of two)
-  const double inv_vol = (i == 0 || i == nx ? 2.0 : 1.0) * (j == 0 || j == ny ? 2.0 : 1.0);
-  f[n] = zero_charge ? 0.0 : (double)(long long)Q[n] * unit * inv_vol;
-  if (dir[n]) phi[n] = k == nz ? V0 : 0.0;
+  // 1/V_n relative to dx^3: 2 per lateral wall the node lies on; a power of two, so folding it
+  // into the unit leaves the one rounding of Q unit unchanged
+  const double ku = unit * (i == 0 || i == nx ? 2.0 : 1.0) * (j == 0 || j == ny ? 2.0 : 1.0);
+  f[n] = zero_charge ? 0.0 : (double)(long long)Q[n] * ku;
+  if (dir[n]) phi[n] = k == nz ? V0fx : 0;
 }
 
 // Residual of the FP64 system r = f - A phi, handed straight to the finest V-cycle level as its
 // right-hand side (rounded to the level's type T, split-colour layout) with a zero initial
-// correction.  The squared norms of h^2 r and of h^2 times the lifted right-hand side (f - A
-// phi_D: only the plane below the anode carries a nonzero Dirichlet term) are accumulated in
-// FP32 -- they only decide convergence -- so the FP64 pipe (1/64 of the FP32 rate on this
-// part) runs just the stencil.  3D launch with blocks (32, 8); block partials land at the
-// block's linear id.
+// correction.  The stencil 6 phi_n - sum of neighbours is an exact int64 sum of fixed-point
+// values; one FMA turns it into r (c = 2^-40 / h^2).  The squared norms of h^2 r and of h^2
+// times the lifted right-hand side (f - A phi_D: only the plane below the anode carries a
+// nonzero Dirichlet term) are accumulated in FP32 -- they only decide convergence -- so the
+// FP64 pipe (1/64 of the FP32 rate on this part) runs three operations per node.  3D launch
+// with blocks (32, 8); block partials land at the block's linear id.
+__device__ __forceinline__ long long nb_sum_fx(const long long *u, int i, int j, int k, int nx, int ny) {
+  const int im = i > 0 ? i - 1 : 1, ip = i < nx ? i + 1 : nx - 1;
+  const int jm = j > 0 ? j - 1 : 1, jp = j < ny ? j + 1 : ny - 1;
+  const int64_t sy = nx + 1, sz = (int64_t)(nx + 1) * (ny + 1);
+  const int64_t c = (int64_t)k * sz + (int64_t)j * sy;
+  return u[c + im] + u[c + ip] + u[(int64_t)k * sz + (int64_t)jm * sy + i] + u[(int64_t)k * sz + (int64_t)jp * sy + i] +
+         u[c - sz + i] + u[c + sz + i];
+}
+
 template <typename T>
-__global__ void k_residual64(const double *phi, const double *f, T *fl, T *ul, const uint8_t *dir, Lv L,
-                             double inv_h2, float h2f, float V0f, double *part, int lift) {
+__global__ void k_residual64(const long long *phi, const double *f, T *fl, T *ul, const uint8_t *dir, Lv L,
+                             double c_fx, float h2f, float V0f, double *part, int lift) {
   __shared__ float sh[2][8];
   const int nx = L.nx, ny = L.ny, nz = L.nz;
   const int i = blockIdx.x * 32 + threadIdx.x;
@@ -268,8 +279,8 @@ __global__ void k_residual64(const double *phi, const double *f, T *fl, T *ul, c
       fl[m] = 0;
     } else {
       const double fn = f[n];
-      const double t = fma(6.0, phi[n], -nb_sum<double>(phi, i, j, k, nx, ny));
-      const double rr = fma(-t, inv_h2, fn);
+      const long long t = 6 * phi[n] - nb_sum_fx(phi, i, j, k, nx, ny);
+      const double rr = fma(-(double)t, c_fx, fn);
       fl[m] = (T)rr;
       const float rs = (float)rr * h2f;
       s = rs * rs;
@@ -325,13 +336,17 @@ __global__ void __launch_bounds__(kSumChunks) k_sum_stage2(const double *mid, do
   if (threadIdx.x == 0) { out[0] = sa[0]; out[1] = sb[0]; }
 }
 
-// phi += e on free nodes (e in the finest level's split layout; z: plane groups of kKZ)
+// phi += e on free nodes, e (finest level, split layout) rounded to the fixed-point grid without
+// FP64 work: e 2^40 is exact in T and converts straight to int64 (z: plane groups of kKZ)
+__device__ __forceinline__ long long to_fx(float e) { return __float2ll_rn(e * 1099511627776.0f); }
+__device__ __forceinline__ long long to_fx(double e) { return __double2ll_rn(e * kPhiScale); }
+
 template <typename T>
-__global__ void k_correct(double *phi, const T *u, const uint8_t *dir, Lv L) {
+__global__ void k_correct(long long *phi, const T *u, const uint8_t *dir, Lv L) {
   const int i = blockIdx.x * 32 + threadIdx.x;
   const int j = blockIdx.y * 8 + threadIdx.y, k0 = blockIdx.z * kKZ;
   if (i > L.nx || j > L.ny) return;
-  double v[kKZ];
+  long long v[kKZ];
   bool ok[kKZ];
 #pragma unroll
   for (int q = 0; q < kKZ; ++q) {
@@ -341,7 +356,7 @@ __global__ void k_correct(double *phi, const T *u, const uint8_t *dir, Lv L) {
     if (ok[q]) {
       const int64_t n = node_index(i, j, k, L.nx, L.ny);
       ok[q] = !dir[n];
-      v[q] = phi[n] + (double)u[sidx(L, i, j, k)];
+      v[q] = phi[n] + to_fx(u[sidx(L, i, j, k)]);
     }
   }
 #pragma unroll
@@ -349,8 +364,11 @@ __global__ void k_correct(double *phi, const T *u, const uint8_t *dir, Lv L) {
     if (ok[q]) phi[node_index(i, j, k0 + q, L.nx, L.ny)] = v[q];
 }
 
-// E = -grad phi at every node, float64 differences rounded once to float32
-__global__ void k_efield(const double *phi, float4 *E, int nx, int ny, int nz, double inv2dx, double invdx) {
+// E = -grad phi at every node: the node difference rounded to f32, times f32(1/(2 dx)) (or
+// f32(1/dx) on the z planes) in f32.  The difference of two fixed-point values is an exact
+// int64; its f32 rounding equals that of the exact FP64 difference, and the 2^-40 folds into the
+// f32 factor exactly, so no FP64 operation is needed.
+__global__ void k_efield(const long long *phi, float4 *E, int nx, int ny, int nz, float c2, float c1) {
   const int64_t sy = nx + 1, sz = (int64_t)(nx + 1) * (ny + 1);
   {
     NODE_IJK(nx, ny)
@@ -358,11 +376,11 @@ __global__ void k_efield(const double *phi, float4 *E, int nx, int ny, int nz, d
     const int jm = j > 0 ? j - 1 : 1, jp = j < ny ? j + 1 : ny - 1;
     const int64_t row = (int64_t)k * sz + (int64_t)j * sy;
     float4 e;
-    e.x = __double2float_rn(__dmul_rn(__dsub_rn(phi[row + im], phi[row + ip]), inv2dx));
-    e.y = __double2float_rn(__dmul_rn(__dsub_rn(phi[(int64_t)k * sz + (int64_t)jm * sy + i], phi[(int64_t)k * sz + (int64_t)jp * sy + i]), inv2dx));
-    if (k == 0) e.z = __double2float_rn(__dmul_rn(__dsub_rn(phi[n], phi[n + sz]), invdx));
-    else if (k == nz) e.z = __double2float_rn(__dmul_rn(__dsub_rn(phi[n - sz], phi[n]), invdx));
-    else e.z = __double2float_rn(__dmul_rn(__dsub_rn(phi[n - sz], phi[n + sz]), inv2dx));
+    e.x = __fmul_rn(__ll2float_rn(phi[row + im] - phi[row + ip]), c2);
+    e.y = __fmul_rn(__ll2float_rn(phi[(int64_t)k * sz + (int64_t)jm * sy + i] - phi[(int64_t)k * sz + (int64_t)jp * sy + i]), c2);
+    if (k == 0) e.z = __fmul_rn(__ll2float_rn(phi[n] - phi[n + sz]), c1);
+    else if (k == nz) e.z = __fmul_rn(__ll2float_rn(phi[n - sz] - phi[n]), c1);
+    else e.z = __fmul_rn(__ll2float_rn(phi[n - sz] - phi[n + sz]), c2);
     e.w = 0.f;
     E[n] = e;
   }
@@ -427,8 +445,9 @@ static void cycle_fine(pic_t *h) {
 
 int stage_efield(pic_t *h) {
   ++h->nlaunch;
-  k_efield<<<node_grid3(h->nx, h->ny, h->nz), node_block(), 0, h->stream>>>(h->phi, h->E, h->nx, h->ny, h->nz,
-                                                                            1.0 / (2.0 * h->dx), 1.0 / h->dx);
+  // f32(1/(2 dx)) 2^-40 and f32(1/dx) 2^-40: rounding then scaling by a power of two
+  const float c2 = (float)(1.0 / (2.0 * h->dx)) * (float)kPhiUnit, c1 = (float)(1.0 / h->dx) * (float)kPhiUnit;
+  k_efield<<<node_grid3(h->nx, h->ny, h->nz), node_block(), 0, h->stream>>>(h->phi, h->E, h->nx, h->ny, h->nz, c2, c1);
   return launch_check(h, "efield");
 }
 
@@ -454,11 +473,12 @@ int stage_solve(pic_t *h, bool zero_charge, double V0) {
   const Lv lv = lv_of(L);
   const double unit = kQe * h->prm.w_min / 1073741824.0 / (h->dx * h->dx * h->dx) / kEps0;
   ++h->nlaunch;
+  const long long V0fx = llrint(V0 * kPhiScale);
   k_rhs<<<node_grid3(h->nx, h->ny, h->nz), node_block(), 0, h->stream>>>(h->Q, h->rhs, h->phi, L.dir, h->nx, h->ny, h->nz,
-                                                                         unit, V0, zero_charge ? 1 : 0);
+                                                                         unit, V0fx, zero_charge ? 1 : 0);
   const dim3 rg = node_grid3(h->nx, h->ny, h->nz);
   const int64_t nb = (int64_t)rg.x * rg.y * rg.z;
-  const double inv_h2 = 1.0 / (h->dx * h->dx);
+  const double inv_h2 = 1.0 / (h->dx * h->dx), c_fx = inv_h2 * kPhiUnit;
   const bool mixed = (h->prm.flags & PIC_F_MIXED_MG) != 0;
   double norms[2] = {0, 0};
   double lifted = 0.0;
@@ -467,10 +487,10 @@ int stage_solve(pic_t *h, bool zero_charge, double V0) {
   for (;; ++cyc) {
     ++h->nlaunch;
     if (mixed)
-      k_residual64<float><<<rg, node_block(), 0, h->stream>>>(h->phi, h->rhs, L.f, L.u, L.dir, lv, inv_h2, h2f, V0f,
+      k_residual64<float><<<rg, node_block(), 0, h->stream>>>(h->phi, h->rhs, L.f, L.u, L.dir, lv, c_fx, h2f, V0f,
                                                               h->red, cyc == 0 ? 1 : 0);
     else
-      k_residual64<double><<<rg, node_block(), 0, h->stream>>>(h->phi, h->rhs, L.fd, L.ud, L.dir, lv, inv_h2, h2f,
+      k_residual64<double><<<rg, node_block(), 0, h->stream>>>(h->phi, h->rhs, L.fd, L.ud, L.dir, lv, c_fx, h2f,
                                                                V0f, h->red, cyc == 0 ? 1 : 0);
     h->nlaunch += 2;
     k_sum_stage1<<<kSumChunks, 256, 0, h->stream>>>(h->red, nb, h->red_mid);

@@ -43,7 +43,7 @@ __device__ __forceinline__ void face_point(const FaceGeom &g, float ua, float ub
 }
 
 // F_f = mean over the 4 corners of (phi one dx outward - phi at the corner) / dx
-__global__ void k_face_field(const int32_t *vcell, const int8_t *dir, int64_t nface, const double *phi, int nx,
+__global__ void k_face_field(const int32_t *vcell, const int8_t *dir, int64_t nface, const long long *phi, int nx,
                              int ny, double dx, double *F) {
   for (int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; f < nface; f += (int64_t)gridDim.x * blockDim.x) {
     const FaceGeom g = face_geom(vcell[f], dir[f], nx, ny);
@@ -56,7 +56,9 @@ __global__ void k_face_field(const int32_t *vcell, const int8_t *dir, int64_t nf
         c[g.t1] = g.ijk[g.t1] + b;
         int o[3] = {c[0], c[1], c[2]};
         o[g.axis] = g.plane + g.sign;
-        acc = __dadd_rn(acc, __dsub_rn(phi[node_index(o[0], o[1], o[2], nx, ny)], phi[node_index(c[0], c[1], c[2], nx, ny)]));
+        // the FP64 difference of two fixed-point values, exactly
+        const long long d = phi[node_index(o[0], o[1], o[2], nx, ny)] - phi[node_index(c[0], c[1], c[2], nx, ny)];
+        acc = __dadd_rn(acc, (double)d * kPhiUnit);
       }
     F[f] = acc / 4.0 / dx;
   }

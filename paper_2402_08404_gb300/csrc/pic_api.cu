@@ -31,6 +31,18 @@ void *dalloc(pic_t *h, size_t bytes) {
   return p;
 }
 
+// give back one allocation made by dalloc (stream-ordered when the caller's allocator is)
+void dfree(pic_t *h, void *p) {
+  if (!p) return;
+  for (size_t i = 0; i < h->allocations.size(); ++i)
+    if (h->allocations[i].first == p) {
+      if (h->free_fn) h->free_fn(p, h->allocations[i].second, (void *)h->stream, h->alloc_user);
+      else cudaFree(p);
+      h->allocations.erase(h->allocations.begin() + i);
+      return;
+    }
+}
+
 static void dfree_all(pic_t *h) {
   for (auto &a : h->allocations) {
     if (h->free_fn) h->free_fn(a.first, a.second, (void *)h->stream, h->alloc_user);
@@ -215,8 +227,20 @@ static int check_err(pic_t *h) {
   return PIC_OK;
 }
 
-__global__ void k_scale(double *phi, int64_t n, double s) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) phi[i] *= s;
+// phi *= s in fixed point (rounded to the nearest 2^-40 V)
+__global__ void k_scale(long long *phi, int64_t n, double s) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    phi[i] = __double2ll_rn((double)phi[i] * s);
+}
+
+__global__ void k_phi_from_double(const double *src, long long *phi, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    phi[i] = __double2ll_rn(src[i] * kPhiScale);
+}
+
+__global__ void k_phi_to_double(const long long *phi, double *dst, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = (double)phi[i] * kPhiUnit;
 }
 
 int pic_create(const pic_geometry_t *geometry, const pic_grid_t *grid, const pic_species_t *species, int nspecies,
@@ -257,7 +281,7 @@ int pic_create(const pic_geometry_t *geometry, const pic_grid_t *grid, const pic
   // grids
   h->solid = alloc_n<uint8_t>(h, h->ncell); A(h->solid);
   h->cheb = alloc_n<uint8_t>(h, h->ncell); A(h->cheb);
-  h->phi = alloc_n<double>(h, h->nnode); A(h->phi);
+  h->phi = alloc_n<long long>(h, h->nnode); A(h->phi);
   h->rhs = alloc_n<double>(h, h->nnode); A(h->rhs);
   h->E = alloc_n<float4>(h, h->nnode); A(h->E);
   h->Q = alloc_n<unsigned long long>(h, h->nnode); A(h->Q);
@@ -388,12 +412,19 @@ int pic_create(const pic_geometry_t *geometry, const pic_grid_t *grid, const pic
   if (cudaMemsetAsync(h->Q, 0, h->nnode * 8, st) != cudaSuccess) rc = PIC_E_CUDA;
   if (rc != PIC_OK) return fail(rc, "memset failed");
   if (mg_build_masks(h) != PIC_OK || emission_tables_upload(h) != PIC_OK) return fail(PIC_E_CUDA, "setup failed");
-  // V0: calibrate from the apex field by a Laplace solve at V0 = 1 (phi is linear in V0)
+  // V0: calibrate from the apex field by a Laplace solve at a reference V_ref (phi is linear in
+  // V0).  V_ref = 1024 V (a power of two, so the rescaling is exact up to the fixed-point
+  // rounding) keeps the 2^-40 V steps of phi ~1e-15 of the solution.
+  constexpr double kVref = 1024.0;
+  if (h->prm.V0 >= kPhiMax) {
+    pic_destroy(h);
+    return PIC_E_INVALID;   // the fixed-point potential holds |phi| < 8192 V
+  }
   if (h->prm.V0 > 0) {
     h->V0 = h->prm.V0;
     rc = stage_solve(h, true, h->V0);
   } else {
-    rc = stage_solve(h, true, 1.0);
+    rc = stage_solve(h, true, kVref);
     if (rc == PIC_OK) rc = stage_face_field(h);
     double F1 = 0.0;
     if (rc == PIC_OK && !G.apex.empty()) {
@@ -405,8 +436,11 @@ int pic_create(const pic_geometry_t *geometry, const pic_grid_t *grid, const pic
       F1 /= (double)G.apex.size();
     }
     if (rc == PIC_OK) {
-      h->V0 = (F1 > 0 && h->prm.apex_field > 0) ? h->prm.apex_field / F1 : 1.0;
-      k_scale<<<grid_for(h->nnode), kThreads, 0, st>>>(h->phi, h->nnode, h->V0);
+      h->V0 = (F1 > 0 && h->prm.apex_field > 0) ? h->prm.apex_field / F1 * kVref : kVref;
+      if (!(h->V0 < kPhiMax)) rc = pic_fail(h, PIC_E_INVALID, "calibrated V0 is not below 8192 V");
+    }
+    if (rc == PIC_OK) {
+      k_scale<<<grid_for(h->nnode), kThreads, 0, st>>>(h->phi, h->nnode, h->V0 / kVref);
       rc = stage_efield(h);
     }
   }
@@ -487,10 +521,20 @@ int pic_get_particles(pic_t *h, int s, float *x, float *y, float *z, float *vx, 
 
 int pic_set_potential(pic_t *h, const double *phi) {
   if (!h || !phi) return PIC_E_INVALID;
-  PIC_CUDA(h, cudaMemcpyAsync(h->phi, phi, h->nnode * 8, cudaMemcpyHostToDevice, h->stream));
-  PIC_TRY(stage_efield(h));
-  PIC_CUDA(h, cudaStreamSynchronize(h->stream));
-  return PIC_OK;
+  for (int64_t i = 0; i < h->nnode; ++i)
+    if (!(fabs(phi[i]) < kPhiMax)) return pic_fail(h, PIC_E_INVALID, "potential outside (-8192, 8192) V or not finite");
+  double *buf = (double *)dalloc(h, (size_t)h->nnode * 8);
+  if (!buf) return pic_fail(h, PIC_E_CUDA, "staging allocation failed");
+  int rc = PIC_OK;
+  if (cudaMemcpyAsync(buf, phi, h->nnode * 8, cudaMemcpyHostToDevice, h->stream) != cudaSuccess) rc = PIC_E_CUDA;
+  if (rc == PIC_OK) {
+    ++h->nlaunch;
+    k_phi_from_double<<<grid_for(h->nnode), kThreads, 0, h->stream>>>(buf, h->phi, h->nnode);
+    rc = stage_efield(h);
+  }
+  if (rc == PIC_OK && cudaStreamSynchronize(h->stream) != cudaSuccess) rc = PIC_E_CUDA;
+  dfree(h, buf);
+  return rc == PIC_OK ? PIC_OK : pic_fail(h, rc, "set_potential failed");
 }
 
 static int d2h(pic_t *h, void *dst, const void *src, size_t bytes) {
@@ -500,7 +544,16 @@ static int d2h(pic_t *h, void *dst, const void *src, size_t bytes) {
   return PIC_OK;
 }
 
-int pic_get_potential(pic_t *h, double *phi) { return h ? d2h(h, phi, h->phi, h->nnode * 8) : PIC_E_INVALID; }
+int pic_get_potential(pic_t *h, double *phi) {
+  if (!h) return PIC_E_INVALID;
+  double *buf = (double *)dalloc(h, (size_t)h->nnode * 8);
+  if (!buf) return pic_fail(h, PIC_E_CUDA, "staging allocation failed");
+  ++h->nlaunch;
+  k_phi_to_double<<<grid_for(h->nnode), kThreads, 0, h->stream>>>(h->phi, buf, h->nnode);
+  const int rc = d2h(h, phi, buf, h->nnode * 8);
+  dfree(h, buf);
+  return rc;
+}
 int pic_get_charge(pic_t *h, int64_t *Q) { return h ? d2h(h, Q, h->Q, h->nnode * 8) : PIC_E_INVALID; }
 
 int pic_get_efield(pic_t *h, float *E) {

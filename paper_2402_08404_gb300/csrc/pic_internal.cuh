@@ -31,6 +31,14 @@ constexpr uint32_t kDead = 0xFFFFFFFFu;
 constexpr int kFracBits = 10;         // CIC fixed-point fraction bits per axis
 constexpr int kSputBits = 24;         // sputter accumulator: atoms * 2^24
 constexpr int kEnergyBits = 20;       // energy accumulators: eV * 2^20
+// The potential is held in fixed point, phi [V] = n 2^-40 (int64 n): the 7-point stencil of the
+// FP64 refinement and the node differences of E are then exact integer sums, and on this part
+// integer adds run at 32x the FP64 rate.  |phi| < 2^13 V keeps n within the 53-bit mantissa, so
+// every value and every difference converts to FP64 exactly.
+constexpr int kPhiShift = 40;
+constexpr double kPhiScale = 1099511627776.0;                  // 2^40
+constexpr double kPhiUnit = 1.0 / 1099511627776.0;             // 2^-40
+constexpr double kPhiMax = 8192.0;                             // |phi| bound [V]
 constexpr int kMaxSegment = 8192;     // SPs of one species in one cell (sort fix-up limit)
 constexpr int kLongCap = 1 << 16;     // queued long segments per sort pass
 // emission surrogate output decoding: log10 J = approx_log10J + y0 kSurY0s (floor
@@ -137,7 +145,7 @@ struct pic_s {
   // device state
   uint8_t *solid = nullptr;      // per cell
   uint8_t *cheb = nullptr;       // per cell: Chebyshev distance to the nearest solid cell (capped)
-  double *phi = nullptr;         // per node
+  long long *phi = nullptr;      // per node, fixed point: phi [V] = phi * 2^-kPhiShift
   double *rhs = nullptr;         // per node: rho/eps0 (FP64)
   float4 *E = nullptr;           // per node
   unsigned long long *Q = nullptr;  // per node, int64 two's complement charge
@@ -245,6 +253,7 @@ int pic_fail(pic_t *h, int code, const std::string &msg);
 // ---- stage entry points implemented in the kernel files --------------------------------------
 namespace pic {
 void *dalloc(pic_t *h, size_t bytes);
+void dfree(pic_t *h, void *p);
 int launch_check(pic_t *h, const char *what);
 
 // scans (k_scan.cu): exclusive scans of n values; n either a host size or a device int64

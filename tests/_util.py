@@ -15,6 +15,12 @@ def small_cfg(**kw):
     return cfg
 
 
+def fixed_phi(phi):
+    """The potential on the library's fixed-point grid (steps of 2^-40 V, round half to even):
+    tests that compare integer or bit-exact results hand both sides these representable values."""
+    return np.round(np.asarray(phi, dtype=np.float64) * 2.0 ** 40) / 2.0 ** 40
+
+
 def grid_of(cfg):
     return Grid(cfg["nx"], cfg["ny"], cfg["nz"], cfg["dx"], cfg["tip_radius"], cfg["tip_height"])
 

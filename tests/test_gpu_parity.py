@@ -13,7 +13,7 @@ from oracle import collide, emission as em, field, heat, particles as P, step as
 from oracle import constants as OC
 from paper_2402_08404_gb300 import synth
 
-from _util import SPECIES, assert_sp_equal, grid_of, oracle_push_sort, small_cfg, sorted_pop
+from _util import SPECIES, assert_sp_equal, fixed_phi, grid_of, oracle_push_sort, small_cfg, sorted_pop
 
 pytestmark = pytest.mark.gpu
 
@@ -63,7 +63,7 @@ def test_efield_bit_exact(pic):
     cfg = small_cfg()
     g = grid_of(cfg)
     sim = make(pic, cfg, cap=16, V0=50.0)
-    phi = field.solve_poisson(g, 50.0) + synth.potential_noise((g.nz + 1, g.ny + 1, g.nx + 1), 0.3, seed=4)
+    phi = fixed_phi(field.solve_poisson(g, 50.0) + synth.potential_noise((g.nz + 1, g.ny + 1, g.nx + 1), 0.3, seed=4))
     sim.set_potential(phi)
     assert np.array_equal(sim.get_efield(), field.efield(g, phi))
     sim.close()
@@ -74,7 +74,7 @@ def _pushed_case(pic, n_sp=20000, seed=2, V0=60.0):
     g = grid_of(cfg)
     sim = make(pic, cfg, V0=V0)
     pop = synth.plasma(cfg, seed=seed)
-    phi = field.solve_poisson(g, V0) + synth.potential_noise((g.nz + 1, g.ny + 1, g.nx + 1), 0.2, seed=seed)
+    phi = fixed_phi(field.solve_poisson(g, V0) + synth.potential_noise((g.nz + 1, g.ny + 1, g.nx + 1), 0.2, seed=seed))
     sim.set_potential(phi)
     load(sim, pop)
     sim.set_clock(3, n_sp)
@@ -148,7 +148,7 @@ def test_collisions_match_oracle(pic):
     u /= np.linalg.norm(u, axis=1)[:, None]
     for a, c in enumerate(("vx", "vy", "vz")):
         pop["e"][c] = (speed * u[:, a]).astype(np.float32)
-    phi = field.solve_poisson(g, V0)
+    phi = fixed_phi(field.solve_poisson(g, V0))
     sim.set_potential(phi)
     load(sim, pop)
     sim.set_clock(3, n_sp)
@@ -220,7 +220,7 @@ def _emit_case(pic, T_tip):
     V0 = field.calibrate_V0(g, cfg["apex_field"])
     sim = make(pic, cfg, V0=V0)
     pop = synth.plasma(cfg, seed=8)
-    phi = field.solve_poisson(g, V0)
+    phi = fixed_phi(field.solve_poisson(g, V0))
     sim.set_potential(phi)
     load(sim, pop)
     sim.set_clock(7, cfg["n_sp"])
