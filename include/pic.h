@@ -185,6 +185,21 @@ int pic_heat(pic_t *h);        /* a10 continuity + heat on the tip cells from th
 int pic_step(pic_t *h, int nsteps);
 int pic_diagnostics(pic_t *h, pic_diag_t *out);
 
+/* Kernel timing (diagnostics of the library; the paper has no counterpart).  pic_num_kernels()
+ * kernels are known by index (pic_kernel_name: "k_push", "k_smooth", ...).  pic_set_kernel_timing
+ * selects kernels by bit mask (bit k = kernel k, 0 = none) and clears the sums; from then on every
+ * launch of a selected kernel is bracketed by a pair of CUDA events on the library stream.
+ * pic_get_kernel_timing synchronises the stream and returns, for kernel k, the launches timed,
+ * their summed duration [ms] and their summed work units (nodes of the level a grid kernel
+ * covers -- the swept colour's slots for k_smooth and k_smooth_first, colour-0 slots for
+ * k_residual --, faces for face kernels, 0 for particle kernels, whose counts stay on the
+ * device).  PIC_E_INVALID for a bad index.  Timing costs two event records per launch; keep the
+ * mask 0 outside measurements. */
+int pic_num_kernels(void);
+const char *pic_kernel_name(int k);
+int pic_set_kernel_timing(pic_t *h, uint64_t mask);
+int pic_get_kernel_timing(pic_t *h, int k, int64_t *launches, double *ms, double *units);
+
 /* Emission current density and Nottingham heat of n surface states (host arrays): F [V/m],
  * T [K], work function [eV], radius of curvature [m] (<= 0 or inf: flat); J [A/m^2], PN [W/m^2].
  * Evaluates the full FP64 thermal-field integral on the device (Sec. 2.3.1). */

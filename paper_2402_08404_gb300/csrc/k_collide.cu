@@ -303,14 +303,14 @@ int stage_collide(pic_t *h) {
     a.V_cell = h->dx * h->dx * h->dx; a.dt = h->prm.dt; a.w_min = h->prm.w_min; a.seed = h->prm.seed;
     a.clk = h->clock; a.pair_cnt = h->pair_cnt; a.pair_off = h->pair_off; a.pair_ncoll = h->pair_ncoll; a.go = go;
     ++h->nlaunch;
-    k_mcc_count<<<grid, kThreads, 0, h->stream>>>(a);
+    { KtScope kt_(h, kidMccCount, 0); k_mcc_count<<<grid, kThreads, 0, h->stream>>>(a); }
     ++h->nlaunch;
     k_set_len<<<1, 1, 0, h->stream>>>(h->tmp_len, h->clock, 0);
     PIC_TRY(scan_u64(h, h->pair_cnt, h->pair_off, 0, h->tmp_len, total));
     ++h->nlaunch;
     k_check_new<<<1, 1, 0, h->stream>>>(h->clock, total, h->sp[PIC_ION].cap, h->sp[PIC_ELECTRON].cap, go);
     ++h->nlaunch;
-    k_mcc_products<<<grid, kThreads, 0, h->stream>>>(a, h->sp[PIC_ION].a);
+    { KtScope kt_(h, kidMccProducts, 0); k_mcc_products<<<grid, kThreads, 0, h->stream>>>(a, h->sp[PIC_ION].a); }
     ++h->nlaunch;
     k_commit_new<<<1, 1, 0, h->stream>>>(h->clock, total, go, cImpactIon);
     PIC_TRY(launch_check(h, "mcc"));
@@ -327,14 +327,14 @@ int stage_collide(pic_t *h) {
     d.dt_fs = h->prm.dt * 1e15; d.seed = h->prm.seed; d.clk = h->clock;
     d.cnt = h->pair_cnt; d.off = h->pair_off; d.nion = h->pair_ncoll; d.go = go;
     ++h->nlaunch;
-    k_dfi_count<<<grid, kThreads, 0, h->stream>>>(d);
+    { KtScope kt_(h, kidDfiCount, 0); k_dfi_count<<<grid, kThreads, 0, h->stream>>>(d); }
     ++h->nlaunch;
     k_set_len<<<1, 1, 0, h->stream>>>(h->tmp_len, h->clock, 1);
     PIC_TRY(scan_u64(h, h->pair_cnt, h->pair_off, 0, h->tmp_len, total));
     ++h->nlaunch;
     k_check_new<<<1, 1, 0, h->stream>>>(h->clock, total, h->sp[PIC_ION].cap, h->sp[PIC_ELECTRON].cap, go);
     ++h->nlaunch;
-    k_dfi_products<<<grid, kThreads, 0, h->stream>>>(d);
+    { KtScope kt_(h, kidDfiProducts, 0); k_dfi_products<<<grid, kThreads, 0, h->stream>>>(d); }
     ++h->nlaunch;
     k_commit_new<<<1, 1, 0, h->stream>>>(h->clock, total, go, cFieldIon);
     PIC_TRY(launch_check(h, "dfi"));

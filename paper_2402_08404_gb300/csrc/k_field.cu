@@ -5,23 +5,30 @@
 // every corner of a solid cell.  Charge density rho_n = Q_n e w_min 2^-30 / V_n with V_n = dx^3
 // halved on each lateral wall the node lies on.
 //
-// Solve: refinement loop in float64 -- r = f - A phi, stop when ||r||/||f_lifted|| < tol, else
-// one V-cycle on A e = r and phi += e.  The V-cycle runs in float32 (mixed form) or float64
-// (plain form): red-black Gauss-Seidel 2+2 sweeps, full-weighting restriction, trilinear
-// prolongation, a one-block smoother on the coarsest level.  Coarse Dirichlet masks are
-// injected from the fine nodes they coincide with.
+// Solve: refinement loop on the fixed-point potential -- t = h^2 (f - A phi) formed exactly in
+// int64 (charge term Q K rounded once, see charge_fx), stop when ||r||/||f_lifted|| < tol, else
+// one V-cycle on A e = r and phi += e rounded to the fixed-point grid.  The V-cycle runs in
+// float32 (mixed form) or float64 (plain form): red-black Gauss-Seidel 2+2 sweeps, full-
+// weighting restriction, trilinear prolongation, and a direct solve on the coarsest level (its
+// inverse operator built at creation).  Coarse Dirichlet masks are injected from the fine nodes
+// they coincide with.
 //
-// Layout: phi (fixed point, 2^-40 V), the right-hand side, E and the fixed-point charge are
-// node arrays in natural order.  The V-cycle levels keep their two colours apart: node (i, j, k) of colour
+// Layout: phi (fixed point, 2^-40 V), E and the fixed-point charge are node arrays in natural
+// order.  The V-cycle levels keep their two colours apart: node (i, j, k) of colour
 // c = (i + j + k) & 1 lives at c * nper + ((k (ny + 1) + j) Xh + (i >> 1)), Xh = (nx + 2) / 2.
 // A colour sweep then reads the other colour and writes its own as contiguous rows, and its
 // 6 neighbours of (i, j, k) sit at slots (i -+ 1) >> 1 of its own row and i >> 1 of the four
 // rows around it, all in the other colour.
+#include <math.h>
+
+#include <algorithm>
+#include <vector>
+
 #include "pic_internal.cuh"
 
 namespace pic {
 
-// ---- natural-order helpers (phi, rhs) ---------------------------------------------------------
+// ---- natural-order helpers ---------------------------------------------------------
 template <typename T>
 __device__ __forceinline__ T nb_sum(const T *u, int i, int j, int k, int nx, int ny) {
   const int im = i > 0 ? i - 1 : 1, ip = i < nx ? i + 1 : nx - 1;
@@ -42,12 +49,31 @@ inline dim3 node_grid3(int nx, int ny, int nz) { return dim3((nx + 1 + 31) / 32,
   const int64_t n = node_index(i, j, k, nx, ny);
 
 // ---- split-colour level geometry -------------------------------------------------------------
+// Division by a fixed divisor d < 2^31 for numerators < 2^32: q = (umulhi(n, m) + n) >> s with
+// s = ceil(log2 d), m = floor(2^32 (2^s - d) / d) + 1 (round-up reciprocal).
+struct FastDiv {
+  uint32_t m, s;
+};
+inline FastDiv make_fastdiv(uint32_t d) {
+  FastDiv f{0, 0};
+  while ((1ull << f.s) < d) ++f.s;
+  f.m = (uint32_t)(((1ull << 32) * ((1ull << f.s) - d)) / d + 1);
+  return f;
+}
+__device__ __forceinline__ uint32_t fdiv(uint32_t n, FastDiv f) {
+  return (uint32_t)(((uint64_t)__umulhi(n, f.m) + n) >> f.s);
+}
+
 struct Lv {
   int nx, ny, nz, Xh;
   int64_t nper;
+  uint32_t P;    // slots per plane and colour, (ny + 1) Xh
+  FastDiv xd;    // division by Xh
 };
 
-inline Lv lv_of(const MgLevel &L) { return Lv{L.nx, L.ny, L.nz, L.Xh, L.nper}; }
+inline Lv lv_of(const MgLevel &L) {
+  return Lv{L.nx, L.ny, L.nz, L.Xh, L.nper, (uint32_t)((L.ny + 1) * L.Xh), make_fastdiv((uint32_t)L.Xh)};
+}
 
 __host__ __device__ __forceinline__ int64_t srow(const Lv &L, int j, int k) {
   return ((int64_t)k * (L.ny + 1) + j) * L.Xh;
@@ -61,9 +87,12 @@ __host__ __device__ __forceinline__ int64_t sidx(const Lv &L, int i, int j, int 
 // planes per thread in the level sweeps
 constexpr int kKZ = 4;
 
-// slot grid: x over slots (32), y over j (8), z over groups of kKZ planes (x colours)
-inline dim3 slot_grid(const Lv &L, int colours) {
-  return dim3((L.Xh + 31) / 32, (L.ny + 1 + 7) / 8, ((L.nz + kKZ) / kKZ) * colours);
+// Level kernels index the slots of a plane flat (x: blocks of kSlotThreads slots, so no row
+// tail leaves a warp mostly idle) and take kKZ planes per thread (y: plane groups x colours);
+// j and t come from one division by Xh.
+constexpr int kSlotThreads = 256;
+inline dim3 flat_grid(const Lv &L, int colours, int planes_per_thread) {
+  return dim3((L.P + kSlotThreads - 1) / kSlotThreads, ((L.nz + planes_per_thread) / planes_per_thread) * colours, 1);
 }
 
 // sum of the 6 neighbours of colour-c node i in row (j, k), read from the other colour uo
@@ -76,127 +105,165 @@ __device__ __forceinline__ T nb_sum_s(const T *uo, const Lv &L, int i, int t, in
          uo[srow(L, j, k - 1) + t] + uo[srow(L, j, k + 1) + t];
 }
 
-// The fine-level sweeps are bound by memory latency, not bandwidth, when a thread waits for its
-// mask before loading the stencil: each thread therefore takes kKZ planes (k0 .. k0 + kKZ - 1)
-// and issues every load of all of them (mask, right-hand side, neighbours) before the first
-// store.  Within one colour pass no value read is written, so the order is free.
-
-// one colour of red-black Gauss-Seidel on A u = f (grid z: plane groups of kKZ)
-template <typename T>
-__global__ void k_smooth(T *u, const T *f, const uint8_t *dirs, Lv L, T h2, int c) {
-  const int t = blockIdx.x * 32 + threadIdx.x;
-  const int j = blockIdx.y * 8 + threadIdx.y, k0 = blockIdx.z * kKZ;
-  if (t >= L.Xh || j > L.ny) return;
+// One colour of red-black Gauss-Seidel on A u = f.  Each thread takes slot q of kKZ planes and
+// issues every load of all of them (right-hand side, mask, the six neighbours of the other
+// colour) before its first store: nothing read in a colour pass is written in it, and every
+// address is inside the level (mirrored at the lateral walls, unused slots clamp into the row),
+// so the loads need not wait for the mask.  first = 1: the other colour is taken as zero (the
+// first sweep after a new right-hand side), so the correction needs no clearing pass; Dirichlet
+// slots of u hold 0 from creation and are never written.
+template <typename T, bool first>
+__global__ void __launch_bounds__(kSlotThreads) k_smooth(T *u, const T *f, const uint8_t *dirs, Lv L, T h2, int c) {
+  const uint32_t q = blockIdx.x * kSlotThreads + threadIdx.x;
+  if (q >= L.P) return;
+  const int j = (int)fdiv(q, L.xd), t = (int)(q - (uint32_t)j * (uint32_t)L.Xh);
+  const int k0 = blockIdx.y * kKZ;
   const T *uo = u + (int64_t)(c ^ 1) * L.nper;
+  T *uc = u + (int64_t)c * L.nper;
+  const T *fc = f + (int64_t)c * L.nper;
+  const uint8_t *dc = dirs + (int64_t)c * L.nper;
+  const int64_t ojm = j > 0 ? -(int64_t)L.Xh : (int64_t)L.Xh, ojp = j < L.ny ? (int64_t)L.Xh : -(int64_t)L.Xh;
   T v[kKZ];
-  int64_t m[kKZ];
-  bool ok[kKZ];
+  uint8_t d[kKZ];
 #pragma unroll
-  for (int q = 0; q < kKZ; ++q) {
-    const int k = k0 + q;
-    const int i = 2 * t + ((j + k + c) & 1);
-    ok[q] = k > 0 && k < L.nz && i <= L.nx;   // the k = 0 and k = nz planes are Dirichlet
-    m[q] = (int64_t)c * L.nper + srow(L, j, k) + t;
-    v[q] = 0;
-    if (ok[q]) {
-      ok[q] = !dirs[m[q]];
-      v[q] = nb_sum_s<T>(uo, L, i, t, j, k) + h2 * f[m[q]];
+  for (int p = 0; p < kKZ; ++p) {
+    const int k = k0 + p;
+    v[p] = 0;
+    d[p] = 1;
+    if (k > 0 && k < L.nz) {   // the k = 0 and k = nz planes are Dirichlet
+      const int64_t m = (int64_t)k * L.P + q;
+      const int i = 2 * t + ((j + k + c) & 1);
+      d[p] = dc[m];
+      if (first) {
+        v[p] = h2 * fc[m];
+      } else {
+        const int im = i > 0 ? i - 1 : 1, ip = i < L.nx ? i + 1 : L.nx - 1;
+        const int64_t rb = m - t;
+        v[p] = uo[rb + (im >> 1)] + uo[rb + (ip >> 1)] + uo[m + ojm] + uo[m + ojp] + uo[m - L.P] + uo[m + L.P] +
+               h2 * fc[m];
+      }
     }
   }
 #pragma unroll
-  for (int q = 0; q < kKZ; ++q)
-    if (ok[q]) u[m[q]] = v[q] * (T)(1.0 / 6.0);
+  for (int p = 0; p < kKZ; ++p)
+    if (!d[p]) uc[(int64_t)(k0 + p) * L.P + q] = v[p] * (T)(1.0 / 6.0);
 }
 
-// r = f - A u at every node (grid z: plane groups of kKZ x 2 colours)
+// r = f - A u at the colour-0 nodes.  The V-cycle's last pre-smoothing sweep updates colour 1,
+// which leaves the colour-1 residual zero up to rounding (each colour-1 value solves its own row
+// of A u = f), so colour 1 is neither evaluated nor stored: k_restrict reads colour 0 only.
+// Grid y: plane groups of kKZ.
 template <typename T>
-__global__ void k_residual(const T *u, const T *f, T *r, const uint8_t *dirs, Lv L, T inv_h2) {
-  const int t = blockIdx.x * 32 + threadIdx.x;
-  const int j = blockIdx.y * 8 + threadIdx.y, k0 = (blockIdx.z >> 1) * kKZ, c = blockIdx.z & 1;
-  if (t >= L.Xh || j > L.ny) return;
-  const T *uo = u + (int64_t)(c ^ 1) * L.nper;
+__global__ void __launch_bounds__(kSlotThreads) k_residual(const T *u, const T *f, T *r, const uint8_t *dirs, Lv L,
+                                                            T inv_h2) {
+  const uint32_t q = blockIdx.x * kSlotThreads + threadIdx.x;
+  if (q >= L.P) return;
+  const int k0 = blockIdx.y * kKZ;
+  const int j = (int)fdiv(q, L.xd), t = (int)(q - (uint32_t)j * (uint32_t)L.Xh);
+  const T *uo = u + L.nper;
+  const int64_t ojm = j > 0 ? -(int64_t)L.Xh : (int64_t)L.Xh, ojp = j < L.ny ? (int64_t)L.Xh : -(int64_t)L.Xh;
   T v[kKZ];
-  int64_t m[kKZ];
-  bool ok[kKZ];
+  uint8_t d[kKZ];
 #pragma unroll
-  for (int q = 0; q < kKZ; ++q) {
-    const int k = k0 + q;
-    const int i = 2 * t + ((j + k + c) & 1);
-    ok[q] = k <= L.nz && i <= L.nx;
-    m[q] = (int64_t)c * L.nper + srow(L, j, k) + t;
-    v[q] = 0;
-    if (ok[q] && k > 0 && k < L.nz) {
-      const bool d = dirs[m[q]];
-      const T rr = f[m[q]] - (6 * u[m[q]] - nb_sum_s<T>(uo, L, i, t, j, k)) * inv_h2;
-      v[q] = d ? (T)0 : rr;
+  for (int p = 0; p < kKZ; ++p) {
+    const int k = k0 + p;
+    v[p] = 0;
+    d[p] = 1;
+    if (k > 0 && k < L.nz) {
+      const int64_t m = (int64_t)k * L.P + q;
+      const int i = 2 * t + ((j + k) & 1);
+      const int im = i > 0 ? i - 1 : 1, ip = i < L.nx ? i + 1 : L.nx - 1;
+      const int64_t rb = m - t;
+      d[p] = dirs[m];
+      const T nb = uo[rb + (im >> 1)] + uo[rb + (ip >> 1)] + uo[m + ojm] + uo[m + ojp] + uo[m - L.P] + uo[m + L.P];
+      v[p] = f[m] - (6 * u[m] - nb) * inv_h2;
     }
   }
 #pragma unroll
-  for (int q = 0; q < kKZ; ++q)
-    if (ok[q]) r[m[q]] = v[q];
+  for (int p = 0; p < kKZ; ++p)
+    if (k0 + p <= L.nz) r[(int64_t)(k0 + p) * L.P + q] = d[p] ? (T)0 : v[p];
 }
 
 __device__ __forceinline__ int mirror(int i, int n) { return i < 0 ? -i : (i > n ? 2 * n - i : i); }
 
-// full weighting of a fine residual onto the coarse right-hand side; coarse u cleared
+// Full weighting of the fine residual onto the coarse right-hand side.  The fine residual is zero
+// at colour-1 nodes (k_residual), and fine node (2I + di, 2J + dj, 2K + dk) has colour
+// (di + dj + dk) & 1 (mirroring keeps parity), so only the 13 even offsets are read: the centre
+// (weight 1/8) and the 12 with two nonzero components (1/32).  One coarse slot per thread, grid
+// y: coarse planes x 2 colours.  Coarse Dirichlet nodes (all of the K = 0 and K = nz planes
+// among them) return before any fine load.  The coarse correction needs no clearing.
 template <typename TF, typename TC>
-__global__ void k_restrict(const TF *rf, Lv Fl, TC *fc, TC *uc, const uint8_t *dirsc, Lv Cl) {
-  const int I = blockIdx.x * 32 + threadIdx.x;
-  const int J = blockIdx.y * 8 + threadIdx.y, K = blockIdx.z;
-  if (I > Cl.nx || J > Cl.ny) return;
-  const int64_t n = sidx(Cl, I, J, K);
-  uc[n] = 0;
+__global__ void __launch_bounds__(kSlotThreads) k_restrict(const TF *rf, Lv Fl, TC *fc, const uint8_t *dirsc, Lv Cl) {
+  const uint32_t q = blockIdx.x * kSlotThreads + threadIdx.x;
+  if (q >= Cl.P) return;
+  const int cc = blockIdx.y & 1, K = blockIdx.y >> 1;
+  const int J = (int)fdiv(q, Cl.xd), T = (int)(q - (uint32_t)J * (uint32_t)Cl.Xh);
+  const int I = 2 * T + ((J + K + cc) & 1);
+  if (I > Cl.nx) return;
+  const int64_t n = (int64_t)cc * Cl.nper + (int64_t)K * Cl.P + q;
   if (dirsc[n]) { fc[n] = 0; return; }
-  // accumulate in the level's precision (float in the mixed form)
-  TC s = 0;
-  for (int dk = -1; dk <= 1; ++dk) {
-    const TC wk = dk == 0 ? (TC)0.5 : (TC)0.25;
-    const int k = 2 * K + dk;
-    for (int dj = -1; dj <= 1; ++dj) {
-      const TC wj = dj == 0 ? (TC)0.5 : (TC)0.25;
-      const int j = mirror(2 * J + dj, Fl.ny);
-      TC row = 0;
-      for (int di = -1; di <= 1; ++di) {
-        const TC wi = di == 0 ? (TC)0.5 : (TC)0.25;
-        const int i = mirror(2 * I + di, Fl.nx);
-        row += wi * (TC)rf[sidx(Fl, i, j, k)];
-      }
-      s += wk * wj * row;
-    }
-  }
-  fc[n] = s;
+  const int i0 = 2 * I, j0 = 2 * J, k0 = 2 * K;
+  const int im = mirror(i0 - 1, Fl.nx), ip = mirror(i0 + 1, Fl.nx);
+  const int jm = mirror(j0 - 1, Fl.ny), jp = mirror(j0 + 1, Fl.ny);
+  // colour-0 fine values (all in the first half of the split layout)
+#define RF(i, j, k) (TC) rf[srow(Fl, (j), (k)) + ((i) >> 1)]
+  const TC ctr = RF(i0, j0, k0);
+  const TC xy = RF(im, jm, k0) + RF(ip, jm, k0) + RF(im, jp, k0) + RF(ip, jp, k0);
+  const TC xz = RF(im, j0, k0 - 1) + RF(ip, j0, k0 - 1) + RF(im, j0, k0 + 1) + RF(ip, j0, k0 + 1);
+  const TC yz = RF(i0, jm, k0 - 1) + RF(i0, jp, k0 - 1) + RF(i0, jm, k0 + 1) + RF(i0, jp, k0 + 1);
+#undef RF
+  fc[n] = (TC)0.125 * ctr + (TC)0.03125 * ((xy + xz) + yz);
 }
 
-// trilinear prolongation of the coarse correction, added on free fine nodes (fine slot grid,
-// z: plane groups of kKZ x 2 colours; all loads before the stores)
+// Trilinear prolongation of the coarse correction, added on free fine nodes (flat fine slots,
+// grid y: plane groups of kKZ x 2 colours; every load before the stores, addresses clamped into
+// the level).
 template <typename TC, typename TF>
-__global__ void k_prolong(const TC *uc, Lv Cl, TF *uf, const uint8_t *dirsf, Lv Fl) {
-  const int t = blockIdx.x * 32 + threadIdx.x;
-  const int j = blockIdx.y * 8 + threadIdx.y, kb = (blockIdx.z >> 1) * kKZ, c = blockIdx.z & 1;
-  if (t >= Fl.Xh || j > Fl.ny) return;
+__global__ void __launch_bounds__(kSlotThreads) k_prolong(const TC *uc, Lv Cl, TF *uf, const uint8_t *dirsf, Lv Fl) {
+  const uint32_t q = blockIdx.x * kSlotThreads + threadIdx.x;
+  if (q >= Fl.P) return;
+  const int c = blockIdx.y & 1, kb = (blockIdx.y >> 1) * kKZ;
+  const int j = (int)fdiv(q, Fl.xd), t = (int)(q - (uint32_t)j * (uint32_t)Fl.Xh);
+  TF *ufc = uf + (int64_t)c * Fl.nper;
+  const uint8_t *dc = dirsf + (int64_t)c * Fl.nper;
   TF v[kKZ];
-  int64_t m[kKZ];
-  bool ok[kKZ];
+  uint8_t d[kKZ];
 #pragma unroll
-  for (int q = 0; q < kKZ; ++q) {
-    const int k = kb + q;
-    const int i = 2 * t + ((j + k + c) & 1);
-    ok[q] = k > 0 && k < Fl.nz && i <= Fl.nx;
-    m[q] = (int64_t)c * Fl.nper + srow(Fl, j, k) + t;
-    v[q] = 0;
-    if (ok[q]) {
-      ok[q] = !dirsf[m[q]];
+  for (int p = 0; p < kKZ; ++p) {
+    const int k = kb + p;
+    v[p] = 0;
+    d[p] = 1;
+    if (k > 0 && k < Fl.nz) {
+      const int64_t m = (int64_t)k * Fl.P + q;
+      const int i = min(2 * t + ((j + k + c) & 1), Fl.nx);
+      d[p] = dc[m];
       const int i0 = i >> 1, j0 = j >> 1, k0 = k >> 1;
       const int i1 = i0 + (i & 1), j1 = j0 + (j & 1), k1 = k0 + (k & 1);
       const TC s = (TC)0.125 * (uc[sidx(Cl, i0, j0, k0)] + uc[sidx(Cl, i1, j0, k0)] + uc[sidx(Cl, i0, j1, k0)] +
                                 uc[sidx(Cl, i1, j1, k0)] + uc[sidx(Cl, i0, j0, k1)] + uc[sidx(Cl, i1, j0, k1)] +
                                 uc[sidx(Cl, i0, j1, k1)] + uc[sidx(Cl, i1, j1, k1)]);
-      v[q] = uf[m[q]] + (TF)s;
+      v[p] = ufc[m] + (TF)s;
     }
   }
 #pragma unroll
-  for (int q = 0; q < kKZ; ++q)
-    if (ok[q]) uf[m[q]] = v[q];
+  for (int p = 0; p < kKZ; ++p)
+    if (!d[p]) ufc[(int64_t)(kb + p) * Fl.P + q] = v[p];
+}
+
+// Direct solve on the coarsest level: u = A^-1 f over its free nodes, with the inverse (times
+// h^2, transposed so that a warp reads consecutive rows of one column) built on the host at
+// creation.  One block; f of the free nodes is staged in shared memory.
+template <typename T>
+__global__ void __launch_bounds__(1024) k_coarse_direct(T *u, const T *f, const T *ainvT, const int32_t *slot, int nf) {
+  extern __shared__ unsigned char smem_raw[];
+  T *fs = reinterpret_cast<T *>(smem_raw);
+  for (int c = threadIdx.x; c < nf; c += blockDim.x) fs[c] = f[slot[c]];
+  __syncthreads();
+  for (int r = threadIdx.x; r < nf; r += blockDim.x) {
+    T acc = 0;
+    for (int c = 0; c < nf; ++c) acc += ainvT[(int64_t)c * nf + r] * fs[c];
+    u[slot[r]] = acc;
+  }
 }
 
 // many red-black sweeps on the (small) coarsest level inside one block
@@ -204,6 +271,9 @@ template <typename T>
 __global__ void k_coarse(T *u, const T *f, const uint8_t *dirs, Lv L, T h2, int sweeps) {
   const int64_t rows = (int64_t)(L.ny + 1) * (L.nz + 1);
   const int64_t slots = rows * L.Xh;
+  for (int64_t q = threadIdx.x; q < 2 * L.nper; q += blockDim.x)
+    if (!dirs[q]) u[q] = 0;
+  __syncthreads();
   for (int s = 0; s < sweeps; ++s)
     for (int c = 0; c < 2; ++c) {
       const T *uo = u + (int64_t)(c ^ 1) * L.nper;
@@ -234,26 +304,42 @@ __global__ void k_split_mask(const uint8_t *dir, uint8_t *dirs, Lv L) {
   dirs[sidx(L, i, j, k)] = dir[n];
 }
 
-// ---- fine level <-> FP64 refinement ---------------------------------------------------------------
-// rho/eps0 from the fixed-point charge; Dirichlet values on the mask (V0 in fixed point)
-__global__ void k_rhs(const unsigned long long *Q, double *f, long long *phi, const uint8_t *dir, int nx, int ny, int nz,
-                      double unit, long long V0fx, int zero_charge) {
+// ---- fine level <-> fixed-point refinement ------------------------------------------------------
+// Dirichlet values on the mask: phi = V0 on the anode plane, 0 elsewhere (V0 in fixed point)
+__global__ void k_dirichlet(long long *phi, const uint8_t *dir, int nx, int ny, int nz, long long V0fx) {
   NODE_IJK(nx, ny)
-  // 1/V_n relative to dx^3: 2 per lateral wall the node lies on; a power of two, so folding it
-  // into the unit leaves the one rounding of Q unit unchanged
-  const double ku = unit * (i == 0 || i == nx ? 2.0 : 1.0) * (j == 0 || j == ny ? 2.0 : 1.0);
-  f[n] = zero_charge ? 0.0 : (double)(long long)Q[n] * ku;
   if (dir[n]) phi[n] = k == nz ? V0fx : 0;
 }
 
-// Residual of the FP64 system r = f - A phi, handed straight to the finest V-cycle level as its
-// right-hand side (rounded to the level's type T, split-colour layout) with a zero initial
-// correction.  The stencil 6 phi_n - sum of neighbours is an exact int64 sum of fixed-point
-// values; one FMA turns it into r (c = 2^-40 / h^2).  The squared norms of h^2 r and of h^2
-// times the lifted right-hand side (f - A phi_D: only the plane below the anode carries a
-// nonzero Dirichlet term) are accumulated in FP32 -- they only decide convergence -- so the
-// FP64 pipe (1/64 of the FP32 rate on this part) runs three operations per node.  3D launch
-// with blocks (32, 8); block partials land at the block's linear id.
+// Charge term of the right-hand side in the potential's fixed point: h^2 rho_n / eps0 in units
+// of 2^-40 V equals Q_n K with K = e w_min 2^10 / (dx eps0) (2 per lateral wall the node lies
+// on, from the halved node volume).  K is held as Kw = K 2^S (< 2^62) and the product is formed
+// exactly in 128 bits and rounded once: (Q_n Kw + 2^(S-1)) >> S, 1 <= S <= 63.
+__device__ __forceinline__ long long charge_fx(long long Qn, unsigned long long Kw, int S) {
+  const unsigned long long lo = (unsigned long long)Qn * Kw;
+  long long hi = __mul64hi(Qn, (long long)Kw);
+  const unsigned long long r = lo + (1ull << (S - 1));
+  hi += r < lo ? 1 : 0;
+  return (long long)((r >> S) | ((unsigned long long)hi << (64 - S)));
+}
+
+// int64 -> float from its two 32-bit halves: the 64-bit conversion runs on the FP64 pipe of this
+// part, the 32-bit ones do not.  Within 1.5 ulp of the correctly rounded value, which is all a
+// V-cycle right-hand side or a convergence norm needs.
+__device__ __forceinline__ float fx_to_float(long long t) {
+  return fmaf((float)(int)(t >> 32), 4294967296.0f, (float)(unsigned)t);
+}
+__device__ __forceinline__ float fx_to_level(long long t, float c) { return fx_to_float(t) * c; }
+__device__ __forceinline__ double fx_to_level(long long t, double c) { return (double)t * c; }
+
+// Residual of the discrete Poisson system in fixed point, t = h^2 (f - A phi) 2^40 = Q_n K -
+// (6 phi_n - sum of neighbours): every term is an int64, so t is exact and no FP64 arithmetic is
+// needed.  t 2^-40 / h^2 goes to the finest V-cycle level as its right-hand side (rounded to
+// the level's type T, split-colour layout); the V-cycle starts from a zero correction (its first
+// sweep).  The squared norms of h^2 r and of h^2 times the lifted right-hand side (only the
+// plane below the anode carries a nonzero Dirichlet term) are accumulated in FP32 -- they only
+// decide convergence.  3D launch with blocks (32, 8); block partials land at the block's
+// linear id.
 __device__ __forceinline__ long long nb_sum_fx(const long long *u, int i, int j, int k, int nx, int ny) {
   const int im = i > 0 ? i - 1 : 1, ip = i < nx ? i + 1 : nx - 1;
   const int jm = j > 0 ? j - 1 : 1, jp = j < ny ? j + 1 : ny - 1;
@@ -264,8 +350,9 @@ __device__ __forceinline__ long long nb_sum_fx(const long long *u, int i, int j,
 }
 
 template <typename T>
-__global__ void k_residual64(const long long *phi, const double *f, T *fl, T *ul, const uint8_t *dir, Lv L,
-                             double c_fx, float h2f, float V0f, double *part, int lift) {
+__global__ void k_residual64(const long long *phi, const unsigned long long *Q, unsigned long long Kfx, int S,
+                             int zero_charge, T *fl, const uint8_t *dir, Lv L, T c_lvl, float V0f, double *part,
+                             int lift) {
   __shared__ float sh[2][8];
   const int nx = L.nx, ny = L.ny, nz = L.nz;
   const int i = blockIdx.x * 32 + threadIdx.x;
@@ -274,20 +361,19 @@ __global__ void k_residual64(const long long *phi, const double *f, T *fl, T *ul
   if (i <= nx && j <= ny) {
     const int64_t n = node_index(i, j, k, nx, ny);
     const int64_t m = sidx(L, i, j, k);
-    ul[m] = 0;
-    if (dir[n]) {
-      fl[m] = 0;
-    } else {
-      const double fn = f[n];
-      const long long t = 6 * phi[n] - nb_sum_fx(phi, i, j, k, nx, ny);
-      const double rr = fma(-(double)t, c_fx, fn);
-      fl[m] = (T)rr;
-      const float rs = (float)rr * h2f;
-      s = rs * rs;
-      if (lift) {
-        const float l = (float)fn * h2f + (k == nz - 1 ? V0f : 0.f);
-        sl = l * l;
-      }
+    const uint8_t d = dir[n];
+    const int wall = (i == 0 || i == nx ? 1 : 0) + (j == 0 || j == ny ? 1 : 0);
+    long long t = 0, f = 0;
+    if (!d) {   // Dirichlet nodes include the k = 0 and k = nz planes: the stencil stays inside
+      f = zero_charge ? 0 : charge_fx((long long)Q[n], Kfx << wall, S);
+      t = f - (6 * phi[n] - nb_sum_fx(phi, i, j, k, nx, ny));
+    }
+    fl[m] = d ? (T)0 : fx_to_level(t, c_lvl);
+    const float rs = fx_to_float(t) * 9.094947017729282e-13f;   // 2^-40
+    s = rs * rs;
+    if (lift && !d) {
+      const float l = fx_to_float(f) * 9.094947017729282e-13f + (k == nz - 1 ? V0f : 0.f);
+      sl = l * l;
     }
   }
   for (int o = 16; o > 0; o >>= 1) {
@@ -406,6 +492,24 @@ template <>
 double *lvl_r<double>(MgLevel &L) { return L.rd; }
 
 template <typename T>
+static const T *coarse_inv(pic_t *h);
+template <>
+const float *coarse_inv<float>(pic_t *h) { return h->coarse_inv_f; }
+template <>
+const double *coarse_inv<double>(pic_t *h) { return h->coarse_inv_d; }
+
+template <typename T>
+static void smooth(pic_t *h, MgLevel &L, const Lv &lv, T h2, int c, bool first) {
+  ++h->nlaunch;
+  KtScope kt_(h, first ? kidSmoothFirst : kidSmooth, (double)L.nper);
+  const dim3 g = flat_grid(lv, 1, kKZ);
+  if (first) k_smooth<T, true><<<g, kSlotThreads, 0, h->stream>>>(lvl_u<T>(L), lvl_f<T>(L), L.dirs, lv, h2, c);
+  else k_smooth<T, false><<<g, kSlotThreads, 0, h->stream>>>(lvl_u<T>(L), lvl_f<T>(L), L.dirs, lv, h2, c);
+}
+
+// V-cycle on level l for A e = f_l, starting from e = 0: 2 red-black pre-sweeps (the first
+// takes e = 0), residual, restriction, the coarser cycle, prolongation, 2 post-sweeps.
+template <typename T>
 static void vcycle(pic_t *h, int l) {
   MgLevel &L = h->mg[l];
   const Lv lv = lv_of(L);
@@ -413,41 +517,44 @@ static void vcycle(pic_t *h, int l) {
   const int last = (int)h->mg.size() - 1;
   if (l == last) {
     ++h->nlaunch;
-    k_coarse<T><<<1, 1024, 0, h->stream>>>(lvl_u<T>(L), lvl_f<T>(L), L.dirs, lv, h2, 60);
+    KtScope kt_(h, kidCoarse, (double)L.nnode);
+    if (h->coarse_n > 0)
+      k_coarse_direct<T><<<1, 1024, h->coarse_n * sizeof(T), h->stream>>>(lvl_u<T>(L), lvl_f<T>(L), coarse_inv<T>(h),
+                                                                          h->coarse_slot, h->coarse_n);
+    else
+      k_coarse<T><<<1, 1024, 0, h->stream>>>(lvl_u<T>(L), lvl_f<T>(L), L.dirs, lv, h2, 60);
     return;
   }
-  const dim3 sg = slot_grid(lv, 1), sg2 = slot_grid(lv, 2), bl = node_block();
   for (int s = 0; s < 2; ++s)
-    for (int c = 0; c < 2; ++c) { ++h->nlaunch; k_smooth<T><<<sg, bl, 0, h->stream>>>(lvl_u<T>(L), lvl_f<T>(L), L.dirs, lv, h2, c); }
+    for (int c = 0; c < 2; ++c) smooth<T>(h, L, lv, h2, c, s == 0 && c == 0);
   ++h->nlaunch;
-  k_residual<T><<<sg2, bl, 0, h->stream>>>(lvl_u<T>(L), lvl_f<T>(L), lvl_r<T>(L), L.dirs, lv, inv_h2);
+  { KtScope kt_(h, kidResidual, (double)L.nper); k_residual<T><<<flat_grid(lv, 1, kKZ), kSlotThreads, 0, h->stream>>>(lvl_u<T>(L), lvl_f<T>(L), lvl_r<T>(L), L.dirs, lv, inv_h2); }
   MgLevel &Cl = h->mg[l + 1];
   const Lv cv = lv_of(Cl);
   ++h->nlaunch;
-  k_restrict<T, T><<<node_grid3(Cl.nx, Cl.ny, Cl.nz), bl, 0, h->stream>>>(lvl_r<T>(L), lv, lvl_f<T>(Cl), lvl_u<T>(Cl),
-                                                                       Cl.dirs, cv);
+  { KtScope kt_(h, kidRestrict, (double)Cl.nnode); k_restrict<T, T><<<flat_grid(cv, 2, 1), kSlotThreads, 0, h->stream>>>(lvl_r<T>(L), lv, lvl_f<T>(Cl), Cl.dirs, cv); }
   vcycle<T>(h, l + 1);
   ++h->nlaunch;
-  k_prolong<T, T><<<sg2, bl, 0, h->stream>>>(lvl_u<T>(Cl), cv, lvl_u<T>(L), L.dirs, lv);
+  { KtScope kt_(h, kidProlong, (double)L.nnode); k_prolong<T, T><<<flat_grid(lv, 2, kKZ), kSlotThreads, 0, h->stream>>>(lvl_u<T>(Cl), cv, lvl_u<T>(L), L.dirs, lv); }
   for (int s = 0; s < 2; ++s)
-    for (int c = 1; c >= 0; --c) { ++h->nlaunch; k_smooth<T><<<sg, bl, 0, h->stream>>>(lvl_u<T>(L), lvl_f<T>(L), L.dirs, lv, h2, c); }
+    for (int c = 1; c >= 0; --c) smooth<T>(h, L, lv, h2, c, false);
 }
 
-// one V-cycle on A e = r (r already on the finest level, e = 0 there) and phi += e
+// one V-cycle on A e = r (r already on the finest level) and phi += e
 template <typename T>
 static void cycle_fine(pic_t *h) {
   MgLevel &L = h->mg[0];
   vcycle<T>(h, 0);
   ++h->nlaunch;
   const dim3 g((L.nx + 1 + 31) / 32, (L.ny + 1 + 7) / 8, (L.nz + 1 + kKZ - 1) / kKZ);
-  k_correct<T><<<g, node_block(), 0, h->stream>>>(h->phi, lvl_u<T>(L), L.dir, lv_of(L));
+  { KtScope kt_(h, kidCorrect, (double)L.nnode); k_correct<T><<<g, node_block(), 0, h->stream>>>(h->phi, lvl_u<T>(L), L.dir, lv_of(L)); }
 }
 
 int stage_efield(pic_t *h) {
   ++h->nlaunch;
   // f32(1/(2 dx)) 2^-40 and f32(1/dx) 2^-40: rounding then scaling by a power of two
   const float c2 = (float)(1.0 / (2.0 * h->dx)) * (float)kPhiUnit, c1 = (float)(1.0 / h->dx) * (float)kPhiUnit;
-  k_efield<<<node_grid3(h->nx, h->ny, h->nz), node_block(), 0, h->stream>>>(h->phi, h->E, h->nx, h->ny, h->nz, c2, c1);
+  { KtScope kt_(h, kidEfield, (double)h->nnode); k_efield<<<node_grid3(h->nx, h->ny, h->nz), node_block(), 0, h->stream>>>(h->phi, h->E, h->nx, h->ny, h->nz, c2, c1); }
   return launch_check(h, "efield");
 }
 
@@ -467,15 +574,106 @@ int mg_build_masks(pic_t *h) {
   return launch_check(h, "mg_masks");
 }
 
+// The coarsest level's operator on its free nodes (6 on the diagonal, -1 per free neighbour,
+// mirrored across the lateral walls, Dirichlet neighbours dropped), inverted on the host by
+// Gauss-Jordan elimination with partial pivoting in FP64, for the direct coarse solve.  Levels
+// with more than kCoarseDirectMax free nodes keep the sweeping solver.
+constexpr int kCoarseDirectMax = 1024;
+int mg_coarse_setup(pic_t *h) {
+  MgLevel &L = h->mg.back();
+  std::vector<uint8_t> dir(L.nnode);
+  PIC_CUDA(h, cudaMemcpyAsync(dir.data(), L.dir, L.nnode, cudaMemcpyDeviceToHost, h->stream));
+  PIC_CUDA(h, cudaStreamSynchronize(h->stream));
+  const Lv lv = lv_of(L);
+  std::vector<int> id(L.nnode, -1);
+  std::vector<int32_t> slot;
+  for (int k = 0; k <= L.nz; ++k)
+    for (int j = 0; j <= L.ny; ++j)
+      for (int i = 0; i <= L.nx; ++i) {
+        const int64_t n = node_index(i, j, k, L.nx, L.ny);
+        if (dir[n]) continue;
+        id[n] = (int)slot.size();
+        slot.push_back((int32_t)sidx(lv, i, j, k));
+      }
+  const int nf = (int)slot.size();
+  h->coarse_n = 0;
+  if (nf == 0 || nf > kCoarseDirectMax) return PIC_OK;
+  std::vector<double> A((size_t)nf * nf, 0.0), X((size_t)nf * nf, 0.0);
+  for (int k = 0; k <= L.nz; ++k)
+    for (int j = 0; j <= L.ny; ++j)
+      for (int i = 0; i <= L.nx; ++i) {
+        const int r = id[node_index(i, j, k, L.nx, L.ny)];
+        if (r < 0) continue;   // free nodes have 0 < k < nz, so k -+ 1 stays inside
+        A[(size_t)r * nf + r] = 6.0;
+        const int nb[6][3] = {{i > 0 ? i - 1 : 1, j, k}, {i < L.nx ? i + 1 : L.nx - 1, j, k},
+                              {i, j > 0 ? j - 1 : 1, k}, {i, j < L.ny ? j + 1 : L.ny - 1, k},
+                              {i, j, k - 1}, {i, j, k + 1}};
+        for (auto &q : nb) {
+          const int c = id[node_index(q[0], q[1], q[2], L.nx, L.ny)];
+          if (c >= 0) A[(size_t)r * nf + c] -= 1.0;
+        }
+      }
+  for (int r = 0; r < nf; ++r) X[(size_t)r * nf + r] = 1.0;
+  for (int col = 0; col < nf; ++col) {
+    int piv = col;
+    for (int r = col + 1; r < nf; ++r)
+      if (fabs(A[(size_t)r * nf + col]) > fabs(A[(size_t)piv * nf + col])) piv = r;
+    if (!(fabs(A[(size_t)piv * nf + col]) > 0)) return PIC_OK;   // singular: keep the sweeps
+    if (piv != col)
+      for (int c = 0; c < nf; ++c) {
+        std::swap(A[(size_t)piv * nf + c], A[(size_t)col * nf + c]);
+        std::swap(X[(size_t)piv * nf + c], X[(size_t)col * nf + c]);
+      }
+    const double inv = 1.0 / A[(size_t)col * nf + col];
+    for (int c = 0; c < nf; ++c) { A[(size_t)col * nf + c] *= inv; X[(size_t)col * nf + c] *= inv; }
+    for (int r = 0; r < nf; ++r) {
+      if (r == col) continue;
+      const double m = A[(size_t)r * nf + col];
+      if (m == 0.0) continue;
+      for (int c = 0; c < nf; ++c) {
+        A[(size_t)r * nf + c] -= m * A[(size_t)col * nf + c];
+        X[(size_t)r * nf + c] -= m * X[(size_t)col * nf + c];
+      }
+    }
+  }
+  // u = (A / h^2)^-1 f = h^2 A^-1 f, stored transposed
+  const double h2 = L.h * L.h;
+  std::vector<double> Td((size_t)nf * nf);
+  std::vector<float> Tf((size_t)nf * nf);
+  for (int r = 0; r < nf; ++r)
+    for (int c = 0; c < nf; ++c) {
+      Td[(size_t)c * nf + r] = h2 * X[(size_t)r * nf + c];
+      Tf[(size_t)c * nf + r] = (float)Td[(size_t)c * nf + r];
+    }
+  h->coarse_inv_d = (double *)dalloc(h, Td.size() * sizeof(double));
+  h->coarse_inv_f = (float *)dalloc(h, Tf.size() * sizeof(float));
+  h->coarse_slot = (int32_t *)dalloc(h, slot.size() * sizeof(int32_t));
+  if (!h->coarse_inv_d || !h->coarse_inv_f || !h->coarse_slot) return pic_fail(h, PIC_E_CUDA, "coarse solver allocation");
+  PIC_CUDA(h, cudaMemcpyAsync(h->coarse_inv_d, Td.data(), Td.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  PIC_CUDA(h, cudaMemcpyAsync(h->coarse_inv_f, Tf.data(), Tf.size() * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+  PIC_CUDA(h, cudaMemcpyAsync(h->coarse_slot, slot.data(), slot.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
+                              h->stream));
+  PIC_CUDA(h, cudaStreamSynchronize(h->stream));
+  h->coarse_n = nf;
+  return PIC_OK;
+}
+
 // Solve for phi with the current deposited charge (or none), anode at V0.
 int stage_solve(pic_t *h, bool zero_charge, double V0) {
   MgLevel &L = h->mg[0];
   const Lv lv = lv_of(L);
-  const double unit = kQe * h->prm.w_min / 1073741824.0 / (h->dx * h->dx * h->dx) / kEps0;
-  ++h->nlaunch;
   const long long V0fx = llrint(V0 * kPhiScale);
-  k_rhs<<<node_grid3(h->nx, h->ny, h->nz), node_block(), 0, h->stream>>>(h->Q, h->rhs, h->phi, L.dir, h->nx, h->ny, h->nz,
-                                                                         unit, V0fx, zero_charge ? 1 : 0);
+  if (!h->dirichlet_valid || h->dirichlet_V0fx != V0fx) {   // the Dirichlet values change only here
+    ++h->nlaunch;
+    { KtScope kt_(h, kidDirichlet, (double)h->nnode); k_dirichlet<<<node_grid3(h->nx, h->ny, h->nz), node_block(), 0, h->stream>>>(h->phi, L.dir, h->nx, h->ny, h->nz, V0fx); }
+    h->dirichlet_valid = true;
+    h->dirichlet_V0fx = V0fx;
+  }
+  // charge factor K = e w_min 2^10 / (dx eps0) as Kw = K 2^S in [2^59, 2^60]
+  const double K = kQe * h->prm.w_min * 1024.0 / (h->dx * kEps0);
+  const int S = 59 - (int)floor(log2(K));
+  if (!(K > 0) || S < 1 || S > 63) return pic_fail(h, PIC_E_INVALID, "charge scale e w_min / (dx eps0) out of range");
+  const unsigned long long Kfx = (unsigned long long)llround(ldexp(K, S));
   const dim3 rg = node_grid3(h->nx, h->ny, h->nz);
   const int64_t nb = (int64_t)rg.x * rg.y * rg.z;
   const double inv_h2 = 1.0 / (h->dx * h->dx), c_fx = inv_h2 * kPhiUnit;
@@ -483,17 +681,15 @@ int stage_solve(pic_t *h, bool zero_charge, double V0) {
   double norms[2] = {0, 0};
   double lifted = 0.0;
   int cyc = 0;
-  const float h2f = (float)(h->dx * h->dx), V0f = (float)V0;
+  const float V0f = (float)V0;
   for (;; ++cyc) {
     ++h->nlaunch;
     if (mixed)
-      k_residual64<float><<<rg, node_block(), 0, h->stream>>>(h->phi, h->rhs, L.f, L.u, L.dir, lv, c_fx, h2f, V0f,
-                                                              h->red, cyc == 0 ? 1 : 0);
+      { KtScope kt_(h, kidResidual64, (double)h->nnode); k_residual64<float><<<rg, node_block(), 0, h->stream>>>(h->phi, h->Q, Kfx, S, zero_charge ? 1 : 0, L.f, L.dir, lv, (float)c_fx, V0f, h->red, cyc == 0 ? 1 : 0); }
     else
-      k_residual64<double><<<rg, node_block(), 0, h->stream>>>(h->phi, h->rhs, L.fd, L.ud, L.dir, lv, c_fx, h2f,
-                                                               V0f, h->red, cyc == 0 ? 1 : 0);
+      { KtScope kt_(h, kidResidual64, (double)h->nnode); k_residual64<double><<<rg, node_block(), 0, h->stream>>>(h->phi, h->Q, Kfx, S, zero_charge ? 1 : 0, L.fd, L.dir, lv, c_fx, V0f, h->red, cyc == 0 ? 1 : 0); }
     h->nlaunch += 2;
-    k_sum_stage1<<<kSumChunks, 256, 0, h->stream>>>(h->red, nb, h->red_mid);
+    { KtScope kt_(h, kidNormSum, (double)nb); k_sum_stage1<<<kSumChunks, 256, 0, h->stream>>>(h->red, nb, h->red_mid); }
     k_sum_stage2<<<1, kSumChunks, 0, h->stream>>>(h->red_mid, h->red_out);
     PIC_CUDA(h, cudaMemcpyAsync(norms, h->red_out, sizeof norms, cudaMemcpyDeviceToHost, h->stream));
     PIC_CUDA(h, cudaStreamSynchronize(h->stream));

@@ -366,7 +366,7 @@ int stage_keys(pic_t *h, int s) {
   Species &S = h->sp[s];
   if (h->keys_valid[s]) PIC_CUDA(h, cudaMemsetAsync(S.cnt, 0, (h->ncell + 1) * sizeof(uint32_t), h->stream));
   ++h->nlaunch;
-  k_keys<<<particle_grid(h), kThreads, 0, h->stream>>>(S.a, S.key, S.cnt, h->nx, h->ny, h->clock, s);
+  { KtScope kt_(h, kidKeys, 0); k_keys<<<particle_grid(h), kThreads, 0, h->stream>>>(S.a, S.key, S.cnt, h->nx, h->ny, h->clock, s); }
   h->keys_valid[s] = true;
   return launch_check(h, "keys");
 }
@@ -385,7 +385,7 @@ int stage_push(pic_t *h) {
     a.acc_sput = (unsigned long long *)h->faces.acc_sput; a.acc_Eb = (unsigned long long *)h->faces.acc_Eb;
     a.clk = h->clock;
     ++h->nlaunch;
-    k_push<<<particle_grid(h), kThreads, 0, h->stream>>>(a);
+    { KtScope kt_(h, kidPush, 0); k_push<<<particle_grid(h), kThreads, 0, h->stream>>>(a); }
     h->keys_valid[s] = true;
   }
   return launch_check(h, "push");
@@ -400,18 +400,18 @@ int stage_sort(pic_t *h) {
     if (!h->keys_valid[s]) PIC_TRY(stage_keys(h, s));
     PIC_TRY(scan_u32(h, S.cnt, S.off, h->ncell, nullptr, S.off + h->ncell));
     ++h->nlaunch;
-    k_scatter<<<particle_grid(h), kThreads, 0, h->stream>>>(S.key, S.cnt, S.off, S.perm, S.skey, h->clock, s);
+    { KtScope kt_(h, kidScatter, 0); k_scatter<<<particle_grid(h), kThreads, 0, h->stream>>>(S.key, S.cnt, S.off, S.perm, S.skey, h->clock, s); }
     PIC_CUDA(h, cudaMemsetAsync(long_n, 0, 2 * sizeof(int), h->stream));   // long_n[0]: long, [1]: mid
     ++h->nlaunch;
-    k_fix_short<<<particle_grid(h), kThreads, 0, h->stream>>>(S.skey, S.off, S.perm, h->ncell, h->mid_list,
+    { KtScope kt_(h, kidFixShort, 0); k_fix_short<<<particle_grid(h), kThreads, 0, h->stream>>>(S.skey, S.off, S.perm, h->ncell, h->mid_list,
                                                               long_n + 1, (int)h->mid_cap, long_list, long_n,
-                                                              long_cap, h->clock);
+                                                              long_cap, h->clock); }
     ++h->nlaunch;
-    k_fix_mid<<<particle_grid(h), kThreads, 0, h->stream>>>(S.perm, h->mid_list, long_n + 1, (int)h->mid_cap);
+    { KtScope kt_(h, kidFixMid, 0); k_fix_mid<<<particle_grid(h), kThreads, 0, h->stream>>>(S.perm, h->mid_list, long_n + 1, (int)h->mid_cap); }
     ++h->nlaunch;
-    k_fix_long<<<h->nsm, 1024, 0, h->stream>>>(S.perm, long_list, long_n, long_cap);
+    { KtScope kt_(h, kidFixLong, 0); k_fix_long<<<h->nsm, 1024, 0, h->stream>>>(S.perm, long_list, long_n, long_cap); }
     ++h->nlaunch;
-    k_gather<<<particle_grid(h), kThreads, 0, h->stream>>>(S.a, S.b, S.perm, S.off, h->ncell);
+    { KtScope kt_(h, kidGather, 0); k_gather<<<particle_grid(h), kThreads, 0, h->stream>>>(S.a, S.b, S.perm, S.off, h->ncell); }
     ++h->nlaunch;
     k_set_count<<<1, 1, 0, h->stream>>>(h->clock, s, S.off, h->ncell);
     std::swap(S.a, S.b);
@@ -423,10 +423,10 @@ int stage_sort(pic_t *h) {
 int stage_deposit(pic_t *h) {
   PIC_CUDA(h, cudaMemsetAsync(h->Q, 0, h->nnode * sizeof(unsigned long long), h->stream));
   ++h->nlaunch;
-  k_deposit<<<particle_grid(h), kThreads, 0, h->stream>>>(h->sp[PIC_ELECTRON].a, -1, h->Q, h->nx, h->ny, h->clock,
-                                                          PIC_ELECTRON);
+  { KtScope kt_(h, kidDeposit, 0); k_deposit<<<particle_grid(h), kThreads, 0, h->stream>>>(h->sp[PIC_ELECTRON].a, -1, h->Q, h->nx, h->ny, h->clock,
+                                                          PIC_ELECTRON); }
   ++h->nlaunch;
-  k_deposit<<<particle_grid(h), kThreads, 0, h->stream>>>(h->sp[PIC_ION].a, 1, h->Q, h->nx, h->ny, h->clock, PIC_ION);
+  { KtScope kt_(h, kidDeposit, 0); k_deposit<<<particle_grid(h), kThreads, 0, h->stream>>>(h->sp[PIC_ION].a, 1, h->Q, h->nx, h->ny, h->clock, PIC_ION); }
   return launch_check(h, "deposit");
 }
 

@@ -143,11 +143,11 @@ static int scan_impl(pic_t *h, const T *in, T *out, int64_t n, const int64_t *n_
   const int nb = 2 * h->nsm;
   T *partial = (T *)h->scan_tmp;
   ++h->nlaunch;
-  k_scan_partial<T><<<nb, kScanThreads, 0, h->stream>>>(in, n, n_dev, partial);
+  { KtScope kt_(h, kidScanPartial, (double)n); k_scan_partial<T><<<nb, kScanThreads, 0, h->stream>>>(in, n, n_dev, partial); }
   ++h->nlaunch;
   k_scan_top<T><<<1, 1024, 0, h->stream>>>(partial, nb, total);
   ++h->nlaunch;
-  k_scan_apply<T><<<nb, kScanThreads, 0, h->stream>>>(in, out, n, n_dev, partial);
+  { KtScope kt_(h, kidScanApply, (double)n); k_scan_apply<T><<<nb, kScanThreads, 0, h->stream>>>(in, out, n, n_dev, partial); }
   return launch_check(h, "scan");
 }
 

@@ -371,8 +371,8 @@ static int face_grid(pic_t *h) { return grid_for(h->faces.n, 128); }
 
 int stage_face_field(pic_t *h) {
   ++h->nlaunch;
-  k_face_field<<<grid_for(h->faces.n), kThreads, 0, h->stream>>>(h->faces.vcell, h->faces.dir, h->faces.n, h->phi, h->nx,
-                                                                 h->ny, h->dx, h->faces.F);
+  { KtScope kt_(h, kidFaceField, (double)h->faces.n); k_face_field<<<grid_for(h->faces.n), kThreads, 0, h->stream>>>(h->faces.vcell, h->faces.dir, h->faces.n, h->phi, h->nx,
+                                                                 h->ny, h->dx, h->faces.F); }
   return launch_check(h, "face_field");
 }
 
@@ -439,29 +439,32 @@ int stage_emit(pic_t *h) {
     a.fb_list = (int32_t *)fc.cnt2;          // scratch: the injection pass rewrites it afterwards
     a.fb_n = h->long_n + 8;
     if ((h->prm.flags & PIC_F_SURROGATE) && surrogate_ready(h)) {
-      PIC_TRY(surrogate_faces(h, &a.elig, &a.Y));
+      {
+        KtScope kt_(h, kidMlpForward, (double)fc.n);
+        PIC_TRY(surrogate_faces(h, &a.elig, &a.Y));
+      }
       PIC_CUDA(h, cudaMemsetAsync(a.fb_n, 0, sizeof(int), h->stream));
       ++h->nlaunch;
-      k_emit_surrogate<<<grid_for(fc.n), kThreads, 0, h->stream>>>(a);
+      { KtScope kt_(h, kidEmitSurrogate, (double)fc.n); k_emit_surrogate<<<grid_for(fc.n), kThreads, 0, h->stream>>>(a); }
       ++h->nlaunch;
       if (fast)
-        k_emit_fallback<true><<<h->nsm * 8, 128, 0, h->stream>>>(a);
+        { KtScope kt_(h, kidEmitFallback, (double)fc.n); k_emit_fallback<true><<<h->nsm * 8, 128, 0, h->stream>>>(a); }
       else
-        k_emit_fallback<false><<<h->nsm * 8, 128, 0, h->stream>>>(a);
+        { KtScope kt_(h, kidEmitFallback, (double)fc.n); k_emit_fallback<false><<<h->nsm * 8, 128, 0, h->stream>>>(a); }
     } else {
       ++h->nlaunch;
       const int blocks = (int)std::min<int64_t>((fc.n + 3) / 4, (int64_t)h->nsm * 16);
       if (fast)
-        k_emit_count<true><<<blocks, 128, 0, h->stream>>>(a);
+        { KtScope kt_(h, kidEmitCount, (double)fc.n); k_emit_count<true><<<blocks, 128, 0, h->stream>>>(a); }
       else
-        k_emit_count<false><<<blocks, 128, 0, h->stream>>>(a);
+        { KtScope kt_(h, kidEmitCount, (double)fc.n); k_emit_count<false><<<blocks, 128, 0, h->stream>>>(a); }
     }
     PIC_TRY(scan_u32(h, fc.cnt, fc.off, fc.n, nullptr, tot1));
     ++h->nlaunch;
     k_check_face_new<<<1, 1, 0, h->stream>>>(h->clock, tot1, nullptr, PIC_ELECTRON, h->sp[PIC_ELECTRON].cap, go);
     ++h->nlaunch;
-    k_emit_write<<<grid_for(fc.n), kThreads, 0, h->stream>>>(h->sp[PIC_ELECTRON].a, fc.vcell, fc.dir, fc.n, fc.cnt,
-                                                             fc.off, h->nx, h->ny, h->prm.seed, h->clock, go);
+    { KtScope kt_(h, kidEmitWrite, (double)fc.n); k_emit_write<<<grid_for(fc.n), kThreads, 0, h->stream>>>(h->sp[PIC_ELECTRON].a, fc.vcell, fc.dir, fc.n, fc.cnt,
+                                                             fc.off, h->nx, h->ny, h->prm.seed, h->clock, go); }
     ++h->nlaunch;
     k_commit_face_new<<<1, 1, 0, h->stream>>>(h->clock, tot1, nullptr, PIC_ELECTRON, go, cEmitted, cEmitted);
     PIC_TRY(launch_check(h, "emit"));
@@ -484,7 +487,7 @@ int stage_inject(pic_t *h) {
   a.cnt = fc.cnt; a.wu = fc.wu; a.cnt2 = fc.cnt2; a.wu2 = fc.wu2;
   a.evap = (fl & PIC_F_EVAP) != 0; a.sput = (fl & PIC_F_SPUTTER) != 0;
   ++h->nlaunch;
-  k_inject_count<<<grid_for(fc.n), kThreads, 0, h->stream>>>(a);
+  { KtScope kt_(h, kidInjectCount, (double)fc.n); k_inject_count<<<grid_for(fc.n), kThreads, 0, h->stream>>>(a); }
   PIC_TRY(scan_u32(h, fc.cnt, fc.off, fc.n, nullptr, tot1));
   PIC_TRY(scan_u32(h, fc.cnt2, fc.off2, fc.n, nullptr, tot2));
   ++h->nlaunch;
@@ -496,7 +499,7 @@ int stage_inject(pic_t *h) {
   w.acc_Es = (unsigned long long *)fc.acc_Es; w.nx = h->nx; w.ny = h->ny; w.seed = h->prm.seed; w.clk = h->clock;
   w.go = go;
   ++h->nlaunch;
-  k_inject_write<<<grid_for(fc.n), kThreads, 0, h->stream>>>(w);
+  { KtScope kt_(h, kidInjectWrite, (double)fc.n); k_inject_write<<<grid_for(fc.n), kThreads, 0, h->stream>>>(w); }
   ++h->nlaunch;
   k_commit_face_new<<<1, 1, 0, h->stream>>>(h->clock, tot1, tot2, PIC_NEUTRAL, go, cEvaporated, cSputtered);
   return launch_check(h, "inject");

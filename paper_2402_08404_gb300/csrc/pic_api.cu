@@ -192,6 +192,47 @@ static T *alloc_n(pic_t *h, int64_t n) {
 
 }  // namespace pic
 
+// ---- kernel timing ----------------------------------------------------------------------------
+namespace pic {
+const char *const kKernelNames[kidNum] = {
+    "k_push", "k_keys", "k_scatter", "k_fix_short", "k_fix_mid", "k_fix_long", "k_gather", "k_scan_partial",
+    "k_scan_apply", "k_deposit", "k_mcc_count", "k_mcc_products", "k_dfi_count", "k_dfi_products", "k_dirichlet",
+    "k_residual64", "k_norm_sum", "k_smooth", "k_smooth_first", "k_residual", "k_restrict", "k_prolong", "k_coarse",
+    "k_correct", "k_efield", "k_face_field", "k_emit_surrogate", "k_emit_fallback", "k_emit_count", "k_emit_write",
+    "k_inject_count", "k_inject_write", "k_mlp_forward", "k_heat"};
+
+KtScope::KtScope(pic_t *h_, int kid_, double units_) : h(h_), kid(kid_), units(units_) {
+  on = h && (h->kt_mask >> kid & 1ull);
+  if (!on) return;
+  const size_t i = h->kt_pend.size();
+  while (h->kt_ev.size() < 2 * (i + 1)) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) { on = false; return; }
+    h->kt_ev.push_back(e);
+  }
+  cudaEventRecord(h->kt_ev[2 * i], h->stream);
+}
+
+KtScope::~KtScope() {
+  if (!on) return;
+  const size_t i = h->kt_pend.size();
+  cudaEventRecord(h->kt_ev[2 * i + 1], h->stream);
+  h->kt_pend.emplace_back(kid, units);
+}
+
+void kt_collect(pic_t *h) {
+  for (size_t i = 0; i < h->kt_pend.size(); ++i) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, h->kt_ev[2 * i], h->kt_ev[2 * i + 1]) != cudaSuccess) continue;
+    const int k = h->kt_pend[i].first;
+    h->kt_ms[k] += t;
+    h->kt_units[k] += h->kt_pend[i].second;
+    h->kt_n[k] += 1;
+  }
+  h->kt_pend.clear();
+}
+}  // namespace pic
+
 using namespace pic;
 
 extern "C" {
@@ -201,6 +242,7 @@ const char *pic_last_error(pic_t *h) { return h ? h->last_error.c_str() : "null 
 void pic_destroy(pic_t *h) {
   if (!h) return;
   cudaStreamSynchronize(h->stream);
+  for (cudaEvent_t e : h->kt_ev) cudaEventDestroy(e);
   mlp_forget(h);
   dfree_all(h);
   delete h;
@@ -282,7 +324,6 @@ int pic_create(const pic_geometry_t *geometry, const pic_grid_t *grid, const pic
   h->solid = alloc_n<uint8_t>(h, h->ncell); A(h->solid);
   h->cheb = alloc_n<uint8_t>(h, h->ncell); A(h->cheb);
   h->phi = alloc_n<long long>(h, h->nnode); A(h->phi);
-  h->rhs = alloc_n<double>(h, h->nnode); A(h->rhs);
   h->E = alloc_n<float4>(h, h->nnode); A(h->E);
   h->Q = alloc_n<unsigned long long>(h, h->nnode); A(h->Q);
   // multigrid hierarchy
@@ -410,8 +451,17 @@ int pic_create(const pic_geometry_t *geometry, const pic_grid_t *grid, const pic
   if (cudaMemsetAsync(h->clock, 0, sizeof(DevClock), st) != cudaSuccess) rc = PIC_E_CUDA;
   if (cudaMemsetAsync(h->phi, 0, h->nnode * 8, st) != cudaSuccess) rc = PIC_E_CUDA;
   if (cudaMemsetAsync(h->Q, 0, h->nnode * 8, st) != cudaSuccess) rc = PIC_E_CUDA;
+  // level corrections: Dirichlet slots stay 0 for good (the sweeps never write them)
+  for (MgLevel &L : h->mg) {
+    const size_t ns = (size_t)2 * L.nper;
+    for (void *p : {(void *)L.u, (void *)L.f, (void *)L.r})
+      if (cudaMemsetAsync(p, 0, ns * sizeof(float), st) != cudaSuccess) rc = PIC_E_CUDA;
+    for (void *p : {(void *)L.ud, (void *)L.fd, (void *)L.rd})
+      if (cudaMemsetAsync(p, 0, ns * sizeof(double), st) != cudaSuccess) rc = PIC_E_CUDA;
+  }
   if (rc != PIC_OK) return fail(rc, "memset failed");
-  if (mg_build_masks(h) != PIC_OK || emission_tables_upload(h) != PIC_OK) return fail(PIC_E_CUDA, "setup failed");
+  if (mg_build_masks(h) != PIC_OK || mg_coarse_setup(h) != PIC_OK || emission_tables_upload(h) != PIC_OK)
+    return fail(PIC_E_CUDA, "setup failed");
   // V0: calibrate from the apex field by a Laplace solve at a reference V_ref (phi is linear in
   // V0).  V_ref = 1024 V (a power of two, so the rescaling is exact up to the fixed-point
   // rounding) keeps the 2^-40 V steps of phi ~1e-15 of the solution.
@@ -441,6 +491,7 @@ int pic_create(const pic_geometry_t *geometry, const pic_grid_t *grid, const pic
     }
     if (rc == PIC_OK) {
       k_scale<<<grid_for(h->nnode), kThreads, 0, st>>>(h->phi, h->nnode, h->V0 / kVref);
+      h->dirichlet_valid = false;
       rc = stage_efield(h);
     }
   }
@@ -530,6 +581,7 @@ int pic_set_potential(pic_t *h, const double *phi) {
   if (rc == PIC_OK) {
     ++h->nlaunch;
     k_phi_from_double<<<grid_for(h->nnode), kThreads, 0, h->stream>>>(buf, h->phi, h->nnode);
+    h->dirichlet_valid = false;
     rc = stage_efield(h);
   }
   if (rc == PIC_OK && cudaStreamSynchronize(h->stream) != cudaSuccess) rc = PIC_E_CUDA;
@@ -709,6 +761,29 @@ int pic_heat(pic_t *h) {
   return PIC_OK;
 }
 
+int pic_num_kernels(void) { return kidNum; }
+
+const char *pic_kernel_name(int k) { return k >= 0 && k < kidNum ? kKernelNames[k] : nullptr; }
+
+int pic_set_kernel_timing(pic_t *h, uint64_t mask) {
+  if (!h) return PIC_E_INVALID;
+  PIC_CUDA(h, cudaStreamSynchronize(h->stream));
+  kt_collect(h);
+  h->kt_mask = mask;
+  for (int k = 0; k < 64; ++k) { h->kt_ms[k] = 0; h->kt_units[k] = 0; h->kt_n[k] = 0; }
+  return PIC_OK;
+}
+
+int pic_get_kernel_timing(pic_t *h, int k, int64_t *launches, double *ms, double *units) {
+  if (!h || k < 0 || k >= kidNum) return PIC_E_INVALID;
+  PIC_CUDA(h, cudaStreamSynchronize(h->stream));
+  kt_collect(h);
+  if (launches) *launches = h->kt_n[k];
+  if (ms) *ms = h->kt_ms[k];
+  if (units) *units = h->kt_units[k];
+  return PIC_OK;
+}
+
 __global__ void k_begin_step(DevClock *clk) {
   for (int i = 0; i < cNum; ++i) clk->ctr[i] = 0;
 }
@@ -740,12 +815,16 @@ int pic_step(pic_t *h, int nsteps) {
     if (rc == PIC_OK) rc = stage_solve(h, false, h->V0);
     cudaEventRecord(ev[6], h->stream);
     ++step;
-    if (rc == PIC_OK && (h->prm.flags & PIC_F_HEAT) && h->prm.n_heat > 0 && step % h->prm.n_heat == 0) rc = stage_heat(h);
+    if (rc == PIC_OK && (h->prm.flags & PIC_F_HEAT) && h->prm.n_heat > 0 && step % h->prm.n_heat == 0) {
+      KtScope kt_(h, kidHeat, (double)h->heat.nvox);
+      rc = stage_heat(h);
+    }
     ++h->nlaunch;
     k_end_step<<<1, 1, 0, h->stream>>>(h->clock);
     cudaEventRecord(ev[7], h->stream);
     // per-stage times summed over the steps of this call (events on the library stream)
     cudaEventSynchronize(ev[7]);
+    kt_collect(h);
     float t;
     for (int i = 0; i < 7; ++i) {
       cudaEventElapsedTime(&t, ev[i], ev[i + 1]);

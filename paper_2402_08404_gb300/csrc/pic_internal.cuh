@@ -146,13 +146,18 @@ struct pic_s {
   uint8_t *solid = nullptr;      // per cell
   uint8_t *cheb = nullptr;       // per cell: Chebyshev distance to the nearest solid cell (capped)
   long long *phi = nullptr;      // per node, fixed point: phi [V] = phi * 2^-kPhiShift
-  double *rhs = nullptr;         // per node: rho/eps0 (FP64)
+  bool dirichlet_valid = false;  // phi holds the Dirichlet values of dirichlet_V0fx on the mask
+  long long dirichlet_V0fx = 0;
   float4 *E = nullptr;           // per node
   unsigned long long *Q = nullptr;  // per node, int64 two's complement charge
   pic::Species sp[3];
   pic::Faces faces;
   pic::Heat heat;
   std::vector<pic::MgLevel> mg;
+  int coarse_n = 0;                 // free nodes of the coarsest level (0: sweeping coarse solver)
+  float *coarse_inv_f = nullptr;    // its inverse operator times h^2, transposed (nf x nf)
+  double *coarse_inv_d = nullptr;
+  int32_t *coarse_slot = nullptr;   // split-layout slot of each free node
   pic::DevClock *clock = nullptr;
   // scratch
   void *scan_tmp = nullptr;      // block partials for scans
@@ -174,6 +179,12 @@ struct pic_s {
   float ms[8] = {0};
   int64_t solid_count = 0;
   int64_t nlaunch = 0;           // kernels launched by the library since create
+  // kernel timing (diagnostics): launches of the kernels in kt_mask are bracketed by event pairs
+  uint64_t kt_mask = 0;
+  std::vector<cudaEvent_t> kt_ev;                   // 2 per recorded launch, reused
+  std::vector<std::pair<int, double>> kt_pend;      // (kernel, units) per recorded launch
+  double kt_ms[64] = {0}, kt_units[64] = {0};
+  int64_t kt_n[64] = {0};
   std::vector<uint8_t> solid_host;  // host copy of the solid-cell mask (load validation)
 };
 
@@ -236,6 +247,32 @@ __host__ __device__ inline int64_t cell_index(int i, int j, int k, int nx, int n
 
 }  // namespace pic
 
+// ---- kernel timing (host) -------------------------------------------------------------------
+namespace pic {
+// Kernels whose launches can be timed one by one (pic_set_kernel_timing); the order is the ABI's.
+enum Kid : int {
+  kidPush = 0, kidKeys, kidScatter, kidFixShort, kidFixMid, kidFixLong, kidGather, kidScanPartial, kidScanApply,
+  kidDeposit, kidMccCount, kidMccProducts, kidDfiCount, kidDfiProducts, kidDirichlet, kidResidual64, kidNormSum,
+  kidSmooth, kidSmoothFirst, kidResidual, kidRestrict, kidProlong, kidCoarse, kidCorrect, kidEfield, kidFaceField,
+  kidEmitSurrogate, kidEmitFallback, kidEmitCount, kidEmitWrite, kidInjectCount, kidInjectWrite, kidMlpForward,
+  kidHeat, kidNum
+};
+extern const char *const kKernelNames[kidNum];
+// Records an event before the launches of its scope and one after them, on the library stream,
+// when kernel `kid` is selected; `units` is the work of the launch (nodes, slots or faces; 0
+// for particle kernels, whose counts live on the device).
+struct KtScope {
+  pic_t *h;
+  int kid;
+  double units;
+  bool on;
+  KtScope(pic_t *h_, int kid_, double units_);
+  ~KtScope();
+};
+// Fold the finished event pairs into the per-kernel sums (the stream must have been synchronised).
+void kt_collect(pic_t *h);
+}  // namespace pic
+
 // ---- error plumbing (host) ------------------------------------------------------------------
 int pic_fail(pic_t *h, int code, const std::string &msg);
 #define PIC_CUDA(h, call)                                                                  \
@@ -277,6 +314,7 @@ int emission_eval_dev(pic_t *h, const double *F, const double *T, const double *
 int stage_efield(pic_t *h);
 int stage_solve(pic_t *h, bool zero_charge, double V0);
 int face_field_mean(pic_t *h, const int64_t *faces, int nf, double *out);
+int mg_coarse_setup(pic_t *h);
 // heat (k_heat.cu)
 int stage_heat(pic_t *h);
 // emission surrogate (k_mlp.cu)

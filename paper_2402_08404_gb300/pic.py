@@ -104,6 +104,11 @@ def lib():
         L.pic_mlp_forward_backward.argtypes = [vp, vp, vp, i64, vp, vp, vp]
         L.pic_surrogate_train.argtypes = [vp, i64, i32, i32, C.c_double, C.c_uint64, vp]
         L.pic_surrogate_eval.argtypes = [vp] * 8 + [i64]
+        L.pic_num_kernels.argtypes = []
+        L.pic_kernel_name.argtypes = [i32]
+        L.pic_kernel_name.restype = C.c_char_p
+        L.pic_set_kernel_timing.argtypes = [vp, C.c_uint64]
+        L.pic_get_kernel_timing.argtypes = [vp, i32, C.POINTER(i64), dp, dp]
         _lib = L
     return _lib
 
@@ -302,6 +307,29 @@ class Pic:
         for name, _ in Diag._fields_:
             v = getattr(d, name)
             out[name] = list(v) if isinstance(v, C.Array) else v
+        return out
+
+    # -- kernel timing (diagnostics) ----------------------------------------------------------------
+    @staticmethod
+    def kernel_names():
+        return [lib().pic_kernel_name(k).decode() for k in range(lib().pic_num_kernels())]
+
+    def set_kernel_timing(self, names=()):
+        """Time every launch of the named kernels (CUDA events on the library stream); () = off."""
+        idx = {n: k for k, n in enumerate(self.kernel_names())}
+        mask = 0
+        for n in names:
+            mask |= 1 << idx[n]
+        self._check(lib().pic_set_kernel_timing(self.h, C.c_uint64(mask)))
+
+    def kernel_timing(self):
+        """{name: (launches, ms, units)} of the kernels timed since the last set_kernel_timing."""
+        out = {}
+        for k, n in enumerate(self.kernel_names()):
+            cnt, ms, un = C.c_int64(), C.c_double(), C.c_double()
+            self._check(lib().pic_get_kernel_timing(self.h, k, C.byref(cnt), C.byref(ms), C.byref(un)))
+            if cnt.value:
+                out[n] = (cnt.value, ms.value, un.value)
         return out
 
     # -- emission surrogate ------------------------------------------------------------------------

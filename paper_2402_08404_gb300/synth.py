@@ -41,6 +41,10 @@ CONFIGS = {
     "medium": dict(nx=128, ny=128, nz=256, dx=0.5e-9, tip_radius=5e-9, tip_height=30e-9,
                    apex_field=10e9, n_sp=4_000_000, dt=5e-17, steps=10_000, T0=300.0,
                    work_function=4.5, w_min=1e-5, w_max_units=1024, n_heat=1000, seed=1),
+    # the production grid with a tenth of its SPs: grid kernels at full size, ~3 GB on the device
+    "production_grid": dict(nx=256, ny=256, nz=512, dx=0.5e-9, tip_radius=5e-9, tip_height=60e-9,
+                            apex_field=10e9, n_sp=2_000_000, dt=5e-17, steps=10_000, T0=300.0,
+                            work_function=4.5, w_min=1e-5, w_max_units=1024, n_heat=1000, seed=1),
     "large": dict(nx=512, ny=512, nz=1024, dx=0.5e-9, tip_radius=10e-9, tip_height=100e-9,
                   apex_field=12e9, n_sp=200_000_000, dt=5e-17, steps=5000, T0=300.0,
                   work_function=4.5, w_min=1e-5, w_max_units=1024, n_heat=1000, seed=1),
