@@ -216,34 +216,51 @@ __global__ void __launch_bounds__(kSlotThreads) k_restrict(const TF *rf, Lv Fl, 
 }
 
 // Trilinear prolongation of the coarse correction, added on free fine nodes (flat fine slots,
-// grid y: plane groups of kKZ x 2 colours; every load before the stores, addresses clamped into
-// the level).
+// grid y: plane groups of kKZ x 2 colours).  Fine slot t of row j has i in {2t, 2t + 1}, so its
+// coarse corners are columns t and t + 1 of rows j >> 1 and (j + 1) >> 1; the kKZ fine planes
+// from an even kb share the coarse planes kb/2 .. kb/2 + 2.  The thread loads those 12 coarse
+// values once (clamped into the level), then its fine values and masks, before any store.
 template <typename TC, typename TF>
 __global__ void __launch_bounds__(kSlotThreads) k_prolong(const TC *uc, Lv Cl, TF *uf, const uint8_t *dirsf, Lv Fl) {
+  static_assert(kKZ == 4, "the plane pairing below assumes four fine planes per thread");
   const uint32_t q = blockIdx.x * kSlotThreads + threadIdx.x;
   if (q >= Fl.P) return;
   const int c = blockIdx.y & 1, kb = (blockIdx.y >> 1) * kKZ;
   const int j = (int)fdiv(q, Fl.xd), t = (int)(q - (uint32_t)j * (uint32_t)Fl.Xh);
   TF *ufc = uf + (int64_t)c * Fl.nper;
   const uint8_t *dc = dirsf + (int64_t)c * Fl.nper;
+  const int t1 = min(t + 1, Cl.nx), j0 = j >> 1, j1 = j0 + (j & 1), Kb = kb >> 1;
+  TC cv[3][4];   // coarse plane Kb + r: (t, j0), (t1, j0), (t, j1), (t1, j1)
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    const int K = min(Kb + r, Cl.nz);
+    cv[r][0] = uc[sidx(Cl, t, j0, K)];
+    cv[r][1] = uc[sidx(Cl, t1, j0, K)];
+    cv[r][2] = uc[sidx(Cl, t, j1, K)];
+    cv[r][3] = uc[sidx(Cl, t1, j1, K)];
+  }
   TF v[kKZ];
   uint8_t d[kKZ];
 #pragma unroll
   for (int p = 0; p < kKZ; ++p) {
     const int k = kb + p;
-    v[p] = 0;
     d[p] = 1;
+    v[p] = 0;
     if (k > 0 && k < Fl.nz) {
       const int64_t m = (int64_t)k * Fl.P + q;
-      const int i = min(2 * t + ((j + k + c) & 1), Fl.nx);
       d[p] = dc[m];
-      const int i0 = i >> 1, j0 = j >> 1, k0 = k >> 1;
-      const int i1 = i0 + (i & 1), j1 = j0 + (j & 1), k1 = k0 + (k & 1);
-      const TC s = (TC)0.125 * (uc[sidx(Cl, i0, j0, k0)] + uc[sidx(Cl, i1, j0, k0)] + uc[sidx(Cl, i0, j1, k0)] +
-                                uc[sidx(Cl, i1, j1, k0)] + uc[sidx(Cl, i0, j0, k1)] + uc[sidx(Cl, i1, j0, k1)] +
-                                uc[sidx(Cl, i0, j1, k1)] + uc[sidx(Cl, i1, j1, k1)]);
-      v[p] = ufc[m] + (TF)s;
+      v[p] = ufc[m];
     }
+  }
+#pragma unroll
+  for (int p = 0; p < kKZ; ++p) {
+    const int k = kb + p;
+    const bool odd = ((j + k + c) & 1) && 2 * t + 1 <= Fl.nx;   // fine i = 2t + 1: corners t and t + 1
+    const int ra = p >> 1, rb = (p + 1) >> 1;                    // coarse planes k >> 1 and (k + 1) >> 1
+    const TC a1 = odd ? cv[ra][1] : cv[ra][0], a3 = odd ? cv[ra][3] : cv[ra][2];
+    const TC b1 = odd ? cv[rb][1] : cv[rb][0], b3 = odd ? cv[rb][3] : cv[rb][2];
+    const TC s = (TC)0.125 * (cv[ra][0] + a1 + cv[ra][2] + a3 + cv[rb][0] + b1 + cv[rb][2] + b3);
+    v[p] = v[p] + (TF)s;
   }
 #pragma unroll
   for (int p = 0; p < kKZ; ++p)
@@ -349,31 +366,56 @@ __device__ __forceinline__ long long nb_sum_fx(const long long *u, int i, int j,
          u[c - sz + i] + u[c + sz + i];
 }
 
+// kKZ planes per thread (grid z: plane groups): the centre column of phi is loaded once for the
+// z differences of all of them, and every load is issued before the arithmetic (all addresses
+// inside the grid; Dirichlet nodes, the k = 0 and k = nz planes among them, discard theirs).
 template <typename T>
-__global__ void k_residual64(const long long *phi, const unsigned long long *Q, unsigned long long Kfx, int S,
-                             int zero_charge, T *fl, const uint8_t *dir, Lv L, T c_lvl, float V0f, double *part,
-                             int lift) {
+__global__ void __launch_bounds__(256) k_residual64(const long long *phi, const unsigned long long *Q,
+                                                    unsigned long long Kfx, int S, int zero_charge, T *fl,
+                                                    const uint8_t *dir, Lv L, T c_lvl, float V0f, double *part,
+                                                    int lift) {
   __shared__ float sh[2][8];
   const int nx = L.nx, ny = L.ny, nz = L.nz;
   const int i = blockIdx.x * 32 + threadIdx.x;
-  const int j = blockIdx.y * 8 + threadIdx.y, k = blockIdx.z;
+  const int j = blockIdx.y * 8 + threadIdx.y, k0 = blockIdx.z * kKZ;
   float s = 0.f, sl = 0.f;
   if (i <= nx && j <= ny) {
-    const int64_t n = node_index(i, j, k, nx, ny);
-    const int64_t m = sidx(L, i, j, k);
-    const uint8_t d = dir[n];
-    const int wall = (i == 0 || i == nx ? 1 : 0) + (j == 0 || j == ny ? 1 : 0);
-    long long t = 0, f = 0;
-    if (!d) {   // Dirichlet nodes include the k = 0 and k = nz planes: the stencil stays inside
-      f = zero_charge ? 0 : charge_fx((long long)Q[n], Kfx << wall, S);
-      t = f - (6 * phi[n] - nb_sum_fx(phi, i, j, k, nx, ny));
+    const int im = i > 0 ? i - 1 : 1, ip = i < nx ? i + 1 : nx - 1;
+    const int jm = j > 0 ? j - 1 : 1, jp = j < ny ? j + 1 : ny - 1;
+    const int64_t sy = nx + 1, sz = (int64_t)(nx + 1) * (ny + 1);
+    const int64_t col = (int64_t)j * sy + i;
+    long long cz[kKZ + 2];
+#pragma unroll
+    for (int p = 0; p < kKZ + 2; ++p) cz[p] = phi[(int64_t)min(max(k0 - 1 + p, 0), nz) * sz + col];
+    long long side[kKZ];
+    unsigned long long qv[kKZ];
+    uint8_t d[kKZ];
+#pragma unroll
+    for (int p = 0; p < kKZ; ++p) {
+      const int k = min(k0 + p, nz);
+      const int64_t pl = (int64_t)k * sz;
+      d[p] = k0 + p <= nz ? dir[pl + col] : 1;
+      side[p] = phi[pl + (int64_t)j * sy + im] + phi[pl + (int64_t)j * sy + ip] + phi[pl + (int64_t)jm * sy + i] +
+                phi[pl + (int64_t)jp * sy + i];
+      qv[p] = Q[pl + col];
     }
-    fl[m] = d ? (T)0 : fx_to_level(t, c_lvl);
-    const float rs = fx_to_float(t) * 9.094947017729282e-13f;   // 2^-40
-    s = rs * rs;
-    if (lift && !d) {
-      const float l = fx_to_float(f) * 9.094947017729282e-13f + (k == nz - 1 ? V0f : 0.f);
-      sl = l * l;
+#pragma unroll
+    for (int p = 0; p < kKZ; ++p) {
+      const int k = k0 + p;
+      if (k > nz) break;
+      const int wall = (i == 0 || i == nx ? 1 : 0) + (j == 0 || j == ny ? 1 : 0);
+      long long t = 0, f = 0;
+      if (!d[p]) {
+        f = zero_charge ? 0 : charge_fx((long long)qv[p], Kfx << wall, S);
+        t = f - (6 * cz[p + 1] - (side[p] + cz[p] + cz[p + 2]));
+      }
+      fl[sidx(L, i, j, k)] = d[p] ? (T)0 : fx_to_level(t, c_lvl);
+      const float rs = fx_to_float(t) * 9.094947017729282e-13f;   // 2^-40
+      s += rs * rs;
+      if (lift && !d[p]) {
+        const float l = fx_to_float(f) * 9.094947017729282e-13f + (k == nz - 1 ? V0f : 0.f);
+        sl += l * l;
+      }
     }
   }
   for (int o = 16; o > 0; o >>= 1) {
@@ -454,21 +496,37 @@ __global__ void k_correct(long long *phi, const T *u, const uint8_t *dir, Lv L) 
 // f32(1/dx) on the z planes) in f32.  The difference of two fixed-point values is an exact
 // int64; its f32 rounding equals that of the exact FP64 difference, and the 2^-40 folds into the
 // f32 factor exactly, so no FP64 operation is needed.
-__global__ void k_efield(const long long *phi, float4 *E, int nx, int ny, int nz, float c2, float c1) {
+__global__ void __launch_bounds__(256) k_efield(const long long *phi, float4 *E, int nx, int ny, int nz, float c2,
+                                                float c1) {
+  const int i = blockIdx.x * 32 + threadIdx.x;
+  const int j = blockIdx.y * 8 + threadIdx.y, k0 = blockIdx.z * kKZ;
+  if (i > nx || j > ny) return;
   const int64_t sy = nx + 1, sz = (int64_t)(nx + 1) * (ny + 1);
-  {
-    NODE_IJK(nx, ny)
-    const int im = i > 0 ? i - 1 : 1, ip = i < nx ? i + 1 : nx - 1;
-    const int jm = j > 0 ? j - 1 : 1, jp = j < ny ? j + 1 : ny - 1;
-    const int64_t row = (int64_t)k * sz + (int64_t)j * sy;
+  const int im = i > 0 ? i - 1 : 1, ip = i < nx ? i + 1 : nx - 1;
+  const int jm = j > 0 ? j - 1 : 1, jp = j < ny ? j + 1 : ny - 1;
+  const int64_t col = (int64_t)j * sy + i;
+  // kKZ planes per thread: the centre column k0 - 1 .. k0 + kKZ (clamped) serves all z differences
+  long long cz[kKZ + 2], dx[kKZ], dy[kKZ];
+#pragma unroll
+  for (int p = 0; p < kKZ + 2; ++p) cz[p] = phi[(int64_t)min(max(k0 - 1 + p, 0), nz) * sz + col];
+#pragma unroll
+  for (int p = 0; p < kKZ; ++p) {
+    const int64_t pl = (int64_t)min(k0 + p, nz) * sz;
+    dx[p] = phi[pl + (int64_t)j * sy + im] - phi[pl + (int64_t)j * sy + ip];
+    dy[p] = phi[pl + (int64_t)jm * sy + i] - phi[pl + (int64_t)jp * sy + i];
+  }
+#pragma unroll
+  for (int p = 0; p < kKZ; ++p) {
+    const int k = k0 + p;
+    if (k > nz) break;
     float4 e;
-    e.x = __fmul_rn(__ll2float_rn(phi[row + im] - phi[row + ip]), c2);
-    e.y = __fmul_rn(__ll2float_rn(phi[(int64_t)k * sz + (int64_t)jm * sy + i] - phi[(int64_t)k * sz + (int64_t)jp * sy + i]), c2);
-    if (k == 0) e.z = __fmul_rn(__ll2float_rn(phi[n] - phi[n + sz]), c1);
-    else if (k == nz) e.z = __fmul_rn(__ll2float_rn(phi[n - sz] - phi[n]), c1);
-    else e.z = __fmul_rn(__ll2float_rn(phi[n - sz] - phi[n + sz]), c2);
+    e.x = __fmul_rn(__ll2float_rn(dx[p]), c2);
+    e.y = __fmul_rn(__ll2float_rn(dy[p]), c2);
+    if (k == 0) e.z = __fmul_rn(__ll2float_rn(cz[p + 1] - cz[p + 2]), c1);
+    else if (k == nz) e.z = __fmul_rn(__ll2float_rn(cz[p] - cz[p + 1]), c1);
+    else e.z = __fmul_rn(__ll2float_rn(cz[p] - cz[p + 2]), c2);
     e.w = 0.f;
-    E[n] = e;
+    E[(int64_t)k * sz + col] = e;
   }
 }
 
@@ -554,7 +612,7 @@ int stage_efield(pic_t *h) {
   ++h->nlaunch;
   // f32(1/(2 dx)) 2^-40 and f32(1/dx) 2^-40: rounding then scaling by a power of two
   const float c2 = (float)(1.0 / (2.0 * h->dx)) * (float)kPhiUnit, c1 = (float)(1.0 / h->dx) * (float)kPhiUnit;
-  { KtScope kt_(h, kidEfield, (double)h->nnode); k_efield<<<node_grid3(h->nx, h->ny, h->nz), node_block(), 0, h->stream>>>(h->phi, h->E, h->nx, h->ny, h->nz, c2, c1); }
+  { KtScope kt_(h, kidEfield, (double)h->nnode); k_efield<<<dim3((h->nx + 1 + 31) / 32, (h->ny + 1 + 7) / 8, (h->nz + kKZ) / kKZ), node_block(), 0, h->stream>>>(h->phi, h->E, h->nx, h->ny, h->nz, c2, c1); }
   return launch_check(h, "efield");
 }
 
@@ -674,7 +732,7 @@ int stage_solve(pic_t *h, bool zero_charge, double V0) {
   const int S = 59 - (int)floor(log2(K));
   if (!(K > 0) || S < 1 || S > 63) return pic_fail(h, PIC_E_INVALID, "charge scale e w_min / (dx eps0) out of range");
   const unsigned long long Kfx = (unsigned long long)llround(ldexp(K, S));
-  const dim3 rg = node_grid3(h->nx, h->ny, h->nz);
+  const dim3 rg((h->nx + 1 + 31) / 32, (h->ny + 1 + 7) / 8, (h->nz + kKZ) / kKZ);
   const int64_t nb = (int64_t)rg.x * rg.y * rg.z;
   const double inv_h2 = 1.0 / (h->dx * h->dx), c_fx = inv_h2 * kPhiUnit;
   const bool mixed = (h->prm.flags & PIC_F_MIXED_MG) != 0;
