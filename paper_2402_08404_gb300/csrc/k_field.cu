@@ -105,28 +105,29 @@ __device__ __forceinline__ T nb_sum_s(const T *uo, const Lv &L, int i, int t, in
          uo[srow(L, j, k - 1) + t] + uo[srow(L, j, k + 1) + t];
 }
 
-// One colour of red-black Gauss-Seidel on A u = f.  Each thread takes slot q of kKZ planes and
+// One colour of red-black Gauss-Seidel on A u = f.  Each thread takes slot q of KZ planes (chosen
+// per level by the autotuner) and
 // issues every load of all of them (right-hand side, mask, the six neighbours of the other
 // colour) before its first store: nothing read in a colour pass is written in it, and every
 // address is inside the level (mirrored at the lateral walls, unused slots clamp into the row),
 // so the loads need not wait for the mask.  first = 1: the other colour is taken as zero (the
 // first sweep after a new right-hand side), so the correction needs no clearing pass; Dirichlet
 // slots of u hold 0 from creation and are never written.
-template <typename T, bool first>
+template <typename T, bool first, int KZ>
 __global__ void __launch_bounds__(kSlotThreads) k_smooth(T *u, const T *f, const uint8_t *dirs, Lv L, T h2, int c) {
   const uint32_t q = blockIdx.x * kSlotThreads + threadIdx.x;
   if (q >= L.P) return;
   const int j = (int)fdiv(q, L.xd), t = (int)(q - (uint32_t)j * (uint32_t)L.Xh);
-  const int k0 = blockIdx.y * kKZ;
+  const int k0 = blockIdx.y * KZ;
   const T *uo = u + (int64_t)(c ^ 1) * L.nper;
   T *uc = u + (int64_t)c * L.nper;
   const T *fc = f + (int64_t)c * L.nper;
   const uint8_t *dc = dirs + (int64_t)c * L.nper;
   const int64_t ojm = j > 0 ? -(int64_t)L.Xh : (int64_t)L.Xh, ojp = j < L.ny ? (int64_t)L.Xh : -(int64_t)L.Xh;
-  T v[kKZ];
-  uint8_t d[kKZ];
+  T v[KZ];
+  uint8_t d[KZ];
 #pragma unroll
-  for (int p = 0; p < kKZ; ++p) {
+  for (int p = 0; p < KZ; ++p) {
     const int k = k0 + p;
     v[p] = 0;
     d[p] = 1;
@@ -145,7 +146,7 @@ __global__ void __launch_bounds__(kSlotThreads) k_smooth(T *u, const T *f, const
     }
   }
 #pragma unroll
-  for (int p = 0; p < kKZ; ++p)
+  for (int p = 0; p < KZ; ++p)
     if (!d[p]) uc[(int64_t)(k0 + p) * L.P + q] = v[p] * (T)(1.0 / 6.0);
 }
 
@@ -340,12 +341,24 @@ __device__ __forceinline__ long long charge_fx(long long Qn, unsigned long long 
   return (long long)((r >> S) | ((unsigned long long)hi << (64 - S)));
 }
 
-// int64 -> float from its two 32-bit halves: the 64-bit conversion runs on the FP64 pipe of this
-// part, the 32-bit ones do not.  Within 1.5 ulp of the correctly rounded value, which is all a
-// V-cycle right-hand side or a convergence norm needs.
-__device__ __forceinline__ float fx_to_float(long long t) {
-  return fmaf((float)(int)(t >> 32), 4294967296.0f, (float)(unsigned)t);
+// int64 -> float rounded to nearest, ties to even, in integer arithmetic: the conversion
+// instruction for 64-bit integers runs on the FP64 pipe of this part.  The magnitude is
+// normalised to bit 63, its top 24 bits are the significand and the 40 bits below decide the
+// rounding; the result equals __ll2float_rn for every input.
+__device__ __forceinline__ float ll2f_rn(long long x) {
+  const unsigned int sgn = (unsigned int)((unsigned long long)x >> 32) & 0x80000000u;
+  unsigned long long a = x < 0 ? 0ull - (unsigned long long)x : (unsigned long long)x;
+  if (a == 0ull) return 0.f;
+  const int lz = __clzll((long long)a);
+  a <<= lz;
+  unsigned int m = (unsigned int)(a >> 40);
+  const unsigned long long rest = a & 0xFFFFFFFFFFull, half = 0x8000000000ull;
+  if (rest > half || (rest == half && (m & 1u))) ++m;
+  int e = 63 - lz;
+  if (m == 0x1000000u) { m >>= 1; ++e; }
+  return __uint_as_float(sgn | ((unsigned int)(e + 127) << 23) | (m & 0x7FFFFFu));
 }
+__device__ __forceinline__ float fx_to_float(long long t) { return ll2f_rn(t); }
 __device__ __forceinline__ float fx_to_level(long long t, float c) { return fx_to_float(t) * c; }
 __device__ __forceinline__ double fx_to_level(long long t, double c) { return (double)t * c; }
 
@@ -520,11 +533,11 @@ __global__ void __launch_bounds__(256) k_efield(const long long *phi, float4 *E,
     const int k = k0 + p;
     if (k > nz) break;
     float4 e;
-    e.x = __fmul_rn(__ll2float_rn(dx[p]), c2);
-    e.y = __fmul_rn(__ll2float_rn(dy[p]), c2);
-    if (k == 0) e.z = __fmul_rn(__ll2float_rn(cz[p + 1] - cz[p + 2]), c1);
-    else if (k == nz) e.z = __fmul_rn(__ll2float_rn(cz[p] - cz[p + 1]), c1);
-    else e.z = __fmul_rn(__ll2float_rn(cz[p] - cz[p + 2]), c2);
+    e.x = __fmul_rn(ll2f_rn(dx[p]), c2);
+    e.y = __fmul_rn(ll2f_rn(dy[p]), c2);
+    if (k == 0) e.z = __fmul_rn(ll2f_rn(cz[p + 1] - cz[p + 2]), c1);
+    else if (k == nz) e.z = __fmul_rn(ll2f_rn(cz[p] - cz[p + 1]), c1);
+    else e.z = __fmul_rn(ll2f_rn(cz[p] - cz[p + 2]), c2);
     e.w = 0.f;
     E[(int64_t)k * sz + col] = e;
   }
@@ -556,13 +569,29 @@ const float *coarse_inv<float>(pic_t *h) { return h->coarse_inv_f; }
 template <>
 const double *coarse_inv<double>(pic_t *h) { return h->coarse_inv_d; }
 
+template <typename T, int KZ>
+static void smooth_kz(pic_t *h, MgLevel &L, const Lv &lv, T h2, int c, bool first) {
+  const dim3 g = flat_grid(lv, 1, KZ);
+  if (first) k_smooth<T, true, KZ><<<g, kSlotThreads, 0, h->stream>>>(lvl_u<T>(L), lvl_f<T>(L), L.dirs, lv, h2, c);
+  else k_smooth<T, false, KZ><<<g, kSlotThreads, 0, h->stream>>>(lvl_u<T>(L), lvl_f<T>(L), L.dirs, lv, h2, c);
+}
+
+// one colour sweep on level l with its tuned planes per thread (1, 2, 4 or 8)
 template <typename T>
-static void smooth(pic_t *h, MgLevel &L, const Lv &lv, T h2, int c, bool first) {
+static void smooth_launch(pic_t *h, MgLevel &L, const Lv &lv, T h2, int c, bool first, int kz) {
+  switch (kz) {
+    case 1: smooth_kz<T, 1>(h, L, lv, h2, c, first); break;
+    case 2: smooth_kz<T, 2>(h, L, lv, h2, c, first); break;
+    case 8: smooth_kz<T, 8>(h, L, lv, h2, c, first); break;
+    default: smooth_kz<T, 4>(h, L, lv, h2, c, first); break;
+  }
+}
+
+template <typename T>
+static void smooth(pic_t *h, int l, MgLevel &L, const Lv &lv, T h2, int c, bool first) {
   ++h->nlaunch;
   KtScope kt_(h, first ? kidSmoothFirst : kidSmooth, (double)L.nper);
-  const dim3 g = flat_grid(lv, 1, kKZ);
-  if (first) k_smooth<T, true><<<g, kSlotThreads, 0, h->stream>>>(lvl_u<T>(L), lvl_f<T>(L), L.dirs, lv, h2, c);
-  else k_smooth<T, false><<<g, kSlotThreads, 0, h->stream>>>(lvl_u<T>(L), lvl_f<T>(L), L.dirs, lv, h2, c);
+  smooth_launch<T>(h, L, lv, h2, c, first, h->tune_smooth_kz[l < 16 ? l : 15]);
 }
 
 // V-cycle on level l for A e = f_l, starting from e = 0: 2 red-black pre-sweeps (the first
@@ -584,7 +613,7 @@ static void vcycle(pic_t *h, int l) {
     return;
   }
   for (int s = 0; s < 2; ++s)
-    for (int c = 0; c < 2; ++c) smooth<T>(h, L, lv, h2, c, s == 0 && c == 0);
+    for (int c = 0; c < 2; ++c) smooth<T>(h, l, L, lv, h2, c, s == 0 && c == 0);
   ++h->nlaunch;
   { KtScope kt_(h, kidResidual, (double)L.nper); k_residual<T><<<flat_grid(lv, 1, kKZ), kSlotThreads, 0, h->stream>>>(lvl_u<T>(L), lvl_f<T>(L), lvl_r<T>(L), L.dirs, lv, inv_h2); }
   MgLevel &Cl = h->mg[l + 1];
@@ -595,7 +624,7 @@ static void vcycle(pic_t *h, int l) {
   ++h->nlaunch;
   { KtScope kt_(h, kidProlong, (double)L.nnode); k_prolong<T, T><<<flat_grid(lv, 2, kKZ), kSlotThreads, 0, h->stream>>>(lvl_u<T>(Cl), cv, lvl_u<T>(L), L.dirs, lv); }
   for (int s = 0; s < 2; ++s)
-    for (int c = 1; c >= 0; --c) smooth<T>(h, L, lv, h2, c, false);
+    for (int c = 1; c >= 0; --c) smooth<T>(h, l, L, lv, h2, c, false);
 }
 
 // one V-cycle on A e = r (r already on the finest level) and phi += e

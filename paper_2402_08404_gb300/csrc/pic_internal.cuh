@@ -56,7 +56,7 @@ enum Ctr {
 };
 
 // error bits set by kernels
-enum ErrBits : int { kErrCapacity = 1, kErrSegment = 2, kErrTimeout = 4, kErrNan = 8 };
+enum ErrBits : int { kErrCapacity = 1, kErrSegment = 2, kErrTimeout = 4, kErrNan = 8, kErrNoconv = 16 };
 
 struct DevClock {
   int64_t step;
@@ -66,6 +66,11 @@ struct DevClock {
   int64_t n_new[3];      // scratch: SPs created by the current pass
   int64_t ctr[cNum];
   int err;
+  // graph form of the Poisson loop (device-side convergence test)
+  int mg_cycles_last;       // cycles of the last solve
+  float mg_rel_last;        // its relative residual
+  double mg_lifted;         // norm of the lifted right-hand side of the current solve
+  int64_t mg_graph_cycles;  // cycles run inside graphs since create (launch accounting)
 };
 
 struct SpeciesBuf {
@@ -179,6 +184,17 @@ struct pic_s {
   float ms[8] = {0};
   int64_t solid_count = 0;
   int64_t nlaunch = 0;           // kernels launched by the library since create
+  // graph form of the step (PIC_F_GRAPH): one captured graph per double-buffer parity
+  cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+  float *graph_a[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};  // S.a.x at capture
+  bool graph_valid = false;
+  int64_t graph_outer_launches = 0, graph_body_launches = 0;
+  cudaStream_t body_stream = nullptr;   // capture stream of the Poisson loop body
+  bool capturing = false;               // stage code is being recorded into a graph
+  bool last_solve_graph = false;        // the last solve ran in a graph (its diagnostics are on the device)
+  // autotuned launch shapes
+  int tune_dep_bps = 8;                 // deposit blocks per SM
+  int tune_smooth_kz[16] = {4, 4, 4, 4, 4, 4, 4, 4, 4, 4, 4, 4, 4, 4, 4, 4};  // planes per thread, by level
   // kernel timing (diagnostics): launches of the kernels in kt_mask are bracketed by event pairs
   uint64_t kt_mask = 0;
   std::vector<cudaEvent_t> kt_ev;                   // 2 per recorded launch, reused
