@@ -61,6 +61,9 @@ extern "C" {
 #define PIC_F_MIXED_MG 0x80u    /* a8: FP32 V-cycles with FP64 residual refinement (else FP64 V-cycles) */
 #define PIC_F_FAST_INTEGRAL 0x100u  /* a1: Gamow quadrature and turning points in FP32 (J, P_N to ~1e-5
                                        relative) in the step and in pic_emission_eval; else all FP64 */
+#define PIC_F_GRAPH 0x200u      /* pic_step replays a CUDA graph of one step (the Poisson loop a device-side
+                                   while node); the first call with new flags runs one step eagerly and
+                                   records the graph; results equal the eager form's bit for bit */
 #define PIC_F_ALL 0xFFu         /* every stage, surrogate and mixed-precision solve; not FAST_INTEGRAL */
 
 typedef struct {

@@ -20,6 +20,7 @@
 // 6 neighbours of (i, j, k) sit at slots (i -+ 1) >> 1 of its own row and i >> 1 of the four
 // rows around it, all in the other colour.
 #include <math.h>
+#include <string.h>
 
 #include <algorithm>
 #include <vector>
@@ -745,54 +746,154 @@ int mg_coarse_setup(pic_t *h) {
   return PIC_OK;
 }
 
-// Solve for phi with the current deposited charge (or none), anode at V0.
-int stage_solve(pic_t *h, bool zero_charge, double V0) {
+// Fixed-point charge scale and launch shape of the refinement (shared by both forms of the solve).
+struct SolveSetup {
+  unsigned long long Kfx;
+  int S;
+  dim3 rg;
+  int64_t nb;
+  double c_fx;
+  bool mixed;
+  float V0f;
+};
+
+// Dirichlet values on phi for V0 (only when they changed) and the charge factor
+// K = e w_min 2^10 / (dx eps0) as Kw = K 2^S in [2^59, 2^60].
+static int solve_setup(pic_t *h, double V0, SolveSetup *ss) {
   MgLevel &L = h->mg[0];
-  const Lv lv = lv_of(L);
   const long long V0fx = llrint(V0 * kPhiScale);
-  if (!h->dirichlet_valid || h->dirichlet_V0fx != V0fx) {   // the Dirichlet values change only here
+  if (!h->dirichlet_valid || h->dirichlet_V0fx != V0fx) {
+    if (h->capturing) return pic_fail(h, PIC_E_INVALID, "Dirichlet values must be set before graph capture");
     ++h->nlaunch;
     { KtScope kt_(h, kidDirichlet, (double)h->nnode); k_dirichlet<<<node_grid3(h->nx, h->ny, h->nz), node_block(), 0, h->stream>>>(h->phi, L.dir, h->nx, h->ny, h->nz, V0fx); }
     h->dirichlet_valid = true;
     h->dirichlet_V0fx = V0fx;
   }
-  // charge factor K = e w_min 2^10 / (dx eps0) as Kw = K 2^S in [2^59, 2^60]
   const double K = kQe * h->prm.w_min * 1024.0 / (h->dx * kEps0);
   const int S = 59 - (int)floor(log2(K));
   if (!(K > 0) || S < 1 || S > 63) return pic_fail(h, PIC_E_INVALID, "charge scale e w_min / (dx eps0) out of range");
-  const unsigned long long Kfx = (unsigned long long)llround(ldexp(K, S));
-  const dim3 rg((h->nx + 1 + 31) / 32, (h->ny + 1 + 7) / 8, (h->nz + kKZ) / kKZ);
-  const int64_t nb = (int64_t)rg.x * rg.y * rg.z;
-  const double inv_h2 = 1.0 / (h->dx * h->dx), c_fx = inv_h2 * kPhiUnit;
-  const bool mixed = (h->prm.flags & PIC_F_MIXED_MG) != 0;
+  ss->Kfx = (unsigned long long)llround(ldexp(K, S));
+  ss->S = S;
+  ss->rg = dim3((h->nx + 1 + 31) / 32, (h->ny + 1 + 7) / 8, (h->nz + kKZ) / kKZ);
+  ss->nb = (int64_t)ss->rg.x * ss->rg.y * ss->rg.z;
+  ss->c_fx = 1.0 / (h->dx * h->dx) * kPhiUnit;
+  ss->mixed = (h->prm.flags & PIC_F_MIXED_MG) != 0;
+  ss->V0f = (float)V0;
+  return PIC_OK;
+}
+
+// residual of the fixed-point system onto the finest level and its two norms in red_out
+static void residual_pass(pic_t *h, const SolveSetup &ss, bool zero_charge, bool lift) {
+  MgLevel &L = h->mg[0];
+  const Lv lv = lv_of(L);
+  ++h->nlaunch;
+  if (ss.mixed)
+    { KtScope kt_(h, kidResidual64, (double)h->nnode); k_residual64<float><<<ss.rg, node_block(), 0, h->stream>>>(h->phi, h->Q, ss.Kfx, ss.S, zero_charge ? 1 : 0, L.f, L.dir, lv, (float)ss.c_fx, ss.V0f, h->red, lift ? 1 : 0); }
+  else
+    { KtScope kt_(h, kidResidual64, (double)h->nnode); k_residual64<double><<<ss.rg, node_block(), 0, h->stream>>>(h->phi, h->Q, ss.Kfx, ss.S, zero_charge ? 1 : 0, L.fd, L.dir, lv, ss.c_fx, ss.V0f, h->red, lift ? 1 : 0); }
+  h->nlaunch += 2;
+  { KtScope kt_(h, kidNormSum, (double)ss.nb); k_sum_stage1<<<kSumChunks, 256, 0, h->stream>>>(h->red, ss.nb, h->red_mid); }
+  k_sum_stage2<<<1, kSumChunks, 0, h->stream>>>(h->red_mid, h->red_out);
+}
+
+// Solve for phi with the current deposited charge (or none), anode at V0: refinement cycles
+// until the relative residual reaches mg_tol, decided on the host after each residual.
+int stage_solve(pic_t *h, bool zero_charge, double V0) {
+  SolveSetup ss;
+  PIC_TRY(solve_setup(h, V0, &ss));
   double norms[2] = {0, 0};
   double lifted = 0.0;
-  int cyc = 0;
-  const float V0f = (float)V0;
-  for (;; ++cyc) {
-    ++h->nlaunch;
-    if (mixed)
-      { KtScope kt_(h, kidResidual64, (double)h->nnode); k_residual64<float><<<rg, node_block(), 0, h->stream>>>(h->phi, h->Q, Kfx, S, zero_charge ? 1 : 0, L.f, L.dir, lv, (float)c_fx, V0f, h->red, cyc == 0 ? 1 : 0); }
-    else
-      { KtScope kt_(h, kidResidual64, (double)h->nnode); k_residual64<double><<<rg, node_block(), 0, h->stream>>>(h->phi, h->Q, Kfx, S, zero_charge ? 1 : 0, L.fd, L.dir, lv, c_fx, V0f, h->red, cyc == 0 ? 1 : 0); }
-    h->nlaunch += 2;
-    { KtScope kt_(h, kidNormSum, (double)nb); k_sum_stage1<<<kSumChunks, 256, 0, h->stream>>>(h->red, nb, h->red_mid); }
-    k_sum_stage2<<<1, kSumChunks, 0, h->stream>>>(h->red_mid, h->red_out);
+  for (int cyc = 0;; ++cyc) {
+    residual_pass(h, ss, zero_charge, cyc == 0);
     PIC_CUDA(h, cudaMemcpyAsync(norms, h->red_out, sizeof norms, cudaMemcpyDeviceToHost, h->stream));
     PIC_CUDA(h, cudaStreamSynchronize(h->stream));
     if (cyc == 0) lifted = sqrt(norms[1]);
     const double rel = lifted > 0 ? sqrt(norms[0]) / lifted : sqrt(norms[0]);
     h->last_mg_res = rel;
     h->last_mg_cycles = cyc;
+    h->last_solve_graph = false;
     if (rel <= h->prm.mg_tol) break;
     if (cyc >= h->prm.mg_max_cycles) {
       PIC_TRY(stage_efield(h));
       return pic_fail(h, PIC_E_NOCONV, "Poisson solve: relative residual " + std::to_string(rel) + " after " +
                                            std::to_string(cyc) + " cycles");
     }
-    if (mixed) cycle_fine<float>(h);
+    if (ss.mixed) cycle_fine<float>(h);
     else cycle_fine<double>(h);
   }
+  return stage_efield(h);
+}
+
+// Device-side convergence test of the graph form (one thread): first = 1 takes the lifted norm of
+// this solve, otherwise one more cycle has run.  The graph's while node repeats (V-cycle,
+// correction, residual, test) for as long as this sets its condition to 1; the cycle cap ends it
+// with the no-convergence error bit.
+__global__ void k_mg_check(const double *norms, DevClock *clk, double tol, int max_cycles, int first,
+                           cudaGraphConditionalHandle cond) {
+  if (first) {
+    clk->mg_lifted = sqrt(norms[1]);
+    clk->mg_cycles_last = 0;
+  } else {
+    clk->mg_cycles_last += 1;
+    clk->mg_graph_cycles += 1;
+  }
+  const double Lf = clk->mg_lifted;
+  const double rel = Lf > 0 ? sqrt(norms[0]) / Lf : sqrt(norms[0]);
+  clk->mg_rel_last = (float)rel;
+  bool more = !(rel <= tol);
+  if (more && clk->mg_cycles_last >= max_cycles) {
+    more = false;
+    clk->err |= kErrNoconv;
+  }
+  cudaGraphSetConditional(cond, more ? 1u : 0u);
+}
+
+// The same solve recorded into the graph being captured on h->stream: residual and test, then a
+// conditional while node whose body (captured on h->body_stream) is one refinement cycle and the
+// next test.  The decision never leaves the device.
+int stage_solve_graph(pic_t *h, double V0) {
+  SolveSetup ss;
+  PIC_TRY(solve_setup(h, V0, &ss));
+  residual_pass(h, ss, false, true);
+  cudaStreamCaptureStatus st;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t *deps = nullptr;
+  size_t nd = 0;
+  PIC_CUDA(h, cudaStreamGetCaptureInfo(h->stream, &st, nullptr, &g, &deps, nullptr, &nd));
+  if (st != cudaStreamCaptureStatusActive) return pic_fail(h, PIC_E_INVALID, "graph solve outside a capture");
+  cudaGraphConditionalHandle cond;
+  PIC_CUDA(h, cudaGraphConditionalHandleCreate(&cond, g, 0, 0));
+  ++h->nlaunch;
+  k_mg_check<<<1, 1, 0, h->stream>>>(h->red_out, h->clock, h->prm.mg_tol, h->prm.mg_max_cycles, 1, cond);
+  PIC_TRY(launch_check(h, "mg_check"));
+  PIC_CUDA(h, cudaStreamGetCaptureInfo(h->stream, &st, nullptr, &g, &deps, nullptr, &nd));
+  cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};
+  np.conditional.handle = cond;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node;
+  PIC_CUDA(h, cudaGraphAddNode(&node, g, deps, nullptr, nd, &np));
+  cudaGraph_t body = np.conditional.phGraph_out[0];
+  PIC_CUDA(h, cudaStreamUpdateCaptureDependencies(h->stream, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+  cudaStream_t outer = h->stream;
+  h->stream = h->body_stream;
+  const int64_t n0 = h->nlaunch;
+  cudaError_t e = cudaStreamBeginCaptureToGraph(h->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+  if (e == cudaSuccess) {
+    if (ss.mixed) cycle_fine<float>(h);
+    else cycle_fine<double>(h);
+    residual_pass(h, ss, false, false);
+    ++h->nlaunch;
+    k_mg_check<<<1, 1, 0, h->stream>>>(h->red_out, h->clock, h->prm.mg_tol, h->prm.mg_max_cycles, 0, cond);
+    cudaGraph_t tmp = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(h->stream, &tmp);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGetLastError();
+  }
+  h->graph_body_launches = h->nlaunch - n0;
+  h->stream = outer;
+  if (e != cudaSuccess) return pic_fail(h, PIC_E_CUDA, std::string("solve loop capture: ") + cudaGetErrorString(e));
+  h->last_solve_graph = true;
   return stage_efield(h);
 }
 

@@ -572,6 +572,7 @@ extern "C" {
 int pic_mlp_num_params(void) { return kNParam; }
 
 int pic_mlp_set_params(pic_t *h, const float *params) {
+  if (h) graph_invalidate(h);   // its buffers may be reallocated
   if (!h || !params) return PIC_E_INVALID;
   MlpState &S = mlp_of(h);
   PIC_TRY(ensure(h, S, 1024));
@@ -593,6 +594,7 @@ int pic_mlp_get_params(pic_t *h, float *params) {
 // x: n x 7 standardised features (host, float); y: n x 2 outputs; optional t (n x 2 targets):
 // then loss (mean over rows of sum 0.5 (y - t)^2) and grad (parameter layout) are returned too.
 int pic_mlp_forward_backward(pic_t *h, const float *x, const float *t, int64_t n, float *y, float *loss, float *grad) {
+  if (h) graph_invalidate(h);   // its buffers may be reallocated
   if (!h || !x || n <= 0 || n > (1 << 22)) return PIC_E_INVALID;
   MlpState &S = mlp_of(h);
   PIC_TRY(ensure(h, S, n));
@@ -630,6 +632,7 @@ int pic_mlp_forward_backward(pic_t *h, const float *x, const float *t, int64_t n
 // stats (optional, 8 doubles): train loss, val RMS |dlog10 J|, val max |dlog10 J| (relevant),
 // fraction of valid bins, fraction of valid held-out samples, ms data, ms train, steps.
 int pic_surrogate_train(pic_t *h, int64_t nsamples, int epochs, int batch, double lr0, uint64_t seed, double *stats) {
+  if (h) graph_invalidate(h);   // its buffers may be reallocated
   if (!h || nsamples < 1024 || epochs < 1 || batch < 256 || batch > 65536) return PIC_E_INVALID;
   MlpState &S = mlp_of(h);
   const int64_t nval = std::max<int64_t>(nsamples / 2, 4096);
@@ -773,6 +776,7 @@ int pic_surrogate_train(pic_t *h, int64_t nsamples, int epochs, int batch, doubl
 // validation bin passed (elsewhere the step uses the full integral).
 int pic_surrogate_eval(pic_t *h, const double *F, const double *T, const double *phi_w, const double *R, double *J,
                        double *PN, uint8_t *valid, int64_t n) {
+  if (h) graph_invalidate(h);   // its buffers may be reallocated
   if (!h || n <= 0 || !F || !T || !phi_w || !R || !J || !PN) return PIC_E_INVALID;
   MlpState &S = mlp_of(h);
   if (!S.trained) return pic_fail(h, PIC_E_INVALID, "surrogate not trained");

@@ -235,6 +235,8 @@ void kt_collect(pic_t *h) {
 
 using namespace pic;
 
+static void graph_free(pic_t *h);
+
 extern "C" {
 
 const char *pic_last_error(pic_t *h) { return h ? h->last_error.c_str() : "null handle"; }
@@ -243,6 +245,8 @@ void pic_destroy(pic_t *h) {
   if (!h) return;
   cudaStreamSynchronize(h->stream);
   for (cudaEvent_t e : h->kt_ev) cudaEventDestroy(e);
+  graph_free(h);
+  if (h->body_stream) cudaStreamDestroy(h->body_stream);
   mlp_forget(h);
   dfree_all(h);
   delete h;
@@ -264,6 +268,7 @@ static int check_err(pic_t *h) {
     PIC_CUDA(h, cudaStreamSynchronize(h->stream));
     if (e & kErrCapacity) return pic_fail(h, PIC_E_CAPACITY, "SP capacity exceeded: new SPs were not added");
     if (e & kErrSegment) return pic_fail(h, PIC_E_CAPACITY, "more SPs of one species in one cell than the sort handles");
+    if (e & kErrNoconv) return pic_fail(h, PIC_E_NOCONV, "Poisson solve did not reach mg_tol within mg_max_cycles");
     return pic_fail(h, PIC_E_INVALID, "device error flag " + std::to_string(e));
   }
   return PIC_OK;
@@ -582,6 +587,7 @@ int pic_set_potential(pic_t *h, const double *phi) {
     ++h->nlaunch;
     k_phi_from_double<<<grid_for(h->nnode), kThreads, 0, h->stream>>>(buf, h->phi, h->nnode);
     h->dirichlet_valid = false;
+    graph_free(h);
     rc = stage_efield(h);
   }
   if (rc == PIC_OK && cudaStreamSynchronize(h->stream) != cudaSuccess) rc = PIC_E_CUDA;
@@ -706,6 +712,7 @@ int pic_sort(pic_t *h);
 int pic_set_flags(pic_t *h, uint32_t flags) {
   if (!h) return PIC_E_INVALID;
   h->prm.flags = flags;
+  graph_free(h);
   return PIC_OK;
 }
 
@@ -789,11 +796,160 @@ __global__ void k_begin_step(DevClock *clk) {
 }
 __global__ void k_end_step(DevClock *clk) { clk->step += 1; }
 
+}  // extern "C"
+
+// ---- graph form of the step ---------------------------------------------------------------------
+// One step recorded into the graph being captured on h->stream: the stages in their eager order,
+// the Poisson loop as a conditional while node.  The heat stage is not part of it.
+static int step_body_graph(pic_t *h) {
+  ++h->nlaunch;
+  k_begin_step<<<1, 1, 0, h->stream>>>(h->clock);
+  PIC_TRY(stage_emit(h));
+  PIC_TRY(stage_push(h));
+  PIC_TRY(stage_sort(h));
+  PIC_TRY(stage_collide(h));
+  PIC_TRY(stage_deposit(h));
+  PIC_TRY(stage_solve_graph(h, h->V0));
+  ++h->nlaunch;
+  k_end_step<<<1, 1, 0, h->stream>>>(h->clock);
+  return launch_check(h, "step capture");
+}
+
+
+static void graph_free(pic_t *h) {
+  for (int p = 0; p < 2; ++p)
+    if (h->gexec[p]) {
+      cudaGraphExecDestroy(h->gexec[p]);
+      h->gexec[p] = nullptr;
+    }
+  h->graph_valid = false;
+}
+
+// Index of the graph whose particle buffers are the current ones, -1 if none
+static int graph_index(pic_t *h) {
+  for (int p = 0; p < 2; ++p) {
+    bool ok = h->gexec[p] != nullptr;
+    for (int s = 0; s < 3; ++s) ok = ok && h->graph_a[p][s] == h->sp[s].a.x;
+    if (ok) return p;
+  }
+  return -1;
+}
+
+namespace pic {
+void graph_invalidate(pic_t *h) {
+  graph_free(h);
+  h->eager_flags = 0xFFFFFFFFu;
+}
+
+// Records one graph per parity of the particle double buffers (the sort swaps them every step,
+// and a graph holds fixed addresses).  Nothing runs during the recording; the host-side buffer
+// assignment is restored afterwards.  Lazily allocated buffers must exist already: a graph is
+// built only after an eager step with the same flags (pic_step does that).
+int graph_build_capture(pic_t *h) {
+  graph_free(h);
+  if (!h->body_stream) PIC_CUDA(h, cudaStreamCreateWithFlags(&h->body_stream, cudaStreamNonBlocking));
+  for (int s = 0; s < 3; ++s)
+    if (h->keys_valid[s]) PIC_TRY(stage_sort(h));   // a step starts from sorted SPs
+  SpeciesBuf saved[3][2];
+  for (int s = 0; s < 3; ++s) { saved[s][0] = h->sp[s].a; saved[s][1] = h->sp[s].b; }
+  const uint64_t kt = h->kt_mask;
+  h->kt_mask = 0;
+  const int64_t n0 = h->nlaunch;
+  int rc = PIC_OK;
+  for (int p = 0; p < 2 && rc == PIC_OK; ++p) {
+    for (int s = 0; s < 3; ++s) h->graph_a[p][s] = h->sp[s].a.x;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) { rc = pic_fail(h, PIC_E_CUDA, std::string("begin capture: ") + cudaGetErrorString(e)); break; }
+    h->capturing = true;
+    const int64_t m0 = h->nlaunch;
+    rc = step_body_graph(h);
+    h->capturing = false;
+    e = cudaStreamEndCapture(h->stream, &g);
+    if (rc == PIC_OK && e != cudaSuccess) rc = pic_fail(h, PIC_E_CUDA, std::string("end capture: ") + cudaGetErrorString(e));
+    if (rc == PIC_OK) {
+      e = cudaGraphInstantiate(&h->gexec[p], g, 0);
+      if (e != cudaSuccess) rc = pic_fail(h, PIC_E_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    }
+    if (g) cudaGraphDestroy(g);
+    h->graph_outer_launches = h->nlaunch - m0 - h->graph_body_launches;
+  }
+  cudaGetLastError();
+  h->nlaunch = n0;
+  h->kt_mask = kt;
+  for (int s = 0; s < 3; ++s) { h->sp[s].a = saved[s][0]; h->sp[s].b = saved[s][1]; h->keys_valid[s] = false; }
+  if (rc != PIC_OK) { graph_free(h); return rc; }
+  h->graph_valid = true;
+  h->graph_flags = h->prm.flags;
+  return PIC_OK;
+}
+
+// Launch the graph of the current parity (one step) and advance the host-side buffer assignment.
+int graph_launch_step(pic_t *h) {
+  const int p = graph_index(h);
+  if (p < 0) return pic_fail(h, PIC_E_INVALID, "no step graph for the current particle buffers");
+  PIC_CUDA(h, cudaGraphLaunch(h->gexec[p], h->stream));
+  for (int s = 0; s < 3; ++s) std::swap(h->sp[s].a, h->sp[s].b);
+  h->nlaunch += h->graph_outer_launches;
+  return PIC_OK;
+}
+
+}  // namespace pic
+
+static int pic_step_graph(pic_t *h, int nsteps, int64_t step) {
+  if (!h->graph_valid || h->graph_flags != h->prm.flags || graph_index(h) < 0) PIC_TRY(graph_build_capture(h));
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventRecord(e0, h->stream);
+  int rc = PIC_OK;
+  for (int it = 0; it < nsteps && rc == PIC_OK; ++it) {
+    rc = graph_launch_step(h);
+    ++step;
+    if (rc == PIC_OK && (h->prm.flags & PIC_F_HEAT) && h->prm.n_heat > 0 && step % h->prm.n_heat == 0) rc = stage_heat(h);
+  }
+  cudaEventRecord(e1, h->stream);
+  cudaEventSynchronize(e1);
+  float t = 0.f;
+  cudaEventElapsedTime(&t, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc == PIC_OK && nsteps > 0) {
+    for (int i = 0; i < 7; ++i) h->ms[i] = 0.f;   // the stages of a graph are not timed apart
+    h->ms[7] = t;
+  }
+  if (rc != PIC_OK) return rc;
+  PIC_TRY(launch_check(h, "graph step"));
+  return check_err(h);
+}
+
+static int pic_step_eager(pic_t *h, int nsteps, int64_t step);
+
+extern "C" {
+
 int pic_step(pic_t *h, int nsteps) {
   if (!h || nsteps < 0) return PIC_E_INVALID;
   DevClock c;
   PIC_TRY(clock_sync(h, &c));
   int64_t step = c.step;
+  bool sorted = true;
+  for (int s = 0; s < 3; ++s) sorted = sorted && !h->keys_valid[s];
+  if ((h->prm.flags & PIC_F_GRAPH) && sorted && nsteps > 0) {
+    // a graph is recorded only after an eager step with the same flags (lazily allocated buffers)
+    if (h->eager_flags != h->prm.flags) {
+      PIC_TRY(pic_step_eager(h, 1, step));
+      ++step;
+      --nsteps;
+    }
+    return nsteps > 0 ? pic_step_graph(h, nsteps, step) : PIC_OK;
+  }
+  return pic_step_eager(h, nsteps, step);
+}
+
+}  // extern "C"
+
+// the step stage by stage from the host, with per-stage event timing
+static int pic_step_eager(pic_t *h, int nsteps, int64_t step) {
   cudaEvent_t ev[8];
   for (int i = 0; i < 8; ++i) cudaEventCreate(&ev[i]);
   float acc_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
@@ -838,8 +994,12 @@ int pic_step(pic_t *h, int nsteps) {
   for (int i = 0; i < 8; ++i) cudaEventDestroy(ev[i]);
   if (rc != PIC_OK) return rc;
   PIC_TRY(launch_check(h, "step"));
-  return check_err(h);
+  PIC_TRY(check_err(h));
+  if (nsteps > 0) h->eager_flags = h->prm.flags;
+  return PIC_OK;
 }
+
+extern "C" {
 
 __global__ void k_sum_w(const int32_t *w, const DevClock *clk, int s, unsigned long long *out) {
   const int64_t n = clk->n[s];
@@ -884,8 +1044,8 @@ int pic_diagnostics(pic_t *h, pic_diag_t *out) {
   out->impact_ionizations = c.ctr[cImpactIon];
   out->field_ionizations = c.ctr[cFieldIon];
   out->ion_impacts = c.ctr[cIonImpacts];
-  out->mg_cycles = h->last_mg_cycles;
-  out->mg_residual = h->last_mg_res;
+  out->mg_cycles = h->last_solve_graph ? c.mg_cycles_last : h->last_mg_cycles;
+  out->mg_residual = h->last_solve_graph ? (double)c.mg_rel_last : h->last_mg_res;
   out->V0 = h->V0;
   const int64_t nf = h->faces.n;
   if (nf) {
@@ -906,7 +1066,7 @@ int pic_diagnostics(pic_t *h, pic_diag_t *out) {
     out->max_T = *std::max_element(T.begin(), T.end());
   }
   for (int i = 0; i < 8; ++i) out->ms[i] = h->ms[i];
-  out->kernel_launches = h->nlaunch;
+  out->kernel_launches = h->nlaunch + c.mg_graph_cycles * h->graph_body_launches;
   out->emission_evals = c.ctr[cWevals];
   out->surrogate_faces = c.ctr[cSurFaces];
   return PIC_OK;

@@ -188,6 +188,8 @@ struct pic_s {
   cudaGraphExec_t gexec[2] = {nullptr, nullptr};
   float *graph_a[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};  // S.a.x at capture
   bool graph_valid = false;
+  uint32_t graph_flags = 0;              // flags the graphs were recorded with
+  uint32_t eager_flags = 0xFFFFFFFFu;   // flags of the last eager step (none yet)
   int64_t graph_outer_launches = 0, graph_body_launches = 0;
   cudaStream_t body_stream = nullptr;   // capture stream of the Poisson loop body
   bool capturing = false;               // stage code is being recorded into a graph
@@ -329,6 +331,10 @@ int emission_eval_dev(pic_t *h, const double *F, const double *T, const double *
 // field (k_field.cu)
 int stage_efield(pic_t *h);
 int stage_solve(pic_t *h, bool zero_charge, double V0);
+int stage_solve_graph(pic_t *h, double V0);
+int graph_build_capture(pic_t *h);
+void graph_invalidate(pic_t *h);   // drop recorded step graphs (buffers they hold may change)
+int graph_launch_step(pic_t *h);
 int face_field_mean(pic_t *h, const int64_t *faces, int nf, double *out);
 int mg_coarse_setup(pic_t *h);
 // heat (k_heat.cu)

@@ -17,6 +17,7 @@ F_EMISSION, F_EVAP, F_SPUTTER, F_IMPACT_ION, F_DFI, F_HEAT, F_SURROGATE, F_MIXED
     0x01, 0x02, 0x04, 0x08, 0x10, 0x20, 0x40, 0x80)
 F_ALL = 0xFF
 F_FAST_INTEGRAL = 0x100
+F_GRAPH = 0x200
 F_PRODUCTION = F_ALL | F_FAST_INTEGRAL     # surrogate, FP32 Gamow quadrature for its fallback, mixed MG
 
 QE = 1.602176634e-19
