@@ -247,6 +247,7 @@ void pic_destroy(pic_t *h) {
   for (cudaEvent_t e : h->kt_ev) cudaEventDestroy(e);
   graph_free(h);
   if (h->body_stream) cudaStreamDestroy(h->body_stream);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   mlp_forget(h);
   dfree_all(h);
   delete h;
@@ -848,6 +849,7 @@ void graph_invalidate(pic_t *h) {
 int graph_build_capture(pic_t *h) {
   graph_free(h);
   if (!h->body_stream) PIC_CUDA(h, cudaStreamCreateWithFlags(&h->body_stream, cudaStreamNonBlocking));
+  if (!h->cap_stream) PIC_CUDA(h, cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
   for (int s = 0; s < 3; ++s)
     if (h->keys_valid[s]) PIC_TRY(stage_sort(h));   // a step starts from sorted SPs
   SpeciesBuf saved[3][2];
@@ -858,14 +860,23 @@ int graph_build_capture(pic_t *h) {
   int rc = PIC_OK;
   for (int p = 0; p < 2 && rc == PIC_OK; ++p) {
     for (int s = 0; s < 3; ++s) h->graph_a[p][s] = h->sp[s].a.x;
+    // recorded on a private stream (the caller's may be the legacy stream, which cannot be
+    // captured); the graph is launched on the caller's stream
     cudaGraph_t g = nullptr;
+    cudaStream_t user = h->stream;
+    h->stream = h->cap_stream;
     cudaError_t e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeRelaxed);
-    if (e != cudaSuccess) { rc = pic_fail(h, PIC_E_CUDA, std::string("begin capture: ") + cudaGetErrorString(e)); break; }
+    if (e != cudaSuccess) {
+      h->stream = user;
+      rc = pic_fail(h, PIC_E_CUDA, std::string("begin capture: ") + cudaGetErrorString(e));
+      break;
+    }
     h->capturing = true;
     const int64_t m0 = h->nlaunch;
     rc = step_body_graph(h);
     h->capturing = false;
     e = cudaStreamEndCapture(h->stream, &g);
+    h->stream = user;
     if (rc == PIC_OK && e != cudaSuccess) rc = pic_fail(h, PIC_E_CUDA, std::string("end capture: ") + cudaGetErrorString(e));
     if (rc == PIC_OK) {
       e = cudaGraphInstantiate(&h->gexec[p], g, 0);

@@ -192,6 +192,7 @@ struct pic_s {
   uint32_t eager_flags = 0xFFFFFFFFu;   // flags of the last eager step (none yet)
   int64_t graph_outer_launches = 0, graph_body_launches = 0;
   cudaStream_t body_stream = nullptr;   // capture stream of the Poisson loop body
+  cudaStream_t cap_stream = nullptr;    // capture stream of the step graphs
   bool capturing = false;               // stage code is being recorded into a graph
   bool last_solve_graph = false;        // the last solve ran in a graph (its diagnostics are on the device)
   // autotuned launch shapes
