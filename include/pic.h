@@ -188,6 +188,32 @@ int pic_heat(pic_t *h);        /* a10 continuity + heat on the tip cells from th
 int pic_step(pic_t *h, int nsteps);
 int pic_diagnostics(pic_t *h, pic_diag_t *out);
 
+/* Ensemble of independent instances (the paper has no counterpart; it runs one tip at a time).
+ * pic_batch_create groups n distinct handles that share one stream (PIC_E_INVALID otherwise); the
+ * handles stay owned by the caller and must outlive the batch.  pic_batch_step advances every
+ * instance by nsteps full steps with ONE CUDA-graph launch per step: the graph holds one branch per
+ * instance (independent, so the GPU runs them concurrently), each branch the instance's step with
+ * its Poisson loop as a device-side while node.  The first call (and any call after an instance's
+ * flags or buffers changed) runs one eager step per instance and records the graphs.  Each
+ * instance's results equal those of pic_step on it alone, bit for bit.  The heat stage runs
+ * between graph launches every n_heat steps of each instance.  Errors name the instance in
+ * pic_batch_last_error.  pic_batch_ms returns the device time of the last pic_batch_step [ms]. */
+typedef struct pic_batch_s pic_batch_t;
+int pic_batch_create(pic_t *const *instances, int n, pic_batch_t **out);
+int pic_batch_step(pic_batch_t *b, int nsteps);
+int pic_batch_ms(pic_batch_t *b, double *ms);
+const char *pic_batch_last_error(pic_batch_t *b);
+void pic_batch_destroy(pic_batch_t *b);
+
+/* Autotuner (no counterpart in the paper): times the launch-shape candidates on this instance's
+ * current state and keeps the fastest -- blocks per SM of the particle kernels (2..32, probed on
+ * the charge deposit, which it leaves as a deposit would) and, per multigrid level, the
+ * smoother's planes per thread (1, 2, 4 or 8, probed on the level's correction, which every solve
+ * rebuilds).  No result depends on the choices.  choices[0] receives the blocks per SM and
+ * choices[1 + l] the planes per thread of level l; returns the number of values written (at most
+ * cap) or a negative PIC_E_* code. */
+int pic_autotune(pic_t *h, int *choices, int cap);
+
 /* Kernel timing (diagnostics of the library; the paper has no counterpart).  pic_num_kernels()
  * kernels are known by index (pic_kernel_name: "k_push", "k_smooth", ...).  pic_set_kernel_timing
  * selects kernels by bit mask (bit k = kernel k, 0 = none) and clears the sums; from then on every

@@ -746,6 +746,42 @@ int mg_coarse_setup(pic_t *h) {
   return PIC_OK;
 }
 
+// Autotuner probe for the smoother: on every level but the coarsest, time 4 colour sweeps of
+// each planes-per-thread candidate (1, 2, 4, 8) on the level's FP32 arrays and keep the fastest.
+// The sweeps only change the level's correction, which every solve rebuilds from zero.
+int tune_smoother(pic_t *h, int *best, int cap) {
+  const int cand[4] = {1, 2, 4, 8};
+  cudaEvent_t e0, e1;
+  PIC_CUDA(h, cudaEventCreate(&e0));
+  PIC_CUDA(h, cudaEventCreate(&e1));
+  const int nl = (int)h->mg.size() - 1;
+  for (int l = 0; l < nl && l < 16; ++l) {
+    MgLevel &L = h->mg[l];
+    const Lv lv = lv_of(L);
+    const float h2 = (float)(L.h * L.h);
+    float best_ms = 1e30f;
+    int pick = h->tune_smooth_kz[l];
+    for (int kz : cand) {
+      float t_min = 1e30f;
+      for (int rep = 0; rep < 3; ++rep) {
+        cudaEventRecord(e0, h->stream);
+        for (int c = 0; c < 4; ++c) smooth_launch<float>(h, L, lv, h2, c & 1, false, kz);
+        cudaEventRecord(e1, h->stream);
+        cudaEventSynchronize(e1);
+        float t = 0.f;
+        cudaEventElapsedTime(&t, e0, e1);
+        t_min = std::min(t_min, t);
+      }
+      if (t_min < best_ms) { best_ms = t_min; pick = kz; }
+    }
+    h->tune_smooth_kz[l] = pick;
+    if (l < cap) best[l] = pick;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return launch_check(h, "tune smoother");
+}
+
 // Fixed-point charge scale and launch shape of the refinement (shared by both forms of the solve).
 struct SolveSetup {
   unsigned long long Kfx;

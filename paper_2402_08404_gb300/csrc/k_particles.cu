@@ -4,6 +4,8 @@
 // Push arithmetic is float32 with every operation rounded on its own (no fused multiply-add),
 // in a fixed order: the new cell keys, boundary events and deposits are integer decisions
 // taken from the pushed positions, so the order is part of the definition.
+#include <algorithm>
+
 #include "pic_internal.cuh"
 #include "dev_common.cuh"
 
@@ -360,7 +362,7 @@ __global__ void __launch_bounds__(256) k_deposit(SpeciesBuf p, int Z, unsigned l
   }
 }
 
-static int particle_grid(pic_t *h) { return h->nsm * 8; }
+static int particle_grid(pic_t *h) { return h->nsm * h->tune_particle_bps; }
 
 int stage_keys(pic_t *h, int s) {
   Species &S = h->sp[s];
@@ -428,6 +430,40 @@ int stage_deposit(pic_t *h) {
   ++h->nlaunch;
   { KtScope kt_(h, kidDeposit, 0); k_deposit<<<particle_grid(h), kThreads, 0, h->stream>>>(h->sp[PIC_ION].a, 1, h->Q, h->nx, h->ny, h->clock, PIC_ION); }
   return launch_check(h, "deposit");
+}
+
+// Autotuner probe for the particle kernels' grid (blocks per SM): each candidate times the
+// deposit (clear + e- and Cu+ launches; the fixed-point sums do not depend on the launch shape,
+// so the probe leaves the charge as a deposit would) and the fastest is kept for every
+// particle kernel.  All of them are grid-stride loops whose results do not depend on the grid.
+int tune_particles(pic_t *h, int *best) {
+  const int cand[5] = {2, 4, 8, 16, 32};
+  cudaEvent_t e0, e1;
+  PIC_CUDA(h, cudaEventCreate(&e0));
+  PIC_CUDA(h, cudaEventCreate(&e1));
+  const int keep = h->tune_particle_bps;
+  float best_ms = 1e30f;
+  int pick = keep;
+  for (int c : cand) {
+    h->tune_particle_bps = c;
+    float t_min = 1e30f;
+    for (int rep = 0; rep < 3; ++rep) {
+      cudaEventRecord(e0, h->stream);
+      const int rc = stage_deposit(h);
+      cudaEventRecord(e1, h->stream);
+      if (rc != PIC_OK) { h->tune_particle_bps = keep; cudaEventDestroy(e0); cudaEventDestroy(e1); return rc; }
+      cudaEventSynchronize(e1);
+      float t = 0.f;
+      cudaEventElapsedTime(&t, e0, e1);
+      t_min = std::min(t_min, t);
+    }
+    if (t_min < best_ms) { best_ms = t_min; pick = c; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  h->tune_particle_bps = pick;
+  *best = pick;
+  return launch_check(h, "tune particles");
 }
 
 }  // namespace pic

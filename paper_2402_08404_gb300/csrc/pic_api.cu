@@ -936,6 +936,234 @@ static int pic_step_graph(pic_t *h, int nsteps, int64_t step) {
 
 static int pic_step_eager(pic_t *h, int nsteps, int64_t step);
 
+// ---- ensemble of independent instances -----------------------------------------------------------
+struct pic_batch_s {
+  std::vector<pic_t *> inst;
+  cudaStream_t stream = nullptr;       // the instances' common stream
+  cudaStream_t cap = nullptr;          // private capture stream
+  cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+  std::vector<float *> graph_a[2];     // S.a.x of every instance and species at capture
+  cudaEvent_t fork = nullptr;
+  std::vector<cudaEvent_t> join;
+  bool valid = false;
+  std::vector<uint32_t> flags;         // each instance's flags at capture
+  float ms = 0.f;
+  std::string err;
+};
+
+static void batch_free_graphs(pic_batch_t *b) {
+  for (int p = 0; p < 2; ++p)
+    if (b->gexec[p]) {
+      cudaGraphExecDestroy(b->gexec[p]);
+      b->gexec[p] = nullptr;
+    }
+  b->valid = false;
+}
+
+static int batch_index(pic_batch_t *b) {
+  for (int p = 0; p < 2; ++p) {
+    if (!b->gexec[p]) continue;
+    bool ok = true;
+    for (size_t i = 0; i < b->inst.size() && ok; ++i)
+      for (int s = 0; s < 3; ++s) ok = ok && b->graph_a[p][3 * i + s] == b->inst[i]->sp[s].a.x;
+    for (size_t i = 0; i < b->inst.size() && ok; ++i) ok = b->flags[i] == b->inst[i]->prm.flags;
+    if (ok) return p;
+  }
+  return -1;
+}
+
+// One graph per buffer parity holding one step of every instance: the capture forks from the
+// batch's private stream into each instance's own capture stream and joins back, so the
+// instances form independent branches that the GPU runs concurrently; each branch holds its
+// instance's Poisson loop as a device-side while node.
+static int batch_capture(pic_batch_t *b) {
+  batch_free_graphs(b);
+  const size_t n = b->inst.size();
+  for (pic_t *h : b->inst) {
+    if (!h->body_stream && cudaStreamCreateWithFlags(&h->body_stream, cudaStreamNonBlocking) != cudaSuccess) return PIC_E_CUDA;
+    if (!h->cap_stream && cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess) return PIC_E_CUDA;
+    for (int s = 0; s < 3; ++s)
+      if (h->keys_valid[s]) PIC_TRY(stage_sort(h));
+  }
+  std::vector<SpeciesBuf> saved(2 * 3 * n);
+  std::vector<uint64_t> kt(n);
+  std::vector<int64_t> n0(n);
+  for (size_t i = 0; i < n; ++i) {
+    for (int s = 0; s < 3; ++s) { saved[6 * i + 2 * s] = b->inst[i]->sp[s].a; saved[6 * i + 2 * s + 1] = b->inst[i]->sp[s].b; }
+    kt[i] = b->inst[i]->kt_mask;
+    b->inst[i]->kt_mask = 0;
+    n0[i] = b->inst[i]->nlaunch;
+  }
+  int rc = PIC_OK;
+  for (int p = 0; p < 2 && rc == PIC_OK; ++p) {
+    b->graph_a[p].assign(3 * n, nullptr);
+    for (size_t i = 0; i < n; ++i)
+      for (int s = 0; s < 3; ++s) b->graph_a[p][3 * i + s] = b->inst[i]->sp[s].a.x;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) { b->err = std::string("begin capture: ") + cudaGetErrorString(e); rc = PIC_E_CUDA; break; }
+    if (cudaEventRecord(b->fork, b->cap) != cudaSuccess) rc = PIC_E_CUDA;
+    for (size_t i = 0; i < n && rc == PIC_OK; ++i) {
+      pic_t *h = b->inst[i];
+      cudaStream_t user = h->stream;
+      h->stream = h->cap_stream;
+      if (cudaStreamWaitEvent(h->stream, b->fork, 0) != cudaSuccess) rc = PIC_E_CUDA;
+      h->capturing = true;
+      const int64_t m0 = h->nlaunch;
+      if (rc == PIC_OK) rc = step_body_graph(h);
+      h->capturing = false;
+      h->graph_outer_launches = h->nlaunch - m0 - h->graph_body_launches;
+      if (rc == PIC_OK && cudaEventRecord(b->join[i], h->stream) != cudaSuccess) rc = PIC_E_CUDA;
+      if (rc == PIC_OK && cudaStreamWaitEvent(b->cap, b->join[i], 0) != cudaSuccess) rc = PIC_E_CUDA;
+      if (rc != PIC_OK) b->err = "instance " + std::to_string(i) + ": " + h->last_error;
+      h->stream = user;
+    }
+    e = cudaStreamEndCapture(b->cap, &g);
+    if (rc == PIC_OK && e != cudaSuccess) { b->err = std::string("end capture: ") + cudaGetErrorString(e); rc = PIC_E_CUDA; }
+    if (rc == PIC_OK && (e = cudaGraphInstantiate(&b->gexec[p], g, 0)) != cudaSuccess) {
+      b->err = std::string("graph instantiate: ") + cudaGetErrorString(e);
+      rc = PIC_E_CUDA;
+    }
+    if (g) cudaGraphDestroy(g);
+  }
+  cudaGetLastError();
+  for (size_t i = 0; i < n; ++i) {
+    pic_t *h = b->inst[i];
+    for (int s = 0; s < 3; ++s) { h->sp[s].a = saved[6 * i + 2 * s]; h->sp[s].b = saved[6 * i + 2 * s + 1]; h->keys_valid[s] = false; }
+    h->kt_mask = kt[i];
+    h->nlaunch = n0[i];
+  }
+  if (rc != PIC_OK) { batch_free_graphs(b); return rc; }
+  b->flags.resize(n);
+  for (size_t i = 0; i < n; ++i) b->flags[i] = b->inst[i]->prm.flags;
+  b->valid = true;
+  return PIC_OK;
+}
+
+extern "C" {
+
+int pic_batch_create(pic_t *const *instances, int n, pic_batch_t **out) {
+  if (!instances || n < 1 || !out) return PIC_E_INVALID;
+  *out = nullptr;
+  pic_batch_t *b = new pic_batch_t();
+  for (int i = 0; i < n; ++i) {
+    if (!instances[i]) { delete b; return PIC_E_INVALID; }
+    for (pic_t *o : b->inst)
+      if (o == instances[i]) { delete b; return PIC_E_INVALID; }   // each instance once
+    b->inst.push_back(instances[i]);
+  }
+  b->stream = b->inst[0]->stream;
+  for (pic_t *h : b->inst)
+    if (h->stream != b->stream) { delete b; return PIC_E_INVALID; }   // one common stream
+  bool ok = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) == cudaSuccess;
+  b->join.assign(n, nullptr);
+  for (int i = 0; i < n && ok; ++i) ok = cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) { pic_batch_destroy(b); return PIC_E_CUDA; }
+  *out = b;
+  return PIC_OK;
+}
+
+void pic_batch_destroy(pic_batch_t *b) {
+  if (!b) return;
+  if (b->stream || b->cap) cudaStreamSynchronize(b->stream);
+  batch_free_graphs(b);
+  if (b->fork) cudaEventDestroy(b->fork);
+  for (cudaEvent_t e : b->join)
+    if (e) cudaEventDestroy(e);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  delete b;
+}
+
+const char *pic_batch_last_error(pic_batch_t *b) { return b ? b->err.c_str() : "null batch"; }
+
+int pic_batch_step(pic_batch_t *b, int nsteps) {
+  if (!b || nsteps < 0) return PIC_E_INVALID;
+  if (nsteps == 0) return PIC_OK;
+  const size_t n = b->inst.size();
+  std::vector<int64_t> step(n);
+  for (size_t i = 0; i < n; ++i) {
+    DevClock c;
+    PIC_TRY(clock_sync(b->inst[i], &c));
+    step[i] = c.step;
+  }
+  // an instance records its graph only after an eager step with its current flags
+  bool eager = false;
+  for (pic_t *h : b->inst) {
+    bool sorted = true;
+    for (int s = 0; s < 3; ++s) sorted = sorted && !h->keys_valid[s];
+    eager = eager || h->eager_flags != h->prm.flags || !sorted;
+  }
+  if (eager) {
+    for (size_t i = 0; i < n; ++i) {
+      const int rc = pic_step_eager(b->inst[i], 1, step[i]);
+      if (rc != PIC_OK) { b->err = "instance " + std::to_string(i) + ": " + b->inst[i]->last_error; return rc; }
+      ++step[i];
+    }
+    if (--nsteps == 0) return PIC_OK;
+  }
+  if (!b->valid || batch_index(b) < 0) PIC_TRY(batch_capture(b));
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventRecord(e0, b->stream);
+  int rc = PIC_OK;
+  for (int it = 0; it < nsteps && rc == PIC_OK; ++it) {
+    const int p = batch_index(b);
+    if (p < 0) { b->err = "no ensemble graph for the current particle buffers"; rc = PIC_E_INVALID; break; }
+    if (cudaGraphLaunch(b->gexec[p], b->stream) != cudaSuccess) { b->err = "graph launch"; rc = PIC_E_CUDA; break; }
+    for (size_t i = 0; i < n; ++i) {
+      pic_t *h = b->inst[i];
+      for (int s = 0; s < 3; ++s) std::swap(h->sp[s].a, h->sp[s].b);
+      h->nlaunch += h->graph_outer_launches;
+      h->last_solve_graph = true;
+      ++step[i];
+      if ((h->prm.flags & PIC_F_HEAT) && h->prm.n_heat > 0 && step[i] % h->prm.n_heat == 0) {
+        rc = stage_heat(h);
+        if (rc != PIC_OK) { b->err = "instance " + std::to_string(i) + ": " + h->last_error; break; }
+      }
+    }
+  }
+  cudaEventRecord(e1, b->stream);
+  cudaEventSynchronize(e1);
+  cudaEventElapsedTime(&b->ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != PIC_OK) return rc;
+  for (size_t i = 0; i < n; ++i) {
+    const int r = check_err(b->inst[i]);
+    if (r != PIC_OK) { b->err = "instance " + std::to_string(i) + ": " + b->inst[i]->last_error; return r; }
+  }
+  return PIC_OK;
+}
+
+int pic_batch_ms(pic_batch_t *b, double *ms) {
+  if (!b || !ms) return PIC_E_INVALID;
+  *ms = b->ms;
+  return PIC_OK;
+}
+
+// Autotuner: time the launch-shape candidates of the particle kernels and of the smoother on
+// this instance's current state and keep the fastest; choices[0] receives the particle blocks
+// per SM, choices[1 + l] the smoother's planes per thread on level l.  Results do not depend on
+// the choices.  Returns the number of values written (<= cap) or a negative error code.
+int pic_autotune(pic_t *h, int *choices, int cap) {
+  if (!h || (cap > 0 && !choices)) return PIC_E_INVALID;
+  int bps = 0;
+  PIC_TRY(tune_particles(h, &bps));
+  int kz[16] = {0};
+  PIC_TRY(tune_smoother(h, kz, 16));
+  graph_invalidate(h);
+  int nw = 0;
+  if (cap > 0) choices[nw++] = bps;
+  const int nl = std::min<int>((int)h->mg.size() - 1, 16);
+  for (int l = 0; l < nl && nw < cap; ++l) choices[nw++] = kz[l];
+  return nw;
+}
+
+}  // extern "C"
+
+
 extern "C" {
 
 int pic_step(pic_t *h, int nsteps) {

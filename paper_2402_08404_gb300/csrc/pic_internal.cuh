@@ -196,7 +196,7 @@ struct pic_s {
   bool capturing = false;               // stage code is being recorded into a graph
   bool last_solve_graph = false;        // the last solve ran in a graph (its diagnostics are on the device)
   // autotuned launch shapes
-  int tune_dep_bps = 8;                 // deposit blocks per SM
+  int tune_particle_bps = 8;            // blocks per SM of the particle kernels (sort, push, deposit)
   int tune_smooth_kz[16] = {4, 4, 4, 4, 4, 4, 4, 4, 4, 4, 4, 4, 4, 4, 4, 4};  // planes per thread, by level
   // kernel timing (diagnostics): launches of the kernels in kt_mask are bracketed by event pairs
   uint64_t kt_mask = 0;
@@ -336,6 +336,9 @@ int stage_solve_graph(pic_t *h, double V0);
 int graph_build_capture(pic_t *h);
 void graph_invalidate(pic_t *h);   // drop recorded step graphs (buffers they hold may change)
 int graph_launch_step(pic_t *h);
+// autotuner probes: time the launch-shape candidates on the current state, keep the fastest
+int tune_particles(pic_t *h, int *best);
+int tune_smoother(pic_t *h, int *best, int cap);
 int face_field_mean(pic_t *h, const int64_t *faces, int nf, double *out);
 int mg_coarse_setup(pic_t *h);
 // heat (k_heat.cu)

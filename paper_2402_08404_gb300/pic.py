@@ -105,6 +105,14 @@ def lib():
         L.pic_mlp_forward_backward.argtypes = [vp, vp, vp, i64, vp, vp, vp]
         L.pic_surrogate_train.argtypes = [vp, i64, i32, i32, C.c_double, C.c_uint64, vp]
         L.pic_surrogate_eval.argtypes = [vp] * 8 + [i64]
+        L.pic_batch_create.argtypes = [C.POINTER(vp), i32, C.POINTER(vp)]
+        L.pic_batch_step.argtypes = [vp, i32]
+        L.pic_batch_ms.argtypes = [vp, dp]
+        L.pic_batch_last_error.argtypes = [vp]
+        L.pic_batch_last_error.restype = C.c_char_p
+        L.pic_batch_destroy.argtypes = [vp]
+        L.pic_batch_destroy.restype = None
+        L.pic_autotune.argtypes = [vp, C.POINTER(i32), i32]
         L.pic_num_kernels.argtypes = []
         L.pic_kernel_name.argtypes = [i32]
         L.pic_kernel_name.restype = C.c_char_p
@@ -310,6 +318,15 @@ class Pic:
             out[name] = list(v) if isinstance(v, C.Array) else v
         return out
 
+    # -- autotuner ------------------------------------------------------------------------------------
+    def autotune(self):
+        """pic_autotune: {"particle_blocks_per_sm": b, "smoother_planes_per_thread": [per level]}."""
+        buf = (C.c_int * 17)()
+        n = lib().pic_autotune(self.h, buf, 17)
+        if n < 0:
+            self._check(n)
+        return {"particle_blocks_per_sm": buf[0], "smoother_planes_per_thread": list(buf[1:n])}
+
     # -- kernel timing (diagnostics) ----------------------------------------------------------------
     @staticmethod
     def kernel_names():
@@ -390,3 +407,37 @@ class Pic:
         P = np.zeros(F.size)
         self._check(lib().pic_emission_eval(self.h, _ptr(F), _ptr(T), _ptr(W), _ptr(R), _ptr(J), _ptr(P), F.size))
         return J, P
+
+
+class Batch:
+    """pic_batch_*: independent instances (sharing one stream) stepped by one graph launch per step."""
+
+    def __init__(self, sims):
+        self.sims = list(sims)
+        arr = (C.c_void_p * len(self.sims))(*[x.h.value for x in self.sims])
+        b = C.c_void_p()
+        rc = lib().pic_batch_create(arr, len(self.sims), C.byref(b))
+        if rc != PIC_OK:
+            raise PicError(rc, "pic_batch_create failed (distinct handles on one stream required)")
+        self.b = b
+
+    def step(self, nsteps=1):
+        rc = lib().pic_batch_step(self.b, int(nsteps))
+        if rc != PIC_OK:
+            raise PicError(rc, lib().pic_batch_last_error(self.b).decode())
+
+    def ms(self):
+        v = C.c_double()
+        lib().pic_batch_ms(self.b, C.byref(v))
+        return v.value
+
+    def close(self):
+        if getattr(self, "b", None):
+            lib().pic_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
