@@ -231,6 +231,16 @@ def run_ours(args):
         launches = d1["kernel_launches"] - d0["kernel_launches"]
         updates = args.steps * 0.5 * (sum(d0["count"]) + sum(d1["count"]))
         sur_faces = d1["surrogate_faces"]
+        # the same form replayed as one CUDA graph per step (Poisson loop as a device-side while node)
+        graph = None
+        if args.graph_steps > 0:
+            sim.set_flags(prod_flags | pic.F_GRAPH)
+            sim.step(2)     # one eager step records the graphs, one replay warms them
+            gm, g0, g1 = timed_steps(sim, stream, args.graph_steps)
+            graph = {"ms_per_step": gm / args.graph_steps, "steps": args.graph_steps,
+                     "particle_updates_per_s": args.graph_steps * 0.5 * (sum(g0["count"]) + sum(g1["count"])) / (gm * 1e-3),
+                     "mg_cycles": g1["mg_cycles"]}
+            sim.set_flags(prod_flags)
         # the plain GPU form on the same state: full FP64 emission integral, FP64 V-cycles
         plain = None
         if args.plain_steps > 0 and prod_flags != plain_flags:
@@ -324,7 +334,7 @@ def run_ours(args):
                        "valid_sample_fraction": round(sur["valid_sample_fraction"], 3),
                        "faces_served_per_step": round(sur_faces / max(sim.nface, 1), 4),
                        "train_s": round((sur["ms_data"] + sur["ms_train"]) / 1e3, 2)},
-                   "plain_form": plain},
+                   "plain_form": plain, "graph_form": graph},
         "roofline": roof,
         "clocks": clk.summary(),
         "e2e": {"value": tot_e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
@@ -417,6 +427,7 @@ def main():
     ap.add_argument("--config", default="production")
     ap.add_argument("--form", default="production", choices=["production", "plain"])
     ap.add_argument("--plain-steps", type=int, default=3)
+    ap.add_argument("--graph-steps", type=int, default=50)
     ap.add_argument("--sur-samples", type=int, default=2_000_000)
     ap.add_argument("--sur-epochs", type=int, default=150)
     ap.add_argument("--mg-tol", type=float, default=1e-6)
