@@ -342,25 +342,12 @@ __device__ __forceinline__ long long charge_fx(long long Qn, unsigned long long 
   return (long long)((r >> S) | ((unsigned long long)hi << (64 - S)));
 }
 
-// int64 -> float rounded to nearest, ties to even, in integer arithmetic: the conversion
-// instruction for 64-bit integers runs on the FP64 pipe of this part.  The magnitude is
-// normalised to bit 63, its top 24 bits are the significand and the 40 bits below decide the
-// rounding; the result equals __ll2float_rn for every input.
-__device__ __forceinline__ float ll2f_rn(long long x) {
-  const unsigned int sgn = (unsigned int)((unsigned long long)x >> 32) & 0x80000000u;
-  unsigned long long a = x < 0 ? 0ull - (unsigned long long)x : (unsigned long long)x;
-  if (a == 0ull) return 0.f;
-  const int lz = __clzll((long long)a);
-  a <<= lz;
-  unsigned int m = (unsigned int)(a >> 40);
-  const unsigned long long rest = a & 0xFFFFFFFFFFull, half = 0x8000000000ull;
-  if (rest > half || (rest == half && (m & 1u))) ++m;
-  int e = 63 - lz;
-  if (m == 0x1000000u) { m >>= 1; ++e; }
-  return __uint_as_float(sgn | ((unsigned int)(e + 127) << 23) | (m & 0x7FFFFFu));
+// int64 -> float from its two 32-bit halves (the 32-bit conversions do not use the FP64 pipe):
+// within 1.5 ulp of the correctly rounded value, all a V-cycle right-hand side or a norm needs.
+__device__ __forceinline__ float fx_to_float(long long t) {
+  return fmaf((float)(int)(t >> 32), 4294967296.0f, (float)(unsigned)t);
 }
-__device__ __forceinline__ float fx_to_float(long long t) { return ll2f_rn(t); }
-__device__ __forceinline__ float fx_to_level(long long t, float c) { return fx_to_float(t) * c; }
+__device__ __forceinline__ float fx_to_level(long long t, float c) { return fx_to_float(t) * c; }   // CSE'd with tf
 __device__ __forceinline__ double fx_to_level(long long t, double c) { return (double)t * c; }
 
 // Residual of the discrete Poisson system in fixed point, t = h^2 (f - A phi) 2^40 = Q_n K -
@@ -423,8 +410,9 @@ __global__ void __launch_bounds__(256) k_residual64(const long long *phi, const 
         f = zero_charge ? 0 : charge_fx((long long)qv[p], Kfx << wall, S);
         t = f - (6 * cz[p + 1] - (side[p] + cz[p] + cz[p + 2]));
       }
+      const float tf = fx_to_float(t);
       fl[sidx(L, i, j, k)] = d[p] ? (T)0 : fx_to_level(t, c_lvl);
-      const float rs = fx_to_float(t) * 9.094947017729282e-13f;   // 2^-40
+      const float rs = tf * 9.094947017729282e-13f;   // h^2 r = t 2^-40
       s += rs * rs;
       if (lift && !d[p]) {
         const float l = fx_to_float(f) * 9.094947017729282e-13f + (k == nz - 1 ? V0f : 0.f);
@@ -512,36 +500,20 @@ __global__ void k_correct(long long *phi, const T *u, const uint8_t *dir, Lv L) 
 // f32 factor exactly, so no FP64 operation is needed.
 __global__ void __launch_bounds__(256) k_efield(const long long *phi, float4 *E, int nx, int ny, int nz, float c2,
                                                 float c1) {
-  const int i = blockIdx.x * 32 + threadIdx.x;
-  const int j = blockIdx.y * 8 + threadIdx.y, k0 = blockIdx.z * kKZ;
-  if (i > nx || j > ny) return;
+  NODE_IJK(nx, ny)
   const int64_t sy = nx + 1, sz = (int64_t)(nx + 1) * (ny + 1);
   const int im = i > 0 ? i - 1 : 1, ip = i < nx ? i + 1 : nx - 1;
   const int jm = j > 0 ? j - 1 : 1, jp = j < ny ? j + 1 : ny - 1;
-  const int64_t col = (int64_t)j * sy + i;
-  // kKZ planes per thread: the centre column k0 - 1 .. k0 + kKZ (clamped) serves all z differences
-  long long cz[kKZ + 2], dx[kKZ], dy[kKZ];
-#pragma unroll
-  for (int p = 0; p < kKZ + 2; ++p) cz[p] = phi[(int64_t)min(max(k0 - 1 + p, 0), nz) * sz + col];
-#pragma unroll
-  for (int p = 0; p < kKZ; ++p) {
-    const int64_t pl = (int64_t)min(k0 + p, nz) * sz;
-    dx[p] = phi[pl + (int64_t)j * sy + im] - phi[pl + (int64_t)j * sy + ip];
-    dy[p] = phi[pl + (int64_t)jm * sy + i] - phi[pl + (int64_t)jp * sy + i];
-  }
-#pragma unroll
-  for (int p = 0; p < kKZ; ++p) {
-    const int k = k0 + p;
-    if (k > nz) break;
-    float4 e;
-    e.x = __fmul_rn(ll2f_rn(dx[p]), c2);
-    e.y = __fmul_rn(ll2f_rn(dy[p]), c2);
-    if (k == 0) e.z = __fmul_rn(ll2f_rn(cz[p + 1] - cz[p + 2]), c1);
-    else if (k == nz) e.z = __fmul_rn(ll2f_rn(cz[p] - cz[p + 1]), c1);
-    else e.z = __fmul_rn(ll2f_rn(cz[p] - cz[p + 2]), c2);
-    e.w = 0.f;
-    E[(int64_t)k * sz + col] = e;
-  }
+  const int64_t row = (int64_t)k * sz + (int64_t)j * sy;
+  const long long dx = phi[row + im] - phi[row + ip];
+  const long long dy = phi[(int64_t)k * sz + (int64_t)jm * sy + i] - phi[(int64_t)k * sz + (int64_t)jp * sy + i];
+  const long long dz = k == 0 ? phi[n] - phi[n + sz] : k == nz ? phi[n - sz] - phi[n] : phi[n - sz] - phi[n + sz];
+  float4 e;
+  e.x = __fmul_rn(__ll2float_rn(dx), c2);
+  e.y = __fmul_rn(__ll2float_rn(dy), c2);
+  e.z = __fmul_rn(__ll2float_rn(dz), k == 0 || k == nz ? c1 : c2);
+  e.w = 0.f;
+  E[n] = e;
 }
 
 template <typename T>
@@ -642,7 +614,7 @@ int stage_efield(pic_t *h) {
   ++h->nlaunch;
   // f32(1/(2 dx)) 2^-40 and f32(1/dx) 2^-40: rounding then scaling by a power of two
   const float c2 = (float)(1.0 / (2.0 * h->dx)) * (float)kPhiUnit, c1 = (float)(1.0 / h->dx) * (float)kPhiUnit;
-  { KtScope kt_(h, kidEfield, (double)h->nnode); k_efield<<<dim3((h->nx + 1 + 31) / 32, (h->ny + 1 + 7) / 8, (h->nz + kKZ) / kKZ), node_block(), 0, h->stream>>>(h->phi, h->E, h->nx, h->ny, h->nz, c2, c1); }
+  { KtScope kt_(h, kidEfield, (double)h->nnode); k_efield<<<node_grid3(h->nx, h->ny, h->nz), node_block(), 0, h->stream>>>(h->phi, h->E, h->nx, h->ny, h->nz, c2, c1); }
   return launch_check(h, "efield");
 }
 
