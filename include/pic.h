@@ -259,6 +259,9 @@ int pic_mlp_forward_backward(pic_t *h, const float *x, const float *t, int64_t n
  * over relevant samples, fraction of valid bins, fraction of valid held-out samples, ms of data
  * generation, ms of training, optimiser steps. */
 int pic_surrogate_train(pic_t *h, int64_t nsamples, int epochs, int batch, double lr, uint64_t seed, double *stats);
+/* Install src's trained surrogate (weights and validity map) in dst, so that one training serves
+ * every instance of an ensemble; PIC_E_INVALID if src has none. */
+int pic_surrogate_copy(pic_t *dst, pic_t *src);
 /* Surrogate J [A/m^2], P_N [W/m^2] of n host tuples (F [V/m], T [K], phi_w [eV], R [m], <= 0 flat);
  * valid[i] = 1 where the step would use the surrogate for that tuple. */
 int pic_surrogate_eval(pic_t *h, const double *F, const double *T, const double *phi_w, const double *R, double *J,

@@ -771,6 +771,25 @@ int pic_surrogate_train(pic_t *h, int64_t nsamples, int epochs, int batch, doubl
   return PIC_OK;
 }
 
+// Install the trained surrogate of src (weights and validity map) in dst: one training serves
+// every instance of an ensemble.  Both handles on the current device; PIC_E_INVALID if src has no
+// trained surrogate.
+int pic_surrogate_copy(pic_t *dst, pic_t *src) {
+  if (!dst || !src || dst == src) return PIC_E_INVALID;
+  graph_invalidate(dst);   // its buffers may be reallocated
+  MlpState &A = mlp_of(src);
+  if (!A.trained) return pic_fail(dst, PIC_E_INVALID, "source instance has no trained surrogate");
+  MlpState &B = mlp_of(dst);
+  PIC_TRY(ensure(dst, B, 1024));
+  PIC_CUDA(dst, cudaStreamSynchronize(src->stream));
+  PIC_CUDA(dst, cudaMemcpyAsync(B.master, A.master, kNParam * 4, cudaMemcpyDeviceToDevice, dst->stream));
+  PIC_CUDA(dst, cudaMemcpyAsync(B.binok, A.binok, kNBin, cudaMemcpyDeviceToDevice, dst->stream));
+  refresh_bf16(dst, B);
+  PIC_CUDA(dst, cudaStreamSynchronize(dst->stream));
+  B.trained = true;
+  return launch_check(dst, "surrogate copy");
+}
+
 // Surrogate evaluation of n host tuples (F [V/m], T [K], phi_w [eV], R [m] or <= 0 flat):
 // J, PN from the network; valid[i] = 1 where the tuple is inside the trained range and its
 // validation bin passed (elsewhere the step uses the full integral).

@@ -147,7 +147,11 @@ __global__ void __launch_bounds__(256, 4) k_push(PushArgs a) {
     if (alive) {
       const uint32_t c = (uint32_t)cell_index(i1, j1, k1, a.nx, a.ny);
       a.key[i] = c;
-      atomicAdd(&a.cnt[c], 1u);
+      // cell-sorted SPs mostly stay in their cell: lanes with the same new cell add their count
+      // with one atomic (the counts are integers, so nothing depends on the grouping)
+      const unsigned act = __activemask();
+      const unsigned grp = __match_any_sync(act, c);
+      if ((int)(threadIdx.x & 31) == __ffs(grp) - 1) atomicAdd(&a.cnt[c], (uint32_t)__popc(grp));
     } else {
       a.key[i] = kDead;
       ++removed;
@@ -334,31 +338,55 @@ __global__ void k_set_count(DevClock *clk, int s, const uint32_t *off, int64_t n
 
 // Cloud-in-cell deposit with quantised fractions: q = floor(frac(x) 2^F), weights 2^F - q on
 // the lower node and q on the upper node per axis; Z w prod(W) added as int64 (exact, order-free).
+// The SPs are cell-sorted, so lanes of a warp that share a cell sit next to each other: such a
+// run of lanes adds its 8 contributions up with a segmented shuffle scan and only its last lane
+// issues the (nonzero) atomics -- the sums are exact integers, so the grouping changes no bit.
 __global__ void __launch_bounds__(256) k_deposit(SpeciesBuf p, int Z, unsigned long long *Q, int nx, int ny,
                                                  const DevClock *clk, int s) {
   const int64_t n = clk->n[s];
   const int64_t sy = nx + 1, sz = (int64_t)(nx + 1) * (ny + 1);
   const int one = 1 << kFracBits;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t w = p.w[i];
-    if (w <= 0) continue;
-    const float x = p.x[i], y = p.y[i], z = p.z[i];
-    const float fi = floorf(x), fj = floorf(y), fk = floorf(z);
-    const int qx = (int)floorf(__fsub_rn(x, fi) * (float)one);
-    const int qy = (int)floorf(__fsub_rn(y, fj) * (float)one);
-    const int qz = (int)floorf(__fsub_rn(z, fk) * (float)one);
-    const int64_t base = (int64_t)fk * sz + (int64_t)fj * sy + (int64_t)fi;
-    const int64_t zw = (int64_t)Z * w;
-    const int64_t wx0 = one - qx, wy0 = one - qy, wz0 = one - qz;
-    const int64_t a00 = zw * wz0 * wy0, a10 = zw * wz0 * qy, a01 = zw * qz * wy0, a11 = zw * qz * qy;
-    atomicAdd(Q + base, (unsigned long long)(a00 * wx0));
-    atomicAdd(Q + base + 1, (unsigned long long)(a00 * qx));
-    atomicAdd(Q + base + sy, (unsigned long long)(a10 * wx0));
-    atomicAdd(Q + base + sy + 1, (unsigned long long)(a10 * qx));
-    atomicAdd(Q + base + sz, (unsigned long long)(a01 * wx0));
-    atomicAdd(Q + base + sz + 1, (unsigned long long)(a01 * qx));
-    atomicAdd(Q + base + sz + sy, (unsigned long long)(a11 * wx0));
-    atomicAdd(Q + base + sz + sy + 1, (unsigned long long)(a11 * qx));
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); i0 < n; i0 += stride) {
+    const int64_t i = i0 + lane;
+    int64_t base = -1;
+    long long c[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    const int32_t w = i < n ? p.w[i] : 0;
+    if (w > 0) {
+      const float x = p.x[i], y = p.y[i], z = p.z[i];
+      const float fi = floorf(x), fj = floorf(y), fk = floorf(z);
+      const int qx = (int)floorf(__fsub_rn(x, fi) * (float)one);
+      const int qy = (int)floorf(__fsub_rn(y, fj) * (float)one);
+      const int qz = (int)floorf(__fsub_rn(z, fk) * (float)one);
+      base = (int64_t)fk * sz + (int64_t)fj * sy + (int64_t)fi;
+      const int64_t zw = (int64_t)Z * w;
+      const int64_t wx0 = one - qx, wy0 = one - qy, wz0 = one - qz;
+      const int64_t a00 = zw * wz0 * wy0, a10 = zw * wz0 * qy, a01 = zw * qz * wy0, a11 = zw * qz * qy;
+      c[0] = a00 * wx0; c[1] = a00 * qx; c[2] = a10 * wx0; c[3] = a10 * qx;
+      c[4] = a01 * wx0; c[5] = a01 * qx; c[6] = a11 * wx0; c[7] = a11 * qx;
+    }
+    const int64_t prev = __shfl_up_sync(0xffffffffu, base, 1);
+    const int64_t next = __shfl_down_sync(0xffffffffu, base, 1);
+    const unsigned heads = __ballot_sync(0xffffffffu, lane == 0 || prev != base);
+    if (heads != 0xffffffffu) {   // some cell holds several lanes: segmented sums
+      const int start = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const long long v = __shfl_up_sync(0xffffffffu, c[q], off);
+          if (lane - off >= start) c[q] += v;
+        }
+      }
+    }
+    if (base >= 0 && (lane == 31 || next != base)) {
+      const int64_t at[8] = {base, base + 1, base + sy, base + sy + 1, base + sz, base + sz + 1, base + sz + sy,
+                             base + sz + sy + 1};
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        if (c[q] != 0) atomicAdd(Q + at[q], (unsigned long long)c[q]);
+    }
   }
 }
 

@@ -113,6 +113,7 @@ def lib():
         L.pic_batch_destroy.argtypes = [vp]
         L.pic_batch_destroy.restype = None
         L.pic_autotune.argtypes = [vp, C.POINTER(i32), i32]
+        L.pic_surrogate_copy.argtypes = [vp, vp]
         L.pic_num_kernels.argtypes = []
         L.pic_kernel_name.argtypes = [i32]
         L.pic_kernel_name.restype = C.c_char_p
@@ -390,6 +391,10 @@ class Pic:
         self._check(lib().pic_surrogate_eval(self.h, _ptr(F), _ptr(T), _ptr(W), _ptr(R), _ptr(J), _ptr(P), _ptr(v),
                                              F.size))
         return J, P, v.astype(bool)
+
+    def surrogate_copy_from(self, other):
+        """Install the trained surrogate of another instance (pic_surrogate_copy)."""
+        self._check(lib().pic_surrogate_copy(self.h, other.h))
 
     def emission_eval_noalloc(self, F, T, W, R):
         """pic_emission_eval_noalloc: the same evaluation staged through the library's fixed
