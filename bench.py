@@ -138,6 +138,9 @@ KERNEL_BYTES_PER_UNIT = {
     "k_dirichlet": 1.0,      # per node: mask 1 (Dirichlet values written on the mask only)
     "k_efield": 24.0,        # per node: phi 8 + E write 16
 }
+# DRAM bytes (read + write) per launch from one ncu capture of the unchanged kernel on the
+# production grid (profiles/dram_traffic_multigrid_production_grid.md): (workload, kernel) -> bytes
+NCU_TRAFFIC_PER_LAUNCH = {("production", "k_smooth"): 35.89e6}
 KERNEL_BYTES_PER_SP = {      # (bytes, species the launches of one step cover)
     "k_push": (56.0, "all"),         # pos+vel+w read 28, pos+vel write 24, key 4
     "k_gather": (76.0, "all"),       # perm 4 + 36 B record read + 36 B record write
@@ -303,6 +306,7 @@ def run_ours(args):
         roof = kernel_roofline(dom_kernel, kt_dom, mean_counts, nnode, args.steps,
                                pk.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"]), pk_src)
     if roof is not None:
+        roof["traffic"] = NCU_TRAFFIC_PER_LAUNCH.get((args.config, dom_kernel))
         roof["kernel_share_of_step"] = round(kt_dom[1] / times[0], 4)
         roof["stage"] = {"stage": dom, "stage_ms": round(stage_ms[dom], 4)}
     elif kind == "hbm":

@@ -310,6 +310,36 @@ __device__ __forceinline__ double warp_sum_d(double v) {
   return v;
 }
 
+// FP32 forms of the supply function and of I(W) for the FAST_INTEGRAL path: the same formulas
+// with float transcendentals (~1e-7 relative per value; the panel sums stay in FP64).  On this
+// part FP64 runs at 1/64 of the FP32 rate, and these two functions dominate an evaluation.
+__host__ __device__ inline float li2_neg_f(float x) {
+  const float u = -log1pf(x);
+  const float u2 = u * u;
+  // B_n/(n+1)! for n = 2, 4, 6, 8 (|u| <= ln 2: the next terms are below FP32 resolution)
+  const float s = u * u2 * (1.0f / 36.0f + u2 * (-1.0f / 3600.0f + u2 * (1.0f / 211680.0f + u2 * (-1.0f / 10886400.0f))));
+  return u - 0.25f * u2 + s;
+}
+__host__ __device__ inline float Lw_f(float w) { return -li2_neg_f(expf(-w)); }
+__host__ __device__ inline float supply_f(float W, float kT) {
+  const float w = W / kT;
+  return kT * (fmaxf(-w, 0.0f) + log1pf(expf(-fabsf(w))));
+}
+__host__ __device__ inline float inner_f(float W, float kT) {
+  const float w = W / kT, k2 = kT * kT;
+  if (w >= 0.0f) return -k2 * (w * log1pf(expf(-w)) + Lw_f(w));
+  return k2 * (0.5f * w * w - 1.6449340668f - w * log1pf(expf(w)) + Lw_f(-w));
+}
+template <bool kFast>
+__host__ __device__ __forceinline__ double supply_sel(double W, double kT) {
+  return kFast ? (double)supply_f((float)W, (float)kT) : supply(W, kT);
+}
+template <bool kFast>
+__host__ __device__ __forceinline__ double inner_sel(double W, double kT) {
+  return kFast ? (double)inner_f((float)W, (float)kT) : inner(W, kT);
+}
+
+
 // The same integrals and panels as current_density, evaluated by a whole warp for one face: the
 // 32 lanes split the (panel, node) work items and sum with a fixed butterfly, so a few faces
 // still fill the FP64 pipes.  Every lane must call it with the same arguments; every lane gets
@@ -342,7 +372,7 @@ __device__ inline void current_density_warp(const Consts &C, const Tables &T, do
     const double lo = top + kT * (p == 0 ? 0.0 : p == 1 ? 4.0 : p == 2 ? 12.0 : p == 3 ? 28.0 : 60.0);
     const double wd = kT * (p == 0 ? 4.0 : p == 1 ? 8.0 : p == 2 ? 16.0 : p == 3 ? 32.0 : 16.0);
     const double c = lo + 0.5 * wd, hw = 0.5 * wd;
-    Pl += hw * T.w16[i] * inner(c + hw * T.x16[i], kT);
+    Pl += hw * T.w16[i] * inner_sel<kFast>(c + hw * T.x16[i], kT);
   }
   double P = warp_sum_d(Pl);
   const double h0 = 4.0 * kT;
@@ -373,8 +403,8 @@ __device__ inline void current_density_warp(const Consts &C, const Tables &T, do
       const double mid = 0.5 * (a + c), hw = 0.5 * (c - a);
       const double W = mid + hw * T.x16[i];
       const double D = transmission_sel<kFast>(b, C, T, W, xm);
-      Jl += hw * T.w16[i] * D * supply(W, kT);
-      Pl += hw * T.w16[i] * D * inner(W, kT);
+      Jl += hw * T.w16[i] * D * supply_sel<kFast>(W, kT);
+      Pl += hw * T.w16[i] * D * inner_sel<kFast>(W, kT);
     }
     J += warp_sum_d(Jl);
     P += warp_sum_d(Pl);
@@ -396,8 +426,8 @@ __device__ inline void current_density_warp(const Consts &C, const Tables &T, do
           const double mid = 0.5 * (lo + hi), hw = 0.5 * (hi - lo);
           const double W = mid + hw * T.x16[i];
           const double D = transmission_sel<kFast>(b, C, T, W, xm);
-          Jl = hw * T.w16[i] * D * supply(W, kT);
-          Pl = hw * T.w16[i] * D * inner(W, kT);
+          Jl = hw * T.w16[i] * D * supply_sel<kFast>(W, kT);
+          Pl = hw * T.w16[i] * D * inner_sel<kFast>(W, kT);
         }
         const double rJ = warp_sum_d(Jl), rP = warp_sum_d(Pl);
         J += rJ;
