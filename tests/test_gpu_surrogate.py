@@ -117,3 +117,20 @@ def test_production_emission_matches_integral(sim):
     assert rel.sum() > 50
     err = np.abs(np.log10(np.maximum(J[pick][rel], 1e-300)) - np.log10(Jr[rel]))
     assert err.max() <= 0.02, (np.sort(err)[-5:],)
+
+
+def test_surrogate_copy_serves_another_instance(sim):
+    """pic_surrogate_copy installs the trained network and its validity map in a second instance
+    (one training for an ensemble): its evaluations equal the source's bit for bit (runs after
+    the training test on the same handle)."""
+    from paper_2402_08404_gb300 import pic
+    other = pic.Pic(dict(synth.CONFIGS["small"]), capacity=50_000, V0=20.0)
+    F, T, W, R = synth.face_tuples(4000, seed=33)
+    with pytest.raises(pic.PicError):
+        sim.surrogate_copy_from(other)        # the source has no trained network
+    other.surrogate_copy_from(sim)
+    J1, P1, v1 = sim.surrogate_eval(F * 1e9, T, W, R * 1e-9)
+    J2, P2, v2 = other.surrogate_eval(F * 1e9, T, W, R * 1e-9)
+    assert v1.sum() > 100
+    assert np.array_equal(v1, v2) and np.array_equal(J1, J2) and np.array_equal(P1, P2)
+    other.close()
