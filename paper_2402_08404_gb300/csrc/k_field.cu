@@ -381,33 +381,35 @@ __global__ void __launch_bounds__(256) k_residual64(const long long *phi, const 
   const int j = blockIdx.y * 8 + threadIdx.y, k0 = blockIdx.z * kKZ;
   float s = 0.f, sl = 0.f;
   if (i <= nx && j <= ny) {
+    // 32-bit node offsets (a grid has fewer than 2^32 nodes, checked at creation)
     const int im = i > 0 ? i - 1 : 1, ip = i < nx ? i + 1 : nx - 1;
     const int jm = j > 0 ? j - 1 : 1, jp = j < ny ? j + 1 : ny - 1;
-    const int64_t sy = nx + 1, sz = (int64_t)(nx + 1) * (ny + 1);
-    const int64_t col = (int64_t)j * sy + i;
+    const uint32_t sy = (uint32_t)(nx + 1), sz = (uint32_t)(nx + 1) * (uint32_t)(ny + 1);
+    const uint32_t col = (uint32_t)j * sy + (uint32_t)i;
+    const int32_t dxm = im - i, dxp = ip - i, dym = (jm - j) * (int32_t)sy, dyp = (jp - j) * (int32_t)sy;
     long long cz[kKZ + 2];
 #pragma unroll
-    for (int p = 0; p < kKZ + 2; ++p) cz[p] = phi[(int64_t)min(max(k0 - 1 + p, 0), nz) * sz + col];
+    for (int p = 0; p < kKZ + 2; ++p) cz[p] = phi[(uint32_t)min(max(k0 - 1 + p, 0), nz) * sz + col];
     long long side[kKZ];
     unsigned long long qv[kKZ];
     uint8_t d[kKZ];
 #pragma unroll
     for (int p = 0; p < kKZ; ++p) {
-      const int k = min(k0 + p, nz);
-      const int64_t pl = (int64_t)k * sz;
-      d[p] = k0 + p <= nz ? dir[pl + col] : 1;
-      side[p] = phi[pl + (int64_t)j * sy + im] + phi[pl + (int64_t)j * sy + ip] + phi[pl + (int64_t)jm * sy + i] +
-                phi[pl + (int64_t)jp * sy + i];
-      qv[p] = Q[pl + col];
+      const uint32_t c = (uint32_t)min(k0 + p, nz) * sz + col;
+      d[p] = k0 + p <= nz ? dir[c] : 1;
+      side[p] = phi[c + dxm] + phi[c + dxp] + phi[c + dym] + phi[c + dyp];
+      qv[p] = Q[c];
     }
+    const int wall = (i == 0 || i == nx ? 1 : 0) + (j == 0 || j == ny ? 1 : 0);
+    const unsigned long long Kw = Kfx << wall;
 #pragma unroll
     for (int p = 0; p < kKZ; ++p) {
       const int k = k0 + p;
       if (k > nz) break;
-      const int wall = (i == 0 || i == nx ? 1 : 0) + (j == 0 || j == ny ? 1 : 0);
       long long t = 0, f = 0;
       if (!d[p]) {
-        f = zero_charge ? 0 : charge_fx((long long)qv[p], Kfx << wall, S);
+        // most nodes carry no charge: the 128-bit product only where there is some
+        f = (zero_charge || qv[p] == 0ull) ? 0 : charge_fx((long long)qv[p], Kw, S);
         t = f - (6 * cz[p + 1] - (side[p] + cz[p] + cz[p + 2]));
       }
       const float tf = fx_to_float(t);
