@@ -220,6 +220,7 @@ struct DfiArgs {
   const float4 *E;
   int nx, ny;
   double dt_fs, pre, c1, c2, expo, lim2;   // rate = pre (c1/E)^expo exp(-c2/E), E in GV/m
+  float lim2f;                             // lim2 in FP32 (screening of the barrier-suppression test)
   uint64_t seed;
   DevClock *clk;
   uint64_t *cnt, *off;
@@ -235,12 +236,20 @@ __global__ void k_dfi_count(DfiArgs a) {
     int k = 0;
     if (w > 0) {
       const float3 e = gather_E(a.E, a.n.x[t], a.n.y[t], a.n.z[t], a.nx, a.ny);
-      const double E2 = __dadd_rn(__dadd_rn(__dmul_rn((double)e.x, (double)e.x), __dmul_rn((double)e.y, (double)e.y)),
-                                  __dmul_rn((double)e.z, (double)e.z));
+      // |E|^2 is defined in FP64 (the oracle's sum of the three exact squares).  It is formed in
+      // FP32 first (within a few ulp) and in FP64 only where the barrier-suppression decision is
+      // close; P32 below only places the guard band, inside which the draw is re-decided from
+      // the FP64 |E|^2.
+      const float E2f = fmaf(e.x, e.x, fmaf(e.y, e.y, e.z * e.z));
+      const bool near_bsi = fabsf(E2f - a.lim2f) <= 1e-5f * a.lim2f;
+      double E2 = (double)E2f;
+      if (near_bsi)
+        E2 = __dadd_rn(__dadd_rn(__dmul_rn((double)e.x, (double)e.x), __dmul_rn((double)e.y, (double)e.y)),
+                       __dmul_rn((double)e.z, (double)e.z));
       if (E2 > a.lim2) {
         k = w;
-      } else if (E2 > 0.0) {
-        const float Eg = sqrtf((float)E2) * 1e-9f;
+      } else if (E2f > 0.0f) {
+        const float Eg = sqrtf(E2f) * 1e-9f;
         const float P32 = (float)a.pre * powf((float)a.c1 / Eg, (float)a.expo) * expf(-(float)a.c2 / Eg) * (float)a.dt_fs;
         const float band = ldexpf(P32, -12);
         const uint64_t id = a.n.id[t];
@@ -254,7 +263,9 @@ __global__ void k_dfi_count(DfiArgs a) {
           }
         }
         if (exact) {
-          const double Ed = sqrt(E2) * 1e-9;
+          const double E2d = __dadd_rn(__dadd_rn(__dmul_rn((double)e.x, (double)e.x), __dmul_rn((double)e.y, (double)e.y)),
+                                       __dmul_rn((double)e.z, (double)e.z));
+          const double Ed = sqrt(E2d) * 1e-9;
           const double P64 = a.pre * pow(a.c1 / Ed, a.expo) * exp(-a.c2 / Ed) * a.dt_fs;
           k = 0;
           for (int i = 0; i < w; i += 4) {
@@ -324,6 +335,7 @@ int stage_collide(pic_t *h) {
     d.c1 = 20.5 * x15; d.c2 = 6.83 * x15; d.expo = 2.0 * nstar - 1.0;
     const double lim = 1.5 * x15 * 1e9;
     d.lim2 = lim * lim;
+    d.lim2f = (float)d.lim2;
     d.dt_fs = h->prm.dt * 1e15; d.seed = h->prm.seed; d.clk = h->clock;
     d.cnt = h->pair_cnt; d.off = h->pair_off; d.nion = h->pair_ncoll; d.go = go;
     ++h->nlaunch;
