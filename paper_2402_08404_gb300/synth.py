@@ -161,13 +161,14 @@ def ensemble_configs(n=64, seed=7):
     """Independent tip instances of the ensemble workload: apex field uniform in 6-12 GV/m, grids
     nx = ny = nz/2 log-uniform between 32 and 128 cells (rounded to multiples of 32, so every
     multigrid level has even sizes), dx uniform in 0.5-1 nm, SPs log-uniform in 1e4-2e6
-    (at most 20 per cell), a 3 nm tip 20 nm high."""
+    (at most 2 per cell, about the production density; denser seeds charge the small grids past
+    the barrier-suppression field), a 3 nm tip 20 nm high."""
     rng = np.random.default_rng(seed)
     out = []
     for i in range(n):
         nx = int(32 * round(2.0 ** rng.uniform(5.0, 7.0) / 32.0))
         dx = rng.uniform(0.5, 1.0) * 1e-9
-        n_sp = int(min(10.0 ** rng.uniform(4.0, math.log10(2e6)), 20 * nx * nx * 2 * nx))
+        n_sp = int(min(10.0 ** rng.uniform(4.0, math.log10(2e6)), 2 * nx * nx * 2 * nx))
         out.append(dict(nx=nx, ny=nx, nz=2 * nx, dx=dx, tip_radius=3e-9, tip_height=20e-9,
                         apex_field=rng.uniform(6.0, 12.0) * 1e9, n_sp=n_sp, dt=5e-17, steps=2000, T0=300.0,
                         work_function=4.5, w_min=1e-5, w_max_units=1024, n_heat=1000, seed=1000 + i))
