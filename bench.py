@@ -419,7 +419,8 @@ def run_ensemble(args):
     with torch.cuda.stream(stream):
         for i, cfg in enumerate(cfgs):
             n = cfg["n_sp"]
-            cap = (int(0.4 * n * 2.5) + 4096, int(0.4 * n * 1.5) + 4096, int(0.2 * n * 4.0) + 4096)
+            # headroom for field emission: at 12 GV/m a small tip emits several thousand SPs per step
+            cap = (int(0.4 * n * 2.5) + 400_000, int(0.4 * n * 1.5) + 100_000, int(0.2 * n * 4.0) + 100_000)
             sim = pic.Pic(cfg, capacity=cap, flags=pic.F_PRODUCTION, mg_tol=args.mg_tol, mg_max_cycles=60, stream=stream)
             pop = synth.plasma(cfg, seed=cfg["seed"])
             for s, k in enumerate("eni"):

@@ -330,13 +330,15 @@ __host__ __device__ inline float inner_f(float W, float kT) {
   if (w >= 0.0f) return -k2 * (w * log1pf(expf(-w)) + Lw_f(w));
   return k2 * (0.5f * w * w - 1.6449340668f - w * log1pf(expf(w)) + Lw_f(-w));
 }
+// FP32 only where it cannot underflow: for W/kT > 80 both functions fall like e^{-W/kT} below
+// the FP32 range, and those energies take the FP64 forms.
 template <bool kFast>
 __host__ __device__ __forceinline__ double supply_sel(double W, double kT) {
-  return kFast ? (double)supply_f((float)W, (float)kT) : supply(W, kT);
+  return (kFast && W < 80.0 * kT) ? (double)supply_f((float)W, (float)kT) : supply(W, kT);
 }
 template <bool kFast>
 __host__ __device__ __forceinline__ double inner_sel(double W, double kT) {
-  return kFast ? (double)inner_f((float)W, (float)kT) : inner(W, kT);
+  return (kFast && W < 80.0 * kT) ? (double)inner_f((float)W, (float)kT) : inner(W, kT);
 }
 
 

@@ -4,8 +4,11 @@
 // in the step wherever its inputs lie in the trained range and a held-out validation bin shows
 // |delta log10 J| <= 0.015; elsewhere the step falls back to the full integral.
 //
-// Arithmetic: the two 128 x 128 hidden layers run on the tensor cores (mma.sync m16n8k16, BF16
-// operands, FP32 accumulation); the input layer (7 features) and the output layer (2 values)
+// Arithmetic: the two 128 x 128 hidden layers run on the tensor cores with BF16 operands and FP32
+// accumulation -- inference (the step's faces, pic_surrogate_eval, the validation map, forward
+// calls without targets) in one fused tcgen05/TMEM kernel (k_mlp_tc.cu); training, which keeps
+// every layer's values for the backward pass, on mma.sync m16n8k16 tiles here.  The input layer
+// (7 features) and the output layer (2 values)
 // are FP32 on the CUDA cores, so the features and the last activations keep FP32 precision
 // (in BF16 a feature step of 2^-9 moves log10 J by up to ~0.04 in the field-emission regime).
 // FP32 master weights, Adam.  Weight gradients reduce over the batch with a fixed split order,
@@ -555,7 +558,7 @@ int surrogate_faces(pic_t *h, const uint8_t **elig_out, const float **Y_out) {
   k_face_rows<<<grid_for(h->faces.n), kThreads, 0, h->stream>>>(h->faces.F, h->faces.owner_vox, h->heat.T, h->prm.T0,
                                                                  h->prm.work_function, h->geo.tip_radius * 1e9,
                                                                  h->faces.n, S.binok, S.X, S.elig);
-  forward(h, S, S.X, h->faces.n);
+  PIC_TRY(mlp_forward_tc(h, S.X, h->faces.n, S.master, S.w2, S.w3, S.Y));
   *elig_out = S.elig;
   *Y_out = S.Y;
   return launch_check(h, "surrogate faces");
@@ -602,7 +605,8 @@ int pic_mlp_forward_backward(pic_t *h, const float *x, const float *t, int64_t n
   for (int64_t i = 0; i < n; ++i)
     for (int c = 0; c < kIn; ++c) X[i * kXld + c] = x[i * kIn + c];
   PIC_CUDA(h, cudaMemcpyAsync(S.X, X.data(), n * kXld * 4, cudaMemcpyHostToDevice, h->stream));
-  forward(h, S, S.X, n);
+  if (t) forward(h, S, S.X, n);   // training: keeps the layer values the gradient needs
+  else PIC_TRY(mlp_forward_tc(h, S.X, n, S.master, S.w2, S.w3, S.Y));   // inference (as in the step)
   if (t) {
     float *Tg = S.dA;   // scratch for targets (rows x 2 fits in rows x kH)
     PIC_CUDA(h, cudaMemcpyAsync(Tg, t, n * 2 * 4, cudaMemcpyHostToDevice, h->stream));
@@ -713,7 +717,7 @@ int pic_surrogate_train(pic_t *h, int64_t nsamples, int epochs, int batch, doubl
   PIC_TRY(launch_check(h, "surrogate train"));
   // validation on the held-out tuples: per-bin max |dlog10 J| where either side is relevant
   const float *Xv = Xall + nsamples * kXld;
-  forward(h, S, Xv, nval);
+  PIC_TRY(mlp_forward_tc(h, Xv, nval, S.master, S.w2, S.w3, S.Y));   // the step's inference kernel
   std::vector<float> Yv(nval * kOut), Tv(nval * 2);
   std::vector<double> hF(nval), hT(nval), hW(nval), hR(nval), hA(nval);
   PIC_CUDA(h, cudaMemcpyAsync(hA.data(), approx + nsamples, nval * 8, cudaMemcpyDeviceToHost, st));
@@ -817,7 +821,7 @@ int pic_surrogate_eval(pic_t *h, const double *F, const double *T, const double 
     k_rows_eligible<<<grid_for(n), kThreads, 0, st>>>(dF, dT, dW, dR, n, S.binok, el);
     ++h->nlaunch;
     k_features_rows<<<grid_for(n), kThreads, 0, st>>>(dF, dT, dW, dR, n, S.X);
-    forward(h, S, S.X, n);
+    if (mlp_forward_tc(h, S.X, n, S.master, S.w2, S.w3, S.Y) != PIC_OK) rc = PIC_E_CUDA;
     ++h->nlaunch;
     k_surrogate_apply<<<grid_for(n), kThreads, 0, st>>>(S.Y, el, dF, dT, dW, n, dJ, dP, el);
     if (cudaMemcpyAsync(J, dJ, n * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||

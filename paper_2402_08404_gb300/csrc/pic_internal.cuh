@@ -347,4 +347,7 @@ int stage_heat(pic_t *h);
 bool surrogate_ready(pic_t *h);
 void mlp_forget(pic_t *h);
 int surrogate_faces(pic_t *h, const uint8_t **elig, const float **Y);
+// fused surrogate forward pass on the tcgen05 tensor cores (k_mlp_tc.cu); __nv_bfloat16 passed as void
+int mlp_forward_tc(pic_t *h, const float *X, int64_t rows, const float *master, const struct __nv_bfloat16 *w2,
+                   const struct __nv_bfloat16 *w3, float *Y);
 }  // namespace pic

@@ -134,3 +134,25 @@ def test_surrogate_copy_serves_another_instance(sim):
     assert v1.sum() > 100
     assert np.array_equal(v1, v2) and np.array_equal(J1, J2) and np.array_equal(P1, P2)
     other.close()
+
+
+def test_tcgen05_inference_matches_reference_forward(sim):
+    """Inference (forward without targets: the fused tcgen05/TMEM kernel the step uses) against the
+    training path's forward (mma.sync tiles) and the FP64 oracle on the same BF16 operands: the
+    two GPU paths differ only in the FP32 accumulation order inside the 128-term products."""
+    rng = np.random.default_rng(4)
+    params = mlp.init_params(rng)
+    params = [(W, rng.normal(0, 0.1, b.size)) for W, b in params]
+    flat = np.concatenate([np.concatenate([W.ravel(), b]) for W, b in params]).astype(np.float32)
+    sim.set_mlp_params(flat)
+    for n in (1, 127, 128, 1000, 70001):     # partial tiles, one tile, many tiles per CTA
+        x = rng.normal(size=(n, mlp.SIZES[0])).astype(np.float32)
+        (y_tc,) = sim.mlp_forward_backward(x)
+        y_ref, _, _ = sim.mlp_forward_backward(x, np.zeros((n, 2), np.float32))
+        assert np.all(np.isfinite(y_tc))
+        assert np.max(np.abs(y_tc - y_ref)) <= 2e-3 * max(1.0, np.max(np.abs(y_ref))), n
+        assert np.linalg.norm(y_tc - y_ref) <= 1e-4 * np.linalg.norm(y_ref) + 1e-6, n
+        if n <= 1000:
+            ref = [(bf16(W) if 0 < li < 3 else W, b) for li, (W, b) in enumerate(unflatten(flat.astype(np.float64)))]
+            yr, _ = mlp.forward(ref, x.astype(np.float64))
+            assert np.linalg.norm(y_tc - yr) <= 1e-2 * np.linalg.norm(yr)
