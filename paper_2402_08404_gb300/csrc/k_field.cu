@@ -70,10 +70,12 @@ struct Lv {
   int64_t nper;
   uint32_t P;    // slots per plane and colour, (ny + 1) Xh
   FastDiv xd;    // division by Xh
+  FastDiv pd;    // division by P
 };
 
 inline Lv lv_of(const MgLevel &L) {
-  return Lv{L.nx, L.ny, L.nz, L.Xh, L.nper, (uint32_t)((L.ny + 1) * L.Xh), make_fastdiv((uint32_t)L.Xh)};
+  const uint32_t P = (uint32_t)((L.ny + 1) * L.Xh);
+  return Lv{L.nx, L.ny, L.nz, L.Xh, L.nper, P, make_fastdiv((uint32_t)L.Xh), make_fastdiv(P)};
 }
 
 __host__ __device__ __forceinline__ int64_t srow(const Lv &L, int j, int k) {
@@ -120,11 +122,15 @@ __global__ void __launch_bounds__(kSlotThreads) k_smooth(T *u, const T *f, const
   if (q >= L.P) return;
   const int j = (int)fdiv(q, L.xd), t = (int)(q - (uint32_t)j * (uint32_t)L.Xh);
   const int k0 = blockIdx.y * KZ;
-  const T *uo = u + (int64_t)(c ^ 1) * L.nper;
-  T *uc = u + (int64_t)c * L.nper;
-  const T *fc = f + (int64_t)c * L.nper;
-  const uint8_t *dc = dirs + (int64_t)c * L.nper;
-  const int64_t ojm = j > 0 ? -(int64_t)L.Xh : (int64_t)L.Xh, ojp = j < L.ny ? (int64_t)L.Xh : -(int64_t)L.Xh;
+  // one 64-bit base per array; every neighbour is a 32-bit offset from it (the integer pipe,
+  // not the memory system, bounds this kernel once the loads are in flight)
+  const size_t base = (size_t)k0 * L.P + q;
+  const T *uo = u + (size_t)(c ^ 1) * L.nper + base;
+  T *uc = u + (size_t)c * L.nper + base;
+  const T *fc = f + (size_t)c * L.nper + base;
+  const uint8_t *dc = dirs + (size_t)c * L.nper + base;
+  const int P = (int)L.P;
+  const int ojm = j > 0 ? -L.Xh : L.Xh, ojp = j < L.ny ? L.Xh : -L.Xh;
   T v[KZ];
   uint8_t d[KZ];
 #pragma unroll
@@ -133,22 +139,21 @@ __global__ void __launch_bounds__(kSlotThreads) k_smooth(T *u, const T *f, const
     v[p] = 0;
     d[p] = 1;
     if (k > 0 && k < L.nz) {   // the k = 0 and k = nz planes are Dirichlet
-      const int64_t m = (int64_t)k * L.P + q;
-      const int i = 2 * t + ((j + k + c) & 1);
-      d[p] = dc[m];
+      const int o = p * P;
+      d[p] = dc[o];
       if (first) {
-        v[p] = h2 * fc[m];
+        v[p] = h2 * fc[o];
       } else {
+        const int i = 2 * t + ((j + k + c) & 1);
         const int im = i > 0 ? i - 1 : 1, ip = i < L.nx ? i + 1 : L.nx - 1;
-        const int64_t rb = m - t;
-        v[p] = uo[rb + (im >> 1)] + uo[rb + (ip >> 1)] + uo[m + ojm] + uo[m + ojp] + uo[m - L.P] + uo[m + L.P] +
-               h2 * fc[m];
+        v[p] = uo[o + (im >> 1) - t] + uo[o + (ip >> 1) - t] + uo[o + ojm] + uo[o + ojp] + uo[o - P] + uo[o + P] +
+               h2 * fc[o];
       }
     }
   }
 #pragma unroll
   for (int p = 0; p < KZ; ++p)
-    if (!d[p]) uc[(int64_t)(k0 + p) * L.P + q] = v[p] * (T)(1.0 / 6.0);
+    if (!d[p]) uc[p * P] = v[p] * (T)(1.0 / 6.0);
 }
 
 // r = f - A u at the colour-0 nodes.  The V-cycle's last pre-smoothing sweep updates colour 1,
@@ -282,6 +287,187 @@ __global__ void __launch_bounds__(1024) k_coarse_direct(T *u, const T *f, const 
     T acc = 0;
     for (int c = 0; c < nf; ++c) acc += ainvT[(int64_t)c * nf + r] * fs[c];
     u[slot[r]] = acc;
+  }
+}
+
+// ---- the coarse tail of the V-cycle in one thread-block cluster --------------------------------
+// Levels from kTailNodes nodes down are too small to fill the GPU: each of their ~11 passes per
+// V-cycle would be a short launch.  One cluster of kTailCtas CTAs runs the whole tail instead --
+// pre-smoothing, residual and restriction level by level, the direct solve on the coarsest
+// level, then prolongation and post-smoothing back up -- with the hardware cluster barrier
+// (barrier.cluster arrive.release / wait.acquire, no spinning on flags) between passes, which
+// also orders the global-memory writes of one pass before the reads of the next.  Each pass is
+// the per-slot arithmetic of the level kernels above (k_smooth, k_residual, k_restrict,
+// k_prolong) spread over the cluster's threads.
+constexpr int kTailCtas = 8, kTailThreads = 1024, kMaxTail = 8;
+constexpr int64_t kTailNodes = 80000;
+
+template <typename T>
+struct TailArgs {
+  int nl;                           // levels in the tail; the last one is the coarsest
+  Lv lv[kMaxTail];
+  T *u[kMaxTail], *f[kMaxTail], *r[kMaxTail];
+  const uint8_t *dirs[kMaxTail];
+  T h2[kMaxTail], inv_h2[kMaxTail];
+  const T *ainv;                    // coarsest level: transposed inverse (times h^2), free slots
+  const int32_t *cslot;
+  int nf;
+};
+
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+}
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;\n" : "=r"(r));
+  return r;
+}
+
+// slot m (colour-array index over all planes) -> (t, j, k)
+__device__ __forceinline__ void slot_tjk(const Lv &L, uint32_t m, int *t, int *j, int *k) {
+  const uint32_t kk = fdiv(m, L.pd), q = m - kk * L.P;
+  const uint32_t jj = fdiv(q, L.xd);
+  *k = (int)kk;
+  *j = (int)jj;
+  *t = (int)(q - jj * (uint32_t)L.Xh);
+}
+
+template <typename T>
+__device__ void tail_smooth(const TailArgs<T> &a, int l, int c, bool first, uint32_t g0, uint32_t gs) {
+  const Lv &L = a.lv[l];
+  T *u = a.u[l];
+  const T *uo = u + (int64_t)(c ^ 1) * L.nper;
+  const T *fc = a.f[l] + (int64_t)c * L.nper;
+  const uint8_t *dc = a.dirs[l] + (int64_t)c * L.nper;
+  const uint32_t n = (uint32_t)L.nper;
+  for (uint32_t m = g0; m < n; m += gs) {
+    int t, j, k;
+    slot_tjk(L, m, &t, &j, &k);
+    if (k == 0 || k == L.nz || dc[m]) continue;
+    T v;
+    if (first) {
+      v = a.h2[l] * fc[m];
+    } else {
+      const int i = 2 * t + ((j + k + c) & 1);
+      const int im = i > 0 ? i - 1 : 1, ip = i < L.nx ? i + 1 : L.nx - 1;
+      const int64_t rb = (int64_t)m - t;
+      const int64_t ojm = j > 0 ? -(int64_t)L.Xh : (int64_t)L.Xh, ojp = j < L.ny ? (int64_t)L.Xh : -(int64_t)L.Xh;
+      v = uo[rb + (im >> 1)] + uo[rb + (ip >> 1)] + uo[m + ojm] + uo[m + ojp] + uo[m - L.P] + uo[m + L.P] +
+          a.h2[l] * fc[m];
+    }
+    u[(int64_t)c * L.nper + m] = v * (T)(1.0 / 6.0);
+  }
+}
+
+template <typename T>
+__device__ void tail_residual(const TailArgs<T> &a, int l, uint32_t g0, uint32_t gs) {
+  const Lv &L = a.lv[l];
+  const T *u = a.u[l], *uo = u + L.nper, *f = a.f[l];
+  T *r = a.r[l];
+  const uint8_t *d = a.dirs[l];
+  const uint32_t n = (uint32_t)L.nper;
+  for (uint32_t m = g0; m < n; m += gs) {
+    int t, j, k;
+    slot_tjk(L, m, &t, &j, &k);
+    T v = 0;
+    if (k > 0 && k < L.nz && !d[m]) {
+      const int i = 2 * t + ((j + k) & 1);
+      const int im = i > 0 ? i - 1 : 1, ip = i < L.nx ? i + 1 : L.nx - 1;
+      const int64_t rb = (int64_t)m - t;
+      const int64_t ojm = j > 0 ? -(int64_t)L.Xh : (int64_t)L.Xh, ojp = j < L.ny ? (int64_t)L.Xh : -(int64_t)L.Xh;
+      const T nb = uo[rb + (im >> 1)] + uo[rb + (ip >> 1)] + uo[m + ojm] + uo[m + ojp] + uo[m - L.P] + uo[m + L.P];
+      v = f[m] - (6 * u[m] - nb) * a.inv_h2[l];
+    }
+    r[m] = v;
+  }
+}
+
+template <typename T>
+__device__ void tail_restrict(const TailArgs<T> &a, int l, uint32_t g0, uint32_t gs) {
+  const Lv &Fl = a.lv[l], &Cl = a.lv[l + 1];
+  const T *rf = a.r[l];
+  T *fc = a.f[l + 1];
+  const uint8_t *dc = a.dirs[l + 1];
+  const uint32_t n = 2u * (uint32_t)Cl.nper;
+  for (uint32_t m2 = g0; m2 < n; m2 += gs) {
+    const int cc = m2 >= (uint32_t)Cl.nper ? 1 : 0;
+    const uint32_t m = m2 - (cc ? (uint32_t)Cl.nper : 0u);
+    int T_, J, K;
+    slot_tjk(Cl, m, &T_, &J, &K);
+    const int I = 2 * T_ + ((J + K + cc) & 1);
+    if (I > Cl.nx) continue;
+    if (dc[m2]) { fc[m2] = 0; continue; }
+    const int i0 = 2 * I, j0 = 2 * J, k0 = 2 * K;
+    const int im = mirror(i0 - 1, Fl.nx), ip = mirror(i0 + 1, Fl.nx);
+    const int jm = mirror(j0 - 1, Fl.ny), jp = mirror(j0 + 1, Fl.ny);
+#define RF(i, j, k) rf[srow(Fl, (j), (k)) + ((i) >> 1)]
+    const T ctr = RF(i0, j0, k0);
+    const T xy = RF(im, jm, k0) + RF(ip, jm, k0) + RF(im, jp, k0) + RF(ip, jp, k0);
+    const T xz = RF(im, j0, k0 - 1) + RF(ip, j0, k0 - 1) + RF(im, j0, k0 + 1) + RF(ip, j0, k0 + 1);
+    const T yz = RF(i0, jm, k0 - 1) + RF(i0, jp, k0 - 1) + RF(i0, jm, k0 + 1) + RF(i0, jp, k0 + 1);
+#undef RF
+    fc[m2] = (T)0.125 * ctr + (T)0.03125 * ((xy + xz) + yz);
+  }
+}
+
+template <typename T>
+__device__ void tail_prolong(const TailArgs<T> &a, int l, uint32_t g0, uint32_t gs) {
+  const Lv &Fl = a.lv[l], &Cl = a.lv[l + 1];
+  const T *uc = a.u[l + 1];
+  T *uf = a.u[l];
+  const uint8_t *df = a.dirs[l];
+  const uint32_t n = 2u * (uint32_t)Fl.nper;
+  for (uint32_t m2 = g0; m2 < n; m2 += gs) {
+    const int c = m2 >= (uint32_t)Fl.nper ? 1 : 0;
+    const uint32_t m = m2 - (c ? (uint32_t)Fl.nper : 0u);
+    int t, j, k;
+    slot_tjk(Fl, m, &t, &j, &k);
+    if (k == 0 || k == Fl.nz || df[m2]) continue;
+    const int i = min(2 * t + ((j + k + c) & 1), Fl.nx);
+    const int i0 = i >> 1, j0 = j >> 1, k0 = k >> 1;
+    const int i1 = i0 + (i & 1), j1 = j0 + (j & 1), k1 = k0 + (k & 1);
+    const T s = (T)0.125 * (uc[sidx(Cl, i0, j0, k0)] + uc[sidx(Cl, i1, j0, k0)] + uc[sidx(Cl, i0, j1, k0)] +
+                            uc[sidx(Cl, i1, j1, k0)] + uc[sidx(Cl, i0, j0, k1)] + uc[sidx(Cl, i1, j0, k1)] +
+                            uc[sidx(Cl, i0, j1, k1)] + uc[sidx(Cl, i1, j1, k1)]);
+    uf[m2] = uf[m2] + s;
+  }
+}
+
+template <typename T>
+__global__ void __cluster_dims__(kTailCtas, 1, 1) __launch_bounds__(kTailThreads, 1) k_vcycle_tail(TailArgs<T> a) {
+  const uint32_t gs = kTailCtas * kTailThreads;
+  const uint32_t g0 = cluster_rank() * kTailThreads + threadIdx.x;
+  const int last = a.nl - 1;
+  for (int l = 0; l < last; ++l) {
+    for (int s = 0; s < 2; ++s)
+      for (int c = 0; c < 2; ++c) {
+        tail_smooth<T>(a, l, c, s == 0 && c == 0, g0, gs);
+        cluster_sync_all();
+      }
+    tail_residual<T>(a, l, g0, gs);
+    cluster_sync_all();
+    tail_restrict<T>(a, l, g0, gs);
+    cluster_sync_all();
+  }
+  // coarsest level: u = A^-1 f on its free nodes (rows spread over the cluster's threads)
+  {
+    const T *f = a.f[last];
+    T *u = a.u[last];
+    for (uint32_t rw = g0; rw < (uint32_t)a.nf; rw += gs) {
+      T acc = 0;
+      for (int c = 0; c < a.nf; ++c) acc += a.ainv[(int64_t)c * a.nf + rw] * f[a.cslot[c]];
+      u[a.cslot[rw]] = acc;
+    }
+    cluster_sync_all();
+  }
+  for (int l = last - 1; l >= 0; --l) {
+    tail_prolong<T>(a, l, g0, gs);
+    cluster_sync_all();
+    for (int s = 0; s < 2; ++s)
+      for (int c = 1; c >= 0; --c) {
+        tail_smooth<T>(a, l, c, false, g0, gs);
+        cluster_sync_all();
+      }
   }
 }
 
@@ -577,6 +763,27 @@ static void vcycle(pic_t *h, int l) {
   const Lv lv = lv_of(L);
   const T h2 = (T)(L.h * L.h), inv_h2 = (T)(1.0 / (L.h * L.h));
   const int last = (int)h->mg.size() - 1;
+  if (l == h->tail_start && l < last) {   // the small levels in one cluster launch
+    TailArgs<T> ta;
+    ta.nl = last - l + 1;
+    for (int q = 0; q < ta.nl; ++q) {
+      MgLevel &M = h->mg[l + q];
+      ta.lv[q] = lv_of(M);
+      ta.u[q] = lvl_u<T>(M);
+      ta.f[q] = lvl_f<T>(M);
+      ta.r[q] = lvl_r<T>(M);
+      ta.dirs[q] = M.dirs;
+      ta.h2[q] = (T)(M.h * M.h);
+      ta.inv_h2[q] = (T)(1.0 / (M.h * M.h));
+    }
+    ta.ainv = coarse_inv<T>(h);
+    ta.cslot = h->coarse_slot;
+    ta.nf = h->coarse_n;
+    ++h->nlaunch;
+    KtScope kt_(h, kidTail, (double)L.nnode);
+    k_vcycle_tail<T><<<kTailCtas, kTailThreads, 0, h->stream>>>(ta);
+    return;
+  }
   if (l == last) {
     ++h->nlaunch;
     KtScope kt_(h, kidCoarse, (double)L.nnode);
@@ -717,6 +924,11 @@ int mg_coarse_setup(pic_t *h) {
                               h->stream));
   PIC_CUDA(h, cudaStreamSynchronize(h->stream));
   h->coarse_n = nf;
+  // the cluster tail takes every level from the first one of at most kTailNodes nodes down
+  const int last = (int)h->mg.size() - 1;
+  h->tail_start = -1;
+  for (int l = 0; l < last; ++l)
+    if (h->mg[l].nnode <= kTailNodes && last - l + 1 <= kMaxTail) { h->tail_start = l; break; }
   return PIC_OK;
 }
 

@@ -1,7 +1,8 @@
 // Emission surrogate inference on the fifth-generation tensor cores (tcgen05, TMEM accumulator):
 // the whole forward pass of the 7 -> 128 -> 128 -> 128 -> 2 MLP in one persistent kernel.
 //
-// A CTA of 128 threads owns a tile of 128 rows (one row per thread) at a time:
+// A CTA of 256 threads owns a tile of 128 rows at a time, two threads per row (each takes half of
+// the 128 columns; warps w and w + 4 share TMEM lanes 32 (w % 4) .. 32 (w % 4) + 31):
 //   layer 1 (7 -> 128, FP32 on the CUDA cores) -> GELU -> BF16 activations in shared memory;
 //   layer 2: 8 tcgen05.mma (M = N = 128, K = 16 each) from shared memory into a 128-column FP32
 //            accumulator in tensor memory; tcgen05.ld brings each row back to its thread for
@@ -31,7 +32,8 @@ namespace pic {
 namespace {
 
 constexpr int kH = 128, kIn = 7, kXld = 8, kOut = 2;
-constexpr int kTile = 128;                     // rows per tile = threads per CTA = MMA M
+constexpr int kTile = 128;                     // rows per tile = MMA M
+constexpr int kThreadsTc = 256;                // two threads per row
 constexpr int kMatBytes = kH * kH * 2;         // one 128 x 128 BF16 operand
 constexpr uint32_t kLBO = 128, kSBO = 2048;    // core-matrix offsets along K and along M/N
 constexpr uint32_t kTmemCols = 128;            // FP32 accumulator columns (N)
@@ -43,6 +45,7 @@ struct Smem {
   alignas(1024) unsigned char W2[kMatBytes];
   alignas(1024) unsigned char W3[kMatBytes];
   float w1[kH * kIn], b1[kH], b2[kH], b3[kH], w4[kOut * kH], b4[kOut];
+  float ypart[2][kTile];                       // second half's output-layer partial sums
   alignas(8) unsigned long long bar;
   uint32_t tmem;
   int fail;
@@ -130,25 +133,28 @@ __device__ __forceinline__ void store8(unsigned char *A, int row, int q, const f
 
 // Y (rows x 2) of the feature rows X (rows x 8, 7 used); master: FP32 parameters in the public
 // layout (W1 b1 W2 b2 W3 b3 W4 b4, row-major [out][in]); w2, w3: their BF16 copies.
-__global__ void __launch_bounds__(kTile, 1) k_mlp_forward_tc(const float *__restrict__ X, int64_t rows,
+__global__ void __launch_bounds__(kThreadsTc, 1) k_mlp_forward_tc(const float *__restrict__ X, int64_t rows,
                                                             const float *__restrict__ master,
                                                             const __nv_bfloat16 *__restrict__ w2,
                                                             const __nv_bfloat16 *__restrict__ w3, float *Y, int *err) {
   extern __shared__ unsigned char smem_raw[];
   Smem &S = *reinterpret_cast<Smem *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const int tid = threadIdx.x, warp = tid >> 5;
+  const int row = tid & (kTile - 1), half = tid >> 7;   // this thread's row and column half
   constexpr int oW1 = 0, oB1 = kH * kIn, oW2 = oB1 + kH, oB2 = oW2 + kH * kH, oW3 = oB2 + kH, oB3 = oW3 + kH * kH,
                 oW4 = oB3 + kH, oB4 = oW4 + kOut * kH;
-  for (int e = tid; e < kH * kH; e += kTile) {
+  for (int e = tid; e < kH * kH; e += kThreadsTc) {
     const int n = e / kH, k = e - n * kH;
     *reinterpret_cast<__nv_bfloat16 *>(S.W2 + core_off(n, k)) = w2[e];
     *reinterpret_cast<__nv_bfloat16 *>(S.W3 + core_off(n, k)) = w3[e];
   }
-  for (int e = tid; e < kH * kIn; e += kTile) S.w1[e] = master[oW1 + e];
-  for (int e = tid; e < kOut * kH; e += kTile) S.w4[e] = master[oW4 + e];
-  S.b1[tid] = master[oB1 + tid];
-  S.b2[tid] = master[oB2 + tid];
-  S.b3[tid] = master[oB3 + tid];
+  for (int e = tid; e < kH * kIn; e += kThreadsTc) S.w1[e] = master[oW1 + e];
+  for (int e = tid; e < kOut * kH; e += kThreadsTc) S.w4[e] = master[oW4 + e];
+  if (tid < kH) {
+    S.b1[tid] = master[oB1 + tid];
+    S.b2[tid] = master[oB2 + tid];
+    S.b3[tid] = master[oB3 + tid];
+  }
   if (tid < kOut) S.b4[tid] = master[oB4 + tid];
   const uint32_t bar = smem_u32(&S.bar);
   if (tid == 0) {
@@ -167,16 +173,16 @@ __global__ void __launch_bounds__(kTile, 1) k_mlp_forward_tc(const float *__rest
   __syncthreads();
   fence_after_sync();
   const uint32_t tmem = S.tmem;
-  const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);   // this warp's 32 lanes (rows)
+  const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16);   // this warp's 32 lanes (rows)
   const uint32_t a_addr = smem_u32(S.A), w_addr[2] = {smem_u32(S.W2), smem_u32(S.W3)};
   uint32_t phase = 0;
   for (int64_t t0 = (int64_t)blockIdx.x * kTile; t0 < rows; t0 += (int64_t)gridDim.x * kTile) {
-    const int64_t r = t0 + tid;
+    const int64_t r = t0 + row;
     float x[kIn];
 #pragma unroll
     for (int c = 0; c < kIn; ++c) x[c] = r < rows ? X[r * kXld + c] : 0.f;
-    // layer 1 (FP32), GELU, BF16 activations of this row
-    for (int q = 0; q < kH / 8; ++q) {
+    // layer 1 (FP32), GELU, BF16 activations of this row's column half
+    for (int q = half * (kH / 16); q < (half + 1) * (kH / 16); ++q) {
       float a[8];
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
@@ -186,7 +192,7 @@ __global__ void __launch_bounds__(kTile, 1) k_mlp_forward_tc(const float *__rest
         for (int c = 0; c < kIn; ++c) z += S.w1[o * kIn + c] * x[c];
         a[u] = gelu_f(z);
       }
-      store8(S.A, tid, q, a);
+      store8(S.A, row, q, a);
     }
     float y0 = 0.f, y1 = 0.f;
     for (int layer = 0; layer < 2; ++layer) {
@@ -208,7 +214,7 @@ __global__ void __launch_bounds__(kTile, 1) k_mlp_forward_tc(const float *__rest
       __syncthreads();
       if (S.fail) break;
       const float *bias = layer == 0 ? S.b2 : S.b3;
-      for (int cc = 0; cc < kH / 32; ++cc) {
+      for (int cc = half * 2; cc < half * 2 + 2; ++cc) {   // this thread's 64 columns
         float v[32];
         tmem_ld32(taddr + 32 * cc, v);
         if (layer == 0) {
@@ -217,7 +223,7 @@ __global__ void __launch_bounds__(kTile, 1) k_mlp_forward_tc(const float *__rest
             float a[8];
 #pragma unroll
             for (int u = 0; u < 8; ++u) a[u] = gelu_f(v[8 * q + u] + bias[32 * cc + 8 * q + u]);
-            store8(S.A, tid, 4 * cc + q, a);
+            store8(S.A, row, 4 * cc + q, a);
           }
         } else {
 #pragma unroll
@@ -233,9 +239,14 @@ __global__ void __launch_bounds__(kTile, 1) k_mlp_forward_tc(const float *__rest
       fence_before_sync();
     }
     if (S.fail) break;
-    if (r < rows) {
-      Y[r * kOut] = y0 + S.b4[0];
-      Y[r * kOut + 1] = y1 + S.b4[1];
+    if (half) {
+      S.ypart[0][row] = y0;
+      S.ypart[1][row] = y1;
+    }
+    __syncthreads();
+    if (!half && r < rows) {
+      Y[r * kOut] = (y0 + S.ypart[0][row]) + S.b4[0];
+      Y[r * kOut + 1] = (y1 + S.ypart[1][row]) + S.b4[1];
     }
     fence_before_sync();
     __syncthreads();   // A and the accumulator are free for the next tile
@@ -249,7 +260,7 @@ __global__ void __launch_bounds__(kTile, 1) k_mlp_forward_tc(const float *__rest
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kTmemCols) : "memory");
 }
 
-// Launch the fused forward pass for `rows` feature rows (one CTA per SM at most).
+// Launch the fused forward pass for `rows` feature rows (two CTAs per SM at most).
 int mlp_forward_tc(pic_t *h, const float *X, int64_t rows, const float *master, const __nv_bfloat16 *w2,
                    const __nv_bfloat16 *w3, float *Y) {
   if (rows <= 0) return PIC_OK;
@@ -262,9 +273,9 @@ int mlp_forward_tc(pic_t *h, const float *X, int64_t rows, const float *master, 
     configured_dev = dev;
   }
   const int64_t tiles = (rows + kTile - 1) / kTile;
-  const int grid = (int)std::min<int64_t>(tiles, (int64_t)h->nsm);
+  const int grid = (int)std::min<int64_t>(tiles, 2 * (int64_t)h->nsm);   // two CTAs fit an SM
   ++h->nlaunch;
-  k_mlp_forward_tc<<<grid, kTile, smem, h->stream>>>(X, rows, master, w2, w3, Y, &h->clock->err);
+  k_mlp_forward_tc<<<grid, kThreadsTc, smem, h->stream>>>(X, rows, master, w2, w3, Y, &h->clock->err);
   return launch_check(h, "mlp forward (tcgen05)");
 }
 

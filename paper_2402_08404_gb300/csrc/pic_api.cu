@@ -197,7 +197,7 @@ namespace pic {
 const char *const kKernelNames[kidNum] = {
     "k_push", "k_keys", "k_scatter", "k_fix_short", "k_fix_mid", "k_fix_long", "k_gather", "k_scan_partial",
     "k_scan_apply", "k_deposit", "k_mcc_count", "k_mcc_products", "k_dfi_count", "k_dfi_products", "k_dirichlet",
-    "k_residual64", "k_norm_sum", "k_smooth", "k_smooth_first", "k_residual", "k_restrict", "k_prolong", "k_coarse",
+    "k_residual64", "k_norm_sum", "k_smooth", "k_smooth_first", "k_residual", "k_restrict", "k_prolong", "k_coarse", "k_vcycle_tail",
     "k_correct", "k_efield", "k_face_field", "k_emit_surrogate", "k_emit_fallback", "k_emit_count", "k_emit_write",
     "k_inject_count", "k_inject_write", "k_mlp_forward", "k_heat"};
 

@@ -163,6 +163,7 @@ struct pic_s {
   float *coarse_inv_f = nullptr;    // its inverse operator times h^2, transposed (nf x nf)
   double *coarse_inv_d = nullptr;
   int32_t *coarse_slot = nullptr;   // split-layout slot of each free node
+  int tail_start = -1;              // first level of the cluster-launched V-cycle tail (-1: none)
   pic::DevClock *clock = nullptr;
   // scratch
   void *scan_tmp = nullptr;      // block partials for scans
@@ -272,7 +273,7 @@ namespace pic {
 enum Kid : int {
   kidPush = 0, kidKeys, kidScatter, kidFixShort, kidFixMid, kidFixLong, kidGather, kidScanPartial, kidScanApply,
   kidDeposit, kidMccCount, kidMccProducts, kidDfiCount, kidDfiProducts, kidDirichlet, kidResidual64, kidNormSum,
-  kidSmooth, kidSmoothFirst, kidResidual, kidRestrict, kidProlong, kidCoarse, kidCorrect, kidEfield, kidFaceField,
+  kidSmooth, kidSmoothFirst, kidResidual, kidRestrict, kidProlong, kidCoarse, kidTail, kidCorrect, kidEfield, kidFaceField,
   kidEmitSurrogate, kidEmitFallback, kidEmitCount, kidEmitWrite, kidInjectCount, kidInjectWrite, kidMlpForward,
   kidHeat, kidNum
 };
