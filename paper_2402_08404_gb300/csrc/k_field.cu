@@ -87,6 +87,13 @@ __host__ __device__ __forceinline__ int64_t sidx(const Lv &L, int i, int j, int 
   return (int64_t)((i + j + k) & 1) * L.nper + srow(L, j, k) + (i >> 1);
 }
 
+// the same in 32-bit arithmetic (both colours of a level hold fewer than 2^32 slots, checked at
+// creation): one index multiply-add chain instead of 64-bit ones
+__device__ __forceinline__ uint32_t sidx32(const Lv &L, int i, int j, int k) {
+  return (uint32_t)((i + j + k) & 1) * (uint32_t)L.nper + ((uint32_t)k * (uint32_t)(L.ny + 1) + (uint32_t)j) * (uint32_t)L.Xh +
+         (uint32_t)(i >> 1);
+}
+
 // planes per thread in the level sweeps
 constexpr int kKZ = 4;
 
@@ -241,10 +248,10 @@ __global__ void __launch_bounds__(kSlotThreads) k_prolong(const TC *uc, Lv Cl, T
 #pragma unroll
   for (int r = 0; r < 3; ++r) {
     const int K = min(Kb + r, Cl.nz);
-    cv[r][0] = uc[sidx(Cl, t, j0, K)];
-    cv[r][1] = uc[sidx(Cl, t1, j0, K)];
-    cv[r][2] = uc[sidx(Cl, t, j1, K)];
-    cv[r][3] = uc[sidx(Cl, t1, j1, K)];
+    cv[r][0] = uc[sidx32(Cl, t, j0, K)];
+    cv[r][1] = uc[sidx32(Cl, t1, j0, K)];
+    cv[r][2] = uc[sidx32(Cl, t, j1, K)];
+    cv[r][3] = uc[sidx32(Cl, t1, j1, K)];
   }
   TF v[kKZ];
   uint8_t d[kKZ];
@@ -599,7 +606,7 @@ __global__ void __launch_bounds__(256) k_residual64(const long long *phi, const 
         t = f - (6 * cz[p + 1] - (side[p] + cz[p] + cz[p + 2]));
       }
       const float tf = fx_to_float(t);
-      fl[sidx(L, i, j, k)] = d[p] ? (T)0 : fx_to_level(t, c_lvl);
+      fl[sidx32(L, i, j, k)] = d[p] ? (T)0 : fx_to_level(t, c_lvl);
       const float rs = tf * 9.094947017729282e-13f;   // h^2 r = t 2^-40
       s += rs * rs;
       if (lift && !d[p]) {

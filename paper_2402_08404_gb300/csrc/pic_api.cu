@@ -299,7 +299,8 @@ int pic_create(const pic_geometry_t *geometry, const pic_grid_t *grid, const pic
   if (grid->nx < 8 || grid->ny < 8 || grid->nz < 8 || (grid->nx & 1) || (grid->ny & 1) || (grid->nz & 1) || !(grid->dx > 0))
     return PIC_E_INVALID;
   if ((int64_t)grid->nx * grid->ny * grid->nz >= (int64_t)0xFFFFFFF0u) return PIC_E_INVALID;
-  if ((int64_t)(grid->nx + 1) * (grid->ny + 1) * (grid->nz + 1) >= (int64_t)0xFFFFFFFFu) return PIC_E_INVALID;
+  // node arrays and the split-colour levels ((nx + 2) slots per row pair) are indexed in 32 bits
+  if ((int64_t)(grid->nx + 2) * (grid->ny + 1) * (grid->nz + 1) >= (int64_t)0xFFFFFFFFu) return PIC_E_INVALID;
   if (!(params->dt > 0) || !(params->w_min > 0) || params->w_max_units < 1) return PIC_E_INVALID;
   for (int s = 0; s < 3; ++s)
     if (species[s].capacity < 1 || species[s].capacity > 0x7FFFFFFF || !(species[s].mass > 0)) return PIC_E_INVALID;
