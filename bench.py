@@ -207,6 +207,8 @@ def run_ours(args):
             sim.load_particles(s, pop[k])
         sim.set_clock(0, n_sp)
         sim.solve_field()
+        # launch shapes picked by the library's autotuner on this state (untimed set-up)
+        tune = sim.autotune() if args.autotune else None
         sur = None
         if prod_flags & pic.F_SURROGATE:
             # the learned emission model: trained here on the library's own FP64 integral (untimed)
@@ -338,7 +340,7 @@ def run_ours(args):
                        "valid_sample_fraction": round(sur["valid_sample_fraction"], 3),
                        "faces_served_per_step": round(sur_faces / max(sim.nface, 1), 4),
                        "train_s": round((sur["ms_data"] + sur["ms_train"]) / 1e3, 2)},
-                   "plain_form": plain, "graph_form": graph},
+                   "plain_form": plain, "graph_form": graph, "autotune": tune},
         "roofline": roof,
         "clocks": clk.summary(),
         "e2e": {"value": tot_e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
@@ -515,6 +517,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-sample", type=int, default=60000)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false")
     args = ap.parse_args()
     if args.impl == "reference":
         out = run_reference(args)
