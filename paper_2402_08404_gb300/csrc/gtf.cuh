@@ -352,6 +352,55 @@ __device__ __forceinline__ double transmission_sel(const Barrier &b, const Const
   return kFast ? transmission_f32(b, C, T, W, xm) : transmission(b, C, T, W, xm);
 }
 
+// Fast path of one energy node: D(W) supply(W) and D(W) I(W) with the turning points, the Gamow
+// quadrature, D and the two Fermi functions in FP32, and FP64 only where FP32 would underflow.
+// G is the same FP32 Gamow exponent as transmission_f32's.  Where D or the Fermi factors fall
+// below the FP32 range (G >= 80 or W >= 80 kT), the product is formed in log space with one
+// FP64 exp: for W >= 80 kT, supply = kT e^{-w} and I = -(kT)^2 (w + 1) e^{-w} to within e^{-w}.
+__device__ inline void eval_fast(const Barrier &b, const Consts &C, const Tables &T, double W, double xm, double kT,
+                                 double inv_kT, double phimFR, double *DS, double *DI) {
+  *DS = 0.0;
+  *DI = 0.0;
+  const double ad = b.phi - W;   // FP64 first: the cancellation near the turning points
+  const float af = (float)ad, Ff = (float)b.F, Rf = (float)b.R, Qf = (float)b.Q;
+  float x1, x2;
+  const float disc = af * af - 4.0f * Qf * Ff;
+  const float sq = sqrtf(fmaxf(disc, 0.0f));
+  if (b.flat) {
+    x1 = 2.0f * Qf / (af + sq);
+    x2 = (af + sq) / (2.0f * Ff);
+  } else {
+    if (phimFR >= W) return;   // the barrier never comes back down to W
+    const float xmf = (float)xm;
+    float lo = xmf;
+    for (int i = 0; i < 200 && uw_f32(false, af, Ff, Rf, Qf, lo) > 0.0f; ++i) lo *= 0.5f;
+    x1 = root_f32(false, af, Ff, Rf, Qf, lo, xmf, disc > 0.0f ? 2.0f * Qf / (af + sq) : 0.5f * xmf);
+    const float sr = af / (Ff * Rf);
+    const float hi = 2.0f * sr * Rf / (1.0f - sr) + 2.0f * xmf;
+    x2 = root_f32(false, af, Ff, Rf, Qf, xmf, hi, disc > 0.0f ? (af + sq) / (2.0f * Ff) : 2.0f * xmf);
+  }
+  const float m = 0.5f * (x1 + x2), h = 0.5f * (x2 - x1);
+  float sg = 0.0f;
+  for (int i = 0; i < 32; ++i) {
+    const float x = m - h * T.c32f[i];
+    sg += T.w32f[i] * sqrtf(fmaxf(uw_f32(b.flat, af, Ff, Rf, Qf, x), 0.0f)) * T.s32f[i];
+  }
+  const float G = (float)C.g * 1.5707963267948966f * h * sg;
+  const double w = W * inv_kT;
+  if (w < 80.0) {
+    const float Wf = (float)W, kTf = (float)kT;
+    const double S = (double)supply_f(Wf, kTf), I = (double)inner_f(Wf, kTf);
+    const double D = G < 80.0f ? (double)(1.0f / (1.0f + expf(G))) : exp(-(double)G);
+    *DS = D * S;
+    *DI = D * I;
+  } else {
+    const double lnD = G < 80.0f ? -(double)log1pf(expf(G)) : -(double)G;
+    const double e = exp(lnD - w);
+    *DS = kT * e;
+    *DI = -(kT * kT) * (w + 1.0) * e;
+  }
+}
+
 // kFast: transmission_f32 at every node (J, P_N to ~1e-5 relative); else all FP64
 template <bool kFast>
 __device__ inline void current_density_warp(const Consts &C, const Tables &T, double F, double Temp, double phi,
@@ -362,7 +411,8 @@ __device__ inline void current_density_warp(const Consts &C, const Tables &T, do
   b.F = F; b.phi = phi; b.Q = C.Q;
   b.flat = !(R > 0.0) || !isfinite(R);
   b.R = b.flat ? 1.0 : R;
-  const double kT = C.kB * Temp;
+  const double kT = C.kB * Temp, inv_kT = 1.0 / kT;
+  const double phimFR = b.flat ? -1e300 : b.phi - b.F * b.R;   // W at or below it: D = 0 (curved)
   double xm, Um;
   barrier_top(b, &xm, &Um);
   const double top = fmax(Um, C.Wlo);
@@ -404,9 +454,17 @@ __device__ inline void current_density_warp(const Consts &C, const Tables &T, do
       }
       const double mid = 0.5 * (a + c), hw = 0.5 * (c - a);
       const double W = mid + hw * T.x16[i];
-      const double D = transmission_sel<kFast>(b, C, T, W, xm);
-      Jl += hw * T.w16[i] * D * supply_sel<kFast>(W, kT);
-      Pl += hw * T.w16[i] * D * inner_sel<kFast>(W, kT);
+      if (kFast) {
+        double DS, DI;
+        eval_fast(b, C, T, W, xm, kT, inv_kT, phimFR, &DS, &DI);
+        const double wt = hw * T.w16[i];
+        Jl += wt * DS;
+        Pl += wt * DI;
+      } else {
+        const double D = transmission_sel<kFast>(b, C, T, W, xm);
+        Jl += hw * T.w16[i] * D * supply_sel<kFast>(W, kT);
+        Pl += hw * T.w16[i] * D * inner_sel<kFast>(W, kT);
+      }
     }
     J += warp_sum_d(Jl);
     P += warp_sum_d(Pl);
@@ -427,9 +485,16 @@ __device__ inline void current_density_warp(const Consts &C, const Tables &T, do
         if (hi > lo) {
           const double mid = 0.5 * (lo + hi), hw = 0.5 * (hi - lo);
           const double W = mid + hw * T.x16[i];
-          const double D = transmission_sel<kFast>(b, C, T, W, xm);
-          Jl = hw * T.w16[i] * D * supply_sel<kFast>(W, kT);
-          Pl = hw * T.w16[i] * D * inner_sel<kFast>(W, kT);
+          if (kFast) {
+            double DS, DI;
+            eval_fast(b, C, T, W, xm, kT, inv_kT, phimFR, &DS, &DI);
+            Jl = hw * T.w16[i] * DS;
+            Pl = hw * T.w16[i] * DI;
+          } else {
+            const double D = transmission_sel<kFast>(b, C, T, W, xm);
+            Jl = hw * T.w16[i] * D * supply_sel<kFast>(W, kT);
+            Pl = hw * T.w16[i] * D * inner_sel<kFast>(W, kT);
+          }
         }
         const double rJ = warp_sum_d(Jl), rP = warp_sum_d(Pl);
         J += rJ;
