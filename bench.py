@@ -140,7 +140,7 @@ KERNEL_BYTES_PER_UNIT = {
 }
 # DRAM bytes (read + write) per launch from one ncu capture of the unchanged kernel on the
 # production grid (profiles/dram_traffic_multigrid_production_grid.md): (workload, kernel) -> bytes
-NCU_TRAFFIC_PER_LAUNCH = {("production", "k_smooth"): 35.89e6}
+NCU_TRAFFIC_PER_LAUNCH = {("production", "k_smooth"): 71.64e6}
 KERNEL_BYTES_PER_SP = {      # (bytes, species the launches of one step cover)
     "k_push": (56.0, "all"),         # pos+vel+w read 28, pos+vel write 24, key 4
     "k_gather": (76.0, "all"),       # perm 4 + 36 B record read + 36 B record write
