@@ -58,16 +58,27 @@ __device__ __forceinline__ int64_t scan_chunk(int64_t n, int nb) {
   return ((n + nb - 1) / nb + kItems - 1) / kItems * kItems;
 }
 
+// per-block chunk sums: whole 16-byte vectors while they last (chunks start on multiples of
+// kItems elements, so the vectors are aligned), the ragged end element by element
 template <typename T>
 __global__ void k_scan_partial(const T *__restrict__ in, int64_t n_host, const int64_t *n_dev, T *partial) {
   __shared__ T sh[33];
+  constexpr int kPer = 16 / (int)sizeof(T);
   const int64_t n = n_dev ? *n_dev : n_host;
   const int nb = gridDim.x;
   const int64_t chunk = scan_chunk(n, nb);
   const int64_t lo = (int64_t)blockIdx.x * chunk;
   const int64_t hi = lo + chunk < n ? lo + chunk : n;
   T s = 0;
-  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) s += in[i];
+  const int64_t nvec = hi > lo ? (hi - lo) / kPer : 0;
+  const uint4 *v = reinterpret_cast<const uint4 *>(in + lo);
+  for (int64_t q = threadIdx.x; q < nvec; q += blockDim.x) {
+    union { uint4 u; T e[kPer]; } x;
+    x.u = v[q];
+#pragma unroll
+    for (int e = 0; e < kPer; ++e) s += x.e[e];
+  }
+  for (int64_t i = lo + nvec * kPer + threadIdx.x; i < hi; i += blockDim.x) s += in[i];
   s = block_sum<T>(s, sh);
   if (threadIdx.x == 0) partial[blockIdx.x] = s;
 }
@@ -140,7 +151,7 @@ __global__ void k_scan_apply(const T *__restrict__ in, T *__restrict__ out, int6
 
 template <typename T>
 static int scan_impl(pic_t *h, const T *in, T *out, int64_t n, const int64_t *n_dev, T *total) {
-  const int nb = 2 * h->nsm;
+  const int nb = 4 * h->nsm;
   T *partial = (T *)h->scan_tmp;
   ++h->nlaunch;
   { KtScope kt_(h, kidScanPartial, (double)n); k_scan_partial<T><<<nb, kScanThreads, 0, h->stream>>>(in, n, n_dev, partial); }

@@ -409,7 +409,7 @@ int pic_create(const pic_geometry_t *geometry, const pic_grid_t *grid, const pic
     A(*p);
   }
   // scratch
-  h->scan_tmp = dalloc(h, (size_t)2 * h->nsm * sizeof(uint64_t)); A(h->scan_tmp);
+  h->scan_tmp = dalloc(h, (size_t)4 * h->nsm * sizeof(uint64_t)); A(h->scan_tmp);   // one partial per scan block
   // residual-norm partials: one pair per block of the 3D node grid (32 x 8 x 1 blocks)
   h->red = alloc_n<double>(h, (int64_t)2 * ((h->nx + 1 + 31) / 32) * ((h->ny + 1 + 7) / 8) * (h->nz + 1)); A(h->red);
   h->red_out = alloc_n<double>(h, 2); A(h->red_out);
