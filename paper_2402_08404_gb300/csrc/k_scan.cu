@@ -151,7 +151,7 @@ __global__ void k_scan_apply(const T *__restrict__ in, T *__restrict__ out, int6
 
 template <typename T>
 static int scan_impl(pic_t *h, const T *in, T *out, int64_t n, const int64_t *n_dev, T *total) {
-  const int nb = 4 * h->nsm;
+  const int nb = 2 * h->nsm;
   T *partial = (T *)h->scan_tmp;
   ++h->nlaunch;
   { KtScope kt_(h, kidScanPartial, (double)n); k_scan_partial<T><<<nb, kScanThreads, 0, h->stream>>>(in, n, n_dev, partial); }
