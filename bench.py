@@ -113,9 +113,10 @@ def stage_units(cfg, counts, mg_cycles, nface, emission_evals):
         "sort": ("hbm", 92.0 * n_sp + 36.0 * ncell),
         # pos + w per charged SP (16 B); node charge cleared and accumulated (16 B/node)
         "deposit": ("hbm", 16.0 * n_chg + 16.0 * nnode),
-        # per refinement cycle ~123 B/node (fixed-point residual 21, fine-level V-cycle 71 and its
-        # coarser levels ~10, correction 21); per solve a last residual 21, Dirichlet mask 1, field 24
-        "solve": ("hbm", (123.0 * max(mg_cycles, 1) + 46.0) * nnode),
+        # per refinement cycle ~153 B/node (fixed-point residual 21, fine-level V-cycle with 3 + 3
+        # sweeps 97 and its coarser levels ~14, correction 21); per solve a last residual 21 and the
+        # field 24
+        "solve": ("hbm", (153.0 * max(mg_cycles, 1) + 45.0) * nnode),
         # MCC + DFI: positions/offsets/velocities of e- and Cu (40 B) + neutral pass (24 B)
         "collide": ("hbm", 40.0 * (counts[0] + counts[1]) + 24.0 * counts[1]),
         # FP64 emission integral: ~640 flops per transmission evaluation (32-node Gamow quadrature,

@@ -95,6 +95,7 @@ typedef struct {
   uint32_t flags;       /* PIC_F_* */
   double mg_tol;        /* relative residual target of the Poisson solve */
   int mg_max_cycles;    /* cap on refinement cycles per solve */
+  int mg_sweeps;        /* red-black sweeps before and after each coarse-grid correction (<= 0: 3) */
 } pic_params_t;
 
 typedef struct {

@@ -8,7 +8,7 @@
 // Solve: refinement loop on the fixed-point potential -- t = h^2 (f - A phi) formed exactly in
 // int64 (charge term Q K rounded once, see charge_fx), stop when ||r||/||f_lifted|| < tol, else
 // one V-cycle on A e = r and phi += e rounded to the fixed-point grid.  The V-cycle runs in
-// float32 (mixed form) or float64 (plain form): red-black Gauss-Seidel 2+2 sweeps, full-
+// float32 (mixed form) or float64 (plain form): red-black Gauss-Seidel sweeps (3+3 by default), full-
 // weighting restriction, trilinear prolongation, and a direct solve on the coarsest level (its
 // inverse operator built at creation).  Coarse Dirichlet masks are injected from the fine nodes
 // they coincide with.
@@ -312,6 +312,7 @@ constexpr int64_t kTailNodes = 80000;
 template <typename T>
 struct TailArgs {
   int nl;                           // levels in the tail; the last one is the coarsest
+  int sweeps;                       // red-black sweeps before and after each coarse correction
   Lv lv[kMaxTail];
   T *u[kMaxTail], *f[kMaxTail], *r[kMaxTail];
   const uint8_t *dirs[kMaxTail];
@@ -446,7 +447,7 @@ __global__ void __cluster_dims__(kTailCtas, 1, 1) __launch_bounds__(kTailThreads
   const uint32_t g0 = cluster_rank() * kTailThreads + threadIdx.x;
   const int last = a.nl - 1;
   for (int l = 0; l < last; ++l) {
-    for (int s = 0; s < 2; ++s)
+    for (int s = 0; s < a.sweeps; ++s)
       for (int c = 0; c < 2; ++c) {
         tail_smooth<T>(a, l, c, s == 0 && c == 0, g0, gs);
         cluster_sync_all();
@@ -470,7 +471,7 @@ __global__ void __cluster_dims__(kTailCtas, 1, 1) __launch_bounds__(kTailThreads
   for (int l = last - 1; l >= 0; --l) {
     tail_prolong<T>(a, l, g0, gs);
     cluster_sync_all();
-    for (int s = 0; s < 2; ++s)
+    for (int s = 0; s < a.sweeps; ++s)
       for (int c = 1; c >= 0; --c) {
         tail_smooth<T>(a, l, c, false, g0, gs);
         cluster_sync_all();
@@ -762,8 +763,8 @@ static void smooth(pic_t *h, int l, MgLevel &L, const Lv &lv, T h2, int c, bool 
   smooth_launch<T>(h, L, lv, h2, c, first, h->tune_smooth_kz[l < 16 ? l : 15]);
 }
 
-// V-cycle on level l for A e = f_l, starting from e = 0: 2 red-black pre-sweeps (the first
-// takes e = 0), residual, restriction, the coarser cycle, prolongation, 2 post-sweeps.
+// V-cycle on level l for A e = f_l, starting from e = 0: mg_sweeps red-black pre-sweeps (the
+// first takes e = 0), residual, restriction, the coarser cycle, prolongation, mg_sweeps post-sweeps.
 template <typename T>
 static void vcycle(pic_t *h, int l) {
   MgLevel &L = h->mg[l];
@@ -773,6 +774,7 @@ static void vcycle(pic_t *h, int l) {
   if (l == h->tail_start && l < last) {   // the small levels in one cluster launch
     TailArgs<T> ta;
     ta.nl = last - l + 1;
+    ta.sweeps = h->mg_sweeps;
     for (int q = 0; q < ta.nl; ++q) {
       MgLevel &M = h->mg[l + q];
       ta.lv[q] = lv_of(M);
@@ -801,7 +803,7 @@ static void vcycle(pic_t *h, int l) {
       k_coarse<T><<<1, 1024, 0, h->stream>>>(lvl_u<T>(L), lvl_f<T>(L), L.dirs, lv, h2, 60);
     return;
   }
-  for (int s = 0; s < 2; ++s)
+  for (int s = 0; s < h->mg_sweeps; ++s)
     for (int c = 0; c < 2; ++c) smooth<T>(h, l, L, lv, h2, c, s == 0 && c == 0);
   ++h->nlaunch;
   { KtScope kt_(h, kidResidual, (double)L.nper); k_residual<T><<<flat_grid(lv, 1, kKZ), kSlotThreads, 0, h->stream>>>(lvl_u<T>(L), lvl_f<T>(L), lvl_r<T>(L), L.dirs, lv, inv_h2); }
@@ -812,7 +814,7 @@ static void vcycle(pic_t *h, int l) {
   vcycle<T>(h, l + 1);
   ++h->nlaunch;
   { KtScope kt_(h, kidProlong, (double)L.nnode); k_prolong<T, T><<<flat_grid(lv, 2, kKZ), kSlotThreads, 0, h->stream>>>(lvl_u<T>(Cl), cv, lvl_u<T>(L), L.dirs, lv); }
-  for (int s = 0; s < 2; ++s)
+  for (int s = 0; s < h->mg_sweeps; ++s)
     for (int c = 1; c >= 0; --c) smooth<T>(h, l, L, lv, h2, c, false);
 }
 

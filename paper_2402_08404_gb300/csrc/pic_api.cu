@@ -311,6 +311,9 @@ int pic_create(const pic_geometry_t *geometry, const pic_grid_t *grid, const pic
   h->geo = *geometry; h->prm = *params;
   if (h->prm.mg_tol <= 0) h->prm.mg_tol = 1e-8;
   if (h->prm.mg_max_cycles <= 0) h->prm.mg_max_cycles = 50;
+  // 3 + 3 sweeps: on the staircased tip a V-cycle contracts the error by ~0.4 with 2 + 2 and ~0.3
+  // with 3 + 3, which reaches a 1e-6 step tolerance in one refinement cycle instead of two
+  h->mg_sweeps = h->prm.mg_sweeps > 0 ? std::min(h->prm.mg_sweeps, 8) : 3;
   h->stream = (cudaStream_t)stream;
   h->alloc = alloc; h->free_fn = free_fn; h->alloc_user = alloc_user;
   int dev = 0;

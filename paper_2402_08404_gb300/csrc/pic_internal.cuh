@@ -164,6 +164,7 @@ struct pic_s {
   double *coarse_inv_d = nullptr;
   int32_t *coarse_slot = nullptr;   // split-layout slot of each free node
   int tail_start = -1;              // first level of the cluster-launched V-cycle tail (-1: none)
+  int mg_sweeps = 3;                // red-black sweeps before and after each coarse correction
   pic::DevClock *clock = nullptr;
   // scratch
   void *scan_tmp = nullptr;      // block partials for scans

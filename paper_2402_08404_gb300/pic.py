@@ -47,7 +47,7 @@ class Params(C.Structure):
     _fields_ = [("dt", C.c_double), ("apex_field", C.c_double), ("V0", C.c_double), ("T0", C.c_double),
                 ("work_function", C.c_double), ("w_min", C.c_double), ("w_max_units", C.c_int),
                 ("n_heat", C.c_int), ("seed", C.c_uint64), ("flags", C.c_uint32), ("mg_tol", C.c_double),
-                ("mg_max_cycles", C.c_int)]
+                ("mg_max_cycles", C.c_int), ("mg_sweeps", C.c_int)]
 
 
 class Diag(C.Structure):
@@ -162,7 +162,7 @@ class Pic:
     """One vacuum-arc PIC-MCC instance on the current CUDA device."""
 
     def __init__(self, cfg, capacity, flags=F_ALL, mg_tol=1e-8, mg_max_cycles=60, V0=0.0, stream=None,
-                 torch_memory=True):
+                 torch_memory=True, mg_sweeps=0):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("libpic needs a CUDA device")
@@ -174,7 +174,7 @@ class Pic:
         grid = GridT(cfg["nx"], cfg["ny"], cfg["nz"], cfg["dx"])
         prm = Params(cfg["dt"], cfg["apex_field"], V0, cfg["T0"], cfg["work_function"], cfg["w_min"],
                      int(cfg["w_max_units"]), int(cfg.get("n_heat", 0)), int(cfg.get("seed", 1)), int(flags),
-                     float(mg_tol), int(mg_max_cycles))
+                     float(mg_tol), int(mg_max_cycles), int(mg_sweeps))
         h = C.c_void_p()
         a = self._alloc.alloc_fn if self._alloc else ALLOC_FN(0)
         f = self._alloc.free_fn if self._alloc else FREE_FN(0)
