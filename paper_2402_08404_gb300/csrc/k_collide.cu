@@ -21,6 +21,9 @@
 namespace pic {
 
 constexpr double kLotzA = 4.5e-18;     // m^2 eV^2  (4.5e-14 cm^2 eV^2)
+// The smallest uniform draw, 0.5 * 2^-24.  When P + guard band is below it, no draw can land
+// under P or inside the band, so the decisions (none) are known without drawing.
+constexpr float kUmin = 2.98023223876953125e-8f;
 
 __device__ __forceinline__ double sigma_ion64(double E) {
   return E > kXiCu ? kLotzA * log(E / kXiCu) / (E * kXiCu) : 0.0;
@@ -94,7 +97,7 @@ __global__ void k_mcc_count(McArgs a) {
       const float band = ldexpf(P32 + u * nW * sig_peak, -12);
       const uint64_t pid = pr.proj_e ? a.e.id[pr.ie] : a.n.id[pr.in];
       bool exact = false;
-      for (int i = 0; i < wp; i += 4) {
+      for (int i = 0; i < wp && P32 + band >= kUmin; i += 4) {
         const U4 r = rng_block(a.seed, kIon, pid, step, (uint32_t)(i >> 2));
         for (int j = 0; j < 4 && i + j < wp; ++j) {
           const float U = u01f(r.v[j]);
@@ -254,7 +257,7 @@ __global__ void k_dfi_count(DfiArgs a) {
         const float band = ldexpf(P32, -12);
         const uint64_t id = a.n.id[t];
         bool exact = false;
-        for (int i = 0; i < w; i += 4) {
+        for (int i = 0; i < w && P32 + band >= kUmin; i += 4) {
           const U4 r = rng_block(a.seed, kDfi, id, step, (uint32_t)(i >> 2));
           for (int j = 0; j < 4 && i + j < w; ++j) {
             const float U = u01f(r.v[j]);
