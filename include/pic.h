@@ -208,11 +208,12 @@ void pic_batch_destroy(pic_batch_t *b);
 
 /* Autotuner (no counterpart in the paper): times the launch-shape candidates on this instance's
  * current state and keeps the fastest -- blocks per SM of the particle kernels (2..32, probed on
- * the charge deposit, which it leaves as a deposit would) and, per multigrid level, the
- * smoother's planes per thread (1, 2, 4 or 8, probed on the level's correction, which every solve
- * rebuilds).  No result depends on the choices.  choices[0] receives the blocks per SM and
- * choices[1 + l] the planes per thread of level l; returns the number of values written (at most
- * cap) or a negative PIC_E_* code. */
+ * the charge deposit, which it leaves as a deposit would), planes per thread of the fixed-point
+ * residual (1, 2 or 4) and, per multigrid level, the smoother's planes per thread (1, 2, 4 or 8;
+ * both probed on solver scratch that every solve rebuilds).  No result depends on the choices.
+ * choices[0] receives the blocks per SM, choices[1] the residual's planes per thread and
+ * choices[2 + l] the smoother's planes per thread on level l; returns the number of values
+ * written (at most cap) or a negative PIC_E_* code. */
 int pic_autotune(pic_t *h, int *choices, int cap);
 
 /* Kernel timing (diagnostics of the library; the paper has no counterpart).  pic_num_kernels()

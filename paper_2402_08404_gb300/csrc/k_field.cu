@@ -564,7 +564,7 @@ __device__ __forceinline__ long long nb_sum_fx(const long long *u, int i, int j,
 // kKZ planes per thread (grid z: plane groups): the centre column of phi is loaded once for the
 // z differences of all of them, and every load is issued before the arithmetic (all addresses
 // inside the grid; Dirichlet nodes, the k = 0 and k = nz planes among them, discard theirs).
-template <typename T>
+template <typename T, int KZ>
 __global__ void __launch_bounds__(256) k_residual64(const long long *phi, const unsigned long long *Q,
                                                     unsigned long long Kfx, int S, int zero_charge, T *fl,
                                                     const uint8_t *dir, Lv L, T c_lvl, float V0f, double *part,
@@ -572,7 +572,7 @@ __global__ void __launch_bounds__(256) k_residual64(const long long *phi, const 
   __shared__ float sh[2][8];
   const int nx = L.nx, ny = L.ny, nz = L.nz;
   const int i = blockIdx.x * 32 + threadIdx.x;
-  const int j = blockIdx.y * 8 + threadIdx.y, k0 = blockIdx.z * kKZ;
+  const int j = blockIdx.y * 8 + threadIdx.y, k0 = blockIdx.z * KZ;
   float s = 0.f, sl = 0.f;
   if (i <= nx && j <= ny) {
     // 32-bit node offsets (a grid has fewer than 2^32 nodes, checked at creation)
@@ -581,14 +581,14 @@ __global__ void __launch_bounds__(256) k_residual64(const long long *phi, const 
     const uint32_t sy = (uint32_t)(nx + 1), sz = (uint32_t)(nx + 1) * (uint32_t)(ny + 1);
     const uint32_t col = (uint32_t)j * sy + (uint32_t)i;
     const int32_t dxm = im - i, dxp = ip - i, dym = (jm - j) * (int32_t)sy, dyp = (jp - j) * (int32_t)sy;
-    long long cz[kKZ + 2];
+    long long cz[KZ + 2];
 #pragma unroll
-    for (int p = 0; p < kKZ + 2; ++p) cz[p] = phi[(uint32_t)min(max(k0 - 1 + p, 0), nz) * sz + col];
-    long long side[kKZ];
-    unsigned long long qv[kKZ];
-    uint8_t d[kKZ];
+    for (int p = 0; p < KZ + 2; ++p) cz[p] = phi[(uint32_t)min(max(k0 - 1 + p, 0), nz) * sz + col];
+    long long side[KZ];
+    unsigned long long qv[KZ];
+    uint8_t d[KZ];
 #pragma unroll
-    for (int p = 0; p < kKZ; ++p) {
+    for (int p = 0; p < KZ; ++p) {
       const uint32_t c = (uint32_t)min(k0 + p, nz) * sz + col;
       d[p] = k0 + p <= nz ? dir[c] : 1;
       side[p] = phi[c + dxm] + phi[c + dxp] + phi[c + dym] + phi[c + dyp];
@@ -597,7 +597,7 @@ __global__ void __launch_bounds__(256) k_residual64(const long long *phi, const 
     const int wall = (i == 0 || i == nx ? 1 : 0) + (j == 0 || j == ny ? 1 : 0);
     const unsigned long long Kw = Kfx << wall;
 #pragma unroll
-    for (int p = 0; p < kKZ; ++p) {
+    for (int p = 0; p < KZ; ++p) {
       const int k = k0 + p;
       if (k > nz) break;
       long long t = 0, f = 0;
@@ -981,8 +981,6 @@ int tune_smoother(pic_t *h, int *best, int cap) {
 struct SolveSetup {
   unsigned long long Kfx;
   int S;
-  dim3 rg;
-  int64_t nb;
   double c_fx;
   bool mixed;
   float V0f;
@@ -1005,26 +1003,80 @@ static int solve_setup(pic_t *h, double V0, SolveSetup *ss) {
   if (!(K > 0) || S < 1 || S > 63) return pic_fail(h, PIC_E_INVALID, "charge scale e w_min / (dx eps0) out of range");
   ss->Kfx = (unsigned long long)llround(ldexp(K, S));
   ss->S = S;
-  ss->rg = dim3((h->nx + 1 + 31) / 32, (h->ny + 1 + 7) / 8, (h->nz + kKZ) / kKZ);
-  ss->nb = (int64_t)ss->rg.x * ss->rg.y * ss->rg.z;
   ss->c_fx = 1.0 / (h->dx * h->dx) * kPhiUnit;
   ss->mixed = (h->prm.flags & PIC_F_MIXED_MG) != 0;
   ss->V0f = (float)V0;
   return PIC_OK;
 }
 
-// residual of the fixed-point system onto the finest level and its two norms in red_out
+// residual of the fixed-point system onto the finest level and its two norms in red_out (the
+// planes per thread are the autotuner's, 1, 2 or 4)
+template <typename T, int KZ>
+static void residual_kz(pic_t *h, const SolveSetup &ss, bool zero_charge, bool lift, T *fl, T c_lvl, double *part,
+                        int64_t *nb) {
+  MgLevel &L = h->mg[0];
+  const dim3 g((h->nx + 1 + 31) / 32, (h->ny + 1 + 7) / 8, (h->nz + KZ) / KZ);
+  *nb = (int64_t)g.x * g.y * g.z;
+  k_residual64<T, KZ><<<g, node_block(), 0, h->stream>>>(h->phi, h->Q, ss.Kfx, ss.S, zero_charge ? 1 : 0, fl, L.dir,
+                                                         lv_of(L), c_lvl, ss.V0f, part, lift ? 1 : 0);
+}
+
+template <typename T>
+static int64_t residual_launch(pic_t *h, const SolveSetup &ss, bool zero_charge, bool lift, T *fl, T c_lvl) {
+  int64_t nb = 0;
+  switch (h->tune_residual_kz) {
+    case 1: residual_kz<T, 1>(h, ss, zero_charge, lift, fl, c_lvl, h->red, &nb); break;
+    case 2: residual_kz<T, 2>(h, ss, zero_charge, lift, fl, c_lvl, h->red, &nb); break;
+    default: residual_kz<T, 4>(h, ss, zero_charge, lift, fl, c_lvl, h->red, &nb); break;
+  }
+  return nb;
+}
+
 static void residual_pass(pic_t *h, const SolveSetup &ss, bool zero_charge, bool lift) {
   MgLevel &L = h->mg[0];
-  const Lv lv = lv_of(L);
   ++h->nlaunch;
-  if (ss.mixed)
-    { KtScope kt_(h, kidResidual64, (double)h->nnode); k_residual64<float><<<ss.rg, node_block(), 0, h->stream>>>(h->phi, h->Q, ss.Kfx, ss.S, zero_charge ? 1 : 0, L.f, L.dir, lv, (float)ss.c_fx, ss.V0f, h->red, lift ? 1 : 0); }
-  else
-    { KtScope kt_(h, kidResidual64, (double)h->nnode); k_residual64<double><<<ss.rg, node_block(), 0, h->stream>>>(h->phi, h->Q, ss.Kfx, ss.S, zero_charge ? 1 : 0, L.fd, L.dir, lv, ss.c_fx, ss.V0f, h->red, lift ? 1 : 0); }
+  int64_t nb;
+  {
+    KtScope kt_(h, kidResidual64, (double)h->nnode);
+    nb = ss.mixed ? residual_launch<float>(h, ss, zero_charge, lift, L.f, (float)ss.c_fx)
+                  : residual_launch<double>(h, ss, zero_charge, lift, L.fd, ss.c_fx);
+  }
   h->nlaunch += 2;
-  { KtScope kt_(h, kidNormSum, (double)ss.nb); k_sum_stage1<<<kSumChunks, 256, 0, h->stream>>>(h->red, ss.nb, h->red_mid); }
+  { KtScope kt_(h, kidNormSum, (double)nb); k_sum_stage1<<<kSumChunks, 256, 0, h->stream>>>(h->red, nb, h->red_mid); }
   k_sum_stage2<<<1, kSumChunks, 0, h->stream>>>(h->red_mid, h->red_out);
+}
+
+// Autotuner probe for the fixed-point residual: planes per thread 1, 2 or 4, each timed three
+// times on the current potential and charge (it only rewrites the finest level's right-hand side
+// and the norm partials, which every solve rebuilds); the fastest is kept.
+int tune_residual(pic_t *h, int *best) {
+  SolveSetup ss;
+  PIC_TRY(solve_setup(h, h->V0, &ss));
+  cudaEvent_t e0, e1;
+  PIC_CUDA(h, cudaEventCreate(&e0));
+  PIC_CUDA(h, cudaEventCreate(&e1));
+  const int cand[3] = {1, 2, 4};
+  float best_ms = 1e30f;
+  int pick = h->tune_residual_kz;
+  for (int kz : cand) {
+    h->tune_residual_kz = kz;
+    float t_min = 1e30f;
+    for (int rep = 0; rep < 3; ++rep) {
+      cudaEventRecord(e0, h->stream);
+      residual_pass(h, ss, false, false);
+      cudaEventRecord(e1, h->stream);
+      cudaEventSynchronize(e1);
+      float t = 0.f;
+      cudaEventElapsedTime(&t, e0, e1);
+      t_min = std::min(t_min, t);
+    }
+    if (t_min < best_ms) { best_ms = t_min; pick = kz; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  h->tune_residual_kz = pick;
+  *best = pick;
+  return launch_check(h, "tune residual");
 }
 
 // Solve for phi with the current deposited charge (or none), anode at V0: refinement cycles

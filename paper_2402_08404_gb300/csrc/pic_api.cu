@@ -1148,9 +1148,10 @@ int pic_batch_ms(pic_batch_t *b, double *ms) {
   return PIC_OK;
 }
 
-// Autotuner: time the launch-shape candidates of the particle kernels and of the smoother on
-// this instance's current state and keep the fastest; choices[0] receives the particle blocks
-// per SM, choices[1 + l] the smoother's planes per thread on level l.  Results do not depend on
+// Autotuner: time the launch-shape candidates of the particle kernels, the fixed-point residual
+// and the smoother on this instance's current state and keep the fastest; choices[0] receives the
+// particle blocks per SM, choices[1] the residual's planes per thread, choices[2 + l] the
+// smoother's planes per thread on level l.  Results do not depend on
 // the choices.  Returns the number of values written (<= cap) or a negative error code.
 int pic_autotune(pic_t *h, int *choices, int cap) {
   if (!h || (cap > 0 && !choices)) return PIC_E_INVALID;
@@ -1158,9 +1159,12 @@ int pic_autotune(pic_t *h, int *choices, int cap) {
   PIC_TRY(tune_particles(h, &bps));
   int kz[16] = {0};
   PIC_TRY(tune_smoother(h, kz, 16));
+  int rkz = 0;
+  PIC_TRY(tune_residual(h, &rkz));
   graph_invalidate(h);
   int nw = 0;
   if (cap > 0) choices[nw++] = bps;
+  if (cap > 1) choices[nw++] = rkz;
   const int nl = std::min<int>((int)h->mg.size() - 1, 16);
   for (int l = 0; l < nl && nw < cap; ++l) choices[nw++] = kz[l];
   return nw;

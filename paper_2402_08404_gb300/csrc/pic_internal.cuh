@@ -199,6 +199,7 @@ struct pic_s {
   bool last_solve_graph = false;        // the last solve ran in a graph (its diagnostics are on the device)
   // autotuned launch shapes
   int tune_particle_bps = 8;            // blocks per SM of the particle kernels (sort, push, deposit)
+  int tune_residual_kz = 4;            // planes per thread of the fixed-point residual
   int tune_smooth_kz[16] = {4, 4, 4, 4, 4, 4, 4, 4, 4, 4, 4, 4, 4, 4, 4, 4};  // planes per thread, by level
   // kernel timing (diagnostics): launches of the kernels in kt_mask are bracketed by event pairs
   uint64_t kt_mask = 0;
@@ -341,6 +342,7 @@ int graph_launch_step(pic_t *h);
 // autotuner probes: time the launch-shape candidates on the current state, keep the fastest
 int tune_particles(pic_t *h, int *best);
 int tune_smoother(pic_t *h, int *best, int cap);
+int tune_residual(pic_t *h, int *best);
 int face_field_mean(pic_t *h, const int64_t *faces, int nf, double *out);
 int mg_coarse_setup(pic_t *h);
 // heat (k_heat.cu)

@@ -321,12 +321,14 @@ class Pic:
 
     # -- autotuner ------------------------------------------------------------------------------------
     def autotune(self):
-        """pic_autotune: {"particle_blocks_per_sm": b, "smoother_planes_per_thread": [per level]}."""
-        buf = (C.c_int * 17)()
-        n = lib().pic_autotune(self.h, buf, 17)
+        """pic_autotune: {"particle_blocks_per_sm": b, "residual_planes_per_thread": r,
+        "smoother_planes_per_thread": [per level]}."""
+        buf = (C.c_int * 18)()
+        n = lib().pic_autotune(self.h, buf, 18)
         if n < 0:
             self._check(n)
-        return {"particle_blocks_per_sm": buf[0], "smoother_planes_per_thread": list(buf[1:n])}
+        return {"particle_blocks_per_sm": buf[0], "residual_planes_per_thread": buf[1],
+                "smoother_planes_per_thread": list(buf[2:n])}
 
     # -- kernel timing (diagnostics) ----------------------------------------------------------------
     @staticmethod

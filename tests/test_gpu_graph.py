@@ -166,6 +166,7 @@ def test_autotune_keeps_results(pic):
     a, b = _build(pic, [cfg, cfg], flags)
     ch = a.autotune()
     assert ch["particle_blocks_per_sm"] in (2, 4, 8, 16, 32)
+    assert ch["residual_planes_per_thread"] in (1, 2, 4)
     assert len(ch["smoother_planes_per_thread"]) >= 1
     assert all(k in (1, 2, 4, 8) for k in ch["smoother_planes_per_thread"])
     for sim in (a, b):
