@@ -20,6 +20,7 @@ collide    impact ionization MCC with SP splitting (eq:colp, eq:du, Sec. 2.3.2) 
 emission   general thermal-field emission current and Nottingham heat (Sec. 2.3.1)
 surface    Clausius-Clapeyron evaporation, injection weights, sputtering, bombardment heat (Sec. 2.3.1-2.3.3)
 heat       tip heat equation with Wiedemann-Franz conductivity and current continuity (eq:heat, eq:cont)
+circuit    RC circuit of the gap and the Shockley-Ramo gap current (Sec. 2.3.1, circuit passage)
 mlp        FP64 forward/backward of the emission surrogate MLP (no counterpart in the paper)
 step       one coupled PIC-MCC step in the paper's order (Sec. 2.3.1, Fig. newpic)
 """
