@@ -200,6 +200,9 @@ def run_ours(args):
     pop = synth.plasma(cfg, seed=cfg["seed"])
     cap = (int(0.4 * n_sp * 1.25), int(0.4 * n_sp * 1.25), int(0.2 * n_sp * 1.5))
     prod_flags = pic.F_PRODUCTION if args.form == "production" else (pic.F_ALL & ~pic.F_SURROGATE & ~pic.F_MIXED_MG)
+    if args.circuit:   # the paper's external circuit: 1 kOhm, 1 pF, Shockley-Ramo gap current
+        cfg["circuit_R"], cfg["circuit_C"] = 1e3, 1e-12
+        prod_flags |= pic.F_CIRCUIT
     plain_flags = pic.F_ALL & ~pic.F_SURROGATE & ~pic.F_MIXED_MG
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
@@ -334,6 +337,8 @@ def run_ours(args):
         "config": {"workload": workload_name(cfg, args.config), "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (2e7 SPs x 36 B SoA + 33.9M-node grids)",
                    "form": form, "poisson_tol": args.mg_tol,
+                   "circuit": ({"R_ohm": 1e3, "C_F": 1e-12, "V_gap_end": d1["V_gap"], "I_gap_end": d1["I_gap"]}
+                               if args.circuit else None),
                    "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()}, "mg_cycles": d1["mg_cycles"],
                    "kernel_ms_per_step": kernel_ms,
                    "surrogate": None if sur is None else {
@@ -519,6 +524,7 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=60000)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false")
+    ap.add_argument("--circuit", action="store_true", help="step with the RC circuit and Shockley-Ramo current")
     args = ap.parse_args()
     if args.impl == "reference":
         out = run_reference(args)

@@ -61,6 +61,7 @@ extern "C" {
 #define PIC_F_MIXED_MG 0x80u    /* a8: FP32 V-cycles with FP64 residual refinement (else FP64 V-cycles) */
 #define PIC_F_FAST_INTEGRAL 0x100u  /* a1: Gamow quadrature and turning points in FP32 (J, P_N to ~1e-5
                                        relative) in the step and in pic_emission_eval; else all FP64 */
+#define PIC_F_CIRCUIT 0x400u    /* the RC circuit drives the anode (needs circuit_R, circuit_C > 0 at create) */
 #define PIC_F_GRAPH 0x200u      /* pic_step replays a CUDA graph of one step (the Poisson loop a device-side
                                    while node); the first call with new flags runs one step eagerly and
                                    records the graph; results equal the eager form's bit for bit */
@@ -96,6 +97,9 @@ typedef struct {
   double mg_tol;        /* relative residual target of the Poisson solve */
   int mg_max_cycles;    /* cap on refinement cycles per solve */
   int mg_sweeps;        /* red-black sweeps before and after each coarse-grid correction (<= 0: 3) */
+  double circuit_R;     /* Ohm: external resistance of the RC circuit (with circuit_C > 0: allocates the
+                           unit Laplace field; the circuit acts while PIC_F_CIRCUIT is set) */
+  double circuit_C;     /* F: gap capacitance of the RC circuit */
 } pic_params_t;
 
 typedef struct {
@@ -116,6 +120,8 @@ typedef struct {
   int64_t kernel_launches;  /* kernels launched by the library since create */
   int64_t emission_evals;   /* transmission evaluations of the emission integral this step */
   int64_t surrogate_faces;  /* faces whose emission came from the surrogate this step */
+  double V_gap;             /* V: gap voltage (V0 without a circuit) */
+  double I_gap, I_tot;      /* A: Shockley-Ramo gap current and circuit current of the last circuit stage */
 } pic_diag_t;
 
 typedef struct pic_s pic_t;
@@ -182,6 +188,11 @@ int pic_emit(pic_t *h);        /* a1 emission + a2 evaporation/sputter injection
 int pic_push(pic_t *h);        /* a3 gather + leapfrog + boundary removal, ion impact records */
 int pic_sort(pic_t *h);        /* a4 stable cell sort of every species, dropping removed SPs */
 int pic_collide(pic_t *h);     /* a5 impact ionization MCC, then a6 field ionization (appends) */
+/* RC circuit (the circuit passage of Sec. 2.3.1, after ArcPIC): I_gap = sum over e- and Cu+ SPs of
+ * q v . E0(x) (Shockley-Ramo, E0 the Laplace field with the anode at unit potential, gathered like
+ * E), then V_gap += dt/C ((V0 - V_gap)/R - I_gap).  pic_step runs it after the push; the following
+ * Poisson solve holds the anode at V_gap.  PIC_E_INVALID without a circuit. */
+int pic_circuit(pic_t *h);
 int pic_deposit(pic_t *h);     /* a7 fixed-point CIC charge deposit of e- and Cu+ */
 int pic_solve_field(pic_t *h); /* a7 deposit, a8 Poisson solve, a9 node field */
 int pic_heat(pic_t *h);        /* a10 continuity + heat on the tip cells from the accumulators */

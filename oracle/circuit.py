@@ -12,8 +12,9 @@ Readings (the paper gives the equations only):
   * the integral is advanced by explicit Euler once per PIC step, from V_gap and I_gap at the
     start of the step: V_gap <- V_gap + dt/C (I_tot - I_gap);
   * I_gap is taken after the push, from the new positions and the half-step velocities of
-    electrons and Cu+ (q = Z e w w_min per SP), with E0 gathered by the same cloud-in-cell
-    weights as E;
+    electrons and Cu+ (q = Z e w w_min per SP) that are still in the vacuum region (SPs the
+    push removed at a boundary no longer move in the gap), with E0 gathered by the same
+    cloud-in-cell weights as E;
   * E0 is the node field of the unit Laplace solution by central differences (one-sided on the
     cathode and anode planes, mirrored at the lateral walls), in float64;
   * the anode potential of the step's Poisson solve is the updated V_gap.

@@ -26,6 +26,7 @@
 #include <vector>
 
 #include "pic_internal.cuh"
+#include "dev_common.cuh"
 
 namespace pic {
 
@@ -524,6 +525,77 @@ __global__ void k_dirichlet(long long *phi, const uint8_t *dir, int nx, int ny, 
   if (dir[n]) phi[n] = k == nz ? V0fx : 0;
 }
 
+// Anode plane (all Dirichlet nodes) at the circuit's gap voltage, rounded to the fixed-point grid.
+__global__ void k_anode_plane(long long *phi, int nx, int ny, int nz, const double *V_gap) {
+  const int64_t np = (int64_t)(nx + 1) * (ny + 1);
+  const long long v = __double2ll_rn(*V_gap * kPhiScale);
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < np; q += (int64_t)gridDim.x * blockDim.x)
+    phi[(int64_t)nz * np + q] = v;
+}
+
+// Unit Laplace field E0 = -grad(phi_L) / V_L of a zero-charge solution phi_L with the anode at
+// V_L: central differences (one-sided on the z = 0 and z = nz planes, mirrored at the walls) in
+// FP64 from the exact fixed-point differences, stored as float4 [1/m].
+__global__ void k_unit_field(const long long *phi, float4 *E0, int nx, int ny, int nz, double c2, double c1) {
+  NODE_IJK(nx, ny)
+  const int64_t sy = nx + 1, sz = (int64_t)(nx + 1) * (ny + 1);
+  const int im = i > 0 ? i - 1 : 1, ip = i < nx ? i + 1 : nx - 1;
+  const int jm = j > 0 ? j - 1 : 1, jp = j < ny ? j + 1 : ny - 1;
+  const int64_t row = (int64_t)k * sz + (int64_t)j * sy;
+  float4 e;
+  e.x = (float)((double)(phi[row + im] - phi[row + ip]) * c2);
+  e.y = (float)((double)(phi[(int64_t)k * sz + (int64_t)jm * sy + i] - phi[(int64_t)k * sz + (int64_t)jp * sy + i]) * c2);
+  if (k == 0) e.z = (float)((double)(phi[n] - phi[n + sz]) * c1);
+  else if (k == nz) e.z = (float)((double)(phi[n - sz] - phi[n]) * c1);
+  else e.z = (float)((double)(phi[n - sz] - phi[n + sz]) * c2);
+  e.w = 0.f;
+  E0[n] = e;
+}
+
+// Shockley-Ramo current of the charged SPs, I = sum Z e w w_min v . E0(x) (E0 gathered like E),
+// over the SPs still in the domain (after a push: key != kDead; sorted SPs: w > 0).  Per-block
+// partial sums in FP64 over a fixed grid of kRamoBlocks blocks, so the summation
+// order, and with it every bit of the result, does not depend on anything but the SP order.
+constexpr int kRamoBlocks = 256;
+__global__ void __launch_bounds__(256) k_ramo_partial(SpeciesBuf e, SpeciesBuf ion, const uint32_t *key_e,
+                                                      const uint32_t *key_i, const float4 *E0, int nx, int ny,
+                                                      const DevClock *clk, double qw, double *part) {
+  __shared__ double sh[8];
+  double acc = 0.0;
+  for (int sp = 0; sp < 2; ++sp) {
+    const SpeciesBuf &p = sp == 0 ? e : ion;
+    const uint32_t *key = sp == 0 ? key_e : key_i;
+    const int64_t n = clk->n[sp == 0 ? PIC_ELECTRON : PIC_ION];
+    const double z = sp == 0 ? -qw : qw;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+      const int32_t w = p.w[i];
+      if (w <= 0 || (key && key[i] == kDead)) continue;
+      const float3 g = gather_E(E0, p.x[i], p.y[i], p.z[i], nx, ny);
+      const float vdot = p.vx[i] * g.x + p.vy[i] * g.y + p.vz[i] * g.z;
+      acc += z * (double)w * (double)vdot;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double b = 0.0;
+    for (int w = 0; w < 8; ++w) b += sh[w];
+    part[blockIdx.x] = b;
+  }
+}
+
+// I_gap from the partials (fixed order), then one explicit Euler step of the RC circuit:
+// I_tot = (V0 - V_gap)/R, V_gap += dt/C (I_tot - I_gap)
+__global__ void k_circuit(const double *part, DevClock *clk, double V0, double R, double Cg, double dt) {
+  double I = 0.0;
+  for (int b = 0; b < kRamoBlocks; ++b) I += part[b];
+  const double Itot = (V0 - clk->V_gap) / R;
+  clk->I_gap = I;
+  clk->I_tot = Itot;
+  clk->V_gap = __dadd_rn(clk->V_gap, __dmul_rn(dt / Cg, Itot - I));   // no contraction: one rounding per operation
+}
+
 // Charge term of the right-hand side in the potential's fixed point: h^2 rho_n / eps0 in units
 // of 2^-40 V equals Q_n K with K = e w_min 2^10 / (dx eps0) (2 per lateral wall the node lies
 // on, from the halved node volume).  K is held as Kw = K 2^S (< 2^62) and the product is formed
@@ -567,12 +639,14 @@ __device__ __forceinline__ long long nb_sum_fx(const long long *u, int i, int j,
 template <typename T, int KZ>
 __global__ void __launch_bounds__(256) k_residual64(const long long *phi, const unsigned long long *Q,
                                                     unsigned long long Kfx, int S, int zero_charge, T *fl,
-                                                    const uint8_t *dir, Lv L, T c_lvl, float V0f, double *part,
+                                                    const uint8_t *dir, Lv L, T c_lvl, float V0f,
+                                                    const double *V_anode, double *part,
                                                     int lift) {
   __shared__ float sh[2][8];
   const int nx = L.nx, ny = L.ny, nz = L.nz;
   const int i = blockIdx.x * 32 + threadIdx.x;
   const int j = blockIdx.y * 8 + threadIdx.y, k0 = blockIdx.z * KZ;
+  if (V_anode) V0f = (float)*V_anode;   // the circuit's gap voltage
   float s = 0.f, sl = 0.f;
   if (i <= nx && j <= ny) {
     // 32-bit node offsets (a grid has fewer than 2^32 nodes, checked at creation)
@@ -984,6 +1058,7 @@ struct SolveSetup {
   double c_fx;
   bool mixed;
   float V0f;
+  const double *V_anode;   // device gap voltage when the circuit drives the anode, else null
 };
 
 // Dirichlet values on phi for V0 (only when they changed) and the charge factor
@@ -991,12 +1066,20 @@ struct SolveSetup {
 static int solve_setup(pic_t *h, double V0, SolveSetup *ss) {
   MgLevel &L = h->mg[0];
   const long long V0fx = llrint(V0 * kPhiScale);
-  if (!h->dirichlet_valid || h->dirichlet_V0fx != V0fx) {
+  const bool circ = circuit_on(h);
+  if (!h->dirichlet_valid || h->dirichlet_V0fx != V0fx || (h->anode_dirty && !circ)) {
     if (h->capturing) return pic_fail(h, PIC_E_INVALID, "Dirichlet values must be set before graph capture");
     ++h->nlaunch;
     { KtScope kt_(h, kidDirichlet, (double)h->nnode); k_dirichlet<<<node_grid3(h->nx, h->ny, h->nz), node_block(), 0, h->stream>>>(h->phi, L.dir, h->nx, h->ny, h->nz, V0fx); }
     h->dirichlet_valid = true;
     h->dirichlet_V0fx = V0fx;
+    h->anode_dirty = false;
+  }
+  if (circ) {   // the anode plane follows the circuit's gap voltage, every solve
+    ++h->nlaunch;
+    h->anode_dirty = true;
+    k_anode_plane<<<grid_for((int64_t)(h->nx + 1) * (h->ny + 1)), kThreads, 0, h->stream>>>(h->phi, h->nx, h->ny, h->nz,
+                                                                                           &h->clock->V_gap);
   }
   const double K = kQe * h->prm.w_min * 1024.0 / (h->dx * kEps0);
   const int S = 59 - (int)floor(log2(K));
@@ -1006,6 +1089,7 @@ static int solve_setup(pic_t *h, double V0, SolveSetup *ss) {
   ss->c_fx = 1.0 / (h->dx * h->dx) * kPhiUnit;
   ss->mixed = (h->prm.flags & PIC_F_MIXED_MG) != 0;
   ss->V0f = (float)V0;
+  ss->V_anode = circ ? &h->clock->V_gap : nullptr;
   return PIC_OK;
 }
 
@@ -1018,7 +1102,7 @@ static void residual_kz(pic_t *h, const SolveSetup &ss, bool zero_charge, bool l
   const dim3 g((h->nx + 1 + 31) / 32, (h->ny + 1 + 7) / 8, (h->nz + KZ) / KZ);
   *nb = (int64_t)g.x * g.y * g.z;
   k_residual64<T, KZ><<<g, node_block(), 0, h->stream>>>(h->phi, h->Q, ss.Kfx, ss.S, zero_charge ? 1 : 0, fl, L.dir,
-                                                         lv_of(L), c_lvl, ss.V0f, part, lift ? 1 : 0);
+                                                         lv_of(L), c_lvl, ss.V0f, ss.V_anode, part, lift ? 1 : 0);
 }
 
 template <typename T>
@@ -1105,6 +1189,42 @@ int stage_solve(pic_t *h, bool zero_charge, double V0) {
     else cycle_fine<double>(h);
   }
   return stage_efield(h);
+}
+
+bool circuit_on(pic_t *h) { return h->E0 != nullptr && h->circuit_ready && (h->prm.flags & PIC_F_CIRCUIT) != 0; }
+
+// After a zero-charge solve with the anode at V_L: the unit Laplace field and the circuit's
+// initial state (V_gap = V0, no current)
+int circuit_setup(pic_t *h, double V_L) {
+  const double c2 = kPhiUnit / (2.0 * h->dx * V_L), c1 = kPhiUnit / (h->dx * V_L);
+  ++h->nlaunch;
+  k_unit_field<<<node_grid3(h->nx, h->ny, h->nz), node_block(), 0, h->stream>>>(h->phi, h->E0, h->nx, h->ny, h->nz, c2, c1);
+  return launch_check(h, "unit field");
+}
+
+int circuit_reset(pic_t *h) {
+  const double st[3] = {h->V0, 0.0, 0.0};
+  PIC_CUDA(h, cudaMemcpyAsync(&h->clock->V_gap, st, sizeof st, cudaMemcpyHostToDevice, h->stream));
+  PIC_CUDA(h, cudaStreamSynchronize(h->stream));
+  h->circuit_ready = true;
+  return PIC_OK;
+}
+
+// The circuit stage of a step: Shockley-Ramo current of the pushed SPs and the RC update.
+int stage_circuit(pic_t *h) {
+  if (!circuit_on(h)) return PIC_OK;
+  const double qw = kQe * h->prm.w_min;
+  h->nlaunch += 2;
+  // after a push the keys mark the removed SPs; sorted SPs are all in the domain
+  const uint32_t *ke = h->keys_valid[PIC_ELECTRON] ? h->sp[PIC_ELECTRON].key : nullptr;
+  const uint32_t *ki = h->keys_valid[PIC_ION] ? h->sp[PIC_ION].key : nullptr;
+  {
+    KtScope kt_(h, kidRamo, 0);
+    k_ramo_partial<<<kRamoBlocks, 256, 0, h->stream>>>(h->sp[PIC_ELECTRON].a, h->sp[PIC_ION].a, ke, ki, h->E0, h->nx,
+                                                       h->ny, h->clock, qw, h->ramo_part);
+  }
+  k_circuit<<<1, 1, 0, h->stream>>>(h->ramo_part, h->clock, h->V0, h->prm.circuit_R, h->prm.circuit_C, h->prm.dt);
+  return launch_check(h, "circuit");
 }
 
 // Device-side convergence test of the graph form (one thread): first = 1 takes the lifted norm of

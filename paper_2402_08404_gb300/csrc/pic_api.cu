@@ -197,7 +197,7 @@ namespace pic {
 const char *const kKernelNames[kidNum] = {
     "k_push", "k_keys", "k_scatter", "k_fix_short", "k_fix_mid", "k_fix_long", "k_gather", "k_scan_partial",
     "k_scan_apply", "k_deposit", "k_mcc_count", "k_mcc_products", "k_dfi_count", "k_dfi_products", "k_dirichlet",
-    "k_residual64", "k_norm_sum", "k_smooth", "k_smooth_first", "k_residual", "k_restrict", "k_prolong", "k_coarse", "k_vcycle_tail",
+    "k_residual64", "k_norm_sum", "k_smooth", "k_smooth_first", "k_residual", "k_restrict", "k_prolong", "k_coarse", "k_vcycle_tail", "k_ramo",
     "k_correct", "k_efield", "k_face_field", "k_emit_surrogate", "k_emit_fallback", "k_emit_count", "k_emit_write",
     "k_inject_count", "k_inject_write", "k_mlp_forward", "k_heat"};
 
@@ -417,6 +417,8 @@ int pic_create(const pic_geometry_t *geometry, const pic_grid_t *grid, const pic
   h->red = alloc_n<double>(h, (int64_t)2 * ((h->nx + 1 + 31) / 32) * ((h->ny + 1 + 7) / 8) * (h->nz + 1)); A(h->red);
   h->red_out = alloc_n<double>(h, 2); A(h->red_out);
   h->red_mid = alloc_n<double>(h, 2 * 128); A(h->red_mid);
+  h->ramo_part = alloc_n<double>(h, 256); A(h->ramo_part);
+  if (h->prm.circuit_R > 0 && h->prm.circuit_C > 0) { h->E0 = alloc_n<float4>(h, h->nnode); A(h->E0); }
   h->tmp_len = alloc_n<int64_t>(h, 16); A(h->tmp_len);
   h->long_list = alloc_n<int2>(h, kLongCap); A(h->long_list);
   {
@@ -484,8 +486,10 @@ int pic_create(const pic_geometry_t *geometry, const pic_grid_t *grid, const pic
   if (h->prm.V0 > 0) {
     h->V0 = h->prm.V0;
     rc = stage_solve(h, true, h->V0);
+    if (rc == PIC_OK && h->E0) rc = circuit_setup(h, h->V0);
   } else {
     rc = stage_solve(h, true, kVref);
+    if (rc == PIC_OK && h->E0) rc = circuit_setup(h, kVref);
     if (rc == PIC_OK) rc = stage_face_field(h);
     double F1 = 0.0;
     if (rc == PIC_OK && !G.apex.empty()) {
@@ -506,6 +510,7 @@ int pic_create(const pic_geometry_t *geometry, const pic_grid_t *grid, const pic
       rc = stage_efield(h);
     }
   }
+  if (rc == PIC_OK && h->E0) rc = circuit_reset(h);
   if (rc != PIC_OK) {
     std::string m = h->last_error;
     pic_destroy(h);
@@ -746,6 +751,14 @@ static int sort_one(pic_t *h, int s) {
   return stage_sort(h);
 }
 
+int pic_circuit(pic_t *h) {
+  if (!h) return PIC_E_INVALID;
+  if (!circuit_on(h)) return pic_fail(h, PIC_E_INVALID, "no circuit: set circuit_R, circuit_C and PIC_F_CIRCUIT");
+  PIC_TRY(stage_circuit(h));
+  PIC_CUDA(h, cudaStreamSynchronize(h->stream));
+  return launch_check(h, "circuit");
+}
+
 int pic_collide(pic_t *h) {
   if (!h) return PIC_E_INVALID;
   PIC_TRY(stage_collide(h));
@@ -812,6 +825,7 @@ static int step_body_graph(pic_t *h) {
   k_begin_step<<<1, 1, 0, h->stream>>>(h->clock);
   PIC_TRY(stage_emit(h));
   PIC_TRY(stage_push(h));
+  PIC_TRY(stage_circuit(h));
   PIC_TRY(stage_sort(h));
   PIC_TRY(stage_collide(h));
   PIC_TRY(stage_deposit(h));
@@ -1209,6 +1223,7 @@ static int pic_step_eager(pic_t *h, int nsteps, int64_t step) {
     rc = stage_emit(h);
     cudaEventRecord(ev[1], h->stream);
     if (rc == PIC_OK) rc = stage_push(h);
+    if (rc == PIC_OK) rc = stage_circuit(h);
     cudaEventRecord(ev[2], h->stream);
     if (rc == PIC_OK) rc = stage_sort(h);
     cudaEventRecord(ev[3], h->stream);
@@ -1316,6 +1331,9 @@ int pic_diagnostics(pic_t *h, pic_diag_t *out) {
   for (int i = 0; i < 8; ++i) out->ms[i] = h->ms[i];
   out->kernel_launches = h->nlaunch + c.mg_graph_cycles * h->graph_body_launches;
   out->emission_evals = c.ctr[cWevals];
+  out->V_gap = h->E0 ? c.V_gap : h->V0;
+  out->I_gap = c.I_gap;
+  out->I_tot = c.I_tot;
   out->surrogate_faces = c.ctr[cSurFaces];
   return PIC_OK;
 }

@@ -71,6 +71,7 @@ struct DevClock {
   float mg_rel_last;        // its relative residual
   double mg_lifted;         // norm of the lifted right-hand side of the current solve
   int64_t mg_graph_cycles;  // cycles run inside graphs since create (launch accounting)
+  double V_gap, I_gap, I_tot;  // RC circuit: gap voltage [V], Shockley-Ramo gap current, circuit current [A]
 };
 
 struct SpeciesBuf {
@@ -151,9 +152,13 @@ struct pic_s {
   uint8_t *solid = nullptr;      // per cell
   uint8_t *cheb = nullptr;       // per cell: Chebyshev distance to the nearest solid cell (capped)
   long long *phi = nullptr;      // per node, fixed point: phi [V] = phi * 2^-kPhiShift
+  bool anode_dirty = false;      // the anode plane holds a circuit's V_gap instead of V0
+  bool circuit_ready = false;    // the circuit state holds V_gap = V0 (set once the unit field exists)
   bool dirichlet_valid = false;  // phi holds the Dirichlet values of dirichlet_V0fx on the mask
   long long dirichlet_V0fx = 0;
   float4 *E = nullptr;           // per node
+  float4 *E0 = nullptr;          // per node: unit Laplace field [1/m] (circuit; null without one)
+  double *ramo_part = nullptr;   // Shockley-Ramo partial sums
   unsigned long long *Q = nullptr;  // per node, int64 two's complement charge
   pic::Species sp[3];
   pic::Faces faces;
@@ -275,7 +280,7 @@ namespace pic {
 enum Kid : int {
   kidPush = 0, kidKeys, kidScatter, kidFixShort, kidFixMid, kidFixLong, kidGather, kidScanPartial, kidScanApply,
   kidDeposit, kidMccCount, kidMccProducts, kidDfiCount, kidDfiProducts, kidDirichlet, kidResidual64, kidNormSum,
-  kidSmooth, kidSmoothFirst, kidResidual, kidRestrict, kidProlong, kidCoarse, kidTail, kidCorrect, kidEfield, kidFaceField,
+  kidSmooth, kidSmoothFirst, kidResidual, kidRestrict, kidProlong, kidCoarse, kidTail, kidRamo, kidCorrect, kidEfield, kidFaceField,
   kidEmitSurrogate, kidEmitFallback, kidEmitCount, kidEmitWrite, kidInjectCount, kidInjectWrite, kidMlpForward,
   kidHeat, kidNum
 };
@@ -345,6 +350,11 @@ int tune_smoother(pic_t *h, int *best, int cap);
 int tune_residual(pic_t *h, int *best);
 int face_field_mean(pic_t *h, const int64_t *faces, int nf, double *out);
 int mg_coarse_setup(pic_t *h);
+// RC circuit and Shockley-Ramo current (k_field.cu)
+bool circuit_on(pic_t *h);
+int circuit_setup(pic_t *h, double V_L);
+int circuit_reset(pic_t *h);
+int stage_circuit(pic_t *h);
 // heat (k_heat.cu)
 int stage_heat(pic_t *h);
 // emission surrogate (k_mlp.cu)

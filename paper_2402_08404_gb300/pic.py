@@ -18,6 +18,7 @@ F_EMISSION, F_EVAP, F_SPUTTER, F_IMPACT_ION, F_DFI, F_HEAT, F_SURROGATE, F_MIXED
 F_ALL = 0xFF
 F_FAST_INTEGRAL = 0x100
 F_GRAPH = 0x200
+F_CIRCUIT = 0x400
 F_PRODUCTION = F_ALL | F_FAST_INTEGRAL     # surrogate, FP32 Gamow quadrature for its fallback, mixed MG
 
 QE = 1.602176634e-19
@@ -47,7 +48,8 @@ class Params(C.Structure):
     _fields_ = [("dt", C.c_double), ("apex_field", C.c_double), ("V0", C.c_double), ("T0", C.c_double),
                 ("work_function", C.c_double), ("w_min", C.c_double), ("w_max_units", C.c_int),
                 ("n_heat", C.c_int), ("seed", C.c_uint64), ("flags", C.c_uint32), ("mg_tol", C.c_double),
-                ("mg_max_cycles", C.c_int), ("mg_sweeps", C.c_int)]
+                ("mg_max_cycles", C.c_int), ("mg_sweeps", C.c_int), ("circuit_R", C.c_double),
+                ("circuit_C", C.c_double)]
 
 
 class Diag(C.Structure):
@@ -58,7 +60,8 @@ class Diag(C.Structure):
                 ("mg_residual", C.c_double), ("V0", C.c_double), ("max_face_field", C.c_double),
                 ("max_J", C.c_double), ("max_T", C.c_double), ("emitted_current", C.c_double),
                 ("ms", C.c_double * 8), ("kernel_launches", C.c_int64), ("emission_evals", C.c_int64),
-                ("surrogate_faces", C.c_int64)]
+                ("surrogate_faces", C.c_int64), ("V_gap", C.c_double), ("I_gap", C.c_double),
+                ("I_tot", C.c_double)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
@@ -80,7 +83,8 @@ def lib():
         L.pic_destroy.restype = None
         L.pic_last_error.argtypes = [vp]
         L.pic_last_error.restype = C.c_char_p
-        for name in ("pic_emit", "pic_push", "pic_sort", "pic_collide", "pic_deposit", "pic_solve_field", "pic_heat"):
+        for name in ("pic_emit", "pic_push", "pic_sort", "pic_collide", "pic_deposit", "pic_solve_field", "pic_heat",
+                     "pic_circuit"):
             getattr(L, name).argtypes = [vp]
         L.pic_step.argtypes = [vp, i32]
         L.pic_load_particles.argtypes = [vp, i32] + [vp] * 8 + [i64]
@@ -174,7 +178,8 @@ class Pic:
         grid = GridT(cfg["nx"], cfg["ny"], cfg["nz"], cfg["dx"])
         prm = Params(cfg["dt"], cfg["apex_field"], V0, cfg["T0"], cfg["work_function"], cfg["w_min"],
                      int(cfg["w_max_units"]), int(cfg.get("n_heat", 0)), int(cfg.get("seed", 1)), int(flags),
-                     float(mg_tol), int(mg_max_cycles), int(mg_sweeps))
+                     float(mg_tol), int(mg_max_cycles), int(mg_sweeps), float(cfg.get("circuit_R", 0.0)),
+                     float(cfg.get("circuit_C", 0.0)))
         h = C.c_void_p()
         a = self._alloc.alloc_fn if self._alloc else ALLOC_FN(0)
         f = self._alloc.free_fn if self._alloc else FREE_FN(0)
@@ -294,6 +299,9 @@ class Pic:
 
     def sort(self):
         self._check(lib().pic_sort(self.h))
+
+    def circuit(self):
+        self._check(lib().pic_circuit(self.h))
 
     def collide(self):
         self._check(lib().pic_collide(self.h))
