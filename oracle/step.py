@@ -4,6 +4,9 @@ Order (Sec. 2.3.1 and Fig. newpic; the paper prints no pseudocode, this is the r
   a1 emission from every exposed face (field from phi^n, temperature of the owner cell)
   a2 surface injection: evaporation, then sputtering from the previous step's ion impacts
   a3 gather + leapfrog push of every SP (new ones included) + boundary removal / ion impacts
+     (with an external circuit, prm circuit_R and circuit_C > 0: then the Shockley-Ramo current
+     of the pushed e- and Cu+ and one Euler step of the RC circuit; the step's Poisson solve
+     holds the anode at the new V_gap)
   a4 stable cell sort of every species (survivors in previous order)
   a5 impact ionization MCC, a6 direct field ionization
   a7 fixed-point charge deposit, a8 Poisson solve, a9 node field
@@ -18,7 +21,7 @@ import math
 
 import numpy as np
 
-from . import collide, emission, field, heat, particles as P, philox, surface
+from . import circuit, collide, emission, field, heat, particles as P, philox, surface
 from . import constants as C
 
 E_, N_, I_ = "e", "n", "i"
@@ -49,6 +52,9 @@ class State:
         for k in self.sp:
             self.sp[k], self.off[k] = P.stable_sort(grid, self.sp[k])
         self.Q = None
+        self.circuit = prm.get("circuit_R", 0) > 0 and prm.get("circuit_C", 0) > 0
+        self.V_gap, self.I_gap, self.I_tot = float(prm["V0"]), 0.0, 0.0
+        self.E0 = None
 
 
 def face_temperature(st):
@@ -194,6 +200,18 @@ def push_all(st):
     return alive
 
 
+def circuit_update(st, alive):
+    """The circuit passage of Sec. 2.3.1: I_gap of the pushed e- and Cu+ still in the domain,
+    then V_gap <- V_gap + dt/C (I_tot - I_gap) with I_tot = (V0 - V_gap)/R."""
+    prm = st.prm
+    if st.E0 is None:
+        st.E0 = circuit.unit_field(st.grid)
+    charged = [(-1, P.take(st.sp[E_], np.nonzero(alive[E_])[0])), (1, P.take(st.sp[I_], np.nonzero(alive[I_])[0]))]
+    st.I_gap = circuit.gap_current(st.E0, charged, prm["w_min"])
+    st.V_gap, st.I_tot = circuit.circuit_step(st.V_gap, st.I_gap, prm["V0"], prm["circuit_R"], prm["circuit_C"],
+                                              prm["dt"])
+
+
 def deposit_all(st):
     g = st.grid
     Q = P.deposit(g, st.sp[E_], -1)
@@ -205,7 +223,7 @@ def solve_field(st):
     g, prm = st.grid, st.prm
     st.Q = deposit_all(st)
     f = field.rhs_from_charge(g, st.Q, prm["w_min"])
-    st.phi = field.solve_poisson(g, prm["V0"], f)
+    st.phi = field.solve_poisson(g, st.V_gap if st.circuit else prm["V0"], f)
     st.E = field.efield(g, st.phi)
 
 
@@ -233,6 +251,8 @@ def step(st, emission_fn=None):
     st.sp[N_] = P.concat(P.concat(st.sp[N_], new_ev), new_sp)
     # a3
     alive = push_all(st)
+    if st.circuit:
+        circuit_update(st, alive)
     # a4
     for k in st.sp:
         st.sp[k], st.off[k] = P.stable_sort(g, st.sp[k], alive[k])

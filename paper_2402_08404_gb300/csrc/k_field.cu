@@ -554,9 +554,9 @@ __global__ void k_unit_field(const long long *phi, float4 *E0, int nx, int ny, i
 
 // Shockley-Ramo current of the charged SPs, I = sum Z e w w_min v . E0(x) (E0 gathered like E),
 // over the SPs still in the domain (after a push: key != kDead; sorted SPs: w > 0).  Per-block
-// partial sums in FP64 over a fixed grid of kRamoBlocks blocks, so the summation
-// order, and with it every bit of the result, does not depend on anything but the SP order.
-constexpr int kRamoBlocks = 256;
+// partial sums in FP64 over a fixed grid of kRamoBlocks blocks (enough warps in flight to cover
+// the gather latency on every SM), so the summation order, and with it every bit of the result,
+// does not depend on anything but the SP order.
 __global__ void __launch_bounds__(256) k_ramo_partial(SpeciesBuf e, SpeciesBuf ion, const uint32_t *key_e,
                                                       const uint32_t *key_i, const float4 *E0, int nx, int ny,
                                                       const DevClock *clk, double qw, double *part) {
@@ -585,11 +585,22 @@ __global__ void __launch_bounds__(256) k_ramo_partial(SpeciesBuf e, SpeciesBuf i
   }
 }
 
-// I_gap from the partials (fixed order), then one explicit Euler step of the RC circuit:
-// I_tot = (V0 - V_gap)/R, V_gap += dt/C (I_tot - I_gap)
-__global__ void k_circuit(const double *part, DevClock *clk, double V0, double R, double Cg, double dt) {
-  double I = 0.0;
-  for (int b = 0; b < kRamoBlocks; ++b) I += part[b];
+// I_gap from the partials (one block: runs of kRamoBlocks/256 partials, then a fixed tree), then
+// one explicit Euler step of the RC circuit: I_tot = (V0 - V_gap)/R, V_gap += dt/C (I_tot - I_gap)
+__global__ void __launch_bounds__(256) k_circuit(const double *part, DevClock *clk, double V0, double R, double Cg,
+                                                 double dt) {
+  __shared__ double sh[256];
+  constexpr int kRun = kRamoBlocks / 256;
+  double a = 0.0;
+  for (int b = 0; b < kRun; ++b) a += part[threadIdx.x * kRun + b];
+  sh[threadIdx.x] = a;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x != 0) return;
+  const double I = sh[0];
   const double Itot = (V0 - clk->V_gap) / R;
   clk->I_gap = I;
   clk->I_tot = Itot;
@@ -1223,7 +1234,7 @@ int stage_circuit(pic_t *h) {
     k_ramo_partial<<<kRamoBlocks, 256, 0, h->stream>>>(h->sp[PIC_ELECTRON].a, h->sp[PIC_ION].a, ke, ki, h->E0, h->nx,
                                                        h->ny, h->clock, qw, h->ramo_part);
   }
-  k_circuit<<<1, 1, 0, h->stream>>>(h->ramo_part, h->clock, h->V0, h->prm.circuit_R, h->prm.circuit_C, h->prm.dt);
+  k_circuit<<<1, 256, 0, h->stream>>>(h->ramo_part, h->clock, h->V0, h->prm.circuit_R, h->prm.circuit_C, h->prm.dt);
   return launch_check(h, "circuit");
 }
 

@@ -417,7 +417,7 @@ int pic_create(const pic_geometry_t *geometry, const pic_grid_t *grid, const pic
   h->red = alloc_n<double>(h, (int64_t)2 * ((h->nx + 1 + 31) / 32) * ((h->ny + 1 + 7) / 8) * (h->nz + 1)); A(h->red);
   h->red_out = alloc_n<double>(h, 2); A(h->red_out);
   h->red_mid = alloc_n<double>(h, 2 * 128); A(h->red_mid);
-  h->ramo_part = alloc_n<double>(h, 256); A(h->ramo_part);
+  h->ramo_part = alloc_n<double>(h, kRamoBlocks); A(h->ramo_part);
   if (h->prm.circuit_R > 0 && h->prm.circuit_C > 0) { h->E0 = alloc_n<float4>(h, h->nnode); A(h->E0); }
   h->tmp_len = alloc_n<int64_t>(h, 16); A(h->tmp_len);
   h->long_list = alloc_n<int2>(h, kLongCap); A(h->long_list);

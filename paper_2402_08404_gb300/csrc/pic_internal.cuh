@@ -28,6 +28,7 @@ constexpr double kLorentz = 2.0e-8;  // W Ohm K^-2 (Sec. 2.1)
 constexpr double kNmax = 1e24;       // m^-3 (1e-6 per cubic Angstrom, Sec. 2.3.2)
 
 constexpr uint32_t kDead = 0xFFFFFFFFu;
+constexpr int kRamoBlocks = 2048;   // blocks (and FP64 partial sums) of the Shockley-Ramo sum
 constexpr int kFracBits = 10;         // CIC fixed-point fraction bits per axis
 constexpr int kSputBits = 24;         // sputter accumulator: atoms * 2^24
 constexpr int kEnergyBits = 20;       // energy accumulators: eV * 2^20

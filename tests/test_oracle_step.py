@@ -73,3 +73,30 @@ def test_sputter_injection_conserves_atoms():
     assert abs(drop.sum() / frac - float(new_sp["w"].astype(np.float64).sum()) * wmin) <= moved.sum() / frac
     # what stays behind is less than one SP of the chosen weight plus one atom
     assert np.all(st.acc_sput[moved] / frac < before[moved] / frac)
+
+
+@pytest.mark.slow
+def test_step_with_circuit_reduces_and_discharges():
+    """With C so large that dt/C (I_tot - I_gap) is below V0's last bit, the circuit-coupled step
+    is the circuit-free step bit for bit.  With the paper's 1 kOhm and 1 pF, the electron current
+    toward the anode (a positive Shockley-Ramo current) lowers V_gap by dt/C I_gap in the first
+    step, and the solve holds the anode at that voltage."""
+    g = Grid(CFG["nx"], CFG["ny"], CFG["nz"], CFG["dx"], CFG["tip_radius"], CFG["tip_height"])
+    V0 = field.calibrate_V0(g, CFG["apex_field"])
+    pop = synth.plasma(CFG, seed=4)
+    phi = field.solve_poisson(g, V0)
+    runs = {}
+    for name, extra in (("none", {}), ("stiff", dict(circuit_R=1e3, circuit_C=1e30)),
+                        ("paper", dict(circuit_R=1e3, circuit_C=1e-12))):
+        st = S.State(g, dict(CFG, V0=V0, next_id=CFG["n_sp"], n_heat=0, **extra), pop, phi)
+        S.step(st)
+        runs[name] = st
+    a, b, c = runs["none"], runs["stiff"], runs["paper"]
+    assert b.V_gap == V0 and b.I_gap != 0.0
+    assert np.array_equal(a.phi, b.phi)
+    for k in "eni":
+        for f in P.FIELDS:
+            assert np.array_equal(a.sp[k][f], b.sp[k][f]), (k, f)
+    assert c.I_gap > 0 and c.I_tot == 0.0
+    assert c.V_gap == pytest.approx(V0 - CFG["dt"] / 1e-12 * c.I_gap, rel=1e-15)
+    assert np.all(c.phi[-1] == c.V_gap) and c.V_gap < V0
