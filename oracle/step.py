@@ -8,7 +8,8 @@ Order (Sec. 2.3.1 and Fig. newpic; the paper prints no pseudocode, this is the r
      of the pushed e- and Cu+ and one Euler step of the RC circuit; the step's Poisson solve
      holds the anode at the new V_gap)
   a4 stable cell sort of every species (survivors in previous order)
-  a5 impact ionization MCC, a6 direct field ionization
+  a5 impact ionization MCC (with prm "elastic": then e-Cu and Cu-Cu elastic collisions and
+     Cu+-Cu charge exchange on the sorted SPs), a6 direct field ionization
   a7 fixed-point charge deposit, a8 Poisson solve, a9 node field
   a10 every n_heat steps: continuity + heat on the tip cells
 
@@ -21,7 +22,7 @@ import math
 
 import numpy as np
 
-from . import circuit, collide, emission, field, heat, particles as P, philox, surface
+from . import circuit, collide, elastic, emission, field, heat, particles as P, philox, surface
 from . import constants as C
 
 E_, N_, I_ = "e", "n", "i"
@@ -260,6 +261,11 @@ def step(st, emission_fn=None):
     ids = collide.Counter(st.next_id)
     ni, ne, ev = collide.impact_ionization(g, prm, st.sp[E_], st.off[E_], st.sp[N_], st.off[N_], st.step, ids)
     st.count["impact_ionizations"] = ev
+    if prm.get("elastic"):
+        st.count["elastic_en"] = elastic.elastic_en(g, prm, st.sp[E_], st.off[E_], st.sp[N_], st.off[N_], st.step)
+        st.count["elastic_nn"] = elastic.elastic_nn(g, prm, st.sp[N_], st.off[N_], st.step)
+        st.count["charge_exchanges"] = elastic.charge_exchange(g, prm, st.sp[I_], st.off[I_], st.sp[N_], st.off[N_],
+                                                               st.step)
     # a6
     ni2, ne2, ev2 = collide.field_ionization(g, prm, st.sp[N_], st.E, st.step, ids)
     st.count["field_ionizations"] = ev2
