@@ -203,6 +203,8 @@ def run_ours(args):
     if args.circuit:   # the paper's external circuit: 1 kOhm, 1 pF, Shockley-Ramo gap current
         cfg["circuit_R"], cfg["circuit_C"] = 1e3, 1e-12
         prod_flags |= pic.F_CIRCUIT
+    if args.elastic:   # elastic e-Cu, Cu-Cu and Cu+-Cu charge exchange with the stand-in cross sections
+        prod_flags |= pic.F_ELASTIC
     plain_flags = pic.F_ALL & ~pic.F_SURROGATE & ~pic.F_MIXED_MG
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
@@ -339,6 +341,8 @@ def run_ours(args):
                    "form": form, "poisson_tol": args.mg_tol,
                    "circuit": ({"R_ohm": 1e3, "C_F": 1e-12, "V_gap_end": d1["V_gap"], "I_gap_end": d1["I_gap"]}
                                if args.circuit else None),
+                   "elastic": ({"e_Cu": d1["elastic_en"], "Cu_Cu": d1["elastic_nn"], "exchange": d1["charge_exchanges"]}
+                               if args.elastic else None),
                    "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()}, "mg_cycles": d1["mg_cycles"],
                    "kernel_ms_per_step": kernel_ms,
                    "surrogate": None if sur is None else {
@@ -525,6 +529,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false")
     ap.add_argument("--circuit", action="store_true", help="step with the RC circuit and Shockley-Ramo current")
+    ap.add_argument("--elastic", action="store_true", help="step with elastic collisions and charge exchange")
     args = ap.parse_args()
     if args.impl == "reference":
         out = run_reference(args)

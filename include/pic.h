@@ -61,6 +61,7 @@ extern "C" {
 #define PIC_F_MIXED_MG 0x80u    /* a8: FP32 V-cycles with FP64 residual refinement (else FP64 V-cycles) */
 #define PIC_F_FAST_INTEGRAL 0x100u  /* a1: Gamow quadrature and turning points in FP32 (J, P_N to ~1e-5
                                        relative) in the step and in pic_emission_eval; else all FP64 */
+#define PIC_F_ELASTIC 0x800u    /* a5: then elastic e-Cu and Cu-Cu collisions and Cu+-Cu charge exchange */
 #define PIC_F_CIRCUIT 0x400u    /* the RC circuit drives the anode (needs circuit_R, circuit_C > 0 at create) */
 #define PIC_F_GRAPH 0x200u      /* pic_step replays a CUDA graph of one step (the Poisson loop a device-side
                                    while node); the first call with new flags runs one step eagerly and
@@ -100,6 +101,9 @@ typedef struct {
   double circuit_R;     /* Ohm: external resistance of the RC circuit (with circuit_C > 0: allocates the
                            unit Laplace field; the circuit acts while PIC_F_CIRCUIT is set) */
   double circuit_C;     /* F: gap capacitance of the RC circuit */
+  double sigma_el_en;   /* m^2: e-Cu elastic cross section (<= 0: 1e-19, a constant stand-in) */
+  double sigma_el_nn;   /* m^2: Cu-Cu elastic cross section (<= 0: hard spheres pi (2 x 128 pm)^2) */
+  double sigma_cx;      /* m^2: Cu+-Cu charge exchange cross section (<= 0: 5e-19, a constant stand-in) */
 } pic_params_t;
 
 typedef struct {
@@ -122,6 +126,7 @@ typedef struct {
   int64_t surrogate_faces;  /* faces whose emission came from the surrogate this step */
   double V_gap;             /* V: gap voltage (V0 without a circuit) */
   double I_gap, I_tot;      /* A: Shockley-Ramo gap current and circuit current of the last circuit stage */
+  int64_t elastic_en, elastic_nn, charge_exchanges;  /* colliding pairs this step (PIC_F_ELASTIC) */
 } pic_diag_t;
 
 typedef struct pic_s pic_t;

@@ -217,6 +217,157 @@ __global__ void k_mcc_products(McArgs a, SpeciesBuf ions) {
   }
 }
 
+// ---- elastic collisions and charge exchange ---------------------------------------------------
+// e + Cu -> e + Cu and Cu + Cu -> Cu + Cu (eq:newv with the velocity difference of eq:du) and
+// Cu+ + Cu -> Cu + Cu+ (the electron hops: the SPs swap velocities), on the cell-sorted SPs of
+// the step.  Whole SPs collide, one draw per pair: U_c < P, P = 1 - exp(-u n_t W_t sigma dt)
+// (eq:colp, the projectile view of impact ionization), decided in FP32 and re-decided in FP64
+// when U_c is within 2^-12 P of the FP32 value, so every decision equals the FP64 one.  The SP
+// with the smaller weight always takes its new velocity, the other with probability
+// w_small / w_large (tested in integers on the 24-bit draw).  Pairs are disjoint, so one thread
+// per projectile updates both SPs without atomics.
+struct ElArgs {
+  SpeciesBuf A, B;              // inter-species: A preferred projectile on ties; like-species: A = B
+  const uint32_t *off_a, *off_b;
+  int sp_a, sp_b;               // species indices (sorted counts on the device clock)
+  int nx, ny;
+  double m_a, m_b, V_cell, dt, w_min, sigma;
+  uint64_t seed;
+  uint32_t pair_purpose, draw_purpose;
+  int exchange, ctr;
+  DevClock *clk;
+};
+
+__device__ __forceinline__ double rn3(double a0, double b0, double a1, double b1, double a2, double b2) {
+  return __dadd_rn(__dadd_rn(__dmul_rn(a0, b0), __dmul_rn(a1, b1)), __dmul_rn(a2, b2));
+}
+
+// R^-1(theta, phi) v = R^T v, R rows (ct cp, ct sp, -st), (-sp, cp, 0), (st cp, st sp, ct)
+__device__ void rot_inv(double th, double ph, const double v[3], double out[3]) {
+  const double ct = cos(th), st = sin(th), cp = cos(ph), sp = sin(ph);
+  out[0] = rn3(ct * cp, v[0], -sp, v[1], st * cp, v[2]);
+  out[1] = rn3(ct * sp, v[0], cp, v[1], st * sp, v[2]);
+  out[2] = rn3(-st, v[0], 0.0, v[1], ct, v[2]);
+}
+
+// eq:du: R^-1(theta,phi) [R^-1(theta',phi') - I] (0,0,u) for u = (ux,uy,uz)
+__device__ void delta_u(double ux, double uy, double uz, double cos_tp, double phi_p, double du[3]) {
+  const double u = sqrt(rn3(ux, ux, uy, uy, uz, uz));
+  double th = 0.0, ph = 0.0;
+  if (u > 0) {
+    double c = uz / u;
+    c = c > 1.0 ? 1.0 : (c < -1.0 ? -1.0 : c);
+    th = acos(c);
+    ph = atan2(uy, ux);
+  }
+  const double pole[3] = {0.0, 0.0, u};
+  double t[3];
+  rot_inv(acos(cos_tp), phi_p, pole, t);
+  t[0] -= pole[0]; t[1] -= pole[1]; t[2] -= pole[2];
+  rot_inv(th, ph, t, du);
+}
+
+// One pair (A[ia] the projectile, B[ib] the target of Nt SPs in the cell).  True if it collided.
+__device__ bool el_pair(const ElArgs &a, const SpeciesBuf &A, int64_t ia, double mA, const SpeciesBuf &B, int64_t ib,
+                        double mB, uint32_t Nt, int64_t step) {
+  const int32_t wa = A.w[ia], wb = B.w[ib];
+  if (wa <= 0 || wb <= 0) return false;
+  const float ax = A.vx[ia], ay = A.vy[ia], az = A.vz[ia];
+  const float bx = B.vx[ib], by = B.vy[ib], bz = B.vz[ib];
+  const double nWsd = (double)Nt / a.V_cell * ((double)wb * a.w_min) * a.sigma * a.dt;   // screening only
+  const float fx = ax - bx, fy = ay - by, fz = az - bz;
+  const float x32 = sqrtf(fx * fx + fy * fy + fz * fz) * (float)nWsd;
+  const float P32 = -expm1f(-x32);
+  const U4 r = rng_block(a.seed, a.draw_purpose, A.id[ia], step, 0);
+  const float U = u01f(r.v[0]);
+  bool hit;
+  if (fabsf(U - P32) > ldexpf(P32, -12)) {
+    hit = U < P32;
+  } else {   // the FP64 definition, in the oracle's order of operations
+    const double dx = (double)ax - (double)bx, dy = (double)ay - (double)by, dz = (double)az - (double)bz;
+    const double u = sqrt(rn3(dx, dx, dy, dy, dz, dz));
+    const double P = -expm1(-(u * ((double)Nt / a.V_cell) * ((double)wb * a.w_min) * a.sigma * a.dt));
+    hit = u01d(r.v[0]) < P;
+  }
+  if (!hit) return false;
+  float na[3], nb[3];
+  if (a.exchange) {
+    na[0] = bx; na[1] = by; na[2] = bz;
+    nb[0] = ax; nb[1] = ay; nb[2] = az;
+  } else {
+    double du[3];
+    delta_u((double)ax - (double)bx, (double)ay - (double)by, (double)az - (double)bz, 2.0 * u01d(r.v[1]) - 1.0,
+            2.0 * kPi * u01d(r.v[2]), du);
+    const double mu = mA * mB / (mA + mB);
+    const double ka = mu / mA, kb = mu / mB;
+    na[0] = (float)((double)ax + ka * du[0]); na[1] = (float)((double)ay + ka * du[1]); na[2] = (float)((double)az + ka * du[2]);
+    nb[0] = (float)((double)bx - kb * du[0]); nb[1] = (float)((double)by - kb * du[1]); nb[2] = (float)((double)bz - kb * du[2]);
+  }
+  // weight rule: U_w < w_small / w_large  <=>  (2 (word >> 8) + 1) w_large < w_small 2^25
+  const bool a_small = wa <= wb;
+  const uint64_t ws = (uint64_t)(a_small ? wa : wb), wl = (uint64_t)(a_small ? wb : wa);
+  const bool large_too = (2ull * (r.v[3] >> 8) + 1ull) * wl < (ws << 25);
+  if (a_small || large_too) { A.vx[ia] = na[0]; A.vy[ia] = na[1]; A.vz[ia] = na[2]; }
+  if (!a_small || large_too) { B.vx[ib] = nb[0]; B.vy[ib] = nb[1]; B.vz[ib] = nb[2]; }
+  return true;
+}
+
+__device__ __forceinline__ void el_count(DevClock *clk, int ctr, int hits) {
+  for (int o = 16; o > 0; o >>= 1) hits += __shfl_down_sync(0xffffffffu, hits, o);
+  if ((threadIdx.x & 31) == 0 && hits) atomicAdd((unsigned long long *)&clk->ctr[ctr], (unsigned long long)hits);
+}
+
+// Inter-species pass (e-Cu elastic, Cu+-Cu exchange): one work item per sorted SP of A then B;
+// the projectile of its cell (fewer SPs, ties: A) resolves its target and collides the pair.
+__global__ void __launch_bounds__(256) k_elastic_inter(ElArgs a) {
+  const int64_t na = a.clk->n_sorted[a.sp_a], nb = a.clk->n_sorted[a.sp_b];
+  const int64_t step = a.clk->step;
+  const int64_t total = na + nb;
+  const int64_t span = (total + 31) & ~31ll;   // whole warps for the counter reduction
+  int hits = 0;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < span; t += (int64_t)gridDim.x * blockDim.x) {
+    if (t < total) {
+      const bool in_a = t < na;
+      const int64_t p = in_a ? t : t - na;
+      const SpeciesBuf &S = in_a ? a.A : a.B;
+      const uint32_t c = (uint32_t)cell_index((int)floorf(S.x[p]), (int)floorf(S.y[p]), (int)floorf(S.z[p]), a.nx, a.ny);
+      const uint32_t Na = a.off_a[c + 1] - a.off_a[c], Nb = a.off_b[c + 1] - a.off_b[c];
+      if (Na > 0 && Nb > 0 && (Na <= Nb) == in_a) {
+        const uint32_t Nt = in_a ? Nb : Na;
+        const uint32_t k = (uint32_t)(p - (in_a ? a.off_a[c] : a.off_b[c]));
+        const uint32_t o = u_index(rng_block(a.seed, a.pair_purpose, c, step, 0).v[0], Nt);
+        const int64_t q = (int64_t)(in_a ? a.off_b[c] : a.off_a[c]) + (k + o) % Nt;
+        hits += in_a ? el_pair(a, a.A, p, a.m_a, a.B, q, a.m_b, Nt, step) : el_pair(a, a.B, p, a.m_b, a.A, q, a.m_a, Nt, step);
+      }
+    }
+    el_count(a.clk, a.ctr, hits);
+    hits = 0;
+  }
+}
+
+// Like-species pass (Cu-Cu): places (o + 2m, o + 2m + 1) mod N of each cell form pair m; the
+// first is the projectile.
+__global__ void __launch_bounds__(256) k_elastic_like(ElArgs a) {
+  const int64_t n = a.clk->n_sorted[a.sp_a];
+  const int64_t step = a.clk->step;
+  const int64_t span = (n + 31) & ~31ll;
+  int hits = 0;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < span; t += (int64_t)gridDim.x * blockDim.x) {
+    if (t < n) {
+      const uint32_t c = (uint32_t)cell_index((int)floorf(a.A.x[t]), (int)floorf(a.A.y[t]), (int)floorf(a.A.z[t]), a.nx, a.ny);
+      const uint32_t N = a.off_a[c + 1] - a.off_a[c];
+      if (N >= 2) {
+        const uint32_t k = (uint32_t)(t - a.off_a[c]);
+        const uint32_t o = u_index(rng_block(a.seed, a.pair_purpose, c, step, 0).v[0], N);
+        const uint32_t q = (k + N - o) % N;   // shuffled place of this SP
+        if ((q & 1u) == 0 && q + 1 < N) hits += el_pair(a, a.A, t, a.m_a, a.A, (int64_t)a.off_a[c] + (k + 1) % N, a.m_a, N, step);
+      }
+    }
+    el_count(a.clk, a.ctr, hits);
+    hits = 0;
+  }
+}
+
 // ---- direct field ionization -----------------------------------------------------------------
 struct DfiArgs {
   SpeciesBuf n, e, ions;
@@ -328,6 +479,32 @@ int stage_collide(pic_t *h) {
     ++h->nlaunch;
     k_commit_new<<<1, 1, 0, h->stream>>>(h->clock, total, go, cImpactIon);
     PIC_TRY(launch_check(h, "mcc"));
+  }
+  if (fl & PIC_F_ELASTIC) {
+    ElArgs a{};
+    a.nx = h->nx; a.ny = h->ny;
+    a.V_cell = h->dx * h->dx * h->dx; a.dt = h->prm.dt; a.w_min = h->prm.w_min; a.seed = h->prm.seed;
+    a.clk = h->clock;
+    const Species &E = h->sp[PIC_ELECTRON], &N = h->sp[PIC_NEUTRAL], &I = h->sp[PIC_ION];
+    // e + Cu elastic
+    a.A = E.a; a.B = N.a; a.off_a = E.off; a.off_b = N.off; a.sp_a = PIC_ELECTRON; a.sp_b = PIC_NEUTRAL;
+    a.m_a = E.mass; a.m_b = N.mass; a.sigma = h->sigma_el_en; a.pair_purpose = kPairEn; a.draw_purpose = kDrawEn;
+    a.exchange = 0; a.ctr = cElasticEn;
+    ++h->nlaunch;
+    { KtScope kt_(h, kidElastic, 0); k_elastic_inter<<<grid, kThreads, 0, h->stream>>>(a); }
+    // Cu + Cu elastic
+    a.A = N.a; a.B = N.a; a.off_a = N.off; a.off_b = N.off; a.sp_a = a.sp_b = PIC_NEUTRAL;
+    a.m_a = a.m_b = N.mass; a.sigma = h->sigma_el_nn; a.pair_purpose = kPairNn; a.draw_purpose = kDrawNn;
+    a.ctr = cElasticNn;
+    ++h->nlaunch;
+    { KtScope kt_(h, kidElastic, 0); k_elastic_like<<<grid, kThreads, 0, h->stream>>>(a); }
+    // Cu+ + Cu charge exchange
+    a.A = I.a; a.B = N.a; a.off_a = I.off; a.off_b = N.off; a.sp_a = PIC_ION; a.sp_b = PIC_NEUTRAL;
+    a.m_a = I.mass; a.m_b = N.mass; a.sigma = h->sigma_cx; a.pair_purpose = kPairCx; a.draw_purpose = kDrawCx;
+    a.exchange = 1; a.ctr = cChargeEx;
+    ++h->nlaunch;
+    { KtScope kt_(h, kidElastic, 0); k_elastic_inter<<<grid, kThreads, 0, h->stream>>>(a); }
+    PIC_TRY(launch_check(h, "elastic"));
   }
   if (fl & PIC_F_DFI) {
     DfiArgs d;

@@ -196,7 +196,7 @@ static T *alloc_n(pic_t *h, int64_t n) {
 namespace pic {
 const char *const kKernelNames[kidNum] = {
     "k_push", "k_keys", "k_scatter", "k_fix_short", "k_fix_mid", "k_fix_long", "k_gather", "k_scan_partial",
-    "k_scan_apply", "k_deposit", "k_mcc_count", "k_mcc_products", "k_dfi_count", "k_dfi_products", "k_dirichlet",
+    "k_scan_apply", "k_deposit", "k_mcc_count", "k_mcc_products", "k_elastic", "k_dfi_count", "k_dfi_products", "k_dirichlet",
     "k_residual64", "k_norm_sum", "k_smooth", "k_smooth_first", "k_residual", "k_restrict", "k_prolong", "k_coarse", "k_vcycle_tail", "k_ramo",
     "k_correct", "k_efield", "k_face_field", "k_emit_surrogate", "k_emit_fallback", "k_emit_count", "k_emit_write",
     "k_inject_count", "k_inject_write", "k_mlp_forward", "k_heat"};
@@ -314,6 +314,10 @@ int pic_create(const pic_geometry_t *geometry, const pic_grid_t *grid, const pic
   // 3 + 3 sweeps: on the staircased tip a V-cycle contracts the error by ~0.4 with 2 + 2 and ~0.3
   // with 3 + 3, which reaches a 1e-6 step tolerance in one refinement cycle instead of two
   h->mg_sweeps = h->prm.mg_sweeps > 0 ? std::min(h->prm.mg_sweeps, 8) : 3;
+  // constant stand-ins: e-Cu 1e-19 m^2, Cu-Cu hard spheres of radius 128 pm, Cu+-Cu 5e-19 m^2
+  h->sigma_el_en = h->prm.sigma_el_en > 0 ? h->prm.sigma_el_en : 1.0e-19;
+  h->sigma_el_nn = h->prm.sigma_el_nn > 0 ? h->prm.sigma_el_nn : kPi * ((2 * 128e-12) * (2 * 128e-12));
+  h->sigma_cx = h->prm.sigma_cx > 0 ? h->prm.sigma_cx : 5.0e-19;
   h->stream = (cudaStream_t)stream;
   h->alloc = alloc; h->free_fn = free_fn; h->alloc_user = alloc_user;
   int dev = 0;
@@ -1306,6 +1310,9 @@ int pic_diagnostics(pic_t *h, pic_diag_t *out) {
   out->sputtered = c.ctr[cSputtered];
   out->impact_ionizations = c.ctr[cImpactIon];
   out->field_ionizations = c.ctr[cFieldIon];
+  out->elastic_en = c.ctr[cElasticEn];
+  out->elastic_nn = c.ctr[cElasticNn];
+  out->charge_exchanges = c.ctr[cChargeEx];
   out->ion_impacts = c.ctr[cIonImpacts];
   out->mg_cycles = h->last_solve_graph ? c.mg_cycles_last : h->last_mg_cycles;
   out->mg_residual = h->last_solve_graph ? (double)c.mg_rel_last : h->last_mg_res;

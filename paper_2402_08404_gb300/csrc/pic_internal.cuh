@@ -48,12 +48,15 @@ constexpr double kSurY0c = 0.0, kSurY0s = 1.0, kSurY1s = 2.0, kSurLogJFloor = -8
 constexpr int kSurOut = 2;
 
 // Philox purposes (one key per purpose)
-enum Purpose : uint32_t { kEmit = 1, kPair = 2, kIon = 3, kScat = 4, kDfi = 5, kEvapP = 6, kSput = 7 };
+enum Purpose : uint32_t {
+  kEmit = 1, kPair = 2, kIon = 3, kScat = 4, kDfi = 5, kEvapP = 6, kSput = 7,
+  kPairEn = 8, kDrawEn = 9, kPairNn = 10, kDrawNn = 11, kPairCx = 12, kDrawCx = 13   // elastic e-Cu, Cu-Cu, exchange
+};
 
 // device counters (int64), indices
 enum Ctr {
   cEmitted = 0, cEvaporated, cSputtered, cImpactIon, cFieldIon, cRemovedE, cRemovedN, cRemovedI,
-  cIonImpacts, cWevals, cSurFaces, cNum
+  cIonImpacts, cWevals, cSurFaces, cElasticEn, cElasticNn, cChargeEx, cNum
 };
 
 // error bits set by kernels
@@ -170,6 +173,7 @@ struct pic_s {
   double *coarse_inv_d = nullptr;
   int32_t *coarse_slot = nullptr;   // split-layout slot of each free node
   int tail_start = -1;              // first level of the cluster-launched V-cycle tail (-1: none)
+  double sigma_el_en = 0, sigma_el_nn = 0, sigma_cx = 0;   // m^2 (elastic and exchange passes)
   int mg_sweeps = 3;                // red-black sweeps before and after each coarse correction
   pic::DevClock *clock = nullptr;
   // scratch
@@ -280,7 +284,7 @@ namespace pic {
 // Kernels whose launches can be timed one by one (pic_set_kernel_timing); the order is the ABI's.
 enum Kid : int {
   kidPush = 0, kidKeys, kidScatter, kidFixShort, kidFixMid, kidFixLong, kidGather, kidScanPartial, kidScanApply,
-  kidDeposit, kidMccCount, kidMccProducts, kidDfiCount, kidDfiProducts, kidDirichlet, kidResidual64, kidNormSum,
+  kidDeposit, kidMccCount, kidMccProducts, kidElastic, kidDfiCount, kidDfiProducts, kidDirichlet, kidResidual64, kidNormSum,
   kidSmooth, kidSmoothFirst, kidResidual, kidRestrict, kidProlong, kidCoarse, kidTail, kidRamo, kidCorrect, kidEfield, kidFaceField,
   kidEmitSurrogate, kidEmitFallback, kidEmitCount, kidEmitWrite, kidInjectCount, kidInjectWrite, kidMlpForward,
   kidHeat, kidNum

@@ -1,0 +1,122 @@
+"""Parity of the elastic e-Cu and Cu-Cu collisions and the Cu+-Cu charge exchange
+(PIC_F_ELASTIC) with the oracle, through the C ABI.
+
+Bars: the collision decisions are integer work (event counts and the set of SPs whose velocity
+turned, bit for bit); the new velocities are FP64 rotations stored in float32, within 1e-6 of
+the oracle's per component (plus 1 m/s).  The cross sections are raised far above the
+stand-in defaults so that a small instance has hundreds of events in every pass.
+"""
+import numpy as np
+import pytest
+
+from oracle import collide, elastic as EL, field, particles as P
+from oracle import constants as OC
+from paper_2402_08404_gb300 import synth
+
+from _util import SPECIES, assert_sp_equal, fixed_phi, grid_of, small_cfg, sorted_pop
+
+pytestmark = pytest.mark.gpu
+
+SIGMAS = dict(sigma_el_en=2e-19, sigma_el_nn=2e-15, sigma_cx=1e-16)
+
+
+@pytest.fixture(scope="module")
+def pic():
+    import os
+    from paper_2402_08404_gb300 import _build
+    if not os.path.exists(_build.LIB):
+        _build.build()
+    from paper_2402_08404_gb300 import pic as m
+    return m
+
+
+def _population(cfg, seed):
+    """Seeded plasma with the species brought together in cells: electrons and ions on neutral
+    positions, half the neutrals on the other half's, energetic electrons, fast ions."""
+    pop = synth.plasma(cfg, seed=seed)
+    rng = np.random.default_rng(seed + 1)
+    nn = len(pop["n"]["x"])
+    half = nn // 2
+    for c in ("x", "y", "z"):
+        pop["n"][c][half:2 * half] = pop["n"][c][:half]
+    for k, lo, hi, m in (("e", 20.0, 300.0, OC.M_E), ("i", 1.0, 50.0, OC.M_CU)):
+        n = len(pop[k]["x"])
+        src = rng.integers(0, nn, n)
+        for c in ("x", "y", "z"):
+            pop[k][c] = pop["n"][c][src].copy()
+        speed = np.sqrt(2 * rng.uniform(lo, hi, n) * OC.E_CHARGE / m)
+        u = rng.normal(size=(n, 3))
+        u /= np.linalg.norm(u, axis=1)[:, None]
+        for a, c in enumerate(("vx", "vy", "vz")):
+            pop[k][c] = (speed * u[:, a]).astype(np.float32)
+    return pop
+
+
+def _setup(pic, flags, V0=60.0, seed=12):
+    cfg = small_cfg(n_sp=30000, w_min=1.0, **SIGMAS)
+    g = grid_of(cfg)
+    sim = pic.Pic(cfg, capacity=200_000, V0=V0, flags=flags)
+    pop = _population(cfg, seed)
+    phi = fixed_phi(field.solve_poisson(g, V0))
+    sim.set_potential(phi)
+    for s, (k, _, _) in enumerate(SPECIES):
+        sim.load_particles(s, pop[k])
+    sim.set_clock(3, cfg["n_sp"])
+    st = sorted_pop(g, pop)
+    offs = {k: P.stable_sort(g, st[k])[1] for k in "eni"}
+    prm = {"dt": cfg["dt"], "seed": cfg["seed"], "w_min": cfg["w_min"], **SIGMAS}
+    return cfg, g, sim, st, offs, prm, field.efield(g, phi)
+
+
+def _velocities_close(got, ref, k):
+    for c in ("vx", "vy", "vz"):
+        a, b = got[c].astype(np.float64), ref[c].astype(np.float64)
+        bad = np.nonzero(~(np.abs(a - b) <= 1e-6 * (np.abs(b) + 1.0)))[0]
+        assert len(bad) == 0, (k, c, bad[:5], a[bad[:5]], b[bad[:5]])
+
+
+def test_elastic_passes_match_oracle(pic):
+    cfg, g, sim, st, offs, prm, E = _setup(pic, pic.F_ELASTIC)
+    before = {k: {c: st[k][c].copy() for c in ("vx", "vy", "vz")} for k in "eni"}
+    ev_en = EL.elastic_en(g, prm, st["e"], offs["e"], st["n"], offs["n"], 3)
+    ev_nn = EL.elastic_nn(g, prm, st["n"], offs["n"], 3)
+    ev_cx = EL.charge_exchange(g, prm, st["i"], offs["i"], st["n"], offs["n"], 3)
+    assert min(ev_en, ev_nn, ev_cx) > 100, (ev_en, ev_nn, ev_cx)
+    sim.collide()
+    d = sim.diagnostics()
+    assert (d["elastic_en"], d["elastic_nn"], d["charge_exchanges"]) == (ev_en, ev_nn, ev_cx)
+    assert d["impact_ionizations"] == 0 and d["field_ionizations"] == 0
+    for s, (k, _, _) in enumerate(SPECIES):
+        got = sim.get_particles(s)
+        assert_sp_equal(got, st[k], fields=("x", "y", "z", "w", "id"))
+        _velocities_close(got, st[k], k)
+        if k in "ei":   # which SPs turned: bit-exact decisions (electron and ion changes are large)
+            moved_ref = np.any([st[k][c] != before[k][c] for c in ("vx", "vy", "vz")], axis=0)
+            moved_got = np.any([got[c] != before[k][c] for c in ("vx", "vy", "vz")], axis=0)
+            assert np.array_equal(moved_got, moved_ref), k
+    sim.close()
+
+
+def test_collide_stage_with_elastic_matches_oracle(pic):
+    """Impact ionization, then the three passes, then field ionization: the oracle step's order."""
+    flags = pic.F_IMPACT_ION | pic.F_DFI | pic.F_ELASTIC
+    cfg, g, sim, st, offs, prm, E = _setup(pic, flags, V0=420.0, seed=13)
+    ids = collide.Counter(cfg["n_sp"])
+    ni, ne, ev = collide.impact_ionization(g, prm, st["e"], offs["e"], st["n"], offs["n"], 3, ids)
+    ev_en = EL.elastic_en(g, prm, st["e"], offs["e"], st["n"], offs["n"], 3)
+    ev_nn = EL.elastic_nn(g, prm, st["n"], offs["n"], 3)
+    ev_cx = EL.charge_exchange(g, prm, st["i"], offs["i"], st["n"], offs["n"], 3)
+    ni2, ne2, ev2 = collide.field_ionization(g, prm, st["n"], E, 3, ids)
+    ref = {"e": P.concat(P.concat(st["e"], ne), ne2), "n": st["n"], "i": P.concat(P.concat(st["i"], ni), ni2)}
+    sim.collide()
+    d = sim.diagnostics()
+    assert ev > 20 and ev2 > 20 and min(ev_en, ev_nn, ev_cx) > 20, (ev, ev2, ev_en, ev_nn, ev_cx)
+    assert (d["impact_ionizations"], d["field_ionizations"]) == (ev, ev2)
+    assert (d["elastic_en"], d["elastic_nn"], d["charge_exchanges"]) == (ev_en, ev_nn, ev_cx)
+    assert d["next_id"] == ids.next_id
+    for s, (k, _, _) in enumerate(SPECIES):
+        got = sim.get_particles(s)
+        assert_sp_equal(got, ref[k], fields=("x", "y", "z", "w", "id"))
+        _velocities_close(got, ref[k], k)
+    sim.close()
+
