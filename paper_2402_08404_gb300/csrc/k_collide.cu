@@ -227,15 +227,26 @@ __global__ void k_mcc_products(McArgs a, SpeciesBuf ions) {
 // w_small / w_large (tested in integers on the 24-bit draw).  Pairs are disjoint, so one thread
 // per projectile updates both SPs without atomics.
 struct ElArgs {
-  SpeciesBuf A, B;              // inter-species: A preferred projectile on ties; like-species: A = B
-  const uint32_t *off_a, *off_b;
-  int sp_a, sp_b;               // species indices (sorted counts on the device clock)
-  int nx, ny;
-  double m_a, m_b, V_cell, dt, w_min, sigma;
+  double V_cell, dt, w_min;
   uint64_t seed;
+  DevClock *clk;
+};
+
+struct ElPass {
+  SpeciesBuf A, B;                          // like-species pass: A only
+  const uint32_t *off_a, *off_b;            // per-cell offsets of the last sort
+  const uint32_t *skey_a, *skey_b;          // cell of each sorted position
+  int sa, sb;                               // species indices (sorted counts on the device clock)
+  double m_a, m_b, sigma;
   uint32_t pair_purpose, draw_purpose;
   int exchange, ctr;
-  DevClock *clk;
+  float nWsd1;                              // w_min sigma dt / V_cell in FP32 (screening only)
+};
+
+struct ElQueue {
+  uint64_t *pair;    // projectile-side index | target-side index << 32 (A index low when A projects)
+  uint32_t *info;    // Nt | projectile in B << 30 | FP64 decision needed << 31
+  int *n, cap;
 };
 
 __device__ __forceinline__ double rn3(double a0, double b0, double a1, double b1, double a2, double b2) {
@@ -267,105 +278,159 @@ __device__ void delta_u(double ux, double uy, double uz, double cos_tp, double p
   rot_inv(th, ph, t, du);
 }
 
-// One pair (A[ia] the projectile, B[ib] the target of Nt SPs in the cell).  True if it collided.
-__device__ bool el_pair(const ElArgs &a, const SpeciesBuf &A, int64_t ia, double mA, const SpeciesBuf &B, int64_t ib,
-                        double mB, uint32_t Nt, int64_t step) {
+// Pass kernels.  A decision kernel runs one work item per sorted SP of one species and only
+// the FP32 test (Philox draws, P in FP32); a pair that collides, or whose draw lies within the
+// guard band of P, goes to a queue.  The apply kernel then takes each queued pair: the FP64
+// decision where the band asked for it, the new velocities, the weight rule.  Pairs of a pass
+// are disjoint, so deferring the updates changes nothing, and the queue order does not matter.
+
+// FP32 test of one pair (A[ia] the projectile): 0 no collision, 1 collision, 2 within the band
+__device__ __forceinline__ int el_decide(const ElArgs &a, const SpeciesBuf &A, int64_t ia, const SpeciesBuf &B,
+                                         int64_t ib, uint32_t Nt, const ElPass &ps, int64_t step) {
   const int32_t wa = A.w[ia], wb = B.w[ib];
-  if (wa <= 0 || wb <= 0) return false;
-  const float ax = A.vx[ia], ay = A.vy[ia], az = A.vz[ia];
-  const float bx = B.vx[ib], by = B.vy[ib], bz = B.vz[ib];
-  const double nWsd = (double)Nt / a.V_cell * ((double)wb * a.w_min) * a.sigma * a.dt;   // screening only
-  const float fx = ax - bx, fy = ay - by, fz = az - bz;
-  const float x32 = sqrtf(fx * fx + fy * fy + fz * fz) * (float)nWsd;
+  if (wa <= 0 || wb <= 0) return 0;
+  const float fx = A.vx[ia] - B.vx[ib], fy = A.vy[ia] - B.vy[ib], fz = A.vz[ia] - B.vz[ib];
+  const float x32 = sqrtf(fx * fx + fy * fy + fz * fz) * ((float)Nt * (float)wb * ps.nWsd1);
   const float P32 = -expm1f(-x32);
-  const U4 r = rng_block(a.seed, a.draw_purpose, A.id[ia], step, 0);
-  const float U = u01f(r.v[0]);
-  bool hit;
-  if (fabsf(U - P32) > ldexpf(P32, -12)) {
-    hit = U < P32;
-  } else {   // the FP64 definition, in the oracle's order of operations
-    const double dx = (double)ax - (double)bx, dy = (double)ay - (double)by, dz = (double)az - (double)bz;
-    const double u = sqrt(rn3(dx, dx, dy, dy, dz, dz));
-    const double P = -expm1(-(u * ((double)Nt / a.V_cell) * ((double)wb * a.w_min) * a.sigma * a.dt));
-    hit = u01d(r.v[0]) < P;
-  }
-  if (!hit) return false;
-  float na[3], nb[3];
-  if (a.exchange) {
-    na[0] = bx; na[1] = by; na[2] = bz;
-    nb[0] = ax; nb[1] = ay; nb[2] = az;
-  } else {
-    double du[3];
-    delta_u((double)ax - (double)bx, (double)ay - (double)by, (double)az - (double)bz, 2.0 * u01d(r.v[1]) - 1.0,
-            2.0 * kPi * u01d(r.v[2]), du);
-    const double mu = mA * mB / (mA + mB);
-    const double ka = mu / mA, kb = mu / mB;
-    na[0] = (float)((double)ax + ka * du[0]); na[1] = (float)((double)ay + ka * du[1]); na[2] = (float)((double)az + ka * du[2]);
-    nb[0] = (float)((double)bx - kb * du[0]); nb[1] = (float)((double)by - kb * du[1]); nb[2] = (float)((double)bz - kb * du[2]);
-  }
-  // weight rule: U_w < w_small / w_large  <=>  (2 (word >> 8) + 1) w_large < w_small 2^25
-  const bool a_small = wa <= wb;
-  const uint64_t ws = (uint64_t)(a_small ? wa : wb), wl = (uint64_t)(a_small ? wb : wa);
-  const bool large_too = (2ull * (r.v[3] >> 8) + 1ull) * wl < (ws << 25);
-  if (a_small || large_too) { A.vx[ia] = na[0]; A.vy[ia] = na[1]; A.vz[ia] = na[2]; }
-  if (!a_small || large_too) { B.vx[ib] = nb[0]; B.vy[ib] = nb[1]; B.vz[ib] = nb[2]; }
-  return true;
+  const float U = u01f(rng_block(a.seed, ps.draw_purpose, A.id[ia], step, 0).v[0]);
+  if (fabsf(U - P32) <= ldexpf(P32, -12)) return 2;
+  return U < P32 ? 1 : 0;
 }
 
-__device__ __forceinline__ void el_count(DevClock *clk, int ctr, int hits) {
-  for (int o = 16; o > 0; o >>= 1) hits += __shfl_down_sync(0xffffffffu, hits, o);
-  if ((threadIdx.x & 31) == 0 && hits) atomicAdd((unsigned long long *)&clk->ctr[ctr], (unsigned long long)hits);
+__device__ __forceinline__ void el_push(const ElQueue &q, int64_t ia, int64_t ib, uint32_t Nt, bool proj_b, int d) {
+  const int slot = atomicAdd(q.n, 1);
+  if (slot >= q.cap) return;   // cannot happen: a pass has fewer pairs than the queue holds
+  q.pair[slot] = (uint64_t)(uint32_t)ia | ((uint64_t)(uint32_t)ib << 32);
+  q.info[slot] = Nt | (proj_b ? 1u << 30 : 0u) | (d == 2 ? 1u << 31 : 0u);
 }
 
-// Inter-species pass (e-Cu elastic, Cu+-Cu exchange): one work item per sorted SP of A then B;
-// the projectile of its cell (fewer SPs, ties: A) resolves its target and collides the pair.
-__global__ void __launch_bounds__(256) k_elastic_inter(ElArgs a) {
-  const int64_t na = a.clk->n_sorted[a.sp_a], nb = a.clk->n_sorted[a.sp_b];
+// The leader of each group of lanes with the same cell draws the cell's pairing word once.
+__device__ __forceinline__ uint32_t cell_word(const ElArgs &a, uint32_t purpose, uint32_t c, bool need, int64_t step) {
+  const unsigned grp = __match_any_sync(0xffffffffu, need ? c : 0xffffffffu);
+  const int leader = __ffs(grp) - 1;
+  uint32_t w = 0;
+  if (need && (int)(threadIdx.x & 31) == leader) w = rng_block(a.seed, purpose, c, step, 0).v[0];
+  return __shfl_sync(0xffffffffu, w, leader);
+}
+
+// Inter-species pass, one item per sorted SP of species A (each pair has exactly one member in
+// A): with Na <= Nb (ties: A) the SP at place k is the projectile of target (k + o) mod Nb;
+// otherwise it is the target of projectile j = (k - o) mod Na of B when j < Nb.
+__global__ void __launch_bounds__(256) k_el_decide_inter(ElArgs a, ElPass ps, ElQueue q) {
+  const int64_t na = a.clk->n_sorted[ps.sa];
   const int64_t step = a.clk->step;
-  const int64_t total = na + nb;
-  const int64_t span = (total + 31) & ~31ll;   // whole warps for the counter reduction
-  int hits = 0;
+  const int64_t span = (na + 31) & ~31ll;   // whole warps: the cell-word exchange needs every lane
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < span; t += (int64_t)gridDim.x * blockDim.x) {
-    if (t < total) {
-      const bool in_a = t < na;
-      const int64_t p = in_a ? t : t - na;
-      const SpeciesBuf &S = in_a ? a.A : a.B;
-      const uint32_t c = (uint32_t)cell_index((int)floorf(S.x[p]), (int)floorf(S.y[p]), (int)floorf(S.z[p]), a.nx, a.ny);
-      const uint32_t Na = a.off_a[c + 1] - a.off_a[c], Nb = a.off_b[c + 1] - a.off_b[c];
-      if (Na > 0 && Nb > 0 && (Na <= Nb) == in_a) {
-        const uint32_t Nt = in_a ? Nb : Na;
-        const uint32_t k = (uint32_t)(p - (in_a ? a.off_a[c] : a.off_b[c]));
-        const uint32_t o = u_index(rng_block(a.seed, a.pair_purpose, c, step, 0).v[0], Nt);
-        const int64_t q = (int64_t)(in_a ? a.off_b[c] : a.off_a[c]) + (k + o) % Nt;
-        hits += in_a ? el_pair(a, a.A, p, a.m_a, a.B, q, a.m_b, Nt, step) : el_pair(a, a.B, p, a.m_b, a.A, q, a.m_a, Nt, step);
-      }
+    uint32_t c = 0, oa = 0, Na = 0, ob = 0, Nb = 0;
+    if (t < na) {
+      c = ps.skey_a[t];
+      oa = ps.off_a[c]; Na = ps.off_a[c + 1] - oa;
+      ob = ps.off_b[c]; Nb = ps.off_b[c + 1] - ob;
     }
-    el_count(a.clk, a.ctr, hits);
-    hits = 0;
+    const bool need = t < na && Nb > 0;
+    const uint32_t w = cell_word(a, ps.pair_purpose, c, need, step);
+    if (!need) continue;
+    const uint32_t k = (uint32_t)(t - oa);
+    if (Na <= Nb) {
+      const uint32_t o = u_index(w, Nb);
+      const int64_t ib = (int64_t)ob + (k + o) % Nb;
+      const int d = el_decide(a, ps.A, t, ps.B, ib, Nb, ps, step);
+      if (d) el_push(q, t, ib, Nb, false, d);
+    } else {
+      const uint32_t o = u_index(w, Na);
+      const uint32_t j = (k + Na - o) % Na;
+      if (j >= Nb) continue;
+      const int64_t ib = (int64_t)ob + j;
+      const int d = el_decide(a, ps.B, ib, ps.A, t, Na, ps, step);
+      if (d) el_push(q, t, ib, Na, true, d);
+    }
   }
 }
 
 // Like-species pass (Cu-Cu): places (o + 2m, o + 2m + 1) mod N of each cell form pair m; the
-// first is the projectile.
-__global__ void __launch_bounds__(256) k_elastic_like(ElArgs a) {
-  const int64_t n = a.clk->n_sorted[a.sp_a];
+// first one is the projectile.
+__global__ void __launch_bounds__(256) k_el_decide_like(ElArgs a, ElPass ps, ElQueue q) {
+  const int64_t n = a.clk->n_sorted[ps.sa];
   const int64_t step = a.clk->step;
   const int64_t span = (n + 31) & ~31ll;
-  int hits = 0;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < span; t += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t c = 0, o0 = 0, N = 0;
     if (t < n) {
-      const uint32_t c = (uint32_t)cell_index((int)floorf(a.A.x[t]), (int)floorf(a.A.y[t]), (int)floorf(a.A.z[t]), a.nx, a.ny);
-      const uint32_t N = a.off_a[c + 1] - a.off_a[c];
-      if (N >= 2) {
-        const uint32_t k = (uint32_t)(t - a.off_a[c]);
-        const uint32_t o = u_index(rng_block(a.seed, a.pair_purpose, c, step, 0).v[0], N);
-        const uint32_t q = (k + N - o) % N;   // shuffled place of this SP
-        if ((q & 1u) == 0 && q + 1 < N) hits += el_pair(a, a.A, t, a.m_a, a.A, (int64_t)a.off_a[c] + (k + 1) % N, a.m_a, N, step);
+      c = ps.skey_a[t];
+      o0 = ps.off_a[c]; N = ps.off_a[c + 1] - o0;
+    }
+    const bool need = t < n && N >= 2;
+    const uint32_t w = cell_word(a, ps.pair_purpose, c, need, step);
+    if (!need) continue;
+    const uint32_t k = (uint32_t)(t - o0);
+    const uint32_t qq = (k + N - u_index(w, N)) % N;   // shuffled place of this SP
+    if ((qq & 1u) || qq + 1 >= N) continue;
+    const int64_t ib = (int64_t)o0 + (k + 1) % N;
+    const int d = el_decide(a, ps.A, t, ps.A, ib, N, ps, step);
+    if (d) el_push(q, t, ib, N, false, d);
+  }
+}
+
+// Queued pairs: the FP64 decision where asked (the definition, in the oracle's order of
+// operations), then eq:newv (or the exchange) and the weight rule.
+__global__ void __launch_bounds__(256) k_el_apply(ElArgs a, ElPass ps, ElQueue q) {
+  const int nq = min(*q.n, q.cap);
+  const int64_t step = a.clk->step;
+  int hits = 0;
+  const int span = (nq + 31) & ~31;
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < span; s += gridDim.x * blockDim.x) {
+    bool hit = false;
+    if (s < nq) {
+      const uint64_t pr = q.pair[s];
+      const uint32_t info = q.info[s];
+      const uint32_t Nt = info & 0x3FFFFFFFu;
+      const bool proj_b = (info >> 30) & 1u;
+      // A' is the projectile, B' its target
+      const SpeciesBuf &A = proj_b ? ps.B : ps.A;
+      const SpeciesBuf &B = proj_b ? ps.A : ps.B;
+      const int64_t ia = proj_b ? (int64_t)(pr >> 32) : (int64_t)(uint32_t)pr;
+      const int64_t ib = proj_b ? (int64_t)(uint32_t)pr : (int64_t)(pr >> 32);
+      const double mA = proj_b ? ps.m_b : ps.m_a, mB = proj_b ? ps.m_a : ps.m_b;
+      const int32_t wa = A.w[ia], wb = B.w[ib];
+      const float ax = A.vx[ia], ay = A.vy[ia], az = A.vz[ia];
+      const float bx = B.vx[ib], by = B.vy[ib], bz = B.vz[ib];
+      const U4 r = rng_block(a.seed, ps.draw_purpose, A.id[ia], step, 0);
+      hit = true;
+      if (info >> 31) {
+        const double dx = (double)ax - (double)bx, dy = (double)ay - (double)by, dz = (double)az - (double)bz;
+        const double u = sqrt(rn3(dx, dx, dy, dy, dz, dz));
+        const double P = -expm1(-(u * ((double)Nt / a.V_cell) * ((double)wb * a.w_min) * ps.sigma * a.dt));
+        hit = u01d(r.v[0]) < P;
+      }
+      if (hit) {
+        float na[3], nb[3];
+        if (ps.exchange) {
+          na[0] = bx; na[1] = by; na[2] = bz;
+          nb[0] = ax; nb[1] = ay; nb[2] = az;
+        } else {
+          double du[3];
+          delta_u((double)ax - (double)bx, (double)ay - (double)by, (double)az - (double)bz, 2.0 * u01d(r.v[1]) - 1.0,
+                  2.0 * kPi * u01d(r.v[2]), du);
+          const double mu = mA * mB / (mA + mB);
+          const double ka = mu / mA, kb = mu / mB;
+          na[0] = (float)((double)ax + ka * du[0]); na[1] = (float)((double)ay + ka * du[1]);
+          na[2] = (float)((double)az + ka * du[2]);
+          nb[0] = (float)((double)bx - kb * du[0]); nb[1] = (float)((double)by - kb * du[1]);
+          nb[2] = (float)((double)bz - kb * du[2]);
+        }
+        // weight rule: U_w < w_small / w_large  <=>  (2 (word >> 8) + 1) w_large < w_small 2^25
+        const bool a_small = wa <= wb;
+        const uint64_t ws = (uint64_t)(a_small ? wa : wb), wl = (uint64_t)(a_small ? wb : wa);
+        const bool large_too = (2ull * (r.v[3] >> 8) + 1ull) * wl < (ws << 25);
+        if (a_small || large_too) { A.vx[ia] = na[0]; A.vy[ia] = na[1]; A.vz[ia] = na[2]; }
+        if (!a_small || large_too) { B.vx[ib] = nb[0]; B.vy[ib] = nb[1]; B.vz[ib] = nb[2]; }
       }
     }
-    el_count(a.clk, a.ctr, hits);
-    hits = 0;
+    int v = hit ? 1 : 0;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    hits += v;
   }
+  if ((threadIdx.x & 31) == 0 && hits) atomicAdd((unsigned long long *)&a.clk->ctr[ps.ctr], (unsigned long long)hits);
 }
 
 // ---- direct field ionization -----------------------------------------------------------------
@@ -482,28 +547,38 @@ int stage_collide(pic_t *h) {
   }
   if (fl & PIC_F_ELASTIC) {
     ElArgs a{};
-    a.nx = h->nx; a.ny = h->ny;
     a.V_cell = h->dx * h->dx * h->dx; a.dt = h->prm.dt; a.w_min = h->prm.w_min; a.seed = h->prm.seed;
     a.clk = h->clock;
     const Species &E = h->sp[PIC_ELECTRON], &N = h->sp[PIC_NEUTRAL], &I = h->sp[PIC_ION];
-    // e + Cu elastic
-    a.A = E.a; a.B = N.a; a.off_a = E.off; a.off_b = N.off; a.sp_a = PIC_ELECTRON; a.sp_b = PIC_NEUTRAL;
-    a.m_a = E.mass; a.m_b = N.mass; a.sigma = h->sigma_el_en; a.pair_purpose = kPairEn; a.draw_purpose = kDrawEn;
-    a.exchange = 0; a.ctr = cElasticEn;
-    ++h->nlaunch;
-    { KtScope kt_(h, kidElastic, 0); k_elastic_inter<<<grid, kThreads, 0, h->stream>>>(a); }
-    // Cu + Cu elastic
-    a.A = N.a; a.B = N.a; a.off_a = N.off; a.off_b = N.off; a.sp_a = a.sp_b = PIC_NEUTRAL;
-    a.m_a = a.m_b = N.mass; a.sigma = h->sigma_el_nn; a.pair_purpose = kPairNn; a.draw_purpose = kDrawNn;
-    a.ctr = cElasticNn;
-    ++h->nlaunch;
-    { KtScope kt_(h, kidElastic, 0); k_elastic_like<<<grid, kThreads, 0, h->stream>>>(a); }
-    // Cu+ + Cu charge exchange
-    a.A = I.a; a.B = N.a; a.off_a = I.off; a.off_b = N.off; a.sp_a = PIC_ION; a.sp_b = PIC_NEUTRAL;
-    a.m_a = I.mass; a.m_b = N.mass; a.sigma = h->sigma_cx; a.pair_purpose = kPairCx; a.draw_purpose = kDrawCx;
-    a.exchange = 1; a.ctr = cChargeEx;
-    ++h->nlaunch;
-    { KtScope kt_(h, kidElastic, 0); k_elastic_inter<<<grid, kThreads, 0, h->stream>>>(a); }
+    auto pass = [&](const Species &A, int sa, const Species &B, int sb, double sigma, uint32_t pp, uint32_t dp, int ex,
+                    int ctr) {
+      ElPass ps{};
+      ps.A = A.a; ps.B = B.a; ps.off_a = A.off; ps.off_b = B.off; ps.skey_a = A.skey; ps.skey_b = B.skey;
+      ps.sa = sa; ps.sb = sb; ps.m_a = A.mass; ps.m_b = B.mass; ps.sigma = sigma;
+      ps.pair_purpose = pp; ps.draw_purpose = dp; ps.exchange = ex; ps.ctr = ctr;
+      ps.nWsd1 = (float)(h->prm.w_min * sigma * h->prm.dt / a.V_cell);
+      return ps;
+    };
+    // queues in the MCC scratch (its last reader, the products kernel, has run); a pass has at
+    // most one queued pair per SP of one species, and capsum covers e- plus Cu
+    const int cap = (int)std::min<int64_t>(E.cap + N.cap, INT32_MAX);
+    ElQueue q[3];
+    for (int p = 0; p < 3; ++p) q[p] = ElQueue{h->pair_cnt, (uint32_t *)h->pair_ncoll, h->long_n + 8 + p, cap};
+    PIC_CUDA(h, cudaMemsetAsync(h->long_n + 8, 0, 3 * sizeof(int), h->stream));
+    const ElPass pen = pass(E, PIC_ELECTRON, N, PIC_NEUTRAL, h->sigma_el_en, kPairEn, kDrawEn, 0, cElasticEn);
+    const ElPass pnn = pass(N, PIC_NEUTRAL, N, PIC_NEUTRAL, h->sigma_el_nn, kPairNn, kDrawNn, 0, cElasticNn);
+    const ElPass pcx = pass(I, PIC_ION, N, PIC_NEUTRAL, h->sigma_cx, kPairCx, kDrawCx, 1, cChargeEx);
+    const int agrid = h->nsm * 2;
+    h->nlaunch += 6;
+    {
+      KtScope kt_(h, kidElastic, 0);
+      k_el_decide_inter<<<grid, kThreads, 0, h->stream>>>(a, pen, q[0]);
+      k_el_apply<<<agrid, kThreads, 0, h->stream>>>(a, pen, q[0]);
+      k_el_decide_like<<<grid, kThreads, 0, h->stream>>>(a, pnn, q[1]);
+      k_el_apply<<<agrid, kThreads, 0, h->stream>>>(a, pnn, q[1]);
+      k_el_decide_inter<<<grid, kThreads, 0, h->stream>>>(a, pcx, q[2]);
+      k_el_apply<<<agrid, kThreads, 0, h->stream>>>(a, pcx, q[2]);
+    }
     PIC_TRY(launch_check(h, "elastic"));
   }
   if (fl & PIC_F_DFI) {
