@@ -35,15 +35,107 @@ __device__ __forceinline__ float sigma_ion32(float E) {
 
 struct McArgs {
   SpeciesBuf e, n;
-  const uint32_t *off_e, *off_n;
-  int nx, ny;
+  const uint32_t *off_e, *off_n;     // per-cell offsets of the last sort
+  const uint32_t *skey_e, *skey_n;   // cell of each sorted position
   double V_cell, dt, w_min;
   uint64_t seed;
   DevClock *clk;
-  uint64_t *pair_cnt, *pair_off;
-  int32_t *pair_ncoll;
   int *go;
 };
+
+// ---- block-ordered compaction of rare events ------------------------------------------------
+// A count kernel gives block b the contiguous work items [b chunk, (b + 1) chunk) and stages the
+// items with an event, in item order, at rec[b chunk ...]; a one-block scan turns the blocks'
+// product counts into offsets; the products kernel (same grid) writes each block's products in
+// item order from its offset.  Slots and ids are thus those of an exclusive scan over all
+// items in item order, without a scan over all items.
+struct EvBlocks {
+  uint64_t *rec;    // staged events: item | payload << 32
+  int *hits;        // events per block
+  uint64_t *cnt;    // products per block: ions | electrons << 32
+  uint64_t *off;    // exclusive offsets of cnt
+};
+
+__device__ __forceinline__ int64_t ev_chunk(int64_t total) {   // items per block, a multiple of 256
+  const int64_t per = (int64_t)gridDim.x * 256;
+  return (total + per - 1) / per * 256;
+}
+
+// Exclusive prefix of v over a 256-thread block in thread order, and the block total.
+__device__ __forceinline__ uint64_t block_scan_u64(uint64_t v, uint64_t *total, uint64_t *sh) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  uint64_t x = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint64_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) sh[w] = x;
+  __syncthreads();
+  uint64_t pre = 0, tot = 0;
+  for (int i = 0; i < 8; ++i) {
+    const uint64_t q = sh[i];
+    pre += i < w ? q : 0ull;
+    tot += q;
+  }
+  __syncthreads();
+  *total = tot;
+  return pre + x - v;
+}
+
+// Stage this tile's events (ev != 0) in item order and add the tile's product count pc.
+__device__ __forceinline__ void ev_stage(const EvBlocks &ev, int64_t lo, int64_t *run, uint64_t *prod, int64_t t,
+                                         uint32_t payload, uint64_t pc, uint64_t *sh) {
+  uint64_t n_tile, p_tile;
+  const uint64_t pos = block_scan_u64(payload ? 1ull : 0ull, &n_tile, sh);
+  block_scan_u64(pc, &p_tile, sh);
+  if (payload) ev.rec[lo + *run + (int64_t)pos] = (uint64_t)t | ((uint64_t)payload << 32);
+  *run += (int64_t)n_tile;
+  *prod += p_tile;
+}
+
+// One block: exclusive scan of the blocks' product counts, the total, and the capacity check.
+__global__ void __launch_bounds__(1024) k_ev_scan(EvBlocks ev, int nblk, uint64_t *total, DevClock *clk,
+                                                  int64_t cap_i, int64_t cap_e, int *go) {
+  __shared__ uint64_t sh[32];
+  uint64_t run = 0;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int base = 0; base < nblk; base += 1024) {
+    const int b = base + threadIdx.x;
+    const uint64_t v = b < nblk ? ev.cnt[b] : 0ull;
+    uint64_t x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint64_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) sh[w] = x;
+    __syncthreads();
+    uint64_t pre = 0, tot = 0;
+    for (int i = 0; i < 32; ++i) {
+      pre += i < w ? sh[i] : 0ull;
+      tot += sh[i];
+    }
+    if (b < nblk) ev.off[b] = run + pre + x - v;
+    run += tot;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    *total = run;
+    const int64_t ni = (int64_t)(run & 0xffffffffu), ne = (int64_t)(run >> 32);
+    const bool ok = clk->n[PIC_ION] + ni <= cap_i && clk->n[PIC_ELECTRON] + ne <= cap_e;
+    *go = ok ? 1 : 0;
+    if (!ok) atomicOr(&clk->err, kErrCapacity);
+  }
+}
+
+// The leader of each group of lanes with the same cell draws the cell's pairing word once and
+// shares it (every lane of the warp takes part).
+__device__ __forceinline__ uint32_t cell_word(uint64_t seed, uint32_t purpose, uint32_t c, bool need, int64_t step) {
+  const unsigned grp = __match_any_sync(0xffffffffu, need ? c : 0xffffffffu);
+  const int leader = __ffs(grp) - 1;
+  uint32_t w = 0;
+  if (need && (int)(threadIdx.x & 31) == leader) w = rng_block(seed, purpose, c, step, 0).v[0];
+  return __shfl_sync(0xffffffffu, w, leader);
+}
 
 struct Pair {
   int64_t ie, in;   // electron index, neutral index
@@ -51,82 +143,106 @@ struct Pair {
   uint32_t Nt;
 };
 
-// Resolve the pair of work item t (t < n_e: electron t; else neutral t - n_e).  false if none.
-__device__ bool resolve_pair(const McArgs &a, int64_t t, int64_t ne, int64_t step, Pair *pr) {
+// Cell and counts of work item t (t < n_e: electron t; else neutral t - n_e); whether the item is
+// the projectile of a pair.
+struct McItem {
+  uint32_t c, oe, Ne, on, Nn;
+  bool proj;
+};
+__device__ __forceinline__ McItem mc_item(const McArgs &a, int64_t t, int64_t ne) {
+  McItem m;
   const bool is_e = t < ne;
-  const int64_t p = is_e ? t : t - ne;
-  const SpeciesBuf &S = is_e ? a.e : a.n;
-  const uint32_t c = (uint32_t)cell_index((int)floorf(S.x[p]), (int)floorf(S.y[p]), (int)floorf(S.z[p]), a.nx, a.ny);
-  const uint32_t Ne = a.off_e[c + 1] - a.off_e[c];
-  const uint32_t Nn = a.off_n[c + 1] - a.off_n[c];
-  if (Ne == 0 || Nn == 0) return false;
-  const bool e_proj = Ne <= Nn;
-  if (e_proj != is_e) return false;
-  const uint32_t Nt = is_e ? Nn : Ne;
-  const uint32_t k = (uint32_t)(p - (is_e ? a.off_e[c] : a.off_n[c]));
-  const U4 r = rng_block(a.seed, kPair, c, step, 0);
-  const uint32_t o = u_index(r.v[0], Nt);
-  const uint32_t tgt = (k + o) % Nt;
-  if (is_e) { pr->ie = p; pr->in = a.off_n[c] + tgt; }
-  else { pr->in = p; pr->ie = a.off_e[c] + tgt; }
-  pr->proj_e = is_e;
-  pr->Nt = Nt;
-  return true;
+  m.c = is_e ? a.skey_e[t] : a.skey_n[t - ne];
+  m.oe = a.off_e[m.c]; m.Ne = a.off_e[m.c + 1] - m.oe;
+  m.on = a.off_n[m.c]; m.Nn = a.off_n[m.c + 1] - m.on;
+  m.proj = m.Ne > 0 && m.Nn > 0 && (m.Ne <= m.Nn) == is_e;
+  return m;
 }
 
-__global__ void k_mcc_count(McArgs a) {
+// The pair of projectile item t, from the cell's pairing word w.
+__device__ __forceinline__ Pair mc_pair(const McItem &m, int64_t t, int64_t ne, uint32_t w) {
+  Pair pr;
+  const bool is_e = t < ne;
+  const int64_t p = is_e ? t : t - ne;
+  pr.Nt = is_e ? m.Nn : m.Ne;
+  const uint32_t k = (uint32_t)(p - (is_e ? m.oe : m.on));
+  const uint32_t tgt = (k + u_index(w, pr.Nt)) % pr.Nt;
+  if (is_e) { pr.ie = p; pr.in = (int64_t)m.on + tgt; }
+  else { pr.in = p; pr.ie = (int64_t)m.oe + tgt; }
+  pr.proj_e = is_e;
+  return pr;
+}
+
+// Sub-particle collisions of one pair (0..min(w_p, w_t)).
+__device__ int mcc_ncoll(const McArgs &a, const Pair &pr, int64_t step) {
+  const float sig_peak = (float)(kLotzA / (2.718281828459045 * kXiCu * kXiCu));
+  const int we = a.e.w[pr.ie], wn = a.n.w[pr.in];
+  const int wp = pr.proj_e ? we : wn, wt = pr.proj_e ? wn : we;
+  const float dvx = a.e.vx[pr.ie] - a.n.vx[pr.in];
+  const float dvy = a.e.vy[pr.ie] - a.n.vy[pr.in];
+  const float dvz = a.e.vz[pr.ie] - a.n.vz[pr.in];
+  const float u2 = dvx * dvx + dvy * dvy + dvz * dvz;
+  const float u = sqrtf(u2);
+  const float E0 = (float)(0.5 * kMe / kQe) * u2;
+  const float nW = (float)((double)pr.Nt / a.V_cell * (double)wt * a.w_min * a.dt);
+  const float x = u * nW * sigma_ion32(E0);
+  const float P32 = -expm1f(-x);
+  const float band = ldexpf(P32 + u * nW * sig_peak, -12);
+  const uint64_t pid = pr.proj_e ? a.e.id[pr.ie] : a.n.id[pr.in];
+  int ncoll = 0;
+  bool exact = false;
+  for (int i = 0; i < wp && P32 + band >= kUmin; i += 4) {
+    const U4 r = rng_block(a.seed, kIon, pid, step, (uint32_t)(i >> 2));
+    for (int j = 0; j < 4 && i + j < wp; ++j) {
+      const float U = u01f(r.v[j]);
+      if (fabsf(U - P32) <= band) exact = true;
+      ncoll += U < P32;
+    }
+  }
+  if (exact) {
+    const double ex = (double)a.e.vx[pr.ie] - (double)a.n.vx[pr.in];
+    const double ey = (double)a.e.vy[pr.ie] - (double)a.n.vy[pr.in];
+    const double ez = (double)a.e.vz[pr.ie] - (double)a.n.vz[pr.in];
+    const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)), __dmul_rn(ez, ez));
+    const double ud = sqrt(d2);
+    const double E0d = 0.5 * kMe * d2 / kQe;
+    const double xd = ud * ((double)pr.Nt / a.V_cell) * ((double)wt * a.w_min) * sigma_ion64(E0d) * a.dt;
+    const double P64 = -expm1(-xd);
+    ncoll = 0;
+    for (int i = 0; i < wp; i += 4) {
+      const U4 r = rng_block(a.seed, kIon, pid, step, (uint32_t)(i >> 2));
+      for (int j = 0; j < 4 && i + j < wp; ++j) ncoll += u01d(r.v[j]) < P64;
+    }
+  }
+  return ncoll > wt ? wt : ncoll;
+}
+
+// Work items: sorted electrons, then sorted neutrals; events staged with payload ncoll.
+__global__ void __launch_bounds__(256) k_mcc_count(McArgs a, EvBlocks ev) {
+  __shared__ uint64_t sh[8];
   const int64_t ne = a.clk->n_sorted[PIC_ELECTRON], nn = a.clk->n_sorted[PIC_NEUTRAL];
   const int64_t step = a.clk->step;
-  const int64_t total = ne + nn;
-  const float sig_peak = (float)(kLotzA / (2.718281828459045 * kXiCu * kXiCu));
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
-    Pair pr;
+  const int64_t total = ne + nn, chunk = ev_chunk(total);
+  const int64_t lo = (int64_t)blockIdx.x * chunk, hi = min(total, lo + chunk);
+  int64_t run = 0;
+  uint64_t prod = 0;
+  for (int64_t base = lo; base < hi; base += 256) {
+    const int64_t t = base + threadIdx.x;
+    McItem m{};
+    if (t < hi) m = mc_item(a, t, ne);
+    const uint32_t w = cell_word(a.seed, kPair, m.c, m.proj, step);
     int ncoll = 0;
-    if (resolve_pair(a, t, ne, step, &pr)) {
-      const int we = a.e.w[pr.ie], wn = a.n.w[pr.in];
-      const int wp = pr.proj_e ? we : wn, wt = pr.proj_e ? wn : we;
-      const float dvx = a.e.vx[pr.ie] - a.n.vx[pr.in];
-      const float dvy = a.e.vy[pr.ie] - a.n.vy[pr.in];
-      const float dvz = a.e.vz[pr.ie] - a.n.vz[pr.in];
-      const float u2 = dvx * dvx + dvy * dvy + dvz * dvz;
-      const float u = sqrtf(u2);
-      const float E0 = (float)(0.5 * kMe / kQe) * u2;
-      const float nW = (float)((double)pr.Nt / a.V_cell * (double)wt * a.w_min * a.dt);
-      const float x = u * nW * sigma_ion32(E0);
-      const float P32 = -expm1f(-x);
-      const float band = ldexpf(P32 + u * nW * sig_peak, -12);
-      const uint64_t pid = pr.proj_e ? a.e.id[pr.ie] : a.n.id[pr.in];
-      bool exact = false;
-      for (int i = 0; i < wp && P32 + band >= kUmin; i += 4) {
-        const U4 r = rng_block(a.seed, kIon, pid, step, (uint32_t)(i >> 2));
-        for (int j = 0; j < 4 && i + j < wp; ++j) {
-          const float U = u01f(r.v[j]);
-          if (fabsf(U - P32) <= band) exact = true;
-          ncoll += U < P32;
-        }
-      }
-      if (exact) {
-        const double ex = (double)a.e.vx[pr.ie] - (double)a.n.vx[pr.in];
-        const double ey = (double)a.e.vy[pr.ie] - (double)a.n.vy[pr.in];
-        const double ez = (double)a.e.vz[pr.ie] - (double)a.n.vz[pr.in];
-        const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)), __dmul_rn(ez, ez));
-        const double ud = sqrt(d2);
-        const double E0d = 0.5 * kMe * d2 / kQe;
-        const double xd = ud * ((double)pr.Nt / a.V_cell) * ((double)wt * a.w_min) * sigma_ion64(E0d) * a.dt;
-        const double P64 = -expm1(-xd);
-        ncoll = 0;
-        for (int i = 0; i < wp; i += 4) {
-          const U4 r = rng_block(a.seed, kIon, pid, step, (uint32_t)(i >> 2));
-          for (int j = 0; j < 4 && i + j < wp; ++j) ncoll += u01d(r.v[j]) < P64;
-        }
-      }
-      if (ncoll > wt) ncoll = wt;
-      a.pair_ncoll[t] = ncoll;
-      a.pair_cnt[t] = ncoll > 0 ? (1ull | ((uint64_t)(ncoll < we ? 2 : 1) << 32)) : 0ull;
-    } else {
-      a.pair_ncoll[t] = 0;
-      a.pair_cnt[t] = 0ull;
+    uint64_t pc = 0;
+    if (m.proj) {
+      const Pair pr = mc_pair(m, t, ne, w);
+      ncoll = mcc_ncoll(a, pr, step);
+      if (ncoll > 0) pc = 1ull | ((uint64_t)(ncoll < a.e.w[pr.ie] ? 2 : 1) << 32);
     }
+    ev_stage(ev, lo, &run, &prod, t, (uint32_t)ncoll, pc, sh);
+  }
+  if (threadIdx.x == 0) {
+    ev.hits[blockIdx.x] = (int)run;
+    ev.cnt[blockIdx.x] = prod;
   }
 }
 
@@ -153,15 +269,6 @@ __device__ __forceinline__ void put_sp(SpeciesBuf &B, int64_t s, float x, float 
   B.x[s] = x; B.y[s] = y; B.z[s] = z; B.vx[s] = vx; B.vy[s] = vy; B.vz[s] = vz; B.w[s] = w; B.id[s] = id;
 }
 
-// capacity check + totals of a packed (ions | electrons << 32) scan
-__global__ void k_check_new(DevClock *clk, const uint64_t *total, int64_t cap_i, int64_t cap_e, int *go) {
-  const uint64_t t = *total;
-  const int64_t ni = (int64_t)(t & 0xffffffffu), ne = (int64_t)(t >> 32);
-  const bool ok = clk->n[PIC_ION] + ni <= cap_i && clk->n[PIC_ELECTRON] + ne <= cap_e;
-  *go = ok ? 1 : 0;
-  if (!ok) atomicOr(&clk->err, kErrCapacity);
-}
-
 __global__ void k_commit_new(DevClock *clk, const uint64_t *total, const int *go, int ctr) {
   if (!*go) return;
   const uint64_t t = *total;
@@ -172,18 +279,33 @@ __global__ void k_commit_new(DevClock *clk, const uint64_t *total, const int *go
   clk->ctr[ctr] += ni;
 }
 
-__global__ void k_mcc_products(McArgs a, SpeciesBuf ions) {
+// Products of the staged pairs, block by block in item order from the block's offset.
+__global__ void __launch_bounds__(256) k_mcc_products(McArgs a, EvBlocks ev, SpeciesBuf ions) {
+  __shared__ uint64_t sh[8];
   if (!*a.go) return;
   const int64_t ne = a.clk->n_sorted[PIC_ELECTRON], nn = a.clk->n_sorted[PIC_NEUTRAL];
   const int64_t ne_all = a.clk->n[PIC_ELECTRON], ni = a.clk->n[PIC_ION];
   const int64_t step = a.clk->step, id_base = a.clk->next_id;
-  const int64_t total = ne + nn;
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
-    const int ncoll = a.pair_ncoll[t];
-    if (ncoll <= 0) continue;
-    Pair pr;
-    resolve_pair(a, t, ne, step, &pr);
-    const uint64_t off = a.pair_off[t];
+  const int64_t lo = (int64_t)blockIdx.x * ev_chunk(ne + nn);
+  const int nh = ev.hits[blockIdx.x];
+  uint64_t run = ev.off[blockIdx.x];
+  for (int base = 0; base < nh; base += 256) {
+    const int i = base + threadIdx.x;
+    Pair pr{};
+    int ncoll = 0;
+    uint64_t pc = 0;
+    if (i < nh) {
+      const uint64_t rec = ev.rec[lo + i];
+      const int64_t t = (int64_t)(uint32_t)rec;
+      ncoll = (int)(rec >> 32);
+      const McItem m = mc_item(a, t, ne);
+      pr = mc_pair(m, t, ne, rng_block(a.seed, kPair, m.c, step, 0).v[0]);
+      pc = 1ull | ((uint64_t)(ncoll < a.e.w[pr.ie] ? 2 : 1) << 32);
+    }
+    uint64_t tile;
+    const uint64_t off = run + block_scan_u64(pc, &tile, sh);
+    run += tile;
+    if (i >= nh) continue;
     const int64_t ion_off = (int64_t)(off & 0xffffffffu), e_off = (int64_t)(off >> 32);
     int64_t id = id_base + ion_off + e_off;
     const int64_t in = pr.in, ie = pr.ie;
@@ -304,15 +426,6 @@ __device__ __forceinline__ void el_push(const ElQueue &q, int64_t ia, int64_t ib
   q.info[slot] = Nt | (proj_b ? 1u << 30 : 0u) | (d == 2 ? 1u << 31 : 0u);
 }
 
-// The leader of each group of lanes with the same cell draws the cell's pairing word once.
-__device__ __forceinline__ uint32_t cell_word(const ElArgs &a, uint32_t purpose, uint32_t c, bool need, int64_t step) {
-  const unsigned grp = __match_any_sync(0xffffffffu, need ? c : 0xffffffffu);
-  const int leader = __ffs(grp) - 1;
-  uint32_t w = 0;
-  if (need && (int)(threadIdx.x & 31) == leader) w = rng_block(a.seed, purpose, c, step, 0).v[0];
-  return __shfl_sync(0xffffffffu, w, leader);
-}
-
 // Inter-species pass, one item per sorted SP of species A (each pair has exactly one member in
 // A): with Na <= Nb (ties: A) the SP at place k is the projectile of target (k + o) mod Nb;
 // otherwise it is the target of projectile j = (k - o) mod Na of B when j < Nb.
@@ -328,7 +441,7 @@ __global__ void __launch_bounds__(256) k_el_decide_inter(ElArgs a, ElPass ps, El
       ob = ps.off_b[c]; Nb = ps.off_b[c + 1] - ob;
     }
     const bool need = t < na && Nb > 0;
-    const uint32_t w = cell_word(a, ps.pair_purpose, c, need, step);
+    const uint32_t w = cell_word(a.seed, ps.pair_purpose, c, need, step);
     if (!need) continue;
     const uint32_t k = (uint32_t)(t - oa);
     if (Na <= Nb) {
@@ -360,7 +473,7 @@ __global__ void __launch_bounds__(256) k_el_decide_like(ElArgs a, ElPass ps, ElQ
       o0 = ps.off_a[c]; N = ps.off_a[c + 1] - o0;
     }
     const bool need = t < n && N >= 2;
-    const uint32_t w = cell_word(a, ps.pair_purpose, c, need, step);
+    const uint32_t w = cell_word(a.seed, ps.pair_purpose, c, need, step);
     if (!need) continue;
     const uint32_t k = (uint32_t)(t - o0);
     const uint32_t qq = (k + N - u_index(w, N)) % N;   // shuffled place of this SP
@@ -440,73 +553,95 @@ struct DfiArgs {
   int nx, ny;
   double dt_fs, pre, c1, c2, expo, lim2;   // rate = pre (c1/E)^expo exp(-c2/E), E in GV/m
   float lim2f;                             // lim2 in FP32 (screening of the barrier-suppression test)
+  float E2skip;                            // |E|^2 below which P dt < 2^-27: no draw can ionize
   uint64_t seed;
   DevClock *clk;
-  uint64_t *cnt, *off;
-  int32_t *nion;
   int *go;
 };
 
-__global__ void k_dfi_count(DfiArgs a) {
+// Sub-particles of neutral t that ionize this step.
+__device__ int dfi_nion(const DfiArgs &a, int64_t t, int64_t step) {
+  const int w = a.n.w[t];
+  if (w <= 0) return 0;
+  const float3 e = gather_E(a.E, a.n.x[t], a.n.y[t], a.n.z[t], a.nx, a.ny);
+  // |E|^2 is defined in FP64 (the oracle's sum of the three exact squares).  It is formed in
+  // FP32 first (within a few ulp) and in FP64 only where the barrier-suppression decision is
+  // close; P32 below only places the guard band, inside which the draw is re-decided from
+  // the FP64 |E|^2.
+  const float E2f = fmaf(e.x, e.x, fmaf(e.y, e.y, e.z * e.z));
+  if (E2f < a.E2skip) return 0;
+  const bool near_bsi = fabsf(E2f - a.lim2f) <= 1e-5f * a.lim2f;
+  double E2 = (double)E2f;
+  if (near_bsi)
+    E2 = __dadd_rn(__dadd_rn(__dmul_rn((double)e.x, (double)e.x), __dmul_rn((double)e.y, (double)e.y)),
+                   __dmul_rn((double)e.z, (double)e.z));
+  if (E2 > a.lim2) return w;
+  int k = 0;
+  const float Eg = sqrtf(E2f) * 1e-9f;
+  const float P32 = (float)a.pre * powf((float)a.c1 / Eg, (float)a.expo) * expf(-(float)a.c2 / Eg) * (float)a.dt_fs;
+  const float band = ldexpf(P32, -12);
+  const uint64_t id = a.n.id[t];
+  bool exact = false;
+  for (int i = 0; i < w && P32 + band >= kUmin; i += 4) {
+    const U4 r = rng_block(a.seed, kDfi, id, step, (uint32_t)(i >> 2));
+    for (int j = 0; j < 4 && i + j < w; ++j) {
+      const float U = u01f(r.v[j]);
+      if (fabsf(U - P32) <= band) exact = true;
+      k += U < P32;
+    }
+  }
+  if (exact) {
+    const double E2d = __dadd_rn(__dadd_rn(__dmul_rn((double)e.x, (double)e.x), __dmul_rn((double)e.y, (double)e.y)),
+                                 __dmul_rn((double)e.z, (double)e.z));
+    const double Ed = sqrt(E2d) * 1e-9;
+    const double P64 = a.pre * pow(a.c1 / Ed, a.expo) * exp(-a.c2 / Ed) * a.dt_fs;
+    k = 0;
+    for (int i = 0; i < w; i += 4) {
+      const U4 r = rng_block(a.seed, kDfi, id, step, (uint32_t)(i >> 2));
+      for (int j = 0; j < 4 && i + j < w; ++j) k += u01d(r.v[j]) < P64;
+    }
+  }
+  return k;
+}
+
+__global__ void __launch_bounds__(256) k_dfi_count(DfiArgs a, EvBlocks ev) {
+  __shared__ uint64_t sh[8];
   const int64_t nn = a.clk->n[PIC_NEUTRAL];
   const int64_t step = a.clk->step;
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nn; t += (int64_t)gridDim.x * blockDim.x) {
-    const int w = a.n.w[t];
-    int k = 0;
-    if (w > 0) {
-      const float3 e = gather_E(a.E, a.n.x[t], a.n.y[t], a.n.z[t], a.nx, a.ny);
-      // |E|^2 is defined in FP64 (the oracle's sum of the three exact squares).  It is formed in
-      // FP32 first (within a few ulp) and in FP64 only where the barrier-suppression decision is
-      // close; P32 below only places the guard band, inside which the draw is re-decided from
-      // the FP64 |E|^2.
-      const float E2f = fmaf(e.x, e.x, fmaf(e.y, e.y, e.z * e.z));
-      const bool near_bsi = fabsf(E2f - a.lim2f) <= 1e-5f * a.lim2f;
-      double E2 = (double)E2f;
-      if (near_bsi)
-        E2 = __dadd_rn(__dadd_rn(__dmul_rn((double)e.x, (double)e.x), __dmul_rn((double)e.y, (double)e.y)),
-                       __dmul_rn((double)e.z, (double)e.z));
-      if (E2 > a.lim2) {
-        k = w;
-      } else if (E2f > 0.0f) {
-        const float Eg = sqrtf(E2f) * 1e-9f;
-        const float P32 = (float)a.pre * powf((float)a.c1 / Eg, (float)a.expo) * expf(-(float)a.c2 / Eg) * (float)a.dt_fs;
-        const float band = ldexpf(P32, -12);
-        const uint64_t id = a.n.id[t];
-        bool exact = false;
-        for (int i = 0; i < w && P32 + band >= kUmin; i += 4) {
-          const U4 r = rng_block(a.seed, kDfi, id, step, (uint32_t)(i >> 2));
-          for (int j = 0; j < 4 && i + j < w; ++j) {
-            const float U = u01f(r.v[j]);
-            if (fabsf(U - P32) <= band) exact = true;
-            k += U < P32;
-          }
-        }
-        if (exact) {
-          const double E2d = __dadd_rn(__dadd_rn(__dmul_rn((double)e.x, (double)e.x), __dmul_rn((double)e.y, (double)e.y)),
-                                       __dmul_rn((double)e.z, (double)e.z));
-          const double Ed = sqrt(E2d) * 1e-9;
-          const double P64 = a.pre * pow(a.c1 / Ed, a.expo) * exp(-a.c2 / Ed) * a.dt_fs;
-          k = 0;
-          for (int i = 0; i < w; i += 4) {
-            const U4 r = rng_block(a.seed, kDfi, id, step, (uint32_t)(i >> 2));
-            for (int j = 0; j < 4 && i + j < w; ++j) k += u01d(r.v[j]) < P64;
-          }
-        }
-      }
-    }
-    a.nion[t] = k;
-    a.cnt[t] = k > 0 ? (1ull | (1ull << 32)) : 0ull;
+  const int64_t chunk = ev_chunk(nn);
+  const int64_t lo = (int64_t)blockIdx.x * chunk, hi = min(nn, lo + chunk);
+  int64_t run = 0;
+  uint64_t prod = 0;
+  for (int64_t base = lo; base < hi; base += 256) {
+    const int64_t t = base + threadIdx.x;
+    const int k = t < hi ? dfi_nion(a, t, step) : 0;
+    ev_stage(ev, lo, &run, &prod, t, (uint32_t)k, k > 0 ? (1ull | (1ull << 32)) : 0ull, sh);
+  }
+  if (threadIdx.x == 0) {
+    ev.hits[blockIdx.x] = (int)run;
+    ev.cnt[blockIdx.x] = prod;
   }
 }
 
-__global__ void k_dfi_products(DfiArgs a) {
+// Products: an ion with the neutral's state and an electron at rest, ion then electron id.
+__global__ void __launch_bounds__(256) k_dfi_products(DfiArgs a, EvBlocks ev) {
+  __shared__ uint64_t sh[8];
   if (!*a.go) return;
   const int64_t nn = a.clk->n[PIC_NEUTRAL], ne = a.clk->n[PIC_ELECTRON], ni = a.clk->n[PIC_ION];
   const int64_t id_base = a.clk->next_id;
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nn; t += (int64_t)gridDim.x * blockDim.x) {
-    const int k = a.nion[t];
-    if (k <= 0) continue;
-    const uint64_t off = a.off[t];
+  const int64_t lo = (int64_t)blockIdx.x * ev_chunk(nn);
+  const int nh = ev.hits[blockIdx.x];
+  uint64_t run = ev.off[blockIdx.x];
+  for (int base = 0; base < nh; base += 256) {
+    const int i = base + threadIdx.x;
+    const uint64_t pc = i < nh ? (1ull | (1ull << 32)) : 0ull;
+    uint64_t tile;
+    const uint64_t off = run + block_scan_u64(pc, &tile, sh);
+    run += tile;
+    if (i >= nh) continue;
+    const uint64_t rec = ev.rec[lo + i];
+    const int64_t t = (int64_t)(uint32_t)rec;
+    const int k = (int)(rec >> 32);
     const int64_t io = (int64_t)(off & 0xffffffffu), eo = (int64_t)(off >> 32);
     const int64_t id = id_base + io + eo;
     put_sp(a.ions, ni + io, a.n.x[t], a.n.y[t], a.n.z[t], a.n.vx[t], a.n.vy[t], a.n.vz[t], k, (uint64_t)id);
@@ -515,9 +650,19 @@ __global__ void k_dfi_products(DfiArgs a) {
   }
 }
 
-__global__ void k_set_len(int64_t *out, const DevClock *clk, int mode) {
-  // mode 0: sorted n_e + sorted n_n (MCC work items), mode 1: all neutrals
-  *out = mode == 0 ? clk->n_sorted[PIC_ELECTRON] + clk->n_sorted[PIC_NEUTRAL] : clk->n[PIC_NEUTRAL];
+// |E|^2 [V^2/m^2] below which the ADK probability per step is under 2^-27 (the rate rises with
+// E below the barrier-suppression limit): there no 24-bit draw (>= 2^-25) can fall under P, so
+// those neutrals are skipped without evaluating the rate.  FP64 bisection, rounded down.
+static float dfi_skip_E2(const DfiArgs &d, double lim) {
+  auto P = [&](double E) { const double Eg = E * 1e-9; return d.pre * pow(d.c1 / Eg, d.expo) * exp(-d.c2 / Eg) * d.dt_fs; };
+  const double target = ldexp(1.0, -27);
+  if (P(lim) <= target) return (float)(d.lim2 * (1.0 - 1e-4));
+  double lo = 1e6, hi = lim;
+  for (int it = 0; it < 200 && hi - lo > 1e-9 * hi; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    (P(mid) < target ? lo : hi) = mid;
+  }
+  return (float)(lo * lo * (1.0 - 1e-5));
 }
 
 int stage_collide(pic_t *h) {
@@ -525,23 +670,20 @@ int stage_collide(pic_t *h) {
   int *go = h->long_n + 4;
   uint64_t *total = (uint64_t *)(h->tmp_len + 2);
   const int grid = h->nsm * 8;
+  // events of the count kernels are staged per block in the MCC scratch; the grid of the count
+  // and products kernels must match
+  const EvBlocks ev{h->pair_cnt, h->ev_hits, h->ev_cnt, h->ev_off};
   if (fl & PIC_F_IMPACT_ION) {
     McArgs a;
-    a.e = h->sp[PIC_ELECTRON].a; a.n = h->sp[PIC_NEUTRAL].a;
-    a.off_e = h->sp[PIC_ELECTRON].off; a.off_n = h->sp[PIC_NEUTRAL].off;
-    a.nx = h->nx; a.ny = h->ny;
+    const Species &E = h->sp[PIC_ELECTRON], &N = h->sp[PIC_NEUTRAL];
+    a.e = E.a; a.n = N.a;
+    a.off_e = E.off; a.off_n = N.off; a.skey_e = E.skey; a.skey_n = N.skey;
     a.V_cell = h->dx * h->dx * h->dx; a.dt = h->prm.dt; a.w_min = h->prm.w_min; a.seed = h->prm.seed;
-    a.clk = h->clock; a.pair_cnt = h->pair_cnt; a.pair_off = h->pair_off; a.pair_ncoll = h->pair_ncoll; a.go = go;
-    ++h->nlaunch;
-    { KtScope kt_(h, kidMccCount, 0); k_mcc_count<<<grid, kThreads, 0, h->stream>>>(a); }
-    ++h->nlaunch;
-    k_set_len<<<1, 1, 0, h->stream>>>(h->tmp_len, h->clock, 0);
-    PIC_TRY(scan_u64(h, h->pair_cnt, h->pair_off, 0, h->tmp_len, total));
-    ++h->nlaunch;
-    k_check_new<<<1, 1, 0, h->stream>>>(h->clock, total, h->sp[PIC_ION].cap, h->sp[PIC_ELECTRON].cap, go);
-    ++h->nlaunch;
-    { KtScope kt_(h, kidMccProducts, 0); k_mcc_products<<<grid, kThreads, 0, h->stream>>>(a, h->sp[PIC_ION].a); }
-    ++h->nlaunch;
+    a.clk = h->clock; a.go = go;
+    h->nlaunch += 4;
+    { KtScope kt_(h, kidMccCount, 0); k_mcc_count<<<grid, 256, 0, h->stream>>>(a, ev); }
+    k_ev_scan<<<1, 1024, 0, h->stream>>>(ev, grid, total, h->clock, h->sp[PIC_ION].cap, E.cap, go);
+    { KtScope kt_(h, kidMccProducts, 0); k_mcc_products<<<grid, 256, 0, h->stream>>>(a, ev, h->sp[PIC_ION].a); }
     k_commit_new<<<1, 1, 0, h->stream>>>(h->clock, total, go, cImpactIon);
     PIC_TRY(launch_check(h, "mcc"));
   }
@@ -591,18 +733,12 @@ int stage_collide(pic_t *h) {
     const double lim = 1.5 * x15 * 1e9;
     d.lim2 = lim * lim;
     d.lim2f = (float)d.lim2;
-    d.dt_fs = h->prm.dt * 1e15; d.seed = h->prm.seed; d.clk = h->clock;
-    d.cnt = h->pair_cnt; d.off = h->pair_off; d.nion = h->pair_ncoll; d.go = go;
-    ++h->nlaunch;
-    { KtScope kt_(h, kidDfiCount, 0); k_dfi_count<<<grid, kThreads, 0, h->stream>>>(d); }
-    ++h->nlaunch;
-    k_set_len<<<1, 1, 0, h->stream>>>(h->tmp_len, h->clock, 1);
-    PIC_TRY(scan_u64(h, h->pair_cnt, h->pair_off, 0, h->tmp_len, total));
-    ++h->nlaunch;
-    k_check_new<<<1, 1, 0, h->stream>>>(h->clock, total, h->sp[PIC_ION].cap, h->sp[PIC_ELECTRON].cap, go);
-    ++h->nlaunch;
-    { KtScope kt_(h, kidDfiProducts, 0); k_dfi_products<<<grid, kThreads, 0, h->stream>>>(d); }
-    ++h->nlaunch;
+    d.dt_fs = h->prm.dt * 1e15; d.seed = h->prm.seed; d.clk = h->clock; d.go = go;
+    d.E2skip = dfi_skip_E2(d, lim);
+    h->nlaunch += 4;
+    { KtScope kt_(h, kidDfiCount, 0); k_dfi_count<<<grid, 256, 0, h->stream>>>(d, ev); }
+    k_ev_scan<<<1, 1024, 0, h->stream>>>(ev, grid, total, h->clock, h->sp[PIC_ION].cap, h->sp[PIC_ELECTRON].cap, go);
+    { KtScope kt_(h, kidDfiProducts, 0); k_dfi_products<<<grid, 256, 0, h->stream>>>(d, ev); }
     k_commit_new<<<1, 1, 0, h->stream>>>(h->clock, total, go, cFieldIon);
     PIC_TRY(launch_check(h, "dfi"));
   }
