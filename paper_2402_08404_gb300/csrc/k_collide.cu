@@ -43,88 +43,60 @@ struct McArgs {
   int *go;
 };
 
-// ---- block-ordered compaction of rare events ------------------------------------------------
-// A count kernel gives block b the contiguous work items [b chunk, (b + 1) chunk) and stages the
-// items with an event, in item order, at rec[b chunk ...]; a one-block scan turns the blocks'
-// product counts into offsets; the products kernel (same grid) writes each block's products in
-// item order from its offset.  Slots and ids are thus those of an exclusive scan over all
-// items in item order, without a scan over all items.
+// ---- ordered compaction of rare events ---------------------------------------------------------
+// Work items are cut into units of kEvUnit consecutive items; warps take units round-robin (so
+// dense regions spread over all warps) and stage each unit's items with an event, in item
+// order, at rec[unit kEvUnit ...].  A scan of the units' product counts gives their offsets; the
+// products kernel writes each unit's products in item order from its offset.  Slots and ids are
+// thus those of an exclusive scan over all items in item order, without a scan over all items.
+constexpr int kEvUnit = 256;
 struct EvBlocks {
   uint64_t *rec;    // staged events: item | payload << 32
-  int *hits;        // events per block
-  uint64_t *cnt;    // products per block: ions | electrons << 32
+  int *hits;        // events per unit
+  uint64_t *cnt;    // products per unit: ions | electrons << 32
   uint64_t *off;    // exclusive offsets of cnt
 };
 
-__device__ __forceinline__ int64_t ev_chunk(int64_t total) {   // items per block, a multiple of 256
-  const int64_t per = (int64_t)gridDim.x * 256;
-  return (total + per - 1) / per * 256;
+__device__ __forceinline__ int ev_warp() { return (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); }
+__device__ __forceinline__ int ev_nwarp() { return (int)((gridDim.x * blockDim.x) >> 5); }
+
+__global__ void k_ev_units(int64_t *out, const DevClock *clk, int mode) {
+  // mode 0: sorted n_e + sorted n_n (MCC work items), mode 1: all neutrals (DFI)
+  const int64_t n = mode == 0 ? clk->n_sorted[PIC_ELECTRON] + clk->n_sorted[PIC_NEUTRAL] : clk->n[PIC_NEUTRAL];
+  *out = (n + kEvUnit - 1) / kEvUnit;
 }
 
-// Exclusive prefix of v over a 256-thread block in thread order, and the block total.
-__device__ __forceinline__ uint64_t block_scan_u64(uint64_t v, uint64_t *total, uint64_t *sh) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+// capacity check + totals of a packed (ions | electrons << 32) scan
+__global__ void k_check_new(DevClock *clk, const uint64_t *total, int64_t cap_i, int64_t cap_e, int *go) {
+  const uint64_t t = *total;
+  const int64_t ni = (int64_t)(t & 0xffffffffu), ne = (int64_t)(t >> 32);
+  const bool ok = clk->n[PIC_ION] + ni <= cap_i && clk->n[PIC_ELECTRON] + ne <= cap_e;
+  *go = ok ? 1 : 0;
+  if (!ok) atomicOr(&clk->err, kErrCapacity);
+}
+
+// Exclusive prefix of v over the warp in lane order, and the warp total.
+__device__ __forceinline__ uint64_t warp_scan_u64(uint64_t v, uint64_t *total) {
+  const int lane = threadIdx.x & 31;
   uint64_t x = v;
   for (int o = 1; o < 32; o <<= 1) {
     const uint64_t y = __shfl_up_sync(0xffffffffu, x, o);
     if (lane >= o) x += y;
   }
-  if (lane == 31) sh[w] = x;
-  __syncthreads();
-  uint64_t pre = 0, tot = 0;
-  for (int i = 0; i < 8; ++i) {
-    const uint64_t q = sh[i];
-    pre += i < w ? q : 0ull;
-    tot += q;
-  }
-  __syncthreads();
-  *total = tot;
-  return pre + x - v;
+  *total = __shfl_sync(0xffffffffu, x, 31);
+  return x - v;
 }
 
-// Stage this tile's events (ev != 0) in item order and add the tile's product count pc.
+// Stage this tile's events (payload != 0) in item order and add the tile's product count pc.
 __device__ __forceinline__ void ev_stage(const EvBlocks &ev, int64_t lo, int64_t *run, uint64_t *prod, int64_t t,
-                                         uint32_t payload, uint64_t pc, uint64_t *sh) {
-  uint64_t n_tile, p_tile;
-  const uint64_t pos = block_scan_u64(payload ? 1ull : 0ull, &n_tile, sh);
-  block_scan_u64(pc, &p_tile, sh);
-  if (payload) ev.rec[lo + *run + (int64_t)pos] = (uint64_t)t | ((uint64_t)payload << 32);
-  *run += (int64_t)n_tile;
+                                         uint32_t payload, uint64_t pc) {
+  const unsigned bal = __ballot_sync(0xffffffffu, payload != 0);
+  const int lane = threadIdx.x & 31;
+  if (payload) ev.rec[lo + *run + __popc(bal & ((1u << lane) - 1u))] = (uint64_t)t | ((uint64_t)payload << 32);
+  uint64_t p_tile;
+  warp_scan_u64(pc, &p_tile);
+  *run += __popc(bal);
   *prod += p_tile;
-}
-
-// One block: exclusive scan of the blocks' product counts, the total, and the capacity check.
-__global__ void __launch_bounds__(1024) k_ev_scan(EvBlocks ev, int nblk, uint64_t *total, DevClock *clk,
-                                                  int64_t cap_i, int64_t cap_e, int *go) {
-  __shared__ uint64_t sh[32];
-  uint64_t run = 0;
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  for (int base = 0; base < nblk; base += 1024) {
-    const int b = base + threadIdx.x;
-    const uint64_t v = b < nblk ? ev.cnt[b] : 0ull;
-    uint64_t x = v;
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint64_t y = __shfl_up_sync(0xffffffffu, x, o);
-      if (lane >= o) x += y;
-    }
-    if (lane == 31) sh[w] = x;
-    __syncthreads();
-    uint64_t pre = 0, tot = 0;
-    for (int i = 0; i < 32; ++i) {
-      pre += i < w ? sh[i] : 0ull;
-      tot += sh[i];
-    }
-    if (b < nblk) ev.off[b] = run + pre + x - v;
-    run += tot;
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    *total = run;
-    const int64_t ni = (int64_t)(run & 0xffffffffu), ne = (int64_t)(run >> 32);
-    const bool ok = clk->n[PIC_ION] + ni <= cap_i && clk->n[PIC_ELECTRON] + ne <= cap_e;
-    *go = ok ? 1 : 0;
-    if (!ok) atomicOr(&clk->err, kErrCapacity);
-  }
 }
 
 // The leader of each group of lanes with the same cell draws the cell's pairing word once and
@@ -219,30 +191,31 @@ __device__ int mcc_ncoll(const McArgs &a, const Pair &pr, int64_t step) {
 
 // Work items: sorted electrons, then sorted neutrals; events staged with payload ncoll.
 __global__ void __launch_bounds__(256) k_mcc_count(McArgs a, EvBlocks ev) {
-  __shared__ uint64_t sh[8];
   const int64_t ne = a.clk->n_sorted[PIC_ELECTRON], nn = a.clk->n_sorted[PIC_NEUTRAL];
   const int64_t step = a.clk->step;
-  const int64_t total = ne + nn, chunk = ev_chunk(total);
-  const int64_t lo = (int64_t)blockIdx.x * chunk, hi = min(total, lo + chunk);
-  int64_t run = 0;
-  uint64_t prod = 0;
-  for (int64_t base = lo; base < hi; base += 256) {
-    const int64_t t = base + threadIdx.x;
-    McItem m{};
-    if (t < hi) m = mc_item(a, t, ne);
-    const uint32_t w = cell_word(a.seed, kPair, m.c, m.proj, step);
-    int ncoll = 0;
-    uint64_t pc = 0;
-    if (m.proj) {
-      const Pair pr = mc_pair(m, t, ne, w);
-      ncoll = mcc_ncoll(a, pr, step);
-      if (ncoll > 0) pc = 1ull | ((uint64_t)(ncoll < a.e.w[pr.ie] ? 2 : 1) << 32);
+  const int64_t total = ne + nn, nunit = (total + kEvUnit - 1) / kEvUnit;
+  for (int64_t unit = ev_warp(); unit < nunit; unit += ev_nwarp()) {
+    const int64_t lo = unit * kEvUnit, hi = min(total, lo + kEvUnit);
+    int64_t run = 0;
+    uint64_t prod = 0;
+    for (int64_t base = lo; base < hi; base += 32) {
+      const int64_t t = base + (threadIdx.x & 31);
+      McItem m{};
+      if (t < hi) m = mc_item(a, t, ne);
+      const uint32_t w = cell_word(a.seed, kPair, m.c, m.proj, step);
+      int ncoll = 0;
+      uint64_t pc = 0;
+      if (m.proj) {
+        const Pair pr = mc_pair(m, t, ne, w);
+        ncoll = mcc_ncoll(a, pr, step);
+        if (ncoll > 0) pc = 1ull | ((uint64_t)(ncoll < a.e.w[pr.ie] ? 2 : 1) << 32);
+      }
+      ev_stage(ev, lo, &run, &prod, t, (uint32_t)ncoll, pc);
     }
-    ev_stage(ev, lo, &run, &prod, t, (uint32_t)ncoll, pc, sh);
-  }
-  if (threadIdx.x == 0) {
-    ev.hits[blockIdx.x] = (int)run;
-    ev.cnt[blockIdx.x] = prod;
+    if ((threadIdx.x & 31) == 0) {
+      ev.hits[unit] = (int)run;
+      ev.cnt[unit] = prod;
+    }
   }
 }
 
@@ -279,63 +252,65 @@ __global__ void k_commit_new(DevClock *clk, const uint64_t *total, const int *go
   clk->ctr[ctr] += ni;
 }
 
-// Products of the staged pairs, block by block in item order from the block's offset.
+// Products of the staged pairs, warp by warp in item order from the warp's offset.
 __global__ void __launch_bounds__(256) k_mcc_products(McArgs a, EvBlocks ev, SpeciesBuf ions) {
-  __shared__ uint64_t sh[8];
   if (!*a.go) return;
   const int64_t ne = a.clk->n_sorted[PIC_ELECTRON], nn = a.clk->n_sorted[PIC_NEUTRAL];
   const int64_t ne_all = a.clk->n[PIC_ELECTRON], ni = a.clk->n[PIC_ION];
   const int64_t step = a.clk->step, id_base = a.clk->next_id;
-  const int64_t lo = (int64_t)blockIdx.x * ev_chunk(ne + nn);
-  const int nh = ev.hits[blockIdx.x];
-  uint64_t run = ev.off[blockIdx.x];
-  for (int base = 0; base < nh; base += 256) {
-    const int i = base + threadIdx.x;
-    Pair pr{};
-    int ncoll = 0;
-    uint64_t pc = 0;
-    if (i < nh) {
-      const uint64_t rec = ev.rec[lo + i];
-      const int64_t t = (int64_t)(uint32_t)rec;
-      ncoll = (int)(rec >> 32);
-      const McItem m = mc_item(a, t, ne);
-      pr = mc_pair(m, t, ne, rng_block(a.seed, kPair, m.c, step, 0).v[0]);
-      pc = 1ull | ((uint64_t)(ncoll < a.e.w[pr.ie] ? 2 : 1) << 32);
+  const int64_t nunit = (ne + nn + kEvUnit - 1) / kEvUnit;
+  for (int64_t unit = ev_warp(); unit < nunit; unit += ev_nwarp()) {
+    const int64_t lo = unit * kEvUnit;
+    const int nh = ev.hits[unit];
+    uint64_t run = ev.off[unit];
+    for (int base = 0; base < nh; base += 32) {
+      const int i = base + (threadIdx.x & 31);
+      Pair pr{};
+      int ncoll = 0;
+      uint64_t pc = 0;
+      if (i < nh) {
+        const uint64_t rec = ev.rec[lo + i];
+        const int64_t t = (int64_t)(uint32_t)rec;
+        ncoll = (int)(rec >> 32);
+        const McItem m = mc_item(a, t, ne);
+        pr = mc_pair(m, t, ne, rng_block(a.seed, kPair, m.c, step, 0).v[0]);
+        pc = 1ull | ((uint64_t)(ncoll < a.e.w[pr.ie] ? 2 : 1) << 32);
+      }
+      uint64_t tile;
+      const uint64_t off = run + warp_scan_u64(pc, &tile);
+      run += tile;
+      if (i >= nh) continue;
+      const int64_t ion_off = (int64_t)(off & 0xffffffffu), e_off = (int64_t)(off >> 32);
+      int64_t id = id_base + ion_off + e_off;
+      const int64_t in = pr.in, ie = pr.ie;
+      const uint64_t pid = pr.proj_e ? a.e.id[ie] : a.n.id[in];
+      // ion with the neutral's position and velocity
+      put_sp(ions, ni + ion_off, a.n.x[in], a.n.y[in], a.n.z[in], a.n.vx[in], a.n.vy[in], a.n.vz[in], ncoll,
+             (uint64_t)id++);
+      a.n.w[in] -= ncoll;
+      // outgoing electrons: (E0 - xi)/2 each, directions by eq:du about u = v_e - v_n
+      const double vnx = a.n.vx[in], vny = a.n.vy[in], vnz = a.n.vz[in];
+      const double ux = (double)a.e.vx[ie] - vnx, uy = (double)a.e.vy[ie] - vny, uz = (double)a.e.vz[ie] - vnz;
+      const double u2 = __dadd_rn(__dadd_rn(__dmul_rn(ux, ux), __dmul_rn(uy, uy)), __dmul_rn(uz, uz));
+      const double E0 = 0.5 * kMe * u2 / kQe;
+      const double Ek = 0.5 * (E0 - kXiCu);
+      const double uk = sqrt(2.0 * Ek * kQe / kMe);
+      const U4 r = rng_block(a.seed, kScat, pid, step, 0);
+      double v1[3], v2[3];
+      scatter_velocity(ux, uy, uz, uk, 2.0 * u01d(r.v[0]) - 1.0, 2.0 * kPi * u01d(r.v[1]), v1);
+      scatter_velocity(ux, uy, uz, uk, 2.0 * u01d(r.v[2]) - 1.0, 2.0 * kPi * u01d(r.v[3]), v2);
+      const int we = a.e.w[ie];
+      int64_t slot = ne_all + e_off;
+      if (ncoll == we) {
+        a.e.vx[ie] = (float)(vnx + v1[0]); a.e.vy[ie] = (float)(vny + v1[1]); a.e.vz[ie] = (float)(vnz + v1[2]);
+      } else {
+        a.e.w[ie] = we - ncoll;
+        put_sp(a.e, slot++, a.e.x[ie], a.e.y[ie], a.e.z[ie], (float)(vnx + v1[0]), (float)(vny + v1[1]),
+               (float)(vnz + v1[2]), ncoll, (uint64_t)id++);
+      }
+      put_sp(a.e, slot, a.n.x[in], a.n.y[in], a.n.z[in], (float)(vnx + v2[0]), (float)(vny + v2[1]), (float)(vnz + v2[2]),
+             ncoll, (uint64_t)id);
     }
-    uint64_t tile;
-    const uint64_t off = run + block_scan_u64(pc, &tile, sh);
-    run += tile;
-    if (i >= nh) continue;
-    const int64_t ion_off = (int64_t)(off & 0xffffffffu), e_off = (int64_t)(off >> 32);
-    int64_t id = id_base + ion_off + e_off;
-    const int64_t in = pr.in, ie = pr.ie;
-    const uint64_t pid = pr.proj_e ? a.e.id[ie] : a.n.id[in];
-    // ion with the neutral's position and velocity
-    put_sp(ions, ni + ion_off, a.n.x[in], a.n.y[in], a.n.z[in], a.n.vx[in], a.n.vy[in], a.n.vz[in], ncoll,
-           (uint64_t)id++);
-    a.n.w[in] -= ncoll;
-    // outgoing electrons: (E0 - xi)/2 each, directions by eq:du about u = v_e - v_n
-    const double vnx = a.n.vx[in], vny = a.n.vy[in], vnz = a.n.vz[in];
-    const double ux = (double)a.e.vx[ie] - vnx, uy = (double)a.e.vy[ie] - vny, uz = (double)a.e.vz[ie] - vnz;
-    const double u2 = __dadd_rn(__dadd_rn(__dmul_rn(ux, ux), __dmul_rn(uy, uy)), __dmul_rn(uz, uz));
-    const double E0 = 0.5 * kMe * u2 / kQe;
-    const double Ek = 0.5 * (E0 - kXiCu);
-    const double uk = sqrt(2.0 * Ek * kQe / kMe);
-    const U4 r = rng_block(a.seed, kScat, pid, step, 0);
-    double v1[3], v2[3];
-    scatter_velocity(ux, uy, uz, uk, 2.0 * u01d(r.v[0]) - 1.0, 2.0 * kPi * u01d(r.v[1]), v1);
-    scatter_velocity(ux, uy, uz, uk, 2.0 * u01d(r.v[2]) - 1.0, 2.0 * kPi * u01d(r.v[3]), v2);
-    const int we = a.e.w[ie];
-    int64_t slot = ne_all + e_off;
-    if (ncoll == we) {
-      a.e.vx[ie] = (float)(vnx + v1[0]); a.e.vy[ie] = (float)(vny + v1[1]); a.e.vz[ie] = (float)(vnz + v1[2]);
-    } else {
-      a.e.w[ie] = we - ncoll;
-      put_sp(a.e, slot++, a.e.x[ie], a.e.y[ie], a.e.z[ie], (float)(vnx + v1[0]), (float)(vny + v1[1]),
-             (float)(vnz + v1[2]), ncoll, (uint64_t)id++);
-    }
-    put_sp(a.e, slot, a.n.x[in], a.n.y[in], a.n.z[in], (float)(vnx + v2[0]), (float)(vny + v2[1]), (float)(vnz + v2[2]),
-           ncoll, (uint64_t)id);
   }
 }
 
@@ -605,48 +580,51 @@ __device__ int dfi_nion(const DfiArgs &a, int64_t t, int64_t step) {
 }
 
 __global__ void __launch_bounds__(256) k_dfi_count(DfiArgs a, EvBlocks ev) {
-  __shared__ uint64_t sh[8];
   const int64_t nn = a.clk->n[PIC_NEUTRAL];
   const int64_t step = a.clk->step;
-  const int64_t chunk = ev_chunk(nn);
-  const int64_t lo = (int64_t)blockIdx.x * chunk, hi = min(nn, lo + chunk);
-  int64_t run = 0;
-  uint64_t prod = 0;
-  for (int64_t base = lo; base < hi; base += 256) {
-    const int64_t t = base + threadIdx.x;
-    const int k = t < hi ? dfi_nion(a, t, step) : 0;
-    ev_stage(ev, lo, &run, &prod, t, (uint32_t)k, k > 0 ? (1ull | (1ull << 32)) : 0ull, sh);
-  }
-  if (threadIdx.x == 0) {
-    ev.hits[blockIdx.x] = (int)run;
-    ev.cnt[blockIdx.x] = prod;
+  const int64_t nunit = (nn + kEvUnit - 1) / kEvUnit;
+  for (int64_t unit = ev_warp(); unit < nunit; unit += ev_nwarp()) {
+    const int64_t lo = unit * kEvUnit, hi = min(nn, lo + kEvUnit);
+    int64_t run = 0;
+    uint64_t prod = 0;
+    for (int64_t base = lo; base < hi; base += 32) {
+      const int64_t t = base + (threadIdx.x & 31);
+      const int k = t < hi ? dfi_nion(a, t, step) : 0;
+      ev_stage(ev, lo, &run, &prod, t, (uint32_t)k, k > 0 ? (1ull | (1ull << 32)) : 0ull);
+    }
+    if ((threadIdx.x & 31) == 0) {
+      ev.hits[unit] = (int)run;
+      ev.cnt[unit] = prod;
+    }
   }
 }
 
 // Products: an ion with the neutral's state and an electron at rest, ion then electron id.
 __global__ void __launch_bounds__(256) k_dfi_products(DfiArgs a, EvBlocks ev) {
-  __shared__ uint64_t sh[8];
   if (!*a.go) return;
   const int64_t nn = a.clk->n[PIC_NEUTRAL], ne = a.clk->n[PIC_ELECTRON], ni = a.clk->n[PIC_ION];
   const int64_t id_base = a.clk->next_id;
-  const int64_t lo = (int64_t)blockIdx.x * ev_chunk(nn);
-  const int nh = ev.hits[blockIdx.x];
-  uint64_t run = ev.off[blockIdx.x];
-  for (int base = 0; base < nh; base += 256) {
-    const int i = base + threadIdx.x;
-    const uint64_t pc = i < nh ? (1ull | (1ull << 32)) : 0ull;
-    uint64_t tile;
-    const uint64_t off = run + block_scan_u64(pc, &tile, sh);
-    run += tile;
-    if (i >= nh) continue;
-    const uint64_t rec = ev.rec[lo + i];
-    const int64_t t = (int64_t)(uint32_t)rec;
-    const int k = (int)(rec >> 32);
-    const int64_t io = (int64_t)(off & 0xffffffffu), eo = (int64_t)(off >> 32);
-    const int64_t id = id_base + io + eo;
-    put_sp(a.ions, ni + io, a.n.x[t], a.n.y[t], a.n.z[t], a.n.vx[t], a.n.vy[t], a.n.vz[t], k, (uint64_t)id);
-    put_sp(a.e, ne + eo, a.n.x[t], a.n.y[t], a.n.z[t], 0.f, 0.f, 0.f, k, (uint64_t)(id + 1));
-    a.n.w[t] -= k;
+  const int64_t nunit = (nn + kEvUnit - 1) / kEvUnit;
+  for (int64_t unit = ev_warp(); unit < nunit; unit += ev_nwarp()) {
+    const int64_t lo = unit * kEvUnit;
+    const int nh = ev.hits[unit];
+    uint64_t run = ev.off[unit];
+    for (int base = 0; base < nh; base += 32) {
+      const int i = base + (threadIdx.x & 31);
+      const uint64_t pc = i < nh ? (1ull | (1ull << 32)) : 0ull;
+      uint64_t tile;
+      const uint64_t off = run + warp_scan_u64(pc, &tile);
+      run += tile;
+      if (i >= nh) continue;
+      const uint64_t rec = ev.rec[lo + i];
+      const int64_t t = (int64_t)(uint32_t)rec;
+      const int k = (int)(rec >> 32);
+      const int64_t io = (int64_t)(off & 0xffffffffu), eo = (int64_t)(off >> 32);
+      const int64_t id = id_base + io + eo;
+      put_sp(a.ions, ni + io, a.n.x[t], a.n.y[t], a.n.z[t], a.n.vx[t], a.n.vy[t], a.n.vz[t], k, (uint64_t)id);
+      put_sp(a.e, ne + eo, a.n.x[t], a.n.y[t], a.n.z[t], 0.f, 0.f, 0.f, k, (uint64_t)(id + 1));
+      a.n.w[t] -= k;
+    }
   }
 }
 
@@ -670,8 +648,7 @@ int stage_collide(pic_t *h) {
   int *go = h->long_n + 4;
   uint64_t *total = (uint64_t *)(h->tmp_len + 2);
   const int grid = h->nsm * 8;
-  // events of the count kernels are staged per block in the MCC scratch; the grid of the count
-  // and products kernels must match
+  // events of the count kernels are staged per unit of 256 work items in the MCC scratch
   const EvBlocks ev{h->pair_cnt, h->ev_hits, h->ev_cnt, h->ev_off};
   if (fl & PIC_F_IMPACT_ION) {
     McArgs a;
@@ -682,7 +659,9 @@ int stage_collide(pic_t *h) {
     a.clk = h->clock; a.go = go;
     h->nlaunch += 4;
     { KtScope kt_(h, kidMccCount, 0); k_mcc_count<<<grid, 256, 0, h->stream>>>(a, ev); }
-    k_ev_scan<<<1, 1024, 0, h->stream>>>(ev, grid, total, h->clock, h->sp[PIC_ION].cap, E.cap, go);
+    k_ev_units<<<1, 1, 0, h->stream>>>(h->tmp_len, h->clock, 0);
+    PIC_TRY(scan_u64(h, ev.cnt, ev.off, 0, h->tmp_len, total));
+    k_check_new<<<1, 1, 0, h->stream>>>(h->clock, total, h->sp[PIC_ION].cap, E.cap, go);
     { KtScope kt_(h, kidMccProducts, 0); k_mcc_products<<<grid, 256, 0, h->stream>>>(a, ev, h->sp[PIC_ION].a); }
     k_commit_new<<<1, 1, 0, h->stream>>>(h->clock, total, go, cImpactIon);
     PIC_TRY(launch_check(h, "mcc"));
@@ -737,7 +716,9 @@ int stage_collide(pic_t *h) {
     d.E2skip = dfi_skip_E2(d, lim);
     h->nlaunch += 4;
     { KtScope kt_(h, kidDfiCount, 0); k_dfi_count<<<grid, 256, 0, h->stream>>>(d, ev); }
-    k_ev_scan<<<1, 1024, 0, h->stream>>>(ev, grid, total, h->clock, h->sp[PIC_ION].cap, h->sp[PIC_ELECTRON].cap, go);
+    k_ev_units<<<1, 1, 0, h->stream>>>(h->tmp_len, h->clock, 1);
+    PIC_TRY(scan_u64(h, ev.cnt, ev.off, 0, h->tmp_len, total));
+    k_check_new<<<1, 1, 0, h->stream>>>(h->clock, total, h->sp[PIC_ION].cap, h->sp[PIC_ELECTRON].cap, go);
     { KtScope kt_(h, kidDfiProducts, 0); k_dfi_products<<<grid, 256, 0, h->stream>>>(d, ev); }
     k_commit_new<<<1, 1, 0, h->stream>>>(h->clock, total, go, cFieldIon);
     PIC_TRY(launch_check(h, "dfi"));

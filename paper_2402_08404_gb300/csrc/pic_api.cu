@@ -393,9 +393,9 @@ int pic_create(const pic_geometry_t *geometry, const pic_grid_t *grid, const pic
   h->pair_cnt = alloc_n<uint64_t>(h, capsum); A(h->pair_cnt);
   h->pair_off = alloc_n<uint64_t>(h, capsum); A(h->pair_off);
   h->pair_ncoll = alloc_n<int32_t>(h, capsum); A(h->pair_ncoll);
-  h->ev_hits = alloc_n<int>(h, 8 * h->nsm); A(h->ev_hits);
-  h->ev_cnt = alloc_n<uint64_t>(h, 8 * h->nsm); A(h->ev_cnt);
-  h->ev_off = alloc_n<uint64_t>(h, 8 * h->nsm); A(h->ev_off);
+  h->ev_hits = alloc_n<int>(h, capsum / 256 + 2); A(h->ev_hits);
+  h->ev_cnt = alloc_n<uint64_t>(h, capsum / 256 + 2); A(h->ev_cnt);
+  h->ev_off = alloc_n<uint64_t>(h, capsum / 256 + 2); A(h->ev_off);
   // faces
   Faces &fc = h->faces;
   fc.n = (int64_t)G.fvcell.size();

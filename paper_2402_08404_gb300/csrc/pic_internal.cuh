@@ -173,7 +173,7 @@ struct pic_s {
   double *coarse_inv_d = nullptr;
   int32_t *coarse_slot = nullptr;   // split-layout slot of each free node
   int tail_start = -1;              // first level of the cluster-launched V-cycle tail (-1: none)
-  int *ev_hits = nullptr;             // collision events staged per block (count kernels' grid)
+  int *ev_hits = nullptr;             // collision events staged per unit of 256 work items
   uint64_t *ev_cnt = nullptr, *ev_off = nullptr;
   double sigma_el_en = 0, sigma_el_nn = 0, sigma_cx = 0;   // m^2 (elastic and exchange passes)
   int mg_sweeps = 3;                // red-black sweeps before and after each coarse correction
