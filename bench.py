@@ -205,10 +205,13 @@ def run_ours(args):
         prod_flags |= pic.F_CIRCUIT
     if args.elastic:   # elastic e-Cu, Cu-Cu and Cu+-Cu charge exchange with the stand-in cross sections
         prod_flags |= pic.F_ELASTIC
+    if args.extrapolate:   # each step's solve starts from 2 phi^n - phi^(n-1)
+        prod_flags |= pic.F_EXTRAPOLATE
     plain_flags = pic.F_ALL & ~pic.F_SURROGATE & ~pic.F_MIXED_MG
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
-        sim = pic.Pic(cfg, capacity=cap, flags=prod_flags, mg_tol=args.mg_tol, mg_max_cycles=60, stream=stream)
+        sim = pic.Pic(cfg, capacity=cap, flags=prod_flags, mg_tol=args.mg_tol, mg_max_cycles=60, stream=stream,
+                      mg_sweeps=args.mg_sweeps)
         for s, k in enumerate("eni"):
             sim.load_particles(s, pop[k])
         sim.set_clock(0, n_sp)
@@ -344,6 +347,7 @@ def run_ours(args):
                    "elastic": ({"e_Cu": d1["elastic_en"], "Cu_Cu": d1["elastic_nn"], "exchange": d1["charge_exchanges"]}
                                if args.elastic else None),
                    "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()}, "mg_cycles": d1["mg_cycles"],
+                   "mg_cycles_per_step": (d1["mg_cycles_total"] - d0["mg_cycles_total"]) / args.steps,
                    "kernel_ms_per_step": kernel_ms,
                    "surrogate": None if sur is None else {
                        "val_rms_dlog10J": round(sur["val_rms_dlog10J"], 4),
@@ -524,12 +528,14 @@ def main():
     ap.add_argument("--sur-samples", type=int, default=2_000_000)
     ap.add_argument("--sur-epochs", type=int, default=150)
     ap.add_argument("--mg-tol", type=float, default=1e-6)
+    ap.add_argument("--mg-sweeps", type=int, default=0, help="red-black sweeps per V-cycle side (0: library default)")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-sample", type=int, default=60000)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false")
     ap.add_argument("--circuit", action="store_true", help="step with the RC circuit and Shockley-Ramo current")
     ap.add_argument("--elastic", action="store_true", help="step with elastic collisions and charge exchange")
+    ap.add_argument("--extrapolate", action="store_true", help="start each solve from the time-extrapolated potential")
     args = ap.parse_args()
     if args.impl == "reference":
         out = run_reference(args)

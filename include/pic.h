@@ -61,6 +61,7 @@ extern "C" {
 #define PIC_F_MIXED_MG 0x80u    /* a8: FP32 V-cycles with FP64 residual refinement (else FP64 V-cycles) */
 #define PIC_F_FAST_INTEGRAL 0x100u  /* a1: Gamow quadrature and turning points in FP32 (J, P_N to ~1e-5
                                        relative) in the step and in pic_emission_eval; else all FP64 */
+#define PIC_F_EXTRAPOLATE 0x1000u /* pic_step starts each solve from 2 phi^n - phi^(n-1) instead of phi^n */
 #define PIC_F_ELASTIC 0x800u    /* a5: then elastic e-Cu and Cu-Cu collisions and Cu+-Cu charge exchange */
 #define PIC_F_CIRCUIT 0x400u    /* the RC circuit drives the anode (needs circuit_R, circuit_C > 0 at create) */
 #define PIC_F_GRAPH 0x200u      /* pic_step replays a CUDA graph of one step (the Poisson loop a device-side
@@ -127,6 +128,7 @@ typedef struct {
   double V_gap;             /* V: gap voltage (V0 without a circuit) */
   double I_gap, I_tot;      /* A: Shockley-Ramo gap current and circuit current of the last circuit stage */
   int64_t elastic_en, elastic_nn, charge_exchanges;  /* colliding pairs this step (PIC_F_ELASTIC) */
+  int64_t mg_cycles_total;  /* Poisson refinement cycles since create (both forms) */
 } pic_diag_t;
 
 typedef struct pic_s pic_t;

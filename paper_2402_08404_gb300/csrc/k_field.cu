@@ -1190,7 +1190,10 @@ int stage_solve(pic_t *h, bool zero_charge, double V0) {
     h->last_mg_res = rel;
     h->last_mg_cycles = cyc;
     h->last_solve_graph = false;
-    if (rel <= h->prm.mg_tol) break;
+    if (rel <= h->prm.mg_tol) {
+      h->mg_cycles_host += cyc;
+      break;
+    }
     if (cyc >= h->prm.mg_max_cycles) {
       PIC_TRY(stage_efield(h));
       return pic_fail(h, PIC_E_NOCONV, "Poisson solve: relative residual " + std::to_string(rel) + " after " +
@@ -1200,6 +1203,35 @@ int stage_solve(pic_t *h, bool zero_charge, double V0) {
     else cycle_fine<double>(h);
   }
   return stage_efield(h);
+}
+
+// Initial guess of a step's solve: phi <- 2 phi^n - phi^(n-1), exact in the fixed point (every
+// |phi| < 2^53), and phi^(n-1) <- phi^n.  Without a previous potential it only records phi^n.
+// Dirichlet values are unchanged by the extrapolation (the anode under a circuit is rewritten
+// by the solve's set-up).
+__global__ void k_extrapolate(long long *phi, long long *phi_prev, int64_t n, const DevClock *clk) {
+  const bool ok = clk->phi_prev_ok != 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const long long p = phi[i];
+    if (ok) phi[i] = 2 * p - phi_prev[i];
+    phi_prev[i] = p;
+  }
+}
+
+__global__ void k_set_prev_ok(DevClock *clk) { clk->phi_prev_ok = 1; }
+
+int stage_extrapolate(pic_t *h) {
+  if (!(h->prm.flags & PIC_F_EXTRAPOLATE)) return PIC_OK;
+  if (!h->phi_prev) {
+    if (h->capturing) return pic_fail(h, PIC_E_INVALID, "extrapolation buffer must exist before graph capture");
+    h->phi_prev = (long long *)dalloc(h, (size_t)h->nnode * sizeof(long long));
+    if (!h->phi_prev) return pic_fail(h, PIC_E_CUDA, "phi_prev allocation failed");
+    PIC_CUDA(h, cudaMemsetAsync(&h->clock->phi_prev_ok, 0, sizeof(int), h->stream));
+  }
+  h->nlaunch += 2;
+  k_extrapolate<<<h->nsm * 8, kThreads, 0, h->stream>>>(h->phi, h->phi_prev, h->nnode, h->clock);
+  k_set_prev_ok<<<1, 1, 0, h->stream>>>(h->clock);
+  return launch_check(h, "extrapolate");
 }
 
 bool circuit_on(pic_t *h) { return h->E0 != nullptr && h->circuit_ready && (h->prm.flags & PIC_F_CIRCUIT) != 0; }

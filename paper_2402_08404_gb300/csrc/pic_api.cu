@@ -605,6 +605,7 @@ int pic_set_potential(pic_t *h, const double *phi) {
     ++h->nlaunch;
     k_phi_from_double<<<grid_for(h->nnode), kThreads, 0, h->stream>>>(buf, h->phi, h->nnode);
     h->dirichlet_valid = false;
+    if (cudaMemsetAsync(&h->clock->phi_prev_ok, 0, sizeof(int), h->stream) != cudaSuccess) rc = PIC_E_CUDA;
     graph_free(h);
     rc = stage_efield(h);
   }
@@ -729,6 +730,9 @@ int pic_sort(pic_t *h);
 
 int pic_set_flags(pic_t *h, uint32_t flags) {
   if (!h) return PIC_E_INVALID;
+  // switching the extrapolation on: the stored previous potential may be many steps old
+  if ((flags & PIC_F_EXTRAPOLATE) && !(h->prm.flags & PIC_F_EXTRAPOLATE) && h->phi_prev)
+    PIC_CUDA(h, cudaMemsetAsync(&h->clock->phi_prev_ok, 0, sizeof(int), h->stream));
   h->prm.flags = flags;
   graph_free(h);
   return PIC_OK;
@@ -836,6 +840,7 @@ static int step_body_graph(pic_t *h) {
   PIC_TRY(stage_sort(h));
   PIC_TRY(stage_collide(h));
   PIC_TRY(stage_deposit(h));
+  PIC_TRY(stage_extrapolate(h));
   PIC_TRY(stage_solve_graph(h, h->V0));
   ++h->nlaunch;
   k_end_step<<<1, 1, 0, h->stream>>>(h->clock);
@@ -1238,6 +1243,7 @@ static int pic_step_eager(pic_t *h, int nsteps, int64_t step) {
     cudaEventRecord(ev[4], h->stream);
     if (rc == PIC_OK) rc = stage_deposit(h);
     cudaEventRecord(ev[5], h->stream);
+    if (rc == PIC_OK) rc = stage_extrapolate(h);
     if (rc == PIC_OK) rc = stage_solve(h, false, h->V0);
     cudaEventRecord(ev[6], h->stream);
     ++step;
@@ -1340,6 +1346,7 @@ int pic_diagnostics(pic_t *h, pic_diag_t *out) {
   }
   for (int i = 0; i < 8; ++i) out->ms[i] = h->ms[i];
   out->kernel_launches = h->nlaunch + c.mg_graph_cycles * h->graph_body_launches;
+  out->mg_cycles_total = h->mg_cycles_host + c.mg_graph_cycles;
   out->emission_evals = c.ctr[cWevals];
   out->V_gap = h->E0 ? c.V_gap : h->V0;
   out->I_gap = c.I_gap;

@@ -70,6 +70,7 @@ struct DevClock {
   int64_t n_new[3];      // scratch: SPs created by the current pass
   int64_t ctr[cNum];
   int err;
+  int phi_prev_ok;       // phi_prev holds the previous step's potential (time extrapolation)
   // graph form of the Poisson loop (device-side convergence test)
   int mg_cycles_last;       // cycles of the last solve
   float mg_rel_last;        // its relative residual
@@ -161,6 +162,7 @@ struct pic_s {
   bool dirichlet_valid = false;  // phi holds the Dirichlet values of dirichlet_V0fx on the mask
   long long dirichlet_V0fx = 0;
   float4 *E = nullptr;           // per node
+  long long *phi_prev = nullptr;  // per node: potential of the previous step (PIC_F_EXTRAPOLATE)
   float4 *E0 = nullptr;          // per node: unit Laplace field [1/m] (circuit; null without one)
   double *ramo_part = nullptr;   // Shockley-Ramo partial sums
   unsigned long long *Q = nullptr;  // per node, int64 two's complement charge
@@ -194,6 +196,7 @@ struct pic_s {
   // state flags and last diagnostics
   bool keys_valid[3] = {false, false, false};
   int last_mg_cycles = 0;
+  int64_t mg_cycles_host = 0;       // refinement cycles of host-driven solves since create
   double last_mg_res = 0;
   float ms[8] = {0};
   int64_t solid_count = 0;
@@ -362,6 +365,7 @@ bool circuit_on(pic_t *h);
 int circuit_setup(pic_t *h, double V_L);
 int circuit_reset(pic_t *h);
 int stage_circuit(pic_t *h);
+int stage_extrapolate(pic_t *h);
 // heat (k_heat.cu)
 int stage_heat(pic_t *h);
 // emission surrogate (k_mlp.cu)

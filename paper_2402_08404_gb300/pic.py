@@ -20,6 +20,7 @@ F_FAST_INTEGRAL = 0x100
 F_GRAPH = 0x200
 F_CIRCUIT = 0x400
 F_ELASTIC = 0x800
+F_EXTRAPOLATE = 0x1000
 F_PRODUCTION = F_ALL | F_FAST_INTEGRAL     # surrogate, FP32 Gamow quadrature for its fallback, mixed MG
 
 QE = 1.602176634e-19
@@ -64,7 +65,7 @@ class Diag(C.Structure):
                 ("ms", C.c_double * 8), ("kernel_launches", C.c_int64), ("emission_evals", C.c_int64),
                 ("surrogate_faces", C.c_int64), ("V_gap", C.c_double), ("I_gap", C.c_double),
                 ("I_tot", C.c_double), ("elastic_en", C.c_int64), ("elastic_nn", C.c_int64),
-                ("charge_exchanges", C.c_int64)]
+                ("charge_exchanges", C.c_int64), ("mg_cycles_total", C.c_int64)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
