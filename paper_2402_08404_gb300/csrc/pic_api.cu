@@ -245,6 +245,7 @@ void pic_destroy(pic_t *h) {
   if (!h) return;
   cudaStreamSynchronize(h->stream);
   for (cudaEvent_t e : h->kt_ev) cudaEventDestroy(e);
+  for (cudaEvent_t e : h->step_ev) cudaEventDestroy(e);
   graph_free(h);
   if (h->body_stream) cudaStreamDestroy(h->body_stream);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
@@ -1224,11 +1225,18 @@ int pic_step(pic_t *h, int nsteps) {
 
 // the step stage by stage from the host, with per-stage event timing
 static int pic_step_eager(pic_t *h, int nsteps, int64_t step) {
-  cudaEvent_t ev[8];
-  for (int i = 0; i < 8; ++i) cudaEventCreate(&ev[i]);
-  float acc_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  // eight events per step, read once after the last step: no host wait between steps beyond
+  // the solve's own convergence checks
+  const size_t need = (size_t)8 * std::max(nsteps, 0);
+  while (h->step_ev.size() < need) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return pic_fail(h, PIC_E_CUDA, "event creation failed");
+    h->step_ev.push_back(e);
+  }
   int rc = PIC_OK;
+  int done = 0;
   for (int it = 0; it < nsteps && rc == PIC_OK; ++it) {
+    cudaEvent_t *ev = h->step_ev.data() + 8 * it;
     cudaEventRecord(ev[0], h->stream);
     ++h->nlaunch;
     k_begin_step<<<1, 1, 0, h->stream>>>(h->clock);
@@ -1254,9 +1262,14 @@ static int pic_step_eager(pic_t *h, int nsteps, int64_t step) {
     ++h->nlaunch;
     k_end_step<<<1, 1, 0, h->stream>>>(h->clock);
     cudaEventRecord(ev[7], h->stream);
-    // per-stage times summed over the steps of this call (events on the library stream)
-    cudaEventSynchronize(ev[7]);
-    kt_collect(h);
+    ++done;
+  }
+  // per-stage times summed over the steps of this call (events on the library stream)
+  float acc_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  if (done > 0) cudaEventSynchronize(h->step_ev[8 * (done - 1) + 7]);
+  kt_collect(h);
+  for (int it = 0; it < done; ++it) {
+    cudaEvent_t *ev = h->step_ev.data() + 8 * it;
     float t;
     for (int i = 0; i < 7; ++i) {
       cudaEventElapsedTime(&t, ev[i], ev[i + 1]);
@@ -1267,7 +1280,6 @@ static int pic_step_eager(pic_t *h, int nsteps, int64_t step) {
   }
   if (rc == PIC_OK && nsteps > 0)
     for (int i = 0; i < 8; ++i) h->ms[i] = acc_ms[i];
-  for (int i = 0; i < 8; ++i) cudaEventDestroy(ev[i]);
   if (rc != PIC_OK) return rc;
   PIC_TRY(launch_check(h, "step"));
   PIC_TRY(check_err(h));

@@ -219,6 +219,7 @@ struct pic_s {
   // kernel timing (diagnostics): launches of the kernels in kt_mask are bracketed by event pairs
   uint64_t kt_mask = 0;
   std::vector<cudaEvent_t> kt_ev;                   // 2 per recorded launch, reused
+  std::vector<cudaEvent_t> step_ev;                 // 8 per step of an eager pic_step call, reused
   std::vector<std::pair<int, double>> kt_pend;      // (kernel, units) per recorded launch
   double kt_ms[64] = {0}, kt_units[64] = {0};
   int64_t kt_n[64] = {0};
