@@ -261,17 +261,20 @@ def step(st, emission_fn=None):
     ids = collide.Counter(st.next_id)
     ni, ne, ev = collide.impact_ionization(g, prm, st.sp[E_], st.off[E_], st.sp[N_], st.off[N_], st.step, ids)
     st.count["impact_ionizations"] = ev
+    el_e, el_i = P.empty(), P.empty()
     if prm.get("elastic"):
-        st.count["elastic_en"] = elastic.elastic_en(g, prm, st.sp[E_], st.off[E_], st.sp[N_], st.off[N_], st.step)
-        st.count["elastic_nn"] = elastic.elastic_nn(g, prm, st.sp[N_], st.off[N_], st.step)
-        st.count["charge_exchanges"] = elastic.charge_exchange(g, prm, st.sp[I_], st.off[I_], st.sp[N_], st.off[N_],
-                                                               st.step)
+        el_e, el_n1, st.count["elastic_en"] = elastic.elastic_en(g, prm, st.sp[E_], st.off[E_], st.sp[N_], st.off[N_],
+                                                                 st.step, ids)
+        el_n2, st.count["elastic_nn"] = elastic.elastic_nn(g, prm, st.sp[N_], st.off[N_], st.step, ids)
+        el_i, el_n3, st.count["charge_exchanges"] = elastic.charge_exchange(g, prm, st.sp[I_], st.off[I_], st.sp[N_],
+                                                                            st.off[N_], st.step, ids)
+        st.sp[N_] = P.concat(P.concat(P.concat(st.sp[N_], el_n1), el_n2), el_n3)
     # a6
     ni2, ne2, ev2 = collide.field_ionization(g, prm, st.sp[N_], st.E, st.step, ids)
     st.count["field_ionizations"] = ev2
     st.next_id = ids.next_id
-    st.sp[I_] = P.concat(P.concat(st.sp[I_], ni), ni2)
-    st.sp[E_] = P.concat(P.concat(st.sp[E_], ne), ne2)
+    st.sp[I_] = P.concat(P.concat(P.concat(st.sp[I_], ni), el_i), ni2)
+    st.sp[E_] = P.concat(P.concat(P.concat(st.sp[E_], ne), el_e), ne2)
     # a7-a9
     solve_field(st)
     # a10

@@ -61,8 +61,9 @@ __device__ __forceinline__ int ev_warp() { return (int)((blockIdx.x * blockDim.x
 __device__ __forceinline__ int ev_nwarp() { return (int)((gridDim.x * blockDim.x) >> 5); }
 
 __global__ void k_ev_units(int64_t *out, const DevClock *clk, int mode) {
-  // mode 0: sorted n_e + sorted n_n (MCC work items), mode 1: all neutrals (DFI)
-  const int64_t n = mode == 0 ? clk->n_sorted[PIC_ELECTRON] + clk->n_sorted[PIC_NEUTRAL] : clk->n[PIC_NEUTRAL];
+  // mode 0: sorted n_e + sorted n_n (MCC work items), 1: all neutrals (DFI), 2 + s: sorted n_s
+  const int64_t n = mode == 0 ? clk->n_sorted[PIC_ELECTRON] + clk->n_sorted[PIC_NEUTRAL]
+                    : mode == 1 ? clk->n[PIC_NEUTRAL] : clk->n_sorted[mode - 2];
   *out = (n + kEvUnit - 1) / kEvUnit;
 }
 
@@ -316,34 +317,32 @@ __global__ void __launch_bounds__(256) k_mcc_products(McArgs a, EvBlocks ev, Spe
 
 // ---- elastic collisions and charge exchange ---------------------------------------------------
 // e + Cu -> e + Cu and Cu + Cu -> Cu + Cu (eq:newv with the velocity difference of eq:du) and
-// Cu+ + Cu -> Cu + Cu+ (the electron hops: the SPs swap velocities), on the cell-sorted SPs of
-// the step.  Whole SPs collide, one draw per pair: U_c < P, P = 1 - exp(-u n_t W_t sigma dt)
-// (eq:colp, the projectile view of impact ionization), decided in FP32 and re-decided in FP64
-// when U_c is within 2^-12 P of the FP32 value, so every decision equals the FP64 one.  The SP
-// with the smaller weight always takes its new velocity, the other with probability
-// w_small / w_large (tested in integers on the 24-bit draw).  Pairs are disjoint, so one thread
-// per projectile updates both SPs without atomics.
+// Cu+ + Cu -> Cu + Cu+ (the colliding sub-particles swap velocities), on the cell-sorted SPs of
+// the step, with the splitting of Sec. 2.3.2: each of the projectile's w_p sub-particles collides
+// iff U_i < P (eq:colp with the paired target's weight), N_coll is capped at the target weight,
+// and the N_coll colliding sub-particles of each side leave their SP as a new SP with the
+// post-collision velocity (the whole SP turns when N_coll is its weight).  The draws are decided
+// in FP32 and re-decided in FP64 when one lies within the guard band of P, as for impact
+// ionization.  Events are staged per unit of work items and their new SPs placed in item order,
+// so ids and slots are deterministic: events of a pass in the order of the pair's member in the
+// pass's first species (e-, Cu+, or the projectile for Cu-Cu), per event the projectile's new SP
+// first.
 struct ElArgs {
   double V_cell, dt, w_min;
   uint64_t seed;
   DevClock *clk;
+  int *go;
 };
 
 struct ElPass {
-  SpeciesBuf A, B;                          // like-species pass: A only
+  SpeciesBuf A, B;                          // like-species pass: A only (B = A)
   const uint32_t *off_a, *off_b;            // per-cell offsets of the last sort
   const uint32_t *skey_a, *skey_b;          // cell of each sorted position
-  int sa, sb;                               // species indices (sorted counts on the device clock)
+  int sa, sb;                               // species indices; like-species pass: sb = sa
   double m_a, m_b, sigma;
-  uint32_t pair_purpose, draw_purpose;
-  int exchange, ctr;
+  uint32_t pair_purpose, draw_purpose, scat_purpose;
+  int exchange, like, ctr;
   float nWsd1;                              // w_min sigma dt / V_cell in FP32 (screening only)
-};
-
-struct ElQueue {
-  uint64_t *pair;    // projectile-side index | target-side index << 32 (A index low when A projects)
-  uint32_t *info;    // Nt | projectile in B << 30 | FP64 decision needed << 31
-  int *n, cap;
 };
 
 __device__ __forceinline__ double rn3(double a0, double b0, double a1, double b1, double a2, double b2) {
@@ -375,150 +374,225 @@ __device__ void delta_u(double ux, double uy, double uz, double cos_tp, double p
   rot_inv(th, ph, t, du);
 }
 
-// Pass kernels.  A decision kernel runs one work item per sorted SP of one species and only
-// the FP32 test (Philox draws, P in FP32); a pair that collides, or whose draw lies within the
-// guard band of P, goes to a queue.  The apply kernel then takes each queued pair: the FP64
-// decision where the band asked for it, the new velocities, the weight rule.  Pairs of a pass
-// are disjoint, so deferring the updates changes nothing, and the queue order does not matter.
+// The pair of work item t of a pass (t a sorted SP of species A; for the like pass the
+// projectile of its pair).  false if t has no pair.  For an inter-species pass with Na <= Nb
+// (ties: A) the SP at place k is the projectile of target (k + o) mod Nb; otherwise it is the
+// target of projectile j = (k - o) mod Na of B when j < Nb.  Like pass: places (o + 2m,
+// o + 2m + 1) mod N form pair m, the first the projectile.
+struct ElPair {
+  int64_t ip, it;   // projectile and target index in their species
+  bool proj_b;      // projectile in species B
+  uint32_t Nt;
+};
 
-// FP32 test of one pair (A[ia] the projectile): 0 no collision, 1 collision, 2 within the band
-__device__ __forceinline__ int el_decide(const ElArgs &a, const SpeciesBuf &A, int64_t ia, const SpeciesBuf &B,
-                                         int64_t ib, uint32_t Nt, const ElPass &ps, int64_t step) {
-  const int32_t wa = A.w[ia], wb = B.w[ib];
-  if (wa <= 0 || wb <= 0) return 0;
-  const float fx = A.vx[ia] - B.vx[ib], fy = A.vy[ia] - B.vy[ib], fz = A.vz[ia] - B.vz[ib];
-  const float x32 = sqrtf(fx * fx + fy * fy + fz * fz) * ((float)Nt * (float)wb * ps.nWsd1);
+struct ElItem {
+  uint32_t c, oa, Na, ob, Nb;
+  bool need;
+};
+
+__device__ __forceinline__ ElItem el_item(const ElPass &ps, int64_t t, int64_t hi) {
+  ElItem m{};
+  if (t >= hi) return m;
+  m.c = ps.skey_a[t];
+  m.oa = ps.off_a[m.c]; m.Na = ps.off_a[m.c + 1] - m.oa;
+  if (ps.like) {
+    m.need = m.Na >= 2;
+  } else {
+    m.ob = ps.off_b[m.c]; m.Nb = ps.off_b[m.c + 1] - m.ob;
+    m.need = m.Nb > 0;
+  }
+  return m;
+}
+
+__device__ __forceinline__ bool el_pair_of(const ElPass &ps, const ElItem &m, int64_t t, uint32_t w, ElPair *pr) {
+  if (!m.need) return false;
+  const uint32_t k = (uint32_t)(t - m.oa);
+  if (ps.like) {
+    const uint32_t q = (k + m.Na - u_index(w, m.Na)) % m.Na;   // shuffled place of this SP
+    if ((q & 1u) || q + 1 >= m.Na) return false;
+    pr->ip = t; pr->it = (int64_t)m.oa + (k + 1) % m.Na; pr->proj_b = false; pr->Nt = m.Na;
+    return true;
+  }
+  if (m.Na <= m.Nb) {
+    pr->ip = t; pr->it = (int64_t)m.ob + (k + u_index(w, m.Nb)) % m.Nb; pr->proj_b = false; pr->Nt = m.Nb;
+    return true;
+  }
+  const uint32_t j = (k + m.Na - u_index(w, m.Na)) % m.Na;
+  if (j >= m.Nb) return false;
+  pr->ip = (int64_t)m.ob + j; pr->it = t; pr->proj_b = true; pr->Nt = m.Na;
+  return true;
+}
+
+// Colliding sub-particles of a pair: #{i < w_p : U_i < P}, capped at w_t.
+__device__ int el_ncoll(const ElArgs &a, const ElPass &ps, const ElPair &pr, int64_t step) {
+  const SpeciesBuf &A = pr.proj_b ? ps.B : ps.A;
+  const SpeciesBuf &B = pr.proj_b ? ps.A : ps.B;
+  const int32_t wp = A.w[pr.ip], wt = B.w[pr.it];
+  if (wp <= 0 || wt <= 0) return 0;
+  const float ax = A.vx[pr.ip], ay = A.vy[pr.ip], az = A.vz[pr.ip];
+  const float bx = B.vx[pr.it], by = B.vy[pr.it], bz = B.vz[pr.it];
+  const float fx = ax - bx, fy = ay - by, fz = az - bz;
+  const float x32 = sqrtf(fx * fx + fy * fy + fz * fz) * ((float)pr.Nt * (float)wt * ps.nWsd1);
   const float P32 = -expm1f(-x32);
-  const float U = u01f(rng_block(a.seed, ps.draw_purpose, A.id[ia], step, 0).v[0]);
-  if (fabsf(U - P32) <= ldexpf(P32, -12)) return 2;
-  return U < P32 ? 1 : 0;
-}
-
-__device__ __forceinline__ void el_push(const ElQueue &q, int64_t ia, int64_t ib, uint32_t Nt, bool proj_b, int d) {
-  const int slot = atomicAdd(q.n, 1);
-  if (slot >= q.cap) return;   // cannot happen: a pass has fewer pairs than the queue holds
-  q.pair[slot] = (uint64_t)(uint32_t)ia | ((uint64_t)(uint32_t)ib << 32);
-  q.info[slot] = Nt | (proj_b ? 1u << 30 : 0u) | (d == 2 ? 1u << 31 : 0u);
-}
-
-// Inter-species pass, one item per sorted SP of species A (each pair has exactly one member in
-// A): with Na <= Nb (ties: A) the SP at place k is the projectile of target (k + o) mod Nb;
-// otherwise it is the target of projectile j = (k - o) mod Na of B when j < Nb.
-__global__ void __launch_bounds__(256) k_el_decide_inter(ElArgs a, ElPass ps, ElQueue q) {
-  const int64_t na = a.clk->n_sorted[ps.sa];
-  const int64_t step = a.clk->step;
-  const int64_t span = (na + 31) & ~31ll;   // whole warps: the cell-word exchange needs every lane
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < span; t += (int64_t)gridDim.x * blockDim.x) {
-    uint32_t c = 0, oa = 0, Na = 0, ob = 0, Nb = 0;
-    if (t < na) {
-      c = ps.skey_a[t];
-      oa = ps.off_a[c]; Na = ps.off_a[c + 1] - oa;
-      ob = ps.off_b[c]; Nb = ps.off_b[c + 1] - ob;
-    }
-    const bool need = t < na && Nb > 0;
-    const uint32_t w = cell_word(a.seed, ps.pair_purpose, c, need, step);
-    if (!need) continue;
-    const uint32_t k = (uint32_t)(t - oa);
-    if (Na <= Nb) {
-      const uint32_t o = u_index(w, Nb);
-      const int64_t ib = (int64_t)ob + (k + o) % Nb;
-      const int d = el_decide(a, ps.A, t, ps.B, ib, Nb, ps, step);
-      if (d) el_push(q, t, ib, Nb, false, d);
-    } else {
-      const uint32_t o = u_index(w, Na);
-      const uint32_t j = (k + Na - o) % Na;
-      if (j >= Nb) continue;
-      const int64_t ib = (int64_t)ob + j;
-      const int d = el_decide(a, ps.B, ib, ps.A, t, Na, ps, step);
-      if (d) el_push(q, t, ib, Na, true, d);
+  const float band = ldexpf(P32, -12);
+  const uint64_t pid = A.id[pr.ip];
+  int n = 0;
+  bool exact = false;
+  for (int i = 0; i < wp && P32 + band >= kUmin; i += 4) {
+    const U4 r = rng_block(a.seed, ps.draw_purpose, pid, step, (uint32_t)(i >> 2));
+    for (int j = 0; j < 4 && i + j < wp; ++j) {
+      const float U = u01f(r.v[j]);
+      if (fabsf(U - P32) <= band) exact = true;
+      n += U < P32;
     }
   }
-}
-
-// Like-species pass (Cu-Cu): places (o + 2m, o + 2m + 1) mod N of each cell form pair m; the
-// first one is the projectile.
-__global__ void __launch_bounds__(256) k_el_decide_like(ElArgs a, ElPass ps, ElQueue q) {
-  const int64_t n = a.clk->n_sorted[ps.sa];
-  const int64_t step = a.clk->step;
-  const int64_t span = (n + 31) & ~31ll;
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < span; t += (int64_t)gridDim.x * blockDim.x) {
-    uint32_t c = 0, o0 = 0, N = 0;
-    if (t < n) {
-      c = ps.skey_a[t];
-      o0 = ps.off_a[c]; N = ps.off_a[c + 1] - o0;
+  if (exact) {   // the FP64 definition, in the oracle's order of operations
+    const double dx = (double)ax - (double)bx, dy = (double)ay - (double)by, dz = (double)az - (double)bz;
+    const double u = sqrt(rn3(dx, dx, dy, dy, dz, dz));
+    const double P = -expm1(-(u * ((double)pr.Nt / a.V_cell) * ((double)wt * a.w_min) * ps.sigma * a.dt));
+    n = 0;
+    for (int i = 0; i < wp; i += 4) {
+      const U4 r = rng_block(a.seed, ps.draw_purpose, pid, step, (uint32_t)(i >> 2));
+      for (int j = 0; j < 4 && i + j < wp; ++j) n += u01d(r.v[j]) < P;
     }
-    const bool need = t < n && N >= 2;
-    const uint32_t w = cell_word(a.seed, ps.pair_purpose, c, need, step);
-    if (!need) continue;
-    const uint32_t k = (uint32_t)(t - o0);
-    const uint32_t qq = (k + N - u_index(w, N)) % N;   // shuffled place of this SP
-    if ((qq & 1u) || qq + 1 >= N) continue;
-    const int64_t ib = (int64_t)o0 + (k + 1) % N;
-    const int d = el_decide(a, ps.A, t, ps.A, ib, N, ps, step);
-    if (d) el_push(q, t, ib, N, false, d);
   }
+  return n < wt ? n : wt;
 }
 
-// Queued pairs: the FP64 decision where asked (the definition, in the oracle's order of
-// operations), then eq:newv (or the exchange) and the weight rule.
-__global__ void __launch_bounds__(256) k_el_apply(ElArgs a, ElPass ps, ElQueue q) {
-  const int nq = min(*q.n, q.cap);
+// New SPs of an event, packed per species of the pass: (in A) | (in B) << 32; the like pass
+// counts both in the low half.
+__device__ __forceinline__ uint64_t el_products(const ElPass &ps, const ElPair &pr, int n) {
+  const SpeciesBuf &A = pr.proj_b ? ps.B : ps.A;
+  const SpeciesBuf &B = pr.proj_b ? ps.A : ps.B;
+  const uint64_t p_new = n < A.w[pr.ip] ? 1u : 0u, t_new = n < B.w[pr.it] ? 1u : 0u;
+  if (ps.like) return p_new + t_new;
+  const uint64_t in_a = pr.proj_b ? t_new : p_new, in_b = pr.proj_b ? p_new : t_new;
+  return in_a | (in_b << 32);
+}
+
+// Work items: the sorted SPs of species A of the pass, in units of kEvUnit taken round-robin
+// by warps; events staged with payload N_coll.
+__global__ void __launch_bounds__(256) k_el_count(ElArgs a, ElPass ps, EvBlocks ev) {
+  const int64_t total = a.clk->n_sorted[ps.sa];
   const int64_t step = a.clk->step;
-  int hits = 0;
-  const int span = (nq + 31) & ~31;
-  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < span; s += gridDim.x * blockDim.x) {
-    bool hit = false;
-    if (s < nq) {
-      const uint64_t pr = q.pair[s];
-      const uint32_t info = q.info[s];
-      const uint32_t Nt = info & 0x3FFFFFFFu;
-      const bool proj_b = (info >> 30) & 1u;
-      // A' is the projectile, B' its target
-      const SpeciesBuf &A = proj_b ? ps.B : ps.A;
-      const SpeciesBuf &B = proj_b ? ps.A : ps.B;
-      const int64_t ia = proj_b ? (int64_t)(pr >> 32) : (int64_t)(uint32_t)pr;
-      const int64_t ib = proj_b ? (int64_t)(uint32_t)pr : (int64_t)(pr >> 32);
-      const double mA = proj_b ? ps.m_b : ps.m_a, mB = proj_b ? ps.m_a : ps.m_b;
-      const int32_t wa = A.w[ia], wb = B.w[ib];
-      const float ax = A.vx[ia], ay = A.vy[ia], az = A.vz[ia];
-      const float bx = B.vx[ib], by = B.vy[ib], bz = B.vz[ib];
-      const U4 r = rng_block(a.seed, ps.draw_purpose, A.id[ia], step, 0);
-      hit = true;
-      if (info >> 31) {
-        const double dx = (double)ax - (double)bx, dy = (double)ay - (double)by, dz = (double)az - (double)bz;
-        const double u = sqrt(rn3(dx, dx, dy, dy, dz, dz));
-        const double P = -expm1(-(u * ((double)Nt / a.V_cell) * ((double)wb * a.w_min) * ps.sigma * a.dt));
-        hit = u01d(r.v[0]) < P;
+  const int64_t nunit = (total + kEvUnit - 1) / kEvUnit;
+  for (int64_t unit = ev_warp(); unit < nunit; unit += ev_nwarp()) {
+    const int64_t lo = unit * kEvUnit, hi = min(total, lo + kEvUnit);
+    int64_t run = 0;
+    uint64_t prod = 0;
+    for (int64_t base = lo; base < hi; base += 32) {
+      const int64_t t = base + (threadIdx.x & 31);
+      const ElItem m = el_item(ps, t, hi);
+      const uint32_t w = cell_word(a.seed, ps.pair_purpose, m.c, m.need, step);
+      ElPair pr;
+      int n = 0;
+      uint64_t pc = 0;
+      if (el_pair_of(ps, m, t, w, &pr)) {
+        n = el_ncoll(a, ps, pr, step);
+        if (n > 0) pc = el_products(ps, pr, n);
       }
-      if (hit) {
-        float na[3], nb[3];
-        if (ps.exchange) {
-          na[0] = bx; na[1] = by; na[2] = bz;
-          nb[0] = ax; nb[1] = ay; nb[2] = az;
-        } else {
-          double du[3];
-          delta_u((double)ax - (double)bx, (double)ay - (double)by, (double)az - (double)bz, 2.0 * u01d(r.v[1]) - 1.0,
-                  2.0 * kPi * u01d(r.v[2]), du);
-          const double mu = mA * mB / (mA + mB);
-          const double ka = mu / mA, kb = mu / mB;
-          na[0] = (float)((double)ax + ka * du[0]); na[1] = (float)((double)ay + ka * du[1]);
-          na[2] = (float)((double)az + ka * du[2]);
-          nb[0] = (float)((double)bx - kb * du[0]); nb[1] = (float)((double)by - kb * du[1]);
-          nb[2] = (float)((double)bz - kb * du[2]);
+      ev_stage(ev, lo, &run, &prod, t, (uint32_t)n, pc);
+    }
+    if ((threadIdx.x & 31) == 0) {
+      ev.hits[unit] = (int)run;
+      ev.cnt[unit] = prod;
+    }
+  }
+}
+
+// capacity check of a pass's new SPs (packed as in el_products)
+__global__ void k_el_check(DevClock *clk, const uint64_t *total, int sa, int sb, int like, int64_t cap_a, int64_t cap_b,
+                           int *go) {
+  const uint64_t t = *total;
+  const int64_t na = (int64_t)(t & 0xffffffffu), nb = like ? 0 : (int64_t)(t >> 32);
+  const bool ok = clk->n[sa] + na <= cap_a && (like || clk->n[sb] + nb <= cap_b);
+  *go = ok ? 1 : 0;
+  if (!ok) atomicOr(&clk->err, kErrCapacity);
+}
+
+__global__ void k_el_commit(DevClock *clk, const uint64_t *total, const int *go, int sa, int sb, int like) {
+  if (!*go) return;
+  const uint64_t t = *total;
+  const int64_t na = (int64_t)(t & 0xffffffffu), nb = like ? 0 : (int64_t)(t >> 32);
+  clk->n[sa] += na;
+  if (!like) clk->n[sb] += nb;
+  clk->next_id += na + nb;
+}
+
+// Events of the staged pairs, unit by unit in item order: the FP64 velocities, the turned or
+// split SPs and the new ones.
+__global__ void __launch_bounds__(256) k_el_products(ElArgs a, ElPass ps, EvBlocks ev) {
+  if (!*a.go) return;
+  const int64_t total = a.clk->n_sorted[ps.sa];
+  const int64_t step = a.clk->step, id_base = a.clk->next_id;
+  const int64_t n_a = a.clk->n[ps.sa], n_b = a.clk->n[ps.sb];
+  const int64_t nunit = (total + kEvUnit - 1) / kEvUnit;
+  int events = 0;
+  for (int64_t unit = ev_warp(); unit < nunit; unit += ev_nwarp()) {
+    const int64_t lo = unit * kEvUnit;
+    const int nh = ev.hits[unit];
+    uint64_t run = ev.off[unit];
+    for (int base = 0; base < nh; base += 32) {
+      const int i = base + (threadIdx.x & 31);
+      ElPair pr{};
+      int n = 0;
+      uint64_t pc = 0;
+      if (i < nh) {
+        const uint64_t rec = ev.rec[lo + i];
+        const int64_t t = (int64_t)(uint32_t)rec;
+        n = (int)(rec >> 32);
+        const ElItem m = el_item(ps, t, total);
+        el_pair_of(ps, m, t, rng_block(a.seed, ps.pair_purpose, m.c, step, 0).v[0], &pr);
+        pc = el_products(ps, pr, n);
+      }
+      uint64_t tile;
+      const uint64_t off = run + warp_scan_u64(pc, &tile);
+      run += tile;
+      if (i >= nh) continue;
+      ++events;
+      SpeciesBuf &A = pr.proj_b ? ps.B : ps.A;
+      SpeciesBuf &B = pr.proj_b ? ps.A : ps.B;
+      const int64_t ip = pr.ip, it = pr.it;
+      const float ax = A.vx[ip], ay = A.vy[ip], az = A.vz[ip];
+      const float bx = B.vx[it], by = B.vy[it], bz = B.vz[it];
+      float na[3], nb[3];
+      if (ps.exchange) {
+        na[0] = bx; na[1] = by; na[2] = bz;
+        nb[0] = ax; nb[1] = ay; nb[2] = az;
+      } else {
+        const U4 r = rng_block(a.seed, ps.scat_purpose, A.id[ip], step, 0);
+        const double mA = pr.proj_b ? ps.m_b : ps.m_a, mB = pr.proj_b ? ps.m_a : ps.m_b;
+        double du[3];
+        delta_u((double)ax - (double)bx, (double)ay - (double)by, (double)az - (double)bz, 2.0 * u01d(r.v[0]) - 1.0,
+                2.0 * kPi * u01d(r.v[1]), du);
+        const double mu = mA * mB / (mA + mB);
+        const double ka = mu / mA, kb = mu / mB;
+        na[0] = (float)((double)ax + ka * du[0]); na[1] = (float)((double)ay + ka * du[1]);
+        na[2] = (float)((double)az + ka * du[2]);
+        nb[0] = (float)((double)bx - kb * du[0]); nb[1] = (float)((double)by - kb * du[1]);
+        nb[2] = (float)((double)bz - kb * du[2]);
+      }
+      // slots: the running offsets of species A (low half) and B (high half); the like pass
+      // keeps both sides in the low half, projectile first
+      int64_t off_a = (int64_t)(off & 0xffffffffu), off_b = (int64_t)(off >> 32);
+      int64_t id = id_base + off_a + off_b;
+      const int32_t wp = A.w[ip], wt = B.w[it];
+      auto place = [&](SpeciesBuf &S, int64_t idx, int32_t w, const float v[3], bool in_b) {
+        if (n == w) {
+          S.vx[idx] = v[0]; S.vy[idx] = v[1]; S.vz[idx] = v[2];
+          return;
         }
-        // weight rule: U_w < w_small / w_large  <=>  (2 (word >> 8) + 1) w_large < w_small 2^25
-        const bool a_small = wa <= wb;
-        const uint64_t ws = (uint64_t)(a_small ? wa : wb), wl = (uint64_t)(a_small ? wb : wa);
-        const bool large_too = (2ull * (r.v[3] >> 8) + 1ull) * wl < (ws << 25);
-        if (a_small || large_too) { A.vx[ia] = na[0]; A.vy[ia] = na[1]; A.vz[ia] = na[2]; }
-        if (!a_small || large_too) { B.vx[ib] = nb[0]; B.vy[ib] = nb[1]; B.vz[ib] = nb[2]; }
-      }
+        S.w[idx] = w - n;
+        const int64_t slot = in_b ? n_b + off_b++ : n_a + off_a++;
+        put_sp(S, slot, S.x[idx], S.y[idx], S.z[idx], v[0], v[1], v[2], n, (uint64_t)id++);
+      };
+      const bool p_in_b = ps.like ? false : pr.proj_b, t_in_b = ps.like ? false : !pr.proj_b;
+      place(A, ip, wp, na, p_in_b);
+      place(B, it, wt, nb, t_in_b);
     }
-    int v = hit ? 1 : 0;
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    hits += v;
   }
-  if ((threadIdx.x & 31) == 0 && hits) atomicAdd((unsigned long long *)&a.clk->ctr[ps.ctr], (unsigned long long)hits);
+  for (int o = 16; o > 0; o >>= 1) events += __shfl_down_sync(0xffffffffu, events, o);
+  if ((threadIdx.x & 31) == 0 && events) atomicAdd((unsigned long long *)&a.clk->ctr[ps.ctr], (unsigned long long)events);
 }
 
 // ---- direct field ionization -----------------------------------------------------------------
@@ -669,36 +743,30 @@ int stage_collide(pic_t *h) {
   if (fl & PIC_F_ELASTIC) {
     ElArgs a{};
     a.V_cell = h->dx * h->dx * h->dx; a.dt = h->prm.dt; a.w_min = h->prm.w_min; a.seed = h->prm.seed;
-    a.clk = h->clock;
+    a.clk = h->clock; a.go = go;
     const Species &E = h->sp[PIC_ELECTRON], &N = h->sp[PIC_NEUTRAL], &I = h->sp[PIC_ION];
-    auto pass = [&](const Species &A, int sa, const Species &B, int sb, double sigma, uint32_t pp, uint32_t dp, int ex,
-                    int ctr) {
+    auto pass = [&](const Species &A, int sa, const Species &B, int sb, double sigma, uint32_t pp, uint32_t dp,
+                    uint32_t sp_, int ex, int like, int ctr) {
       ElPass ps{};
       ps.A = A.a; ps.B = B.a; ps.off_a = A.off; ps.off_b = B.off; ps.skey_a = A.skey; ps.skey_b = B.skey;
       ps.sa = sa; ps.sb = sb; ps.m_a = A.mass; ps.m_b = B.mass; ps.sigma = sigma;
-      ps.pair_purpose = pp; ps.draw_purpose = dp; ps.exchange = ex; ps.ctr = ctr;
+      ps.pair_purpose = pp; ps.draw_purpose = dp; ps.scat_purpose = sp_; ps.exchange = ex; ps.like = like; ps.ctr = ctr;
       ps.nWsd1 = (float)(h->prm.w_min * sigma * h->prm.dt / a.V_cell);
       return ps;
     };
-    // queues in the MCC scratch (its last reader, the products kernel, has run); a pass has at
-    // most one queued pair per SP of one species, and capsum covers e- plus Cu
-    const int cap = (int)std::min<int64_t>(E.cap + N.cap, INT32_MAX);
-    ElQueue q[3];
-    for (int p = 0; p < 3; ++p) q[p] = ElQueue{h->pair_cnt, (uint32_t *)h->pair_ncoll, h->long_n + 8 + p, cap};
-    PIC_CUDA(h, cudaMemsetAsync(h->long_n + 8, 0, 3 * sizeof(int), h->stream));
-    const ElPass pen = pass(E, PIC_ELECTRON, N, PIC_NEUTRAL, h->sigma_el_en, kPairEn, kDrawEn, 0, cElasticEn);
-    const ElPass pnn = pass(N, PIC_NEUTRAL, N, PIC_NEUTRAL, h->sigma_el_nn, kPairNn, kDrawNn, 0, cElasticNn);
-    const ElPass pcx = pass(I, PIC_ION, N, PIC_NEUTRAL, h->sigma_cx, kPairCx, kDrawCx, 1, cChargeEx);
-    const int agrid = h->nsm * 2;
-    h->nlaunch += 6;
-    {
-      KtScope kt_(h, kidElastic, 0);
-      k_el_decide_inter<<<grid, kThreads, 0, h->stream>>>(a, pen, q[0]);
-      k_el_apply<<<agrid, kThreads, 0, h->stream>>>(a, pen, q[0]);
-      k_el_decide_like<<<grid, kThreads, 0, h->stream>>>(a, pnn, q[1]);
-      k_el_apply<<<agrid, kThreads, 0, h->stream>>>(a, pnn, q[1]);
-      k_el_decide_inter<<<grid, kThreads, 0, h->stream>>>(a, pcx, q[2]);
-      k_el_apply<<<agrid, kThreads, 0, h->stream>>>(a, pcx, q[2]);
+    const ElPass passes[3] = {
+        pass(E, PIC_ELECTRON, N, PIC_NEUTRAL, h->sigma_el_en, kPairEn, kDrawEn, kScatEn, 0, 0, cElasticEn),
+        pass(N, PIC_NEUTRAL, N, PIC_NEUTRAL, h->sigma_el_nn, kPairNn, kDrawNn, kScatNn, 0, 1, cElasticNn),
+        pass(I, PIC_ION, N, PIC_NEUTRAL, h->sigma_cx, kPairCx, kDrawCx, 0, 1, 0, cChargeEx)};
+    for (int p = 0; p < 3; ++p) {
+      const ElPass &ps = passes[p];
+      h->nlaunch += 4;
+      { KtScope kt_(h, kidElastic, 0); k_el_count<<<grid, 256, 0, h->stream>>>(a, ps, ev); }
+      k_ev_units<<<1, 1, 0, h->stream>>>(h->tmp_len, h->clock, 2 + ps.sa);
+      PIC_TRY(scan_u64(h, ev.cnt, ev.off, 0, h->tmp_len, total));
+      k_el_check<<<1, 1, 0, h->stream>>>(h->clock, total, ps.sa, ps.sb, ps.like, h->sp[ps.sa].cap, h->sp[ps.sb].cap, go);
+      { KtScope kt_(h, kidElastic, 0); k_el_products<<<grid, 256, 0, h->stream>>>(a, ps, ev); }
+      k_el_commit<<<1, 1, 0, h->stream>>>(h->clock, total, go, ps.sa, ps.sb, ps.like);
     }
     PIC_TRY(launch_check(h, "elastic"));
   }

@@ -50,7 +50,8 @@ constexpr int kSurOut = 2;
 // Philox purposes (one key per purpose)
 enum Purpose : uint32_t {
   kEmit = 1, kPair = 2, kIon = 3, kScat = 4, kDfi = 5, kEvapP = 6, kSput = 7,
-  kPairEn = 8, kDrawEn = 9, kPairNn = 10, kDrawNn = 11, kPairCx = 12, kDrawCx = 13   // elastic e-Cu, Cu-Cu, exchange
+  kPairEn = 8, kDrawEn = 9, kPairNn = 10, kDrawNn = 11, kPairCx = 12, kDrawCx = 13,   // elastic e-Cu, Cu-Cu, exchange
+  kScatEn = 14, kScatNn = 15
 };
 
 // device counters (int64), indices

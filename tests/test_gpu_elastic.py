@@ -1,10 +1,10 @@
 """Parity of the elastic e-Cu and Cu-Cu collisions and the Cu+-Cu charge exchange
 (PIC_F_ELASTIC) with the oracle, through the C ABI.
 
-Bars: the collision decisions are integer work (event counts and the set of SPs whose velocity
-turned, bit for bit); the new velocities are FP64 rotations stored in float32, within 1e-6 of
-the oracle's per component (plus 1 m/s).  The cross sections are raised far above the
-stand-in defaults so that a small instance has hundreds of events in every pass.
+Bars: the collision decisions and the splitting are integer work (event counts, weights, new
+SPs, ids and slots, bit for bit); the new velocities are FP64 rotations stored in float32,
+within 1e-6 of the oracle's per component (plus 1 m/s).  The cross sections are raised far above
+the stand-in defaults so that a small instance has hundreds of events in every pass.
 """
 import numpy as np
 import pytest
@@ -75,48 +75,60 @@ def _velocities_close(got, ref, k):
         assert len(bad) == 0, (k, c, bad[:5], a[bad[:5]], b[bad[:5]])
 
 
+def _oracle_passes(g, prm, st, offs, ids):
+    """The three passes on the sorted state st (modified in place); the new SPs per species."""
+    el_e, n1, ev_en = EL.elastic_en(g, prm, st["e"], offs["e"], st["n"], offs["n"], 3, ids)
+    n2, ev_nn = EL.elastic_nn(g, prm, st["n"], offs["n"], 3, ids)
+    el_i, n3, ev_cx = EL.charge_exchange(g, prm, st["i"], offs["i"], st["n"], offs["n"], 3, ids)
+    return el_e, P.concat(P.concat(n1, n2), n3), el_i, (ev_en, ev_nn, ev_cx)
+
+
 def test_elastic_passes_match_oracle(pic):
     cfg, g, sim, st, offs, prm, E = _setup(pic, pic.F_ELASTIC)
     before = {k: {c: st[k][c].copy() for c in ("vx", "vy", "vz")} for k in "eni"}
-    ev_en = EL.elastic_en(g, prm, st["e"], offs["e"], st["n"], offs["n"], 3)
-    ev_nn = EL.elastic_nn(g, prm, st["n"], offs["n"], 3)
-    ev_cx = EL.charge_exchange(g, prm, st["i"], offs["i"], st["n"], offs["n"], 3)
-    assert min(ev_en, ev_nn, ev_cx) > 100, (ev_en, ev_nn, ev_cx)
+    nsort = {k: len(st[k]["x"]) for k in "eni"}
+    ids = collide.Counter(cfg["n_sp"])
+    el_e, el_n, el_i, evs = _oracle_passes(g, prm, st, offs, ids)
+    assert min(evs) > 100, evs
+    assert min(len(el_e["w"]), len(el_n["w"]), len(el_i["w"])) > 20   # the splitting is exercised
+    ref = {"e": P.concat(st["e"], el_e), "n": P.concat(st["n"], el_n), "i": P.concat(st["i"], el_i)}
     sim.collide()
     d = sim.diagnostics()
-    assert (d["elastic_en"], d["elastic_nn"], d["charge_exchanges"]) == (ev_en, ev_nn, ev_cx)
+    assert (d["elastic_en"], d["elastic_nn"], d["charge_exchanges"]) == evs
     assert d["impact_ionizations"] == 0 and d["field_ionizations"] == 0
-    for s, (k, _, _) in enumerate(SPECIES):
-        got = sim.get_particles(s)
-        assert_sp_equal(got, st[k], fields=("x", "y", "z", "w", "id"))
-        _velocities_close(got, st[k], k)
-        if k in "ei":   # which SPs turned: bit-exact decisions (electron and ion changes are large)
-            moved_ref = np.any([st[k][c] != before[k][c] for c in ("vx", "vy", "vz")], axis=0)
-            moved_got = np.any([got[c] != before[k][c] for c in ("vx", "vy", "vz")], axis=0)
+    assert d["next_id"] == ids.next_id
+    for s_, (k, _, _) in enumerate(SPECIES):
+        got = sim.get_particles(s_)
+        assert_sp_equal(got, ref[k], fields=("x", "y", "z", "w", "id"))
+        _velocities_close(got, ref[k], k)
+        if k in "ei":   # which sorted SPs turned whole: bit-exact decisions
+            m = nsort[k]
+            moved_ref = np.any([ref[k][c][:m] != before[k][c] for c in ("vx", "vy", "vz")], axis=0)
+            moved_got = np.any([got[c][:m] != before[k][c] for c in ("vx", "vy", "vz")], axis=0)
             assert np.array_equal(moved_got, moved_ref), k
     sim.close()
 
 
 def test_collide_stage_with_elastic_matches_oracle(pic):
-    """Impact ionization, then the three passes, then field ionization: the oracle step's order."""
+    """Impact ionization, then the three passes, then field ionization: the oracle step's order
+    and its order of the new SPs."""
     flags = pic.F_IMPACT_ION | pic.F_DFI | pic.F_ELASTIC
     cfg, g, sim, st, offs, prm, E = _setup(pic, flags, V0=420.0, seed=13)
     ids = collide.Counter(cfg["n_sp"])
     ni, ne, ev = collide.impact_ionization(g, prm, st["e"], offs["e"], st["n"], offs["n"], 3, ids)
-    ev_en = EL.elastic_en(g, prm, st["e"], offs["e"], st["n"], offs["n"], 3)
-    ev_nn = EL.elastic_nn(g, prm, st["n"], offs["n"], 3)
-    ev_cx = EL.charge_exchange(g, prm, st["i"], offs["i"], st["n"], offs["n"], 3)
+    el_e, el_n, el_i, evs = _oracle_passes(g, prm, st, offs, ids)
+    st["n"] = P.concat(st["n"], el_n)
     ni2, ne2, ev2 = collide.field_ionization(g, prm, st["n"], E, 3, ids)
-    ref = {"e": P.concat(P.concat(st["e"], ne), ne2), "n": st["n"], "i": P.concat(P.concat(st["i"], ni), ni2)}
+    ref = {"e": P.concat(P.concat(P.concat(st["e"], ne), el_e), ne2), "n": st["n"],
+           "i": P.concat(P.concat(P.concat(st["i"], ni), el_i), ni2)}
     sim.collide()
     d = sim.diagnostics()
-    assert ev > 20 and ev2 > 20 and min(ev_en, ev_nn, ev_cx) > 20, (ev, ev2, ev_en, ev_nn, ev_cx)
+    assert ev > 20 and ev2 > 20 and min(evs) > 20, (ev, ev2, evs)
     assert (d["impact_ionizations"], d["field_ionizations"]) == (ev, ev2)
-    assert (d["elastic_en"], d["elastic_nn"], d["charge_exchanges"]) == (ev_en, ev_nn, ev_cx)
+    assert (d["elastic_en"], d["elastic_nn"], d["charge_exchanges"]) == evs
     assert d["next_id"] == ids.next_id
-    for s, (k, _, _) in enumerate(SPECIES):
-        got = sim.get_particles(s)
+    for s_, (k, _, _) in enumerate(SPECIES):
+        got = sim.get_particles(s_)
         assert_sp_equal(got, ref[k], fields=("x", "y", "z", "w", "id"))
         _velocities_close(got, ref[k], k)
     sim.close()
-
