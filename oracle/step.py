@@ -9,7 +9,8 @@ Order (Sec. 2.3.1 and Fig. newpic; the paper prints no pseudocode, this is the r
      holds the anode at the new V_gap)
   a4 stable cell sort of every species (survivors in previous order)
   a5 impact ionization MCC (with prm "elastic": then e-Cu and Cu-Cu elastic collisions and
-     Cu+-Cu charge exchange on the sorted SPs), a6 direct field ionization
+     Cu+-Cu charge exchange; with prm "coulomb": then e-e, e-Cu+ and Cu+-Cu+ Coulomb
+     collisions; all on the sorted SPs), a6 direct field ionization
   a7 fixed-point charge deposit, a8 Poisson solve, a9 node field
   a10 every n_heat steps: continuity + heat on the tip cells
 
@@ -22,7 +23,7 @@ import math
 
 import numpy as np
 
-from . import circuit, collide, elastic, emission, field, heat, particles as P, philox, surface
+from . import circuit, collide, coulomb, elastic, emission, field, heat, particles as P, philox, surface
 from . import constants as C
 
 E_, N_, I_ = "e", "n", "i"
@@ -269,6 +270,10 @@ def step(st, emission_fn=None):
         el_i, el_n3, st.count["charge_exchanges"] = elastic.charge_exchange(g, prm, st.sp[I_], st.off[I_], st.sp[N_],
                                                                             st.off[N_], st.step, ids)
         st.sp[N_] = P.concat(P.concat(P.concat(st.sp[N_], el_n1), el_n2), el_n3)
+    if prm.get("coulomb"):
+        st.count["coulomb_ee"] = coulomb.coulomb_ee(g, prm, st.sp[E_], st.off[E_], st.step)
+        st.count["coulomb_ei"] = coulomb.coulomb_ei(g, prm, st.sp[E_], st.off[E_], st.sp[I_], st.off[I_], st.step)
+        st.count["coulomb_ii"] = coulomb.coulomb_ii(g, prm, st.sp[I_], st.off[I_], st.step)
     # a6
     ni2, ne2, ev2 = collide.field_ionization(g, prm, st.sp[N_], st.E, st.step, ids)
     st.count["field_ionizations"] = ev2
