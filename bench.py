@@ -207,6 +207,8 @@ def run_ours(args):
         prod_flags |= pic.F_ELASTIC
     if args.extrapolate:   # each step's solve starts from 2 phi^n - phi^(n-1)
         prod_flags |= pic.F_EXTRAPOLATE
+    if args.coulomb:   # e-e, e-Cu+, Cu+-Cu+ Coulomb collisions (lnL = 10)
+        prod_flags |= pic.F_COULOMB
     plain_flags = pic.F_ALL & ~pic.F_SURROGATE & ~pic.F_MIXED_MG
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
@@ -346,6 +348,8 @@ def run_ours(args):
                                if args.circuit else None),
                    "elastic": ({"e_Cu": d1["elastic_en"], "Cu_Cu": d1["elastic_nn"], "exchange": d1["charge_exchanges"]}
                                if args.elastic else None),
+                   "coulomb": ({"e_e": d1["coulomb_ee"], "e_Cu+": d1["coulomb_ei"], "Cu+_Cu+": d1["coulomb_ii"]}
+                               if args.coulomb else None),
                    "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()}, "mg_cycles": d1["mg_cycles"],
                    "mg_cycles_per_step": (d1["mg_cycles_total"] - d0["mg_cycles_total"]) / args.steps,
                    "kernel_ms_per_step": kernel_ms,
@@ -536,6 +540,7 @@ def main():
     ap.add_argument("--circuit", action="store_true", help="step with the RC circuit and Shockley-Ramo current")
     ap.add_argument("--elastic", action="store_true", help="step with elastic collisions and charge exchange")
     ap.add_argument("--extrapolate", action="store_true", help="start each solve from the time-extrapolated potential")
+    ap.add_argument("--coulomb", action="store_true", help="step with Coulomb collisions between charged SPs")
     args = ap.parse_args()
     if args.impl == "reference":
         out = run_reference(args)

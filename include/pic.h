@@ -61,6 +61,7 @@ extern "C" {
 #define PIC_F_MIXED_MG 0x80u    /* a8: FP32 V-cycles with FP64 residual refinement (else FP64 V-cycles) */
 #define PIC_F_FAST_INTEGRAL 0x100u  /* a1: Gamow quadrature and turning points in FP32 (J, P_N to ~1e-5
                                        relative) in the step and in pic_emission_eval; else all FP64 */
+#define PIC_F_COULOMB 0x2000u  /* a5: then e-e, e-Cu+, Cu+-Cu+ Coulomb collisions (binary small-angle method) */
 #define PIC_F_EXTRAPOLATE 0x1000u /* pic_step starts each solve from 2 phi^n - phi^(n-1) instead of phi^n */
 #define PIC_F_ELASTIC 0x800u    /* a5: then elastic e-Cu and Cu-Cu collisions and Cu+-Cu charge exchange */
 #define PIC_F_CIRCUIT 0x400u    /* the RC circuit drives the anode (needs circuit_R, circuit_C > 0 at create) */
@@ -105,6 +106,7 @@ typedef struct {
   double sigma_el_en;   /* m^2: e-Cu elastic cross section (<= 0: 1e-19, a constant stand-in) */
   double sigma_el_nn;   /* m^2: Cu-Cu elastic cross section (<= 0: hard spheres pi (2 x 128 pm)^2) */
   double sigma_cx;      /* m^2: Cu+-Cu charge exchange cross section (<= 0: 5e-19, a constant stand-in) */
+  double coulomb_log;   /* Coulomb logarithm of the Coulomb collisions (<= 0: 10) */
 } pic_params_t;
 
 typedef struct {
@@ -129,6 +131,7 @@ typedef struct {
   double I_gap, I_tot;      /* A: Shockley-Ramo gap current and circuit current of the last circuit stage */
   int64_t elastic_en, elastic_nn, charge_exchanges;  /* colliding pairs this step (PIC_F_ELASTIC) */
   int64_t mg_cycles_total;  /* Poisson refinement cycles since create (both forms) */
+  int64_t coulomb_ee, coulomb_ei, coulomb_ii;  /* pairs turned this step (PIC_F_COULOMB) */
 } pic_diag_t;
 
 typedef struct pic_s pic_t;

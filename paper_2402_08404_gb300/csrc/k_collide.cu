@@ -595,6 +595,77 @@ __global__ void __launch_bounds__(256) k_el_products(ElArgs a, ElPass ps, EvBloc
   if ((threadIdx.x & 31) == 0 && events) atomicAdd((unsigned long long *)&a.clk->ctr[ps.ctr], (unsigned long long)events);
 }
 
+// ---- Coulomb collisions ---------------------------------------------------------------------
+// e-e, e-Cu+ and Cu+-Cu+ by the binary small-angle method the paper cites (Table colls): every
+// pair turns its relative velocity u by theta, with delta = tan(theta/2) normal of variance
+// <delta^2> = q_a^2 q_b^2 n lnL dt / (8 pi eps0^2 m_ab^2 u^3) (n the target density n_t W_t as in
+// eq:colp) and a uniform azimuth; the velocity difference is eq:du and eq:newv gives the new
+// velocities.  Whole SPs turn (the lighter always, the heavier with probability w_s/w_l, tested
+// in integers).  No decision depends on floating point, so the turn is computed in FP32: sin and
+// cos of theta from delta directly (no cancellation at small angles), the azimuth and the
+// Box-Muller angle by sincospif.  Pairings as for the elastic passes.
+struct CoPass {
+  ElPass ps;        // species, offsets, sort keys, pairing purpose, like flag
+  float K;          // q_a^2 q_b^2 lnL dt w_min / (8 pi eps0^2 m_ab^2 V_cell): <delta^2> = K Nt W_t / u^3
+  float ka, kb;     // m_ab / m_a, m_ab / m_b of species A and B of the pass
+  uint32_t draw_purpose;
+};
+
+__device__ __forceinline__ void co_turn(const CoPass &cp, const ElPair &pr, int64_t step, uint64_t seed, int *hits) {
+  const ElPass &ps = cp.ps;
+  SpeciesBuf A = pr.proj_b ? ps.B : ps.A;
+  SpeciesBuf B = pr.proj_b ? ps.A : ps.B;
+  const int32_t wa = A.w[pr.ip], wb = B.w[pr.it];
+  if (wa <= 0 || wb <= 0) return;
+  const float ax = A.vx[pr.ip], ay = A.vy[pr.ip], az = A.vz[pr.ip];
+  const float bx = B.vx[pr.it], by = B.vy[pr.it], bz = B.vz[pr.it];
+  const float ux = ax - bx, uy = ay - by, uz = az - bz;
+  const float u2 = ux * ux + uy * uy + uz * uz;
+  if (u2 == 0.0f) return;
+  const float u = sqrtf(u2);
+  float d2 = cp.K * (float)pr.Nt * (float)wb / (u2 * u);
+  if (!(d2 < 1e30f)) d2 = 1e30f;
+  const U4 r = rng_block(seed, cp.draw_purpose, A.id[pr.ip], step, 0);
+  const float g = sqrtf(-2.0f * logf(u01f(r.v[0]))) * cospif(2.0f * u01f(r.v[1]));
+  const float dd = d2 * g * g;                          // delta^2 of this pair
+  const float sin_t = 2.0f * sqrtf(dd) / (1.0f + dd);   // |sin theta|
+  const float cm1 = -2.0f * dd / (1.0f + dd);           // cos theta - 1
+  float sp, cpf;
+  sincospif(2.0f * u01f(r.v[2]), &sp, &cpf);
+  // [R^-1(theta, phi) - I] (0, 0, u), then R^-1 of the angles of u
+  const float v0 = u * sin_t * cpf, v1 = u * sin_t * sp, v2 = u * cm1;
+  const float uperp = sqrtf(ux * ux + uy * uy);
+  const float ct = uz / u, st = uperp / u;
+  const float cph = uperp > 0.0f ? ux / uperp : 1.0f, sph = uperp > 0.0f ? uy / uperp : 0.0f;
+  const float dux = ct * cph * v0 - sph * v1 + st * cph * v2;
+  const float duy = ct * sph * v0 + cph * v1 + st * sph * v2;
+  const float duz = -st * v0 + ct * v2;
+  const float ka = pr.proj_b ? cp.kb : cp.ka, kb = pr.proj_b ? cp.ka : cp.kb;
+  const bool a_small = wa <= wb;
+  const uint64_t ws = (uint64_t)(a_small ? wa : wb), wl = (uint64_t)(a_small ? wb : wa);
+  const bool large_too = (2ull * (r.v[3] >> 8) + 1ull) * wl < (ws << 25);
+  if (a_small || large_too) { A.vx[pr.ip] = ax + ka * dux; A.vy[pr.ip] = ay + ka * duy; A.vz[pr.ip] = az + ka * duz; }
+  if (!a_small || large_too) { B.vx[pr.it] = bx - kb * dux; B.vy[pr.it] = by - kb * duy; B.vz[pr.it] = bz - kb * duz; }
+  ++*hits;
+}
+
+// One pass: one item per sorted SP of species A (whole warps: the cell's pairing word is shared).
+__global__ void __launch_bounds__(256) k_coulomb(CoPass cp, uint64_t seed, DevClock *clk, int ctr) {
+  const ElPass &ps = cp.ps;
+  const int64_t n = clk->n_sorted[ps.sa];
+  const int64_t step = clk->step;
+  const int64_t span = (n + 31) & ~31ll;
+  int hits = 0;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < span; t += (int64_t)gridDim.x * blockDim.x) {
+    const ElItem m = el_item(ps, t, n);
+    const uint32_t w = cell_word(seed, ps.pair_purpose, m.c, m.need, step);
+    ElPair pr;
+    if (el_pair_of(ps, m, t, w, &pr)) co_turn(cp, pr, step, seed, &hits);
+  }
+  for (int o = 16; o > 0; o >>= 1) hits += __shfl_down_sync(0xffffffffu, hits, o);
+  if ((threadIdx.x & 31) == 0 && hits) atomicAdd((unsigned long long *)&clk->ctr[ctr], (unsigned long long)hits);
+}
+
 // ---- direct field ionization -----------------------------------------------------------------
 struct DfiArgs {
   SpeciesBuf n, e, ions;
@@ -769,6 +840,34 @@ int stage_collide(pic_t *h) {
       k_el_commit<<<1, 1, 0, h->stream>>>(h->clock, total, go, ps.sa, ps.sb, ps.like);
     }
     PIC_TRY(launch_check(h, "elastic"));
+  }
+  if (fl & PIC_F_COULOMB) {
+    const Species &E = h->sp[PIC_ELECTRON], &I = h->sp[PIC_ION];
+    const double lnL = h->prm.coulomb_log > 0 ? h->prm.coulomb_log : 10.0;
+    auto pass = [&](const Species &A, int sa, const Species &B, int sb, double qa, double qb, uint32_t pp, uint32_t dp,
+                    int like) {
+      CoPass cp{};
+      ElPass &ps = cp.ps;
+      ps.A = A.a; ps.B = B.a; ps.off_a = A.off; ps.off_b = B.off; ps.skey_a = A.skey; ps.skey_b = B.skey;
+      ps.sa = sa; ps.sb = sb; ps.m_a = A.mass; ps.m_b = B.mass; ps.pair_purpose = pp; ps.like = like;
+      const double mab = A.mass * B.mass / (A.mass + B.mass);
+      const double V = h->dx * h->dx * h->dx;
+      cp.K = (float)(qa * qa * qb * qb * lnL * h->prm.dt * h->prm.w_min / (8.0 * kPi * kEps0 * kEps0 * mab * mab * V));
+      cp.ka = (float)(mab / A.mass); cp.kb = (float)(mab / B.mass);
+      cp.draw_purpose = dp;
+      return cp;
+    };
+    const CoPass ee = pass(E, PIC_ELECTRON, E, PIC_ELECTRON, kQe, kQe, kPairEe, kDrawEe, 1);
+    const CoPass ei = pass(E, PIC_ELECTRON, I, PIC_ION, kQe, kQe, kPairEi, kDrawEi, 0);
+    const CoPass ii = pass(I, PIC_ION, I, PIC_ION, kQe, kQe, kPairIi, kDrawIi, 1);
+    h->nlaunch += 3;
+    {
+      KtScope kt_(h, kidCoulomb, 0);
+      k_coulomb<<<grid, 256, 0, h->stream>>>(ee, h->prm.seed, h->clock, cCoulombEe);
+      k_coulomb<<<grid, 256, 0, h->stream>>>(ei, h->prm.seed, h->clock, cCoulombEi);
+      k_coulomb<<<grid, 256, 0, h->stream>>>(ii, h->prm.seed, h->clock, cCoulombIi);
+    }
+    PIC_TRY(launch_check(h, "coulomb"));
   }
   if (fl & PIC_F_DFI) {
     DfiArgs d;

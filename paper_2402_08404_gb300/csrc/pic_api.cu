@@ -196,7 +196,7 @@ static T *alloc_n(pic_t *h, int64_t n) {
 namespace pic {
 const char *const kKernelNames[kidNum] = {
     "k_push", "k_keys", "k_scatter", "k_fix_short", "k_fix_mid", "k_fix_long", "k_gather", "k_scan_partial",
-    "k_scan_apply", "k_deposit", "k_mcc_count", "k_mcc_products", "k_elastic", "k_dfi_count", "k_dfi_products", "k_dirichlet",
+    "k_scan_apply", "k_deposit", "k_mcc_count", "k_mcc_products", "k_elastic", "k_coulomb", "k_dfi_count", "k_dfi_products", "k_dirichlet",
     "k_residual64", "k_norm_sum", "k_smooth", "k_smooth_first", "k_residual", "k_restrict", "k_prolong", "k_coarse", "k_vcycle_tail", "k_ramo",
     "k_correct", "k_efield", "k_face_field", "k_emit_surrogate", "k_emit_fallback", "k_emit_count", "k_emit_write",
     "k_inject_count", "k_inject_write", "k_mlp_forward", "k_heat"};
@@ -1334,6 +1334,9 @@ int pic_diagnostics(pic_t *h, pic_diag_t *out) {
   out->elastic_en = c.ctr[cElasticEn];
   out->elastic_nn = c.ctr[cElasticNn];
   out->charge_exchanges = c.ctr[cChargeEx];
+  out->coulomb_ee = c.ctr[cCoulombEe];
+  out->coulomb_ei = c.ctr[cCoulombEi];
+  out->coulomb_ii = c.ctr[cCoulombIi];
   out->ion_impacts = c.ctr[cIonImpacts];
   out->mg_cycles = h->last_solve_graph ? c.mg_cycles_last : h->last_mg_cycles;
   out->mg_residual = h->last_solve_graph ? (double)c.mg_rel_last : h->last_mg_res;

@@ -51,13 +51,14 @@ constexpr int kSurOut = 2;
 enum Purpose : uint32_t {
   kEmit = 1, kPair = 2, kIon = 3, kScat = 4, kDfi = 5, kEvapP = 6, kSput = 7,
   kPairEn = 8, kDrawEn = 9, kPairNn = 10, kDrawNn = 11, kPairCx = 12, kDrawCx = 13,   // elastic e-Cu, Cu-Cu, exchange
-  kScatEn = 14, kScatNn = 15
+  kScatEn = 14, kScatNn = 15,
+  kPairEe = 16, kDrawEe = 17, kPairEi = 18, kDrawEi = 19, kPairIi = 20, kDrawIi = 21   // Coulomb
 };
 
 // device counters (int64), indices
 enum Ctr {
   cEmitted = 0, cEvaporated, cSputtered, cImpactIon, cFieldIon, cRemovedE, cRemovedN, cRemovedI,
-  cIonImpacts, cWevals, cSurFaces, cElasticEn, cElasticNn, cChargeEx, cNum
+  cIonImpacts, cWevals, cSurFaces, cElasticEn, cElasticNn, cChargeEx, cCoulombEe, cCoulombEi, cCoulombIi, cNum
 };
 
 // error bits set by kernels
@@ -291,7 +292,7 @@ namespace pic {
 // Kernels whose launches can be timed one by one (pic_set_kernel_timing); the order is the ABI's.
 enum Kid : int {
   kidPush = 0, kidKeys, kidScatter, kidFixShort, kidFixMid, kidFixLong, kidGather, kidScanPartial, kidScanApply,
-  kidDeposit, kidMccCount, kidMccProducts, kidElastic, kidDfiCount, kidDfiProducts, kidDirichlet, kidResidual64, kidNormSum,
+  kidDeposit, kidMccCount, kidMccProducts, kidElastic, kidCoulomb, kidDfiCount, kidDfiProducts, kidDirichlet, kidResidual64, kidNormSum,
   kidSmooth, kidSmoothFirst, kidResidual, kidRestrict, kidProlong, kidCoarse, kidTail, kidRamo, kidCorrect, kidEfield, kidFaceField,
   kidEmitSurrogate, kidEmitFallback, kidEmitCount, kidEmitWrite, kidInjectCount, kidInjectWrite, kidMlpForward,
   kidHeat, kidNum

@@ -21,6 +21,7 @@ F_GRAPH = 0x200
 F_CIRCUIT = 0x400
 F_ELASTIC = 0x800
 F_EXTRAPOLATE = 0x1000
+F_COULOMB = 0x2000
 F_PRODUCTION = F_ALL | F_FAST_INTEGRAL     # surrogate, FP32 Gamow quadrature for its fallback, mixed MG
 
 QE = 1.602176634e-19
@@ -52,7 +53,7 @@ class Params(C.Structure):
                 ("n_heat", C.c_int), ("seed", C.c_uint64), ("flags", C.c_uint32), ("mg_tol", C.c_double),
                 ("mg_max_cycles", C.c_int), ("mg_sweeps", C.c_int), ("circuit_R", C.c_double),
                 ("circuit_C", C.c_double), ("sigma_el_en", C.c_double), ("sigma_el_nn", C.c_double),
-                ("sigma_cx", C.c_double)]
+                ("sigma_cx", C.c_double), ("coulomb_log", C.c_double)]
 
 
 class Diag(C.Structure):
@@ -65,7 +66,8 @@ class Diag(C.Structure):
                 ("ms", C.c_double * 8), ("kernel_launches", C.c_int64), ("emission_evals", C.c_int64),
                 ("surrogate_faces", C.c_int64), ("V_gap", C.c_double), ("I_gap", C.c_double),
                 ("I_tot", C.c_double), ("elastic_en", C.c_int64), ("elastic_nn", C.c_int64),
-                ("charge_exchanges", C.c_int64), ("mg_cycles_total", C.c_int64)]
+                ("charge_exchanges", C.c_int64), ("mg_cycles_total", C.c_int64), ("coulomb_ee", C.c_int64),
+                ("coulomb_ei", C.c_int64), ("coulomb_ii", C.c_int64)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
@@ -184,7 +186,8 @@ class Pic:
                      int(cfg["w_max_units"]), int(cfg.get("n_heat", 0)), int(cfg.get("seed", 1)), int(flags),
                      float(mg_tol), int(mg_max_cycles), int(mg_sweeps), float(cfg.get("circuit_R", 0.0)),
                      float(cfg.get("circuit_C", 0.0)), float(cfg.get("sigma_el_en", 0.0)),
-                     float(cfg.get("sigma_el_nn", 0.0)), float(cfg.get("sigma_cx", 0.0)))
+                     float(cfg.get("sigma_el_nn", 0.0)), float(cfg.get("sigma_cx", 0.0)),
+                     float(cfg.get("coulomb_log", 0.0)))
         h = C.c_void_p()
         a = self._alloc.alloc_fn if self._alloc else ALLOC_FN(0)
         f = self._alloc.free_fn if self._alloc else FREE_FN(0)

@@ -57,3 +57,27 @@ def assert_sp_equal(got, ref, fields=("x", "y", "z", "vx", "vy", "vz", "w", "id"
         if not np.array_equal(a, b):
             bad = np.nonzero(a != b)[0]
             raise AssertionError(f"field {f}: {len(bad)} mismatches, first at {bad[:5]}: {a[bad[:5]]} vs {b[bad[:5]]}")
+
+
+def colocated_population(cfg, seed):
+    """Seeded plasma with the species brought together in cells: electrons and ions on neutral
+    positions, half the neutrals on the other half's, electrons of 20-300 eV and ions of 1-50 eV
+    in random directions (collision tests)."""
+    from paper_2402_08404_gb300 import synth
+    pop = synth.plasma(cfg, seed=seed)
+    rng = np.random.default_rng(seed + 1)
+    nn = len(pop["n"]["x"])
+    half = nn // 2
+    for c in ("x", "y", "z"):
+        pop["n"][c][half:2 * half] = pop["n"][c][:half]
+    for k, lo, hi, m in (("e", 20.0, 300.0, OC.M_E), ("i", 1.0, 50.0, OC.M_CU)):
+        n = len(pop[k]["x"])
+        src = rng.integers(0, nn, n)
+        for c in ("x", "y", "z"):
+            pop[k][c] = pop["n"][c][src].copy()
+        speed = np.sqrt(2 * rng.uniform(lo, hi, n) * OC.E_CHARGE / m)
+        u = rng.normal(size=(n, 3))
+        u /= np.linalg.norm(u, axis=1)[:, None]
+        for a, c in enumerate(("vx", "vy", "vz")):
+            pop[k][c] = (speed * u[:, a]).astype(np.float32)
+    return pop

@@ -13,7 +13,7 @@ from oracle import collide, elastic as EL, field, particles as P
 from oracle import constants as OC
 from paper_2402_08404_gb300 import synth
 
-from _util import SPECIES, assert_sp_equal, fixed_phi, grid_of, small_cfg, sorted_pop
+from _util import SPECIES, assert_sp_equal, colocated_population, fixed_phi, grid_of, small_cfg, sorted_pop
 
 pytestmark = pytest.mark.gpu
 
@@ -30,33 +30,11 @@ def pic():
     return m
 
 
-def _population(cfg, seed):
-    """Seeded plasma with the species brought together in cells: electrons and ions on neutral
-    positions, half the neutrals on the other half's, energetic electrons, fast ions."""
-    pop = synth.plasma(cfg, seed=seed)
-    rng = np.random.default_rng(seed + 1)
-    nn = len(pop["n"]["x"])
-    half = nn // 2
-    for c in ("x", "y", "z"):
-        pop["n"][c][half:2 * half] = pop["n"][c][:half]
-    for k, lo, hi, m in (("e", 20.0, 300.0, OC.M_E), ("i", 1.0, 50.0, OC.M_CU)):
-        n = len(pop[k]["x"])
-        src = rng.integers(0, nn, n)
-        for c in ("x", "y", "z"):
-            pop[k][c] = pop["n"][c][src].copy()
-        speed = np.sqrt(2 * rng.uniform(lo, hi, n) * OC.E_CHARGE / m)
-        u = rng.normal(size=(n, 3))
-        u /= np.linalg.norm(u, axis=1)[:, None]
-        for a, c in enumerate(("vx", "vy", "vz")):
-            pop[k][c] = (speed * u[:, a]).astype(np.float32)
-    return pop
-
-
 def _setup(pic, flags, V0=60.0, seed=12):
     cfg = small_cfg(n_sp=30000, w_min=1.0, **SIGMAS)
     g = grid_of(cfg)
     sim = pic.Pic(cfg, capacity=200_000, V0=V0, flags=flags)
-    pop = _population(cfg, seed)
+    pop = colocated_population(cfg, seed)
     phi = fixed_phi(field.solve_poisson(g, V0))
     sim.set_potential(phi)
     for s, (k, _, _) in enumerate(SPECIES):
