@@ -18,6 +18,7 @@ field      7-point Poisson operator and direct solve, node field E = -grad(phi) 
 particles  CIC gather, leapfrog push, DDA boundary test, stable cell sort, fixed-point deposit (Sec. 2.2)
 collide    impact ionization MCC with SP splitting (eq:colp, eq:du, Sec. 2.3.2) and ADK field ionization (eq:dfi)
 elastic    elastic e-Cu and Cu-Cu collisions (eq:newv, eq:du) and Cu+-Cu charge exchange (Table colls)
+merge      superparticle merging in over-full cells (Sec. 2.3.2)
 coulomb    binary Coulomb collisions e-e, e-Cu+, Cu+-Cu+ (Table colls, the cited small-angle method)
 emission   general thermal-field emission current and Nottingham heat (Sec. 2.3.1)
 surface    Clausius-Clapeyron evaporation, injection weights, sputtering, bombardment heat (Sec. 2.3.1-2.3.3)

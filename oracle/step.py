@@ -7,7 +7,8 @@ Order (Sec. 2.3.1 and Fig. newpic; the paper prints no pseudocode, this is the r
      (with an external circuit, prm circuit_R and circuit_C > 0: then the Shockley-Ramo current
      of the pushed e- and Cu+ and one Euler step of the RC circuit; the step's Poisson solve
      holds the anode at the new V_gap)
-  a4 stable cell sort of every species (survivors in previous order)
+  a4 stable cell sort of every species (survivors in previous order); with prm merge_max > 0,
+     SP merging in the over-full cells
   a5 impact ionization MCC (with prm "elastic": then e-Cu and Cu-Cu elastic collisions and
      Cu+-Cu charge exchange; with prm "coulomb": then e-e, e-Cu+ and Cu+-Cu+ Coulomb
      collisions; all on the sorted SPs), a6 direct field ionization
@@ -23,7 +24,7 @@ import math
 
 import numpy as np
 
-from . import circuit, collide, coulomb, elastic, emission, field, heat, particles as P, philox, surface
+from . import circuit, collide, coulomb, elastic, emission, field, heat, merge, particles as P, philox, surface
 from . import constants as C
 
 E_, N_, I_ = "e", "n", "i"
@@ -258,6 +259,9 @@ def step(st, emission_fn=None):
     # a4
     for k in st.sp:
         st.sp[k], st.off[k] = P.stable_sort(g, st.sp[k], alive[k])
+    if prm.get("merge_max", 0) > 0:
+        st.count["merged"] = sum(merge.merge_species(st.sp[k], st.off[k], prm["merge_max"], prm["w_max_units"])
+                                 for k in (E_, N_, I_))
     # a5
     ids = collide.Counter(st.next_id)
     ni, ne, ev = collide.impact_ionization(g, prm, st.sp[E_], st.off[E_], st.sp[N_], st.off[N_], st.step, ids)
