@@ -209,6 +209,9 @@ def run_ours(args):
         prod_flags |= pic.F_EXTRAPOLATE
     if args.coulomb:   # e-e, e-Cu+, Cu+-Cu+ Coulomb collisions (lnL = 10)
         prod_flags |= pic.F_COULOMB
+    if args.merge > 0:   # SP merging in cells above this many SPs of a species
+        cfg["merge_max"] = args.merge
+        prod_flags |= pic.F_MERGE
     plain_flags = pic.F_ALL & ~pic.F_SURROGATE & ~pic.F_MIXED_MG
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
@@ -350,6 +353,7 @@ def run_ours(args):
                                if args.elastic else None),
                    "coulomb": ({"e_e": d1["coulomb_ee"], "e_Cu+": d1["coulomb_ei"], "Cu+_Cu+": d1["coulomb_ii"]}
                                if args.coulomb else None),
+                   "merge": ({"merge_max": args.merge, "merged_last_step": d1["merged"]} if args.merge > 0 else None),
                    "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()}, "mg_cycles": d1["mg_cycles"],
                    "mg_cycles_per_step": (d1["mg_cycles_total"] - d0["mg_cycles_total"]) / args.steps,
                    "kernel_ms_per_step": kernel_ms,
@@ -541,6 +545,7 @@ def main():
     ap.add_argument("--elastic", action="store_true", help="step with elastic collisions and charge exchange")
     ap.add_argument("--extrapolate", action="store_true", help="start each solve from the time-extrapolated potential")
     ap.add_argument("--coulomb", action="store_true", help="step with Coulomb collisions between charged SPs")
+    ap.add_argument("--merge", type=int, default=0, help="merge SPs in cells above this many SPs of a species (0: off)")
     args = ap.parse_args()
     if args.impl == "reference":
         out = run_reference(args)

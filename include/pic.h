@@ -61,6 +61,7 @@ extern "C" {
 #define PIC_F_MIXED_MG 0x80u    /* a8: FP32 V-cycles with FP64 residual refinement (else FP64 V-cycles) */
 #define PIC_F_FAST_INTEGRAL 0x100u  /* a1: Gamow quadrature and turning points in FP32 (J, P_N to ~1e-5
                                        relative) in the step and in pic_emission_eval; else all FP64 */
+#define PIC_F_MERGE 0x4000u    /* a4: after the sort, SP merging in cells above merge_max SPs of a species */
 #define PIC_F_COULOMB 0x2000u  /* a5: then e-e, e-Cu+, Cu+-Cu+ Coulomb collisions (binary small-angle method) */
 #define PIC_F_EXTRAPOLATE 0x1000u /* pic_step starts each solve from 2 phi^n - phi^(n-1) instead of phi^n */
 #define PIC_F_ELASTIC 0x800u    /* a5: then elastic e-Cu and Cu-Cu collisions and Cu+-Cu charge exchange */
@@ -107,6 +108,7 @@ typedef struct {
   double sigma_el_nn;   /* m^2: Cu-Cu elastic cross section (<= 0: hard spheres pi (2 x 128 pm)^2) */
   double sigma_cx;      /* m^2: Cu+-Cu charge exchange cross section (<= 0: 5e-19, a constant stand-in) */
   double coulomb_log;   /* Coulomb logarithm of the Coulomb collisions (<= 0: 10) */
+  int merge_max;        /* SPs of a species per cell above which pairs merge (PIC_F_MERGE; <= 0: 32) */
 } pic_params_t;
 
 typedef struct {
@@ -132,6 +134,7 @@ typedef struct {
   int64_t elastic_en, elastic_nn, charge_exchanges;  /* colliding pairs this step (PIC_F_ELASTIC) */
   int64_t mg_cycles_total;  /* Poisson refinement cycles since create (both forms) */
   int64_t coulomb_ee, coulomb_ei, coulomb_ii;  /* pairs turned this step (PIC_F_COULOMB) */
+  int64_t merged;           /* SP pairs merged this step (PIC_F_MERGE) */
 } pic_diag_t;
 
 typedef struct pic_s pic_t;
@@ -198,6 +201,12 @@ int pic_emit(pic_t *h);        /* a1 emission + a2 evaporation/sputter injection
 int pic_push(pic_t *h);        /* a3 gather + leapfrog + boundary removal, ion impact records */
 int pic_sort(pic_t *h);        /* a4 stable cell sort of every species, dropping removed SPs */
 int pic_collide(pic_t *h);     /* a5 impact ionization MCC, then a6 field ionization (appends) */
+/* SP merging (Sec. 2.3.2) on cell-sorted SPs: in a cell holding N > merge_max SPs of a species the
+ * SPs at places 2m, 2m+1 merge for m < min(N - merge_max, N/2) into their centre of mass
+ * (w = w1 + w2, a = a1 mu/w2 + a2 mu/w1, mu = w1 w2/(w1 + w2)); the second keeps weight 0 until the
+ * next sort.  pic_step runs it after the sort when PIC_F_MERGE is set; PIC_E_INVALID without the
+ * flag or on unsorted SPs. */
+int pic_merge(pic_t *h);
 /* RC circuit (the circuit passage of Sec. 2.3.1, after ArcPIC): I_gap = sum over e- and Cu+ SPs of
  * q v . E0(x) (Shockley-Ramo, E0 the Laplace field with the anode at unit potential, gathered like
  * E), then V_gap += dt/C ((V0 - V_gap)/R - I_gap).  pic_step runs it after the push; the following

@@ -421,6 +421,61 @@ int stage_push(pic_t *h) {
   return launch_check(h, "push");
 }
 
+// ---- SP merging (Sec. 2.3.2) -------------------------------------------------------------------
+// In a cell holding N > M SPs of a species, the SPs at cell-sorted places 2m and 2m + 1 merge for
+// m < min(N - M, N/2): w = w1 + w2 and, with mu = w1 w2 / (w1 + w2), every position and velocity
+// component a = a1 mu/w2 + a2 mu/w1 (the centre of mass), in FP64 with one rounding per
+// operation in that order and one rounding to FP32.  Pairs holding a zero weight, or summing
+// above the weight cap, stay.  The merged SP keeps the first place and its id; the second keeps
+// weight 0 and leaves at the next sort.  The centre of mass lies in the cell, so the order and
+// the offsets stay valid.  One thread per cell (coalesced offset reads; cells above the cap are
+// rare).
+__device__ __forceinline__ float merge_comp(double w1, double w2, float a1, float a2) {
+  const double mu = __ddiv_rn(__dmul_rn(w1, w2), __dadd_rn(w1, w2));
+  return (float)__dadd_rn(__dmul_rn((double)a1, __ddiv_rn(mu, w2)), __dmul_rn((double)a2, __ddiv_rn(mu, w1)));
+}
+
+__global__ void __launch_bounds__(256) k_merge(SpeciesBuf p, const uint32_t *off, int64_t ncell, uint32_t M, int32_t wmax,
+                                               DevClock *clk) {
+  int done = 0;
+  const int64_t span = (ncell + 31) & ~31ll;
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < span; c += (int64_t)gridDim.x * blockDim.x) {
+    if (c >= ncell) continue;
+    const uint32_t o = off[c], N = off[c + 1] - o;
+    if (N <= M) continue;
+    const uint32_t nm = min(N - M, N / 2);
+    for (uint32_t m = 0; m < nm; ++m) {
+      const int64_t a = (int64_t)o + 2 * m, b = a + 1;
+      const int32_t w1 = p.w[a], w2 = p.w[b];
+      if (w1 <= 0 || w2 <= 0 || (int64_t)w1 + w2 > wmax) continue;
+      const double d1 = w1, d2 = w2;
+      p.x[a] = merge_comp(d1, d2, p.x[a], p.x[b]);
+      p.y[a] = merge_comp(d1, d2, p.y[a], p.y[b]);
+      p.z[a] = merge_comp(d1, d2, p.z[a], p.z[b]);
+      p.vx[a] = merge_comp(d1, d2, p.vx[a], p.vx[b]);
+      p.vy[a] = merge_comp(d1, d2, p.vy[a], p.vy[b]);
+      p.vz[a] = merge_comp(d1, d2, p.vz[a], p.vz[b]);
+      p.w[a] = w1 + w2;
+      p.w[b] = 0;
+      ++done;
+    }
+  }
+  for (int s = 16; s > 0; s >>= 1) done += __shfl_down_sync(0xffffffffu, done, s);
+  if ((threadIdx.x & 31) == 0 && done) atomicAdd((unsigned long long *)&clk->ctr[cMerged], (unsigned long long)done);
+}
+
+int stage_merge(pic_t *h) {
+  if (!(h->prm.flags & PIC_F_MERGE)) return PIC_OK;
+  for (int s = 0; s < 3; ++s) if (h->keys_valid[s]) return pic_fail(h, PIC_E_INVALID, "merging needs cell-sorted SPs");
+  const uint32_t M = h->prm.merge_max > 0 ? (uint32_t)h->prm.merge_max : 32u;
+  const int32_t wmax = h->prm.w_max_units > 0 ? h->prm.w_max_units : INT32_MAX;
+  h->nlaunch += 3;
+  KtScope kt_(h, kidMerge, 0);
+  for (int s = 0; s < 3; ++s)
+    k_merge<<<h->nsm * 8, kThreads, 0, h->stream>>>(h->sp[s].a, h->sp[s].off, h->ncell, M, wmax, h->clock);
+  return launch_check(h, "merge");
+}
+
 int stage_sort(pic_t *h) {
   int2 *long_list = h->long_list;
   int *long_n = h->long_n;

@@ -196,7 +196,7 @@ static T *alloc_n(pic_t *h, int64_t n) {
 namespace pic {
 const char *const kKernelNames[kidNum] = {
     "k_push", "k_keys", "k_scatter", "k_fix_short", "k_fix_mid", "k_fix_long", "k_gather", "k_scan_partial",
-    "k_scan_apply", "k_deposit", "k_mcc_count", "k_mcc_products", "k_elastic", "k_coulomb", "k_dfi_count", "k_dfi_products", "k_dirichlet",
+    "k_scan_apply", "k_deposit", "k_mcc_count", "k_mcc_products", "k_elastic", "k_coulomb", "k_merge", "k_dfi_count", "k_dfi_products", "k_dirichlet",
     "k_residual64", "k_norm_sum", "k_smooth", "k_smooth_first", "k_residual", "k_restrict", "k_prolong", "k_coarse", "k_vcycle_tail", "k_ramo",
     "k_correct", "k_efield", "k_face_field", "k_emit_surrogate", "k_emit_fallback", "k_emit_count", "k_emit_write",
     "k_inject_count", "k_inject_write", "k_mlp_forward", "k_heat"};
@@ -757,6 +757,14 @@ int pic_sort(pic_t *h) {
   return check_err(h);
 }
 
+int pic_merge(pic_t *h) {
+  if (!h) return PIC_E_INVALID;
+  if (!(h->prm.flags & PIC_F_MERGE)) return pic_fail(h, PIC_E_INVALID, "merging is off: set PIC_F_MERGE");
+  PIC_TRY(stage_merge(h));
+  PIC_CUDA(h, cudaStreamSynchronize(h->stream));
+  return check_err(h);
+}
+
 static int sort_one(pic_t *h, int s) {
   // sort only species s: mark the others as not needing work by sorting all (cheap at load time)
   (void)s;
@@ -839,6 +847,7 @@ static int step_body_graph(pic_t *h) {
   PIC_TRY(stage_push(h));
   PIC_TRY(stage_circuit(h));
   PIC_TRY(stage_sort(h));
+  PIC_TRY(stage_merge(h));
   PIC_TRY(stage_collide(h));
   PIC_TRY(stage_deposit(h));
   PIC_TRY(stage_extrapolate(h));
@@ -1246,6 +1255,7 @@ static int pic_step_eager(pic_t *h, int nsteps, int64_t step) {
     if (rc == PIC_OK) rc = stage_circuit(h);
     cudaEventRecord(ev[2], h->stream);
     if (rc == PIC_OK) rc = stage_sort(h);
+    if (rc == PIC_OK) rc = stage_merge(h);
     cudaEventRecord(ev[3], h->stream);
     if (rc == PIC_OK) rc = stage_collide(h);
     cudaEventRecord(ev[4], h->stream);
@@ -1337,6 +1347,7 @@ int pic_diagnostics(pic_t *h, pic_diag_t *out) {
   out->coulomb_ee = c.ctr[cCoulombEe];
   out->coulomb_ei = c.ctr[cCoulombEi];
   out->coulomb_ii = c.ctr[cCoulombIi];
+  out->merged = c.ctr[cMerged];
   out->ion_impacts = c.ctr[cIonImpacts];
   out->mg_cycles = h->last_solve_graph ? c.mg_cycles_last : h->last_mg_cycles;
   out->mg_residual = h->last_solve_graph ? (double)c.mg_rel_last : h->last_mg_res;

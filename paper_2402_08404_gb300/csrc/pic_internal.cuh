@@ -58,7 +58,7 @@ enum Purpose : uint32_t {
 // device counters (int64), indices
 enum Ctr {
   cEmitted = 0, cEvaporated, cSputtered, cImpactIon, cFieldIon, cRemovedE, cRemovedN, cRemovedI,
-  cIonImpacts, cWevals, cSurFaces, cElasticEn, cElasticNn, cChargeEx, cCoulombEe, cCoulombEi, cCoulombIi, cNum
+  cIonImpacts, cWevals, cSurFaces, cElasticEn, cElasticNn, cChargeEx, cCoulombEe, cCoulombEi, cCoulombIi, cMerged, cNum
 };
 
 // error bits set by kernels
@@ -292,7 +292,7 @@ namespace pic {
 // Kernels whose launches can be timed one by one (pic_set_kernel_timing); the order is the ABI's.
 enum Kid : int {
   kidPush = 0, kidKeys, kidScatter, kidFixShort, kidFixMid, kidFixLong, kidGather, kidScanPartial, kidScanApply,
-  kidDeposit, kidMccCount, kidMccProducts, kidElastic, kidCoulomb, kidDfiCount, kidDfiProducts, kidDirichlet, kidResidual64, kidNormSum,
+  kidDeposit, kidMccCount, kidMccProducts, kidElastic, kidCoulomb, kidMerge, kidDfiCount, kidDfiProducts, kidDirichlet, kidResidual64, kidNormSum,
   kidSmooth, kidSmoothFirst, kidResidual, kidRestrict, kidProlong, kidCoarse, kidTail, kidRamo, kidCorrect, kidEfield, kidFaceField,
   kidEmitSurrogate, kidEmitFallback, kidEmitCount, kidEmitWrite, kidInjectCount, kidInjectWrite, kidMlpForward,
   kidHeat, kidNum
@@ -369,6 +369,7 @@ int circuit_setup(pic_t *h, double V_L);
 int circuit_reset(pic_t *h);
 int stage_circuit(pic_t *h);
 int stage_extrapolate(pic_t *h);
+int stage_merge(pic_t *h);
 // heat (k_heat.cu)
 int stage_heat(pic_t *h);
 // emission surrogate (k_mlp.cu)

@@ -22,6 +22,7 @@ F_CIRCUIT = 0x400
 F_ELASTIC = 0x800
 F_EXTRAPOLATE = 0x1000
 F_COULOMB = 0x2000
+F_MERGE = 0x4000
 F_PRODUCTION = F_ALL | F_FAST_INTEGRAL     # surrogate, FP32 Gamow quadrature for its fallback, mixed MG
 
 QE = 1.602176634e-19
@@ -53,7 +54,7 @@ class Params(C.Structure):
                 ("n_heat", C.c_int), ("seed", C.c_uint64), ("flags", C.c_uint32), ("mg_tol", C.c_double),
                 ("mg_max_cycles", C.c_int), ("mg_sweeps", C.c_int), ("circuit_R", C.c_double),
                 ("circuit_C", C.c_double), ("sigma_el_en", C.c_double), ("sigma_el_nn", C.c_double),
-                ("sigma_cx", C.c_double), ("coulomb_log", C.c_double)]
+                ("sigma_cx", C.c_double), ("coulomb_log", C.c_double), ("merge_max", C.c_int)]
 
 
 class Diag(C.Structure):
@@ -67,7 +68,7 @@ class Diag(C.Structure):
                 ("surrogate_faces", C.c_int64), ("V_gap", C.c_double), ("I_gap", C.c_double),
                 ("I_tot", C.c_double), ("elastic_en", C.c_int64), ("elastic_nn", C.c_int64),
                 ("charge_exchanges", C.c_int64), ("mg_cycles_total", C.c_int64), ("coulomb_ee", C.c_int64),
-                ("coulomb_ei", C.c_int64), ("coulomb_ii", C.c_int64)]
+                ("coulomb_ei", C.c_int64), ("coulomb_ii", C.c_int64), ("merged", C.c_int64)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
@@ -90,7 +91,7 @@ def lib():
         L.pic_last_error.argtypes = [vp]
         L.pic_last_error.restype = C.c_char_p
         for name in ("pic_emit", "pic_push", "pic_sort", "pic_collide", "pic_deposit", "pic_solve_field", "pic_heat",
-                     "pic_circuit"):
+                     "pic_circuit", "pic_merge"):
             getattr(L, name).argtypes = [vp]
         L.pic_step.argtypes = [vp, i32]
         L.pic_load_particles.argtypes = [vp, i32] + [vp] * 8 + [i64]
@@ -187,7 +188,7 @@ class Pic:
                      float(mg_tol), int(mg_max_cycles), int(mg_sweeps), float(cfg.get("circuit_R", 0.0)),
                      float(cfg.get("circuit_C", 0.0)), float(cfg.get("sigma_el_en", 0.0)),
                      float(cfg.get("sigma_el_nn", 0.0)), float(cfg.get("sigma_cx", 0.0)),
-                     float(cfg.get("coulomb_log", 0.0)))
+                     float(cfg.get("coulomb_log", 0.0)), int(cfg.get("merge_max", 0)))
         h = C.c_void_p()
         a = self._alloc.alloc_fn if self._alloc else ALLOC_FN(0)
         f = self._alloc.free_fn if self._alloc else FREE_FN(0)
@@ -307,6 +308,9 @@ class Pic:
 
     def sort(self):
         self._check(lib().pic_sort(self.h))
+
+    def merge(self):
+        self._check(lib().pic_merge(self.h))
 
     def circuit(self):
         self._check(lib().pic_circuit(self.h))

@@ -51,4 +51,5 @@ def test_struct_layouts_match_header():
     assert [f for f, _ in pic.Params._fields_] == ["dt", "apex_field", "V0", "T0", "work_function", "w_min",
                                                     "w_max_units", "n_heat", "seed", "flags", "mg_tol",
                                                     "mg_max_cycles", "mg_sweeps", "circuit_R", "circuit_C",
-                                                    "sigma_el_en", "sigma_el_nn", "sigma_cx", "coulomb_log"]
+                                                    "sigma_el_en", "sigma_el_nn", "sigma_cx", "coulomb_log",
+                                                    "merge_max"]
