@@ -430,9 +430,8 @@ int stage_push(pic_t *h) {
 // weight 0 and leaves at the next sort.  The centre of mass lies in the cell, so the order and
 // the offsets stay valid.  One thread per cell (coalesced offset reads; cells above the cap are
 // rare).
-__device__ __forceinline__ float merge_comp(double w1, double w2, float a1, float a2) {
-  const double mu = __ddiv_rn(__dmul_rn(w1, w2), __dadd_rn(w1, w2));
-  return (float)__dadd_rn(__dmul_rn((double)a1, __ddiv_rn(mu, w2)), __dmul_rn((double)a2, __ddiv_rn(mu, w1)));
+__device__ __forceinline__ float merge_comp(double q1, double q2, float a1, float a2) {   // q1 = mu/w2, q2 = mu/w1
+  return (float)__dadd_rn(__dmul_rn((double)a1, q1), __dmul_rn((double)a2, q2));
 }
 
 __global__ void __launch_bounds__(256) k_merge(SpeciesBuf p, const uint32_t *off, int64_t ncell, uint32_t M, int32_t wmax,
@@ -449,12 +448,14 @@ __global__ void __launch_bounds__(256) k_merge(SpeciesBuf p, const uint32_t *off
       const int32_t w1 = p.w[a], w2 = p.w[b];
       if (w1 <= 0 || w2 <= 0 || (int64_t)w1 + w2 > wmax) continue;
       const double d1 = w1, d2 = w2;
-      p.x[a] = merge_comp(d1, d2, p.x[a], p.x[b]);
-      p.y[a] = merge_comp(d1, d2, p.y[a], p.y[b]);
-      p.z[a] = merge_comp(d1, d2, p.z[a], p.z[b]);
-      p.vx[a] = merge_comp(d1, d2, p.vx[a], p.vx[b]);
-      p.vy[a] = merge_comp(d1, d2, p.vy[a], p.vy[b]);
-      p.vz[a] = merge_comp(d1, d2, p.vz[a], p.vz[b]);
+      const double mu = __ddiv_rn(__dmul_rn(d1, d2), __dadd_rn(d1, d2));
+      const double q1 = __ddiv_rn(mu, d2), q2 = __ddiv_rn(mu, d1);
+      p.x[a] = merge_comp(q1, q2, p.x[a], p.x[b]);
+      p.y[a] = merge_comp(q1, q2, p.y[a], p.y[b]);
+      p.z[a] = merge_comp(q1, q2, p.z[a], p.z[b]);
+      p.vx[a] = merge_comp(q1, q2, p.vx[a], p.vx[b]);
+      p.vy[a] = merge_comp(q1, q2, p.vy[a], p.vy[b]);
+      p.vz[a] = merge_comp(q1, q2, p.vz[a], p.vz[b]);
       p.w[a] = w1 + w2;
       p.w[b] = 0;
       ++done;
