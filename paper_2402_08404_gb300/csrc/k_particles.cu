@@ -428,37 +428,55 @@ int stage_push(pic_t *h) {
 // operation in that order and one rounding to FP32.  Pairs holding a zero weight, or summing
 // above the weight cap, stay.  The merged SP keeps the first place and its id; the second keeps
 // weight 0 and leaves at the next sort.  The centre of mass lies in the cell, so the order and
-// the offsets stay valid.  One thread per cell (coalesced offset reads; cells above the cap are
-// rare).
+// the offsets stay valid.
 __device__ __forceinline__ float merge_comp(double q1, double q2, float a1, float a2) {   // q1 = mu/w2, q2 = mu/w1
   return (float)__dadd_rn(__dmul_rn((double)a1, q1), __dmul_rn((double)a2, q2));
 }
 
+__device__ __forceinline__ int merge_cell(SpeciesBuf &p, uint32_t o, uint32_t N, uint32_t M, int32_t wmax) {
+  int done = 0;
+  const uint32_t nm = min(N - M, N / 2);
+  for (uint32_t m = 0; m < nm; ++m) {
+    const int64_t a = (int64_t)o + 2 * m, b = a + 1;
+    const int32_t w1 = p.w[a], w2 = p.w[b];
+    if (w1 <= 0 || w2 <= 0 || (int64_t)w1 + w2 > wmax) continue;
+    const double d1 = w1, d2 = w2;
+    const double mu = __ddiv_rn(__dmul_rn(d1, d2), __dadd_rn(d1, d2));
+    const double q1 = __ddiv_rn(mu, d2), q2 = __ddiv_rn(mu, d1);
+    p.x[a] = merge_comp(q1, q2, p.x[a], p.x[b]);
+    p.y[a] = merge_comp(q1, q2, p.y[a], p.y[b]);
+    p.z[a] = merge_comp(q1, q2, p.z[a], p.z[b]);
+    p.vx[a] = merge_comp(q1, q2, p.vx[a], p.vx[b]);
+    p.vy[a] = merge_comp(q1, q2, p.vy[a], p.vy[b]);
+    p.vz[a] = merge_comp(q1, q2, p.vz[a], p.vz[b]);
+    p.w[a] = w1 + w2;
+    p.w[b] = 0;
+    ++done;
+  }
+  return done;
+}
+
+// Four consecutive cells per thread: one aligned 16-byte load of their offsets (c0 a multiple of
+// 4; the table holds ncell + 1 entries) and the fifth offset, so enough bytes are in flight to
+// stream the table.
 __global__ void __launch_bounds__(256) k_merge(SpeciesBuf p, const uint32_t *off, int64_t ncell, uint32_t M, int32_t wmax,
                                                DevClock *clk) {
   int done = 0;
-  const int64_t span = (ncell + 31) & ~31ll;
-  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < span; c += (int64_t)gridDim.x * blockDim.x) {
-    if (c >= ncell) continue;
-    const uint32_t o = off[c], N = off[c + 1] - o;
-    if (N <= M) continue;
-    const uint32_t nm = min(N - M, N / 2);
-    for (uint32_t m = 0; m < nm; ++m) {
-      const int64_t a = (int64_t)o + 2 * m, b = a + 1;
-      const int32_t w1 = p.w[a], w2 = p.w[b];
-      if (w1 <= 0 || w2 <= 0 || (int64_t)w1 + w2 > wmax) continue;
-      const double d1 = w1, d2 = w2;
-      const double mu = __ddiv_rn(__dmul_rn(d1, d2), __dadd_rn(d1, d2));
-      const double q1 = __ddiv_rn(mu, d2), q2 = __ddiv_rn(mu, d1);
-      p.x[a] = merge_comp(q1, q2, p.x[a], p.x[b]);
-      p.y[a] = merge_comp(q1, q2, p.y[a], p.y[b]);
-      p.z[a] = merge_comp(q1, q2, p.z[a], p.z[b]);
-      p.vx[a] = merge_comp(q1, q2, p.vx[a], p.vx[b]);
-      p.vy[a] = merge_comp(q1, q2, p.vy[a], p.vy[b]);
-      p.vz[a] = merge_comp(q1, q2, p.vz[a], p.vz[b]);
-      p.w[a] = w1 + w2;
-      p.w[b] = 0;
-      ++done;
+  const int64_t ngroup = (ncell + 3) >> 2;
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < ngroup; g += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c0 = g << 2;
+    uint32_t o[5];
+    if (c0 + 4 <= ncell) {
+      const uint4 v = *reinterpret_cast<const uint4 *>(off + c0);
+      o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w; o[4] = off[c0 + 4];
+    } else {
+      for (int j = 0; j < 5; ++j) o[j] = off[min<int64_t>(c0 + j, ncell)];
+    }
+    if (o[4] - o[0] <= M) continue;   // four cells together within the cap: none above it
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const uint32_t N = o[j + 1] - o[j];
+      if (c0 + j < ncell && N > M) done += merge_cell(p, o[j], N, M, wmax);
     }
   }
   for (int s = 16; s > 0; s >>= 1) done += __shfl_down_sync(0xffffffffu, done, s);
