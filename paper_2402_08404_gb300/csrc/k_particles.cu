@@ -470,7 +470,7 @@ __global__ void __launch_bounds__(256) k_merge(SpeciesBuf p, const uint32_t *off
       const uint4 v = *reinterpret_cast<const uint4 *>(off + c0);
       o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w; o[4] = off[c0 + 4];
     } else {
-      for (int j = 0; j < 5; ++j) o[j] = off[min<int64_t>(c0 + j, ncell)];
+      for (int j = 0; j < 5; ++j) o[j] = off[c0 + j < ncell ? c0 + j : ncell];
     }
     if (o[4] - o[0] <= M) continue;   // four cells together within the cap: none above it
 #pragma unroll
