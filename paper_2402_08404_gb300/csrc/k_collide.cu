@@ -650,7 +650,7 @@ __device__ __forceinline__ void co_turn(const CoPass &cp, const ElPair &pr, int6
 }
 
 // One pass: one item per sorted SP of species A (whole warps: the cell's pairing word is shared).
-__global__ void __launch_bounds__(256) k_coulomb(CoPass cp, uint64_t seed, DevClock *clk, int ctr) {
+__global__ void __launch_bounds__(256, 4) k_coulomb(CoPass cp, uint64_t seed, DevClock *clk, int ctr) {
   const ElPass &ps = cp.ps;
   const int64_t n = clk->n_sorted[ps.sa];
   const int64_t step = clk->step;
