@@ -433,11 +433,20 @@ __device__ __forceinline__ float merge_comp(double q1, double q2, float a1, floa
   return (float)__dadd_rn(__dmul_rn((double)a1, q1), __dmul_rn((double)a2, q2));
 }
 
-__device__ __forceinline__ int merge_cell(SpeciesBuf &p, uint32_t o, uint32_t N, uint32_t M, int32_t wmax) {
+// One work item per sorted SP (its cell from the sort's per-position key): the SP at an even
+// place 2m of a cell above the cap merges with its successor when m < min(N - M, N/2), so the
+// pairs of a dense cell spread over many threads.
+__global__ void __launch_bounds__(256) k_merge(SpeciesBuf p, const uint32_t *off, const uint32_t *skey, int s, uint32_t M,
+                                               int32_t wmax, DevClock *clk) {
+  const int64_t n = clk->n_sorted[s];
   int done = 0;
-  const uint32_t nm = min(N - M, N / 2);
-  for (uint32_t m = 0; m < nm; ++m) {
-    const int64_t a = (int64_t)o + 2 * m, b = a + 1;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t c = skey[t];
+    const uint32_t o = off[c], N = off[c + 1] - o;
+    if (N <= M) continue;
+    const uint32_t q = (uint32_t)(t - o);
+    if ((q & 1u) || q / 2 >= min(N - M, N / 2)) continue;
+    const int64_t a = t, b = t + 1;
     const int32_t w1 = p.w[a], w2 = p.w[b];
     if (w1 <= 0 || w2 <= 0 || (int64_t)w1 + w2 > wmax) continue;
     const double d1 = w1, d2 = w2;
@@ -453,33 +462,7 @@ __device__ __forceinline__ int merge_cell(SpeciesBuf &p, uint32_t o, uint32_t N,
     p.w[b] = 0;
     ++done;
   }
-  return done;
-}
-
-// Four consecutive cells per thread: one aligned 16-byte load of their offsets (c0 a multiple of
-// 4; the table holds ncell + 1 entries) and the fifth offset, so enough bytes are in flight to
-// stream the table.
-__global__ void __launch_bounds__(256) k_merge(SpeciesBuf p, const uint32_t *off, int64_t ncell, uint32_t M, int32_t wmax,
-                                               DevClock *clk) {
-  int done = 0;
-  const int64_t ngroup = (ncell + 3) >> 2;
-  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < ngroup; g += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t c0 = g << 2;
-    uint32_t o[5];
-    if (c0 + 4 <= ncell) {
-      const uint4 v = *reinterpret_cast<const uint4 *>(off + c0);
-      o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w; o[4] = off[c0 + 4];
-    } else {
-      for (int j = 0; j < 5; ++j) o[j] = off[c0 + j < ncell ? c0 + j : ncell];
-    }
-    if (o[4] - o[0] <= M) continue;   // four cells together within the cap: none above it
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const uint32_t N = o[j + 1] - o[j];
-      if (c0 + j < ncell && N > M) done += merge_cell(p, o[j], N, M, wmax);
-    }
-  }
-  for (int s = 16; s > 0; s >>= 1) done += __shfl_down_sync(0xffffffffu, done, s);
+  for (int sh = 16; sh > 0; sh >>= 1) done += __shfl_down_sync(0xffffffffu, done, sh);
   if ((threadIdx.x & 31) == 0 && done) atomicAdd((unsigned long long *)&clk->ctr[cMerged], (unsigned long long)done);
 }
 
@@ -491,7 +474,7 @@ int stage_merge(pic_t *h) {
   h->nlaunch += 3;
   KtScope kt_(h, kidMerge, 0);
   for (int s = 0; s < 3; ++s)
-    k_merge<<<h->nsm * 8, kThreads, 0, h->stream>>>(h->sp[s].a, h->sp[s].off, h->ncell, M, wmax, h->clock);
+    k_merge<<<h->nsm * 8, kThreads, 0, h->stream>>>(h->sp[s].a, h->sp[s].off, h->sp[s].skey, s, M, wmax, h->clock);
   return launch_check(h, "merge");
 }
 
