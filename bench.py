@@ -361,6 +361,7 @@ def run_ours(args):
                        "val_rms_dlog10J": round(sur["val_rms_dlog10J"], 4),
                        "valid_sample_fraction": round(sur["valid_sample_fraction"], 3),
                        "faces_served_per_step": round(sur_faces / max(sim.nface, 1), 4),
+                       "fallback_faces_last_step": {"outside_range": d1["fallback_range"], "bin_not_validated": d1["fallback_bin"]},
                        "train_s": round((sur["ms_data"] + sur["ms_train"]) / 1e3, 2)},
                    "plain_form": plain, "graph_form": graph, "autotune": tune},
         "roofline": roof,

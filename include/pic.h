@@ -135,6 +135,8 @@ typedef struct {
   int64_t mg_cycles_total;  /* Poisson refinement cycles since create (both forms) */
   int64_t coulomb_ee, coulomb_ei, coulomb_ii;  /* pairs turned this step (PIC_F_COULOMB) */
   int64_t merged;           /* SP pairs merged this step (PIC_F_MERGE) */
+  int64_t fallback_range, fallback_bin;  /* faces the surrogate left to the integral this step:
+                                            outside its trained range / in a bin that failed validation */
 } pic_diag_t;
 
 typedef struct pic_s pic_t;

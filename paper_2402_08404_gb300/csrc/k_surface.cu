@@ -146,6 +146,8 @@ __global__ void k_emit_surrogate(EmitArgs a) {
       }
       if (!use) {
         a.fb_list[atomicAdd(a.fb_n, 1)] = (int32_t)f;
+        // why the integral runs: outside the trained range, or in a bin that failed validation
+        atomicAdd((unsigned long long *)&a.clk->ctr[e == 0 ? cFbRange : cFbBin], 1ull);
         continue;
       }
       surrogate_out(a.Y, f, ap, &J, &P);

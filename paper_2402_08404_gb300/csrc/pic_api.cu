@@ -1348,6 +1348,8 @@ int pic_diagnostics(pic_t *h, pic_diag_t *out) {
   out->coulomb_ei = c.ctr[cCoulombEi];
   out->coulomb_ii = c.ctr[cCoulombIi];
   out->merged = c.ctr[cMerged];
+  out->fallback_range = c.ctr[cFbRange];
+  out->fallback_bin = c.ctr[cFbBin];
   out->ion_impacts = c.ctr[cIonImpacts];
   out->mg_cycles = h->last_solve_graph ? c.mg_cycles_last : h->last_mg_cycles;
   out->mg_residual = h->last_solve_graph ? (double)c.mg_rel_last : h->last_mg_res;

@@ -58,7 +58,7 @@ enum Purpose : uint32_t {
 // device counters (int64), indices
 enum Ctr {
   cEmitted = 0, cEvaporated, cSputtered, cImpactIon, cFieldIon, cRemovedE, cRemovedN, cRemovedI,
-  cIonImpacts, cWevals, cSurFaces, cElasticEn, cElasticNn, cChargeEx, cCoulombEe, cCoulombEi, cCoulombIi, cMerged, cNum
+  cIonImpacts, cWevals, cSurFaces, cElasticEn, cElasticNn, cChargeEx, cCoulombEe, cCoulombEi, cCoulombIi, cMerged, cFbRange, cFbBin, cNum
 };
 
 // error bits set by kernels

@@ -68,7 +68,8 @@ class Diag(C.Structure):
                 ("surrogate_faces", C.c_int64), ("V_gap", C.c_double), ("I_gap", C.c_double),
                 ("I_tot", C.c_double), ("elastic_en", C.c_int64), ("elastic_nn", C.c_int64),
                 ("charge_exchanges", C.c_int64), ("mg_cycles_total", C.c_int64), ("coulomb_ee", C.c_int64),
-                ("coulomb_ei", C.c_int64), ("coulomb_ii", C.c_int64), ("merged", C.c_int64)]
+                ("coulomb_ei", C.c_int64), ("coulomb_ii", C.c_int64), ("merged", C.c_int64),
+                ("fallback_range", C.c_int64), ("fallback_bin", C.c_int64)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
