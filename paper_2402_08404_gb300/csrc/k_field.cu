@@ -779,22 +779,6 @@ __global__ void k_correct(long long *phi, const T *u, const uint8_t *dir, Lv L) 
 // f32(1/dx) on the z planes) in f32.  The difference of two fixed-point values is an exact
 // int64; its f32 rounding equals that of the exact FP64 difference, and the 2^-40 folds into the
 // f32 factor exactly, so no FP64 operation is needed.
-// RN(d) of an int64 d with 32-bit conversions only (the 64-bit conversion runs on the FP64 pipe,
-// which is narrow on this GPU): |d| < 2^31 converts directly; otherwise the top 30 bits of |d|
-// and one sticky bit for the rest form a 31-bit integer whose rounding to 24 bits is that of |d|
-// (the guard bit lies inside the top 30 bits), and the power-of-two scale is exact.  Round to
-// nearest is symmetric, so the sign goes back on at the end.
-__device__ __forceinline__ float ll2f_rn(long long d) {
-  if (d >= -2147483647LL && d <= 2147483647LL) return __int2float_rn((int)d);
-  const unsigned long long a = d < 0 ? 0ull - (unsigned long long)d : (unsigned long long)d;
-  const int sh = 64 - __clzll((long long)a) - 30;   // >= 2
-  const unsigned int v = (unsigned int)(a >> sh);
-  const unsigned int sticky = (a & ((1ull << sh) - 1ull)) != 0ull ? 1u : 0u;
-  const float f = __int2float_rn((int)((v << 1) | sticky));
-  const float r = __fmul_rn(f, __int_as_float((127 + sh - 1) << 23));   // 2^(sh-1), exact
-  return d < 0 ? -r : r;
-}
-
 __global__ void __launch_bounds__(256) k_efield(const long long *phi, float4 *E, int nx, int ny, int nz, float c2,
                                                 float c1) {
   NODE_IJK(nx, ny)
@@ -806,9 +790,9 @@ __global__ void __launch_bounds__(256) k_efield(const long long *phi, float4 *E,
   const long long dy = phi[(int64_t)k * sz + (int64_t)jm * sy + i] - phi[(int64_t)k * sz + (int64_t)jp * sy + i];
   const long long dz = k == 0 ? phi[n] - phi[n + sz] : k == nz ? phi[n - sz] - phi[n] : phi[n - sz] - phi[n + sz];
   float4 e;
-  e.x = __fmul_rn(ll2f_rn(dx), c2);
-  e.y = __fmul_rn(ll2f_rn(dy), c2);
-  e.z = __fmul_rn(ll2f_rn(dz), k == 0 || k == nz ? c1 : c2);
+  e.x = __fmul_rn(__ll2float_rn(dx), c2);
+  e.y = __fmul_rn(__ll2float_rn(dy), c2);
+  e.z = __fmul_rn(__ll2float_rn(dz), k == 0 || k == nz ? c1 : c2);
   e.w = 0.f;
   E[n] = e;
 }
