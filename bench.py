@@ -183,6 +183,19 @@ def timed_steps(sim, stream, steps, clk=None):
     return e0.elapsed_time(e1), d0, d1
 
 
+def reduce_over_ranks(dist, elapsed_ms, updates, e2e_rate, device):
+    """Whole-job numbers of N replicas: the slowest rank's time and the work summed over ranks
+    (updates in the timed region, end-to-end update rates).  dist None: one process."""
+    if dist is None:
+        return elapsed_ms, updates, e2e_rate
+    import torch
+    t = torch.tensor([elapsed_ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    u = torch.tensor([updates, e2e_rate], device=device, dtype=torch.float64)
+    dist.all_reduce(u)
+    return t.item(), u[0].item(), u[1].item()
+
+
 def run_ours(args):
     import torch
     rank = int(os.environ.get("RANK", "0"))
@@ -294,16 +307,8 @@ def run_ours(args):
         torch.cuda.synchronize()
         e2e_s = max(time.perf_counter() - t0, 1e-9)
     # max time over ranks, sum of work
-    times = [elapsed_ms]
-    tot_updates = updates
-    tot_e2e = e2e_updates / e2e_s
-    if dist:
-        t = torch.tensor([elapsed_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        u = torch.tensor([updates, e2e_updates / e2e_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(u)
-        times = [t.item()]
-        tot_updates, tot_e2e = u[0].item(), u[1].item()
+    t_max, tot_updates, tot_e2e = reduce_over_ranks(dist, elapsed_ms, updates, e2e_updates / e2e_s, "cuda")
+    times = [t_max]
     if rank != 0:
         if dist:
             dist.destroy_process_group()
