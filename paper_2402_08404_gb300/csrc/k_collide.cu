@@ -1,5 +1,8 @@
 // Monte Carlo collisions: impact ionization Cu + e -> Cu+ + 2e with SP splitting (Sec. 2.2,
-// eq:colp, eq:du, Sec. 2.3.2) and direct field ionization of neutrals (eq:dfi, Sec. 2.3.4).
+// eq:colp, eq:du, Sec. 2.3.2) and direct field ionization of neutrals (eq:dfi, Sec. 2.3.4);
+// with their flags, elastic e-Cu and Cu-Cu collisions and Cu+-Cu charge exchange (eq:newv,
+// with splitting) and binary Coulomb collisions between charged SPs (Table colls), in the
+// order impact ionization, elastic passes, Coulomb passes, field ionization.
 //
 // Pairing in a cell with N_e electron SPs and N_n neutral SPs: the species with fewer SPs (tie:
 // electrons) is the projectile; projectile k meets target (k + o_c) mod N_t, o_c =
