@@ -478,33 +478,64 @@ int stage_merge(pic_t *h) {
   return launch_check(h, "merge");
 }
 
-int stage_sort(pic_t *h) {
+// Loaded SPs must lie inside the domain and outside the tip: the smallest offending index of
+// each kind (bad[0]: outside, bad[1]: inside the tip; all ones when there is none).
+__global__ void k_validate(SpeciesBuf p, int64_t n, const uint8_t *solid, int nx, int ny, int nz,
+                           unsigned long long *bad) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float x = p.x[i], y = p.y[i], z = p.z[i];
+    if (!(x >= 0.f && x < (float)nx && y >= 0.f && y < (float)ny && z >= 0.f && z < (float)nz))
+      atomicMin(&bad[0], (unsigned long long)i);
+    else if (solid[cell_index((int)floorf(x), (int)floorf(y), (int)floorf(z), nx, ny)])
+      atomicMin(&bad[1], (unsigned long long)i);
+  }
+}
+
+int validate_loaded(pic_t *h, const SpeciesBuf &p, int64_t n) {
+  unsigned long long *bad = (unsigned long long *)(h->tmp_len + 14);
+  PIC_CUDA(h, cudaMemsetAsync(bad, 0xff, 2 * sizeof(unsigned long long), h->stream));
+  ++h->nlaunch;
+  k_validate<<<particle_grid(h), kThreads, 0, h->stream>>>(p, n, h->solid, h->nx, h->ny, h->nz, bad);
+  unsigned long long hb[2];
+  PIC_CUDA(h, cudaMemcpyAsync(hb, bad, sizeof hb, cudaMemcpyDeviceToHost, h->stream));
+  PIC_CUDA(h, cudaStreamSynchronize(h->stream));
+  if (hb[0] != ~0ull) return pic_fail(h, PIC_E_INVALID, "SP " + std::to_string(hb[0]) + " outside the domain");
+  if (hb[1] != ~0ull) return pic_fail(h, PIC_E_INVALID, "SP " + std::to_string(hb[1]) + " inside the tip");
+  return PIC_OK;
+}
+
+// Counting sort of one species by cell: scan of the per-cell counts, scatter, the fix-ups that
+// make the order stable, gather into the other buffer, swap.
+int sort_species(pic_t *h, int s) {
   int2 *long_list = h->long_list;
   int *long_n = h->long_n;
   const int long_cap = kLongCap;
-  for (int s = 0; s < 3; ++s) {
-    Species &S = h->sp[s];
-    if (!h->keys_valid[s]) PIC_TRY(stage_keys(h, s));
-    PIC_TRY(scan_u32(h, S.cnt, S.off, h->ncell, nullptr, S.off + h->ncell));
-    ++h->nlaunch;
-    { KtScope kt_(h, kidScatter, 0); k_scatter<<<particle_grid(h), kThreads, 0, h->stream>>>(S.key, S.cnt, S.off, S.perm, S.skey, h->clock, s); }
-    PIC_CUDA(h, cudaMemsetAsync(long_n, 0, 2 * sizeof(int), h->stream));   // long_n[0]: long, [1]: mid
-    ++h->nlaunch;
-    { KtScope kt_(h, kidFixShort, 0); k_fix_short<<<particle_grid(h), kThreads, 0, h->stream>>>(S.skey, S.off, S.perm, h->ncell, h->mid_list,
-                                                              long_n + 1, (int)h->mid_cap, long_list, long_n,
-                                                              long_cap, h->clock); }
-    ++h->nlaunch;
-    { KtScope kt_(h, kidFixMid, 0); k_fix_mid<<<particle_grid(h), kThreads, 0, h->stream>>>(S.perm, h->mid_list, long_n + 1, (int)h->mid_cap); }
-    ++h->nlaunch;
-    { KtScope kt_(h, kidFixLong, 0); k_fix_long<<<h->nsm, 1024, 0, h->stream>>>(S.perm, long_list, long_n, long_cap); }
-    ++h->nlaunch;
-    { KtScope kt_(h, kidGather, 0); k_gather<<<particle_grid(h), kThreads, 0, h->stream>>>(S.a, S.b, S.perm, S.off, h->ncell); }
-    ++h->nlaunch;
-    k_set_count<<<1, 1, 0, h->stream>>>(h->clock, s, S.off, h->ncell);
-    std::swap(S.a, S.b);
-    h->keys_valid[s] = false;
-  }
+  Species &S = h->sp[s];
+  if (!h->keys_valid[s]) PIC_TRY(stage_keys(h, s));
+  PIC_TRY(scan_u32(h, S.cnt, S.off, h->ncell, nullptr, S.off + h->ncell));
+  ++h->nlaunch;
+  { KtScope kt_(h, kidScatter, 0); k_scatter<<<particle_grid(h), kThreads, 0, h->stream>>>(S.key, S.cnt, S.off, S.perm, S.skey, h->clock, s); }
+  PIC_CUDA(h, cudaMemsetAsync(long_n, 0, 2 * sizeof(int), h->stream));   // long_n[0]: long, [1]: mid
+  ++h->nlaunch;
+  { KtScope kt_(h, kidFixShort, 0); k_fix_short<<<particle_grid(h), kThreads, 0, h->stream>>>(S.skey, S.off, S.perm, h->ncell, h->mid_list,
+                                                            long_n + 1, (int)h->mid_cap, long_list, long_n,
+                                                            long_cap, h->clock); }
+  ++h->nlaunch;
+  { KtScope kt_(h, kidFixMid, 0); k_fix_mid<<<particle_grid(h), kThreads, 0, h->stream>>>(S.perm, h->mid_list, long_n + 1, (int)h->mid_cap); }
+  ++h->nlaunch;
+  { KtScope kt_(h, kidFixLong, 0); k_fix_long<<<h->nsm, 1024, 0, h->stream>>>(S.perm, long_list, long_n, long_cap); }
+  ++h->nlaunch;
+  { KtScope kt_(h, kidGather, 0); k_gather<<<particle_grid(h), kThreads, 0, h->stream>>>(S.a, S.b, S.perm, S.off, h->ncell); }
+  ++h->nlaunch;
+  k_set_count<<<1, 1, 0, h->stream>>>(h->clock, s, S.off, h->ncell);
+  std::swap(S.a, S.b);
+  h->keys_valid[s] = false;
   return launch_check(h, "sort");
+}
+
+int stage_sort(pic_t *h) {
+  for (int s = 0; s < 3; ++s) PIC_TRY(sort_species(h, s));
+  return PIC_OK;
 }
 
 int stage_deposit(pic_t *h) {

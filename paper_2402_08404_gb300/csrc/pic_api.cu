@@ -536,7 +536,6 @@ int pic_set_clock(pic_t *h, int64_t step, int64_t next_id) {
   return PIC_OK;
 }
 
-static int sort_one(pic_t *h, int s);
 
 int pic_load_particles(pic_t *h, int s, const float *x, const float *y, const float *z, const float *vx, const float *vy,
                        const float *vz, const int32_t *w, const uint64_t *id, int64_t n) {
@@ -544,29 +543,25 @@ int pic_load_particles(pic_t *h, int s, const float *x, const float *y, const fl
   Species &S = h->sp[s];
   if (n > S.cap) return pic_fail(h, PIC_E_CAPACITY, "load exceeds the species capacity");
   if (n > 0 && (!x || !y || !z || !vx || !vy || !vz || !w || !id)) return PIC_E_INVALID;
-  // validation: inside the domain and outside the tip (host copy of the solid mask)
-  const std::vector<uint8_t> &solid = h->solid_host;
-  for (int64_t p = 0; p < n; ++p) {
-    if (!(x[p] >= 0 && x[p] < h->nx && y[p] >= 0 && y[p] < h->ny && z[p] >= 0 && z[p] < h->nz))
-      return pic_fail(h, PIC_E_INVALID, "SP " + std::to_string(p) + " outside the domain");
-    if (solid[cell_index((int)floorf(x[p]), (int)floorf(y[p]), (int)floorf(z[p]), h->nx, h->ny)])
-      return pic_fail(h, PIC_E_INVALID, "SP " + std::to_string(p) + " inside the tip");
-  }
+  // the new SPs go to the scratch buffer first and replace the current ones only once the device
+  // has checked that every one lies inside the domain and outside the tip
   cudaStream_t st = h->stream;
   if (n) {
-    PIC_CUDA(h, cudaMemcpyAsync(S.a.x, x, n * 4, cudaMemcpyHostToDevice, st));
-    PIC_CUDA(h, cudaMemcpyAsync(S.a.y, y, n * 4, cudaMemcpyHostToDevice, st));
-    PIC_CUDA(h, cudaMemcpyAsync(S.a.z, z, n * 4, cudaMemcpyHostToDevice, st));
-    PIC_CUDA(h, cudaMemcpyAsync(S.a.vx, vx, n * 4, cudaMemcpyHostToDevice, st));
-    PIC_CUDA(h, cudaMemcpyAsync(S.a.vy, vy, n * 4, cudaMemcpyHostToDevice, st));
-    PIC_CUDA(h, cudaMemcpyAsync(S.a.vz, vz, n * 4, cudaMemcpyHostToDevice, st));
-    PIC_CUDA(h, cudaMemcpyAsync(S.a.w, w, n * 4, cudaMemcpyHostToDevice, st));
-    PIC_CUDA(h, cudaMemcpyAsync(S.a.id, id, n * 8, cudaMemcpyHostToDevice, st));
+    PIC_CUDA(h, cudaMemcpyAsync(S.b.x, x, n * 4, cudaMemcpyHostToDevice, st));
+    PIC_CUDA(h, cudaMemcpyAsync(S.b.y, y, n * 4, cudaMemcpyHostToDevice, st));
+    PIC_CUDA(h, cudaMemcpyAsync(S.b.z, z, n * 4, cudaMemcpyHostToDevice, st));
+    PIC_CUDA(h, cudaMemcpyAsync(S.b.vx, vx, n * 4, cudaMemcpyHostToDevice, st));
+    PIC_CUDA(h, cudaMemcpyAsync(S.b.vy, vy, n * 4, cudaMemcpyHostToDevice, st));
+    PIC_CUDA(h, cudaMemcpyAsync(S.b.vz, vz, n * 4, cudaMemcpyHostToDevice, st));
+    PIC_CUDA(h, cudaMemcpyAsync(S.b.w, w, n * 4, cudaMemcpyHostToDevice, st));
+    PIC_CUDA(h, cudaMemcpyAsync(S.b.id, id, n * 8, cudaMemcpyHostToDevice, st));
+    PIC_TRY(validate_loaded(h, S.b, n));
   }
+  std::swap(S.a, S.b);
   PIC_CUDA(h, cudaMemcpyAsync(&h->clock->n[s], &n, 8, cudaMemcpyHostToDevice, st));
   PIC_CUDA(h, cudaStreamSynchronize(st));
-  PIC_TRY(stage_keys(h, s));
-  PIC_TRY(sort_one(h, s));
+  PIC_TRY(stage_keys(h, s));   // clears the counts a push may have left, then counts the new SPs
+  PIC_TRY(sort_species(h, s));
   return check_err(h);
 }
 
@@ -726,7 +721,6 @@ int pic_set_face_accumulators(pic_t *h, const double *evap, const double *heat, 
 }
 
 // ---- stages -------------------------------------------------------------------------------
-static int sort_one(pic_t *h, int s);
 int pic_sort(pic_t *h);
 
 int pic_set_flags(pic_t *h, uint32_t flags) {
@@ -765,11 +759,6 @@ int pic_merge(pic_t *h) {
   return check_err(h);
 }
 
-static int sort_one(pic_t *h, int s) {
-  // sort only species s: mark the others as not needing work by sorting all (cheap at load time)
-  (void)s;
-  return stage_sort(h);
-}
 
 int pic_circuit(pic_t *h) {
   if (!h) return PIC_E_INVALID;

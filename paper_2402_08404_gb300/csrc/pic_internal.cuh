@@ -370,6 +370,8 @@ int circuit_reset(pic_t *h);
 int stage_circuit(pic_t *h);
 int stage_extrapolate(pic_t *h);
 int stage_merge(pic_t *h);
+int sort_species(pic_t *h, int s);
+int validate_loaded(pic_t *h, const SpeciesBuf &p, int64_t n);
 // heat (k_heat.cu)
 int stage_heat(pic_t *h);
 // emission surrogate (k_mlp.cu)
