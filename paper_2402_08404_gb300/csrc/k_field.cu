@@ -139,6 +139,17 @@ __global__ void __launch_bounds__(kSlotThreads) k_smooth(T *u, const T *f, const
   const uint8_t *dc = dirs + (size_t)c * L.nper + base;
   const int P = (int)L.P;
   const int ojm = j > 0 ? -L.Xh : L.Xh, ojp = j < L.ny ? L.Xh : -L.Xh;
+  // x-neighbour offsets (mirrored at the walls) for the two node parities along z; plane p has
+  // parity par0 ^ (p & 1), known at compile time in the unrolled loop
+  const int par0 = (j + k0 + c) & 1;
+  int oxm[2], oxp[2];
+#pragma unroll
+  for (int e = 0; e < 2; ++e) {
+    const int i = 2 * t + (par0 ^ e);
+    const int im = i > 0 ? i - 1 : 1, ip = i < L.nx ? i + 1 : L.nx - 1;
+    oxm[e] = (im >> 1) - t;
+    oxp[e] = (ip >> 1) - t;
+  }
   T v[KZ];
   uint8_t d[KZ];
 #pragma unroll
@@ -152,9 +163,7 @@ __global__ void __launch_bounds__(kSlotThreads) k_smooth(T *u, const T *f, const
       if (first) {
         v[p] = h2 * fc[o];
       } else {
-        const int i = 2 * t + ((j + k + c) & 1);
-        const int im = i > 0 ? i - 1 : 1, ip = i < L.nx ? i + 1 : L.nx - 1;
-        v[p] = uo[o + (im >> 1) - t] + uo[o + (ip >> 1) - t] + uo[o + ojm] + uo[o + ojp] + uo[o - P] + uo[o + P] +
+        v[p] = uo[o + oxm[p & 1]] + uo[o + oxp[p & 1]] + uo[o + ojm] + uo[o + ojp] + uo[o - P] + uo[o + P] +
                h2 * fc[o];
       }
     }
