@@ -186,6 +186,16 @@ __global__ void __launch_bounds__(kSlotThreads) k_residual(const T *u, const T *
   const int j = (int)fdiv(q, L.xd), t = (int)(q - (uint32_t)j * (uint32_t)L.Xh);
   const T *uo = u + L.nper;
   const int64_t ojm = j > 0 ? -(int64_t)L.Xh : (int64_t)L.Xh, ojp = j < L.ny ? (int64_t)L.Xh : -(int64_t)L.Xh;
+  // x-neighbour offsets of the two node parities along z (plane p: parity par0 ^ (p & 1))
+  const int par0 = (j + k0) & 1;
+  int oxm[2], oxp[2];
+#pragma unroll
+  for (int e = 0; e < 2; ++e) {
+    const int i = 2 * t + (par0 ^ e);
+    const int im = i > 0 ? i - 1 : 1, ip = i < L.nx ? i + 1 : L.nx - 1;
+    oxm[e] = (im >> 1) - t;
+    oxp[e] = (ip >> 1) - t;
+  }
   T v[kKZ];
   uint8_t d[kKZ];
 #pragma unroll
@@ -195,11 +205,8 @@ __global__ void __launch_bounds__(kSlotThreads) k_residual(const T *u, const T *
     d[p] = 1;
     if (k > 0 && k < L.nz) {
       const int64_t m = (int64_t)k * L.P + q;
-      const int i = 2 * t + ((j + k) & 1);
-      const int im = i > 0 ? i - 1 : 1, ip = i < L.nx ? i + 1 : L.nx - 1;
-      const int64_t rb = m - t;
       d[p] = dirs[m];
-      const T nb = uo[rb + (im >> 1)] + uo[rb + (ip >> 1)] + uo[m + ojm] + uo[m + ojp] + uo[m - L.P] + uo[m + L.P];
+      const T nb = uo[m + oxm[p & 1]] + uo[m + oxp[p & 1]] + uo[m + ojm] + uo[m + ojp] + uo[m - L.P] + uo[m + L.P];
       v[p] = f[m] - (6 * u[m] - nb) * inv_h2;
     }
   }
