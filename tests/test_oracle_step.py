@@ -100,3 +100,28 @@ def test_step_with_circuit_reduces_and_discharges():
     assert c.I_gap > 0 and c.I_tot == 0.0
     assert c.V_gap == pytest.approx(V0 - CFG["dt"] / 1e-12 * c.I_gap, rel=1e-15)
     assert np.all(c.phi[-1] == c.V_gap) and c.V_gap < V0
+
+
+@pytest.mark.slow
+def test_step_with_every_next_process_keeps_the_books():
+    """One step with the elastic and Coulomb passes, merging and the circuit: ids stay unique and
+    the new ones consecutive, every process ran,
+    the deposited charge equals the SP charge, and the solve holds the anode at V_gap."""
+    g = Grid(CFG["nx"], CFG["ny"], CFG["nz"], CFG["dx"], CFG["tip_radius"], CFG["tip_height"])
+    V0 = field.calibrate_V0(g, CFG["apex_field"])
+    pop = synth.plasma(CFG, seed=6)
+    prm = dict(CFG, V0=V0, next_id=CFG["n_sp"], n_heat=0, elastic=True, coulomb=True, merge_max=2,
+               circuit_R=1e3, circuit_C=1e-12, sigma_el_en=5e-19, sigma_el_nn=5e-17, sigma_cx=5e-18)
+    st = S.State(g, prm, pop, field.solve_poisson(g, V0))
+    id0 = st.next_id
+    S.step(st)
+    for k in ("elastic_en", "elastic_nn", "charge_exchanges", "coulomb_ee", "coulomb_ei", "coulomb_ii", "merged"):
+        assert k in st.count
+    assert st.count["coulomb_ee"] > 0 and st.count["merged"] > 0
+    ids = np.concatenate([st.sp[k]["id"] for k in "eni"])
+    assert len(np.unique(ids)) == len(ids)
+    new = np.sort(ids[ids >= id0])
+    assert np.array_equal(new, np.arange(id0, st.next_id, dtype=np.uint64))
+    assert int(st.Q.sum()) == (int(st.sp["i"]["w"].sum()) - int(st.sp["e"]["w"].sum())) << 30
+    assert st.V_gap < V0 or st.I_gap <= 0.0
+    assert np.all(st.phi[-1] == st.V_gap)
