@@ -104,9 +104,9 @@ def test_step_with_circuit_reduces_and_discharges():
 
 @pytest.mark.slow
 def test_step_with_every_next_process_keeps_the_books():
-    """One step with the elastic and Coulomb passes, merging and the circuit: ids stay unique and
-    the new ones consecutive, every process ran,
-    the deposited charge equals the SP charge, and the solve holds the anode at V_gap."""
+    """One step with the elastic and Coulomb passes, merging and the circuit: every process ran,
+    ids stay unique and the new ones consecutive, the deposited charge equals the SP charge, and
+    the solve holds the anode at V_gap."""
     g = Grid(CFG["nx"], CFG["ny"], CFG["nz"], CFG["dx"], CFG["tip_radius"], CFG["tip_height"])
     V0 = field.calibrate_V0(g, CFG["apex_field"])
     pop = synth.plasma(CFG, seed=6)
