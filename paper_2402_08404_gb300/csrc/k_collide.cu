@@ -796,7 +796,7 @@ int stage_collide(pic_t *h) {
   int *go = h->long_n + 4;
   uint64_t *total = (uint64_t *)(h->tmp_len + 2);
   const int grid = h->nsm * 8;
-  // events of the count kernels are staged per unit of 256 work items in the MCC scratch
+  // events of the count kernels are staged per unit of 256 work items in the collision scratch
   const EvBlocks ev{h->pair_cnt, h->ev_hits, h->ev_cnt, h->ev_off};
   if (fl & PIC_F_IMPACT_ION) {
     McArgs a;

@@ -391,9 +391,10 @@ int pic_create(const pic_geometry_t *geometry, const pic_grid_t *grid, const pic
     S.off = alloc_n<uint32_t>(h, h->ncell + 1); A(S.off);
     if (s != PIC_ION) capsum += S.cap;
   }
+  // one staging slot per collision work item: impact ionization takes e- + Cu, field ionization
+  // Cu, the elastic passes e-, Cu or Cu+ alone
+  capsum = std::max<int64_t>(capsum, h->sp[PIC_ION].cap);
   h->pair_cnt = alloc_n<uint64_t>(h, capsum); A(h->pair_cnt);
-  h->pair_off = alloc_n<uint64_t>(h, capsum); A(h->pair_off);
-  h->pair_ncoll = alloc_n<int32_t>(h, capsum); A(h->pair_ncoll);
   h->ev_hits = alloc_n<int>(h, capsum / 256 + 2); A(h->ev_hits);
   h->ev_cnt = alloc_n<uint64_t>(h, capsum / 256 + 2); A(h->ev_cnt);
   h->ev_off = alloc_n<uint64_t>(h, capsum / 256 + 2); A(h->ev_off);

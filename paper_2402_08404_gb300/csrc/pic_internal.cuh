@@ -184,9 +184,7 @@ struct pic_s {
   pic::DevClock *clock = nullptr;
   // scratch
   void *scan_tmp = nullptr;      // block partials for scans
-  uint64_t *pair_cnt = nullptr;  // per projectile / neutral: packed product counts
-  uint64_t *pair_off = nullptr;
-  int32_t *pair_ncoll = nullptr;
+  uint64_t *pair_cnt = nullptr;  // staged collision events (item | payload << 32), one slot per work item
   double *red = nullptr;         // reduction partials
   double *red_out = nullptr;
   double *red_mid = nullptr;     // first-stage sums of the partials (2 x 128)
