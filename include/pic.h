@@ -61,15 +61,16 @@ extern "C" {
 #define PIC_F_MIXED_MG 0x80u    /* a8: FP32 V-cycles with FP64 residual refinement (else FP64 V-cycles) */
 #define PIC_F_FAST_INTEGRAL 0x100u  /* a1: Gamow quadrature and turning points in FP32 (J, P_N to ~1e-5
                                        relative) in the step and in pic_emission_eval; else all FP64 */
-#define PIC_F_MERGE 0x4000u    /* a4: after the sort, SP merging in cells above merge_max SPs of a species */
-#define PIC_F_COULOMB 0x2000u  /* a5: then e-e, e-Cu+, Cu+-Cu+ Coulomb collisions (binary small-angle method) */
-#define PIC_F_EXTRAPOLATE 0x1000u /* pic_step starts each solve from 2 phi^n - phi^(n-1) instead of phi^n */
-#define PIC_F_ELASTIC 0x800u    /* a5: then elastic e-Cu and Cu-Cu collisions and Cu+-Cu charge exchange */
-#define PIC_F_CIRCUIT 0x400u    /* the RC circuit drives the anode (needs circuit_R, circuit_C > 0 at create) */
 #define PIC_F_GRAPH 0x200u      /* pic_step replays a CUDA graph of one step (the Poisson loop a device-side
                                    while node); the first call with new flags runs one step eagerly and
                                    records the graph; results equal the eager form's bit for bit */
-#define PIC_F_ALL 0xFFu         /* every stage, surrogate and mixed-precision solve; not FAST_INTEGRAL */
+#define PIC_F_CIRCUIT 0x400u    /* the RC circuit drives the anode (needs circuit_R, circuit_C > 0 at create) */
+#define PIC_F_ELASTIC 0x800u    /* a5: then elastic e-Cu and Cu-Cu collisions and Cu+-Cu charge exchange */
+#define PIC_F_EXTRAPOLATE 0x1000u /* pic_step starts each solve from 2 phi^n - phi^(n-1) instead of phi^n */
+#define PIC_F_COULOMB 0x2000u   /* a5: then e-e, e-Cu+, Cu+-Cu+ Coulomb collisions (binary small-angle method) */
+#define PIC_F_MERGE 0x4000u     /* a4: after the sort, SP merging in cells above merge_max SPs of a species */
+#define PIC_F_ALL 0xFFu         /* every stage, surrogate and mixed-precision solve; not FAST_INTEGRAL and
+                                   none of the opt-in flags 0x200-0x4000 */
 
 typedef struct {
   double tip_radius; /* m */
