@@ -114,3 +114,49 @@ def test_production_size_step_stages(pic):
     assert np.max(np.abs(J[pick][rel_] / Jr[rel_] - 1)) <= 1e-4
     assert np.max(np.abs(PN[pick][rel_] - Pr[rel_]) / (np.abs(Pr[rel_]) + 0.05 * Jr[rel_])) <= 1e-4
     sim.close()
+
+
+def test_production_size_optional_processes(pic):
+    """The optional processes at the production size, by properties that hold at any size:
+    merging keeps every species' weight and momentum (float32 rounding) and merges in the dense
+    cells; the collide stage with elastic and Coulomb passes moves weight only from Cu to Cu+
+    (and adds as much to e-), keeps ids unique, and turns pairs in every Coulomb pass."""
+    cfg = dict(synth.CONFIGS["production"], merge_max=8)
+    n = cfg["n_sp"]
+    pop = synth.plasma(cfg, seed=cfg["seed"])
+    cap = (int(0.4 * n * 1.25), int(0.4 * n * 1.25), int(0.2 * n * 1.5))
+    flags = (pic.F_ALL & ~pic.F_SURROGATE) | pic.F_FAST_INTEGRAL | pic.F_ELASTIC | pic.F_COULOMB | pic.F_MERGE
+    sim = pic.Pic(cfg, capacity=cap, flags=flags, mg_tol=1e-6, mg_max_cycles=60)
+    for s, (k, _, _) in enumerate(SPECIES):
+        sim.load_particles(s, pop[k])
+    sim.set_clock(0, n)
+    sim.solve_field()
+
+    def moments(s):
+        sp_ = sim.get_particles(s)
+        w = sp_["w"].astype(np.int64)
+        p = [float((w * sp_[c].astype(np.float64)).sum()) for c in ("vx", "vy", "vz")]
+        a = [float((w * np.abs(sp_[c].astype(np.float64))).sum()) for c in ("vx", "vy", "vz")]
+        return int(w.sum()), p, a
+
+    before = [moments(s) for s in range(3)]
+    sim.merge()
+    d = sim.diagnostics()
+    assert d["merged"] > 0
+    for s in range(3):
+        w1, p1, _ = moments(s)
+        w0, p0, a0 = before[s]
+        assert w1 == w0
+        for c in range(3):
+            assert abs(p1[c] - p0[c]) <= 1e-5 * a0[c] + 1e-30, (s, c)
+
+    w0 = _weights(sim)
+    sim.collide()
+    d = sim.diagnostics()
+    w1 = _weights(sim)
+    assert w1[1] + w1[2] == w0[1] + w0[2]
+    assert w1[0] - w0[0] == w1[2] - w0[2]
+    ids = np.concatenate([sim.get_particles(s)["id"] for s in range(3)])
+    assert len(np.unique(ids)) == len(ids)
+    assert d["coulomb_ee"] > 0 and d["coulomb_ei"] > 0 and d["coulomb_ii"] > 0
+    sim.close()
