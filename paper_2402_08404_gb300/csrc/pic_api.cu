@@ -333,7 +333,6 @@ int pic_create(const pic_geometry_t *geometry, const pic_grid_t *grid, const pic
   };
   HostGeom G;
   build_geometry(h, G);
-  h->solid_host = G.solid;
   bool okalloc = true;
   auto A = [&](void *p) { if (!p) okalloc = false; };
   // grids

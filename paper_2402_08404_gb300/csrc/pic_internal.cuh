@@ -223,7 +223,6 @@ struct pic_s {
   std::vector<std::pair<int, double>> kt_pend;      // (kernel, units) per recorded launch
   double kt_ms[64] = {0}, kt_units[64] = {0};
   int64_t kt_n[64] = {0};
-  std::vector<uint8_t> solid_host;  // host copy of the solid-cell mask (load validation)
 };
 
 namespace pic {
