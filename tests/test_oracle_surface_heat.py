@@ -126,3 +126,33 @@ def test_mlp_gradients_match_finite_differences():
         assert grads[li][1][1] == pytest.approx((lp - lm) / (2 * h), rel=1e-5, abs=1e-9)
     assert mlp.gelu(np.array([0.0]))[0] == 0.0
     assert mlp.gelu(np.array([30.0]))[0] == pytest.approx(30.0)
+
+
+def test_bf16_rounding_known_values():
+    """Round to nearest even at 8 significand bits: 1 + 2^-9 -> 1; the tie 1 + 2^-8 -> 1 (even);
+    the tie 1 + 3 2^-8 -> 1 + 2^-6 (even); 1 + 2^-7 is representable; signs are symmetric."""
+    v = np.array([1 + 2.0 ** -9, 1 + 2.0 ** -8, 1 + 3 * 2.0 ** -8, 1 + 2.0 ** -7, -(1 + 3 * 2.0 ** -8), 0.0])
+    assert list(mlp.bf16(v)) == [1.0, 1.0, 1 + 2.0 ** -6, 1 + 2.0 ** -7, -(1 + 2.0 ** -6), 0.0]
+    assert mlp.near_bf16_tie(np.array([1 + 2.0 ** -8]))[0] and not mlp.near_bf16_tie(np.array([1.0]))[0]
+
+
+def test_mlp_bf16_operands_stay_within_rounding_of_the_exact_network():
+    """With BF16 operands the outputs and gradients differ from the float64 network by the
+    rounding only: within a few BF16 steps (2^-8) of the scale of the summed terms, and the bias
+    gradients of the BF16 layers sum the unrounded values."""
+    rng = np.random.default_rng(3)
+    params = [(W, rng.normal(0, 0.1, b.size)) for W, b in mlp.init_params(rng)]
+    params = [(mlp.bf16(W) if li in mlp.BF16_LAYERS else W, b) for li, (W, b) in enumerate(params)]
+    x = rng.normal(size=(64, mlp.SIZES[0]))
+    y = rng.normal(size=(64, 2))
+    o64, _ = mlp.forward(params, x)
+    o16, _ = mlp.forward(params, x, bf16_operands=True)
+    scale = np.abs(o64).max()
+    assert 0 < np.abs(o16 - o64).max() <= 8 * 2.0 ** -8 * scale
+    _, g64 = mlp.loss_and_grad(params, x, y)
+    _, g16 = mlp.loss_and_grad(params, x, y, bf16_operands=True)
+    for (gw, gb), (hw, hb) in zip(g64, g16):
+        assert np.abs(gw - hw).max() <= 8 * 2.0 ** -8 * np.abs(gw).max()
+        assert np.abs(gb - hb).max() <= 8 * 2.0 ** -8 * np.abs(gb).max()
+    # the output layer's gradients see no rounded operand of their own
+    assert not np.array_equal(g64[1][0], g16[1][0])
