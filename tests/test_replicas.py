@@ -55,3 +55,37 @@ def test_reference_arm_runs_on_rank_0_only(monkeypatch):
     monkeypatch.setenv("RANK", "1")
     args = argparse.Namespace(config="small", cpu_sample=2000, steps=1, warmup=0)
     assert bench.run_reference(args) is None
+
+
+def _ens_rank(rank, world, port, n, out):
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    import bench
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    idx = bench.ensemble_share(n, world, rank)
+    rows = [[float(i), float(i * i) + 0.5, float(rank)] for i in idx]     # stands in for an instance's diagnostics
+    out[rank] = (idx, bench.gather_instances(dist, idx, rows, n, "cpu"))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_ensemble_partition_gloo_world_size_2():
+    """The ensemble is split over the ranks: every instance is stepped by exactly one rank, and
+    the gathered per-instance table equals the one a single process writes for all instances."""
+    sys.path.insert(0, ROOT)
+    import bench
+    n = 13
+    port = 31500 + (os.getpid() % 2000)
+    with mp.Manager() as man:
+        out = man.dict()
+        mp.spawn(_ens_rank, args=(2, port, n, out), nprocs=2, join=True)
+        res = dict(out)
+    shares = [res[r][0] for r in (0, 1)]
+    assert sorted(shares[0] + shares[1]) == list(range(n)) and not set(shares[0]) & set(shares[1])
+    one = bench.gather_instances(None, list(range(n)), [[float(i), float(i * i) + 0.5, 0.0] for i in range(n)], n, "cpu")
+    for r in (0, 1):
+        table = res[r][1]
+        assert not np.isnan(table).any()
+        assert np.array_equal(table[:, :2], one[:, :2])
+        assert np.array_equal(table[:, 2], np.array([i % 2 for i in range(n)], dtype=float))   # the rank that stepped it
