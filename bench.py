@@ -140,15 +140,52 @@ KERNEL_BYTES_PER_UNIT = {
     "k_efield": 24.0,        # per node: phi 8 + E write 16
 }
 # DRAM bytes (read + write) per launch from one ncu capture of the unchanged kernel on the
-# production grid (profiles/dram_traffic_multigrid_production_grid.md): (workload, kernel) ->
-# bytes.  Empty while the dominant kernel has changed since its capture: the smoother's
-# neighbour offsets were restructured after the 71.64 MB capture, so the bench reports null.
+# production grid: (workload, kernel) -> bytes.  A kernel that has changed since its capture has
+# no entry (the bench then reports null).
 NCU_TRAFFIC_PER_LAUNCH = {}
 KERNEL_BYTES_PER_SP = {      # (bytes, species the launches of one step cover)
-    "k_push": (56.0, "all"),         # pos+vel+w read 28, pos+vel write 24, key 4
+    "k_push": (56.0, "all"),         # pos+vel+w read 28, pos+vel write 24, key 4 (+ 8 B per node of charge)
     "k_gather": (76.0, "all"),       # perm 4 + 36 B record read + 36 B record write
     "k_deposit": (16.0, "charged"),  # pos + w of e- and Cu+ (+ 8 B per node of charge, below)
 }
+
+
+# The particle kernels of the benchmark spec's figure (push with its fused charge deposit, impact and
+# field ionization), their algorithmic bytes per step:
+#   push + crossers + clearing the charge: 56 B per SP (read pos+vel 24 + w 4, write pos+vel 24,
+#     cell key 4) + 8 B per node (the deposited charge written once);
+#   impact ionization (count + products): read vel + w + id (24 B) per e- and Cu SP;
+#   field ionization (count + products): read pos + w (16 B) per Cu SP.
+PARTICLE_KERNELS = ("k_push", "k_cross", "k_mcc_count", "k_mcc_products", "k_dfi_count", "k_dfi_products")
+
+
+def particle_roofline(kt, counts, nnode, steps, hbm_peak, pk_src):
+    """Roofline of the push + deposit + MCC + DFI kernels over the timed region (their summed
+    event-timed durations against their summed algorithmic bytes)."""
+    n_all = sum(counts)
+    parts = {
+        "push_deposit": (("k_push", "k_cross"), 56.0 * n_all + 8.0 * nnode),
+        "impact_ionization": (("k_mcc_count", "k_mcc_products"), 24.0 * (counts[0] + counts[1])),
+        "field_ionization": (("k_dfi_count", "k_dfi_products"), 16.0 * counts[1]),
+    }
+    out, tot_b, tot_ms = {}, 0.0, 0.0
+    for name, (ks, b) in parts.items():
+        ms = sum(kt[k][1] for k in ks if k in kt)
+        if ms <= 0:
+            continue
+        ach = b * steps / (ms * 1e-3) / 1e9
+        out[name] = {"ms_per_step": round(ms / steps, 4), "alg_bytes_per_step": round(b), "achieved_gbs": round(ach, 1),
+                     "frac": round(ach / hbm_peak, 4)}
+        tot_b += b * steps
+        tot_ms += ms
+    if tot_ms <= 0:
+        return None
+    ach = tot_b / (tot_ms * 1e-3) / 1e9
+    return {"bound": "hbm", "achieved": round(ach, 1), "peak": hbm_peak, "unit": "GB/s", "frac": round(ach / hbm_peak, 4),
+            "kernels": list(PARTICLE_KERNELS), "ms_per_step": round(tot_ms / steps, 4), "parts": out,
+            "alg_bytes": "56 B per SP + 8 B per node (push, crossers, charge clear + deposit); 24 B per e- and Cu SP "
+                         "(impact ionization); 16 B per Cu SP (field ionization)",
+            "peak_source": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)" if pk_src == "measured" else pk_src}
 
 
 def kernel_roofline(name, timing, counts, nnode, steps, hbm_peak, pk_src):
@@ -160,8 +197,9 @@ def kernel_roofline(name, timing, counts, nnode, steps, hbm_peak, pk_src):
     elif name in KERNEL_BYTES_PER_SP:
         b, which = KERNEL_BYTES_PER_SP[name]
         n = sum(counts) if which == "all" else counts[0] + counts[2]
-        alg = b * n * steps + (8.0 * nnode * steps if name == "k_deposit" else 0.0)
-        per_unit = f"{b:g} B per SP x {n:.4g} SPs per step" + (" + 8 B per node" if name == "k_deposit" else "")
+        node_b = 8.0 if name in ("k_deposit", "k_push") else 0.0
+        alg = b * n * steps + node_b * nnode * steps
+        per_unit = f"{b:g} B per SP x {n:.4g} SPs per step" + (" + 8 B per node" if node_b else "")
     else:
         return None
     achieved = alg / (ms * 1e-3) / 1e9
@@ -250,7 +288,8 @@ def run_ours(args):
         sim.step(2)
         kt_all = sim.kernel_timing()
         dom_kernel = max(kt_all, key=lambda k: kt_all[k][1])
-        sim.set_kernel_timing([dom_kernel])
+        timed = sorted({dom_kernel, *[k for k in PARTICLE_KERNELS if k in kt_all]})
+        sim.set_kernel_timing(timed)
         if dist:
             dist.barrier()
         with ClockSampler(local) as clk:
@@ -258,7 +297,8 @@ def run_ours(args):
             torch.cuda.profiler.start()
             elapsed_ms, d0, d1 = timed_steps(sim, stream, args.steps)
             torch.cuda.profiler.stop()
-        kt_dom = sim.kernel_timing().get(dom_kernel)
+        kt_live = sim.kernel_timing()
+        kt_dom = kt_live.get(dom_kernel)
         sim.set_kernel_timing([])
         if dist:
             dist.barrier()
@@ -348,6 +388,8 @@ def run_ours(args):
         roof = {"bound": "alu", "achieved": round(achieved, 4), "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": round(achieved / FP64_PEAK_TFLOPS, 4), "traffic": None, "kernel_stage": dom,
                 "peak_source": "nominal FP64 rate", "stage_ms": round(stage_ms[dom], 4)}
+    roof_p = particle_roofline(kt_live, mean_counts, nnode, args.steps, pk.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"]),
+                               pk_src)
     kernel_ms = {k: round(v[1] / 2, 4) for k, v in sorted(kt_all.items(), key=lambda kv: -kv[1][1])[:20]}
     ms_step = times[0] / args.steps
     form = ("surrogate emission (FP32-Gamow integral where it falls back) + FP32 V-cycles with FP64 refinement"
@@ -377,6 +419,7 @@ def run_ours(args):
                        "train_s": round((sur["ms_data"] + sur["ms_train"]) / 1e3, 2)},
                    "plain_form": plain, "graph_form": graph, "autotune": tune},
         "roofline": roof,
+        "roofline_particles": roof_p,
         "clocks": clk.summary(),
         "e2e": {"value": tot_e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(__import__("ctypes").sizeof(pic.Diag))},
@@ -441,16 +484,59 @@ def cpu_baseline(cfg, pop, sample, steps=1, warmup=0):
             "seconds": round(t_total, 3)}
 
 
+def ensemble_share(n, world, rank):
+    """The ensemble's instances that one rank steps: rank, rank + world, ...  Every instance
+    belongs to exactly one rank (the instances are independent: no collective on the data path)."""
+    return list(range(rank, n, world))
+
+
+def gather_instances(dist, idx, rows, n, device):
+    """Per-instance diagnostics of every rank, on every rank: rows (len(idx) x k) of this rank's
+    instances idx -> an n x k table (NaN where no rank reported).  One all_gather of a small
+    padded block after the timed region (dist None: one process)."""
+    import torch
+    rows = np.asarray(rows, dtype=np.float64).reshape(len(idx), -1)
+    k = rows.shape[1]
+    table = np.full((n, k), np.nan)
+    if dist is None:
+        table[idx] = rows
+        return table
+    world = dist.get_world_size()
+    m = (n + world - 1) // world
+    buf = torch.full((m, k + 1), float("nan"), dtype=torch.float64, device=device)
+    if len(idx):
+        buf[:len(idx), 0] = torch.tensor(idx, dtype=torch.float64, device=device)
+        buf[:len(idx), 1:] = torch.tensor(rows, device=device)
+    outs = [torch.empty_like(buf) for _ in range(world)]
+    dist.all_gather(outs, buf)
+    for o in outs:
+        for r in o.cpu().numpy():
+            if not np.isnan(r[0]):
+                table[int(r[0])] = r[1:]
+    return table
+
+
 def run_ensemble(args):
     """64 independent instances (apex fields 6-12 GV/m, grids 32x32x64 to 128x128x256) stepped by
     one CUDA-graph launch per step through pic_batch_step, against the same instances stepped one
-    after another in the eager form.  Surrogate trained once (instance 0) and shared; every
-    instance autotuned on its own grid."""
+    after another in the eager form.  With N ranks the one ensemble is partitioned: rank r steps
+    instances r, r + N, ... (strong scaling: the job is fixed), and the per-instance diagnostics
+    are gathered after the timed region.  Each rank trains the surrogate once on its first
+    instance (the same seed everywhere, so the same network) and shares it; every instance is
+    autotuned on its own grid."""
     import torch
-    from paper_2402_08404_gb300 import pic, synth
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     rank = int(os.environ.get("RANK", "0"))
-    cfgs = synth.ensemble_configs(n=args.ensemble_n, seed=7 + rank)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2402_08404_gb300 import pic, synth
+    cfgs_all = synth.ensemble_configs(n=args.ensemble_n, seed=7)
+    mine = ensemble_share(len(cfgs_all), world, rank)
+    cfgs = [cfgs_all[i] for i in mine]
     stream = torch.cuda.Stream()
     sims, tunes = [], []
     with torch.cuda.stream(stream):
@@ -483,7 +569,9 @@ def run_ensemble(args):
         serial_s = (time.perf_counter() - t0) / max(args.ensemble_serial_steps, 1)
         batch = pic.Batch(sims)
         batch.step(max(args.warmup, 2))
-        with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+        if dist:
+            dist.barrier()
+        with ClockSampler(local) as clk:
             d0 = [sim.diagnostics() for sim in sims]
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -492,28 +580,39 @@ def run_ensemble(args):
             e1.record(stream)
             torch.cuda.synchronize()
             ms = e0.elapsed_time(e1)
+        if dist:
+            dist.barrier()
         d1 = [sim.diagnostics() for sim in sims]
     updates = args.steps * 0.5 * sum(sum(a["count"]) + sum(b["count"]) for a, b in zip(d0, d1))
-    grids = sorted({(c["nx"], c["ny"], c["nz"]) for c in cfgs})
-    out = {
-        "metric": "ensemble PIC-MCC particle-updates/s (one graph launch per step)", "value": updates / (ms * 1e-3),
-        "unit": "particle-updates/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32+f64+bf16", "data": "synthetic (seeded plasma, Philox)",
-        "config": {"workload": f"ensemble: {len(cfgs)} instances, apex 6-12 GV/m, grids {grids[0]}..{grids[-1]}, "
-                               f"dx 0.5-1 nm, {sum(c['n_sp'] for c in cfgs):.3g} SPs in all (1e4-2e6 each)",
-                   "form": "production (surrogate, FP32-Gamow fallback, mixed MG), graph per step",
-                   "eager_serial_ms_per_step": round(serial_s * 1e3, 3),
-                   "eager_serial_particle_updates_per_s": c0 / serial_s,
-                   "speedup_vs_eager_serial": round(serial_s * 1e3 / (ms / args.steps), 3),
-                   "autotune_examples": tunes[:3],
-                   "mg_cycles": [d["mg_cycles"] for d in d1[:8]]},
-        "clocks": clk.summary(),
-    }
+    t_max, tot_updates, tot_serial = reduce_over_ranks(dist, ms, updates, c0 / serial_s, "cuda")
+    # per-instance diagnostics of the whole ensemble: step, SPs per species, mg cycles
+    table = gather_instances(dist, mine, [[d["step"], *d["count"], d["mg_cycles"]] for d in d1], len(cfgs_all), "cuda")
     batch.close()
     for sim in sims:
         sim.close()
-    return out
+    if dist:
+        dist.destroy_process_group()
+    if rank != 0:
+        return None
+    grids = sorted({(c["nx"], c["ny"], c["nz"]) for c in cfgs_all})
+    return {
+        "metric": "ensemble PIC-MCC particle-updates/s (one graph launch per step)", "value": tot_updates / (t_max * 1e-3),
+        "unit": "particle-updates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
+        "dtype": "f32+f64+bf16", "data": "synthetic (seeded plasma, Philox)",
+        "config": {"workload": f"ensemble: {len(cfgs_all)} instances, apex 6-12 GV/m, grids {grids[0]}..{grids[-1]}, "
+                               f"dx 0.5-1 nm, {sum(c['n_sp'] for c in cfgs_all):.3g} SPs in all (1e4-2e6 each)",
+                   "parallelism": f"instances partitioned over {world} rank(s) (rank r: r, r+{world}, ...)",
+                   "form": "production (surrogate, FP32-Gamow fallback, mixed MG), graph per step",
+                   "eager_serial_ms_per_step": round(serial_s * 1e3, 3),
+                   "eager_serial_particle_updates_per_s": tot_serial,
+                   "speedup_vs_eager_serial": round(serial_s * 1e3 / (ms / args.steps), 3),
+                   "instances_stepped": int(np.sum(~np.isnan(table[:, 0]))),
+                   "instance_steps": sorted(set(table[:, 0][~np.isnan(table[:, 0])].astype(int).tolist())),
+                   "autotune_examples": tunes[:3],
+                   "mg_cycles": [int(v) for v in table[:8, 4] if not np.isnan(v)]},
+        "clocks": clk.summary(),
+    }
 
 
 def run_reference(args):

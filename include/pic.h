@@ -167,6 +167,26 @@ int pic_get_particles(pic_t *h, int species, float *x, float *y, float *z, float
 /* Step counter (keys the random draws) and the next id to hand out. */
 int pic_set_clock(pic_t *h, int64_t step, int64_t next_id);
 
+/* Checkpoint and resume (the paper runs each simulation to its end; this serves long runs).
+ * pic_save writes the handle's whole evolving state to the file at `path` (created or
+ * truncated): the device clock (step, next id, counts, counters, circuit state), every species'
+ * SPs in their device order with the per-cell offsets and sorted-place cell keys of the last
+ * sort, the fixed-point potential, the deposited charge, the previous potential when
+ * PIC_F_EXTRAPOLATE keeps one, the per-face emission values and accumulators, the tip
+ * temperature, the surrogate's weights and validity map, V0 and the flags.  It must be called
+ * between steps or after pic_sort (PIC_E_INVALID while pushed SPs await their sort).
+ * pic_load reads such a file into a handle created with the same grid, geometry, species charges
+ * and masses and physical parameters (dt, apex_field, V0, T0, work_function, w_min, w_max_units,
+ * n_heat, seed, circuit and collision parameters): PIC_E_INVALID names the first input that
+ * differs; the solver controls (mg_tol, mg_max_cycles, mg_sweeps) may differ and the flags are
+ * taken from the file.  PIC_E_CAPACITY if a species holds more SPs than this handle's capacity
+ * (the handle is then unchanged).  After any other failure during the read the handle's state
+ * is undefined and must be loaded again before stepping.  Every random draw is keyed by (seed,
+ * purpose, id, step), so stepping a loaded handle repeats the uninterrupted run bit for bit, in
+ * the eager and the graph form.  The file is in native byte order. */
+int pic_save(pic_t *h, const char *path);
+int pic_load(pic_t *h, const char *path);
+
 /* Node arrays are (nz+1)*(ny+1)*(nx+1), index (k*(ny+1)+j)*(nx+1)+i.
  * The library holds the potential in fixed point, steps of 2^-40 V (~9.1e-13 V), so that the
  * Poisson stencil and the node differences of E are exact integer sums; pic_set_potential rounds
@@ -198,6 +218,11 @@ int pic_set_face_accumulators(pic_t *h, const double *evap, const double *heat, 
 /* Replace the PIC_F_* flags (e.g. switch the surrogate or the mixed-precision solve on or off
  * between steps of the same state). */
 int pic_set_flags(pic_t *h, uint32_t flags);
+
+/* Replace the Poisson solve's controls: relative residual target (> 0) and cap on refinement
+ * cycles per solve (>= 1).  The next solve that cannot reach mg_tol within the cap returns
+ * PIC_E_NOCONV. */
+int pic_set_solver(pic_t *h, double mg_tol, int mg_max_cycles);
 
 /* Stages of one step (each also usable alone; pic_step runs them all in this order). */
 int pic_emit(pic_t *h);        /* a1 emission + a2 evaporation/sputter injection (appends SPs) */
@@ -266,7 +291,8 @@ int pic_get_kernel_timing(pic_t *h, int k, int64_t *launches, double *ms, double
 
 /* Emission current density and Nottingham heat of n surface states (host arrays): F [V/m],
  * T [K], work function [eV], radius of curvature [m] (<= 0 or inf: flat); J [A/m^2], PN [W/m^2].
- * Evaluates the full FP64 thermal-field integral on the device (Sec. 2.3.1). */
+ * Evaluates the full FP64 thermal-field integral on the device (Sec. 2.3.1).  The handle's
+ * device (current at pic_create) must be current: PIC_E_INVALID otherwise. */
 int pic_emission_eval(pic_t *h, const double *F, const double *T, const double *phi_w,
                       const double *R, double *J, double *PN, int64_t n);
 
@@ -311,8 +337,9 @@ int pic_surrogate_eval(pic_t *h, const double *F, const double *T, const double 
  * built into the library (1.5 MiB, held on every GPU that loads it until exit); no cudaMalloc,
  * cudaFree or allocating routine is called.  The first call on a device looks the array's
  * address up (cudaGetSymbolAddress) with that device current: make it before any stream
- * capture starts there.  All calls share the array, so calls whose work overlaps on the GPU
- * race and must be serialised by the caller. */
+ * capture starts there.  The handle's device must be current (PIC_E_INVALID otherwise).  All
+ * calls share the array, so calls whose work overlaps on the GPU race and must be serialised by
+ * the caller. */
 #define PIC_NOALLOC_MAX_TUPLES 32768
 int pic_emission_eval_noalloc(pic_t *h, const double *F, const double *T, const double *phi_w,
                               const double *R, double *J, double *PN, int64_t n);

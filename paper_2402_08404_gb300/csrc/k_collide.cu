@@ -97,19 +97,25 @@ __device__ __forceinline__ void ev_stage(const EvBlocks &ev, int64_t lo, int64_t
   const unsigned bal = __ballot_sync(0xffffffffu, payload != 0);
   const int lane = threadIdx.x & 31;
   if (payload) ev.rec[lo + *run + __popc(bal & ((1u << lane) - 1u))] = (uint64_t)t | ((uint64_t)payload << 32);
-  uint64_t p_tile;
-  warp_scan_u64(pc, &p_tile);
   *run += __popc(bal);
-  *prod += p_tile;
+  if (__any_sync(0xffffffffu, pc != 0)) {   // most tiles have no event
+    uint64_t p_tile;
+    warp_scan_u64(pc, &p_tile);
+    *prod += p_tile;
+  }
 }
 
-// The leader of each group of lanes with the same cell draws the cell's pairing word once and
-// shares it (every lane of the warp takes part).
+// The leader of each run of adjacent lanes with the same cell draws the cell's pairing word once
+// and shares it (every lane of the warp takes part).  Work items come cell-sorted, so a cell's
+// lanes are adjacent; a cell split over two runs draws the same word twice.
 __device__ __forceinline__ uint32_t cell_word(uint64_t seed, uint32_t purpose, uint32_t c, bool need, int64_t step) {
-  const unsigned grp = __match_any_sync(0xffffffffu, need ? c : 0xffffffffu);
-  const int leader = __ffs(grp) - 1;
+  const int lane = threadIdx.x & 31;
+  const uint32_t key = need ? c : 0xffffffffu;
+  const uint32_t prev = __shfl_up_sync(0xffffffffu, key, 1);
+  const unsigned heads = __ballot_sync(0xffffffffu, lane == 0 || prev != key);
+  const int leader = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
   uint32_t w = 0;
-  if (need && (int)(threadIdx.x & 31) == leader) w = rng_block(seed, purpose, c, step, 0).v[0];
+  if (need && lane == leader) w = rng_block(seed, purpose, c, step, 0).v[0];
   return __shfl_sync(0xffffffffu, w, leader);
 }
 

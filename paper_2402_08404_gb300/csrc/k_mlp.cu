@@ -837,3 +837,36 @@ int pic_surrogate_eval(pic_t *h, const double *F, const double *T, const double 
 }
 
 }  // extern "C"
+
+namespace pic {
+
+// Surrogate state for pic_save / pic_load: the FP32 master weights (pic_mlp_num_params floats)
+// and the per-bin validity map (surrogate_bins bytes); *trained says whether the step may use it.
+int surrogate_bins() { return kNBin; }
+
+int surrogate_export(pic_t *h, float *master, uint8_t *binok, int *trained) {
+  MlpState &S = mlp_of(h);
+  *trained = S.trained ? 1 : 0;
+  if (!S.ready) {
+    memset(master, 0, kNParam * 4);
+    memset(binok, 0, kNBin);
+    return PIC_OK;
+  }
+  PIC_CUDA(h, cudaMemcpyAsync(master, S.master, kNParam * 4, cudaMemcpyDeviceToHost, h->stream));
+  PIC_CUDA(h, cudaMemcpyAsync(binok, S.binok, kNBin, cudaMemcpyDeviceToHost, h->stream));
+  PIC_CUDA(h, cudaStreamSynchronize(h->stream));
+  return PIC_OK;
+}
+
+int surrogate_import(pic_t *h, const float *master, const uint8_t *binok, int trained) {
+  MlpState &S = mlp_of(h);
+  PIC_TRY(ensure(h, S, 1024));
+  PIC_CUDA(h, cudaMemcpyAsync(S.master, master, kNParam * 4, cudaMemcpyHostToDevice, h->stream));
+  PIC_CUDA(h, cudaMemcpyAsync(S.binok, binok, kNBin, cudaMemcpyHostToDevice, h->stream));
+  refresh_bf16(h, S);
+  PIC_CUDA(h, cudaStreamSynchronize(h->stream));
+  S.trained = trained != 0;
+  return launch_check(h, "surrogate import");
+}
+
+}  // namespace pic

@@ -82,14 +82,17 @@ struct PushArgs {
   int64_t nface;
   unsigned long long *acc_sput, *acc_Eb;
   DevClock *clk;
+  unsigned long long *Q;   // charge deposit of the pushed SPs (null: no deposit)
+  int Z;                   // charge number of the species
+  uint32_t *xq;            // queue of SPs whose move may cross the tip or the domain boundary
+  int *xq_n;               // its length
 };
 
 // The rare path of the push (an SP whose move may reach a solid cell or leave the domain): the
 // FP64 cell traversal and, for an ion that hits the tip or the cathode, the sputter and
-// bombardment accumulators of the face it hits.  Kept out of line so that the common path
-// of k_push needs few registers.  Returns true when the SP is removed.
-__device__ __noinline__ bool crosser_event(const PushArgs &a, float x, float y, float z, float x1, float y1, float z1,
-                                          float vx, float vy, float vz, int32_t w) {
+// bombardment accumulators of the face it hits.  Returns true when the SP is removed.
+__device__ bool crosser_event(const PushArgs &a, float x, float y, float z, float x1, float y1, float z1,
+                              float vx, float vy, float vz, int32_t w) {
   const double p0[3] = {(double)x, (double)y, (double)z};
   const double p1[3] = {(double)x1, (double)y1, (double)z1};
   int64_t vcell = -1;
@@ -111,53 +114,303 @@ __device__ __noinline__ bool crosser_event(const PushArgs &a, float x, float y, 
   return true;
 }
 
-__global__ void __launch_bounds__(256, 4) k_push(PushArgs a) {
+// Cloud-in-cell weights of a position (cell units) with quantised fractions: the lower corner's
+// node index and q = floor(frac 2^F) per axis, packed as qx | qy << 10 | qz << 20.
+__device__ __forceinline__ uint32_t cic_corner(float x, float y, float z, int nx, int ny, uint32_t *qpack) {
+  const float fi = floorf(x), fj = floorf(y), fk = floorf(z);
+  const float one = (float)(1 << kFracBits);
+  const uint32_t qx = (uint32_t)floorf(__fsub_rn(x, fi) * one);
+  const uint32_t qy = (uint32_t)floorf(__fsub_rn(y, fj) * one);
+  const uint32_t qz = (uint32_t)floorf(__fsub_rn(z, fk) * one);
+  *qpack = qx | (qy << 10) | (qz << 20);
+  return (uint32_t)node_index((int)fi, (int)fj, (int)fk, nx, ny);
+}
+
+// The 8 node charges Z w prod(W) of one SP (int64, exact): corner c = dx + 2 dy + 4 dz.
+__device__ __forceinline__ void cic_charges(uint32_t qpack, int32_t zw, long long c[8]) {
+  const int64_t one = 1 << kFracBits;
+  const int64_t qx = qpack & 1023u, qy = (qpack >> 10) & 1023u, qz = qpack >> 20;
+  const int64_t a00 = (int64_t)zw * (one - qz) * (one - qy), a10 = (int64_t)zw * (one - qz) * qy;
+  const int64_t a01 = (int64_t)zw * qz * (one - qy), a11 = (int64_t)zw * qz * qy;
+  c[0] = a00 * (one - qx); c[1] = a00 * qx; c[2] = a10 * (one - qx); c[3] = a10 * qx;
+  c[4] = a01 * (one - qx); c[5] = a01 * qx; c[6] = a11 * (one - qx); c[7] = a11 * qx;
+}
+
+__device__ __forceinline__ void cic_global(unsigned long long *Q, uint32_t base, uint32_t qpack, int32_t zw, int nx,
+                                           int ny) {
+  long long c[8];
+  cic_charges(qpack, zw, c);
+  const int64_t sy = nx + 1, sz = (int64_t)(nx + 1) * (ny + 1);
+#pragma unroll
+  for (int q = 0; q < 8; ++q)
+    if (c[q] != 0) atomicAdd(Q + base + (q & 1) + ((q >> 1) & 1) * sy + (q >> 2) * sz, (unsigned long long)c[q]);
+}
+
+// Leapfrog of one SP from its position and the (optional) field at x^n.
+__device__ __forceinline__ void leapfrog(float qmdt, float dtdx, float3 e, bool charged, float &x, float &y, float &z,
+                                         float &vx, float &vy, float &vz) {
+  if (charged) {
+    vx = __fadd_rn(vx, __fmul_rn(qmdt, e.x));
+    vy = __fadd_rn(vy, __fmul_rn(qmdt, e.y));
+    vz = __fadd_rn(vz, __fmul_rn(qmdt, e.z));
+  }
+  x = __fadd_rn(x, __fmul_rn(vx, dtdx));
+  y = __fadd_rn(y, __fmul_rn(vy, dtdx));
+  z = __fadd_rn(z, __fmul_rn(vz, dtdx));
+}
+
+// E at x^n from the shared-memory copy of the tile's node windows: window (dz, dy) holds the
+// nodes lo + (dz sz + dy sy) + [0, L).
+__device__ __forceinline__ float3 gather_E_win(const float4 *sE, int L, uint32_t lo, float x, float y, float z, int nx,
+                                               int ny) {
+  const float fi = floorf(x), fj = floorf(y), fk = floorf(z);
+  const float fx = __fsub_rn(x, fi), fy = __fsub_rn(y, fj), fz = __fsub_rn(z, fk);
+  const int o = (int)((uint32_t)node_index((int)fi, (int)fj, (int)fk, nx, ny) - lo);
+  const float4 e000 = sE[o], e100 = sE[o + 1], e010 = sE[L + o], e110 = sE[L + o + 1];
+  const float4 e001 = sE[2 * L + o], e101 = sE[2 * L + o + 1], e011 = sE[3 * L + o], e111 = sE[3 * L + o + 1];
+  float3 r;
+  r.x = lerp_rn(lerp_rn(lerp_rn(e000.x, e100.x, fx), lerp_rn(e010.x, e110.x, fx), fy),
+                lerp_rn(lerp_rn(e001.x, e101.x, fx), lerp_rn(e011.x, e111.x, fx), fy), fz);
+  r.y = lerp_rn(lerp_rn(lerp_rn(e000.y, e100.y, fx), lerp_rn(e010.y, e110.y, fx), fy),
+                lerp_rn(lerp_rn(e001.y, e101.y, fx), lerp_rn(e011.y, e111.y, fx), fy), fz);
+  r.z = lerp_rn(lerp_rn(lerp_rn(e000.z, e100.z, fx), lerp_rn(e010.z, e110.z, fx), fy),
+                lerp_rn(lerp_rn(e001.z, e101.z, fx), lerp_rn(e011.z, e111.z, fx), fy), fz);
+  return r;
+}
+
+// Cell of the pushed position and whether the move stays clear of the tip and the walls: an SP
+// that stays in its cell, or moves m cells (Chebyshev) from a cell at Chebyshev distance > m from
+// every solid cell while staying inside, cannot meet a boundary.  Returns 0 clear (cell in *c),
+// 1 possible crosser, 2 non-finite position (removed).
+__device__ __forceinline__ int move_class(const PushArgs &a, float x, float y, float z, float x1, float y1, float z1,
+                                          uint32_t *c) {
+  if (!(isfinite(x1) && isfinite(y1) && isfinite(z1))) return 2;
+  const int i0 = (int)floorf(x), j0 = (int)floorf(y), k0 = (int)floorf(z);
+  const int i1 = (int)fminf(fmaxf(floorf(x1), -1.f), (float)a.nx);
+  const int j1 = (int)fminf(fmaxf(floorf(y1), -1.f), (float)a.ny);
+  const int k1 = (int)fminf(fmaxf(floorf(z1), -1.f), (float)a.nz);
+  if (i1 != i0 || j1 != j0 || k1 != k0) {
+    const int m = max(abs(i1 - i0), max(abs(j1 - j0), abs(k1 - k0)));
+    const bool inside = i1 >= 0 && i1 < a.nx && j1 >= 0 && j1 < a.ny && k1 >= 0 && k1 < a.nz;
+    if (!(inside && (int)a.cheb[cell_index(i0, j0, k0, a.nx, a.ny)] > m)) return 1;
+  }
+  *c = (uint32_t)cell_index(i1, j1, k1, a.nx, a.ny);
+  return 0;
+}
+
+// count of the SP's new cell: lanes of a warp with the same cell add their count with one atomic
+__device__ __forceinline__ void count_cell(uint32_t *cnt, uint32_t c, bool on) {
+  const unsigned grp = __match_any_sync(0xffffffffu, on ? c : kDead);
+  if (on && (int)(threadIdx.x & 31) == __ffs(grp) - 1) atomicAdd(&cnt[c], (uint32_t)__popc(grp));
+}
+
+// append the lanes with `on` to the crosser queue (one atomic per warp)
+__device__ __forceinline__ void enqueue(const PushArgs &a, int64_t i, bool on) {
+  const unsigned bal = __ballot_sync(0xffffffffu, on);
+  if (!bal) return;
+  const int lane = threadIdx.x & 31, leader = __ffs(bal) - 1;
+  int base = 0;
+  if (lane == leader) base = atomicAdd(a.xq_n, __popc(bal));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  if (on) a.xq[base + __popc(bal & ((1u << lane) - 1u))] = (uint32_t)i;
+}
+
+// Push of the neutral species (ballistic, no field, no charge).
+__global__ void __launch_bounds__(256) k_push_neutral(PushArgs a) {
   const int64_t n = a.clk->n[a.species];
   int removed = 0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t w = a.p.w[i];
-    if (w <= 0) { a.key[i] = kDead; continue; }
-    const float x = a.p.x[i], y = a.p.y[i], z = a.p.z[i];
-    float vx = a.p.vx[i], vy = a.p.vy[i], vz = a.p.vz[i];
-    if (a.charged) {
-      const float3 e = gather_E(a.E, x, y, z, a.nx, a.ny);
-      vx = __fadd_rn(vx, __fmul_rn(a.qmdt, e.x));
-      vy = __fadd_rn(vy, __fmul_rn(a.qmdt, e.y));
-      vz = __fadd_rn(vz, __fmul_rn(a.qmdt, e.z));
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < n; i0 += stride) {   // warp-uniform trip count
+    const int64_t i = i0 + threadIdx.x;
+    const int32_t w = i < n ? a.p.w[i] : 0;
+    bool clear = false, cross = false;
+    uint32_t c = kDead;
+    if (w > 0) {
+      float x = a.p.x[i], y = a.p.y[i], z = a.p.z[i];
+      float vx = a.p.vx[i], vy = a.p.vy[i], vz = a.p.vz[i];
+      const float x0 = x, y0 = y, z0 = z;
+      leapfrog(0.f, a.dtdx, make_float3(0.f, 0.f, 0.f), false, x, y, z, vx, vy, vz);
+      const int cls = move_class(a, x0, y0, z0, x, y, z, &c);
+      clear = cls == 0;
+      cross = cls == 1;
+      if (!cross) { a.p.x[i] = x; a.p.y[i] = y; a.p.z[i] = z; }
+      if (cls == 2) ++removed;
     }
+    if (i < n && !clear && !cross) a.key[i] = kDead;
+    if (clear) a.key[i] = c;
+    count_cell(a.cnt, c, clear);
+    enqueue(a, i, cross);
+  }
+  for (int o = 16; o > 0; o >>= 1) removed += __shfl_down_sync(0xffffffffu, removed, o);
+  if ((threadIdx.x & 31) == 0 && removed)
+    atomicAdd((unsigned long long *)&a.clk->ctr[cRemovedE + a.species], (unsigned long long)removed);
+}
+
+// Push of a charged species, tile by tile: a tile is kPushTile consecutive SPs (cell-sorted by the
+// last sort, apart from the SPs created since).  When the tile's lower-corner nodes span at most
+// kWinSpan node indices, the field of the nodes it reads is first copied into shared memory (four
+// windows of consecutive nodes, one per (dy, dz) corner offset) and gathered from there, and
+// with `a.Q` the tile's CIC charges are summed in shared-memory windows of the new positions and
+// flushed with one global int64 atomic per touched node; otherwise every SP gathers from global
+// memory and adds its 8 charges with global atomics.  The charges are exact integers, so the
+// grouping changes no bit.  SPs whose move may meet the tip or a wall are left to k_cross
+// (velocity written, position kept).
+constexpr int kPushThreads = 256, kPushR = 4, kPushTile = kPushThreads * kPushR;
+constexpr int kWinSpan = 640;                      // node span of a tile that uses the E windows
+constexpr int kWinLen = kWinSpan + 2;              // window length (nodes) for the field
+constexpr int kQWinSpan = 2 * kWinLen - 2;          // node span of a tile that uses the charge windows
+
+__device__ __forceinline__ void block_minmax(uint32_t lo, uint32_t hi, unsigned *s_lo, unsigned *s_hi) {
+  lo = __reduce_min_sync(0xffffffffu, lo);
+  hi = __reduce_max_sync(0xffffffffu, hi);
+  if ((threadIdx.x & 31) == 0) {
+    atomicMin(s_lo, lo);
+    atomicMax(s_hi, hi);
+  }
+}
+
+template <bool kDep>
+__global__ void __launch_bounds__(kPushThreads, 4) k_push_charged(PushArgs a) {
+  __shared__ __align__(16) float4 sE[4 * kWinLen];
+  __shared__ unsigned s_span[4];   // lo, hi of the old corners; lo, hi of the new corners
+  unsigned long long *sQ = reinterpret_cast<unsigned long long *>(sE);
+  const int64_t n = a.clk->n[a.species];
+  const int64_t ntile = (n + kPushTile - 1) / kPushTile;
+  const int tid = threadIdx.x;
+  const uint32_t sy = a.nx + 1, sz = (uint32_t)(a.nx + 1) * (a.ny + 1);
+  if (tid == 0) { s_span[0] = 0xFFFFFFFFu; s_span[1] = 0; s_span[2] = 0xFFFFFFFFu; s_span[3] = 0; }
+  __syncthreads();
+  int removed = 0;
+  for (int64_t tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
+    const int64_t t0 = tile * kPushTile;
+    float x[kPushR], y[kPushR], z[kPushR];
+    int32_t w[kPushR];
+    uint32_t lo = 0xFFFFFFFFu, hi = 0;
+#pragma unroll
+    for (int r = 0; r < kPushR; ++r) {
+      const int64_t i = t0 + r * kPushThreads + tid;
+      w[r] = i < n ? a.p.w[i] : 0;
+      x[r] = y[r] = z[r] = 0.f;
+      if (w[r] > 0) {
+        x[r] = a.p.x[i]; y[r] = a.p.y[i]; z[r] = a.p.z[i];
+        const uint32_t b = (uint32_t)node_index((int)floorf(x[r]), (int)floorf(y[r]), (int)floorf(z[r]), a.nx, a.ny);
+        lo = min(lo, b);
+        hi = max(hi, b);
+      }
+    }
+    block_minmax(lo, hi, &s_span[0], &s_span[1]);
+    __syncthreads();
+    const uint32_t elo = s_span[0], ehi = s_span[1];
+    const bool ewin = ehi >= elo && ehi - elo <= (uint32_t)kWinSpan;
+    const int eL = ewin ? (int)(ehi - elo) + 2 : 0;
+    if (ewin)
+      for (int e = tid; e < 4 * eL; e += kPushThreads) {
+        const int win = e / eL, o = e - win * eL;
+        sE[e] = __ldg(a.E + elo + (uint32_t)o + (uint32_t)(win & 1) * sy + (uint32_t)(win >> 1) * sz);
+      }
+    __syncthreads();
+    if (tid == 0) { s_span[0] = 0xFFFFFFFFu; s_span[1] = 0; }
+    uint32_t base[kPushR], qp[kPushR];
+    lo = 0xFFFFFFFFu;
+    hi = 0;
+#pragma unroll
+    for (int r = 0; r < kPushR; ++r) {
+      const int64_t i = t0 + r * kPushThreads + tid;
+      bool clear = false, cross = false;
+      uint32_t c = kDead;
+      base[r] = kDead;
+      if (w[r] > 0) {
+        float vx = a.p.vx[i], vy = a.p.vy[i], vz = a.p.vz[i];
+        const float3 e = ewin ? gather_E_win(sE, eL, elo, x[r], y[r], z[r], a.nx, a.ny)
+                              : gather_E(a.E, x[r], y[r], z[r], a.nx, a.ny);
+        float x1 = x[r], y1 = y[r], z1 = z[r];
+        leapfrog(a.qmdt, a.dtdx, e, true, x1, y1, z1, vx, vy, vz);
+        a.p.vx[i] = vx; a.p.vy[i] = vy; a.p.vz[i] = vz;
+        const int cls = move_class(a, x[r], y[r], z[r], x1, y1, z1, &c);
+        clear = cls == 0;
+        cross = cls == 1;
+        if (!cross) { a.p.x[i] = x1; a.p.y[i] = y1; a.p.z[i] = z1; }
+        if (cls == 2) ++removed;
+        if (clear && kDep) {
+          base[r] = cic_corner(x1, y1, z1, a.nx, a.ny, &qp[r]);
+          lo = min(lo, base[r]);
+          hi = max(hi, base[r]);
+        }
+      }
+      if (i < n && !clear && !cross) a.key[i] = kDead;
+      if (clear) a.key[i] = c;
+      count_cell(a.cnt, c, clear);
+      enqueue(a, i, cross);
+    }
+    if (kDep) {
+      block_minmax(lo, hi, &s_span[2], &s_span[3]);
+      __syncthreads();   // every gather of the tile is done: the windows' memory is free
+      const uint32_t qlo = s_span[2], qhi = s_span[3];
+      const bool qwin = qhi >= qlo && qhi - qlo <= (uint32_t)kQWinSpan;
+      const int qL = qwin ? (int)(qhi - qlo) + 2 : 0;
+      if (qwin)
+        for (int e = tid; e < 4 * qL; e += kPushThreads) sQ[e] = 0ull;
+      __syncthreads();
+      if (tid == 0) { s_span[2] = 0xFFFFFFFFu; s_span[3] = 0; }
+#pragma unroll
+      for (int r = 0; r < kPushR; ++r) {
+        if (base[r] == kDead) continue;
+        const int32_t zw = a.Z * w[r];
+        if (qwin) {
+          long long c[8];
+          cic_charges(qp[r], zw, c);
+          const int o = (int)(base[r] - qlo);
+#pragma unroll
+          for (int q = 0; q < 8; ++q)
+            if (c[q] != 0) atomicAdd(sQ + ((q >> 1) * qL + o + (q & 1)), (unsigned long long)c[q]);
+        } else {
+          cic_global(a.Q, base[r], qp[r], zw, a.nx, a.ny);
+        }
+      }
+      __syncthreads();
+      if (qwin)
+        for (int e = tid; e < 4 * qL; e += kPushThreads) {
+          const unsigned long long v = sQ[e];
+          const int win = e / qL, o = e - win * qL;
+          if (v) atomicAdd(a.Q + qlo + (uint32_t)o + (uint32_t)(win & 1) * sy + (uint32_t)(win >> 1) * sz, v);
+        }
+    }
+    __syncthreads();   // the windows are reused by the next tile
+  }
+  for (int o = 16; o > 0; o >>= 1) removed += __shfl_down_sync(0xffffffffu, removed, o);
+  if ((threadIdx.x & 31) == 0 && removed)
+    atomicAdd((unsigned long long *)&a.clk->ctr[cRemovedE + a.species], (unsigned long long)removed);
+}
+
+// The queued crossers of a push: the same float32 move from the kept position and the pushed
+// velocity, then the FP64 traversal decides removal (and records ion impacts); survivors get
+// their key, count and (with a.Q) charge.
+__global__ void __launch_bounds__(256) k_cross(PushArgs a) {
+  const int nq = *a.xq_n;
+  int removed = 0;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x) {
+    const uint32_t i = a.xq[q];
+    const float x = a.p.x[i], y = a.p.y[i], z = a.p.z[i];
+    const float vx = a.p.vx[i], vy = a.p.vy[i], vz = a.p.vz[i];
+    const int32_t w = a.p.w[i];
     const float x1 = __fadd_rn(x, __fmul_rn(vx, a.dtdx));
     const float y1 = __fadd_rn(y, __fmul_rn(vy, a.dtdx));
     const float z1 = __fadd_rn(z, __fmul_rn(vz, a.dtdx));
     a.p.x[i] = x1; a.p.y[i] = y1; a.p.z[i] = z1;
-    a.p.vx[i] = vx; a.p.vy[i] = vy; a.p.vz[i] = vz;
-    const int i0 = (int)floorf(x), j0 = (int)floorf(y), k0 = (int)floorf(z);
-    bool alive = isfinite(x1) && isfinite(y1) && isfinite(z1);
-    int i1 = 0, j1 = 0, k1 = 0;
-    if (alive) {
-      i1 = (int)fminf(fmaxf(floorf(x1), -1.f), (float)a.nx);
-      j1 = (int)fminf(fmaxf(floorf(y1), -1.f), (float)a.ny);
-      k1 = (int)fminf(fmaxf(floorf(z1), -1.f), (float)a.nz);
-      if (i1 != i0 || j1 != j0 || k1 != k0) {
-        const int m = max(abs(i1 - i0), max(abs(j1 - j0), abs(k1 - k0)));
-        const bool inside = i1 >= 0 && i1 < a.nx && j1 >= 0 && j1 < a.ny && k1 >= 0 && k1 < a.nz;
-        const bool clear = inside && (int)a.cheb[cell_index(i0, j0, k0, a.nx, a.ny)] > m;
-        if (!clear) alive = !crosser_event(a, x, y, z, x1, y1, z1, vx, vy, vz, w);
-      }
-    }
-    if (alive) {
-      const uint32_t c = (uint32_t)cell_index(i1, j1, k1, a.nx, a.ny);
-      a.key[i] = c;
-      // cell-sorted SPs mostly stay in their cell: lanes with the same new cell add their count
-      // with one atomic (the counts are integers, so nothing depends on the grouping)
-      const unsigned act = __activemask();
-      const unsigned grp = __match_any_sync(act, c);
-      if ((int)(threadIdx.x & 31) == __ffs(grp) - 1) atomicAdd(&a.cnt[c], (uint32_t)__popc(grp));
-    } else {
+    if (crosser_event(a, x, y, z, x1, y1, z1, vx, vy, vz, w)) {
       a.key[i] = kDead;
       ++removed;
+      continue;
+    }
+    const uint32_t c = (uint32_t)cell_index((int)floorf(x1), (int)floorf(y1), (int)floorf(z1), a.nx, a.ny);
+    a.key[i] = c;
+    atomicAdd(&a.cnt[c], 1u);
+    if (a.Q) {
+      uint32_t qp;
+      const uint32_t b = cic_corner(x1, y1, z1, a.nx, a.ny, &qp);
+      cic_global(a.Q, b, qp, a.Z * w, a.nx, a.ny);
     }
   }
-  // one atomic per warp for the removal counter
   for (int o = 16; o > 0; o >>= 1) removed += __shfl_down_sync(0xffffffffu, removed, o);
   if ((threadIdx.x & 31) == 0 && removed)
     atomicAdd((unsigned long long *)&a.clk->ctr[cRemovedE + a.species], (unsigned long long)removed);
@@ -401,7 +654,12 @@ int stage_keys(pic_t *h, int s) {
   return launch_check(h, "keys");
 }
 
-int stage_push(pic_t *h) {
+int stage_push(pic_t *h, bool deposit) {
+  if (deposit) {   // timed with the push: clearing the charge is part of producing it
+    KtScope kt_(h, kidPush, 0);
+    PIC_CUDA(h, cudaMemsetAsync(h->Q, 0, h->nnode * sizeof(unsigned long long), h->stream));
+  }
+  PIC_CUDA(h, cudaMemsetAsync(h->xq_n, 0, 3 * sizeof(int), h->stream));
   for (int s = 0; s < 3; ++s) {
     Species &S = h->sp[s];
     if (h->keys_valid[s]) PIC_CUDA(h, cudaMemsetAsync(S.cnt, 0, (h->ncell + 1) * sizeof(uint32_t), h->stream));
@@ -414,8 +672,18 @@ int stage_push(pic_t *h) {
     a.face_key = h->faces.key; a.nface = h->faces.n;
     a.acc_sput = (unsigned long long *)h->faces.acc_sput; a.acc_Eb = (unsigned long long *)h->faces.acc_Eb;
     a.clk = h->clock;
-    ++h->nlaunch;
-    { KtScope kt_(h, kidPush, 0); k_push<<<particle_grid(h), kThreads, 0, h->stream>>>(a); }
+    a.Q = deposit && S.Z != 0 ? h->Q : nullptr;
+    a.Z = S.Z;
+    a.xq = S.perm;   // free until the sort
+    a.xq_n = h->xq_n + s;
+    h->nlaunch += 2;
+    {
+      KtScope kt_(h, kidPush, 0);
+      if (S.Z == 0) k_push_neutral<<<particle_grid(h), kThreads, 0, h->stream>>>(a);
+      else if (a.Q) k_push_charged<true><<<h->nsm * 4, kPushThreads, 0, h->stream>>>(a);
+      else k_push_charged<false><<<h->nsm * 4, kPushThreads, 0, h->stream>>>(a);
+    }
+    { KtScope kt_(h, kidCross, 0); k_cross<<<h->nsm * 2, 256, 0, h->stream>>>(a); }
     h->keys_valid[s] = true;
   }
   return launch_check(h, "push");
@@ -436,8 +704,11 @@ __device__ __forceinline__ float merge_comp(double q1, double q2, float a1, floa
 // One work item per sorted SP (its cell from the sort's per-position key): the SP at an even
 // place 2m of a cell above the cap merges with its successor when m < min(N - M, N/2), so the
 // pairs of a dense cell spread over many threads.
+// With Q (the push has deposited this step's charge), a merged pair of a charged species moves its
+// charge: the two SPs' CIC charges are taken off and the merged SP's added (exact int64 sums).
 __global__ void __launch_bounds__(256) k_merge(SpeciesBuf p, const uint32_t *off, const uint32_t *skey, int s, uint32_t M,
-                                               int32_t wmax, DevClock *clk) {
+                                               int32_t wmax, DevClock *clk, unsigned long long *Q, int Z, int nx,
+                                               int ny) {
   const int64_t n = clk->n_sorted[s];
   int done = 0;
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
@@ -452,6 +723,13 @@ __global__ void __launch_bounds__(256) k_merge(SpeciesBuf p, const uint32_t *off
     const double d1 = w1, d2 = w2;
     const double mu = __ddiv_rn(__dmul_rn(d1, d2), __dadd_rn(d1, d2));
     const double q1 = __ddiv_rn(mu, d2), q2 = __ddiv_rn(mu, d1);
+    if (Q) {
+      uint32_t qa, qb;
+      const uint32_t ba = cic_corner(p.x[a], p.y[a], p.z[a], nx, ny, &qa);
+      const uint32_t bb = cic_corner(p.x[b], p.y[b], p.z[b], nx, ny, &qb);
+      cic_global(Q, ba, qa, -Z * w1, nx, ny);
+      cic_global(Q, bb, qb, -Z * w2, nx, ny);
+    }
     p.x[a] = merge_comp(q1, q2, p.x[a], p.x[b]);
     p.y[a] = merge_comp(q1, q2, p.y[a], p.y[b]);
     p.z[a] = merge_comp(q1, q2, p.z[a], p.z[b]);
@@ -460,13 +738,18 @@ __global__ void __launch_bounds__(256) k_merge(SpeciesBuf p, const uint32_t *off
     p.vz[a] = merge_comp(q1, q2, p.vz[a], p.vz[b]);
     p.w[a] = w1 + w2;
     p.w[b] = 0;
+    if (Q) {
+      uint32_t qm;
+      const uint32_t bm = cic_corner(p.x[a], p.y[a], p.z[a], nx, ny, &qm);
+      cic_global(Q, bm, qm, Z * (w1 + w2), nx, ny);
+    }
     ++done;
   }
   for (int sh = 16; sh > 0; sh >>= 1) done += __shfl_down_sync(0xffffffffu, done, sh);
   if ((threadIdx.x & 31) == 0 && done) atomicAdd((unsigned long long *)&clk->ctr[cMerged], (unsigned long long)done);
 }
 
-int stage_merge(pic_t *h) {
+int stage_merge(pic_t *h, bool fix_charge) {
   if (!(h->prm.flags & PIC_F_MERGE)) return PIC_OK;
   for (int s = 0; s < 3; ++s) if (h->keys_valid[s]) return pic_fail(h, PIC_E_INVALID, "merging needs cell-sorted SPs");
   const uint32_t M = h->prm.merge_max > 0 ? (uint32_t)h->prm.merge_max : 32u;
@@ -474,7 +757,9 @@ int stage_merge(pic_t *h) {
   h->nlaunch += 3;
   KtScope kt_(h, kidMerge, 0);
   for (int s = 0; s < 3; ++s)
-    k_merge<<<h->nsm * 8, kThreads, 0, h->stream>>>(h->sp[s].a, h->sp[s].off, h->sp[s].skey, s, M, wmax, h->clock);
+    k_merge<<<h->nsm * 8, kThreads, 0, h->stream>>>(h->sp[s].a, h->sp[s].off, h->sp[s].skey, s, M, wmax, h->clock,
+                                                    fix_charge && h->sp[s].Z != 0 ? h->Q : nullptr, h->sp[s].Z,
+                                                    h->nx, h->ny);
   return launch_check(h, "merge");
 }
 

@@ -57,6 +57,16 @@ int launch_check(pic_t *h, const char *what) {
   return PIC_OK;
 }
 
+int check_device(pic_t *h) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return pic_fail(h, PIC_E_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+  if (dev != h->device)
+    return pic_fail(h, PIC_E_INVALID, "the current device (" + std::to_string(dev) + ") is not the handle's device (" +
+                                          std::to_string(h->device) + "); make it current first");
+  return PIC_OK;
+}
+
 // ---- host geometry (same rules as the statement in pic.h) -----------------------------------
 struct HostGeom {
   std::vector<uint8_t> solid, cheb, dir0;
@@ -199,7 +209,7 @@ const char *const kKernelNames[kidNum] = {
     "k_scan_apply", "k_deposit", "k_mcc_count", "k_mcc_products", "k_elastic", "k_coulomb", "k_merge", "k_dfi_count", "k_dfi_products", "k_dirichlet",
     "k_residual64", "k_norm_sum", "k_smooth", "k_smooth_first", "k_residual", "k_restrict", "k_prolong", "k_coarse", "k_vcycle_tail", "k_ramo",
     "k_correct", "k_efield", "k_face_field", "k_emit_surrogate", "k_emit_fallback", "k_emit_count", "k_emit_write",
-    "k_inject_count", "k_inject_write", "k_mlp_forward", "k_heat"};
+    "k_inject_count", "k_inject_write", "k_mlp_forward", "k_heat", "k_cross"};
 
 KtScope::KtScope(pic_t *h_, int kid_, double units_) : h(h_), kid(kid_), units(units_) {
   on = h && (h->kt_mask >> kid & 1ull);
@@ -323,6 +333,7 @@ int pic_create(const pic_geometry_t *geometry, const pic_grid_t *grid, const pic
   h->alloc = alloc; h->free_fn = free_fn; h->alloc_user = alloc_user;
   int dev = 0;
   cudaGetDevice(&dev);
+  h->device = dev;
   cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, dev);
   if (h->nsm <= 0) h->nsm = 148;
   auto fail = [&](int code, const std::string &m) {
@@ -436,6 +447,7 @@ int pic_create(const pic_geometry_t *geometry, const pic_grid_t *grid, const pic
     h->mid_list = alloc_n<int2>(h, h->mid_cap); A(h->mid_list);
   }
   h->long_n = alloc_n<int>(h, 16); A(h->long_n);
+  h->xq_n = alloc_n<int>(h, 4); A(h->xq_n);
   h->clock = alloc_n<DevClock>(h, 1); A(h->clock);
   if (!okalloc) return fail(PIC_E_CUDA, "device allocation failed");
   // uploads
@@ -733,6 +745,14 @@ int pic_set_flags(pic_t *h, uint32_t flags) {
   return PIC_OK;
 }
 
+int pic_set_solver(pic_t *h, double mg_tol, int mg_max_cycles) {
+  if (!h || !(mg_tol > 0) || mg_max_cycles < 1) return PIC_E_INVALID;
+  h->prm.mg_tol = mg_tol;
+  h->prm.mg_max_cycles = mg_max_cycles;
+  graph_invalidate(h);   // the recorded convergence test holds the old values
+  return PIC_OK;
+}
+
 int pic_emit(pic_t *h) {
   if (!h) return PIC_E_INVALID;
   PIC_TRY(stage_emit(h));
@@ -833,12 +853,11 @@ static int step_body_graph(pic_t *h) {
   ++h->nlaunch;
   k_begin_step<<<1, 1, 0, h->stream>>>(h->clock);
   PIC_TRY(stage_emit(h));
-  PIC_TRY(stage_push(h));
+  PIC_TRY(stage_push(h, true));   // the charge deposit runs in the push (see pic_step_eager)
   PIC_TRY(stage_circuit(h));
   PIC_TRY(stage_sort(h));
-  PIC_TRY(stage_merge(h));
+  PIC_TRY(stage_merge(h, true));
   PIC_TRY(stage_collide(h));
-  PIC_TRY(stage_deposit(h));
   PIC_TRY(stage_extrapolate(h));
   PIC_TRY(stage_solve_graph(h, h->V0));
   ++h->nlaunch;
@@ -1240,15 +1259,20 @@ static int pic_step_eager(pic_t *h, int nsteps, int64_t step) {
     k_begin_step<<<1, 1, 0, h->stream>>>(h->clock);
     rc = stage_emit(h);
     cudaEventRecord(ev[1], h->stream);
-    if (rc == PIC_OK) rc = stage_push(h);
+    // The charge of the step is deposited by the push, from the pushed positions of the charged
+    // SPs that stay in the domain.  Nothing after it changes the charge on any node: impact and
+    // field ionization put the new ion and its electron on the same position with the same weight
+    // (their CIC charges cancel exactly), SP splitting keeps the position and the weight sum, the
+    // elastic, exchange and Coulomb passes change velocities only, and merging moves its pairs'
+    // charges itself.  The deposit stage of the step is therefore empty; its time is in the push.
+    if (rc == PIC_OK) rc = stage_push(h, true);
     if (rc == PIC_OK) rc = stage_circuit(h);
     cudaEventRecord(ev[2], h->stream);
     if (rc == PIC_OK) rc = stage_sort(h);
-    if (rc == PIC_OK) rc = stage_merge(h);
+    if (rc == PIC_OK) rc = stage_merge(h, true);
     cudaEventRecord(ev[3], h->stream);
     if (rc == PIC_OK) rc = stage_collide(h);
     cudaEventRecord(ev[4], h->stream);
-    if (rc == PIC_OK) rc = stage_deposit(h);
     cudaEventRecord(ev[5], h->stream);
     if (rc == PIC_OK) rc = stage_extrapolate(h);
     if (rc == PIC_OK) rc = stage_solve(h, false, h->V0);
@@ -1375,6 +1399,7 @@ int pic_diagnostics(pic_t *h, pic_diag_t *out) {
 int pic_emission_eval(pic_t *h, const double *F, const double *T, const double *phi_w, const double *R, double *J,
                       double *PN, int64_t n) {
   if (!h || n < 0 || (n > 0 && (!F || !T || !phi_w || !R || !J || !PN))) return PIC_E_INVALID;
+  PIC_TRY(check_device(h));
   if (n == 0) return PIC_OK;
   double *buf = nullptr;
   PIC_CUDA(h, cudaMalloc(&buf, (size_t)n * 6 * 8));

@@ -154,6 +154,7 @@ struct pic_s {
   std::vector<std::pair<void *, size_t>> allocations;
   std::string last_error;
   int nsm = 148;
+  int device = -1;               // CUDA device current at pic_create; every later call must run there
 
   // device state
   uint8_t *solid = nullptr;      // per cell
@@ -193,6 +194,7 @@ struct pic_s {
   int2 *mid_list = nullptr;      // sort: 5..32-SP cell segments queued for the warp-level fix-up
   int64_t mid_cap = 0;
   int *long_n = nullptr;
+  int *xq_n = nullptr;           // push: lengths of the per-species crosser queues
   // state flags and last diagnostics
   bool keys_valid[3] = {false, false, false};
   int last_mg_cycles = 0;
@@ -292,7 +294,7 @@ enum Kid : int {
   kidDeposit, kidMccCount, kidMccProducts, kidElastic, kidCoulomb, kidMerge, kidDfiCount, kidDfiProducts, kidDirichlet, kidResidual64, kidNormSum,
   kidSmooth, kidSmoothFirst, kidResidual, kidRestrict, kidProlong, kidCoarse, kidTail, kidRamo, kidCorrect, kidEfield, kidFaceField,
   kidEmitSurrogate, kidEmitFallback, kidEmitCount, kidEmitWrite, kidInjectCount, kidInjectWrite, kidMlpForward,
-  kidHeat, kidNum
+  kidHeat, kidCross, kidNum
 };
 extern const char *const kKernelNames[kidNum];
 // Records an event before the launches of its scope and one after them, on the library stream,
@@ -329,6 +331,8 @@ namespace pic {
 void *dalloc(pic_t *h, size_t bytes);
 void dfree(pic_t *h, void *p);
 int launch_check(pic_t *h, const char *what);
+// PIC_E_INVALID when the calling thread's current device is not the handle's device
+int check_device(pic_t *h);
 
 // scans (k_scan.cu): exclusive scans of n values; n either a host size or a device int64
 int scan_u32(pic_t *h, const uint32_t *in, uint32_t *out, int64_t n, const int64_t *n_dev, uint32_t *total);
@@ -336,7 +340,8 @@ int scan_u64(pic_t *h, const uint64_t *in, uint64_t *out, int64_t n, const int64
 
 // particles (k_particles.cu)
 int stage_keys(pic_t *h, int s);
-int stage_push(pic_t *h);
+// deposit: clear the charge and add the pushed SPs' CIC charges in the push (the step's form)
+int stage_push(pic_t *h, bool deposit = false);
 int stage_sort(pic_t *h);
 int stage_deposit(pic_t *h);
 // collisions (k_collide.cu)
@@ -366,7 +371,8 @@ int circuit_setup(pic_t *h, double V_L);
 int circuit_reset(pic_t *h);
 int stage_circuit(pic_t *h);
 int stage_extrapolate(pic_t *h);
-int stage_merge(pic_t *h);
+// fix_charge: the push deposited this step's charge, merged pairs move theirs
+int stage_merge(pic_t *h, bool fix_charge = false);
 int sort_species(pic_t *h, int s);
 int validate_loaded(pic_t *h, const SpeciesBuf &p, int64_t n);
 // heat (k_heat.cu)
@@ -375,6 +381,9 @@ int stage_heat(pic_t *h);
 bool surrogate_ready(pic_t *h);
 void mlp_forget(pic_t *h);
 int surrogate_faces(pic_t *h, const uint8_t **elig, const float **Y);
+int surrogate_bins();
+int surrogate_export(pic_t *h, float *master, uint8_t *binok, int *trained);
+int surrogate_import(pic_t *h, const float *master, const uint8_t *binok, int trained);
 // fused surrogate forward pass on the tcgen05 tensor cores (k_mlp_tc.cu); __nv_bfloat16 passed as void
 int mlp_forward_tc(pic_t *h, const float *X, int64_t rows, const float *master, const struct __nv_bfloat16 *w2,
                    const struct __nv_bfloat16 *w3, float *Y);

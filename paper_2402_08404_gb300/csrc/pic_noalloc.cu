@@ -10,7 +10,9 @@
 // library holds it (1.5 MiB) until the process exits.  Host code must not pass the symbol
 // itself to a kernel (on the host it is only a stand-in); its device address is looked up once
 // per device with cudaGetSymbolAddress, with that device current, on the first call made on
-// that device.  Make that first call before any stream capture starts on the device.
+// that device.  Make that first call before any stream capture starts on the device.  A call
+// made while another device is current is refused with PIC_E_INVALID (the staging address and
+// the handle's stream would belong to different GPUs).
 //
 // All calls share the one array: two calls whose work overlaps on the GPU (different streams,
 // different threads) race on it and must be serialised by the caller.  Nothing in it has to
@@ -31,11 +33,11 @@ constexpr int kMaxDevices = 128;
 static std::mutex g_staging_mutex;
 static double *g_staging_ptr[kMaxDevices] = {};
 
-// Device address of the staging array on the current device (looked up once per device).
+// Device address of the staging array on the handle's device, which the caller has checked is
+// current (looked up once per device).
 static int staging_address(pic_t *h, double **out) {
-  int dev = -1;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return pic_fail(h, PIC_E_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+  const int dev = h->device;
+  cudaError_t e = cudaSuccess;
   if (dev < 0 || dev >= kMaxDevices) return pic_fail(h, PIC_E_INVALID, "device index out of range");
   std::lock_guard<std::mutex> lock(g_staging_mutex);
   if (!g_staging_ptr[dev]) {
@@ -60,6 +62,7 @@ extern "C" int pic_emission_eval_noalloc(pic_t *h, const double *F, const double
     return pic_fail(h, PIC_E_INVALID, "pic_emission_eval_noalloc: n = " + std::to_string(n) +
                                           " exceeds the fixed staging size of " + std::to_string(kNoAllocMax) +
                                           " tuples; split the call");
+  PIC_TRY(check_device(h));
   if (n == 0) return PIC_OK;
   double *buf = nullptr;
   PIC_TRY(staging_address(h, &buf));

@@ -98,6 +98,8 @@ def lib():
         L.pic_load_particles.argtypes = [vp, i32] + [vp] * 8 + [i64]
         L.pic_get_particles.argtypes = [vp, i32] + [vp] * 8 + [i64, C.POINTER(i64)]
         L.pic_set_clock.argtypes = [vp, i64, i64]
+        L.pic_save.argtypes = [vp, C.c_char_p]
+        L.pic_load.argtypes = [vp, C.c_char_p]
         for name in ("pic_set_potential", "pic_get_potential", "pic_get_efield", "pic_get_charge",
                      "pic_set_temperature", "pic_get_temperature"):
             getattr(L, name).argtypes = [vp, vp]
@@ -111,6 +113,7 @@ def lib():
         L.pic_emission_eval.argtypes = [vp] * 7 + [i64]
         L.pic_emission_eval_noalloc.argtypes = [vp] * 7 + [i64]
         L.pic_set_flags.argtypes = [vp, C.c_uint32]
+        L.pic_set_solver.argtypes = [vp, C.c_double, i32]
         L.pic_mlp_num_params.argtypes = []
         L.pic_mlp_set_params.argtypes = [vp, vp]
         L.pic_mlp_get_params.argtypes = [vp, vp]
@@ -243,6 +246,14 @@ class Pic:
     def set_clock(self, step, next_id):
         self._check(lib().pic_set_clock(self.h, int(step), int(next_id)))
 
+    def save(self, path):
+        """pic_save: the whole evolving state to a file (between steps or after a sort)."""
+        self._check(lib().pic_save(self.h, os.fsencode(path)))
+
+    def load(self, path):
+        """pic_load: state from a pic_save file into this handle (same creation inputs)."""
+        self._check(lib().pic_load(self.h, os.fsencode(path)))
+
     def set_potential(self, phi):
         a = np.ascontiguousarray(phi, dtype=np.float64).reshape(-1)
         assert a.size == self.nnode
@@ -299,6 +310,9 @@ class Pic:
 
     def set_flags(self, flags):
         self._check(lib().pic_set_flags(self.h, int(flags)))
+
+    def set_solver(self, mg_tol, mg_max_cycles):
+        self._check(lib().pic_set_solver(self.h, float(mg_tol), int(mg_max_cycles)))
 
     # -- stages --------------------------------------------------------------------------------
     def emit(self):

@@ -40,6 +40,18 @@ def test_noalloc_matches_allocating_entry_point_twice(sim):
         assert np.allclose(P, P_ref, rtol=1e-12, atol=1e-30)
 
 
+def test_noalloc_at_its_full_size(sim):
+    # n equal to the array's size: the last slot of every staged sub-array is used
+    n = 32768
+    F, T, W, R = synth.face_tuples(n, seed=9)
+    R = np.where(np.arange(n) % 5 == 0, -1.0, R * 1e-9)
+    J_ref, P_ref = sim.emission_eval(F * 1e9, T, W, R)
+    J, P = sim.emission_eval_noalloc(F * 1e9, T, W, R)
+    assert np.allclose(J, J_ref, rtol=1e-12, atol=0.0)
+    assert np.allclose(P, P_ref, rtol=1e-12, atol=1e-30)
+    assert J[-1] == J_ref[-1] and P[-1] == P_ref[-1]
+
+
 def test_noalloc_rejects_sizes_beyond_its_array(sim):
     from paper_2402_08404_gb300 import pic
     n = 32768 + 1
