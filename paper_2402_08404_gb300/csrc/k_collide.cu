@@ -199,30 +199,67 @@ __device__ int mcc_ncoll(const McArgs &a, const Pair &pr, int64_t step) {
   return ncoll > wt ? wt : ncoll;
 }
 
-// Work items: sorted electrons, then sorted neutrals; events staged with payload ncoll.
+// Work items: sorted electrons, then sorted neutrals; events staged with payload ncoll.  A warp
+// takes a unit of kEvUnit items in two passes: the first finds the unit's projectiles (the items
+// of the species with fewer SPs in their cell) and queues their pairs in shared memory in item
+// order; the second evaluates the queued pairs 32 at a time, so every lane works on a pair (the
+// projectiles are a fraction of the items, and evaluating them in place left most lanes idle).
+struct McQueued {
+  uint32_t t;        // work item
+  uint32_t ie, in;   // electron and neutral of the pair
+  uint32_t nt;       // target SPs in the cell; bit 31: the electron is the projectile
+};
+
 __global__ void __launch_bounds__(256) k_mcc_count(McArgs a, EvBlocks ev) {
+  __shared__ McQueued queue[256 / 32][kEvUnit];
+  McQueued *qw = queue[threadIdx.x >> 5];
+  const int lane = threadIdx.x & 31;
   const int64_t ne = a.clk->n_sorted[PIC_ELECTRON], nn = a.clk->n_sorted[PIC_NEUTRAL];
   const int64_t step = a.clk->step;
   const int64_t total = ne + nn, nunit = (total + kEvUnit - 1) / kEvUnit;
   for (int64_t unit = ev_warp(); unit < nunit; unit += ev_nwarp()) {
     const int64_t lo = unit * kEvUnit, hi = min(total, lo + kEvUnit);
-    int64_t run = 0;
-    uint64_t prod = 0;
+    int nq = 0;
     for (int64_t base = lo; base < hi; base += 32) {
-      const int64_t t = base + (threadIdx.x & 31);
+      const int64_t t = base + lane;
       McItem m{};
       if (t < hi) m = mc_item(a, t, ne);
       const uint32_t w = cell_word(a.seed, kPair, m.c, m.proj, step);
-      int ncoll = 0;
-      uint64_t pc = 0;
+      const unsigned bal = __ballot_sync(0xffffffffu, m.proj);
       if (m.proj) {
         const Pair pr = mc_pair(m, t, ne, w);
+        McQueued e;
+        e.t = (uint32_t)(t - lo);
+        e.ie = (uint32_t)pr.ie;
+        e.in = (uint32_t)pr.in;
+        e.nt = pr.Nt | (pr.proj_e ? 0x80000000u : 0u);
+        qw[nq + __popc(bal & ((1u << lane) - 1u))] = e;
+      }
+      nq += __popc(bal);
+    }
+    __syncwarp();
+    int64_t run = 0;
+    uint64_t prod = 0;
+    for (int b = 0; b < nq; b += 32) {
+      const int i = b + lane;
+      int ncoll = 0;
+      uint64_t pc = 0;
+      int64_t t = lo;
+      if (i < nq) {
+        const McQueued e = qw[i];
+        Pair pr;
+        pr.ie = e.ie;
+        pr.in = e.in;
+        pr.proj_e = (e.nt >> 31) & 1;
+        pr.Nt = e.nt & 0x7fffffffu;
+        t = lo + e.t;
         ncoll = mcc_ncoll(a, pr, step);
         if (ncoll > 0) pc = 1ull | ((uint64_t)(ncoll < a.e.w[pr.ie] ? 2 : 1) << 32);
       }
       ev_stage(ev, lo, &run, &prod, t, (uint32_t)ncoll, pc);
     }
-    if ((threadIdx.x & 31) == 0) {
+    __syncwarp();
+    if (lane == 0) {
       ev.hits[unit] = (int)run;
       ev.cnt[unit] = prod;
     }

@@ -127,13 +127,22 @@ __device__ __forceinline__ uint32_t cic_corner(float x, float y, float z, int nx
 }
 
 // The 8 node charges Z w prod(W) of one SP (int64, exact): corner c = dx + 2 dy + 4 dz.
+// The 8 weight products W = prod over the axes of (2^F - q) or q, corner c = dx + 2 dy + 4 dz
+// (each below 2^30, exact in 32 bits).
+__device__ __forceinline__ void cic_weights(uint32_t qpack, uint32_t W[8]) {
+  const uint32_t one = 1u << kFracBits;
+  const uint32_t qx = qpack & 1023u, qy = (qpack >> 10) & 1023u, qz = qpack >> 20;
+  const uint32_t a00 = (one - qz) * (one - qy), a10 = (one - qz) * qy, a01 = qz * (one - qy), a11 = qz * qy;
+  W[0] = a00 * (one - qx); W[1] = a00 * qx; W[2] = a10 * (one - qx); W[3] = a10 * qx;
+  W[4] = a01 * (one - qx); W[5] = a01 * qx; W[6] = a11 * (one - qx); W[7] = a11 * qx;
+}
+
+// The 8 node charges Z w W of one SP (int64, exact).
 __device__ __forceinline__ void cic_charges(uint32_t qpack, int32_t zw, long long c[8]) {
-  const int64_t one = 1 << kFracBits;
-  const int64_t qx = qpack & 1023u, qy = (qpack >> 10) & 1023u, qz = qpack >> 20;
-  const int64_t a00 = (int64_t)zw * (one - qz) * (one - qy), a10 = (int64_t)zw * (one - qz) * qy;
-  const int64_t a01 = (int64_t)zw * qz * (one - qy), a11 = (int64_t)zw * qz * qy;
-  c[0] = a00 * (one - qx); c[1] = a00 * qx; c[2] = a10 * (one - qx); c[3] = a10 * qx;
-  c[4] = a01 * (one - qx); c[5] = a01 * qx; c[6] = a11 * (one - qx); c[7] = a11 * qx;
+  uint32_t W[8];
+  cic_weights(qpack, W);
+#pragma unroll
+  for (int q = 0; q < 8; ++q) c[q] = (long long)zw * (long long)W[q];
 }
 
 __device__ __forceinline__ void cic_global(unsigned long long *Q, uint32_t base, uint32_t qpack, int32_t zw, int nx,
@@ -157,25 +166,6 @@ __device__ __forceinline__ void leapfrog(float qmdt, float dtdx, float3 e, bool 
   x = __fadd_rn(x, __fmul_rn(vx, dtdx));
   y = __fadd_rn(y, __fmul_rn(vy, dtdx));
   z = __fadd_rn(z, __fmul_rn(vz, dtdx));
-}
-
-// E at x^n from the shared-memory copy of the tile's node windows: window (dz, dy) holds the
-// nodes lo + (dz sz + dy sy) + [0, L).
-__device__ __forceinline__ float3 gather_E_win(const float4 *sE, int L, uint32_t lo, float x, float y, float z, int nx,
-                                               int ny) {
-  const float fi = floorf(x), fj = floorf(y), fk = floorf(z);
-  const float fx = __fsub_rn(x, fi), fy = __fsub_rn(y, fj), fz = __fsub_rn(z, fk);
-  const int o = (int)((uint32_t)node_index((int)fi, (int)fj, (int)fk, nx, ny) - lo);
-  const float4 e000 = sE[o], e100 = sE[o + 1], e010 = sE[L + o], e110 = sE[L + o + 1];
-  const float4 e001 = sE[2 * L + o], e101 = sE[2 * L + o + 1], e011 = sE[3 * L + o], e111 = sE[3 * L + o + 1];
-  float3 r;
-  r.x = lerp_rn(lerp_rn(lerp_rn(e000.x, e100.x, fx), lerp_rn(e010.x, e110.x, fx), fy),
-                lerp_rn(lerp_rn(e001.x, e101.x, fx), lerp_rn(e011.x, e111.x, fx), fy), fz);
-  r.y = lerp_rn(lerp_rn(lerp_rn(e000.y, e100.y, fx), lerp_rn(e010.y, e110.y, fx), fy),
-                lerp_rn(lerp_rn(e001.y, e101.y, fx), lerp_rn(e011.y, e111.y, fx), fy), fz);
-  r.z = lerp_rn(lerp_rn(lerp_rn(e000.z, e100.z, fx), lerp_rn(e010.z, e110.z, fx), fy),
-                lerp_rn(lerp_rn(e001.z, e101.z, fx), lerp_rn(e011.z, e111.z, fx), fy), fz);
-  return r;
 }
 
 // Cell of the pushed position and whether the move stays clear of the tip and the walls: an SP
@@ -246,139 +236,72 @@ __global__ void __launch_bounds__(256) k_push_neutral(PushArgs a) {
     atomicAdd((unsigned long long *)&a.clk->ctr[cRemovedE + a.species], (unsigned long long)removed);
 }
 
-// Push of a charged species, tile by tile: a tile is kPushTile consecutive SPs (cell-sorted by the
-// last sort, apart from the SPs created since).  When the tile's lower-corner nodes span at most
-// kWinSpan node indices, the field of the nodes it reads is first copied into shared memory (four
-// windows of consecutive nodes, one per (dy, dz) corner offset) and gathered from there, and
-// with `a.Q` the tile's CIC charges are summed in shared-memory windows of the new positions and
-// flushed with one global int64 atomic per touched node; otherwise every SP gathers from global
-// memory and adds its 8 charges with global atomics.  The charges are exact integers, so the
-// grouping changes no bit.  SPs whose move may meet the tip or a wall are left to k_cross
-// (velocity written, position kept).
-constexpr int kPushThreads = 256, kPushR = 4, kPushTile = kPushThreads * kPushR;
-constexpr int kWinSpan = 640;                      // node span of a tile that uses the E windows
-constexpr int kWinLen = kWinSpan + 2;              // window length (nodes) for the field
-constexpr int kQWinSpan = 2 * kWinLen - 2;          // node span of a tile that uses the charge windows
-
-__device__ __forceinline__ void block_minmax(uint32_t lo, uint32_t hi, unsigned *s_lo, unsigned *s_hi) {
-  lo = __reduce_min_sync(0xffffffffu, lo);
-  hi = __reduce_max_sync(0xffffffffu, hi);
-  if ((threadIdx.x & 31) == 0) {
-    atomicMin(s_lo, lo);
-    atomicMax(s_hi, hi);
-  }
-}
-
+// Push of a charged species, one SP per thread in the SPs' device order (cell-sorted by the last
+// sort, apart from the SPs created since): field gather at x^n, leapfrog, and the move's class.
+// SPs whose move may meet the tip or a wall are left to k_cross (velocity written, position
+// kept).  With kDep the CIC charges of the pushed SPs are added to a.Q: lanes of a warp whose new
+// lower corner is the same node (neighbours in the cell order) sum their 8 charges with a
+// segmented shuffle scan and the last lane of each run issues the atomics.  The charges are exact
+// integers, so the grouping changes no bit.  (Per-run warp reductions on 21-bit limbs were
+// measured twice as slow: the runs are reduced one after another.)  (Staging the field and the charge of a tile of SPs
+// in shared-memory windows was measured slower: the barriers between the phases of a tile cost
+// more than the L1 and L2 traffic they save.)
 template <bool kDep>
-__global__ void __launch_bounds__(kPushThreads, 4) k_push_charged(PushArgs a) {
-  __shared__ __align__(16) float4 sE[4 * kWinLen];
-  __shared__ unsigned s_span[4];   // lo, hi of the old corners; lo, hi of the new corners
-  unsigned long long *sQ = reinterpret_cast<unsigned long long *>(sE);
+__global__ void __launch_bounds__(256, 4) k_push_charged(PushArgs a) {
   const int64_t n = a.clk->n[a.species];
-  const int64_t ntile = (n + kPushTile - 1) / kPushTile;
-  const int tid = threadIdx.x;
-  const uint32_t sy = a.nx + 1, sz = (uint32_t)(a.nx + 1) * (a.ny + 1);
-  if (tid == 0) { s_span[0] = 0xFFFFFFFFu; s_span[1] = 0; s_span[2] = 0xFFFFFFFFu; s_span[3] = 0; }
-  __syncthreads();
+  const int lane = threadIdx.x & 31;
   int removed = 0;
-  for (int64_t tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
-    const int64_t t0 = tile * kPushTile;
-    float x[kPushR], y[kPushR], z[kPushR];
-    int32_t w[kPushR];
-    uint32_t lo = 0xFFFFFFFFu, hi = 0;
-#pragma unroll
-    for (int r = 0; r < kPushR; ++r) {
-      const int64_t i = t0 + r * kPushThreads + tid;
-      w[r] = i < n ? a.p.w[i] : 0;
-      x[r] = y[r] = z[r] = 0.f;
-      if (w[r] > 0) {
-        x[r] = a.p.x[i]; y[r] = a.p.y[i]; z[r] = a.p.z[i];
-        const uint32_t b = (uint32_t)node_index((int)floorf(x[r]), (int)floorf(y[r]), (int)floorf(z[r]), a.nx, a.ny);
-        lo = min(lo, b);
-        hi = max(hi, b);
-      }
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < n; i0 += stride) {
+    const int64_t i = i0 + threadIdx.x;
+    const int32_t w = i < n ? a.p.w[i] : 0;
+    bool clear = false, cross = false;
+    uint32_t c = kDead, base = kDead, qp = 0;
+    if (w > 0) {
+      const float x = a.p.x[i], y = a.p.y[i], z = a.p.z[i];
+      float vx = a.p.vx[i], vy = a.p.vy[i], vz = a.p.vz[i];
+      const float3 e = gather_E(a.E, x, y, z, a.nx, a.ny);
+      float x1 = x, y1 = y, z1 = z;
+      leapfrog(a.qmdt, a.dtdx, e, true, x1, y1, z1, vx, vy, vz);
+      a.p.vx[i] = vx; a.p.vy[i] = vy; a.p.vz[i] = vz;
+      const int cls = move_class(a, x, y, z, x1, y1, z1, &c);
+      clear = cls == 0;
+      cross = cls == 1;
+      if (!cross) { a.p.x[i] = x1; a.p.y[i] = y1; a.p.z[i] = z1; }
+      if (cls == 2) ++removed;
+      if (clear && kDep) base = cic_corner(x1, y1, z1, a.nx, a.ny, &qp);
     }
-    block_minmax(lo, hi, &s_span[0], &s_span[1]);
-    __syncthreads();
-    const uint32_t elo = s_span[0], ehi = s_span[1];
-    const bool ewin = ehi >= elo && ehi - elo <= (uint32_t)kWinSpan;
-    const int eL = ewin ? (int)(ehi - elo) + 2 : 0;
-    if (ewin)
-      for (int e = tid; e < 4 * eL; e += kPushThreads) {
-        const int win = e / eL, o = e - win * eL;
-        sE[e] = __ldg(a.E + elo + (uint32_t)o + (uint32_t)(win & 1) * sy + (uint32_t)(win >> 1) * sz);
-      }
-    __syncthreads();
-    if (tid == 0) { s_span[0] = 0xFFFFFFFFu; s_span[1] = 0; }
-    uint32_t base[kPushR], qp[kPushR];
-    lo = 0xFFFFFFFFu;
-    hi = 0;
-#pragma unroll
-    for (int r = 0; r < kPushR; ++r) {
-      const int64_t i = t0 + r * kPushThreads + tid;
-      bool clear = false, cross = false;
-      uint32_t c = kDead;
-      base[r] = kDead;
-      if (w[r] > 0) {
-        float vx = a.p.vx[i], vy = a.p.vy[i], vz = a.p.vz[i];
-        const float3 e = ewin ? gather_E_win(sE, eL, elo, x[r], y[r], z[r], a.nx, a.ny)
-                              : gather_E(a.E, x[r], y[r], z[r], a.nx, a.ny);
-        float x1 = x[r], y1 = y[r], z1 = z[r];
-        leapfrog(a.qmdt, a.dtdx, e, true, x1, y1, z1, vx, vy, vz);
-        a.p.vx[i] = vx; a.p.vy[i] = vy; a.p.vz[i] = vz;
-        const int cls = move_class(a, x[r], y[r], z[r], x1, y1, z1, &c);
-        clear = cls == 0;
-        cross = cls == 1;
-        if (!cross) { a.p.x[i] = x1; a.p.y[i] = y1; a.p.z[i] = z1; }
-        if (cls == 2) ++removed;
-        if (clear && kDep) {
-          base[r] = cic_corner(x1, y1, z1, a.nx, a.ny, &qp[r]);
-          lo = min(lo, base[r]);
-          hi = max(hi, base[r]);
-        }
-      }
-      if (i < n && !clear && !cross) a.key[i] = kDead;
-      if (clear) a.key[i] = c;
-      count_cell(a.cnt, c, clear);
-      enqueue(a, i, cross);
-    }
+    if (i < n && !clear && !cross) a.key[i] = kDead;
+    if (clear) a.key[i] = c;
+    count_cell(a.cnt, c, clear);
+    enqueue(a, i, cross);
     if (kDep) {
-      block_minmax(lo, hi, &s_span[2], &s_span[3]);
-      __syncthreads();   // every gather of the tile is done: the windows' memory is free
-      const uint32_t qlo = s_span[2], qhi = s_span[3];
-      const bool qwin = qhi >= qlo && qhi - qlo <= (uint32_t)kQWinSpan;
-      const int qL = qwin ? (int)(qhi - qlo) + 2 : 0;
-      if (qwin)
-        for (int e = tid; e < 4 * qL; e += kPushThreads) sQ[e] = 0ull;
-      __syncthreads();
-      if (tid == 0) { s_span[2] = 0xFFFFFFFFu; s_span[3] = 0; }
+      long long cc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+      if (base != kDead) cic_charges(qp, a.Z * w, cc);
+      const uint32_t prev = __shfl_up_sync(0xffffffffu, base, 1);
+      const uint32_t next = __shfl_down_sync(0xffffffffu, base, 1);
+      const unsigned heads = __ballot_sync(0xffffffffu, lane == 0 || prev != base);
+      if (heads != 0xffffffffu) {   // segmented inclusive scan, as many rounds as the longest run needs
+        const int start = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
+        const int maxrun = (int)__reduce_max_sync(0xffffffffu, (unsigned)(lane - start + 1));
+        for (int off = 1; off < maxrun; off <<= 1) {
 #pragma unroll
-      for (int r = 0; r < kPushR; ++r) {
-        if (base[r] == kDead) continue;
-        const int32_t zw = a.Z * w[r];
-        if (qwin) {
-          long long c[8];
-          cic_charges(qp[r], zw, c);
-          const int o = (int)(base[r] - qlo);
-#pragma unroll
-          for (int q = 0; q < 8; ++q)
-            if (c[q] != 0) atomicAdd(sQ + ((q >> 1) * qL + o + (q & 1)), (unsigned long long)c[q]);
-        } else {
-          cic_global(a.Q, base[r], qp[r], zw, a.nx, a.ny);
+          for (int q = 0; q < 8; ++q) {
+            const long long v = __shfl_up_sync(0xffffffffu, cc[q], off);
+            if (lane - off >= start) cc[q] += v;
+          }
         }
       }
-      __syncthreads();
-      if (qwin)
-        for (int e = tid; e < 4 * qL; e += kPushThreads) {
-          const unsigned long long v = sQ[e];
-          const int win = e / qL, o = e - win * qL;
-          if (v) atomicAdd(a.Q + qlo + (uint32_t)o + (uint32_t)(win & 1) * sy + (uint32_t)(win >> 1) * sz, v);
-        }
+      if (base != kDead && (lane == 31 || next != base)) {
+        const int64_t sy = a.nx + 1, sz = (int64_t)(a.nx + 1) * (a.ny + 1);
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          if (cc[q] != 0) atomicAdd(a.Q + base + (q & 1) + ((q >> 1) & 1) * sy + (q >> 2) * sz, (unsigned long long)cc[q]);
+      }
     }
-    __syncthreads();   // the windows are reused by the next tile
   }
   for (int o = 16; o > 0; o >>= 1) removed += __shfl_down_sync(0xffffffffu, removed, o);
-  if ((threadIdx.x & 31) == 0 && removed)
+  if (lane == 0 && removed)
     atomicAdd((unsigned long long *)&a.clk->ctr[cRemovedE + a.species], (unsigned long long)removed);
 }
 
@@ -680,8 +603,8 @@ int stage_push(pic_t *h, bool deposit) {
     {
       KtScope kt_(h, kidPush, 0);
       if (S.Z == 0) k_push_neutral<<<particle_grid(h), kThreads, 0, h->stream>>>(a);
-      else if (a.Q) k_push_charged<true><<<h->nsm * 4, kPushThreads, 0, h->stream>>>(a);
-      else k_push_charged<false><<<h->nsm * 4, kPushThreads, 0, h->stream>>>(a);
+      else if (a.Q) k_push_charged<true><<<particle_grid(h), kThreads, 0, h->stream>>>(a);
+      else k_push_charged<false><<<particle_grid(h), kThreads, 0, h->stream>>>(a);
     }
     { KtScope kt_(h, kidCross, 0); k_cross<<<h->nsm * 2, 256, 0, h->stream>>>(a); }
     h->keys_valid[s] = true;
