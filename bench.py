@@ -153,7 +153,8 @@ KERNEL_BYTES_PER_SP = {      # (bytes, species the launches of one step cover)
 # The particle kernels of the benchmark spec's figure (push with its fused charge deposit, impact and
 # field ionization), their algorithmic bytes per step:
 #   push + crossers + clearing the charge: 56 B per SP (read pos+vel 24 + w 4, write pos+vel 24,
-#     cell key 4) + 8 B per node (the deposited charge written once);
+#     cell key 4) + 8 B per node (the deposited charge written once) + 12 B per node (the node
+#     field read once: cell-sorted SPs share their cells' corners);
 #   impact ionization (count + products): read vel + w + id (24 B) per e- and Cu SP;
 #   field ionization (count + products): read pos + w (16 B) per Cu SP.
 PARTICLE_KERNELS = ("k_push", "k_cross", "k_mcc_count", "k_mcc_products", "k_dfi_count", "k_dfi_products")
@@ -164,7 +165,7 @@ def particle_roofline(kt, counts, nnode, steps, hbm_peak, pk_src):
     event-timed durations against their summed algorithmic bytes)."""
     n_all = sum(counts)
     parts = {
-        "push_deposit": (("k_push", "k_cross"), 56.0 * n_all + 8.0 * nnode),
+        "push_deposit": (("k_push", "k_cross"), 56.0 * n_all + 20.0 * nnode),
         "impact_ionization": (("k_mcc_count", "k_mcc_products"), 24.0 * (counts[0] + counts[1])),
         "field_ionization": (("k_dfi_count", "k_dfi_products"), 16.0 * counts[1]),
     }
@@ -183,8 +184,8 @@ def particle_roofline(kt, counts, nnode, steps, hbm_peak, pk_src):
     ach = tot_b / (tot_ms * 1e-3) / 1e9
     return {"bound": "hbm", "achieved": round(ach, 1), "peak": hbm_peak, "unit": "GB/s", "frac": round(ach / hbm_peak, 4),
             "kernels": list(PARTICLE_KERNELS), "ms_per_step": round(tot_ms / steps, 4), "parts": out,
-            "alg_bytes": "56 B per SP + 8 B per node (push, crossers, charge clear + deposit); 24 B per e- and Cu SP "
-                         "(impact ionization); 16 B per Cu SP (field ionization)",
+            "alg_bytes": "56 B per SP + 8 B per node of charge + 12 B per node of field (push, crossers, charge clear + "
+                         "deposit); 24 B per e- and Cu SP (impact ionization); 16 B per Cu SP (field ionization)",
             "peak_source": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)" if pk_src == "measured" else pk_src}
 
 
@@ -416,7 +417,9 @@ def run_ours(args):
                        "valid_sample_fraction": round(sur["valid_sample_fraction"], 3),
                        "faces_served_per_step": round(sur_faces / max(sim.nface, 1), 4),
                        "fallback_faces_last_step": {"outside_range": d1["fallback_range"], "bin_not_validated": d1["fallback_bin"]},
-                       "train_s": round((sur["ms_data"] + sur["ms_train"]) / 1e3, 2)},
+                       "train_s": round((sur["ms_data"] + sur["ms_train"]) / 1e3, 2),
+                       "data_s": round(sur["ms_data"] / 1e3, 2), "optimiser_steps": int(sur["steps"]),
+                       "train_ms_per_optimiser_step": round(sur["ms_train"] / max(sur["steps"], 1), 4)},
                    "plain_form": plain, "graph_form": graph, "autotune": tune},
         "roofline": roof,
         "roofline_particles": roof_p,
@@ -427,6 +430,11 @@ def run_ours(args):
     }
     if args.cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(cfg, pop, args.cpu_sample, steps=1)
+        out["cpu_baseline"]["nproc"] = os.cpu_count()
+        if args.cpu_cores:
+            # the same oracle on every host core and on 16 (the paper's thread count, Sec. 3.2)
+            out["cpu_baseline_cores"] = [cpu_baseline(cfg, pop, args.cpu_sample // 2, steps=1, workers=w)
+                                         for w in sorted({os.cpu_count() or 1, 16})]
     sim.close()
     if dist:
         dist.destroy_process_group()
@@ -434,24 +442,32 @@ def run_ours(args):
 
 
 # ---- the oracle on a bounded sample -----------------------------------------------------------
-def cpu_baseline(cfg, pop, sample, steps=1, warmup=0):
-    """Oracle particle stages (push + boundary, stable sort, impact + field ionization, deposit)
-    on a uniform sample of the workload's SPs, on the full production geometry with a uniform
-    applied field.  Returns the particle-update rate of the oracle as it stands."""
+def _oracle_sample(pop, sample, seed):
+    """A uniform sample of about `sample` SPs of the workload (each species in proportion)."""
+    rng = np.random.default_rng(seed)
+    n_tot = sum(len(pop[k]["x"]) for k in "eni")
+    out = {}
+    for k in "eni":
+        n = len(pop[k]["x"])
+        idx = np.sort(rng.choice(n, size=max(1, int(sample * n / n_tot)), replace=False))
+        out[k] = {f: np.asarray(v)[idx] for f, v in pop[k].items()}
+    return out
+
+
+def _oracle_particle_steps(args):
+    """The oracle's particle stages (push + boundary, stable sort, impact + field ionization,
+    deposit) on one sample, on the full geometry with a uniform applied field: (SP updates timed,
+    seconds).  Module level so that a spawned worker can run it."""
+    cfg, sp0, steps, warmup = args
+    sys.path.insert(0, ROOT)
     from oracle import collide, field, particles as P
     from oracle.grid import Grid
     from oracle import constants as OC
-    rng = np.random.default_rng(0)
     g = Grid(cfg["nx"], cfg["ny"], cfg["nz"], cfg["dx"], cfg["tip_radius"], cfg["tip_height"])
     phi = (cfg["apex_field"] / 5.0) * g.dx * np.arange(g.nz + 1, dtype=np.float64)[:, None, None] * np.ones((1, g.ny + 1, g.nx + 1))
     phi[g.dirichlet_mask() & (np.arange(g.nz + 1)[:, None, None] < g.nz)] = 0.0
     E = field.efield(g, phi)
-    n_tot = sum(len(pop[k]["x"]) for k in "eni")
-    sp = {}
-    for k in "eni":
-        n = len(pop[k]["x"])
-        idx = np.sort(rng.choice(n, size=max(1, int(sample * n / n_tot)), replace=False))
-        sp[k], _ = P.stable_sort(g, {f: np.asarray(v)[idx] for f, v in pop[k].items()})
+    sp = {k: P.stable_sort(g, v)[0] for k, v in sp0.items()}
     prm = {"dt": cfg["dt"], "seed": cfg["seed"], "w_min": cfg["w_min"]}
     m = {"e": OC.M_E, "n": OC.M_CU, "i": OC.M_CU}
     z = {"e": -1, "n": 0, "i": 1}
@@ -477,11 +493,30 @@ def cpu_baseline(cfg, pop, sample, steps=1, warmup=0):
         if it >= warmup:
             done += count
             t_total += dt_
-    return {"value": done / t_total, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{sample} SPs drawn uniformly from the workload, full production grid, uniform applied field; "
-                      f"oracle particle stages (push+boundary, stable sort, MCC, DFI, deposit), {steps} step(s); "
-                      f"single-threaded numpy; the grid stages (33.9M-node CG, 75k-face integrals) are not sampled",
-            "seconds": round(t_total, 3)}
+    return done, t_total
+
+
+def cpu_baseline(cfg, pop, sample, steps=1, warmup=0, workers=1):
+    """The oracle's particle-update rate as it stands, on host cores.  workers = 1: one process
+    (single-threaded numpy).  workers > 1: that many spawned processes, each running the oracle on
+    its own sample of the same size (the samples are independent, as the workload's cells are),
+    the rate being all their SP updates over the slowest worker's time."""
+    samples = [_oracle_sample(pop, sample, 1000 + w) for w in range(workers)]
+    jobs = [(cfg, sp, steps, warmup) for sp in samples]
+    if workers == 1:
+        res = [_oracle_particle_steps(jobs[0])]
+    else:
+        import multiprocessing as mp
+        with mp.get_context("spawn").Pool(workers) as pool:
+            res = pool.map(_oracle_particle_steps, jobs)
+    done = sum(r[0] for r in res)
+    t_max = max(r[1] for r in res)
+    return {"value": done / t_max, "unit": UNIT, "cores": workers, "kind": "oracle",
+            "sample": f"{sample} SPs drawn uniformly from the workload per process ({workers} process(es)), the workload's full "
+                      f"grid, uniform applied field; oracle particle stages (push+boundary, stable sort, "
+                      f"MCC, DFI, deposit), {steps} step(s); numpy, one thread per process; the grid stages "
+                      f"(33.9M-node CG, 75k-face integrals) are not sampled",
+            "seconds": round(t_max, 3)}
 
 
 def ensemble_share(n, world, rank):
@@ -652,6 +687,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-sample", type=int, default=60000)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--no-cpu-cores", dest="cpu_cores", action="store_false",
+                    help="skip the oracle timed on all host cores and on 16 processes")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false")
     ap.add_argument("--circuit", action="store_true", help="step with the RC circuit and Shockley-Ramo current")
     ap.add_argument("--elastic", action="store_true", help="step with elastic collisions and charge exchange")

@@ -4,10 +4,12 @@
 // in the step wherever its inputs lie in the trained range and a held-out validation bin shows
 // |delta log10 J| <= 0.015; elsewhere the step falls back to the full integral.
 //
-// Arithmetic: the two 128 x 128 hidden layers run on the tensor cores with BF16 operands and FP32
-// accumulation -- inference (the step's faces, pic_surrogate_eval, the validation map, forward
-// calls without targets) in one fused tcgen05/TMEM kernel (k_mlp_tc.cu); training, which keeps
-// every layer's values for the backward pass, on mma.sync m16n8k16 tiles here.  The input layer
+// Arithmetic: the two 128 x 128 hidden layers run on the fifth-generation tensor cores (tcgen05,
+// TMEM accumulators) with BF16 operands and FP32 accumulation -- inference (the step's faces,
+// pic_surrogate_eval, the validation map, forward calls without targets) in one fused kernel, and
+// training, which keeps every layer's values for the backward pass, as separate products through
+// one tiled GEMM kernel (k_mlp_tc.cu: forward, input gradients, and weight gradients split over
+// the batch with a fixed-order sum).  The input layer
 // (7 features) and the output layer (2 values)
 // are FP32 on the CUDA cores, so the features and the last activations keep FP32 precision
 // (in BF16 a feature step of 2^-9 moves log10 J by up to ~0.04 in the field-emission regime).
@@ -88,85 +90,7 @@ void mlp_forget(pic_t *h) {
     }
 }
 
-// ---- tensor-core GEMM: C(M,N) = A(M,K) B(K,N), BF16 in, FP32 accumulate ---------------------
-__device__ __forceinline__ uint32_t pack_bf16(__nv_bfloat16 lo, __nv_bfloat16 hi) {
-  return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
-}
-
-__device__ __forceinline__ void mma16816(float c[4], const uint32_t a[4], const uint32_t b[2]) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};\n"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-
-struct Gemm {
-  const __nv_bfloat16 *A;
-  int64_t sam, sak;        // A(m,k) = A[m sam + k sak]
-  const __nv_bfloat16 *B;
-  int64_t sbk, sbn;        // B(k,n) = B[k sbk + n sbn]
-  float *C;
-  int64_t scm, scn;        // C(m,n) = C[m scm + n scn]  (split-K: partial z at C + z M N, row-major)
-  int M, N, K, splits;
-};
-
-// 64 x 64 output tile per block, 4 warps of 32 x 32, K in steps of 16
-__global__ void __launch_bounds__(128) k_gemm(Gemm g) {
-  __shared__ __nv_bfloat16 As[64][24];
-  __shared__ __nv_bfloat16 Bs[64][24];   // Bs[n][k]
-  const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
-  const int per = ((g.K + g.splits - 1) / g.splits + 15) / 16 * 16;
-  const int kb = blockIdx.z * per, ke = min(g.K, kb + per);
-  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, wm = w >> 1, wn = w & 1;
-  const int gq = lane >> 2, tq = lane & 3;
-  float acc[2][4][4];
-  for (int i = 0; i < 2; ++i)
-    for (int j = 0; j < 4; ++j)
-      for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
-  const __nv_bfloat16 zero = __float2bfloat16(0.f);
-  for (int k0 = kb; k0 < ke; k0 += 16) {
-    for (int e = tid; e < 64 * 16; e += 128) {
-      const int r = e >> 4, c = e & 15, m = m0 + r, k = k0 + c;
-      As[r][c] = (m < g.M && k < ke) ? g.A[(int64_t)m * g.sam + (int64_t)k * g.sak] : zero;
-      const int n = n0 + r;
-      Bs[r][c] = (n < g.N && k < ke) ? g.B[(int64_t)k * g.sbk + (int64_t)n * g.sbn] : zero;
-    }
-    __syncthreads();
-    for (int i = 0; i < 2; ++i) {
-      const int rb = wm * 32 + i * 16;
-      uint32_t a[4];
-      a[0] = pack_bf16(As[rb + gq][2 * tq], As[rb + gq][2 * tq + 1]);
-      a[1] = pack_bf16(As[rb + gq + 8][2 * tq], As[rb + gq + 8][2 * tq + 1]);
-      a[2] = pack_bf16(As[rb + gq][2 * tq + 8], As[rb + gq][2 * tq + 9]);
-      a[3] = pack_bf16(As[rb + gq + 8][2 * tq + 8], As[rb + gq + 8][2 * tq + 9]);
-      for (int j = 0; j < 4; ++j) {
-        const int cb = wn * 32 + j * 8;
-        uint32_t b[2];
-        b[0] = pack_bf16(Bs[cb + gq][2 * tq], Bs[cb + gq][2 * tq + 1]);
-        b[1] = pack_bf16(Bs[cb + gq][2 * tq + 8], Bs[cb + gq][2 * tq + 9]);
-        mma16816(acc[i][j], a, b);
-      }
-    }
-    __syncthreads();
-  }
-  float *out = g.C;
-  int64_t scm = g.scm, scn = g.scn;
-  if (g.splits > 1) {
-    out = g.C + (int64_t)blockIdx.z * g.M * g.N;
-    scm = g.N;
-    scn = 1;
-  }
-  for (int i = 0; i < 2; ++i)
-    for (int j = 0; j < 4; ++j) {
-      const int r = m0 + wm * 32 + i * 16 + gq, c = n0 + wn * 32 + j * 8 + 2 * tq;
-      const float v[4] = {acc[i][j][0], acc[i][j][1], acc[i][j][2], acc[i][j][3]};
-      const int rr[4] = {r, r, r + 8, r + 8}, cc[4] = {c, c + 1, c, c + 1};
-      for (int e = 0; e < 4; ++e)
-        if (rr[e] < g.M && cc[e] < g.N) out[(int64_t)rr[e] * scm + (int64_t)cc[e] * scn] = v[e];
-    }
-}
-
+// ---- tensor-core GEMMs: C(M,128) = A(M,K) B(K,128), BF16 in, FP32 accumulate (tcgen05) -----------
 // C(m,n) = sum_z partial[z](m,n) in fixed order
 __global__ void k_reduce_splits(const float *part, int splits, int M, int N, float *C, int64_t scm, int64_t scn) {
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < M * N; e += gridDim.x * blockDim.x) {
@@ -176,16 +100,18 @@ __global__ void k_reduce_splits(const float *part, int splits, int M, int N, flo
   }
 }
 
-static void gemm(pic_t *h, MlpState &S, const __nv_bfloat16 *A, int64_t sam, int64_t sak, const __nv_bfloat16 *B,
-                 int64_t sbk, int64_t sbn, float *C, int64_t scm, int64_t scn, int M, int N, int K, int splits) {
-  Gemm g{A, sam, sak, B, sbk, sbn, splits > 1 ? S.part : C, scm, scn, M, N, K, splits};
-  dim3 grid((N + 63) / 64, (M + 63) / 64, splits);
-  ++h->nlaunch;
-  k_gemm<<<grid, 128, 0, h->stream>>>(g);
+// every training product has N = 128 (the hidden width); a product whose K is the batch is split
+// over CTAs (splits partials in S.part, then the fixed-order sum)
+static int gemm(pic_t *h, MlpState &S, const __nv_bfloat16 *A, int64_t sam, int64_t sak, const __nv_bfloat16 *B,
+                int64_t sbk, int64_t sbn, float *C, int64_t scm, int64_t scn, int M, int N, int K, int splits) {
+  if (N != kH) return pic_fail(h, PIC_E_INVALID, "training GEMM with N != 128");
+  GemmTcArgs g{A, sam, sak, B, sbk, sbn, splits > 1 ? S.part : C, scm, scn, M, K, splits, 0};
+  PIC_TRY(gemm_tc(h, g));
   if (splits > 1) {
     ++h->nlaunch;
     k_reduce_splits<<<std::max(1, (M * N + 255) / 256), 256, 0, h->stream>>>(S.part, splits, M, N, C, scm, scn);
   }
+  return PIC_OK;
 }
 
 // ---- FP32 layers and elementwise ---------------------------------------------------------------
@@ -453,18 +379,19 @@ static void refresh_bf16(pic_t *h, MlpState &S) {
 static int eg(int64_t n) { return (int)std::min<int64_t>((n + 255) / 256, 4096); }
 
 // forward of feature rows X -> Y (rows x 2, bias included); keeps Z1..Z3, A1, A2, A3
-static void forward(pic_t *h, MlpState &S, const float *X, int64_t rows) {
+static int forward(pic_t *h, MlpState &S, const float *X, int64_t rows) {
   const int M = (int)rows;
   ++h->nlaunch;
   k_layer1<<<eg(rows * kH), 256, 0, h->stream>>>(X, S.master + kOffW1, S.master + kOffB1, S.Z1, S.A1, rows);
-  gemm(h, S, S.A1, kH, 1, S.w2, 1, kH, S.Z2, kH, 1, M, kH, kH, 1);
+  PIC_TRY(gemm(h, S, S.A1, kH, 1, S.w2, 1, kH, S.Z2, kH, 1, M, kH, kH, 1));
   ++h->nlaunch;
   k_bias_gelu<<<eg(rows * kH), 256, 0, h->stream>>>(S.Z2, S.master + kOffB2, S.A2, nullptr, rows);
-  gemm(h, S, S.A2, kH, 1, S.w3, 1, kH, S.Z3, kH, 1, M, kH, kH, 1);
+  PIC_TRY(gemm(h, S, S.A2, kH, 1, S.w3, 1, kH, S.Z3, kH, 1, M, kH, kH, 1));
   ++h->nlaunch;
   k_bias_gelu<<<eg(rows * kH), 256, 0, h->stream>>>(S.Z3, S.master + kOffB3, nullptr, S.A3, rows);
   ++h->nlaunch;
   k_layer4<<<eg(rows * 32), 256, 0, h->stream>>>(S.A3, S.master + kOffW4, S.master + kOffB4, S.Y, rows);
+  return PIC_OK;
 }
 
 // FP32 weight and bias gradient of a small layer into S.grad: the layouts keep b right after W
@@ -484,23 +411,24 @@ static int backward(pic_t *h, MlpState &S, const float *X, const float *Tg, int6
   const int M = (int)rows;
   ++h->nlaunch;
   k_out_loss<<<nloss_blocks, 256, 0, h->stream>>>(S.Y, Tg, S.dY, rows, S.loss);
-  const int splits = (int)std::min<int64_t>(16, std::max<int64_t>(1, rows / 512));
+  // weight gradients: the batch (K) split into ranges of 128 rows, one CTA each
+  const int splits = (int)std::min<int64_t>(kSplitMax, std::max<int64_t>(1, (rows + 127) / 128));
   // layer 4 (FP32): dW4 = dY^T A3, db4; dZ3 = (dY W4) gelu'(Z3)
   wgrad32(h, S, S.dY, kOut, S.A3, kH, kOut, kH, rows, kOffW4);
   ++h->nlaunch;
   k_layer4_bwd<<<eg(rows * kH), 256, 0, h->stream>>>(S.dY, S.master + kOffW4, S.Z3, S.dZ, S.dZb, rows);
   // layer 3 (tensor cores): dW3 = dZ3^T A2, db3, dA2 = dZ3 W3
-  gemm(h, S, S.dZb, 1, kH, S.A2, kH, 1, S.grad + kOffW3, kH, 1, kH, kH, M, splits);
+  PIC_TRY(gemm(h, S, S.dZb, 1, kH, S.A2, kH, 1, S.grad + kOffW3, kH, 1, kH, kH, M, splits));
   ++h->nlaunch;
   k_colsum<<<kH, 256, 0, h->stream>>>(S.dZ, rows, kH, S.grad + kOffB3);
-  gemm(h, S, S.dZb, kH, 1, S.w3, kH, 1, S.dA, kH, 1, M, kH, kH, 1);
+  PIC_TRY(gemm(h, S, S.dZb, kH, 1, S.w3, kH, 1, S.dA, kH, 1, M, kH, kH, 1));
   ++h->nlaunch;
   k_gelu_bwd<<<eg(rows * kH), 256, 0, h->stream>>>(S.dA, S.Z2, S.dZ, S.dZb, rows);
   // layer 2 (tensor cores): dW2 = dZ2^T A1, db2, dA1 = dZ2 W2
-  gemm(h, S, S.dZb, 1, kH, S.A1, kH, 1, S.grad + kOffW2, kH, 1, kH, kH, M, splits);
+  PIC_TRY(gemm(h, S, S.dZb, 1, kH, S.A1, kH, 1, S.grad + kOffW2, kH, 1, kH, kH, M, splits));
   ++h->nlaunch;
   k_colsum<<<kH, 256, 0, h->stream>>>(S.dZ, rows, kH, S.grad + kOffB2);
-  gemm(h, S, S.dZb, kH, 1, S.w2, kH, 1, S.dA, kH, 1, M, kH, kH, 1);
+  PIC_TRY(gemm(h, S, S.dZb, kH, 1, S.w2, kH, 1, S.dA, kH, 1, M, kH, kH, 1));
   ++h->nlaunch;
   k_gelu_bwd<<<eg(rows * kH), 256, 0, h->stream>>>(S.dA, S.Z1, S.dZ, nullptr, rows);
   // layer 1 (FP32): dW1 = dZ1^T X, db1
@@ -605,7 +533,7 @@ int pic_mlp_forward_backward(pic_t *h, const float *x, const float *t, int64_t n
   for (int64_t i = 0; i < n; ++i)
     for (int c = 0; c < kIn; ++c) X[i * kXld + c] = x[i * kIn + c];
   PIC_CUDA(h, cudaMemcpyAsync(S.X, X.data(), n * kXld * 4, cudaMemcpyHostToDevice, h->stream));
-  if (t) forward(h, S, S.X, n);   // training: keeps the layer values the gradient needs
+  if (t) PIC_TRY(forward(h, S, S.X, n));   // training: keeps the layer values the gradient needs
   else PIC_TRY(mlp_forward_tc(h, S.X, n, S.master, S.w2, S.w3, S.Y));   // inference (as in the step)
   if (t) {
     float *Tg = S.dA;   // scratch for targets (rows x 2 fits in rows x kH)
@@ -695,7 +623,7 @@ int pic_surrogate_train(pic_t *h, int64_t nsamples, int epochs, int batch, doubl
       const int64_t r0 = ((b + (int64_t)ep * 7919) % steps_per_epoch) * batch;
       const float *Xb = Xall + r0 * kXld;
       const float *Tb = Tall + r0 * 2;
-      forward(h, S, Xb, batch);
+      PIC_TRY(forward(h, S, Xb, batch));
       PIC_TRY(backward(h, S, Xb, Tb, batch, 16));
       const double lr = lr0 * (0.01 + 0.99 * 0.5 * (1.0 + cos(3.141592653589793 * (double)step / (double)total)));
       const int t = step + 1;

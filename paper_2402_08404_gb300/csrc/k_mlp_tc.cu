@@ -279,4 +279,131 @@ int mlp_forward_tc(pic_t *h, const float *X, int64_t rows, const float *master, 
   return launch_check(h, "mlp forward (tcgen05)");
 }
 
+
+// ---- training GEMMs on the tensor cores -------------------------------------------------------
+// C(M x 128) = A(M x K) B(K x 128) with BF16 operands and FP32 accumulation in tensor memory, for
+// the surrogate's training: the hidden layers' forward products (K = 128), the gradients of their
+// inputs (K = 128) and their weight gradients (M = 128, K = the batch, split over CTAs).  The
+// operands are addressed with element strides, A(m, k) = A[m sam + k sak] and B(k, n) =
+// B[k sbk + n sbn], so the transposed products need no transposed copies: each CTA stages a
+// 128 x 128 block of A (rows m0.., columns k0..) and of B (all 128 columns n, rows k0..) into
+// shared memory in the K-major core-matrix layout, zero outside the matrices, and one thread
+// issues the eight K = 16 MMAs of the block.  CTA (x, z) owns rows 128 x and the z-th range of K;
+// with several ranges each CTA writes its own partial (row-major M x 128 at C + z M 128), which a
+// fixed-order sum then adds, so the result does not depend on scheduling.
+namespace {
+constexpr int kGemmThreads = 128;   // one thread per row of the tile (its TMEM lane)
+struct GemmSmem {
+  alignas(1024) unsigned char A[kMatBytes];
+  alignas(1024) unsigned char B[kMatBytes];
+  alignas(8) unsigned long long bar;
+  uint32_t tmem;
+  int fail;
+};
+}  // namespace
+
+__global__ void __launch_bounds__(kGemmThreads, 1) k_gemm_tc(GemmTcArgs g, int *err) {
+  extern __shared__ unsigned char smem_raw[];
+  GemmSmem &S = *reinterpret_cast<GemmSmem *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int m0 = blockIdx.x * kTile;
+  const int kb = blockIdx.z * g.kper, ke = min(g.K, kb + g.kper);
+  const uint32_t bar = smem_u32(&S.bar);
+  if (tid == 0) {
+    S.fail = 0;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&S.tmem)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  const uint32_t tmem = S.tmem;
+  const uint32_t a_addr = smem_u32(S.A), b_addr = smem_u32(S.B);
+  const __nv_bfloat16 zero = __float2bfloat16(0.f);
+  const __nv_bfloat16 *Ag = static_cast<const __nv_bfloat16 *>(g.A), *Bg = static_cast<const __nv_bfloat16 *>(g.B);
+  uint32_t phase = 0;
+  bool any = false;
+  for (int k0 = kb; k0 < ke; k0 += kH) {
+    // stage A (rows m0.., columns k0..) and B (columns n, rows k0..) into the core-matrix layout;
+    // the element order follows the unit stride of each operand so that global reads coalesce
+    for (int e = tid; e < kH * kH; e += kGemmThreads) {
+      const int hi = e >> 7, lo = e & (kH - 1);
+      const int am = g.sak == 1 ? hi : lo, ak = g.sak == 1 ? lo : hi;
+      const int m = m0 + am, k = k0 + ak;
+      *reinterpret_cast<__nv_bfloat16 *>(S.A + core_off(am, ak)) =
+          (m < g.M && k < ke) ? Ag[(int64_t)m * g.sam + (int64_t)k * g.sak] : zero;
+      const int bn = g.sbn == 1 ? lo : hi, bk = g.sbn == 1 ? hi : lo;
+      const int kk = k0 + bk;
+      *reinterpret_cast<__nv_bfloat16 *>(S.B + core_off(bn, bk)) =
+          kk < ke ? Bg[(int64_t)kk * g.sbk + (int64_t)bn * g.sbn] : zero;
+    }
+    fence_proxy_async();
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    if (tid == 0) {
+#pragma unroll
+      for (int q = 0; q < kH / 16; ++q)
+        mma_bf16(tmem, smem_desc(a_addr + q * 2 * kLBO), smem_desc(b_addr + q * 2 * kLBO), (any || q > 0) ? 1u : 0u);
+      mma_commit(bar);
+    }
+    any = true;
+    const bool ok = bar_wait(bar, phase);
+    phase ^= 1u;
+    if (!ok) atomicExch(&S.fail, 1);
+    fence_after_sync();
+    __syncthreads();   // the MMAs have read the staged blocks: they may be overwritten
+    if (S.fail) break;
+  }
+  if (!S.fail) {
+    float *C = g.C;
+    int64_t scm = g.scm, scn = g.scn;
+    if (g.splits > 1) {
+      C = g.C + (int64_t)blockIdx.z * g.M * kH;
+      scm = kH;
+      scn = 1;
+    }
+    const int r = m0 + tid;
+    const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
+    for (int cc = 0; cc < kH / 32; ++cc) {
+      float v[32];
+      if (any) tmem_ld32(taddr + 32 * cc, v);
+      else
+        for (int u = 0; u < 32; ++u) v[u] = 0.f;
+      if (r < g.M)
+        for (int u = 0; u < 32; ++u) C[(int64_t)r * scm + (int64_t)(32 * cc + u) * scn] = v[u];
+    }
+  }
+  if (S.fail && tid == 0) atomicOr(err, kErrTimeout);
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kTmemCols) : "memory");
+}
+
+int gemm_tc(pic_t *h, const GemmTcArgs &g0) {
+  GemmTcArgs g = g0;
+  g.kper = (g.K + g.splits - 1) / g.splits;
+  g.kper = (g.kper + kH - 1) / kH * kH;
+  const int smem = (int)sizeof(GemmSmem) + 1024;
+  static int configured_dev = -1;
+  int dev = 0;
+  PIC_CUDA(h, cudaGetDevice(&dev));
+  if (configured_dev != dev) {
+    PIC_CUDA(h, cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    configured_dev = dev;
+  }
+  const dim3 grid((g.M + kTile - 1) / kTile, 1, g.splits);
+  ++h->nlaunch;
+  k_gemm_tc<<<grid, kGemmThreads, smem, h->stream>>>(g, &h->clock->err);
+  return launch_check(h, "gemm (tcgen05)");
+}
+
 }  // namespace pic

@@ -384,6 +384,20 @@ int surrogate_faces(pic_t *h, const uint8_t **elig, const float **Y);
 int surrogate_bins();
 int surrogate_export(pic_t *h, float *master, uint8_t *binok, int *trained);
 int surrogate_import(pic_t *h, const float *master, const uint8_t *binok, int trained);
+// training GEMM on the tcgen05 tensor cores (k_mlp_tc.cu): C(M x 128) = A(M x K) B(K x 128), BF16
+// operands (A(m, k) = A[m sam + k sak], B(k, n) = B[k sbk + n sbn]), FP32 result C(m, n) =
+// C[m scm + n scn]; with splits > 1 the K range is split over CTAs and CTA z writes its partial
+// row-major at C + z M 128 (summed afterwards in a fixed order); kper is set by gemm_tc
+struct GemmTcArgs {
+  const void *A;
+  int64_t sam, sak;
+  const void *B;
+  int64_t sbk, sbn;
+  float *C;
+  int64_t scm, scn;
+  int M, K, splits, kper;
+};
+int gemm_tc(pic_t *h, const GemmTcArgs &g);
 // fused surrogate forward pass on the tcgen05 tensor cores (k_mlp_tc.cu); __nv_bfloat16 passed as void
 int mlp_forward_tc(pic_t *h, const float *X, int64_t rows, const float *master, const struct __nv_bfloat16 *w2,
                    const struct __nv_bfloat16 *w3, float *Y);

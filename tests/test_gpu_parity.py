@@ -341,3 +341,26 @@ def test_full_steps_keep_the_books(pic):
         assert d["total_charge_fixed"] == (d["weight"][2] - d["weight"][0]) << 30
     assert d["step"] == 4
     sim.close()
+
+
+def test_poisson_on_a_grid_above_the_cluster_tail_matches_oracle(pic):
+    """A grid whose finest multigrid levels run as separate launches above the cluster-launched
+    tail (65x65x129 nodes): the mixed-precision refinement reaches mg_tol = 1e-10 and matches the
+    oracle's CG solution to 1e-8 of its scale."""
+    cfg = small_cfg(nx=64, ny=64, nz=128, tip_radius=4e-9, tip_height=40e-9, n_sp=100_000)
+    g = grid_of(cfg)
+    pop = synth.plasma(cfg, seed=12)
+    sim = make(pic, cfg, cap=400_000, V0=60.0, mg_tol=1e-10, mg_max_cycles=200)
+    load(sim, pop)
+    sim.solve_field()
+    ref = sorted_pop(g, pop)
+    Q = P.deposit(g, ref["i"], 1, Q=P.deposit(g, ref["e"], -1))
+    assert np.array_equal(sim.get_charge(), Q)
+    f = field.rhs_from_charge(g, Q, cfg["w_min"])
+    phi_ref = field.solve_poisson(g, 60.0, f)
+    got = sim.get_potential()
+    assert np.max(np.abs(got - phi_ref)) <= 1e-8 * np.max(np.abs(phi_ref))
+    d = sim.diagnostics()
+    assert d["mg_residual"] <= 1e-10
+    assert field.relative_residual(g, got, f, 60.0) <= 2e-10
+    sim.close()
