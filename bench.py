@@ -142,7 +142,10 @@ KERNEL_BYTES_PER_UNIT = {
 # DRAM bytes (read + write) per launch from one ncu capture of the unchanged kernel on the
 # production grid: (workload, kernel) -> bytes.  A kernel that has changed since its capture has
 # no entry (the bench then reports null).
-NCU_TRAFFIC_PER_LAUNCH = {}
+# k_smooth: the non-first sweeps of levels 0-2 (11 launches per level and step) move 193.17, 19.32
+# and 2.48 MB per launch (read + write), captured on the production grid with a tenth of the SPs
+# (the smoother's traffic depends on the grid alone), 71.65 MB per launch on average.
+NCU_TRAFFIC_PER_LAUNCH = {("production", "k_smooth"): 71.65e6}
 KERNEL_BYTES_PER_SP = {      # (bytes, species the launches of one step cover)
     "k_push": (56.0, "all"),         # pos+vel+w read 28, pos+vel write 24, key 4 (+ 8 B per node of charge)
     "k_gather": (76.0, "all"),       # perm 4 + 36 B record read + 36 B record write
@@ -251,6 +254,7 @@ def run_ours(args):
     cfg = dict(synth.CONFIGS[args.config])
     cfg["seed"] = cfg["seed"] + rank
     n_sp = cfg["n_sp"]
+    nnode_ = (cfg["nx"] + 1) * (cfg["ny"] + 1) * (cfg["nz"] + 1)
     pop = synth.plasma(cfg, seed=cfg["seed"])
     cap = (int(0.4 * n_sp * 1.25), int(0.4 * n_sp * 1.25), int(0.2 * n_sp * 1.5))
     prod_flags = pic.F_PRODUCTION if args.form == "production" else (pic.F_ALL & ~pic.F_SURROGATE & ~pic.F_MIXED_MG)
@@ -354,6 +358,44 @@ def run_ours(args):
             e2e_updates += e2e_step()
         torch.cuda.synchronize()
         e2e_s = max(time.perf_counter() - t0, 1e-9)
+        # the same workload at a larger w_min: more real particles per SP, so the collision
+        # processes produce events every step and the solve sees the space charge of the seeded
+        # plasma (untimed for the headline; its own event-timed numbers)
+        rich = None
+        if args.rich_steps > 0:
+            sim_r = None
+            try:
+                cfg_r = dict(cfg, w_min=args.rich_wmin)
+                sim_r = pic.Pic(cfg_r, capacity=tuple(2 * c for c in cap), flags=prod_flags, mg_tol=args.mg_tol,
+                                mg_max_cycles=60, stream=stream, mg_sweeps=args.mg_sweeps)
+                for s_, k in enumerate("eni"):
+                    sim_r.load_particles(s_, pop[k])
+                sim_r.set_clock(0, n_sp)
+                sim_r.solve_field()
+                if sur is not None:
+                    sim_r.surrogate_copy_from(sim)
+                sim_r.step(2)
+                sim_r.set_kernel_timing([k for k in PARTICLE_KERNELS] + ["k_smooth", "k_residual64"])
+                rm, r0, r1 = timed_steps(sim_r, stream, args.rich_steps)
+                kt_r = sim_r.kernel_timing()
+                mc_r = [0.5 * (a + b) for a, b in zip(r0["count"], r1["count"])]
+                rich = {"w_min": args.rich_wmin, "steps": args.rich_steps, "ms_per_step": rm / args.rich_steps,
+                        "particle_updates_per_s": args.rich_steps * sum(mc_r) / (rm * 1e-3),
+                        "impact_ionizations_last_step": r1["impact_ionizations"],
+                        "field_ionizations_last_step": r1["field_ionizations"],
+                        "mg_cycles_per_step": (r1["mg_cycles_total"] - r0["mg_cycles_total"]) / args.rich_steps,
+                        "max_face_field": r1["max_face_field"], "count_end": r1["count"],
+                        "stage_ms": {k: round(r1["ms"][i] / args.rich_steps, 4) for i, k in
+                                     enumerate(["emit", "push", "sort", "collide", "deposit", "solve", "heat"])},
+                        "kernel_ms_per_step": {k: round(v[1] / args.rich_steps, 4) for k, v in kt_r.items()},
+                        "roofline_particles": particle_roofline(kt_r, mc_r, nnode_, args.rich_steps,
+                                                                peaks()[0].get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"]),
+                                                                peaks()[1])}
+            except Exception as ex:   # a refused step (capacity, no convergence) is reported, not fatal
+                rich = {"w_min": args.rich_wmin, "error": str(ex)}
+            finally:
+                if sim_r is not None:
+                    sim_r.close()
     # max time over ranks, sum of work
     t_max, tot_updates, tot_e2e = reduce_over_ranks(dist, elapsed_ms, updates, e2e_updates / e2e_s, "cuda")
     times = [t_max]
@@ -420,7 +462,7 @@ def run_ours(args):
                        "train_s": round((sur["ms_data"] + sur["ms_train"]) / 1e3, 2),
                        "data_s": round(sur["ms_data"] / 1e3, 2), "optimiser_steps": int(sur["steps"]),
                        "train_ms_per_optimiser_step": round(sur["ms_train"] / max(sur["steps"], 1), 4)},
-                   "plain_form": plain, "graph_form": graph, "autotune": tune},
+                   "plain_form": plain, "graph_form": graph, "collision_rich": rich, "autotune": tune},
         "roofline": roof,
         "roofline_particles": roof_p,
         "clocks": clk.summary(),
@@ -685,6 +727,8 @@ def main():
     ap.add_argument("--mg-tol", type=float, default=1e-6)
     ap.add_argument("--mg-sweeps", type=int, default=0, help="red-black sweeps per V-cycle side (0: library default)")
     ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--rich-steps", type=int, default=10, help="steps of the collision-rich form (0: skip)")
+    ap.add_argument("--rich-wmin", type=float, default=1e-3, help="w_min of the collision-rich form")
     ap.add_argument("--cpu-sample", type=int, default=60000)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-cpu-cores", dest="cpu_cores", action="store_false",

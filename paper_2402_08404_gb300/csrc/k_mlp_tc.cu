@@ -285,28 +285,79 @@ int mlp_forward_tc(pic_t *h, const float *X, int64_t rows, const float *master, 
 // the surrogate's training: the hidden layers' forward products (K = 128), the gradients of their
 // inputs (K = 128) and their weight gradients (M = 128, K = the batch, split over CTAs).  The
 // operands are addressed with element strides, A(m, k) = A[m sam + k sak] and B(k, n) =
-// B[k sbk + n sbn], so the transposed products need no transposed copies: each CTA stages a
-// 128 x 128 block of A (rows m0.., columns k0..) and of B (all 128 columns n, rows k0..) into
-// shared memory in the K-major core-matrix layout, zero outside the matrices, and one thread
-// issues the eight K = 16 MMAs of the block.  CTA (x, z) owns rows 128 x and the z-th range of K;
-// with several ranges each CTA writes its own partial (row-major M x 128 at C + z M 128), which a
-// fixed-order sum then adds, so the result does not depend on scheduling.
+// B[k sbk + n sbn], so the transposed products read the stored matrices directly.  CTA (x, y, z)
+// owns rows 128 x, columns 64 y and the z-th range of K: it stages 128 x 128 blocks of A and
+// 64 x 128 blocks of B into shared memory in the K-major core-matrix layout with 16-byte
+// transfers (an operand stored with unit stride along M or N is transposed in registers, 8 x 8
+// elements at a time), zero outside the matrices, and one thread issues the eight K = 16 MMAs of
+// a block.  With several K ranges each CTA writes its own partial (row-major M x 128 at
+// C + z M 128), which a fixed-order sum then adds, so the result does not depend on scheduling.
 namespace {
 constexpr int kGemmThreads = 128;   // one thread per row of the tile (its TMEM lane)
+constexpr int kGemmN = 64;          // columns per CTA (MMA N)
+constexpr uint32_t kIdesc64 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kGemmN >> 3) << 17) |
+                              ((uint32_t)(kTile >> 4) << 24);
 struct GemmSmem {
-  alignas(1024) unsigned char A[kMatBytes];
-  alignas(1024) unsigned char B[kMatBytes];
+  alignas(1024) unsigned char A[kTile * kH * 2];
+  alignas(1024) unsigned char B[kGemmN * kH * 2];
   alignas(8) unsigned long long bar;
   uint32_t tmem;
   int fail;
 };
+
+__device__ __forceinline__ void mma_bf16_n64(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(kIdesc64), "r"(accumulate));
+}
+
+// One 128-row-wide (rows = the tile's M or N index) by 128-K block of a strided BF16 operand into
+// the core-matrix layout: X(r, k) = src[(r0 + r) sr + (k0 + k) sk] for r < nr, valid where
+// r0 + r < rmax and k0 + k < kmax (zero elsewhere).  Unit stride along K: each thread moves 16-byte
+// rows of 8 K-elements.  Unit stride along r: each thread loads 8 rows of K (8 r-elements each),
+// transposes the 8 x 8 block in registers and stores 8 16-byte rows.
+__device__ __forceinline__ void stage_block(unsigned char *dst, const __nv_bfloat16 *src, int64_t sr, int64_t sk, int r0,
+                                            int nr, int rmax, int k0, int kmax, int tid) {
+  if (sk == 1) {
+    for (int e = tid; e < nr * (kH / 8); e += kGemmThreads) {
+      const int r = e >> 4, k8 = (e & 15) * 8;
+      uint4 v = make_uint4(0u, 0u, 0u, 0u);
+      if (r0 + r < rmax && k0 + k8 < kmax)
+        v = *reinterpret_cast<const uint4 *>(src + (int64_t)(r0 + r) * sr + (k0 + k8));
+      *reinterpret_cast<uint4 *>(dst + core_off(r, k8)) = v;
+    }
+  } else {
+    for (int e = tid; e < (nr / 8) * (kH / 8); e += kGemmThreads) {
+      const int rb = (e % (nr / 8)) * 8, kb = (e / (nr / 8)) * 8;
+      uint32_t in[8][4];
+#pragma unroll
+      for (int kk = 0; kk < 8; ++kk) {
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (k0 + kb + kk < kmax && r0 + rb < rmax)
+          v = *reinterpret_cast<const uint4 *>(src + (int64_t)(k0 + kb + kk) * sk + (r0 + rb));
+        in[kk][0] = v.x; in[kk][1] = v.y; in[kk][2] = v.z; in[kk][3] = v.w;
+      }
+#pragma unroll
+      for (int rr = 0; rr < 8; ++rr) {
+        const uint32_t sel = (rr & 1) ? 0x7632u : 0x5410u;
+        uint4 o;
+        o.x = __byte_perm(in[0][rr >> 1], in[1][rr >> 1], sel);
+        o.y = __byte_perm(in[2][rr >> 1], in[3][rr >> 1], sel);
+        o.z = __byte_perm(in[4][rr >> 1], in[5][rr >> 1], sel);
+        o.w = __byte_perm(in[6][rr >> 1], in[7][rr >> 1], sel);
+        *reinterpret_cast<uint4 *>(dst + core_off(rb + rr, kb)) = o;
+      }
+    }
+  }
+}
 }  // namespace
 
 __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm_tc(GemmTcArgs g, int *err) {
   extern __shared__ unsigned char smem_raw[];
   GemmSmem &S = *reinterpret_cast<GemmSmem *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const int tid = threadIdx.x, warp = tid >> 5;
-  const int m0 = blockIdx.x * kTile;
+  const int m0 = blockIdx.x * kTile, n0 = blockIdx.y * kGemmN;
   const int kb = blockIdx.z * g.kper, ke = min(g.K, kb + g.kper);
   const uint32_t bar = smem_u32(&S.bar);
   if (tid == 0) {
@@ -316,7 +367,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm_tc(GemmTcArgs g, int *
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&S.tmem)),
-                 "r"(kTmemCols)
+                 "r"((uint32_t)kGemmN)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
   }
@@ -325,24 +376,12 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm_tc(GemmTcArgs g, int *
   fence_after_sync();
   const uint32_t tmem = S.tmem;
   const uint32_t a_addr = smem_u32(S.A), b_addr = smem_u32(S.B);
-  const __nv_bfloat16 zero = __float2bfloat16(0.f);
   const __nv_bfloat16 *Ag = static_cast<const __nv_bfloat16 *>(g.A), *Bg = static_cast<const __nv_bfloat16 *>(g.B);
   uint32_t phase = 0;
   bool any = false;
   for (int k0 = kb; k0 < ke; k0 += kH) {
-    // stage A (rows m0.., columns k0..) and B (columns n, rows k0..) into the core-matrix layout;
-    // the element order follows the unit stride of each operand so that global reads coalesce
-    for (int e = tid; e < kH * kH; e += kGemmThreads) {
-      const int hi = e >> 7, lo = e & (kH - 1);
-      const int am = g.sak == 1 ? hi : lo, ak = g.sak == 1 ? lo : hi;
-      const int m = m0 + am, k = k0 + ak;
-      *reinterpret_cast<__nv_bfloat16 *>(S.A + core_off(am, ak)) =
-          (m < g.M && k < ke) ? Ag[(int64_t)m * g.sam + (int64_t)k * g.sak] : zero;
-      const int bn = g.sbn == 1 ? lo : hi, bk = g.sbn == 1 ? hi : lo;
-      const int kk = k0 + bk;
-      *reinterpret_cast<__nv_bfloat16 *>(S.B + core_off(bn, bk)) =
-          kk < ke ? Bg[(int64_t)kk * g.sbk + (int64_t)bn * g.sbn] : zero;
-    }
+    stage_block(S.A, Ag, g.sam, g.sak, m0, kTile, g.M, k0, ke, tid);
+    stage_block(S.B, Bg, g.sbn, g.sbk, n0, kGemmN, kH, k0, ke, tid);
     fence_proxy_async();
     fence_before_sync();
     __syncthreads();
@@ -350,7 +389,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm_tc(GemmTcArgs g, int *
     if (tid == 0) {
 #pragma unroll
       for (int q = 0; q < kH / 16; ++q)
-        mma_bf16(tmem, smem_desc(a_addr + q * 2 * kLBO), smem_desc(b_addr + q * 2 * kLBO), (any || q > 0) ? 1u : 0u);
+        mma_bf16_n64(tmem, smem_desc(a_addr + q * 2 * kLBO), smem_desc(b_addr + q * 2 * kLBO), (any || q > 0) ? 1u : 0u);
       mma_commit(bar);
     }
     any = true;
@@ -371,13 +410,20 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm_tc(GemmTcArgs g, int *
     }
     const int r = m0 + tid;
     const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
-    for (int cc = 0; cc < kH / 32; ++cc) {
+    for (int cc = 0; cc < kGemmN / 32; ++cc) {
       float v[32];
       if (any) tmem_ld32(taddr + 32 * cc, v);
       else
         for (int u = 0; u < 32; ++u) v[u] = 0.f;
-      if (r < g.M)
-        for (int u = 0; u < 32; ++u) C[(int64_t)r * scm + (int64_t)(32 * cc + u) * scn] = v[u];
+      if (r < g.M) {
+        float *row = C + (int64_t)r * scm + (int64_t)(n0 + 32 * cc) * scn;
+        if (scn == 1 && (((uintptr_t)row & 15) == 0)) {
+#pragma unroll
+          for (int u = 0; u < 32; u += 4) *reinterpret_cast<float4 *>(row + u) = make_float4(v[u], v[u + 1], v[u + 2], v[u + 3]);
+        } else {
+          for (int u = 0; u < 32; ++u) row[(int64_t)u * scn] = v[u];
+        }
+      }
     }
   }
   if (S.fail && tid == 0) atomicOr(err, kErrTimeout);
@@ -385,11 +431,16 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_gemm_tc(GemmTcArgs g, int *
   __syncthreads();
   fence_after_sync();
   if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kTmemCols) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"((uint32_t)kGemmN) : "memory");
 }
 
 int gemm_tc(pic_t *h, const GemmTcArgs &g0) {
   GemmTcArgs g = g0;
+  // the 16-byte staging needs the unit-stride operand 16-byte aligned along that dimension
+  if (!(g.sak == 1 || g.sam == 1) || !(g.sbk == 1 || g.sbn == 1) || ((uintptr_t)g.A & 15) || ((uintptr_t)g.B & 15) ||
+      (g.sak != 1 && g.sak % 8) || (g.sak == 1 && g.sam % 8) || (g.sbk != 1 && g.sbk % 8) || (g.sbk == 1 && g.sbn % 8) ||
+      (g.sam == 1 && g.M % 8) || ((g.sak == 1 || g.sbk == 1) && g.K % 8))
+    return pic_fail(h, PIC_E_INVALID, "gemm_tc: operand layout not supported");
   g.kper = (g.K + g.splits - 1) / g.splits;
   g.kper = (g.kper + kH - 1) / kH * kH;
   const int smem = (int)sizeof(GemmSmem) + 1024;
@@ -400,7 +451,7 @@ int gemm_tc(pic_t *h, const GemmTcArgs &g0) {
     PIC_CUDA(h, cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     configured_dev = dev;
   }
-  const dim3 grid((g.M + kTile - 1) / kTile, 1, g.splits);
+  const dim3 grid((g.M + kTile - 1) / kTile, kH / kGemmN, g.splits);
   ++h->nlaunch;
   k_gemm_tc<<<grid, kGemmThreads, smem, h->stream>>>(g, &h->clock->err);
   return launch_check(h, "gemm (tcgen05)");
