@@ -1,7 +1,8 @@
 """Monte Carlo collisions of the step (test infrastructure only).
 
 Impact ionization Cu + e -> Cu+ + 2e (Sec. 2.2, Table colls) with SP splitting (Sec. 2.3.2),
-and direct field ionization of neutrals (Sec. 2.3.4, eq:dfi).
+the Cu2+ channels of Table colls (Cu + e -> Cu2+ + 3e, Cu+ + e -> Cu2+ + 2e), and direct field
+ionization of neutrals (Sec. 2.3.4, eq:dfi).
 
 Readings where the paper is silent or ambiguous (each listed in the design notes):
   * Pairing (Sec. 2.2 cites Takizuka-Abe): in a cell with N_e electron SPs and N_n neutral
@@ -37,15 +38,32 @@ from . import philox
 
 LOTZ_A = 4.5e-14 * 1e-4           # m^2 eV^2
 F32 = np.float32
+# Cu2+ channels (Table colls).  The paper's cross sections are not available; stand-ins of the
+# same Lotz form: direct double ionization of Cu (threshold xi_1 + xi_2) with a tenth of the
+# single-ionization constant (the paper calls these cross sections "fairly small"), and
+# ionization of Cu+ with the Lotz constant per electron times the 10 electrons of its 3d shell.
+XI_DOUBLE = C.XI_CU_EV + C.XI2_CU_EV
+LOTZ_A_DOUBLE = LOTZ_A / 10.0
+LOTZ_Q_CU1 = 10
 
 
-def sigma_ion(E_eV, xi=C.XI_CU_EV):
-    """Lotz-form stand-in cross section [m^2]; 0 at or below threshold."""
+def sigma_ion(E_eV, xi=C.XI_CU_EV, a=LOTZ_A):
+    """Lotz-form stand-in cross section a ln(E/xi) / (E xi) [m^2]; 0 at or below threshold."""
     E = np.asarray(E_eV, dtype=np.float64)
     out = np.zeros_like(E)
     m = E > xi
-    out[m] = LOTZ_A * np.log(E[m] / xi) / (E[m] * xi)
+    out[m] = a * np.log(E[m] / xi) / (E[m] * xi)
     return out
+
+
+def sigma_double(E_eV):
+    """Cu + e -> Cu2+ + 3e stand-in [m^2]."""
+    return sigma_ion(E_eV, XI_DOUBLE, LOTZ_A_DOUBLE)
+
+
+def sigma_ion2(E_eV):
+    """Cu+ + e -> Cu2+ + 2e stand-in [m^2]."""
+    return sigma_ion(E_eV, C.XI2_CU_EV, LOTZ_A * LOTZ_Q_CU1)
 
 
 def rot_inv(theta, phi, vec):
@@ -88,68 +106,151 @@ def _append(lst):
     return {k: np.array([d[k] for d in lst], dtype=P.DTYPES[k]) for k in P.FIELDS}
 
 
-def impact_ionization(grid, prm, e, e_off, n, n_off, step, ids):
+def _pairs(seed, purpose, step, e_off, t_off):
+    """Inter-species pairs of every cell holding both species, projectile species first in the
+    order (pairs with an electron projectile in cell order, then the others): (projectile,
+    target, target SPs in the cell) with the projectile the species with fewer SPs (tie: the
+    electrons) and target (k + o_c) mod N_t."""
+    cnt_e, cnt_t = np.diff(e_off), np.diff(t_off)
+    pairs_e, pairs_t = [], []
+    for c in np.nonzero((cnt_e > 0) & (cnt_t > 0))[0]:
+        Ne, Nt = int(cnt_e[c]), int(cnt_t[c])
+        if Ne <= Nt:
+            o = int(philox.uniform_index(seed, purpose, c, step, 0, Nt))
+            for k in range(Ne):
+                pairs_e.append((e_off[c] + k, t_off[c] + (k + o) % Nt, Nt))
+        else:
+            o = int(philox.uniform_index(seed, purpose, c, step, 0, Ne))
+            for k in range(Nt):
+                pairs_t.append((t_off[c] + k, e_off[c] + (k + o) % Ne, Ne))
+    return [(True, p) for p in pairs_e] + [(False, p) for p in pairs_t]
+
+
+def _split_electron(e, ie, ncoll, v, ids, new_e):
+    """The ncoll colliding sub-particles of electron SP ie take velocity v: the whole SP turns
+    when ncoll is its weight, else they leave as a new SP (Sec. 2.3.2)."""
+    we = int(e["w"][ie])
+    if ncoll == we:
+        e["vx"][ie], e["vy"][ie], e["vz"][ie] = F32(v[0]), F32(v[1]), F32(v[2])
+    else:
+        e["w"][ie] = we - ncoll
+        new_e.append(_new_sp(e["x"][ie], e["y"][ie], e["z"][ie], v[0], v[1], v[2], ncoll, ids.take()))
+
+
+def impact_ionization(grid, prm, e, e_off, n, n_off, step, ids, double=False):
     """One MCC pass over all cells.  e, n: cell-sorted electron / neutral SPs (modified in
-    place: weights and velocities); returns (new ions, new electrons, number of events)."""
+    place: weights and velocities); returns (new ions, new electrons, number of events).
+
+    double: the Cu2+ channel Cu + e -> Cu2+ + 3e competes for the same draws, by the total
+    cross section (the paper gives eq:colp for one process): P_T = 1 - exp(-u n_t W_t
+    (sigma_1 + sigma_2) dt), and sub-particle i ionizes once when U_i < P_T sigma_1/sigma_T and
+    twice when P_T sigma_1/sigma_T <= U_i < P_T; N_1 capped at the target weight, N_2 at what
+    is left of it.  Without the channel (or below its threshold) sigma_2 = 0 and the single
+    decisions are those of the one-process pass.  The double events are applied after all
+    single ones, in the same pair order (Cu2+, the scattered electron when the electron SP
+    splits, two secondary electrons; E0 - xi_1 - xi_2 shared equally by the three outgoing
+    electrons, directions by eq:du); returns then also (new Cu2+, new electrons, double
+    events)."""
     V_cell = grid.dx ** 3
     dt = prm["dt"]
     seed = prm["seed"]
     w_min = prm["w_min"]
-    ncell = grid.ncell
-    cnt_e = np.diff(e_off)
-    cnt_n = np.diff(n_off)
-    both = np.nonzero((cnt_e > 0) & (cnt_n > 0))[0]
-    pairs_e, pairs_n = [], []          # (projectile index, target index)
-    for c in both:
-        Ne, Nn = int(cnt_e[c]), int(cnt_n[c])
-        if Ne <= Nn:
-            o = int(philox.uniform_index(seed, philox.PAIR, c, step, 0, Nn))
-            for k in range(Ne):
-                pairs_e.append((c, e_off[c] + k, n_off[c] + (k + o) % Nn, Nn))
-        else:
-            o = int(philox.uniform_index(seed, philox.PAIR, c, step, 0, Ne))
-            for k in range(Nn):
-                pairs_n.append((c, n_off[c] + k, e_off[c] + (k + o) % Ne, Ne))
     new_i, new_e = [], []
+    dbl = []
     events = 0
-    for proj_is_e, plist in ((True, pairs_e), (False, pairs_n)):
-        for (c, pi, ti, Nt) in plist:
-            ie, inn = (pi, ti) if proj_is_e else (ti, pi)
-            we, wn = int(e["w"][ie]), int(n["w"][inn])
-            ve = np.array([e["vx"][ie], e["vy"][ie], e["vz"][ie]], dtype=np.float64)
-            vn = np.array([n["vx"][inn], n["vy"][inn], n["vz"][inn]], dtype=np.float64)
-            uvec = ve - vn
-            u2 = uvec[0] * uvec[0] + uvec[1] * uvec[1] + uvec[2] * uvec[2]
-            u = math.sqrt(u2)
-            E0 = 0.5 * C.M_E * u2 / C.E_CHARGE
-            sig = float(sigma_ion(E0))
-            wt = wn if proj_is_e else we
-            wp = we if proj_is_e else wn
-            x = u * (Nt / V_cell) * (wt * w_min) * sig * dt
-            prob = -math.expm1(-x)
-            proj_id = int(e["id"][ie] if proj_is_e else n["id"][inn])
-            U = philox.uniform(seed, philox.ION, proj_id, step, np.arange(wp))
-            ncoll = int(np.sum(U < prob))
-            ncoll = min(ncoll, wt)
-            if ncoll == 0:
-                continue
-            events += 1
-            # products: ion, scattered electron, secondary electron
-            new_i.append(_new_sp(n["x"][inn], n["y"][inn], n["z"][inn], n["vx"][inn], n["vy"][inn],
-                                 n["vz"][inn], ncoll, ids.take()))
-            n["w"][inn] = wn - ncoll
-            Ek = 0.5 * (E0 - C.XI_CU_EV)
-            uk = math.sqrt(2.0 * Ek * C.E_CHARGE / C.M_E)
-            Us = philox.uniform(seed, philox.SCAT, proj_id, step, np.arange(4))
-            v1 = vn + scatter_velocity(uvec, uk, 2.0 * Us[0] - 1.0, 2.0 * math.pi * Us[1])
-            v2 = vn + scatter_velocity(uvec, uk, 2.0 * Us[2] - 1.0, 2.0 * math.pi * Us[3])
-            if ncoll == we:
-                e["vx"][ie], e["vy"][ie], e["vz"][ie] = F32(v1[0]), F32(v1[1]), F32(v1[2])
-            else:
-                e["w"][ie] = we - ncoll
-                new_e.append(_new_sp(e["x"][ie], e["y"][ie], e["z"][ie], v1[0], v1[1], v1[2], ncoll, ids.take()))
-            new_e.append(_new_sp(n["x"][inn], n["y"][inn], n["z"][inn], v2[0], v2[1], v2[2], ncoll, ids.take()))
-    return _append(new_i), _append(new_e), events
+    for proj_is_e, (pi, ti, Nt) in _pairs(seed, philox.PAIR, step, e_off, n_off):
+        ie, inn = (pi, ti) if proj_is_e else (ti, pi)
+        we, wn = int(e["w"][ie]), int(n["w"][inn])
+        ve = np.array([e["vx"][ie], e["vy"][ie], e["vz"][ie]], dtype=np.float64)
+        vn = np.array([n["vx"][inn], n["vy"][inn], n["vz"][inn]], dtype=np.float64)
+        uvec = ve - vn
+        u2 = uvec[0] * uvec[0] + uvec[1] * uvec[1] + uvec[2] * uvec[2]
+        u = math.sqrt(u2)
+        E0 = 0.5 * C.M_E * u2 / C.E_CHARGE
+        wt = wn if proj_is_e else we
+        wp = we if proj_is_e else wn
+        s1 = float(sigma_ion(E0))
+        sT = s1 + float(sigma_double(E0)) if double else s1
+        PT = -math.expm1(-(u * (Nt / V_cell) * (wt * w_min) * sT * dt))
+        P1 = PT * (s1 / sT) if sT > 0 else 0.0
+        proj_id = int(e["id"][ie] if proj_is_e else n["id"][inn])
+        U = philox.uniform(seed, philox.ION, proj_id, step, np.arange(wp))
+        ncoll = min(int(np.sum(U < P1)), wt)
+        if double:
+            n2 = min(int(np.sum((U >= P1) & (U < PT))), wt - ncoll)
+            if n2 > 0:
+                dbl.append((ie, inn, proj_id, n2, uvec, E0, vn))
+        if ncoll == 0:
+            continue
+        events += 1
+        # products: ion, scattered electron, secondary electron
+        new_i.append(_new_sp(n["x"][inn], n["y"][inn], n["z"][inn], n["vx"][inn], n["vy"][inn],
+                             n["vz"][inn], ncoll, ids.take()))
+        n["w"][inn] = wn - ncoll
+        Ek = 0.5 * (E0 - C.XI_CU_EV)
+        uk = math.sqrt(2.0 * Ek * C.E_CHARGE / C.M_E)
+        Us = philox.uniform(seed, philox.SCAT, proj_id, step, np.arange(4))
+        v1 = vn + scatter_velocity(uvec, uk, 2.0 * Us[0] - 1.0, 2.0 * math.pi * Us[1])
+        v2 = vn + scatter_velocity(uvec, uk, 2.0 * Us[2] - 1.0, 2.0 * math.pi * Us[3])
+        _split_electron(e, ie, ncoll, v1, ids, new_e)
+        new_e.append(_new_sp(n["x"][inn], n["y"][inn], n["z"][inn], v2[0], v2[1], v2[2], ncoll, ids.take()))
+    if not double:
+        return _append(new_i), _append(new_e), events
+    new_j, new_e2 = [], []
+    for (ie, inn, proj_id, n2, uvec, E0, vn) in dbl:
+        new_j.append(_new_sp(n["x"][inn], n["y"][inn], n["z"][inn], n["vx"][inn], n["vy"][inn], n["vz"][inn], n2,
+                             ids.take()))
+        n["w"][inn] = int(n["w"][inn]) - n2
+        uk = math.sqrt(2.0 * (E0 - XI_DOUBLE) / 3.0 * C.E_CHARGE / C.M_E)
+        Us = philox.uniform(seed, philox.SCAT2, proj_id, step, np.arange(6))
+        vs = [vn + scatter_velocity(uvec, uk, 2.0 * Us[2 * q] - 1.0, 2.0 * math.pi * Us[2 * q + 1]) for q in range(3)]
+        _split_electron(e, ie, n2, vs[0], ids, new_e2)
+        for v in vs[1:]:
+            new_e2.append(_new_sp(n["x"][inn], n["y"][inn], n["z"][inn], v[0], v[1], v[2], n2, ids.take()))
+    return _append(new_i), _append(new_e), events, _append(new_j), _append(new_e2), len(dbl)
+
+
+def ion_ionization(grid, prm, e, e_off, i, i_off, step, ids):
+    """Cu+ + e -> Cu2+ + 2e (Table colls) on the cell-sorted electrons and Cu+, with the pairing,
+    the per-sub-particle probability and the splitting of impact ionization (own Philox
+    purposes): Cu2+ of weight N with the Cu+ SP's position and velocity, the Cu+ SP loses N, the
+    electron SP splits, a secondary electron at the Cu+ position; E0 - xi_2 shared equally by the
+    two outgoing electrons (eq:du about u = v_e - v_i).  e, i modified in place; returns (new Cu2+,
+    new electrons, events)."""
+    V_cell = grid.dx ** 3
+    dt, seed, w_min = prm["dt"], prm["seed"], prm["w_min"]
+    new_j, new_e = [], []
+    events = 0
+    for proj_is_e, (pi, ti, Nt) in _pairs(seed, philox.PAIR_IZ, step, e_off, i_off):
+        ie, ii = (pi, ti) if proj_is_e else (ti, pi)
+        we, wi = int(e["w"][ie]), int(i["w"][ii])
+        if we <= 0 or wi <= 0:
+            continue
+        ve = np.array([e["vx"][ie], e["vy"][ie], e["vz"][ie]], dtype=np.float64)
+        vi = np.array([i["vx"][ii], i["vy"][ii], i["vz"][ii]], dtype=np.float64)
+        uvec = ve - vi
+        u2 = uvec[0] * uvec[0] + uvec[1] * uvec[1] + uvec[2] * uvec[2]
+        u = math.sqrt(u2)
+        E0 = 0.5 * C.M_E * u2 / C.E_CHARGE
+        wt = wi if proj_is_e else we
+        wp = we if proj_is_e else wi
+        prob = -math.expm1(-(u * (Nt / V_cell) * (wt * w_min) * float(sigma_ion2(E0)) * dt))
+        proj_id = int(e["id"][ie] if proj_is_e else i["id"][ii])
+        U = philox.uniform(seed, philox.ION_IZ, proj_id, step, np.arange(wp))
+        ncoll = min(int(np.sum(U < prob)), wt)
+        if ncoll == 0:
+            continue
+        events += 1
+        new_j.append(_new_sp(i["x"][ii], i["y"][ii], i["z"][ii], i["vx"][ii], i["vy"][ii], i["vz"][ii], ncoll,
+                             ids.take()))
+        i["w"][ii] = wi - ncoll
+        uk = math.sqrt(2.0 * 0.5 * (E0 - C.XI2_CU_EV) * C.E_CHARGE / C.M_E)
+        Us = philox.uniform(seed, philox.SCAT_IZ, proj_id, step, np.arange(4))
+        v1 = vi + scatter_velocity(uvec, uk, 2.0 * Us[0] - 1.0, 2.0 * math.pi * Us[1])
+        v2 = vi + scatter_velocity(uvec, uk, 2.0 * Us[2] - 1.0, 2.0 * math.pi * Us[3])
+        _split_electron(e, ie, ncoll, v1, ids, new_e)
+        new_e.append(_new_sp(i["x"][ii], i["y"][ii], i["z"][ii], v2[0], v2[1], v2[2], ncoll, ids.take()))
+    return _append(new_j), _append(new_e), events
 
 
 # --------------------------------------------------------------------------------------

@@ -26,6 +26,9 @@ LORENTZ = 2.0e-8                  # W Ohm K^-2
 
 # Sec. 2.3.3 (Eq. 14): ionization potential of Cu (first ionization, textbook; not printed).
 XI_CU_EV = 7.726
+# Second ionization energy of Cu (Cu+ -> Cu2+, textbook; not printed): the threshold of the
+# Cu2+ channels of Table colls (Cu+ + e -> Cu2+ + 2e; Cu + e -> Cu2+ + 3e at XI_CU_EV + XI2_CU_EV).
+XI2_CU_EV = 20.292
 
 # Sec. 2.3.2: maximum SP number density n_max = 1e-6 per cubic Angstrom.
 N_MAX = 1e-6 * 1e30               # m^-3

@@ -1,6 +1,6 @@
 """Coulomb collisions between charged SPs by the binary method the paper cites (Table colls:
-e-e, Cu+-e, Cu+-Cu+; Takizuka and Abe, J. Comput. Phys. 25, 205 (1977)).  Test
-infrastructure only.
+e-e, Cu+-e, Cu+-Cu+, and with Cu2+ (Sec. 2.2: between all charged species) e-Cu2+, Cu+-Cu2+,
+Cu2+-Cu2+; Takizuka and Abe, J. Comput. Phys. 25, 205 (1977)).  Test infrastructure only.
 
 Every pair scatters every step by a small random angle theta: delta = tan(theta/2) is normal
 with zero mean and variance
@@ -11,9 +11,9 @@ new velocities.
 
 Readings (the paper names the method, not these details):
   * Three passes after the elastic passes (or impact ionization) and before field ionization:
-    e-e, e-Cu+, Cu+-Cu+, each on the cell-sorted SPs with the pairings of the elastic passes
-    (inter-species: fewer SPs project, ties the electrons; like-species: shuffled places
-    (o + 2m, o + 2m + 1) mod N).
+    e-e, e-Cu+, Cu+-Cu+ (then e-Cu2+, Cu+-Cu2+, Cu2+-Cu2+ when Cu2+ is simulated), each on the
+    cell-sorted SPs with the pairings of the elastic passes (inter-species: fewer SPs project,
+    ties the first-named species; like-species: shuffled places (o + 2m, o + 2m + 1) mod N).
   * n is the target species' real density as the pair sees it, n_t W_t (the target SP
     density times the paired target's weight), as in eq:colp.
   * lnL is a constant parameter (default 10): the paper gives no plasma parameter for it.
@@ -33,6 +33,7 @@ from . import philox
 from .elastic import delta_u
 
 PAIR_EE, DRAW_EE, PAIR_EI, DRAW_EI, PAIR_II, DRAW_II = 16, 17, 18, 19, 20, 21
+PAIR_EJ, DRAW_EJ, PAIR_IJ, DRAW_IJ, PAIR_JJ, DRAW_JJ = 26, 27, 28, 29, 30, 31
 COULOMB_LOG = 10.0
 F32 = np.float32
 
@@ -116,21 +117,40 @@ def coulomb_ii(grid, prm, i, i_off, step):
     return _like(grid, prm, i, i_off, C.E_CHARGE, C.M_CU, PAIR_II, DRAW_II, step)
 
 
+def coulomb_jj(grid, prm, j, j_off, step):
+    """Cu2+ + Cu2+ between the Cu2+ SPs of each cell; returns events."""
+    return _like(grid, prm, j, j_off, 2.0 * C.E_CHARGE, C.M_CU, PAIR_JJ, DRAW_JJ, step)
+
+
+def _inter(grid, prm, A, a_off, B, b_off, qa, qb, ma, mb, pair_purpose, draw, step):
+    """A + B pairs of every cell holding both (fewer SPs project, ties A); returns events."""
+    V_cell = grid.dx ** 3
+    cnt_a, cnt_b = np.diff(a_off), np.diff(b_off)
+    events = 0
+    for c in np.nonzero((cnt_a > 0) & (cnt_b > 0))[0]:
+        Na, Nb = int(cnt_a[c]), int(cnt_b[c])
+        if Na <= Nb:
+            o = int(philox.uniform_index(prm["seed"], pair_purpose, c, step, 0, Nb))
+            for k in range(Na):
+                events += _pair(A, a_off[c] + k, B, b_off[c] + (k + o) % Nb, qa, qb, ma, mb, Nb, V_cell, prm, draw, step)
+        else:
+            o = int(philox.uniform_index(prm["seed"], pair_purpose, c, step, 0, Na))
+            for k in range(Nb):
+                events += _pair(B, b_off[c] + k, A, a_off[c] + (k + o) % Na, qb, qa, mb, ma, Na, V_cell, prm, draw, step)
+    return events
+
+
 def coulomb_ei(grid, prm, e, e_off, i, i_off, step):
     """e + Cu+ pairs (fewer SPs project, ties the electrons); returns events."""
-    V_cell = grid.dx ** 3
-    cnt_e, cnt_i = np.diff(e_off), np.diff(i_off)
-    events = 0
-    for c in np.nonzero((cnt_e > 0) & (cnt_i > 0))[0]:
-        Ne, Ni = int(cnt_e[c]), int(cnt_i[c])
-        if Ne <= Ni:
-            o = int(philox.uniform_index(prm["seed"], PAIR_EI, c, step, 0, Ni))
-            for k in range(Ne):
-                events += _pair(e, e_off[c] + k, i, i_off[c] + (k + o) % Ni, -C.E_CHARGE, C.E_CHARGE, C.M_E, C.M_CU,
-                                Ni, V_cell, prm, DRAW_EI, step)
-        else:
-            o = int(philox.uniform_index(prm["seed"], PAIR_EI, c, step, 0, Ne))
-            for k in range(Ni):
-                events += _pair(i, i_off[c] + k, e, e_off[c] + (k + o) % Ne, C.E_CHARGE, -C.E_CHARGE, C.M_CU, C.M_E,
-                                Ne, V_cell, prm, DRAW_EI, step)
-    return events
+    return _inter(grid, prm, e, e_off, i, i_off, -C.E_CHARGE, C.E_CHARGE, C.M_E, C.M_CU, PAIR_EI, DRAW_EI, step)
+
+
+def coulomb_ej(grid, prm, e, e_off, j, j_off, step):
+    """e + Cu2+ pairs (fewer SPs project, ties the electrons); returns events."""
+    return _inter(grid, prm, e, e_off, j, j_off, -C.E_CHARGE, 2.0 * C.E_CHARGE, C.M_E, C.M_CU, PAIR_EJ, DRAW_EJ,
+                  step)
+
+
+def coulomb_ij(grid, prm, i, i_off, j, j_off, step):
+    """Cu+ + Cu2+ pairs (fewer SPs project, ties Cu+); returns events."""
+    return _inter(grid, prm, i, i_off, j, j_off, C.E_CHARGE, 2.0 * C.E_CHARGE, C.M_CU, C.M_CU, PAIR_IJ, DRAW_IJ, step)

@@ -19,6 +19,9 @@ _S32 = np.uint64(32)
 
 # purposes of the draws (one key per purpose)
 EMIT, PAIR, ION, SCAT, DFI, EVAP, SPUT = 1, 2, 3, 4, 5, 6, 7
+# Cu2+ channels: scattering of double ionization; pairing, draws and scattering of the
+# ionization of Cu+ (the Coulomb passes with Cu2+ keep their purposes in coulomb.py)
+SCAT2, PAIR_IZ, ION_IZ, SCAT_IZ = 22, 23, 24, 25
 
 
 def philox4x32_10(c0, c1, c2, c3, k0, k1):

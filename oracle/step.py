@@ -4,20 +4,24 @@ Order (Sec. 2.3.1 and Fig. newpic; the paper prints no pseudocode, this is the r
   a1 emission from every exposed face (field from phi^n, temperature of the owner cell)
   a2 surface injection: evaporation, then sputtering from the previous step's ion impacts
   a3 gather + leapfrog push of every SP (new ones included) + boundary removal / ion impacts
-     (with an external circuit, prm circuit_R and circuit_C > 0: then the Shockley-Ramo current
-     of the pushed e- and Cu+ and one Euler step of the RC circuit; the step's Poisson solve
-     holds the anode at the new V_gap)
+     (Cu+ and Cu2+ alike; with an external circuit, prm circuit_R and circuit_C > 0: then the
+     Shockley-Ramo current of the pushed e-, Cu+ and Cu2+ and one Euler step of the RC circuit;
+     the step's Poisson solve holds the anode at the new V_gap)
   a4 stable cell sort of every species (survivors in previous order); with prm merge_max > 0,
      SP merging in the over-full cells
-  a5 impact ionization MCC (with prm "elastic": then e-Cu and Cu-Cu elastic collisions and
-     Cu+-Cu charge exchange; with prm "coulomb": then e-e, e-Cu+ and Cu+-Cu+ Coulomb
-     collisions; all on the sorted SPs), a6 direct field ionization
+  a5 impact ionization MCC (with prm "ion2": the Cu2+ channels of Table colls, double
+     ionization of Cu inside the same pass and then Cu+ + e -> Cu2+ + 2e; with prm "elastic":
+     then e-Cu and Cu-Cu elastic collisions and Cu+-Cu charge exchange; with prm "coulomb": then
+     e-e, e-Cu+ and Cu+-Cu+ Coulomb collisions, and with "ion2" also e-Cu2+, Cu+-Cu2+ and
+     Cu2+-Cu2+; all on the sorted SPs), a6 direct field ionization
   a7 fixed-point charge deposit, a8 Poisson solve, a9 node field
   a10 every n_heat steps: continuity + heat on the tip cells
 
 New SPs take consecutive ids in this order: emitted electrons (face order), evaporated
 neutrals (face order), sputtered neutrals (face order), MCC products (pair order: ion,
-scattered electron, secondary electron), DFI products (neutral order: ion, electron).
+scattered electron, secondary electron; then the double ionizations in pair order: Cu2+,
+scattered electron, two secondary electrons; then the Cu+ ionizations: Cu2+, scattered
+electron, secondary electron), elastic products, DFI products (neutral order: ion, electron).
 Within each species, new SPs are appended after the existing ones in the same order.
 """
 import math
@@ -27,8 +31,9 @@ import numpy as np
 from . import circuit, collide, coulomb, elastic, emission, field, heat, merge, particles as P, philox, surface
 from . import constants as C
 
-E_, N_, I_ = "e", "n", "i"
-SPECIES = {E_: (-1, C.M_E), N_: (0, C.M_CU), I_: (1, C.M_CU)}
+E_, N_, I_, J_ = "e", "n", "i", "j"
+SPECIES = {E_: (-1, C.M_E), N_: (0, C.M_CU), I_: (1, C.M_CU), J_: (2, C.M_CU)}
+IONS = (I_, J_)
 F32 = np.float32
 
 
@@ -37,6 +42,8 @@ class State:
         self.grid = grid
         self.prm = dict(prm)
         self.sp = {k: {f: np.asarray(v[f]).astype(P.DTYPES[f]).copy() for f in P.FIELDS} for k, v in species.items()}
+        for k in SPECIES:               # Cu2+ (and any species not given) starts empty
+            self.sp.setdefault(k, P.empty())
         self.phi = np.asarray(phi, dtype=np.float64).copy()
         self.E = field.efield(grid, self.phi)
         ncv = int(grid.solid.sum())
@@ -191,8 +198,8 @@ def push_all(st):
         sp_ = st.sp[k]
         qmdt = P.kick_factor(Z, m, prm["dt"]) if Z != 0 else 0.0
         new = P.push_f32(sp_, st.E, qmdt, dtdx)
-        a, impacts = P.boundary(g, sp_, new, k == I_, m)
-        if k == I_:
+        a, impacts = P.boundary(g, sp_, new, k in IONS, m)
+        if k in IONS:
             record_impacts(st, impacts)
         for c, v in zip(("x", "y", "z", "vx", "vy", "vz"), new):
             sp_[c] = v.astype(np.float32)
@@ -200,6 +207,8 @@ def push_all(st):
         st.count["removed_" + k] = int((~a).sum())
         if k == I_:
             st.count["ion_impacts"] = len(impacts)
+        elif k == J_:
+            st.count["ion_impacts"] += len(impacts)
     return alive
 
 
@@ -209,7 +218,7 @@ def circuit_update(st, alive):
     prm = st.prm
     if st.E0 is None:
         st.E0 = circuit.unit_field(st.grid)
-    charged = [(-1, P.take(st.sp[E_], np.nonzero(alive[E_])[0])), (1, P.take(st.sp[I_], np.nonzero(alive[I_])[0]))]
+    charged = [(SPECIES[k][0], P.take(st.sp[k], np.nonzero(alive[k])[0])) for k in (E_, I_, J_)]
     st.I_gap = circuit.gap_current(st.E0, charged, prm["w_min"])
     st.V_gap, st.I_tot = circuit.circuit_step(st.V_gap, st.I_gap, prm["V0"], prm["circuit_R"], prm["circuit_C"],
                                               prm["dt"])
@@ -219,6 +228,7 @@ def deposit_all(st):
     g = st.grid
     Q = P.deposit(g, st.sp[E_], -1)
     Q = P.deposit(g, st.sp[I_], 1, Q=Q)
+    Q = P.deposit(g, st.sp[J_], 2, Q=Q)
     return Q
 
 
@@ -261,11 +271,17 @@ def step(st, emission_fn=None):
         st.sp[k], st.off[k] = P.stable_sort(g, st.sp[k], alive[k])
     if prm.get("merge_max", 0) > 0:
         st.count["merged"] = sum(merge.merge_species(st.sp[k], st.off[k], prm["merge_max"], prm["w_max_units"])
-                                 for k in (E_, N_, I_))
+                                 for k in (E_, N_, I_, J_))
     # a5
     ids = collide.Counter(st.next_id)
-    ni, ne, ev = collide.impact_ionization(g, prm, st.sp[E_], st.off[E_], st.sp[N_], st.off[N_], st.step, ids)
-    st.count["impact_ionizations"] = ev
+    ion2 = bool(prm.get("ion2"))
+    mcc = collide.impact_ionization(g, prm, st.sp[E_], st.off[E_], st.sp[N_], st.off[N_], st.step, ids, double=ion2)
+    ni, ne, st.count["impact_ionizations"] = mcc[:3]
+    nj, ne_d, nj_iz, ne_iz = P.empty(), P.empty(), P.empty(), P.empty()
+    if ion2:
+        nj, ne_d, st.count["double_ionizations"] = mcc[3:]
+        nj_iz, ne_iz, st.count["ion_ionizations"] = collide.ion_ionization(g, prm, st.sp[E_], st.off[E_], st.sp[I_],
+                                                                           st.off[I_], st.step, ids)
     el_e, el_i = P.empty(), P.empty()
     if prm.get("elastic"):
         el_e, el_n1, st.count["elastic_en"] = elastic.elastic_en(g, prm, st.sp[E_], st.off[E_], st.sp[N_], st.off[N_],
@@ -278,12 +294,17 @@ def step(st, emission_fn=None):
         st.count["coulomb_ee"] = coulomb.coulomb_ee(g, prm, st.sp[E_], st.off[E_], st.step)
         st.count["coulomb_ei"] = coulomb.coulomb_ei(g, prm, st.sp[E_], st.off[E_], st.sp[I_], st.off[I_], st.step)
         st.count["coulomb_ii"] = coulomb.coulomb_ii(g, prm, st.sp[I_], st.off[I_], st.step)
+        if ion2:
+            st.count["coulomb_ej"] = coulomb.coulomb_ej(g, prm, st.sp[E_], st.off[E_], st.sp[J_], st.off[J_], st.step)
+            st.count["coulomb_ij"] = coulomb.coulomb_ij(g, prm, st.sp[I_], st.off[I_], st.sp[J_], st.off[J_], st.step)
+            st.count["coulomb_jj"] = coulomb.coulomb_jj(g, prm, st.sp[J_], st.off[J_], st.step)
     # a6
     ni2, ne2, ev2 = collide.field_ionization(g, prm, st.sp[N_], st.E, st.step, ids)
     st.count["field_ionizations"] = ev2
     st.next_id = ids.next_id
     st.sp[I_] = P.concat(P.concat(P.concat(st.sp[I_], ni), el_i), ni2)
-    st.sp[E_] = P.concat(P.concat(P.concat(st.sp[E_], ne), el_e), ne2)
+    st.sp[E_] = P.concat(P.concat(P.concat(P.concat(P.concat(st.sp[E_], ne), ne_d), ne_iz), el_e), ne2)
+    st.sp[J_] = P.concat(P.concat(st.sp[J_], nj), nj_iz)
     # a7-a9
     solve_field(st)
     # a10
