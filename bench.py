@@ -103,7 +103,7 @@ class ClockSampler:
 # ---- algorithmic traffic per stage (bytes) -------------------------------------------------------
 def stage_units(cfg, counts, mg_cycles, nface, emission_evals):
     n_sp = sum(counts)
-    n_chg = counts[0] + counts[2]
+    n_chg = counts[0] + sum(counts[2:])     # e-, Cu+ (and Cu2+)
     ncell = cfg["nx"] * cfg["ny"] * cfg["nz"]
     nnode = (cfg["nx"] + 1) * (cfg["ny"] + 1) * (cfg["nz"] + 1)
     return {
@@ -270,6 +270,9 @@ def run_ours(args):
     if args.merge > 0:   # SP merging in cells above this many SPs of a species
         cfg["merge_max"] = args.merge
         prod_flags |= pic.F_MERGE
+    if args.ion2:   # Cu2+: double ionization, ionization of Cu+, Coulomb pairs with Cu2+ (with --coulomb)
+        prod_flags |= pic.F_ION2
+        cap = cap + (int(0.2 * n_sp * 0.5),)
     plain_flags = pic.F_ALL & ~pic.F_SURROGATE & ~pic.F_MIXED_MG
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
@@ -451,6 +454,10 @@ def run_ours(args):
                    "coulomb": ({"e_e": d1["coulomb_ee"], "e_Cu+": d1["coulomb_ei"], "Cu+_Cu+": d1["coulomb_ii"]}
                                if args.coulomb else None),
                    "merge": ({"merge_max": args.merge, "merged_last_step": d1["merged"]} if args.merge > 0 else None),
+                   "ion2": ({"double_ionizations_last_step": d1["double_ionizations"],
+                             "cu1_ionizations_last_step": d1["ion_ionizations"], "count_cu2_end": d1["count"][3],
+                             "coulomb_e_cu2_last_step": d1["coulomb_ej"], "coulomb_cu1_cu2_last_step": d1["coulomb_ij"],
+                             "coulomb_cu2_cu2_last_step": d1["coulomb_jj"]} if args.ion2 else None),
                    "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()}, "mg_cycles": d1["mg_cycles"],
                    "mg_cycles_per_step": (d1["mg_cycles_total"] - d0["mg_cycles_total"]) / args.steps,
                    "kernel_ms_per_step": kernel_ms,
@@ -738,6 +745,8 @@ def main():
     ap.add_argument("--elastic", action="store_true", help="step with elastic collisions and charge exchange")
     ap.add_argument("--extrapolate", action="store_true", help="start each solve from the time-extrapolated potential")
     ap.add_argument("--coulomb", action="store_true", help="step with Coulomb collisions between charged SPs")
+    ap.add_argument("--ion2", action="store_true", help="step with Cu2+ and its channels (double ionization, Cu+ "
+                                                         "ionization; with --coulomb its Coulomb pairs)")
     ap.add_argument("--merge", type=int, default=0, help="merge SPs in cells above this many SPs of a species (0: off)")
     args = ap.parse_args()
     if args.impl == "reference":

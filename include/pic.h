@@ -15,7 +15,8 @@
  * a Cu tip (cylinder + hemispherical cap on the axis x = nx/2, y = ny/2) is made of solid cells
  * whose centres lie inside it; all corners of solid cells are held at phi = 0.
  *
- * Species are indexed PIC_ELECTRON = 0, PIC_NEUTRAL = 1 (Cu), PIC_ION = 2 (Cu+).  Every SP has a
+ * Species are indexed PIC_ELECTRON = 0, PIC_NEUTRAL = 1 (Cu), PIC_ION = 2 (Cu+), PIC_ION2 = 3
+ * (Cu2+, present while PIC_F_ION2 is set: Table colls and Sec. 2.2).  Every SP has a
  * position in cell units (x/dx, float), a velocity [m/s] (float), a weight in units of w_min
  * (int32) and a 64-bit id that keys all its random draws (Philox4x32-10).
  *
@@ -48,7 +49,8 @@ extern "C" {
 #define PIC_ELECTRON 0
 #define PIC_NEUTRAL 1
 #define PIC_ION 2
-#define PIC_NSPECIES 3
+#define PIC_ION2 3
+#define PIC_NSPECIES 4
 
 /* flags of pic_params_t */
 #define PIC_F_EMISSION 0x01u    /* a1: thermal-field emission */
@@ -69,8 +71,16 @@ extern "C" {
 #define PIC_F_EXTRAPOLATE 0x1000u /* pic_step starts each solve from 2 phi^n - phi^(n-1) instead of phi^n */
 #define PIC_F_COULOMB 0x2000u   /* a5: then e-e, e-Cu+, Cu+-Cu+ Coulomb collisions (binary small-angle method) */
 #define PIC_F_MERGE 0x4000u     /* a4: after the sort, SP merging in cells above merge_max SPs of a species */
+#define PIC_F_ION2 0x8000u      /* Cu2+ (species PIC_ION2) and the Cu2+ channels of Table colls: with
+                                   PIC_F_IMPACT_ION double ionization Cu + e -> Cu2+ + 3e competing with
+                                   single ionization by the total cross section, then Cu+ + e -> Cu2+ + 2e;
+                                   with PIC_F_COULOMB also e-Cu2+, Cu+-Cu2+, Cu2+-Cu2+ Coulomb passes.
+                                   Cu2+ SPs are pushed, sorted, merged, deposited (charge 2), counted in
+                                   the gap current and sputter on impact like Cu+.  Stand-in Lotz cross
+                                   sections: a = 4.5e-15 cm^2 eV^2 at xi_1 + xi_2 = 28.018 eV (double),
+                                   a = 4.5e-13 cm^2 eV^2 at xi_2 = 20.292 eV (Cu+) */
 #define PIC_F_ALL 0xFFu         /* every stage, surrogate and mixed-precision solve; not FAST_INTEGRAL and
-                                   none of the opt-in flags 0x200-0x4000 */
+                                   none of the opt-in flags 0x200-0x8000 */
 
 typedef struct {
   double tip_radius; /* m */
@@ -83,7 +93,7 @@ typedef struct {
 } pic_grid_t;
 
 typedef struct {
-  int charge_e;     /* charge number: -1, 0, +1 */
+  int charge_e;     /* charge number: -1, 0, +1, +2 */
   double mass;      /* kg */
   int64_t capacity; /* maximum number of SPs held */
 } pic_species_t;
@@ -118,7 +128,7 @@ typedef struct {
   int64_t weight[PIC_NSPECIES];         /* sum of weights per species (units of w_min) */
   int64_t emitted, evaporated, sputtered;           /* SPs created this step */
   int64_t impact_ionizations, field_ionizations;    /* events this step */
-  int64_t removed[PIC_NSPECIES], ion_impacts;       /* this step */
+  int64_t removed[PIC_NSPECIES], ion_impacts;       /* this step (impacts of Cu+ and Cu2+) */
   int64_t total_charge_fixed;           /* sum of deposited node charge (units e w_min 2^-30) */
   int mg_cycles;                        /* cycles of the last Poisson solve */
   double mg_residual;                   /* relative residual of the last Poisson solve */
@@ -138,6 +148,9 @@ typedef struct {
   int64_t merged;           /* SP pairs merged this step (PIC_F_MERGE) */
   int64_t fallback_range, fallback_bin;  /* faces the surrogate left to the integral this step:
                                             outside its trained range / in a bin that failed validation */
+  int64_t double_ionizations, ion_ionizations;  /* Cu2+ events this step (PIC_F_ION2): Cu + e -> Cu2+ + 3e,
+                                                   Cu+ + e -> Cu2+ + 2e */
+  int64_t coulomb_ej, coulomb_ij, coulomb_jj;   /* Coulomb pairs with Cu2+ turned this step */
 } pic_diag_t;
 
 typedef struct pic_s pic_t;
@@ -147,7 +160,9 @@ typedef void (*pic_free_fn)(void *ptr, size_t bytes, void *stream, void *user);
 /* Create a handle (Sec. 2.1 statement of the problem): builds the staircased geometry, the
  * face list and the multigrid hierarchy on the device, then calibrates V0 from apex_field by a
  * Laplace solve (unless params->V0 > 0) and solves for the initial potential.
- * species: PIC_NSPECIES entries in the order electron, Cu, Cu+. */
+ * species: nspecies entries in the order electron, Cu, Cu+, Cu2+ (nspecies 4), or the first three
+ * (nspecies 3: Cu2+ then holds at most one SP, and PIC_F_ION2 fails with PIC_E_CAPACITY as soon as a
+ * Cu2+ channel produces more).  PIC_E_INVALID for any other nspecies. */
 int pic_create(const pic_geometry_t *geometry, const pic_grid_t *grid, const pic_species_t *species,
                int nspecies, const pic_params_t *params, pic_alloc_fn alloc, pic_free_fn free_fn,
                void *alloc_user, void *stream, pic_t **out);
@@ -228,19 +243,20 @@ int pic_set_solver(pic_t *h, double mg_tol, int mg_max_cycles);
 int pic_emit(pic_t *h);        /* a1 emission + a2 evaporation/sputter injection (appends SPs) */
 int pic_push(pic_t *h);        /* a3 gather + leapfrog + boundary removal, ion impact records */
 int pic_sort(pic_t *h);        /* a4 stable cell sort of every species, dropping removed SPs */
-int pic_collide(pic_t *h);     /* a5 impact ionization MCC, then a6 field ionization (appends) */
+int pic_collide(pic_t *h);     /* a5 impact ionization MCC (with PIC_F_ION2 the Cu2+ channels), the elastic
+                                  and Coulomb passes of their flags, then a6 field ionization (appends) */
 /* SP merging (Sec. 2.3.2) on cell-sorted SPs: in a cell holding N > merge_max SPs of a species the
  * SPs at places 2m, 2m+1 merge for m < min(N - merge_max, N/2) into their centre of mass
  * (w = w1 + w2, a = a1 mu/w2 + a2 mu/w1, mu = w1 w2/(w1 + w2)); the second keeps weight 0 until the
  * next sort.  pic_step runs it after the sort when PIC_F_MERGE is set; PIC_E_INVALID without the
  * flag or on unsorted SPs. */
 int pic_merge(pic_t *h);
-/* RC circuit (the circuit passage of Sec. 2.3.1, after ArcPIC): I_gap = sum over e- and Cu+ SPs of
+/* RC circuit (the circuit passage of Sec. 2.3.1, after ArcPIC): I_gap = sum over e-, Cu+ (and Cu2+) SPs of
  * q v . E0(x) (Shockley-Ramo, E0 the Laplace field with the anode at unit potential, gathered like
  * E), then V_gap += dt/C ((V0 - V_gap)/R - I_gap).  pic_step runs it after the push; the following
  * Poisson solve holds the anode at V_gap.  PIC_E_INVALID without a circuit. */
 int pic_circuit(pic_t *h);
-int pic_deposit(pic_t *h);     /* a7 fixed-point CIC charge deposit of e- and Cu+ */
+int pic_deposit(pic_t *h);     /* a7 fixed-point CIC charge deposit of e-, Cu+ (and Cu2+, charge 2) */
 int pic_solve_field(pic_t *h); /* a7 deposit, a8 Poisson solve, a9 node field */
 int pic_heat(pic_t *h);        /* a10 continuity + heat on the tip cells from the accumulators */
 /* nsteps full steps a1..a10 (heat every n_heat steps); the step counter advances by nsteps. */

@@ -40,7 +40,7 @@ LOTZ_A = 4.5e-14 * 1e-4           # m^2 eV^2
 F32 = np.float32
 # Cu2+ channels (Table colls).  The paper's cross sections are not available; stand-ins of the
 # same Lotz form: direct double ionization of Cu (threshold xi_1 + xi_2) with a tenth of the
-# single-ionization constant (the paper calls these cross sections "fairly small"), and
+# single-ionization constant (Sec. 2.2 expects these cross sections to be small), and
 # ionization of Cu+ with the Lotz constant per electron times the 10 electrons of its 3d shell.
 XI_DOUBLE = C.XI_CU_EV + C.XI2_CU_EV
 LOTZ_A_DOUBLE = LOTZ_A / 10.0

@@ -213,7 +213,7 @@ def push_all(st):
 
 
 def circuit_update(st, alive):
-    """The circuit passage of Sec. 2.3.1: I_gap of the pushed e- and Cu+ still in the domain,
+    """The circuit passage of Sec. 2.3.1: I_gap of the pushed e-, Cu+ and Cu2+ still in the domain,
     then V_gap <- V_gap + dt/C (I_tot - I_gap) with I_tot = (V0 - V_gap)/R."""
     prm = st.prm
     if st.E0 is None:

@@ -1,49 +1,66 @@
 // Monte Carlo collisions: impact ionization Cu + e -> Cu+ + 2e with SP splitting (Sec. 2.2,
 // eq:colp, eq:du, Sec. 2.3.2) and direct field ionization of neutrals (eq:dfi, Sec. 2.3.4);
-// with their flags, elastic e-Cu and Cu-Cu collisions and Cu+-Cu charge exchange (eq:newv,
-// with splitting) and binary Coulomb collisions between charged SPs (Table colls), in the
-// order impact ionization, elastic passes, Coulomb passes, field ionization.
+// with their flags, the Cu2+ channels of Table colls (Cu + e -> Cu2+ + 3e inside the impact
+// ionization pass, then Cu+ + e -> Cu2+ + 2e), elastic e-Cu and Cu-Cu collisions and Cu+-Cu
+// charge exchange (eq:newv, with splitting) and binary Coulomb collisions between charged SPs
+// (Table colls), in the order impact ionization, Cu+ ionization, elastic passes, Coulomb passes,
+// field ionization.
 //
-// Pairing in a cell with N_e electron SPs and N_n neutral SPs: the species with fewer SPs (tie:
+// Pairing in a cell with N_e electron SPs and N_t target SPs: the species with fewer SPs (tie:
 // electrons) is the projectile; projectile k meets target (k + o_c) mod N_t, o_c =
 // floor(U_PAIR(cell, step) N_t).  Each of the w_p sub-particles of a projectile collides iff
 // U_i < P, P = 1 - exp(-u n_t W_t sigma(E0) dt), n_t the target SP density and W_t the paired
-// target's weight in real particles; N_coll is capped at the target weight.
+// target's weight in real particles; N_coll is capped at the target weight.  With the double
+// channel the total cross section sets P_T and a sub-particle ionizes once below
+// P_T sigma_1/sigma_T and twice between that and P_T.
 //
-// Decisions: P is evaluated in float32; any draw within a guard band of P (2^-12 relative to P
-// plus the largest P this relative speed can reach) re-decides the whole pair with P in
-// float64, so every decision equals the float64 decision.
+// Decisions: P is evaluated in float32; any draw within a guard band of a threshold (2^-12
+// relative to it plus the largest value this relative speed can reach) re-decides the whole
+// pair in float64, so every decision equals the float64 decision.
 //
 // Products are written in a fixed order so ids and slots are deterministic: pairs with an
-// electron projectile in cell-sorted electron order, then pairs with a neutral projectile in
-// cell-sorted neutral order; per pair the ion, the scattered electron (when the electron SP
-// is split) and the secondary electron take consecutive ids.
+// electron projectile in cell-sorted electron order, then pairs with a target projectile in
+// cell-sorted target order; per pair the ion, the scattered electron (when the electron SP
+// is split) and the secondary electron take consecutive ids; the double events follow all single
+// ones in the same pair order (Cu2+, scattered electron, two secondary electrons).
 #include "pic_internal.cuh"
 #include "dev_common.cuh"
 
 namespace pic {
 
-constexpr double kLotzA = 4.5e-18;     // m^2 eV^2  (4.5e-14 cm^2 eV^2)
+constexpr double kLotzA = 4.5e-18;     // m^2 eV^2  (4.5e-14 cm^2 eV^2), Cu + e -> Cu+ + 2e
+// Stand-ins of the Cu2+ channels (same Lotz form): double ionization of Cu with a tenth of the
+// single constant at xi_1 + xi_2, and ionization of Cu+ with ten times it (ten 3d electrons) at xi_2
+constexpr double kLotzDouble = 4.5e-19, kXiDouble = 28.018;
+constexpr double kLotzIz = 4.5e-17;
 // The smallest uniform draw, 0.5 * 2^-24.  When P + guard band is below it, no draw can land
 // under P or inside the band, so the decisions (none) are known without drawing.
 constexpr float kUmin = 2.98023223876953125e-8f;
 
-__device__ __forceinline__ double sigma_ion64(double E) {
-  return E > kXiCu ? kLotzA * log(E / kXiCu) / (E * kXiCu) : 0.0;
+__device__ __forceinline__ double lotz64(double E, double xi, double a) {
+  return E > xi ? a * log(E / xi) / (E * xi) : 0.0;
 }
-__device__ __forceinline__ float sigma_ion32(float E) {
-  const float xi = (float)kXiCu;
-  return E > xi ? (float)kLotzA * logf(E / xi) / (E * xi) : 0.0f;
+__device__ __forceinline__ float lotz32(float E, float xi, float a) {
+  return E > xi ? a * logf(E / xi) / (E * xi) : 0.0f;
 }
 
+// One impact-ionization pass: electrons against a heavy target species (Cu, or Cu+ for the Cu+
+// pass) producing an ion of the next charge.
 struct McArgs {
-  SpeciesBuf e, n;
+  SpeciesBuf e, n;                   // electrons and the target species
+  SpeciesBuf prod, j;                // single-channel products; Cu2+ (double channel)
   const uint32_t *off_e, *off_n;     // per-cell offsets of the last sort
   const uint32_t *skey_e, *skey_n;   // cell of each sorted position
   double V_cell, dt, w_min;
+  double xi, lotz;                   // threshold [eV] and Lotz constant [m^2 eV^2] of the single channel
+  float xi32, lotz32, sig_peak;      // the same in FP32; largest sigma_T (a/(e xi^2) summed over channels)
+  uint32_t pur_pair, pur_draw, pur_scat;
+  int sn, sprod;                     // species of the target and of the single products
+  int dbl;                           // the double channel competes (Cu target)
   uint64_t seed;
   DevClock *clk;
   int *go;
+  const uint64_t *total1;            // products kernel: totals of the single products (ions | e << 32)
 };
 
 // ---- ordered compaction of rare events ---------------------------------------------------------
@@ -58,15 +75,20 @@ struct EvBlocks {
   int *hits;        // events per unit
   uint64_t *cnt;    // products per unit: ions | electrons << 32
   uint64_t *off;    // exclusive offsets of cnt
+  uint64_t *cnt2;   // second product kind per unit (double ionization: Cu2+ | electrons << 32)
+  uint64_t *off2;   // exclusive offsets of cnt2
 };
 
 __device__ __forceinline__ int ev_warp() { return (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); }
 __device__ __forceinline__ int ev_nwarp() { return (int)((gridDim.x * blockDim.x) >> 5); }
 
+// Units of work items: mode 0 sorted e- + sorted Cu (impact ionization), 1 all neutrals (DFI),
+// 2 + s sorted species s (elastic passes), 6 sorted e- + sorted Cu+ (Cu+ ionization)
 __global__ void k_ev_units(int64_t *out, const DevClock *clk, int mode) {
-  // mode 0: sorted n_e + sorted n_n (MCC work items), 1: all neutrals (DFI), 2 + s: sorted n_s
-  const int64_t n = mode == 0 ? clk->n_sorted[PIC_ELECTRON] + clk->n_sorted[PIC_NEUTRAL]
-                    : mode == 1 ? clk->n[PIC_NEUTRAL] : clk->n_sorted[mode - 2];
+  const int64_t n = mode == 0   ? clk->n_sorted[PIC_ELECTRON] + clk->n_sorted[PIC_NEUTRAL]
+                    : mode == 1 ? clk->n[PIC_NEUTRAL]
+                    : mode == 6 ? clk->n_sorted[PIC_ELECTRON] + clk->n_sorted[PIC_ION]
+                                : clk->n_sorted[mode - 2];
   *out = (n + kEvUnit - 1) / kEvUnit;
 }
 
@@ -75,6 +97,18 @@ __global__ void k_check_new(DevClock *clk, const uint64_t *total, int64_t cap_i,
   const uint64_t t = *total;
   const int64_t ni = (int64_t)(t & 0xffffffffu), ne = (int64_t)(t >> 32);
   const bool ok = clk->n[PIC_ION] + ni <= cap_i && clk->n[PIC_ELECTRON] + ne <= cap_e;
+  *go = ok ? 1 : 0;
+  if (!ok) atomicOr(&clk->err, kErrCapacity);
+}
+
+// the same for an impact-ionization pass: single products (species sprod | e-) and, with
+// total2, double products (Cu2+ | e-)
+__global__ void k_mcc_check(DevClock *clk, const uint64_t *total1, const uint64_t *total2, int sprod, int64_t cap_p,
+                            int64_t cap_e, int64_t cap_j, int *go) {
+  const uint64_t t = *total1, u = total2 ? *total2 : 0ull;
+  const int64_t np = (int64_t)(t & 0xffffffffu), ne = (int64_t)(t >> 32) + (int64_t)(u >> 32);
+  const int64_t nj = (int64_t)(u & 0xffffffffu) + (sprod == PIC_ION2 ? np : 0);
+  const bool ok = clk->n[sprod] + np <= cap_p && clk->n[PIC_ELECTRON] + ne <= cap_e && clk->n[PIC_ION2] + nj <= cap_j;
   *go = ok ? 1 : 0;
   if (!ok) atomicOr(&clk->err, kErrCapacity);
 }
@@ -120,12 +154,12 @@ __device__ __forceinline__ uint32_t cell_word(uint64_t seed, uint32_t purpose, u
 }
 
 struct Pair {
-  int64_t ie, in;   // electron index, neutral index
+  int64_t ie, in;   // electron index, target index
   int proj_e;       // 1: electron is the projectile
   uint32_t Nt;
 };
 
-// Cell and counts of work item t (t < n_e: electron t; else neutral t - n_e); whether the item is
+// Cell and counts of work item t (t < n_e: electron t; else target t - n_e); whether the item is
 // the projectile of a pair.
 struct McItem {
   uint32_t c, oe, Ne, on, Nn;
@@ -155,9 +189,9 @@ __device__ __forceinline__ Pair mc_pair(const McItem &m, int64_t t, int64_t ne, 
   return pr;
 }
 
-// Sub-particle collisions of one pair (0..min(w_p, w_t)).
-__device__ int mcc_ncoll(const McArgs &a, const Pair &pr, int64_t step) {
-  const float sig_peak = (float)(kLotzA / (2.718281828459045 * kXiCu * kXiCu));
+// Sub-particle collisions of one pair: the single channel's count (0..min(w_p, w_t)) and, with
+// the double channel, *n2 = #{P_1 <= U_i < P_T} capped at what the single ones leave of w_t.
+__device__ int mcc_ncoll(const McArgs &a, const Pair &pr, int64_t step, int *n2) {
   const int we = a.e.w[pr.ie], wn = a.n.w[pr.in];
   const int wp = pr.proj_e ? we : wn, wt = pr.proj_e ? wn : we;
   const float dvx = a.e.vx[pr.ie] - a.n.vx[pr.in];
@@ -167,46 +201,61 @@ __device__ int mcc_ncoll(const McArgs &a, const Pair &pr, int64_t step) {
   const float u = sqrtf(u2);
   const float E0 = (float)(0.5 * kMe / kQe) * u2;
   const float nW = (float)((double)pr.Nt / a.V_cell * (double)wt * a.w_min * a.dt);
-  const float x = u * nW * sigma_ion32(E0);
-  const float P32 = -expm1f(-x);
-  const float band = ldexpf(P32 + u * nW * sig_peak, -12);
+  const float s1 = lotz32(E0, a.xi32, a.lotz32);
+  const float sT = a.dbl ? s1 + lotz32(E0, (float)kXiDouble, (float)kLotzDouble) : s1;
+  const float PT = -expm1f(-(u * nW * sT));
+  const float P1 = a.dbl ? (sT > 0.0f ? PT * (s1 / sT) : 0.0f) : PT;
+  const float reach = u * nW * a.sig_peak;
+  const float band1 = ldexpf(P1 + reach, -12), bandT = ldexpf(PT + reach, -12);
   const uint64_t pid = pr.proj_e ? a.e.id[pr.ie] : a.n.id[pr.in];
-  int ncoll = 0;
+  int c1 = 0, c2 = 0;
   bool exact = false;
-  for (int i = 0; i < wp && P32 + band >= kUmin; i += 4) {
-    const U4 r = rng_block(a.seed, kIon, pid, step, (uint32_t)(i >> 2));
+  for (int i = 0; i < wp && PT + bandT >= kUmin; i += 4) {
+    const U4 r = rng_block(a.seed, a.pur_draw, pid, step, (uint32_t)(i >> 2));
     for (int j = 0; j < 4 && i + j < wp; ++j) {
       const float U = u01f(r.v[j]);
-      if (fabsf(U - P32) <= band) exact = true;
-      ncoll += U < P32;
+      if (fabsf(U - P1) <= band1 || (a.dbl && fabsf(U - PT) <= bandT)) exact = true;
+      c1 += U < P1;
+      c2 += U >= P1 && U < PT;
     }
   }
-  if (exact) {
+  if (exact) {   // the FP64 definition, in the oracle's order of operations
     const double ex = (double)a.e.vx[pr.ie] - (double)a.n.vx[pr.in];
     const double ey = (double)a.e.vy[pr.ie] - (double)a.n.vy[pr.in];
     const double ez = (double)a.e.vz[pr.ie] - (double)a.n.vz[pr.in];
     const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)), __dmul_rn(ez, ez));
     const double ud = sqrt(d2);
     const double E0d = 0.5 * kMe * d2 / kQe;
-    const double xd = ud * ((double)pr.Nt / a.V_cell) * ((double)wt * a.w_min) * sigma_ion64(E0d) * a.dt;
-    const double P64 = -expm1(-xd);
-    ncoll = 0;
+    const double s1d = lotz64(E0d, a.xi, a.lotz);
+    const double sTd = a.dbl ? s1d + lotz64(E0d, kXiDouble, kLotzDouble) : s1d;
+    const double PTd = -expm1(-(ud * ((double)pr.Nt / a.V_cell) * ((double)wt * a.w_min) * sTd * a.dt));
+    const double P1d = sTd > 0.0 ? PTd * (s1d / sTd) : 0.0;
+    c1 = 0;
+    c2 = 0;
     for (int i = 0; i < wp; i += 4) {
-      const U4 r = rng_block(a.seed, kIon, pid, step, (uint32_t)(i >> 2));
-      for (int j = 0; j < 4 && i + j < wp; ++j) ncoll += u01d(r.v[j]) < P64;
+      const U4 r = rng_block(a.seed, a.pur_draw, pid, step, (uint32_t)(i >> 2));
+      for (int j = 0; j < 4 && i + j < wp; ++j) {
+        const double U = u01d(r.v[j]);
+        c1 += U < P1d;
+        c2 += U >= P1d && U < PTd;
+      }
     }
   }
-  return ncoll > wt ? wt : ncoll;
+  c1 = c1 > wt ? wt : c1;
+  if (n2) *n2 = a.dbl ? (c2 > wt - c1 ? wt - c1 : c2) : 0;
+  return c1;
 }
 
-// Work items: sorted electrons, then sorted neutrals; events staged with payload ncoll.  A warp
-// takes a unit of kEvUnit items in two passes: the first finds the unit's projectiles (the items
-// of the species with fewer SPs in their cell) and queues their pairs in shared memory in item
-// order; the second evaluates the queued pairs 32 at a time, so every lane works on a pair (the
-// projectiles are a fraction of the items, and evaluating them in place left most lanes idle).
+// Work items: sorted electrons, then sorted targets; a pair with an event is staged with payload
+// n1 (with the double channel: n1 | bit 31, so pairs with only double events are staged too).  A
+// warp takes a unit of kEvUnit items in two passes: the first finds the unit's projectiles (the
+// items of the species with fewer SPs in their cell) and queues their pairs in shared memory in
+// item order; the second evaluates the queued pairs 32 at a time, so every lane works on a pair
+// (the projectiles are a fraction of the items, and evaluating them in place left most lanes
+// idle).
 struct McQueued {
   uint32_t t;        // work item
-  uint32_t ie, in;   // electron and neutral of the pair
+  uint32_t ie, in;   // electron and target of the pair
   uint32_t nt;       // target SPs in the cell; bit 31: the electron is the projectile
 };
 
@@ -214,7 +263,7 @@ __global__ void __launch_bounds__(256) k_mcc_count(McArgs a, EvBlocks ev) {
   __shared__ McQueued queue[256 / 32][kEvUnit];
   McQueued *qw = queue[threadIdx.x >> 5];
   const int lane = threadIdx.x & 31;
-  const int64_t ne = a.clk->n_sorted[PIC_ELECTRON], nn = a.clk->n_sorted[PIC_NEUTRAL];
+  const int64_t ne = a.clk->n_sorted[PIC_ELECTRON], nn = a.clk->n_sorted[a.sn];
   const int64_t step = a.clk->step;
   const int64_t total = ne + nn, nunit = (total + kEvUnit - 1) / kEvUnit;
   for (int64_t unit = ev_warp(); unit < nunit; unit += ev_nwarp()) {
@@ -224,7 +273,7 @@ __global__ void __launch_bounds__(256) k_mcc_count(McArgs a, EvBlocks ev) {
       const int64_t t = base + lane;
       McItem m{};
       if (t < hi) m = mc_item(a, t, ne);
-      const uint32_t w = cell_word(a.seed, kPair, m.c, m.proj, step);
+      const uint32_t w = cell_word(a.seed, a.pur_pair, m.c, m.proj, step);
       const unsigned bal = __ballot_sync(0xffffffffu, m.proj);
       if (m.proj) {
         const Pair pr = mc_pair(m, t, ne, w);
@@ -239,11 +288,11 @@ __global__ void __launch_bounds__(256) k_mcc_count(McArgs a, EvBlocks ev) {
     }
     __syncwarp();
     int64_t run = 0;
-    uint64_t prod = 0;
+    uint64_t prod = 0, prod2 = 0;
     for (int b = 0; b < nq; b += 32) {
       const int i = b + lane;
-      int ncoll = 0;
-      uint64_t pc = 0;
+      int ncoll = 0, n2 = 0;
+      uint64_t pc = 0, pc2 = 0;
       int64_t t = lo;
       if (i < nq) {
         const McQueued e = qw[i];
@@ -253,15 +302,24 @@ __global__ void __launch_bounds__(256) k_mcc_count(McArgs a, EvBlocks ev) {
         pr.proj_e = (e.nt >> 31) & 1;
         pr.Nt = e.nt & 0x7fffffffu;
         t = lo + e.t;
-        ncoll = mcc_ncoll(a, pr, step);
-        if (ncoll > 0) pc = 1ull | ((uint64_t)(ncoll < a.e.w[pr.ie] ? 2 : 1) << 32);
+        ncoll = mcc_ncoll(a, pr, step, &n2);
+        const int we = a.e.w[pr.ie];
+        if (ncoll > 0) pc = 1ull | ((uint64_t)(ncoll < we ? 2 : 1) << 32);
+        if (n2 > 0) pc2 = 1ull | ((uint64_t)(n2 < we - ncoll ? 3 : 2) << 32);
       }
-      ev_stage(ev, lo, &run, &prod, t, (uint32_t)ncoll, pc);
+      const uint32_t payload = a.dbl ? ((ncoll > 0 || n2 > 0) ? (0x80000000u | (uint32_t)ncoll) : 0u) : (uint32_t)ncoll;
+      ev_stage(ev, lo, &run, &prod, t, payload, pc);
+      if (a.dbl && __any_sync(0xffffffffu, pc2 != 0)) {
+        uint64_t t2;
+        warp_scan_u64(pc2, &t2);
+        prod2 += t2;
+      }
     }
     __syncwarp();
     if (lane == 0) {
       ev.hits[unit] = (int)run;
       ev.cnt[unit] = prod;
+      if (a.dbl) ev.cnt2[unit] = prod2;
     }
   }
 }
@@ -299,64 +357,118 @@ __global__ void k_commit_new(DevClock *clk, const uint64_t *total, const int *go
   clk->ctr[ctr] += ni;
 }
 
-// Products of the staged pairs, warp by warp in item order from the warp's offset.
-__global__ void __launch_bounds__(256) k_mcc_products(McArgs a, EvBlocks ev, SpeciesBuf ions) {
+// commit of an impact-ionization pass: single products (one ion per event) and double ones
+__global__ void k_mcc_commit(DevClock *clk, const uint64_t *total1, const uint64_t *total2, const int *go, int sprod,
+                             int ctr) {
+  if (!*go) return;
+  const uint64_t t = *total1, u = total2 ? *total2 : 0ull;
+  const int64_t np = (int64_t)(t & 0xffffffffu), ne = (int64_t)(t >> 32);
+  const int64_t nj = (int64_t)(u & 0xffffffffu), ne2 = (int64_t)(u >> 32);
+  clk->n[sprod] += np;
+  clk->n[PIC_ELECTRON] += ne + ne2;
+  clk->n[PIC_ION2] += nj;
+  clk->next_id += np + ne + nj + ne2;
+  clk->ctr[ctr] += np;
+  clk->ctr[cDoubleIon] += nj;
+}
+
+// Products of the staged pairs, warp by warp in item order from the warp's offsets.  Each
+// thread's pair is its own (an SP belongs to one pair of a pass), so the pre-collision weights
+// and velocities it reads are untouched until it writes them.
+__global__ void __launch_bounds__(256) k_mcc_products(McArgs a, EvBlocks ev) {
   if (!*a.go) return;
-  const int64_t ne = a.clk->n_sorted[PIC_ELECTRON], nn = a.clk->n_sorted[PIC_NEUTRAL];
-  const int64_t ne_all = a.clk->n[PIC_ELECTRON], ni = a.clk->n[PIC_ION];
+  const int64_t ne = a.clk->n_sorted[PIC_ELECTRON], nn = a.clk->n_sorted[a.sn];
+  const int64_t ne_all = a.clk->n[PIC_ELECTRON], np_all = a.clk->n[a.sprod], nj_all = a.clk->n[PIC_ION2];
   const int64_t step = a.clk->step, id_base = a.clk->next_id;
+  const uint64_t t1 = *a.total1;
+  const int64_t single_e = (int64_t)(t1 >> 32), single_all = (int64_t)(t1 & 0xffffffffu) + single_e;
   const int64_t nunit = (ne + nn + kEvUnit - 1) / kEvUnit;
   for (int64_t unit = ev_warp(); unit < nunit; unit += ev_nwarp()) {
     const int64_t lo = unit * kEvUnit;
     const int nh = ev.hits[unit];
-    uint64_t run = ev.off[unit];
+    uint64_t run = ev.off[unit], run2 = a.dbl ? ev.off2[unit] : 0ull;
     for (int base = 0; base < nh; base += 32) {
       const int i = base + (threadIdx.x & 31);
       Pair pr{};
-      int ncoll = 0;
-      uint64_t pc = 0;
+      int ncoll = 0, n2 = 0, we = 0;
+      uint64_t pc = 0, pc2 = 0;
       if (i < nh) {
         const uint64_t rec = ev.rec[lo + i];
         const int64_t t = (int64_t)(uint32_t)rec;
-        ncoll = (int)(rec >> 32);
+        ncoll = (int)((rec >> 32) & 0x7fffffffu);
         const McItem m = mc_item(a, t, ne);
-        pr = mc_pair(m, t, ne, rng_block(a.seed, kPair, m.c, step, 0).v[0]);
-        pc = 1ull | ((uint64_t)(ncoll < a.e.w[pr.ie] ? 2 : 1) << 32);
+        pr = mc_pair(m, t, ne, rng_block(a.seed, a.pur_pair, m.c, step, 0).v[0]);
+        if (a.dbl) mcc_ncoll(a, pr, step, &n2);
+        we = a.e.w[pr.ie];
+        if (ncoll > 0) pc = 1ull | ((uint64_t)(ncoll < we ? 2 : 1) << 32);
+        if (n2 > 0) pc2 = 1ull | ((uint64_t)(n2 < we - ncoll ? 3 : 2) << 32);
       }
       uint64_t tile;
       const uint64_t off = run + warp_scan_u64(pc, &tile);
       run += tile;
+      uint64_t off2 = 0;
+      if (a.dbl) {
+        off2 = run2 + warp_scan_u64(pc2, &tile);
+        run2 += tile;
+      }
       if (i >= nh) continue;
-      const int64_t ion_off = (int64_t)(off & 0xffffffffu), e_off = (int64_t)(off >> 32);
-      int64_t id = id_base + ion_off + e_off;
       const int64_t in = pr.in, ie = pr.ie;
+      const int wn = a.n.w[in];
       const uint64_t pid = pr.proj_e ? a.e.id[ie] : a.n.id[in];
-      // ion with the neutral's position and velocity
-      put_sp(ions, ni + ion_off, a.n.x[in], a.n.y[in], a.n.z[in], a.n.vx[in], a.n.vy[in], a.n.vz[in], ncoll,
-             (uint64_t)id++);
-      a.n.w[in] -= ncoll;
-      // outgoing electrons: (E0 - xi)/2 each, directions by eq:du about u = v_e - v_n
       const double vnx = a.n.vx[in], vny = a.n.vy[in], vnz = a.n.vz[in];
       const double ux = (double)a.e.vx[ie] - vnx, uy = (double)a.e.vy[ie] - vny, uz = (double)a.e.vz[ie] - vnz;
       const double u2 = __dadd_rn(__dadd_rn(__dmul_rn(ux, ux), __dmul_rn(uy, uy)), __dmul_rn(uz, uz));
       const double E0 = 0.5 * kMe * u2 / kQe;
-      const double Ek = 0.5 * (E0 - kXiCu);
-      const double uk = sqrt(2.0 * Ek * kQe / kMe);
-      const U4 r = rng_block(a.seed, kScat, pid, step, 0);
-      double v1[3], v2[3];
-      scatter_velocity(ux, uy, uz, uk, 2.0 * u01d(r.v[0]) - 1.0, 2.0 * kPi * u01d(r.v[1]), v1);
-      scatter_velocity(ux, uy, uz, uk, 2.0 * u01d(r.v[2]) - 1.0, 2.0 * kPi * u01d(r.v[3]), v2);
-      const int we = a.e.w[ie];
-      int64_t slot = ne_all + e_off;
-      if (ncoll == we) {
-        a.e.vx[ie] = (float)(vnx + v1[0]); a.e.vy[ie] = (float)(vny + v1[1]); a.e.vz[ie] = (float)(vnz + v1[2]);
-      } else {
-        a.e.w[ie] = we - ncoll;
-        put_sp(a.e, slot++, a.e.x[ie], a.e.y[ie], a.e.z[ie], (float)(vnx + v1[0]), (float)(vny + v1[1]),
-               (float)(vnz + v1[2]), ncoll, (uint64_t)id++);
+      const float tx = a.n.x[in], ty = a.n.y[in], tz = a.n.z[in];
+      const float tvx = a.n.vx[in], tvy = a.n.vy[in], tvz = a.n.vz[in];
+      if (ncoll > 0) {
+        const int64_t ion_off = (int64_t)(off & 0xffffffffu), e_off = (int64_t)(off >> 32);
+        int64_t id = id_base + ion_off + e_off;
+        // ion of the next charge with the target's position and velocity
+        put_sp(a.prod, np_all + ion_off, tx, ty, tz, tvx, tvy, tvz, ncoll, (uint64_t)id++);
+        // outgoing electrons: (E0 - xi)/2 each, directions by eq:du about u = v_e - v_t
+        const double Ek = 0.5 * (E0 - a.xi);
+        const double uk = sqrt(2.0 * Ek * kQe / kMe);
+        const U4 r = rng_block(a.seed, a.pur_scat, pid, step, 0);
+        double v1[3], v2[3];
+        scatter_velocity(ux, uy, uz, uk, 2.0 * u01d(r.v[0]) - 1.0, 2.0 * kPi * u01d(r.v[1]), v1);
+        scatter_velocity(ux, uy, uz, uk, 2.0 * u01d(r.v[2]) - 1.0, 2.0 * kPi * u01d(r.v[3]), v2);
+        int64_t slot = ne_all + e_off;
+        if (ncoll == we) {
+          a.e.vx[ie] = (float)(vnx + v1[0]); a.e.vy[ie] = (float)(vny + v1[1]); a.e.vz[ie] = (float)(vnz + v1[2]);
+        } else {
+          put_sp(a.e, slot++, a.e.x[ie], a.e.y[ie], a.e.z[ie], (float)(vnx + v1[0]), (float)(vny + v1[1]),
+                 (float)(vnz + v1[2]), ncoll, (uint64_t)id++);
+        }
+        put_sp(a.e, slot, tx, ty, tz, (float)(vnx + v2[0]), (float)(vny + v2[1]), (float)(vnz + v2[2]), ncoll, (uint64_t)id);
       }
-      put_sp(a.e, slot, a.n.x[in], a.n.y[in], a.n.z[in], (float)(vnx + v2[0]), (float)(vny + v2[1]), (float)(vnz + v2[2]),
-             ncoll, (uint64_t)id);
+      if (n2 > 0) {
+        // Cu2+ and three outgoing electrons of (E0 - xi_1 - xi_2)/3 each, after every single product
+        const int64_t j_off = (int64_t)(off2 & 0xffffffffu), e_off = (int64_t)(off2 >> 32);
+        int64_t id = id_base + single_all + j_off + e_off;
+        put_sp(a.j, nj_all + j_off, tx, ty, tz, tvx, tvy, tvz, n2, (uint64_t)id++);
+        const double uk = sqrt(2.0 * (E0 - kXiDouble) / 3.0 * kQe / kMe);
+        const U4 r0 = rng_block(a.seed, kScat2, pid, step, 0), r1 = rng_block(a.seed, kScat2, pid, step, 1);
+        double v[3][3];
+        scatter_velocity(ux, uy, uz, uk, 2.0 * u01d(r0.v[0]) - 1.0, 2.0 * kPi * u01d(r0.v[1]), v[0]);
+        scatter_velocity(ux, uy, uz, uk, 2.0 * u01d(r0.v[2]) - 1.0, 2.0 * kPi * u01d(r0.v[3]), v[1]);
+        scatter_velocity(ux, uy, uz, uk, 2.0 * u01d(r1.v[0]) - 1.0, 2.0 * kPi * u01d(r1.v[1]), v[2]);
+        const int we1 = we - ncoll;   // the electron SP's weight after the single channel
+        int64_t slot = ne_all + single_e + e_off;
+        if (n2 == we1) {
+          a.e.vx[ie] = (float)(vnx + v[0][0]); a.e.vy[ie] = (float)(vny + v[0][1]); a.e.vz[ie] = (float)(vnz + v[0][2]);
+        } else {
+          put_sp(a.e, slot++, a.e.x[ie], a.e.y[ie], a.e.z[ie], (float)(vnx + v[0][0]), (float)(vny + v[0][1]),
+                 (float)(vnz + v[0][2]), n2, (uint64_t)id++);
+        }
+        for (int q = 1; q < 3; ++q)
+          put_sp(a.e, slot++, tx, ty, tz, (float)(vnx + v[q][0]), (float)(vny + v[q][1]), (float)(vnz + v[q][2]), n2,
+                 (uint64_t)id++);
+      }
+      // weights last: the electron keeps we - n1 - n2 unless it turned whole, the target loses n1 + n2
+      if (ncoll > 0 && ncoll < we) a.e.w[ie] = we - ncoll - (n2 > 0 && n2 < we - ncoll ? n2 : 0);
+      else if (ncoll == 0 && n2 > 0 && n2 < we) a.e.w[ie] = we - n2;
+      a.n.w[in] = wn - ncoll - n2;
     }
   }
 }
@@ -840,22 +952,41 @@ int stage_collide(pic_t *h) {
   uint64_t *total = (uint64_t *)(h->tmp_len + 2);
   const int grid = h->nsm * 8;
   // events of the count kernels are staged per unit of 256 work items in the collision scratch
-  const EvBlocks ev{h->pair_cnt, h->ev_hits, h->ev_cnt, h->ev_off};
-  if (fl & PIC_F_IMPACT_ION) {
-    McArgs a;
-    const Species &E = h->sp[PIC_ELECTRON], &N = h->sp[PIC_NEUTRAL];
-    a.e = E.a; a.n = N.a;
+  const EvBlocks ev{h->pair_cnt, h->ev_hits, h->ev_cnt, h->ev_off, h->ev_cnt2, h->ev_off2};
+  const bool ion2 = nsp_active(h) > PIC_ION2;
+  uint64_t *total2 = (uint64_t *)(h->tmp_len + 3);
+  // one impact-ionization pass: electrons on the target species sn, products of species sprod
+  auto mcc_pass = [&](int sn, int sprod, double xi, double lotz, uint32_t pp, uint32_t pd, uint32_t ps, int dbl,
+                      int ctr, int units_mode, int kid_count, int kid_products) -> int {
+    McArgs a{};
+    const Species &E = h->sp[PIC_ELECTRON], &N = h->sp[sn];
+    a.e = E.a; a.n = N.a; a.prod = h->sp[sprod].a; a.j = h->sp[PIC_ION2].a;
     a.off_e = E.off; a.off_n = N.off; a.skey_e = E.skey; a.skey_n = N.skey;
     a.V_cell = h->dx * h->dx * h->dx; a.dt = h->prm.dt; a.w_min = h->prm.w_min; a.seed = h->prm.seed;
-    a.clk = h->clock; a.go = go;
+    a.xi = xi; a.lotz = lotz; a.xi32 = (float)xi; a.lotz32 = (float)lotz;
+    double peak = lotz / (2.718281828459045 * xi * xi);
+    if (dbl) peak += kLotzDouble / (2.718281828459045 * kXiDouble * kXiDouble);
+    a.sig_peak = (float)peak;
+    a.pur_pair = pp; a.pur_draw = pd; a.pur_scat = ps;
+    a.sn = sn; a.sprod = sprod; a.dbl = dbl;
+    a.clk = h->clock; a.go = go; a.total1 = total;
     h->nlaunch += 4;
-    { KtScope kt_(h, kidMccCount, 0); k_mcc_count<<<grid, 256, 0, h->stream>>>(a, ev); }
-    k_ev_units<<<1, 1, 0, h->stream>>>(h->tmp_len, h->clock, 0);
+    { KtScope kt_(h, kid_count, 0); k_mcc_count<<<grid, 256, 0, h->stream>>>(a, ev); }
+    k_ev_units<<<1, 1, 0, h->stream>>>(h->tmp_len, h->clock, units_mode);
     PIC_TRY(scan_u64(h, ev.cnt, ev.off, 0, h->tmp_len, total));
-    k_check_new<<<1, 1, 0, h->stream>>>(h->clock, total, h->sp[PIC_ION].cap, E.cap, go);
-    { KtScope kt_(h, kidMccProducts, 0); k_mcc_products<<<grid, 256, 0, h->stream>>>(a, ev, h->sp[PIC_ION].a); }
-    k_commit_new<<<1, 1, 0, h->stream>>>(h->clock, total, go, cImpactIon);
-    PIC_TRY(launch_check(h, "mcc"));
+    if (dbl) PIC_TRY(scan_u64(h, ev.cnt2, ev.off2, 0, h->tmp_len, total2));
+    k_mcc_check<<<1, 1, 0, h->stream>>>(h->clock, total, dbl ? total2 : nullptr, sprod, h->sp[sprod].cap, E.cap,
+                                        h->sp[PIC_ION2].cap, go);
+    { KtScope kt_(h, kid_products, 0); k_mcc_products<<<grid, 256, 0, h->stream>>>(a, ev); }
+    k_mcc_commit<<<1, 1, 0, h->stream>>>(h->clock, total, dbl ? total2 : nullptr, go, sprod, ctr);
+    return launch_check(h, "mcc");
+  };
+  if (fl & PIC_F_IMPACT_ION) {
+    PIC_TRY(mcc_pass(PIC_NEUTRAL, PIC_ION, kXiCu, kLotzA, kPair, kIon, kScat, ion2 ? 1 : 0, cImpactIon, 0, kidMccCount,
+                     kidMccProducts));
+    if (ion2)   // Cu+ + e -> Cu2+ + 2e on the Cu+ as the single pass left them
+      PIC_TRY(mcc_pass(PIC_ION, PIC_ION2, kXi2Cu, kLotzIz, kPairIz, kIonIz, kScatIz, 0, cIonIon, 6, kidMccCount,
+                       kidMccProducts));
   }
   if (fl & PIC_F_ELASTIC) {
     ElArgs a{};
@@ -912,6 +1043,17 @@ int stage_collide(pic_t *h) {
       k_coulomb<<<grid, 256, 0, h->stream>>>(ee, h->prm.seed, h->clock, cCoulombEe);
       k_coulomb<<<grid, 256, 0, h->stream>>>(ei, h->prm.seed, h->clock, cCoulombEi);
       k_coulomb<<<grid, 256, 0, h->stream>>>(ii, h->prm.seed, h->clock, cCoulombIi);
+    }
+    if (ion2) {   // with Cu2+: e-Cu2+, Cu+-Cu2+, Cu2+-Cu2+ (Sec. 2.2: between all charged species)
+      const Species &J = h->sp[PIC_ION2];
+      const CoPass ej = pass(E, PIC_ELECTRON, J, PIC_ION2, kQe, 2.0 * kQe, kPairEj, kDrawEj, 0);
+      const CoPass ij = pass(I, PIC_ION, J, PIC_ION2, kQe, 2.0 * kQe, kPairIj, kDrawIj, 0);
+      const CoPass jj = pass(J, PIC_ION2, J, PIC_ION2, 2.0 * kQe, 2.0 * kQe, kPairJj, kDrawJj, 1);
+      h->nlaunch += 3;
+      KtScope kt_(h, kidCoulomb, 0);
+      k_coulomb<<<grid, 256, 0, h->stream>>>(ej, h->prm.seed, h->clock, cCoulombEj);
+      k_coulomb<<<grid, 256, 0, h->stream>>>(ij, h->prm.seed, h->clock, cCoulombIj);
+      k_coulomb<<<grid, 256, 0, h->stream>>>(jj, h->prm.seed, h->clock, cCoulombJj);
     }
     PIC_TRY(launch_check(h, "coulomb"));
   }

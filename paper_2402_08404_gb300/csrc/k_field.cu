@@ -573,16 +573,18 @@ __global__ void k_unit_field(const long long *phi, float4 *E0, int nx, int ny, i
 // partial sums in FP64 over a fixed grid of kRamoBlocks blocks (enough warps in flight to cover
 // the gather latency on every SM), so the summation order, and with it every bit of the result,
 // does not depend on anything but the SP order.
-__global__ void __launch_bounds__(256) k_ramo_partial(SpeciesBuf e, SpeciesBuf ion, const uint32_t *key_e,
-                                                      const uint32_t *key_i, const float4 *E0, int nx, int ny,
+// Species in the order e-, Cu+, Cu2+ (nsp = 2 without Cu2+).
+__global__ void __launch_bounds__(256) k_ramo_partial(SpeciesBuf e, SpeciesBuf ion, SpeciesBuf ion2,
+                                                      const uint32_t *key_e, const uint32_t *key_i,
+                                                      const uint32_t *key_j, int nsp, const float4 *E0, int nx, int ny,
                                                       const DevClock *clk, double qw, double *part) {
   __shared__ double sh[8];
   double acc = 0.0;
-  for (int sp = 0; sp < 2; ++sp) {
-    const SpeciesBuf &p = sp == 0 ? e : ion;
-    const uint32_t *key = sp == 0 ? key_e : key_i;
-    const int64_t n = clk->n[sp == 0 ? PIC_ELECTRON : PIC_ION];
-    const double z = sp == 0 ? -qw : qw;
+  for (int sp = 0; sp < nsp; ++sp) {
+    const SpeciesBuf &p = sp == 0 ? e : (sp == 1 ? ion : ion2);
+    const uint32_t *key = sp == 0 ? key_e : (sp == 1 ? key_i : key_j);
+    const int64_t n = clk->n[sp == 0 ? PIC_ELECTRON : (sp == 1 ? PIC_ION : PIC_ION2)];
+    const double z = sp == 0 ? -qw : (sp == 1 ? qw : 2.0 * qw);
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
       const int32_t w = p.w[i];
       if (w <= 0 || (key && key[i] == kDead)) continue;
@@ -1277,10 +1279,12 @@ int stage_circuit(pic_t *h) {
   // after a push the keys mark the removed SPs; sorted SPs are all in the domain
   const uint32_t *ke = h->keys_valid[PIC_ELECTRON] ? h->sp[PIC_ELECTRON].key : nullptr;
   const uint32_t *ki = h->keys_valid[PIC_ION] ? h->sp[PIC_ION].key : nullptr;
+  const uint32_t *kj = h->keys_valid[PIC_ION2] ? h->sp[PIC_ION2].key : nullptr;
   {
     KtScope kt_(h, kidRamo, 0);
-    k_ramo_partial<<<kRamoBlocks, 256, 0, h->stream>>>(h->sp[PIC_ELECTRON].a, h->sp[PIC_ION].a, ke, ki, h->E0, h->nx,
-                                                       h->ny, h->clock, qw, h->ramo_part);
+    k_ramo_partial<<<kRamoBlocks, 256, 0, h->stream>>>(h->sp[PIC_ELECTRON].a, h->sp[PIC_ION].a, h->sp[PIC_ION2].a, ke, ki,
+                                                       kj, nsp_active(h) > PIC_ION2 ? 3 : 2, h->E0, h->nx, h->ny,
+                                                       h->clock, qw, h->ramo_part);
   }
   k_circuit<<<1, 256, 0, h->stream>>>(h->ramo_part, h->clock, h->V0, h->prm.circuit_R, h->prm.circuit_C, h->prm.dt);
   return launch_check(h, "circuit");

@@ -582,15 +582,15 @@ int stage_push(pic_t *h, bool deposit) {
     KtScope kt_(h, kidPush, 0);
     PIC_CUDA(h, cudaMemsetAsync(h->Q, 0, h->nnode * sizeof(unsigned long long), h->stream));
   }
-  PIC_CUDA(h, cudaMemsetAsync(h->xq_n, 0, 3 * sizeof(int), h->stream));
-  for (int s = 0; s < 3; ++s) {
+  PIC_CUDA(h, cudaMemsetAsync(h->xq_n, 0, PIC_NSPECIES * sizeof(int), h->stream));
+  for (int s = 0; s < nsp_active(h); ++s) {
     Species &S = h->sp[s];
     if (h->keys_valid[s]) PIC_CUDA(h, cudaMemsetAsync(S.cnt, 0, (h->ncell + 1) * sizeof(uint32_t), h->stream));
     PushArgs a;
     a.p = S.a; a.key = S.key; a.cnt = S.cnt; a.E = h->E; a.solid = h->solid; a.cheb = h->cheb;
     a.nx = h->nx; a.ny = h->ny; a.nz = h->nz; a.qmdt = S.qmdt;
     a.dtdx = (float)(h->prm.dt / h->dx);
-    a.charged = S.Z != 0; a.ion = s == PIC_ION; a.species = s;
+    a.charged = S.Z != 0; a.ion = s == PIC_ION || s == PIC_ION2; a.species = s;
     a.mass = S.mass; a.w_min = h->prm.w_min;
     a.face_key = h->faces.key; a.nface = h->faces.n;
     a.acc_sput = (unsigned long long *)h->faces.acc_sput; a.acc_Eb = (unsigned long long *)h->faces.acc_Eb;
@@ -674,12 +674,13 @@ __global__ void __launch_bounds__(256) k_merge(SpeciesBuf p, const uint32_t *off
 
 int stage_merge(pic_t *h, bool fix_charge) {
   if (!(h->prm.flags & PIC_F_MERGE)) return PIC_OK;
-  for (int s = 0; s < 3; ++s) if (h->keys_valid[s]) return pic_fail(h, PIC_E_INVALID, "merging needs cell-sorted SPs");
+  const int ns = nsp_active(h);
+  for (int s = 0; s < ns; ++s) if (h->keys_valid[s]) return pic_fail(h, PIC_E_INVALID, "merging needs cell-sorted SPs");
   const uint32_t M = h->prm.merge_max > 0 ? (uint32_t)h->prm.merge_max : 32u;
   const int32_t wmax = h->prm.w_max_units > 0 ? h->prm.w_max_units : INT32_MAX;
-  h->nlaunch += 3;
+  h->nlaunch += ns;
   KtScope kt_(h, kidMerge, 0);
-  for (int s = 0; s < 3; ++s)
+  for (int s = 0; s < ns; ++s)
     k_merge<<<h->nsm * 8, kThreads, 0, h->stream>>>(h->sp[s].a, h->sp[s].off, h->sp[s].skey, s, M, wmax, h->clock,
                                                     fix_charge && h->sp[s].Z != 0 ? h->Q : nullptr, h->sp[s].Z,
                                                     h->nx, h->ny);
@@ -742,7 +743,7 @@ int sort_species(pic_t *h, int s) {
 }
 
 int stage_sort(pic_t *h) {
-  for (int s = 0; s < 3; ++s) PIC_TRY(sort_species(h, s));
+  for (int s = 0; s < nsp_active(h); ++s) PIC_TRY(sort_species(h, s));
   return PIC_OK;
 }
 
@@ -753,6 +754,11 @@ int stage_deposit(pic_t *h) {
                                                           PIC_ELECTRON); }
   ++h->nlaunch;
   { KtScope kt_(h, kidDeposit, 0); k_deposit<<<particle_grid(h), kThreads, 0, h->stream>>>(h->sp[PIC_ION].a, 1, h->Q, h->nx, h->ny, h->clock, PIC_ION); }
+  if (nsp_active(h) > PIC_ION2) {
+    ++h->nlaunch;
+    KtScope kt_(h, kidDeposit, 0);
+    k_deposit<<<particle_grid(h), kThreads, 0, h->stream>>>(h->sp[PIC_ION2].a, 2, h->Q, h->nx, h->ny, h->clock, PIC_ION2);
+  }
   return launch_check(h, "deposit");
 }
 

@@ -256,7 +256,7 @@ struct InjArgs {
   const double *Tvox;
   double T0, A, dt, w_min, V_cell;
   int w_max;
-  const uint32_t *off_e, *off_n, *off_i;
+  const uint32_t *off_e, *off_n, *off_i, *off_j;   // off_j: null without Cu2+
   double *acc_evap, *acc_heat;
   long long *acc_sput;
   uint32_t *cnt, *wu, *cnt2, *wu2;
@@ -268,7 +268,8 @@ __global__ void k_inject_count(InjArgs a) {
     const int v = a.owner_vox[f];
     const double T = v >= 0 ? a.Tvox[v] : a.T0;
     const int32_t c = a.vcell[f];
-    const double nsp = (double)((a.off_e[c + 1] - a.off_e[c]) + (a.off_n[c + 1] - a.off_n[c]) + (a.off_i[c + 1] - a.off_i[c]));
+    const double nsp = (double)((a.off_e[c + 1] - a.off_e[c]) + (a.off_n[c + 1] - a.off_n[c]) + (a.off_i[c + 1] - a.off_i[c]) +
+                                (a.off_j ? a.off_j[c + 1] - a.off_j[c] : 0u));
     const double ncell = nsp / a.V_cell;
     uint32_t n1 = 0, w1 = 0, n2 = 0, w2 = 0;
     if (a.evap) {
@@ -485,6 +486,7 @@ int stage_inject(pic_t *h) {
   a.Tvox = h->heat.T; a.T0 = h->prm.T0; a.A = h->dx * h->dx; a.dt = h->prm.dt; a.w_min = h->prm.w_min;
   a.V_cell = h->dx * h->dx * h->dx; a.w_max = h->prm.w_max_units;
   a.off_e = h->sp[PIC_ELECTRON].off; a.off_n = h->sp[PIC_NEUTRAL].off; a.off_i = h->sp[PIC_ION].off;
+  a.off_j = nsp_active(h) > PIC_ION2 ? h->sp[PIC_ION2].off : nullptr;
   a.acc_evap = fc.acc_evap; a.acc_heat = fc.acc_heat; a.acc_sput = (long long *)fc.acc_sput;
   a.cnt = fc.cnt; a.wu = fc.wu; a.cnt2 = fc.cnt2; a.wu2 = fc.wu2;
   a.evap = (fl & PIC_F_EVAP) != 0; a.sput = (fl & PIC_F_SPUTTER) != 0;

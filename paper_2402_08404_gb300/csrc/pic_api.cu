@@ -305,7 +305,8 @@ __global__ void k_phi_to_double(const long long *phi, double *dst, int64_t n) {
 int pic_create(const pic_geometry_t *geometry, const pic_grid_t *grid, const pic_species_t *species, int nspecies,
                const pic_params_t *params, pic_alloc_fn alloc, pic_free_fn free_fn, void *alloc_user, void *stream,
                pic_t **out) {
-  if (!geometry || !grid || !species || !params || !out || nspecies != PIC_NSPECIES) return PIC_E_INVALID;
+  if (!geometry || !grid || !species || !params || !out || (nspecies != 3 && nspecies != PIC_NSPECIES))
+    return PIC_E_INVALID;
   *out = nullptr;
   if (grid->nx < 8 || grid->ny < 8 || grid->nz < 8 || (grid->nx & 1) || (grid->ny & 1) || (grid->nz & 1) || !(grid->dx > 0))
     return PIC_E_INVALID;
@@ -313,8 +314,12 @@ int pic_create(const pic_geometry_t *geometry, const pic_grid_t *grid, const pic
   // node arrays and the split-colour levels ((nx + 2) slots per row pair) are indexed in 32 bits
   if ((int64_t)(grid->nx + 2) * (grid->ny + 1) * (grid->nz + 1) >= (int64_t)0xFFFFFFFFu) return PIC_E_INVALID;
   if (!(params->dt > 0) || !(params->w_min > 0) || params->w_max_units < 1) return PIC_E_INVALID;
-  for (int s = 0; s < 3; ++s)
-    if (species[s].capacity < 1 || species[s].capacity > 0x7FFFFFFF || !(species[s].mass > 0)) return PIC_E_INVALID;
+  // three species given: Cu2+ takes Cu+'s mass, charge 2 and room for one SP
+  pic_species_t spc[PIC_NSPECIES];
+  for (int s = 0; s < nspecies; ++s) spc[s] = species[s];
+  if (nspecies == 3) { spc[PIC_ION2] = species[PIC_ION]; spc[PIC_ION2].charge_e = 2; spc[PIC_ION2].capacity = 1; }
+  for (int s = 0; s < PIC_NSPECIES; ++s)
+    if (spc[s].capacity < 1 || spc[s].capacity > 0x7FFFFFFF || !(spc[s].mass > 0)) return PIC_E_INVALID;
   pic_t *h = new pic_t();
   h->nx = grid->nx; h->ny = grid->ny; h->nz = grid->nz; h->dx = grid->dx;
   h->ncell = (int64_t)h->nx * h->ny * h->nz;
@@ -378,11 +383,11 @@ int pic_create(const pic_geometry_t *geometry, const pic_grid_t *grid, const pic
   }
   // species
   int64_t capsum = 0;
-  for (int s = 0; s < 3; ++s) {
+  for (int s = 0; s < PIC_NSPECIES; ++s) {
     Species &S = h->sp[s];
-    S.Z = species[s].charge_e;
-    S.mass = species[s].mass;
-    S.cap = species[s].capacity;
+    S.Z = spc[s].charge_e;
+    S.mass = spc[s].mass;
+    S.cap = spc[s].capacity;
     S.qmdt = (float)((double)S.Z * kQe / S.mass * h->prm.dt);
     for (SpeciesBuf *B : {&S.a, &S.b}) {
       B->x = alloc_n<float>(h, S.cap); A(B->x);
@@ -399,15 +404,16 @@ int pic_create(const pic_geometry_t *geometry, const pic_grid_t *grid, const pic
     S.skey = alloc_n<uint32_t>(h, S.cap); A(S.skey);
     S.cnt = alloc_n<uint32_t>(h, h->ncell + 1); A(S.cnt);
     S.off = alloc_n<uint32_t>(h, h->ncell + 1); A(S.off);
-    if (s != PIC_ION) capsum += S.cap;
   }
-  // one staging slot per collision work item: impact ionization takes e- + Cu, field ionization
-  // Cu, the elastic passes e-, Cu or Cu+ alone
-  capsum = std::max<int64_t>(capsum, h->sp[PIC_ION].cap);
+  // one staging slot per collision work item: impact ionization takes e- + Cu, the ionization of
+  // Cu+ e- + Cu+, field ionization Cu, the elastic passes e-, Cu or Cu+ alone
+  capsum = std::max(h->sp[PIC_ELECTRON].cap + h->sp[PIC_NEUTRAL].cap, h->sp[PIC_ELECTRON].cap + h->sp[PIC_ION].cap);
   h->pair_cnt = alloc_n<uint64_t>(h, capsum); A(h->pair_cnt);
   h->ev_hits = alloc_n<int>(h, capsum / 256 + 2); A(h->ev_hits);
   h->ev_cnt = alloc_n<uint64_t>(h, capsum / 256 + 2); A(h->ev_cnt);
   h->ev_off = alloc_n<uint64_t>(h, capsum / 256 + 2); A(h->ev_off);
+  h->ev_cnt2 = alloc_n<uint64_t>(h, capsum / 256 + 2); A(h->ev_cnt2);
+  h->ev_off2 = alloc_n<uint64_t>(h, capsum / 256 + 2); A(h->ev_off2);
   // faces
   Faces &fc = h->faces;
   fc.n = (int64_t)G.fvcell.size();
@@ -438,11 +444,11 @@ int pic_create(const pic_geometry_t *geometry, const pic_grid_t *grid, const pic
   h->red_mid = alloc_n<double>(h, 2 * 128); A(h->red_mid);
   h->ramo_part = alloc_n<double>(h, kRamoBlocks); A(h->ramo_part);
   if (h->prm.circuit_R > 0 && h->prm.circuit_C > 0) { h->E0 = alloc_n<float4>(h, h->nnode); A(h->E0); }
-  h->tmp_len = alloc_n<int64_t>(h, 16); A(h->tmp_len);
+  h->tmp_len = alloc_n<int64_t>(h, 24); A(h->tmp_len);
   h->long_list = alloc_n<int2>(h, kLongCap); A(h->long_list);
   {
     int64_t mc = 0;
-    for (int s = 0; s < 3; ++s) mc = std::max<int64_t>(mc, h->sp[s].cap);
+    for (int s = 0; s < PIC_NSPECIES; ++s) mc = std::max<int64_t>(mc, h->sp[s].cap);
     h->mid_cap = std::min<int64_t>(mc / 5 + 1024, INT32_MAX);   // a queued segment holds >= 5 SPs
     h->mid_list = alloc_n<int2>(h, h->mid_cap); A(h->mid_list);
   }
@@ -475,8 +481,9 @@ int pic_create(const pic_geometry_t *geometry, const pic_grid_t *grid, const pic
   }
 #undef UP
   if (rc != PIC_OK) return fail(rc, "upload failed");
-  for (uint32_t *p : {h->sp[0].cnt, h->sp[1].cnt, h->sp[2].cnt, h->sp[0].off, h->sp[1].off, h->sp[2].off})
-    if (cudaMemsetAsync(p, 0, (h->ncell + 1) * 4, st) != cudaSuccess) rc = PIC_E_CUDA;
+  for (int s = 0; s < PIC_NSPECIES; ++s)
+    for (uint32_t *p : {h->sp[s].cnt, h->sp[s].off})
+      if (cudaMemsetAsync(p, 0, (h->ncell + 1) * 4, st) != cudaSuccess) rc = PIC_E_CUDA;
   for (double *p : {fc.acc_evap, fc.acc_heat, fc.acc_charge, fc.F, fc.J, fc.PN})
     if (cudaMemsetAsync(p, 0, std::max<int64_t>(fc.n, 1) * 8, st) != cudaSuccess) rc = PIC_E_CUDA;
   for (int64_t *p : {fc.acc_sput, fc.acc_Eb, fc.acc_Es})
@@ -551,7 +558,7 @@ int pic_set_clock(pic_t *h, int64_t step, int64_t next_id) {
 
 int pic_load_particles(pic_t *h, int s, const float *x, const float *y, const float *z, const float *vx, const float *vy,
                        const float *vz, const int32_t *w, const uint64_t *id, int64_t n) {
-  if (!h || s < 0 || s > 2 || n < 0) return PIC_E_INVALID;
+  if (!h || s < 0 || s >= PIC_NSPECIES || n < 0) return PIC_E_INVALID;
   Species &S = h->sp[s];
   if (n > S.cap) return pic_fail(h, PIC_E_CAPACITY, "load exceeds the species capacity");
   if (n > 0 && (!x || !y || !z || !vx || !vy || !vz || !w || !id)) return PIC_E_INVALID;
@@ -579,7 +586,7 @@ int pic_load_particles(pic_t *h, int s, const float *x, const float *y, const fl
 
 int pic_get_particles(pic_t *h, int s, float *x, float *y, float *z, float *vx, float *vy, float *vz, int32_t *w,
                       uint64_t *id, int64_t cap, int64_t *n_out) {
-  if (!h || s < 0 || s > 2) return PIC_E_INVALID;
+  if (!h || s < 0 || s >= PIC_NSPECIES) return PIC_E_INVALID;
   DevClock c;
   PIC_TRY(clock_sync(h, &c));
   const int64_t n = c.n[s];
@@ -879,7 +886,7 @@ static void graph_free(pic_t *h) {
 static int graph_index(pic_t *h) {
   for (int p = 0; p < 2; ++p) {
     bool ok = h->gexec[p] != nullptr;
-    for (int s = 0; s < 3; ++s) ok = ok && h->graph_a[p][s] == h->sp[s].a.x;
+    for (int s = 0; s < nsp_active(h); ++s) ok = ok && h->graph_a[p][s] == h->sp[s].a.x;
     if (ok) return p;
   }
   return -1;
@@ -899,16 +906,16 @@ int graph_build_capture(pic_t *h) {
   graph_free(h);
   if (!h->body_stream) PIC_CUDA(h, cudaStreamCreateWithFlags(&h->body_stream, cudaStreamNonBlocking));
   if (!h->cap_stream) PIC_CUDA(h, cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
-  for (int s = 0; s < 3; ++s)
+  for (int s = 0; s < PIC_NSPECIES; ++s)
     if (h->keys_valid[s]) PIC_TRY(stage_sort(h));   // a step starts from sorted SPs
-  SpeciesBuf saved[3][2];
-  for (int s = 0; s < 3; ++s) { saved[s][0] = h->sp[s].a; saved[s][1] = h->sp[s].b; }
+  SpeciesBuf saved[PIC_NSPECIES][2];
+  for (int s = 0; s < PIC_NSPECIES; ++s) { saved[s][0] = h->sp[s].a; saved[s][1] = h->sp[s].b; }
   const uint64_t kt = h->kt_mask;
   h->kt_mask = 0;
   const int64_t n0 = h->nlaunch;
   int rc = PIC_OK;
   for (int p = 0; p < 2 && rc == PIC_OK; ++p) {
-    for (int s = 0; s < 3; ++s) h->graph_a[p][s] = h->sp[s].a.x;
+    for (int s = 0; s < PIC_NSPECIES; ++s) h->graph_a[p][s] = h->sp[s].a.x;
     // recorded on a private stream (the caller's may be the legacy stream, which cannot be
     // captured); the graph is launched on the caller's stream
     cudaGraph_t g = nullptr;
@@ -937,7 +944,7 @@ int graph_build_capture(pic_t *h) {
   cudaGetLastError();
   h->nlaunch = n0;
   h->kt_mask = kt;
-  for (int s = 0; s < 3; ++s) { h->sp[s].a = saved[s][0]; h->sp[s].b = saved[s][1]; h->keys_valid[s] = false; }
+  for (int s = 0; s < PIC_NSPECIES; ++s) { h->sp[s].a = saved[s][0]; h->sp[s].b = saved[s][1]; h->keys_valid[s] = false; }
   if (rc != PIC_OK) { graph_free(h); return rc; }
   h->graph_valid = true;
   h->graph_flags = h->prm.flags;
@@ -949,7 +956,7 @@ int graph_launch_step(pic_t *h) {
   const int p = graph_index(h);
   if (p < 0) return pic_fail(h, PIC_E_INVALID, "no step graph for the current particle buffers");
   PIC_CUDA(h, cudaGraphLaunch(h->gexec[p], h->stream));
-  for (int s = 0; s < 3; ++s) std::swap(h->sp[s].a, h->sp[s].b);
+  for (int s = 0; s < nsp_active(h); ++s) std::swap(h->sp[s].a, h->sp[s].b);
   h->nlaunch += h->graph_outer_launches;
   return PIC_OK;
 }
@@ -986,6 +993,8 @@ static int pic_step_graph(pic_t *h, int nsteps, int64_t step) {
 static int pic_step_eager(pic_t *h, int nsteps, int64_t step);
 
 // ---- ensemble of independent instances -----------------------------------------------------------
+constexpr int kNs = PIC_NSPECIES;   // species slots per instance in the batch tables
+
 struct pic_batch_s {
   std::vector<pic_t *> inst;
   cudaStream_t stream = nullptr;       // the instances' common stream
@@ -1014,7 +1023,7 @@ static int batch_index(pic_batch_t *b) {
     if (!b->gexec[p]) continue;
     bool ok = true;
     for (size_t i = 0; i < b->inst.size() && ok; ++i)
-      for (int s = 0; s < 3; ++s) ok = ok && b->graph_a[p][3 * i + s] == b->inst[i]->sp[s].a.x;
+      for (int s = 0; s < nsp_active(b->inst[i]); ++s) ok = ok && b->graph_a[p][kNs * i + s] == b->inst[i]->sp[s].a.x;
     for (size_t i = 0; i < b->inst.size() && ok; ++i) ok = b->flags[i] == b->inst[i]->prm.flags;
     if (ok) return p;
   }
@@ -1031,23 +1040,23 @@ static int batch_capture(pic_batch_t *b) {
   for (pic_t *h : b->inst) {
     if (!h->body_stream && cudaStreamCreateWithFlags(&h->body_stream, cudaStreamNonBlocking) != cudaSuccess) return PIC_E_CUDA;
     if (!h->cap_stream && cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess) return PIC_E_CUDA;
-    for (int s = 0; s < 3; ++s)
+    for (int s = 0; s < PIC_NSPECIES; ++s)
       if (h->keys_valid[s]) PIC_TRY(stage_sort(h));
   }
-  std::vector<SpeciesBuf> saved(2 * 3 * n);
+  std::vector<SpeciesBuf> saved(2 * kNs * n);
   std::vector<uint64_t> kt(n);
   std::vector<int64_t> n0(n);
   for (size_t i = 0; i < n; ++i) {
-    for (int s = 0; s < 3; ++s) { saved[6 * i + 2 * s] = b->inst[i]->sp[s].a; saved[6 * i + 2 * s + 1] = b->inst[i]->sp[s].b; }
+    for (int s = 0; s < kNs; ++s) { saved[2 * (kNs * i + s)] = b->inst[i]->sp[s].a; saved[2 * (kNs * i + s) + 1] = b->inst[i]->sp[s].b; }
     kt[i] = b->inst[i]->kt_mask;
     b->inst[i]->kt_mask = 0;
     n0[i] = b->inst[i]->nlaunch;
   }
   int rc = PIC_OK;
   for (int p = 0; p < 2 && rc == PIC_OK; ++p) {
-    b->graph_a[p].assign(3 * n, nullptr);
+    b->graph_a[p].assign(kNs * n, nullptr);
     for (size_t i = 0; i < n; ++i)
-      for (int s = 0; s < 3; ++s) b->graph_a[p][3 * i + s] = b->inst[i]->sp[s].a.x;
+      for (int s = 0; s < kNs; ++s) b->graph_a[p][kNs * i + s] = b->inst[i]->sp[s].a.x;
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeRelaxed);
     if (e != cudaSuccess) { b->err = std::string("begin capture: ") + cudaGetErrorString(e); rc = PIC_E_CUDA; break; }
@@ -1078,7 +1087,11 @@ static int batch_capture(pic_batch_t *b) {
   cudaGetLastError();
   for (size_t i = 0; i < n; ++i) {
     pic_t *h = b->inst[i];
-    for (int s = 0; s < 3; ++s) { h->sp[s].a = saved[6 * i + 2 * s]; h->sp[s].b = saved[6 * i + 2 * s + 1]; h->keys_valid[s] = false; }
+    for (int s = 0; s < kNs; ++s) {
+      h->sp[s].a = saved[2 * (kNs * i + s)];
+      h->sp[s].b = saved[2 * (kNs * i + s) + 1];
+      h->keys_valid[s] = false;
+    }
     h->kt_mask = kt[i];
     h->nlaunch = n0[i];
   }
@@ -1140,7 +1153,7 @@ int pic_batch_step(pic_batch_t *b, int nsteps) {
   bool eager = false;
   for (pic_t *h : b->inst) {
     bool sorted = true;
-    for (int s = 0; s < 3; ++s) sorted = sorted && !h->keys_valid[s];
+    for (int s = 0; s < PIC_NSPECIES; ++s) sorted = sorted && !h->keys_valid[s];
     eager = eager || h->eager_flags != h->prm.flags || !sorted;
   }
   if (eager) {
@@ -1163,7 +1176,7 @@ int pic_batch_step(pic_batch_t *b, int nsteps) {
     if (cudaGraphLaunch(b->gexec[p], b->stream) != cudaSuccess) { b->err = "graph launch"; rc = PIC_E_CUDA; break; }
     for (size_t i = 0; i < n; ++i) {
       pic_t *h = b->inst[i];
-      for (int s = 0; s < 3; ++s) std::swap(h->sp[s].a, h->sp[s].b);
+      for (int s = 0; s < nsp_active(h); ++s) std::swap(h->sp[s].a, h->sp[s].b);
       h->nlaunch += h->graph_outer_launches;
       h->last_solve_graph = true;
       ++step[i];
@@ -1225,7 +1238,7 @@ int pic_step(pic_t *h, int nsteps) {
   PIC_TRY(clock_sync(h, &c));
   int64_t step = c.step;
   bool sorted = true;
-  for (int s = 0; s < 3; ++s) sorted = sorted && !h->keys_valid[s];
+  for (int s = 0; s < PIC_NSPECIES; ++s) sorted = sorted && !h->keys_valid[s];
   if ((h->prm.flags & PIC_F_GRAPH) && sorted && nsteps > 0) {
     // a graph is recorded only after an eager step with the same flags (lazily allocated buffers)
     if (h->eager_flags != h->prm.flags) {
@@ -1335,20 +1348,20 @@ int pic_diagnostics(pic_t *h, pic_diag_t *out) {
   PIC_TRY(clock_sync(h, &c));
   out->step = c.step;
   out->next_id = c.next_id;
-  unsigned long long *sums = (unsigned long long *)(h->tmp_len + 10);
-  PIC_CUDA(h, cudaMemsetAsync(sums, 0, 4 * 8, h->stream));
-  for (int s = 0; s < 3; ++s) {
+  unsigned long long *sums = (unsigned long long *)(h->tmp_len + 16);
+  PIC_CUDA(h, cudaMemsetAsync(sums, 0, (PIC_NSPECIES + 1) * 8, h->stream));
+  for (int s = 0; s < PIC_NSPECIES; ++s) {
     out->count[s] = c.n[s];
     ++h->nlaunch;
     k_sum_w<<<h->nsm * 4, kThreads, 0, h->stream>>>(h->sp[s].a.w, h->clock, s, sums + s);
     out->removed[s] = c.ctr[cRemovedE + s];
   }
   ++h->nlaunch;
-  k_sum_q<<<h->nsm * 4, kThreads, 0, h->stream>>>(h->Q, h->nnode, sums + 3);
-  unsigned long long hs[4];
+  k_sum_q<<<h->nsm * 4, kThreads, 0, h->stream>>>(h->Q, h->nnode, sums + PIC_NSPECIES);
+  unsigned long long hs[PIC_NSPECIES + 1];
   PIC_TRY(d2h(h, hs, sums, sizeof hs));
-  for (int s = 0; s < 3; ++s) out->weight[s] = (int64_t)hs[s];
-  out->total_charge_fixed = (int64_t)hs[3];
+  for (int s = 0; s < PIC_NSPECIES; ++s) out->weight[s] = (int64_t)hs[s];
+  out->total_charge_fixed = (int64_t)hs[PIC_NSPECIES];
   out->emitted = c.ctr[cEmitted];
   out->evaporated = c.ctr[cEvaporated];
   out->sputtered = c.ctr[cSputtered];
@@ -1360,6 +1373,11 @@ int pic_diagnostics(pic_t *h, pic_diag_t *out) {
   out->coulomb_ee = c.ctr[cCoulombEe];
   out->coulomb_ei = c.ctr[cCoulombEi];
   out->coulomb_ii = c.ctr[cCoulombIi];
+  out->double_ionizations = c.ctr[cDoubleIon];
+  out->ion_ionizations = c.ctr[cIonIon];
+  out->coulomb_ej = c.ctr[cCoulombEj];
+  out->coulomb_ij = c.ctr[cCoulombIj];
+  out->coulomb_jj = c.ctr[cCoulombJj];
   out->merged = c.ctr[cMerged];
   out->fallback_range = c.ctr[cFbRange];
   out->fallback_bin = c.ctr[cFbBin];

@@ -21,6 +21,7 @@ constexpr double kHbar = 1.054571817e-34;
 constexpr double kPi = 3.141592653589793;
 constexpr double kMcu = 63.546 * kAmu;
 constexpr double kXiCu = 7.726;      // eV, first ionization energy of Cu
+constexpr double kXi2Cu = 20.292;    // eV, second ionization energy of Cu (Cu+ -> Cu2+)
 constexpr double kEvap = 3.43;       // eV (Sec. 2.3.1)
 constexpr double kTboil = 2835.0;    // K
 constexpr double kPatm = 101325.0;   // Pa
@@ -52,13 +53,16 @@ enum Purpose : uint32_t {
   kEmit = 1, kPair = 2, kIon = 3, kScat = 4, kDfi = 5, kEvapP = 6, kSput = 7,
   kPairEn = 8, kDrawEn = 9, kPairNn = 10, kDrawNn = 11, kPairCx = 12, kDrawCx = 13,   // elastic e-Cu, Cu-Cu, exchange
   kScatEn = 14, kScatNn = 15,
-  kPairEe = 16, kDrawEe = 17, kPairEi = 18, kDrawEi = 19, kPairIi = 20, kDrawIi = 21   // Coulomb
+  kPairEe = 16, kDrawEe = 17, kPairEi = 18, kDrawEi = 19, kPairIi = 20, kDrawIi = 21,  // Coulomb
+  kScat2 = 22, kPairIz = 23, kIonIz = 24, kScatIz = 25,       // Cu2+: double ionization, Cu+ ionization
+  kPairEj = 26, kDrawEj = 27, kPairIj = 28, kDrawIj = 29, kPairJj = 30, kDrawJj = 31   // Coulomb with Cu2+
 };
 
 // device counters (int64), indices
 enum Ctr {
-  cEmitted = 0, cEvaporated, cSputtered, cImpactIon, cFieldIon, cRemovedE, cRemovedN, cRemovedI,
-  cIonImpacts, cWevals, cSurFaces, cElasticEn, cElasticNn, cChargeEx, cCoulombEe, cCoulombEi, cCoulombIi, cMerged, cFbRange, cFbBin, cNum
+  cEmitted = 0, cEvaporated, cSputtered, cImpactIon, cFieldIon, cRemovedE, cRemovedN, cRemovedI, cRemovedJ,
+  cIonImpacts, cWevals, cSurFaces, cElasticEn, cElasticNn, cChargeEx, cCoulombEe, cCoulombEi, cCoulombIi, cMerged, cFbRange,
+  cFbBin, cDoubleIon, cIonIon, cCoulombEj, cCoulombIj, cCoulombJj, cNum
 };
 
 // error bits set by kernels
@@ -67,9 +71,9 @@ enum ErrBits : int { kErrCapacity = 1, kErrSegment = 2, kErrTimeout = 4, kErrNan
 struct DevClock {
   int64_t step;
   int64_t next_id;
-  int64_t n[3];          // SPs held per species
-  int64_t n_sorted[3];   // leading SPs covered by the last cell sort (per-cell offsets valid)
-  int64_t n_new[3];      // scratch: SPs created by the current pass
+  int64_t n[PIC_NSPECIES];          // SPs held per species
+  int64_t n_sorted[PIC_NSPECIES];   // leading SPs covered by the last cell sort (per-cell offsets valid)
+  int64_t n_new[PIC_NSPECIES];      // scratch: SPs created by the current pass
   int64_t ctr[cNum];
   int err;
   int phi_prev_ok;       // phi_prev holds the previous step's potential (time extrapolation)
@@ -169,7 +173,7 @@ struct pic_s {
   float4 *E0 = nullptr;          // per node: unit Laplace field [1/m] (circuit; null without one)
   double *ramo_part = nullptr;   // Shockley-Ramo partial sums
   unsigned long long *Q = nullptr;  // per node, int64 two's complement charge
-  pic::Species sp[3];
+  pic::Species sp[PIC_NSPECIES];
   pic::Faces faces;
   pic::Heat heat;
   std::vector<pic::MgLevel> mg;
@@ -180,6 +184,7 @@ struct pic_s {
   int tail_start = -1;              // first level of the cluster-launched V-cycle tail (-1: none)
   int *ev_hits = nullptr;             // collision events staged per unit of 256 work items
   uint64_t *ev_cnt = nullptr, *ev_off = nullptr;
+  uint64_t *ev_cnt2 = nullptr, *ev_off2 = nullptr;   // second product kind per unit (double ionization)
   double sigma_el_en = 0, sigma_el_nn = 0, sigma_cx = 0;   // m^2 (elastic and exchange passes)
   int mg_sweeps = 3;                // red-black sweeps before and after each coarse correction
   pic::DevClock *clock = nullptr;
@@ -196,7 +201,7 @@ struct pic_s {
   int *long_n = nullptr;
   int *xq_n = nullptr;           // push: lengths of the per-species crosser queues
   // state flags and last diagnostics
-  bool keys_valid[3] = {false, false, false};
+  bool keys_valid[PIC_NSPECIES] = {false, false, false, false};
   int last_mg_cycles = 0;
   int64_t mg_cycles_host = 0;       // refinement cycles of host-driven solves since create
   double last_mg_res = 0;
@@ -205,7 +210,7 @@ struct pic_s {
   int64_t nlaunch = 0;           // kernels launched by the library since create
   // graph form of the step (PIC_F_GRAPH): one captured graph per double-buffer parity
   cudaGraphExec_t gexec[2] = {nullptr, nullptr};
-  float *graph_a[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};  // S.a.x at capture
+  float *graph_a[2][PIC_NSPECIES] = {};  // S.a.x at capture
   bool graph_valid = false;
   uint32_t graph_flags = 0;              // flags the graphs were recorded with
   uint32_t eager_flags = 0xFFFFFFFFu;   // flags of the last eager step (none yet)
@@ -226,6 +231,10 @@ struct pic_s {
   double kt_ms[64] = {0}, kt_units[64] = {0};
   int64_t kt_n[64] = {0};
 };
+
+// Species the step works on: Cu2+ only while PIC_F_ION2 is set (without it Cu2+ SPs are not made,
+// and any held stay as they are)
+inline int nsp_active(const pic_t *h) { return (h->prm.flags & PIC_F_ION2) ? PIC_NSPECIES : 3; }
 
 namespace pic {
 

@@ -31,14 +31,14 @@
 namespace pic {
 
 constexpr char kMagic[8] = {'P', 'I', 'C', 'S', 'T', 'A', 'T', 'E'};
-constexpr uint32_t kVersion = 1;
+constexpr uint32_t kVersion = 2;   // 2: four species (Cu2+)
 
 struct SaveHeader {
   uint32_t version, endian, header_bytes, clock_bytes;
   pic_grid_t grid;
   pic_geometry_t geo;
-  int32_t Z[3];
-  double mass[3];
+  int32_t Z[PIC_NSPECIES];
+  double mass[PIC_NSPECIES];
   pic_params_t prm;
   double V0;
   int64_t nface, nvox, nnode, ncell;
@@ -119,7 +119,7 @@ static void fill_header(pic_t *h, SaveHeader &H) {
   H.clock_bytes = sizeof(DevClock);
   H.grid.nx = h->nx; H.grid.ny = h->ny; H.grid.nz = h->nz; H.grid.dx = h->dx;
   H.geo = h->geo;
-  for (int s = 0; s < 3; ++s) { H.Z[s] = h->sp[s].Z; H.mass[s] = h->sp[s].mass; }
+  for (int s = 0; s < PIC_NSPECIES; ++s) { H.Z[s] = h->sp[s].Z; H.mass[s] = h->sp[s].mass; }
   H.prm = h->prm;
   H.V0 = h->V0;
   H.nface = h->faces.n; H.nvox = h->heat.nvox; H.nnode = h->nnode; H.ncell = h->ncell;
@@ -142,7 +142,7 @@ static int compatible(pic_t *h, const SaveHeader &F, const SaveHeader &M) {
   auto bad = [&](const char *what) { return pic_fail(h, PIC_E_INVALID, std::string("pic_load: ") + what + " differs"); };
   if (F.grid.nx != M.grid.nx || F.grid.ny != M.grid.ny || F.grid.nz != M.grid.nz || F.grid.dx != M.grid.dx) return bad("grid");
   if (F.geo.tip_radius != M.geo.tip_radius || F.geo.tip_height != M.geo.tip_height) return bad("tip geometry");
-  for (int s = 0; s < 3; ++s)
+  for (int s = 0; s < PIC_NSPECIES; ++s)
     if (F.Z[s] != M.Z[s] || F.mass[s] != M.mass[s]) return bad("species charge or mass");
   const pic_params_t &a = F.prm, &b = M.prm;
   if (a.dt != b.dt || a.apex_field != b.apex_field || a.V0 != b.V0 || a.T0 != b.T0 ||
@@ -167,7 +167,7 @@ extern "C" {
 int pic_save(pic_t *h, const char *path) {
   if (!h || !path) return PIC_E_INVALID;
   PIC_TRY(check_device(h));
-  for (int s = 0; s < 3; ++s)
+  for (int s = 0; s < PIC_NSPECIES; ++s)
     if (h->keys_valid[s])
       return pic_fail(h, PIC_E_INVALID, "pic_save: SPs were pushed but not yet sorted; save between steps or after pic_sort");
   DevClock c;
@@ -190,7 +190,7 @@ int pic_save(pic_t *h, const char *path) {
   PIC_TRY(put(h, F.f, kMagic, sizeof kMagic));
   PIC_TRY(put(h, F.f, &H, sizeof H));
   PIC_TRY(put(h, F.f, &c, sizeof c));
-  for (int s = 0; s < 3; ++s) {
+  for (int s = 0; s < PIC_NSPECIES; ++s) {
     const int64_t n = c.n[s];
     const SpeciesBuf &a = h->sp[s].a;
     PIC_TRY(put_tag(h, F.f, tSpecies, (uint64_t)n * 36));
@@ -245,14 +245,14 @@ int pic_load(pic_t *h, const char *path) {
   PIC_TRY(compatible(h, H, M));
   DevClock c;
   PIC_TRY(get(h, F.f, &c, sizeof c));
-  for (int s = 0; s < 3; ++s)
+  for (int s = 0; s < PIC_NSPECIES; ++s)
     if (c.n[s] < 0 || c.n[s] > h->sp[s].cap || c.n_sorted[s] < 0 || c.n_sorted[s] > c.n[s])
       return pic_fail(h, PIC_E_CAPACITY, "pic_load: species " + std::to_string(s) + " holds " + std::to_string(c.n[s]) +
                                              " SPs, more than this handle's capacity " + std::to_string(h->sp[s].cap));
   // from here the handle's state is being replaced: any failure leaves it unusable for stepping
   graph_invalidate(h);
   std::vector<char> buf;
-  for (int s = 0; s < 3; ++s) {
+  for (int s = 0; s < PIC_NSPECIES; ++s) {
     const int64_t n = c.n[s];
     const SpeciesBuf &a = h->sp[s].a;
     PIC_TRY(expect_tag(h, F.f, tSpecies, (uint64_t)n * 36));

@@ -12,7 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libpic.so")
 
 PIC_OK, PIC_E_INVALID, PIC_E_CAPACITY, PIC_E_NOCONV, PIC_E_TIMEOUT, PIC_E_CUDA = 0, -1, -2, -3, -4, -5
-ELECTRON, NEUTRAL, ION = 0, 1, 2
+ELECTRON, NEUTRAL, ION, ION2 = 0, 1, 2, 3
 F_EMISSION, F_EVAP, F_SPUTTER, F_IMPACT_ION, F_DFI, F_HEAT, F_SURROGATE, F_MIXED_MG = (
     0x01, 0x02, 0x04, 0x08, 0x10, 0x20, 0x40, 0x80)
 F_ALL = 0xFF
@@ -23,6 +23,7 @@ F_ELASTIC = 0x800
 F_EXTRAPOLATE = 0x1000
 F_COULOMB = 0x2000
 F_MERGE = 0x4000
+F_ION2 = 0x8000
 F_PRODUCTION = F_ALL | F_FAST_INTEGRAL     # surrogate, FP32 Gamow quadrature for its fallback, mixed MG
 
 QE = 1.602176634e-19
@@ -58,9 +59,9 @@ class Params(C.Structure):
 
 
 class Diag(C.Structure):
-    _fields_ = [("step", C.c_int64), ("next_id", C.c_int64), ("count", C.c_int64 * 3), ("weight", C.c_int64 * 3),
+    _fields_ = [("step", C.c_int64), ("next_id", C.c_int64), ("count", C.c_int64 * 4), ("weight", C.c_int64 * 4),
                 ("emitted", C.c_int64), ("evaporated", C.c_int64), ("sputtered", C.c_int64),
-                ("impact_ionizations", C.c_int64), ("field_ionizations", C.c_int64), ("removed", C.c_int64 * 3),
+                ("impact_ionizations", C.c_int64), ("field_ionizations", C.c_int64), ("removed", C.c_int64 * 4),
                 ("ion_impacts", C.c_int64), ("total_charge_fixed", C.c_int64), ("mg_cycles", C.c_int),
                 ("mg_residual", C.c_double), ("V0", C.c_double), ("max_face_field", C.c_double),
                 ("max_J", C.c_double), ("max_T", C.c_double), ("emitted_current", C.c_double),
@@ -69,7 +70,9 @@ class Diag(C.Structure):
                 ("I_tot", C.c_double), ("elastic_en", C.c_int64), ("elastic_nn", C.c_int64),
                 ("charge_exchanges", C.c_int64), ("mg_cycles_total", C.c_int64), ("coulomb_ee", C.c_int64),
                 ("coulomb_ei", C.c_int64), ("coulomb_ii", C.c_int64), ("merged", C.c_int64),
-                ("fallback_range", C.c_int64), ("fallback_bin", C.c_int64)]
+                ("fallback_range", C.c_int64), ("fallback_bin", C.c_int64), ("double_ionizations", C.c_int64),
+                ("ion_ionizations", C.c_int64), ("coulomb_ej", C.c_int64), ("coulomb_ij", C.c_int64),
+                ("coulomb_jj", C.c_int64)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
@@ -167,10 +170,13 @@ class _TorchAllocator:
         self.free_fn = FREE_FN(free)
 
 
-def species_table(cap):
+def species_table(cap, ion2=False):
+    """e-, Cu, Cu+, Cu2+ entries; Cu2+ room: cap[3] if given, else Cu+'s with F_ION2, else 1024 SPs."""
     if np.isscalar(cap):
         cap = (cap, cap, cap)
-    return (SpeciesT * 3)(SpeciesT(-1, ME, int(cap[0])), SpeciesT(0, MCU, int(cap[1])), SpeciesT(1, MCU, int(cap[2])))
+    cap_j = cap[3] if len(cap) > 3 else (cap[2] if ion2 else 1024)
+    return (SpeciesT * 4)(SpeciesT(-1, ME, int(cap[0])), SpeciesT(0, MCU, int(cap[1])), SpeciesT(1, MCU, int(cap[2])),
+                          SpeciesT(2, MCU, int(cap_j)))
 
 
 class Pic:
@@ -196,7 +202,8 @@ class Pic:
         h = C.c_void_p()
         a = self._alloc.alloc_fn if self._alloc else ALLOC_FN(0)
         f = self._alloc.free_fn if self._alloc else FREE_FN(0)
-        rc = L.pic_create(C.byref(geo), C.byref(grid), species_table(capacity), 3, C.byref(prm), a, f, None,
+        rc = L.pic_create(C.byref(geo), C.byref(grid), species_table(capacity, bool(flags & F_ION2)), 4,
+                          C.byref(prm), a, f, None,
                           C.c_void_p(self.stream.cuda_stream), C.byref(h))
         if rc != PIC_OK:
             raise PicError(rc, "pic_create failed")
