@@ -346,11 +346,21 @@ def run_ours(args):
                 pinned[k][f] = a
         h2d = sum(a.nbytes for k in pinned for a in pinned[k].values())
 
+        e2e_phase = {"load_ms": 0.0, "step_ms": 0.0, "diagnostics_ms": 0.0}
+
         def e2e_step():
-            for s, k in enumerate("eni"):
-                sim.load_particles(s, pinned[k])
+            # host clock per phase (each phase ends in a stream synchronisation of the library)
+            t = time.perf_counter()
+            sim.load_all([pinned[k] for k in "eni"])
+            t1 = time.perf_counter()
             sim.step(1)
-            return sum(sim.diagnostics()["count"])
+            torch.cuda.synchronize()
+            t2 = time.perf_counter()
+            n = sum(sim.diagnostics()["count"])
+            t3 = time.perf_counter()
+            for k, v in zip(e2e_phase, (t1 - t, t2 - t1, t3 - t2)):
+                e2e_phase[k] += v * 1e3
+            return n
 
         if args.e2e_steps > 0:
             e2e_step()   # one untimed warm-up step, as for the device-timed region
@@ -474,7 +484,8 @@ def run_ours(args):
         "roofline_particles": roof_p,
         "clocks": clk.summary(),
         "e2e": {"value": tot_e2e, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-                "d2h_bytes_per_step": int(__import__("ctypes").sizeof(pic.Diag))},
+                "d2h_bytes_per_step": int(__import__("ctypes").sizeof(pic.Diag)),
+                "phase_ms_per_step": {k: round(v / max(args.e2e_steps + 1, 1), 3) for k, v in e2e_phase.items()}},
         "gpu_launches": int(launches),
     }
     if args.cpu_baseline:

@@ -175,6 +175,19 @@ const char *pic_last_error(pic_t *h);
 int pic_load_particles(pic_t *h, int species, const float *x, const float *y, const float *z,
                        const float *vx, const float *vy, const float *vz, const int32_t *w,
                        const uint64_t *id, int64_t n);
+/* The SPs of every species in one call: sp[s] for species s = 0 .. nspecies-1 (host SoA arrays
+ * of length sp[s].n, pinned memory for full copy bandwidth).  Each species is checked and sorted
+ * as by pic_load_particles, while the next species' host-to-device copies run on a second stream
+ * of the library; the call returns once every species is in place.  Errors as for
+ * pic_load_particles; on an error in species s the species before s are loaded and the others
+ * unchanged (the same outcome as the sequence of pic_load_particles calls). */
+typedef struct {
+  const float *x, *y, *z, *vx, *vy, *vz;
+  const int32_t *w;
+  const uint64_t *id;
+  int64_t n;
+} pic_host_species_t;
+int pic_load_all(pic_t *h, const pic_host_species_t *sp, int nspecies);
 /* Copy out the SPs of one species in their current device order (cell-sorted part first, then
  * SPs created since the last sort); n_out receives the count.  PIC_E_CAPACITY if cap is short. */
 int pic_get_particles(pic_t *h, int species, float *x, float *y, float *z, float *vx, float *vy,

@@ -72,11 +72,19 @@ __global__ void k_scan_partial(const T *__restrict__ in, int64_t n_host, const i
   T s = 0;
   const int64_t nvec = hi > lo ? (hi - lo) / kPer : 0;
   const uint4 *v = reinterpret_cast<const uint4 *>(in + lo);
-  for (int64_t q = threadIdx.x; q < nvec; q += blockDim.x) {
-    union { uint4 u; T e[kPer]; } x;
-    x.u = v[q];
+  // four independent vector loads in flight per thread before any sum
+  constexpr int kU = 4;
+  for (int64_t q0 = threadIdx.x; q0 < nvec; q0 += (int64_t)kU * blockDim.x) {
+    union { uint4 u; T e[kPer]; } x[kU];
 #pragma unroll
-    for (int e = 0; e < kPer; ++e) s += x.e[e];
+    for (int u = 0; u < kU; ++u) {
+      const int64_t q = q0 + (int64_t)u * blockDim.x;
+      x[u].u = q < nvec ? v[q] : make_uint4(0u, 0u, 0u, 0u);
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u)
+#pragma unroll
+      for (int e = 0; e < kPer; ++e) s += x[u].e[e];
   }
   for (int64_t i = lo + nvec * kPer + threadIdx.x; i < hi; i += blockDim.x) s += in[i];
   s = block_sum<T>(s, sh);
@@ -112,11 +120,11 @@ __global__ void k_scan_apply(const T *__restrict__ in, T *__restrict__ out, int6
   const int64_t lo = (int64_t)blockIdx.x * chunk;
   const int64_t hi = lo + chunk < n ? lo + chunk : n;
   T carry = partial[blockIdx.x];
-  for (int64_t base = lo; base < hi; base += (int64_t)blockDim.x * kItems) {
+  using Run = union { uint4 q[kVec]; T e[kItems]; };
+  // the run of kItems elements a thread takes at base (zeros past hi)
+  auto load_run = [&](int64_t base, Run &v) {
     const int64_t i0 = base + (int64_t)threadIdx.x * kItems;
-    const bool whole = i0 + kItems <= hi;
-    union { uint4 q[kVec]; T e[kItems]; } v;
-    if (whole) {
+    if (i0 + kItems <= hi) {
       const uint4 *src = reinterpret_cast<const uint4 *>(in + i0);
 #pragma unroll
       for (int q = 0; q < kVec; ++q) v.q[q] = src[q];
@@ -124,6 +132,15 @@ __global__ void k_scan_apply(const T *__restrict__ in, T *__restrict__ out, int6
 #pragma unroll
       for (int q = 0; q < kItems; ++q) v.e[q] = i0 + q < hi ? in[i0 + q] : T(0);
     }
+  };
+  const int64_t span = (int64_t)blockDim.x * kItems;
+  Run nxt;
+  if (lo < hi) load_run(lo, nxt);
+  for (int64_t base = lo; base < hi; base += span) {
+    const int64_t i0 = base + (int64_t)threadIdx.x * kItems;
+    const bool whole = i0 + kItems <= hi;
+    Run v = nxt;
+    if (base + span < hi) load_run(base + span, nxt);   // the next run's loads overlap this run's scan
     T s = 0;
 #pragma unroll
     for (int q = 0; q < kItems; ++q) s += v.e[q];

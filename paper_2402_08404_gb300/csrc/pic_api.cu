@@ -259,6 +259,12 @@ void pic_destroy(pic_t *h) {
   graph_free(h);
   if (h->body_stream) cudaStreamDestroy(h->body_stream);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  if (h->copy_stream) {
+    cudaStreamSynchronize(h->copy_stream);
+    cudaStreamDestroy(h->copy_stream);
+  }
+  for (cudaEvent_t e : h->copy_ev)
+    if (e) cudaEventDestroy(e);
   mlp_forget(h);
   dfree_all(h);
   delete h;
@@ -581,6 +587,69 @@ int pic_load_particles(pic_t *h, int s, const float *x, const float *y, const fl
   PIC_CUDA(h, cudaStreamSynchronize(st));
   PIC_TRY(stage_keys(h, s));   // clears the counts a push may have left, then counts the new SPs
   PIC_TRY(sort_species(h, s));
+  return check_err(h);
+}
+
+// Every species in one call: the copies of species s + 1 run on a second stream while species
+// s is checked and sorted on the library stream.  A species is swapped in only after its own
+// check has passed (the host waits for that check alone), so a failure leaves the species
+// before it loaded and the rest unchanged, as the same sequence of pic_load_particles calls would.
+int pic_load_all(pic_t *h, const pic_host_species_t *sp, int nspecies) {
+  if (!h || !sp || nspecies < 1 || nspecies > PIC_NSPECIES) return PIC_E_INVALID;
+  PIC_TRY(check_device(h));
+  if (h->capturing) return pic_fail(h, PIC_E_INVALID, "pic_load_all during graph capture");
+  for (int s = 0; s < nspecies; ++s) {
+    const pic_host_species_t &a = sp[s];
+    if (a.n < 0) return PIC_E_INVALID;
+    if (a.n > h->sp[s].cap) return pic_fail(h, PIC_E_CAPACITY, "load exceeds the species capacity");
+    if (a.n > 0 && (!a.x || !a.y || !a.z || !a.vx || !a.vy || !a.vz || !a.w || !a.id)) return PIC_E_INVALID;
+  }
+  if (!h->copy_stream) PIC_CUDA(h, cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking));
+  for (cudaEvent_t &e : h->copy_ev)
+    if (!e) PIC_CUDA(h, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  cudaStream_t cs = h->copy_stream, st = h->stream;
+  // the copies overwrite the scratch buffers: after all work queued so far
+  PIC_CUDA(h, cudaEventRecord(h->copy_ev[PIC_NSPECIES], st));
+  PIC_CUDA(h, cudaStreamWaitEvent(cs, h->copy_ev[PIC_NSPECIES], 0));
+  auto issue = [&](int s) -> int {
+    const pic_host_species_t &a = sp[s];
+    const SpeciesBuf &B = h->sp[s].b;
+    const int64_t n = a.n;
+    if (n) {
+      PIC_CUDA(h, cudaMemcpyAsync(B.x, a.x, n * 4, cudaMemcpyHostToDevice, cs));
+      PIC_CUDA(h, cudaMemcpyAsync(B.y, a.y, n * 4, cudaMemcpyHostToDevice, cs));
+      PIC_CUDA(h, cudaMemcpyAsync(B.z, a.z, n * 4, cudaMemcpyHostToDevice, cs));
+      PIC_CUDA(h, cudaMemcpyAsync(B.vx, a.vx, n * 4, cudaMemcpyHostToDevice, cs));
+      PIC_CUDA(h, cudaMemcpyAsync(B.vy, a.vy, n * 4, cudaMemcpyHostToDevice, cs));
+      PIC_CUDA(h, cudaMemcpyAsync(B.vz, a.vz, n * 4, cudaMemcpyHostToDevice, cs));
+      PIC_CUDA(h, cudaMemcpyAsync(B.w, a.w, n * 4, cudaMemcpyHostToDevice, cs));
+      PIC_CUDA(h, cudaMemcpyAsync(B.id, a.id, n * 8, cudaMemcpyHostToDevice, cs));
+    }
+    PIC_CUDA(h, cudaEventRecord(h->copy_ev[s], cs));
+    return PIC_OK;
+  };
+  int rc = issue(0);
+  for (int s = 0; s < nspecies && rc == PIC_OK; ++s) {
+    if (s + 1 < nspecies) rc = issue(s + 1);
+    if (rc != PIC_OK) break;
+    Species &S = h->sp[s];
+    const int64_t n = sp[s].n;
+    if (cudaStreamWaitEvent(st, h->copy_ev[s], 0) != cudaSuccess) { rc = pic_fail(h, PIC_E_CUDA, "wait copy"); break; }
+    if (n) {
+      rc = validate_loaded(h, S.b, n);   // waits for this species' check only
+      if (rc != PIC_OK) break;
+    }
+    std::swap(S.a, S.b);
+    if (cudaMemcpyAsync(&h->clock->n[s], &sp[s].n, 8, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+      rc = pic_fail(h, PIC_E_CUDA, "count upload");
+      break;
+    }
+    rc = stage_keys(h, s);
+    if (rc == PIC_OK) rc = sort_species(h, s);
+  }
+  cudaStreamSynchronize(cs);   // no copy outlives the call (the host arrays may go away)
+  if (rc != PIC_OK) return rc;
+  PIC_CUDA(h, cudaStreamSynchronize(st));
   return check_err(h);
 }
 

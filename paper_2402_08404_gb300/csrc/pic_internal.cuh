@@ -217,6 +217,8 @@ struct pic_s {
   int64_t graph_outer_launches = 0, graph_body_launches = 0;
   cudaStream_t body_stream = nullptr;   // capture stream of the Poisson loop body
   cudaStream_t cap_stream = nullptr;    // capture stream of the step graphs
+  cudaStream_t copy_stream = nullptr;   // pic_load_all: host-to-device copies beside the sorts
+  cudaEvent_t copy_ev[PIC_NSPECIES + 1] = {};   // [s]: species s copied; [PIC_NSPECIES]: the call's start
   bool capturing = false;               // stage code is being recorded into a graph
   bool last_solve_graph = false;        // the last solve ran in a graph (its diagnostics are on the device)
   // autotuned launch shapes

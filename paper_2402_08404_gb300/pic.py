@@ -45,6 +45,10 @@ class GridT(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("dx", C.c_double)]
 
 
+class HostSpeciesT(C.Structure):
+    _fields_ = [(k, C.c_void_p) for k in ("x", "y", "z", "vx", "vy", "vz", "w", "id")] + [("n", C.c_int64)]
+
+
 class SpeciesT(C.Structure):
     _fields_ = [("charge_e", C.c_int), ("mass", C.c_double), ("capacity", C.c_int64)]
 
@@ -100,6 +104,7 @@ def lib():
         L.pic_step.argtypes = [vp, i32]
         L.pic_load_particles.argtypes = [vp, i32] + [vp] * 8 + [i64]
         L.pic_get_particles.argtypes = [vp, i32] + [vp] * 8 + [i64, C.POINTER(i64)]
+        L.pic_load_all.argtypes = [vp, C.POINTER(HostSpeciesT), i32]
         L.pic_set_clock.argtypes = [vp, i64, i64]
         L.pic_save.argtypes = [vp, C.c_char_p]
         L.pic_load.argtypes = [vp, C.c_char_p]
@@ -237,6 +242,18 @@ class Pic:
                 (("x", np.float32), ("y", np.float32), ("z", np.float32), ("vx", np.float32), ("vy", np.float32),
                  ("vz", np.float32), ("w", np.int32), ("id", np.uint64))]
         self._check(lib().pic_load_particles(self.h, species, *[_ptr(a) for a in arrs], len(arrs[0])))
+
+    def load_all(self, pops):
+        """pic_load_all: pops[s] holds the SoA arrays of species s (pinned host memory copies at full
+        bandwidth); the next species' copies overlap the current one's check and sort."""
+        keep, tab = [], (HostSpeciesT * len(pops))()
+        for s, sp in enumerate(pops):
+            arrs = [np.ascontiguousarray(sp[k], dtype=t) for k, t in
+                    (("x", np.float32), ("y", np.float32), ("z", np.float32), ("vx", np.float32), ("vy", np.float32),
+                     ("vz", np.float32), ("w", np.int32), ("id", np.uint64))]
+            keep.append(arrs)
+            tab[s] = HostSpeciesT(*[_ptr(a) for a in arrs], len(arrs[0]))
+        self._check(lib().pic_load_all(self.h, tab, len(pops)))
 
     def get_particles(self, species, cap=None):
         n = C.c_int64()

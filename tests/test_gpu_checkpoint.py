@@ -216,3 +216,50 @@ def test_capacity_refusal_adds_no_sp_and_checkpoint_restores(pic, tmp_path):
     sim.load(path)
     assert_same(before, state(sim))
     sim.close()
+
+
+def test_load_all_equals_species_by_species_and_stops_at_a_bad_species(pic):
+    # pic_load_all (copies of the next species beside the current one's check and sort) leaves the
+    # state of the pic_load_particles sequence; a species that fails its check leaves the species
+    # before it loaded and itself and the rest unchanged
+    import torch
+    cfg = small_cfg(n_sp=20000)
+    flags = pic.F_ALL & ~pic.F_SURROGATE
+    a = fresh(pic, cfg, flags)
+    b = fresh(pic, cfg, flags)
+    pop = synth.plasma(cfg, seed=21)
+    pinned = []
+    for k, _, _ in SPECIES:      # pinned host copies, as a caller streaming states in would hold them
+        d = {}
+        for f, v in pop[k].items():
+            t = torch.empty(len(v), dtype={np.float32: torch.float32, np.int32: torch.int32,
+                                           np.uint64: torch.int64}[v.dtype.type], pin_memory=True)
+            arr = t.numpy().view(v.dtype)
+            arr[:] = v
+            d[f] = arr
+        pinned.append(d)
+    for s, (k, _, _) in enumerate(SPECIES):
+        a.load_particles(s, pop[k])
+    b.load_all(pinned)
+    for s in range(3):
+        ga, gb = a.get_particles(s), b.get_particles(s)
+        for f in ga:
+            assert np.array_equal(ga[f], gb[f]), (s, f)
+    # a second state whose Cu species holds an SP outside the domain
+    pop2 = synth.plasma(cfg, seed=22)
+    pop2["n"]["x"][17] = np.float32(cfg["nx"] + 3)
+    with pytest.raises(pic.PicError):
+        b.load_all([pop2[k] for k, _, _ in SPECIES])
+    e_new = b.get_particles(0)
+    a.load_particles(0, pop2["e"])
+    e_ref = a.get_particles(0)
+    for f in e_ref:
+        assert np.array_equal(e_new[f], e_ref[f]), f          # species 0 was loaded
+    for s in (1, 2):
+        g = b.get_particles(s)
+        ref = a.get_particles(s)                                # a still holds the first state there
+        for f in ref:
+            assert np.array_equal(g[f], ref[f]), (s, f)         # species 1, 2 unchanged
+    b.step(1)                                                   # the handle stays usable
+    a.close()
+    b.close()
