@@ -160,3 +160,80 @@ def test_production_size_optional_processes(pic):
     assert len(np.unique(ids)) == len(ids)
     assert d["coulomb_ee"] > 0 and d["coulomb_ei"] > 0 and d["coulomb_ii"] > 0
     sim.close()
+
+
+def test_production_size_collisions_sampled_against_the_oracle(pic):
+    """Impact and field ionization at the production size, with w_min raised to 1e-3 so that both
+    produce events (the bench's collision-rich form), checked cell by cell against the oracle:
+    every cell whose SPs the GPU changed (at most 4000 of them) and 300 random cells holding both
+    e- and Cu.  The oracle's MCC and DFI on those cells' SPs alone (pairing, draws and field
+    depend on the cell, its SPs and the node field only) must give the same weights (bit for
+    bit), velocities (within 1e-6 of the species' largest speed) and new SPs (positions and
+    weights bit for bit; ids are numbered over the whole grid and are checked for uniqueness)."""
+    from oracle import collide
+    cfg = dict(synth.CONFIGS["production"], w_min=1e-3)
+    n = cfg["n_sp"]
+    pop = synth.plasma(cfg, seed=cfg["seed"])
+    cap = (int(0.4 * n * 1.5), int(0.4 * n * 1.25), int(0.2 * n * 2.0))
+    flags = (pic.F_ALL & ~pic.F_SURROGATE) | pic.F_FAST_INTEGRAL
+    sim = pic.Pic(cfg, capacity=cap, flags=flags, mg_tol=1e-6, mg_max_cycles=60)
+    for s, (k, _, _) in enumerate(SPECIES):
+        sim.load_particles(s, pop[k])
+    sim.set_clock(0, n)
+    sim.solve_field()
+    g = grid_of(cfg)
+    E = field.efield(g, sim.get_potential())
+    before = [sim.get_particles(s) for s in range(3)]
+    sim.collide()
+    d = sim.diagnostics()
+    after = [sim.get_particles(s) for s in range(3)]
+    assert d["impact_ionizations"] > 100 and d["field_ionizations"] > 1000, d
+    ids = np.concatenate([a["id"] for a in after])
+    assert len(np.unique(ids)) == len(ids)
+
+    keys = [P.cell_keys(g, b) for b in before]
+    ne, nn, ni = (len(b["x"]) for b in before)
+    changed = set()
+    for s, m in ((0, ne), (1, nn)):
+        moved = (after[s]["w"][:m] != before[s]["w"]) | (after[s]["vx"][:m] != before[s]["vx"])
+        changed.update(np.unique(keys[s][moved]).tolist())
+    rng = np.random.default_rng(5)
+    changed = sorted(changed)
+    if len(changed) > 4000:
+        changed = sorted(rng.choice(changed, size=4000, replace=False).tolist())
+    both = np.intersect1d(np.unique(keys[0]), np.unique(keys[1]))
+    cells = np.union1d(changed, rng.choice(both, size=300, replace=False))
+    sel = [np.isin(keys[s], cells) for s in range(2)]
+    assert sel[0].sum() > 100 and sel[1].sum() > 1000
+
+    # the oracle on the selected cells alone (cell order is kept, so the sub-arrays are sorted)
+    e_sub, e_off = P.stable_sort(g, P.take(before[0], np.nonzero(sel[0])[0]))
+    n_sub, n_off = P.stable_sort(g, P.take(before[1], np.nonzero(sel[1])[0]))
+    prm = dict(cfg)
+    ids_o = collide.Counter(1 << 40)
+    ni_o, ne_o, ev = collide.impact_ionization(g, prm, e_sub, e_off, n_sub, n_off, 0, ids_o)
+    ni2_o, ne2_o, ev2 = collide.field_ionization(g, prm, n_sub, E, 0, ids_o)
+    assert ev > 0 and ev2 > 0
+
+    for s, sub in ((0, e_sub), (1, n_sub)):
+        idx = np.nonzero(sel[s])[0]
+        got = {f: after[s][f][idx] for f in P.FIELDS}
+        assert np.array_equal(got["id"], sub["id"])
+        assert np.array_equal(got["w"], sub["w"]), s
+        vmax = max(float(np.abs(sub[c]).max()) for c in ("vx", "vy", "vz"))
+        for c in ("vx", "vy", "vz"):
+            assert np.max(np.abs(got[c].astype(np.float64) - sub[c])) <= 1e-6 * vmax, (s, c)
+
+    def products(new, s):
+        k = P.cell_keys(g, new)
+        m = np.isin(k, cells)
+        rows = np.stack([k[m].astype(np.float64), new["x"][m], new["y"][m], new["z"][m], new["w"][m]], 1)
+        return rows[np.lexsort(rows.T[::-1])]
+
+    new_i = {f: after[2][f][ni:] for f in P.FIELDS}
+    new_e = {f: after[0][f][ne:] for f in P.FIELDS}
+    want_i = P.concat(ni_o, ni2_o)
+    want_e = P.concat(ne_o, ne2_o)
+    assert np.array_equal(products(new_i, 2), products(want_i, 2))
+    assert np.array_equal(products(new_e, 0), products(want_e, 0))
+    sim.close()

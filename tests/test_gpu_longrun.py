@@ -1,0 +1,130 @@
+"""Long runs of the small workload on the GPU against the oracle's.
+
+tests/golden/longrun_small.json holds the oracle's 100-step runs of the small workload (32x32x64
+cells, 5e4 SPs, every process of the plain method, heat every 10 steps) for seeds 1..8, written
+by tests/golden/make_longrun.py.  The CUDA path runs the same seeds from the same initial bits
+(the oracle's V0 and its Laplace potential on the fixed-point grid) in the plain form (full
+FP64 emission integral, FP64 V-cycles).
+
+* While both runs hold the same state, every integer of the step (counts, weights, events,
+  removals, ids) is equal.  The runs part when the potentials differ in a bit that reaches an
+  integer decision: the oracle solves Poisson by CG to 1e-13, the library by multigrid to
+  mg_tol, so the node field, a float32 rounding of potential differences, eventually differs by
+  one ulp at some node, and a later position, cell or CIC fraction of an SP near it follows.
+  The test reports the first step where seed 1's integers part and requires the runs to agree
+  on every step before it.
+* Over the seeds, at steps 25, 50, 75 and 100, the mean over the 8 seeds of each inventory
+  (SP count and weight of e-, Cu, Cu+), of the cumulative event counts (emitted, ionizations,
+  removals, ion impacts), of the emitted current and of the tip temperature lies within the
+  oracle's seed-spread band: mean +- 4 sigma / sqrt(8), sigma the oracle's spread over the seeds
+  (4 rather than 3 standard errors: 60 comparisons are made, and at 3 one of them would fall
+  outside by chance in one run of six).
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import field
+from oracle.grid import Grid
+from paper_2402_08404_gb300 import synth
+
+from _util import SPECIES
+
+pytestmark = pytest.mark.gpu
+
+GOLD_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "longrun_small.json")
+EVENT_KEYS = ("emitted", "evaporated", "sputtered", "impact_ionizations", "field_ionizations", "removed_e",
+              "removed_n", "removed_i", "ion_impacts")
+INVENTORY_KEYS = ("count_e", "count_n", "count_i", "weight_e", "weight_n", "weight_i")
+FLOAT_KEYS = ("emitted_current", "max_T")
+
+
+@pytest.fixture(scope="module")
+def gold():
+    with open(GOLD_PATH) as f:
+        return json.load(f)
+
+
+@pytest.fixture(scope="module")
+def runs(gold):
+    from paper_2402_08404_gb300 import _build
+    if not os.path.exists(_build.LIB):
+        _build.build()
+    from paper_2402_08404_gb300 import pic
+    out = {}
+    for seed in sorted(gold["seeds"], key=int):
+        out[seed] = run_gpu(pic, int(seed), gold["seeds"][seed]["V0"], gold["steps"], gold["n_heat"])
+    return out
+
+
+def run_gpu(pic, seed, V0, steps, n_heat):
+    cfg = dict(synth.CONFIGS["small"], n_heat=n_heat, seed=seed)
+    g = Grid(cfg["nx"], cfg["ny"], cfg["nz"], cfg["dx"], cfg["tip_radius"], cfg["tip_height"])
+    flags = pic.F_ALL & ~pic.F_SURROGATE & ~pic.F_MIXED_MG
+    sim = pic.Pic(cfg, capacity=400_000, flags=flags, V0=V0, mg_tol=1e-12, mg_max_cycles=200)
+    sim.set_potential(np.round(field.solve_poisson(g, V0) * 2.0 ** 40) / 2.0 ** 40)
+    pop = synth.plasma(cfg, seed=seed)
+    for s, (k, _, _) in enumerate(SPECIES):
+        sim.load_particles(s, pop[k])
+    sim.set_clock(0, cfg["n_sp"])
+    rows = {k: [] for k in INVENTORY_KEYS + EVENT_KEYS + ("next_id", "emitted_current", "max_T")}
+    for _ in range(steps):
+        sim.step(1)
+        d = sim.diagnostics()
+        for s, k in enumerate("eni"):
+            rows["count_" + k].append(d["count"][s])
+            rows["weight_" + k].append(d["weight"][s])
+            rows["removed_" + k].append(d["removed"][s])
+        for k in ("emitted", "evaporated", "sputtered", "impact_ionizations", "field_ionizations", "ion_impacts",
+                  "next_id", "emitted_current", "max_T"):
+            rows[k].append(d[k])
+    sim.close()
+    return rows
+
+
+def first_parting(gold_seed, run, keys):
+    for t in range(len(run["next_id"])):
+        if any(run[k][t] != gold_seed[k][t] for k in keys):
+            return t + 1
+    return None
+
+
+def test_seed1_integers_equal_until_the_runs_part(gold, runs):
+    keys = [k for k in gold["int_keys"]]
+    g1, r1 = gold["seeds"]["1"], runs["1"]
+    part = first_parting(g1, r1, keys)
+    upto = gold["steps"] if part is None else part - 1
+    print(f"seed 1: every integer of the step equals the oracle's for steps 1..{upto}"
+          + ("" if part is None else f"; first parting at step {part}: " +
+             ", ".join(f"{k} {r1[k][part - 1]} vs {g1[k][part - 1]}" for k in keys if r1[k][part - 1] != g1[k][part - 1])))
+    assert upto >= 5, upto
+    # while the states agree the floats of the step agree to their arithmetic's tolerance
+    for t in range(upto):
+        assert r1["emitted_current"][t] == pytest.approx(g1["emitted_current"][t], rel=1e-6, abs=1e-18)
+        assert r1["max_T"][t] == pytest.approx(g1["max_T"][t], rel=1e-9)
+
+
+@pytest.mark.parametrize("checkpoint", [25, 50, 75, 100])
+def test_seed_means_within_the_oracle_band(gold, runs, checkpoint):
+    seeds = sorted(gold["seeds"], key=int)
+    n = len(seeds)
+    assert n >= 8 and gold["steps"] >= checkpoint
+    t = checkpoint - 1
+
+    def value(src, k):
+        if k in EVENT_KEYS:
+            return float(np.sum(src[k][:t + 1]))       # cumulative events up to the checkpoint
+        return float(src[k][t])
+
+    bad = []
+    for k in INVENTORY_KEYS + EVENT_KEYS + FLOAT_KEYS:
+        o = np.array([value(gold["seeds"][s], k) for s in seeds])
+        g = np.array([value(runs[s], k) for s in seeds])
+        # a floor for quantities the seeds hardly move (the tip temperature): the float parity bar
+        # of a single step (1e-6 relative)
+        band = 4.0 * o.std(ddof=1) / np.sqrt(n) + (1e-6 * abs(o.mean()) if k in FLOAT_KEYS else 0.0)
+        if abs(g.mean() - o.mean()) > band:
+            bad.append((k, g.mean(), o.mean(), band))
+    assert not bad, bad
