@@ -43,8 +43,13 @@ FLOAT_KEYS = ("emitted_current", "max_T")
 
 @pytest.fixture(scope="module")
 def gold():
+    if not os.path.exists(GOLD_PATH):
+        pytest.skip("tests/golden/longrun_small.json not written (tests/golden/make_longrun.py)")
     with open(GOLD_PATH) as f:
-        return json.load(f)
+        g = json.load(f)
+    if g["steps"] < 100 or len(g["seeds"]) < 8:
+        pytest.skip("tests/golden/longrun_small.json holds fewer than 100 steps of 8 seeds")
+    return g
 
 
 @pytest.fixture(scope="module")
