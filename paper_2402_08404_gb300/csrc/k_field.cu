@@ -665,12 +665,15 @@ __device__ __forceinline__ long long nb_sum_fx(const long long *u, int i, int j,
 // kKZ planes per thread (grid z: plane groups): the centre column of phi is loaded once for the
 // z differences of all of them, and every load is issued before the arithmetic (all addresses
 // inside the grid; Dirichlet nodes, the k = 0 and k = nz planes among them, discard theirs).
-template <typename T, int KZ>
+// With E, the pass also writes the node field of this potential, by the arithmetic of k_efield
+// from the same loads (the solve's last residual follows its last correction, so the field of
+// the converged potential comes without another pass over phi).
+template <typename T, int KZ, bool kE>
 __global__ void __launch_bounds__(256) k_residual64(const long long *phi, const unsigned long long *Q,
                                                     unsigned long long Kfx, int S, int zero_charge, T *fl,
                                                     const uint8_t *dir, Lv L, T c_lvl, float V0f,
                                                     const double *V_anode, double *part,
-                                                    int lift) {
+                                                    int lift, float4 *E, float c2, float c1) {
   __shared__ float sh[2][8];
   const int nx = L.nx, ny = L.ny, nz = L.nz;
   const int i = blockIdx.x * 32 + threadIdx.x;
@@ -687,14 +690,19 @@ __global__ void __launch_bounds__(256) k_residual64(const long long *phi, const 
     long long cz[KZ + 2];
 #pragma unroll
     for (int p = 0; p < KZ + 2; ++p) cz[p] = phi[(uint32_t)min(max(k0 - 1 + p, 0), nz) * sz + col];
-    long long side[KZ];
+    long long side[KZ], exd[KZ], eyd[KZ];
     unsigned long long qv[KZ];
     uint8_t d[KZ];
 #pragma unroll
     for (int p = 0; p < KZ; ++p) {
       const uint32_t c = (uint32_t)min(k0 + p, nz) * sz + col;
       d[p] = k0 + p <= nz ? dir[c] : 1;
-      side[p] = phi[c + dxm] + phi[c + dxp] + phi[c + dym] + phi[c + dyp];
+      const long long pxm = phi[c + dxm], pxp = phi[c + dxp], pym = phi[c + dym], pyp = phi[c + dyp];
+      side[p] = pxm + pxp + pym + pyp;
+      if (kE) {
+        exd[p] = pxm - pxp;
+        eyd[p] = pym - pyp;
+      }
       qv[p] = Q[c];
     }
     const int wall = (i == 0 || i == nx ? 1 : 0) + (j == 0 || j == ny ? 1 : 0);
@@ -711,6 +719,15 @@ __global__ void __launch_bounds__(256) k_residual64(const long long *phi, const 
       }
       const float tf = fx_to_float(t);
       fl[sidx32(L, i, j, k)] = d[p] ? (T)0 : fx_to_level(t, c_lvl);
+      if (kE) {
+        const long long dz = k == 0 ? cz[p + 1] - cz[p + 2] : k == nz ? cz[p] - cz[p + 1] : cz[p] - cz[p + 2];
+        float4 e;
+        e.x = __fmul_rn(__ll2float_rn(exd[p]), c2);
+        e.y = __fmul_rn(__ll2float_rn(eyd[p]), c2);
+        e.z = __fmul_rn(__ll2float_rn(dz), k == 0 || k == nz ? c1 : c2);
+        e.w = 0.f;
+        E[(uint32_t)k * sz + col] = e;
+      }
       const float rs = tf * 9.094947017729282e-13f;   // h^2 r = t 2^-40
       s += rs * rs;
       if (lift && !d[p]) {
@@ -931,10 +948,12 @@ static void cycle_fine(pic_t *h) {
   { KtScope kt_(h, kidCorrect, (double)L.nnode); k_correct<T><<<g, node_block(), 0, h->stream>>>(h->phi, lvl_u<T>(L), L.dir, lv_of(L)); }
 }
 
+static void efield_factors(const pic_t *h, float *c2, float *c1);
+
 int stage_efield(pic_t *h) {
   ++h->nlaunch;
-  // f32(1/(2 dx)) 2^-40 and f32(1/dx) 2^-40: rounding then scaling by a power of two
-  const float c2 = (float)(1.0 / (2.0 * h->dx)) * (float)kPhiUnit, c1 = (float)(1.0 / h->dx) * (float)kPhiUnit;
+  float c2, c1;
+  efield_factors(h, &c2, &c1);
   { KtScope kt_(h, kidEfield, (double)h->nnode); k_efield<<<node_grid3(h->nx, h->ny, h->nz), node_block(), 0, h->stream>>>(h->phi, h->E, h->nx, h->ny, h->nz, c2, c1); }
   return launch_check(h, "efield");
 }
@@ -1124,35 +1143,52 @@ static int solve_setup(pic_t *h, double V0, SolveSetup *ss) {
 
 // residual of the fixed-point system onto the finest level and its two norms in red_out (the
 // planes per thread are the autotuner's, 1, 2 or 4)
+// f32(1/(2 dx)) 2^-40 and f32(1/dx) 2^-40 of the node field: rounding then scaling by a power of two
+static void efield_factors(const pic_t *h, float *c2, float *c1) {
+  *c2 = (float)(1.0 / (2.0 * h->dx)) * (float)kPhiUnit;
+  *c1 = (float)(1.0 / h->dx) * (float)kPhiUnit;
+}
+
 template <typename T, int KZ>
-static void residual_kz(pic_t *h, const SolveSetup &ss, bool zero_charge, bool lift, T *fl, T c_lvl, double *part,
-                        int64_t *nb) {
+static void residual_kz(pic_t *h, const SolveSetup &ss, bool zero_charge, bool lift, bool efield, T *fl, T c_lvl,
+                        double *part, int64_t *nb) {
   MgLevel &L = h->mg[0];
   const dim3 g((h->nx + 1 + 31) / 32, (h->ny + 1 + 7) / 8, (h->nz + KZ) / KZ);
   *nb = (int64_t)g.x * g.y * g.z;
-  k_residual64<T, KZ><<<g, node_block(), 0, h->stream>>>(h->phi, h->Q, ss.Kfx, ss.S, zero_charge ? 1 : 0, fl, L.dir,
-                                                         lv_of(L), c_lvl, ss.V0f, ss.V_anode, part, lift ? 1 : 0);
+  float c2, c1;
+  efield_factors(h, &c2, &c1);
+  if (efield)
+    k_residual64<T, KZ, true><<<g, node_block(), 0, h->stream>>>(h->phi, h->Q, ss.Kfx, ss.S, zero_charge ? 1 : 0, fl,
+                                                                 L.dir, lv_of(L), c_lvl, ss.V0f, ss.V_anode, part,
+                                                                 lift ? 1 : 0, h->E, c2, c1);
+  else
+    k_residual64<T, KZ, false><<<g, node_block(), 0, h->stream>>>(h->phi, h->Q, ss.Kfx, ss.S, zero_charge ? 1 : 0, fl,
+                                                                  L.dir, lv_of(L), c_lvl, ss.V0f, ss.V_anode, part,
+                                                                  lift ? 1 : 0, nullptr, c2, c1);
 }
 
 template <typename T>
-static int64_t residual_launch(pic_t *h, const SolveSetup &ss, bool zero_charge, bool lift, T *fl, T c_lvl) {
+static int64_t residual_launch(pic_t *h, const SolveSetup &ss, bool zero_charge, bool lift, bool efield, T *fl,
+                               T c_lvl) {
   int64_t nb = 0;
-  switch (h->tune_residual_kz) {
-    case 1: residual_kz<T, 1>(h, ss, zero_charge, lift, fl, c_lvl, h->red, &nb); break;
-    case 2: residual_kz<T, 2>(h, ss, zero_charge, lift, fl, c_lvl, h->red, &nb); break;
-    default: residual_kz<T, 4>(h, ss, zero_charge, lift, fl, c_lvl, h->red, &nb); break;
+  // with the field, two planes per thread at most (four take ~95 registers)
+  switch (efield ? std::min(h->tune_residual_kz, 2) : h->tune_residual_kz) {
+    case 1: residual_kz<T, 1>(h, ss, zero_charge, lift, efield, fl, c_lvl, h->red, &nb); break;
+    case 2: residual_kz<T, 2>(h, ss, zero_charge, lift, efield, fl, c_lvl, h->red, &nb); break;
+    default: residual_kz<T, 4>(h, ss, zero_charge, lift, efield, fl, c_lvl, h->red, &nb); break;
   }
   return nb;
 }
 
-static void residual_pass(pic_t *h, const SolveSetup &ss, bool zero_charge, bool lift) {
+// efield: the pass also writes the node field of the current potential
+static void residual_pass(pic_t *h, const SolveSetup &ss, bool zero_charge, bool lift, bool efield = false) {
   MgLevel &L = h->mg[0];
   ++h->nlaunch;
   int64_t nb;
   {
     KtScope kt_(h, kidResidual64, (double)h->nnode);
-    nb = ss.mixed ? residual_launch<float>(h, ss, zero_charge, lift, L.f, (float)ss.c_fx)
-                  : residual_launch<double>(h, ss, zero_charge, lift, L.fd, ss.c_fx);
+    nb = ss.mixed ? residual_launch<float>(h, ss, zero_charge, lift, efield, L.f, (float)ss.c_fx)
+                  : residual_launch<double>(h, ss, zero_charge, lift, efield, L.fd, ss.c_fx);
   }
   h->nlaunch += 2;
   { KtScope kt_(h, kidNormSum, (double)nb); k_sum_stage1<<<kSumChunks, 256, 0, h->stream>>>(h->red, nb, h->red_mid); }
@@ -1200,7 +1236,9 @@ int stage_solve(pic_t *h, bool zero_charge, double V0) {
   double norms[2] = {0, 0};
   double lifted = 0.0;
   for (int cyc = 0;; ++cyc) {
-    residual_pass(h, ss, zero_charge, cyc == 0);
+    // after a correction the residual pass also writes the field: if the test passes, that is
+    // the field of the converged potential
+    residual_pass(h, ss, zero_charge, cyc == 0, cyc > 0);
     PIC_CUDA(h, cudaMemcpyAsync(norms, h->red_out, sizeof norms, cudaMemcpyDeviceToHost, h->stream));
     PIC_CUDA(h, cudaStreamSynchronize(h->stream));
     if (cyc == 0) lifted = sqrt(norms[1]);
@@ -1210,6 +1248,7 @@ int stage_solve(pic_t *h, bool zero_charge, double V0) {
     h->last_solve_graph = false;
     if (rel <= h->prm.mg_tol) {
       h->mg_cycles_host += cyc;
+      if (cyc > 0) return launch_check(h, "solve");   // the field came with the last residual
       break;
     }
     if (cyc >= h->prm.mg_max_cycles) {
