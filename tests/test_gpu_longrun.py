@@ -7,12 +7,13 @@ by tests/golden/make_longrun.py.  The CUDA path runs the same seeds from the sam
 FP64 emission integral, FP64 V-cycles).
 
 * While both runs hold the same state, every integer of the step (counts, weights, events,
-  removals, ids) is equal.  The runs part when the potentials differ in a bit that reaches an
-  integer decision: the oracle solves Poisson by CG to 1e-13, the library by multigrid to
-  mg_tol, so the node field, a float32 rounding of potential differences, eventually differs by
-  one ulp at some node, and a later position, cell or CIC fraction of an SP near it follows.
-  The test reports the first step where seed 1's integers part and requires the runs to agree
-  on every step before it.
+  removals, ids) is equal.  The runs would part when the potentials differ in a bit that reaches
+  an integer decision: the oracle solves Poisson by CG to 1e-13, the library by multigrid to
+  mg_tol, so the node field, a float32 rounding of potential differences, could differ by one
+  ulp at some node, and a later position, cell or CIC fraction of an SP near it would follow.
+  The test reports, for every seed, the steps before the first parting and requires at least 50
+  of them, with the emitted current and tip temperature within their float bars over those
+  steps (observed: no seed parts within its 100 steps).
 * Over the seeds, at steps 25, 50, 75 and 100, the mean over the 8 seeds of each inventory
   (SP count and weight of e-, Cu, Cu+), of the cumulative event counts (emitted, ionizations,
   removals, ion impacts), of the emitted current and of the tip temperature lies within the
@@ -96,19 +97,25 @@ def first_parting(gold_seed, run, keys):
     return None
 
 
-def test_seed1_integers_equal_until_the_runs_part(gold, runs):
+def test_integers_equal_until_the_runs_part(gold, runs):
     keys = [k for k in gold["int_keys"]]
-    g1, r1 = gold["seeds"]["1"], runs["1"]
-    part = first_parting(g1, r1, keys)
-    upto = gold["steps"] if part is None else part - 1
-    print(f"seed 1: every integer of the step equals the oracle's for steps 1..{upto}"
-          + ("" if part is None else f"; first parting at step {part}: " +
-             ", ".join(f"{k} {r1[k][part - 1]} vs {g1[k][part - 1]}" for k in keys if r1[k][part - 1] != g1[k][part - 1])))
-    assert upto >= 5, upto
-    # while the states agree the floats of the step agree to their arithmetic's tolerance
-    for t in range(upto):
-        assert r1["emitted_current"][t] == pytest.approx(g1["emitted_current"][t], rel=1e-6, abs=1e-18)
-        assert r1["max_T"][t] == pytest.approx(g1["max_T"][t], rel=1e-9)
+    parting = {}
+    for seed in sorted(gold["seeds"], key=int):
+        part = first_parting(gold["seeds"][seed], runs[seed], keys)
+        parting[seed] = gold["steps"] if part is None else part - 1
+    print("steps over which every integer equals the oracle's, by seed:", parting)
+    for seed, upto in parting.items():
+        g, r = gold["seeds"][seed], runs[seed]
+        if upto < gold["steps"]:
+            print(f"seed {seed} first parts at step {upto + 1}: " +
+                  ", ".join(f"{k} {r[k][upto]} vs {g[k][upto]}" for k in keys if r[k][upto] != g[k][upto]))
+        # every run stays on the oracle's integer trajectory for at least half the run (observed:
+        # all 100 steps of every seed)
+        assert upto >= 50, (seed, upto)
+        # while the states agree the floats of the step agree to their arithmetic's tolerance
+        for t in range(upto):
+            assert r["emitted_current"][t] == pytest.approx(g["emitted_current"][t], rel=1e-6, abs=1e-18), (seed, t)
+            assert r["max_T"][t] == pytest.approx(g["max_T"][t], rel=1e-9), (seed, t)
 
 
 @pytest.mark.parametrize("checkpoint", [25, 50, 75, 100])
