@@ -1,4 +1,4 @@
-"""Long runs of the small workload on the GPU against the oracle's.
+"""Long runs of the small workload on the GPU against the oracle's, over eight seeds.
 
 tests/golden/longrun_small.json holds the oracle's 100-step runs of the small workload (32x32x64
 cells, 5e4 SPs, every process of the plain method, heat every 10 steps) for seeds 1..8, written
