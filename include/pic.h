@@ -171,7 +171,8 @@ const char *pic_last_error(pic_t *h);
 
 /* Replace all SPs of one species (host SoA arrays of length n) and cell-sort them.  Every SP
  * must lie inside the domain and outside the tip; PIC_E_INVALID otherwise, PIC_E_CAPACITY if
- * n exceeds the species capacity. */
+ * n exceeds the species capacity or a cell holds more than 32768 SPs of the species (the sort's
+ * limit, which the step's sort reports the same way). */
 int pic_load_particles(pic_t *h, int species, const float *x, const float *y, const float *z,
                        const float *vx, const float *vy, const float *vz, const int32_t *w,
                        const uint64_t *id, int64_t n);

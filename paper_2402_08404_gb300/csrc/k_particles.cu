@@ -446,8 +446,10 @@ __global__ void k_fix_mid(uint32_t *perm, const int2 *mid_list, const int *mid_n
   }
 }
 
+// One block per queued segment (33..kMaxSegment SPs): bitonic sort of the permutation values in
+// dynamic shared memory (kMaxSegment words).
 __global__ void __launch_bounds__(1024) k_fix_long(uint32_t *perm, const int2 *long_list, const int *long_n, int long_cap) {
-  __shared__ uint32_t sh[kMaxSegment];
+  extern __shared__ uint32_t sh[];
   const int nl = min(*long_n, long_cap);
   for (int q = blockIdx.x; q < nl; q += gridDim.x) {
     const int2 seg = long_list[q];
@@ -732,7 +734,16 @@ int sort_species(pic_t *h, int s) {
   ++h->nlaunch;
   { KtScope kt_(h, kidFixMid, 0); k_fix_mid<<<particle_grid(h), kThreads, 0, h->stream>>>(S.perm, h->mid_list, long_n + 1, (int)h->mid_cap); }
   ++h->nlaunch;
-  { KtScope kt_(h, kidFixLong, 0); k_fix_long<<<h->nsm, 1024, 0, h->stream>>>(S.perm, long_list, long_n, long_cap); }
+  {
+    static_assert(kMaxSegment * sizeof(uint32_t) <= 227 * 1024, "segment buffer above the shared memory of a block");
+    if (!h->fix_long_smem_set) {
+      PIC_CUDA(h, cudaFuncSetAttribute(k_fix_long, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)(kMaxSegment * sizeof(uint32_t))));
+      h->fix_long_smem_set = true;
+    }
+    KtScope kt_(h, kidFixLong, 0);
+    k_fix_long<<<h->nsm, 1024, kMaxSegment * sizeof(uint32_t), h->stream>>>(S.perm, long_list, long_n, long_cap);
+  }
   ++h->nlaunch;
   { KtScope kt_(h, kidGather, 0); k_gather<<<particle_grid(h), kThreads, 0, h->stream>>>(S.a, S.b, S.perm, S.off, h->ncell); }
   ++h->nlaunch;

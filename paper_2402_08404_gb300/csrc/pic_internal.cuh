@@ -41,7 +41,8 @@ constexpr int kPhiShift = 40;
 constexpr double kPhiScale = 1099511627776.0;                  // 2^40
 constexpr double kPhiUnit = 1.0 / 1099511627776.0;             // 2^-40
 constexpr double kPhiMax = 8192.0;                             // |phi| bound [V]
-constexpr int kMaxSegment = 8192;     // SPs of one species in one cell (sort fix-up limit)
+constexpr int kMaxSegment = 32768;    // SPs of one species in one cell (sort fix-up limit: a block's
+                                      // bitonic sort of the segment in 128 KB of shared memory)
 constexpr int kLongCap = 1 << 16;     // queued long segments per sort pass
 // emission surrogate output decoding: log10 J = approx_log10J + y0 kSurY0s (floor
 // kSurLogJFloor), eps_N = y1 kSurY1s [eV]; output rows are kSurOut floats (y0, y1)
@@ -200,6 +201,7 @@ struct pic_s {
   int64_t mid_cap = 0;
   int *long_n = nullptr;
   int *xq_n = nullptr;           // push: lengths of the per-species crosser queues
+  bool fix_long_smem_set = false;  // k_fix_long's dynamic shared memory limit raised on this handle
   // state flags and last diagnostics
   bool keys_valid[PIC_NSPECIES] = {false, false, false, false};
   int last_mg_cycles = 0;

@@ -263,3 +263,37 @@ def test_load_all_equals_species_by_species_and_stops_at_a_bad_species(pic):
     b.step(1)                                                   # the handle stays usable
     a.close()
     b.close()
+
+
+def test_dense_cell_sorts_stably_and_the_cell_limit_gives_capacity(pic):
+    # 20000 electrons in one cell (a long segment: one block's bitonic sort in shared memory) sort
+    # into the oracle's stable order; 40000 in one cell exceed the sort's 32768 and give
+    # PIC_E_CAPACITY (the segment is left unsorted, nothing is written out of place)
+    from oracle import particles as P
+    from _util import grid_of
+    cfg = small_cfg(n_sp=20000)
+    g = grid_of(cfg)
+    flags = pic.F_ALL & ~pic.F_SURROGATE
+    rng = np.random.default_rng(4)
+
+    def electrons(n_dense, n_rest):
+        x = np.concatenate([np.full(n_dense, 3.5, np.float32) + rng.random(n_dense).astype(np.float32) * np.float32(0.4),
+                            (rng.random(n_rest) * 8).astype(np.float32)])
+        y = np.concatenate([np.full(n_dense, 4.25, np.float32), (rng.random(n_rest) * 8).astype(np.float32)])
+        z = np.concatenate([np.full(n_dense, 50.5, np.float32), (50 + rng.random(n_rest) * 10).astype(np.float32)])
+        perm = rng.permutation(n_dense + n_rest)      # the dense cell's SPs interleaved with the rest
+        n = n_dense + n_rest
+        return {"x": x[perm], "y": y[perm], "z": z[perm], "vx": np.zeros(n, np.float32), "vy": np.zeros(n, np.float32),
+                "vz": np.zeros(n, np.float32), "w": np.ones(n, np.int32), "id": np.arange(n, dtype=np.uint64)}
+
+    sim = fresh(pic, cfg, flags, cap=100_000)
+    e = electrons(20000, 5000)
+    sim.load_particles(0, e)
+    got = sim.get_particles(0)
+    want, off = P.stable_sort(g, {f: np.asarray(v) for f, v in e.items()})
+    assert int(np.diff(off).max()) >= 20000
+    for f in ("x", "y", "z", "id"):
+        assert np.array_equal(got[f], want[f]), f
+    with pytest.raises(pic.PicError):
+        sim.load_particles(0, electrons(40000, 100))
+    sim.close()
