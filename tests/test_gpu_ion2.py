@@ -115,3 +115,31 @@ def test_graph_form_with_cu2_equals_the_eager_form(pic):
     assert np.array_equal(a.get_charge(), b.get_charge())
     a.close()
     b.close()
+
+
+def test_resume_with_cu2_repeats_the_uninterrupted_run(pic, tmp_path):
+    # the checkpoint holds the fourth species: n steps, save, m steps against a fresh handle loaded
+    # from the file and stepped m, bit for bit
+    cfg = dict(CFG, w_min=2.0)
+    g, V0, phi, pop = setup(cfg, seed=11)
+    ref = make(pic, cfg, pop, phi, V0)
+    ref.step(2)
+    path = str(tmp_path / "ion2.pic")
+    ref.save(path)
+    ref.step(2)
+    want = [ref.get_particles(s) for s in range(4)]
+    dref = ref.diagnostics()
+    qref = ref.get_charge()
+    ref.close()
+    sim = make(pic, cfg, population(cfg, seed=12), phi, V0)   # another state, replaced by the load
+    sim.load(path)
+    sim.step(2)
+    d = sim.diagnostics()
+    for s in range(4):
+        assert_sp_equal(sim.get_particles(s), want[s])
+    assert np.array_equal(sim.get_charge(), qref)
+    for k in ("step", "next_id", "count", "weight", "double_ionizations", "ion_ionizations", "coulomb_ej",
+              "coulomb_ij", "coulomb_jj", "V_gap"):
+        assert d[k] == dref[k], k
+    assert dref["count"][3] > 0
+    sim.close()
