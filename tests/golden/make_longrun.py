@@ -1,9 +1,12 @@
-"""Write tests/golden/longrun_small.json: the oracle's long runs of the small workload.
+"""Write tests/golden/longrun_<variant>.json: the oracle's long runs of the small workload.
 
 The small workload (32x32x64 cells, dx = 1 nm, tip r = 3 nm h = 20 nm, 8 GV/m apex field,
 5e4 seeded SPs, dt = 0.05 fs) is stepped 100 times by the oracle (oracle/step.py, every
 process of the plain method, heat every 10 steps) for seeds 1..8 (the seed keys both the
-seeded population and the Philox streams).  Per step it records the integer diagnostics and the
+seeded population and the Philox streams).  Variant "small" is that workload as it is (a cold
+tip that barely emits); variant "small_dense" heats the tip to 2000 K, raises the apex field to
+12 GV/m and w_min to 0.1 (ten times the real particles per SP), so that emission, impact and
+field ionization and the space charge of the ions act during the run.  Per step it records the integer diagnostics and the
 emitted current and tip temperature, which tests/test_gpu_longrun.py compares with the CUDA
 path: bit for bit while the two runs share their state, statistically over the seeds after.
 
@@ -11,7 +14,7 @@ The initial potential is the Laplace solution for V0 calibrated by the oracle, r
 library's fixed-point grid (steps of 2^-40 V), so that both sides start from the same bits; the
 test recomputes it with the oracle.  Calls only oracle/ and the seeded input generator.
 
-  python tests/golden/make_longrun.py [--steps 100] [--seeds 1-8] [--workers 8]
+  python tests/golden/make_longrun.py [--variant small|small_dense] [--steps 100] [--seeds 1-8] [--workers 8]
 """
 import argparse
 import json
@@ -25,25 +28,26 @@ sys.path.insert(0, ROOT)
 
 import numpy as np  # noqa: E402
 
-OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "longrun_small.json")
+HERE = os.path.dirname(os.path.abspath(__file__))
 N_HEAT = 10
+VARIANTS = {"small": {}, "small_dense": {"T0": 2000.0, "apex_field": 12e9, "w_min": 0.1}}
 INT_KEYS = ("count_e", "count_n", "count_i", "weight_e", "weight_n", "weight_i", "emitted", "evaporated",
             "sputtered", "impact_ionizations", "field_ionizations", "removed_e", "removed_n", "removed_i",
             "ion_impacts", "next_id")
 FLOAT_KEYS = ("emitted_current", "max_T")
 
 
-def workload():
+def workload(variant="small"):
     from paper_2402_08404_gb300 import synth
-    return dict(synth.CONFIGS["small"], n_heat=N_HEAT)
+    return dict(synth.CONFIGS["small"], n_heat=N_HEAT, **VARIANTS[variant])
 
 
-def initial_state(seed):
+def initial_state(seed, variant="small"):
     """(grid, oracle state, V0) of the seeded small workload for one seed."""
     from oracle import field, step as S
     from oracle.grid import Grid
     from paper_2402_08404_gb300 import synth
-    cfg = dict(workload(), seed=seed)
+    cfg = dict(workload(variant), seed=seed)
     g = Grid(cfg["nx"], cfg["ny"], cfg["nz"], cfg["dx"], cfg["tip_radius"], cfg["tip_height"])
     V0 = field.calibrate_V0(g, cfg["apex_field"])
     phi = np.round(field.solve_poisson(g, V0) * 2.0 ** 40) / 2.0 ** 40
@@ -67,9 +71,9 @@ def record(st):
 
 
 def run_seed(args):
-    seed, steps = args
+    seed, steps, variant = args
     from oracle import step as S
-    g, st, V0 = initial_state(seed)
+    g, st, V0 = initial_state(seed, variant)
     rows = []
     t0 = time.time()
     for _ in range(steps):
@@ -80,6 +84,7 @@ def run_seed(args):
 
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--variant", default="small", choices=sorted(VARIANTS))
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--seeds", default="1-8")
     ap.add_argument("--workers", type=int, default=8)
@@ -87,18 +92,22 @@ def main():
     lo, hi = (int(v) for v in a.seeds.split("-"))
     seeds = list(range(lo, hi + 1))
     with mp.get_context("spawn").Pool(min(a.workers, len(seeds))) as pool:
-        res = pool.map(run_seed, [(s, a.steps) for s in seeds])
-    out = {"workload": "small: 32x32x64 cells, dx 1 nm, tip r 3 nm h 20 nm, 8 GV/m, 5e4 SPs, dt 0.05 fs, "
+        res = pool.map(run_seed, [(s, a.steps, a.variant) for s in seeds])
+    cfg = workload(a.variant)
+    out = {"workload": f"{a.variant}: 32x32x64 cells, dx 1 nm, tip r 3 nm h 20 nm, T0 {cfg['T0']:g} K, "
+                       f"apex {cfg['apex_field'] * 1e-9:g} GV/m, w_min {cfg['w_min']:g}, 5e4 SPs, dt 0.05 fs, "
                        f"heat every {N_HEAT} steps; every process of the plain method",
+           "variant": a.variant, "overrides": VARIANTS[a.variant],
            "generator": "tests/golden/make_longrun.py (oracle/step.py only)",
            "steps": a.steps, "n_heat": N_HEAT, "int_keys": list(INT_KEYS), "float_keys": list(FLOAT_KEYS),
            "seeds": {}}
     for seed, V0, rows, sec in sorted(res):
         out["seeds"][str(seed)] = {"V0": V0, "seconds": round(sec, 1),
                                    **{k: [r[k] for r in rows] for k in INT_KEYS + FLOAT_KEYS}}
-    with open(OUT, "w") as f:
+    path = os.path.join(HERE, f"longrun_{a.variant}.json")
+    with open(path, "w") as f:
         json.dump(out, f, separators=(",", ":"))
-    print("wrote", OUT, {s: out["seeds"][s]["seconds"] for s in out["seeds"]})
+    print("wrote", path, {s: out["seeds"][s]["seconds"] for s in out["seeds"]})
 
 
 if __name__ == "__main__":

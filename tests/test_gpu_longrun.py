@@ -1,10 +1,12 @@
 """Long runs of the small workload on the GPU against the oracle's, over eight seeds.
 
-tests/golden/longrun_small.json holds the oracle's 100-step runs of the small workload (32x32x64
-cells, 5e4 SPs, every process of the plain method, heat every 10 steps) for seeds 1..8, written
-by tests/golden/make_longrun.py.  The CUDA path runs the same seeds from the same initial bits
-(the oracle's V0 and its Laplace potential on the fixed-point grid) in the plain form (full
-FP64 emission integral, FP64 V-cycles).
+tests/golden/longrun_<variant>.json holds the oracle's 100-step runs of the small workload
+(32x32x64 cells, 5e4 SPs, every process of the plain method, heat every 10 steps) for seeds
+1..8, written by tests/golden/make_longrun.py: variant "small" as the workload is (a cold tip
+that barely emits), variant "small_dense" with a 2000 K tip, a 12 GV/m apex field and w_min
+0.1 (emission, impact and field ionization and the ions' space charge all act).  The CUDA path
+runs the same seeds from the same initial bits (the oracle's V0 and its Laplace potential on
+the fixed-point grid) in the plain form (full FP64 emission integral, FP64 V-cycles).
 
 * While both runs hold the same state, every integer of the step (counts, weights, events,
   removals, ids) is equal.  The runs would part when the potentials differ in a bit that reaches
@@ -18,8 +20,8 @@ FP64 emission integral, FP64 V-cycles).
   (SP count and weight of e-, Cu, Cu+), of the cumulative event counts (emitted, ionizations,
   removals, ion impacts), of the emitted current and of the tip temperature lies within the
   oracle's seed-spread band: mean +- 4 sigma / sqrt(8), sigma the oracle's spread over the seeds
-  (4 rather than 3 standard errors: 60 comparisons are made, and at 3 one of them would fall
-  outside by chance in one run of six).
+  (4 rather than 3 standard errors: 68 comparisons are made, and at 3 one of them would fall
+  outside by chance in one run of six); the float quantities get a floor of 1e-6 of their value.
 """
 import json
 import os
@@ -35,21 +37,23 @@ from _util import SPECIES
 
 pytestmark = pytest.mark.gpu
 
-GOLD_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "longrun_small.json")
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+VARIANTS = ("small", "small_dense")
 EVENT_KEYS = ("emitted", "evaporated", "sputtered", "impact_ionizations", "field_ionizations", "removed_e",
               "removed_n", "removed_i", "ion_impacts")
 INVENTORY_KEYS = ("count_e", "count_n", "count_i", "weight_e", "weight_n", "weight_i")
 FLOAT_KEYS = ("emitted_current", "max_T")
 
 
-@pytest.fixture(scope="module")
-def gold():
-    if not os.path.exists(GOLD_PATH):
-        pytest.skip("tests/golden/longrun_small.json not written (tests/golden/make_longrun.py)")
-    with open(GOLD_PATH) as f:
+@pytest.fixture(scope="module", params=VARIANTS)
+def gold(request):
+    path = os.path.join(GOLDEN, f"longrun_{request.param}.json")
+    if not os.path.exists(path):
+        pytest.skip(f"{os.path.basename(path)} not written (tests/golden/make_longrun.py --variant {request.param})")
+    with open(path) as f:
         g = json.load(f)
     if g["steps"] < 100 or len(g["seeds"]) < 8:
-        pytest.skip("tests/golden/longrun_small.json holds fewer than 100 steps of 8 seeds")
+        pytest.skip(f"{os.path.basename(path)} holds fewer than 100 steps of 8 seeds")
     return g
 
 
@@ -61,12 +65,13 @@ def runs(gold):
     from paper_2402_08404_gb300 import pic
     out = {}
     for seed in sorted(gold["seeds"], key=int):
-        out[seed] = run_gpu(pic, int(seed), gold["seeds"][seed]["V0"], gold["steps"], gold["n_heat"])
+        out[seed] = run_gpu(pic, int(seed), gold["seeds"][seed]["V0"], gold["steps"], gold["n_heat"],
+                            gold.get("overrides", {}))
     return out
 
 
-def run_gpu(pic, seed, V0, steps, n_heat):
-    cfg = dict(synth.CONFIGS["small"], n_heat=n_heat, seed=seed)
+def run_gpu(pic, seed, V0, steps, n_heat, overrides):
+    cfg = dict(synth.CONFIGS["small"], n_heat=n_heat, seed=seed, **overrides)
     g = Grid(cfg["nx"], cfg["ny"], cfg["nz"], cfg["dx"], cfg["tip_radius"], cfg["tip_height"])
     flags = pic.F_ALL & ~pic.F_SURROGATE & ~pic.F_MIXED_MG
     sim = pic.Pic(cfg, capacity=400_000, flags=flags, V0=V0, mg_tol=1e-12, mg_max_cycles=200)
