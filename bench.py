@@ -15,10 +15,15 @@ copied in from pinned host memory and the diagnostics read back, every step.
 --impl reference times the FP64 CPU oracle (the only reference this paper has) on a bounded
 particle sample of the same workload.
 """
+import os
+
+# the CPU baseline states the threads it uses: one per process (numpy's BLAS pool would add more)
+for _v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
 import argparse
 import json
 import math
-import os
 import statistics
 import subprocess
 import sys

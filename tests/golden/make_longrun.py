@@ -23,6 +23,11 @@ import os
 import sys
 import time
 
+# one thread per worker process: the seeds run in parallel, and numpy's BLAS pool in every
+# worker would oversubscribe the cores
+for _v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
 ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
 sys.path.insert(0, ROOT)
 
