@@ -14,8 +14,8 @@ the fixed-point grid) in the plain form (full FP64 emission integral, FP64 V-cyc
   mg_tol, so the node field, a float32 rounding of potential differences, could differ by one
   ulp at some node, and a later position, cell or CIC fraction of an SP near it would follow.
   The test reports, for every seed, the steps before the first parting and requires at least 50
-  of them, with the emitted current and tip temperature within their float bars over those
-  steps (observed: no seed parts within its 100 steps).
+  of them, with the emitted current within 1e-6 and the tip temperature within 2e-9 per heat
+  step done over those steps.
 * Over the seeds, at steps 25, 50, 75 and 100, the mean over the 8 seeds of each inventory
   (SP count and weight of e-, Cu, Cu+), of the cumulative event counts (emitted, ionizations,
   removals, ion impacts), of the emitted current and of the tip temperature lies within the
@@ -104,23 +104,30 @@ def first_parting(gold_seed, run, keys):
 
 def test_integers_equal_until_the_runs_part(gold, runs):
     keys = [k for k in gold["int_keys"]]
-    parting = {}
+    n_heat = gold["n_heat"]
+    parting, worst = {}, {}
     for seed in sorted(gold["seeds"], key=int):
-        part = first_parting(gold["seeds"][seed], runs[seed], keys)
-        parting[seed] = gold["steps"] if part is None else part - 1
-    print("steps over which every integer equals the oracle's, by seed:", parting)
-    for seed, upto in parting.items():
         g, r = gold["seeds"][seed], runs[seed]
+        part = first_parting(g, r, keys)
+        upto = gold["steps"] if part is None else part - 1
+        parting[seed] = upto
         if upto < gold["steps"]:
-            print(f"seed {seed} first parts at step {upto + 1}: " +
+            print(f"variant {gold.get('variant', 'small')}, seed {seed} first parts at step {upto + 1}: " +
                   ", ".join(f"{k} {r[k][upto]} vs {g[k][upto]}" for k in keys if r[k][upto] != g[k][upto]))
-        # every run stays on the oracle's integer trajectory for at least half the run (observed:
-        # all 100 steps of every seed)
+        # while the states agree, the floats of the step: the emitted current within 1e-6 (the
+        # single-step bar) and the tip temperature within 2e-9 per heat step done (each heat step
+        # agrees to 1e-9 with the oracle's; the differences carry into the next)
+        dj = max((abs(r["emitted_current"][t] - g["emitted_current"][t]) / max(abs(g["emitted_current"][t]), 1e-12)
+                  for t in range(upto)), default=0.0)
+        dt = max((abs(r["max_T"][t] - g["max_T"][t]) / g["max_T"][t] / (2e-9 * (1 + (t + 1) // n_heat))
+                  for t in range(upto)), default=0.0)
+        worst[seed] = (dj, dt)
+    print(f"variant {gold.get('variant', 'small')}: steps with every integer equal, by seed: {parting}; "
+          f"largest relative current difference and temperature difference over its bar, by seed: {worst}")
+    for seed, upto in parting.items():
+        # every run stays on the oracle's integer trajectory for at least half the run
         assert upto >= 50, (seed, upto)
-        # while the states agree the floats of the step agree to their arithmetic's tolerance
-        for t in range(upto):
-            assert r["emitted_current"][t] == pytest.approx(g["emitted_current"][t], rel=1e-6, abs=1e-18), (seed, t)
-            assert r["max_T"][t] == pytest.approx(g["max_T"][t], rel=1e-9), (seed, t)
+        assert worst[seed][0] <= 1e-6 and worst[seed][1] <= 1.0, (seed, worst[seed])
 
 
 @pytest.mark.parametrize("checkpoint", [25, 50, 75, 100])
