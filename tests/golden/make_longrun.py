@@ -6,7 +6,9 @@ process of the plain method, heat every 10 steps) for seeds 1..8 (the seed keys 
 seeded population and the Philox streams).  Variant "small" is that workload as it is (a cold
 tip that barely emits); variant "small_dense" heats the tip to 2000 K, raises the apex field to
 12 GV/m and w_min to 0.1 (ten times the real particles per SP), so that emission, impact and
-field ionization and the space charge of the ions act during the run.  Per step it records the integer diagnostics and the
+field ionization and the space charge of the ions act during the run; variant "small_all" adds
+every optional process (elastic collisions, Coulomb collisions, the Cu2+ channels, merging, the
+RC circuit).  Per step it records the integer diagnostics and the
 emitted current and tip temperature, which tests/test_gpu_longrun.py compares with the CUDA
 path: bit for bit while the two runs share their state, statistically over the seeds after.
 
@@ -14,7 +16,7 @@ The initial potential is the Laplace solution for V0 calibrated by the oracle, r
 library's fixed-point grid (steps of 2^-40 V), so that both sides start from the same bits; the
 test recomputes it with the oracle.  Calls only oracle/ and the seeded input generator.
 
-  python tests/golden/make_longrun.py [--variant small|small_dense] [--steps 100] [--seeds 1-8] [--workers 8]
+  python tests/golden/make_longrun.py [--variant small|small_dense|small_all] [--steps 100] [--seeds 1-8] [--workers 8]
 """
 import argparse
 import json
@@ -35,11 +37,29 @@ import numpy as np  # noqa: E402
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 N_HEAT = 10
-VARIANTS = {"small": {}, "small_dense": {"T0": 2000.0, "apex_field": 12e9, "w_min": 0.1}}
+DENSE = {"T0": 2000.0, "apex_field": 12e9, "w_min": 0.1}
+# "small_all": the dense variant with every optional process: elastic collisions and charge
+# exchange, Coulomb collisions, the Cu2+ channels, SP merging above 16 SPs of a species per
+# cell, and the RC circuit (1 kOhm, 1 pF)
+ALL = dict(DENSE, elastic=True, coulomb=True, ion2=True, merge_max=16, circuit_R=1e3, circuit_C=1e-12,
+           coulomb_log=10.0)
+VARIANTS = {"small": {}, "small_dense": DENSE, "small_all": ALL}
 INT_KEYS = ("count_e", "count_n", "count_i", "weight_e", "weight_n", "weight_i", "emitted", "evaporated",
             "sputtered", "impact_ionizations", "field_ionizations", "removed_e", "removed_n", "removed_i",
             "ion_impacts", "next_id")
 FLOAT_KEYS = ("emitted_current", "max_T")
+# recorded for the variant with every optional process
+ALL_INT_KEYS = ("count_j", "weight_j", "removed_j", "double_ionizations", "ion_ionizations", "elastic_en",
+                "elastic_nn", "charge_exchanges", "coulomb_ee", "coulomb_ei", "coulomb_ii", "coulomb_ej", "coulomb_ij",
+                "coulomb_jj", "merged")
+ALL_FLOAT_KEYS = ("V_gap",)
+
+
+def keys_of(variant):
+    """(integer keys, float keys) recorded for a variant."""
+    if variant == "small_all":
+        return INT_KEYS + ALL_INT_KEYS, FLOAT_KEYS + ALL_FLOAT_KEYS
+    return INT_KEYS, FLOAT_KEYS
 
 
 def workload(variant="small"):
@@ -63,15 +83,18 @@ def initial_state(seed, variant="small"):
 
 def record(st):
     r = {}
-    for k in "eni":
+    for k in "enij":
         r["count_" + k] = int(len(st.sp[k]["x"]))
         r["weight_" + k] = int(st.sp[k]["w"].astype(np.int64).sum())
     for k in ("emitted", "evaporated", "sputtered", "impact_ionizations", "field_ionizations", "removed_e",
-              "removed_n", "removed_i", "ion_impacts"):
+              "removed_n", "removed_i", "removed_j", "ion_impacts", "double_ionizations", "ion_ionizations",
+              "elastic_en", "elastic_nn", "charge_exchanges", "coulomb_ee", "coulomb_ei", "coulomb_ii", "coulomb_ej",
+              "coulomb_ij", "coulomb_jj", "merged"):
         r[k] = int(st.count.get(k, 0))
     r["next_id"] = int(st.next_id)
     r["emitted_current"] = float(np.sum(st.last_J) * st.grid.dx ** 2)
     r["max_T"] = float(np.max(st.T))
+    r["V_gap"] = float(st.V_gap)
     return r
 
 
@@ -104,11 +127,12 @@ def main():
                        f"heat every {N_HEAT} steps; every process of the plain method",
            "variant": a.variant, "overrides": VARIANTS[a.variant],
            "generator": "tests/golden/make_longrun.py (oracle/step.py only)",
-           "steps": a.steps, "n_heat": N_HEAT, "int_keys": list(INT_KEYS), "float_keys": list(FLOAT_KEYS),
+           "steps": a.steps, "n_heat": N_HEAT, "int_keys": list(keys_of(a.variant)[0]),
+           "float_keys": list(keys_of(a.variant)[1]),
            "seeds": {}}
     for seed, V0, rows, sec in sorted(res):
-        out["seeds"][str(seed)] = {"V0": V0, "seconds": round(sec, 1),
-                                   **{k: [r[k] for r in rows] for k in INT_KEYS + FLOAT_KEYS}}
+        ik, fk = keys_of(a.variant)
+        out["seeds"][str(seed)] = {"V0": V0, "seconds": round(sec, 1), **{k: [r[k] for r in rows] for k in ik + fk}}
     path = os.path.join(HERE, f"longrun_{a.variant}.json")
     with open(path, "w") as f:
         json.dump(out, f, separators=(",", ":"))
