@@ -1235,10 +1235,14 @@ int stage_solve(pic_t *h, bool zero_charge, double V0) {
   PIC_TRY(solve_setup(h, V0, &ss));
   double norms[2] = {0, 0};
   double lifted = 0.0;
+  // The residual pass after a correction also writes the field once this solve has run as many
+  // cycles as the previous one (at least one): if the test then passes, that is the field of the
+  // converged potential.  Earlier passes do not write it (a solve of many cycles would otherwise
+  // write the field after each of them).
+  const int field_from = std::max(h->last_mg_cycles, 1);
   for (int cyc = 0;; ++cyc) {
-    // after a correction the residual pass also writes the field: if the test passes, that is
-    // the field of the converged potential
-    residual_pass(h, ss, zero_charge, cyc == 0, cyc > 0);
+    const bool with_field = cyc >= field_from;
+    residual_pass(h, ss, zero_charge, cyc == 0, with_field);
     PIC_CUDA(h, cudaMemcpyAsync(norms, h->red_out, sizeof norms, cudaMemcpyDeviceToHost, h->stream));
     PIC_CUDA(h, cudaStreamSynchronize(h->stream));
     if (cyc == 0) lifted = sqrt(norms[1]);
@@ -1248,7 +1252,7 @@ int stage_solve(pic_t *h, bool zero_charge, double V0) {
     h->last_solve_graph = false;
     if (rel <= h->prm.mg_tol) {
       h->mg_cycles_host += cyc;
-      if (cyc > 0) return launch_check(h, "solve");   // the field came with the last residual
+      if (with_field) return launch_check(h, "solve");   // the field came with the last residual
       break;
     }
     if (cyc >= h->prm.mg_max_cycles) {
