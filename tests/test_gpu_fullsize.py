@@ -237,3 +237,68 @@ def test_production_size_collisions_sampled_against_the_oracle(pic):
     assert np.array_equal(products(new_i, 2), products(want_i, 2))
     assert np.array_equal(products(new_e, 0), products(want_e, 0))
     sim.close()
+
+
+def test_production_size_cu2_channels_sampled_against_the_oracle(pic):
+    """The Cu2+ channels at the production size (w_min 1e-3, electrons of the seeded state):
+    impact ionization with the double channel and the ionization of Cu+, cell by cell against the
+    oracle as above (every cell the GPU changed, up to 3000, and 300 random cells holding
+    electrons and Cu or Cu+): weights bit for bit, velocities within 1e-6 of the largest speed,
+    new Cu+, Cu2+ and electrons by position and weight."""
+    from oracle import collide
+    cfg = dict(synth.CONFIGS["production"], w_min=1e-3)
+    n = cfg["n_sp"]
+    pop = synth.plasma(cfg, seed=cfg["seed"])
+    cap = (int(0.4 * n * 1.5), int(0.4 * n * 1.25), int(0.2 * n * 2.0), int(0.2 * n))
+    flags = pic.F_IMPACT_ION | pic.F_ION2
+    sim = pic.Pic(cfg, capacity=cap, flags=flags, mg_tol=1e-6, mg_max_cycles=60)
+    for s, (k, _, _) in enumerate(SPECIES):
+        sim.load_particles(s, pop[k])
+    sim.set_clock(0, n)
+    g = grid_of(cfg)
+    before = [sim.get_particles(s) for s in range(3)]
+    sim.collide()
+    d = sim.diagnostics()
+    after = [sim.get_particles(s) for s in range(4)]
+    assert d["impact_ionizations"] > 100 and d["double_ionizations"] > 0 and d["ion_ionizations"] > 0, d
+    ids = np.concatenate([a["id"] for a in after])
+    assert len(np.unique(ids)) == len(ids)
+    keys = [P.cell_keys(g, b) for b in before]
+    ne, nn, ni = (len(b["x"]) for b in before)
+    changed = set()
+    for s, m in ((0, ne), (1, nn), (2, ni)):
+        moved = (after[s]["w"][:m] != before[s]["w"]) | (after[s]["vx"][:m] != before[s]["vx"])
+        changed.update(np.unique(keys[s][moved]).tolist())
+    rng = np.random.default_rng(6)
+    changed = sorted(changed)
+    if len(changed) > 3000:
+        changed = sorted(rng.choice(changed, size=3000, replace=False).tolist())
+    both = np.union1d(np.intersect1d(np.unique(keys[0]), np.unique(keys[1])),
+                      np.intersect1d(np.unique(keys[0]), np.unique(keys[2])))
+    cells = np.union1d(changed, rng.choice(both, size=300, replace=False))
+    sel = [np.isin(keys[s], cells) for s in range(3)]
+    subs = [P.stable_sort(g, P.take(before[s], np.nonzero(sel[s])[0])) for s in range(3)]
+    (e_sub, e_off), (n_sub, n_off), (i_sub, i_off) = subs
+    ids_o = collide.Counter(1 << 40)
+    ni_o, ne_o, ev, nj_o, ne2_o, ev2 = collide.impact_ionization(g, dict(cfg), e_sub, e_off, n_sub, n_off, 0, ids_o,
+                                                                   double=True)
+    nj3_o, ne3_o, ev3 = collide.ion_ionization(g, dict(cfg), e_sub, e_off, i_sub, i_off, 0, ids_o)
+    assert ev > 0 and ev3 > 0
+    for s, sub in ((0, e_sub), (1, n_sub), (2, i_sub)):
+        idx = np.nonzero(sel[s])[0]
+        got = {f: after[s][f][idx] for f in P.FIELDS}
+        assert np.array_equal(got["id"], sub["id"]) and np.array_equal(got["w"], sub["w"]), s
+        vmax = max(float(np.abs(sub[c]).max()) for c in ("vx", "vy", "vz"))
+        for c in ("vx", "vy", "vz"):
+            assert np.max(np.abs(got[c].astype(np.float64) - sub[c])) <= 1e-6 * vmax, (s, c)
+
+    def products(new):
+        k = P.cell_keys(g, new)
+        m = np.isin(k, cells)
+        rows = np.stack([k[m].astype(np.float64), new["x"][m], new["y"][m], new["z"][m], new["w"][m]], 1)
+        return rows[np.lexsort(rows.T[::-1])]
+
+    for s, start, want in ((2, ni, ni_o), (3, 0, P.concat(nj_o, nj3_o)), (0, ne, P.concat(P.concat(ne_o, ne2_o), ne3_o))):
+        new = {f: after[s][f][start:] for f in P.FIELDS}
+        assert np.array_equal(products(new), products(want)), s
+    sim.close()
