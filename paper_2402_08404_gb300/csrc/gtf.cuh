@@ -472,18 +472,29 @@ __device__ inline void current_density_warp(const Consts &C, const Tables &T, do
     for (double pos = B, w = htop; nB < 64; w *= 2.0) { ++nB; pos = fmax(pos - w, M); if (pos == M) break; }
     double Jl = 0.0;
     Pl = 0.0;
-    for (int q = lane; q < 16 * (nA + nB); q += 32) {
-      const int pnl = q >> 4, i = q & 15;
-      double a, c;
-      if (pnl < nA) {
-        a = fmin(A + h0 * (ldexp(1.0, pnl) - 1.0), M);
-        c = fmin(A + h0 * (ldexp(1.0, pnl + 1) - 1.0), M);
-      } else {
-        const int p2 = pnl - nA;
-        c = fmax(B - htop * (ldexp(1.0, p2) - 1.0), M);
-        a = fmax(B - htop * (ldexp(1.0, p2 + 1) - 1.0), M);
+    // A round covers two panels (16 nodes each). The bounds of a panel are the same on its 16
+    // lanes, so lane L works out those of panel 32 g + L once per group g of 32 panels and
+    // the lanes take theirs by shuffle: the FP64 pipe, the one this loop is bound by, sees one
+    // bounds computation per 32 panels instead of one per round.
+    double gmid = 0.0, ghw = 0.0;
+    for (int base = 0; base < 16 * (nA + nB); base += 32) {
+      const int q = base + lane, pnl = q >> 4, i = q & 15;
+      if ((base & 511) == 0) {
+        const int pg = (base >> 4) + lane;
+        double a, c;
+        if (pg < nA) {
+          a = fmin(A + h0 * (ldexp(1.0, pg) - 1.0), M);
+          c = fmin(A + h0 * (ldexp(1.0, pg + 1) - 1.0), M);
+        } else {
+          const int p2 = pg - nA;
+          c = fmax(B - htop * (ldexp(1.0, p2) - 1.0), M);
+          a = fmax(B - htop * (ldexp(1.0, p2 + 1) - 1.0), M);
+        }
+        gmid = 0.5 * (a + c);
+        ghw = 0.5 * (c - a);
       }
-      const double mid = 0.5 * (a + c), hw = 0.5 * (c - a);
+      const double mid = __shfl_sync(0xffffffffu, gmid, pnl & 31), hw = __shfl_sync(0xffffffffu, ghw, pnl & 31);
+      if (q >= 16 * (nA + nB)) continue;
       const double W = mid + hw * T.x16[i];
       if (kFast) {
         double DS, DI;
@@ -507,10 +518,17 @@ __device__ inline void current_density_warp(const Consts &C, const Tables &T, do
     if (B > Wcut) {
       const double w0 = B == top ? htop : h0;
       const int half = lane >> 4, i = lane & 15;
+      // panel bounds by shuffle, as above: lane L holds those of panel 32 g + L
+      double ghi = 0.0, glo = 0.0;
       for (int r = 0; r < 32; ++r) {
         const int pnl = 2 * r + half;
-        const double hi = fmax(B - w0 * (ldexp(1.0, pnl) - 1.0), Wcut);
-        const double lo = fmax(B - w0 * (ldexp(1.0, pnl + 1) - 1.0), Wcut);
+        if ((r & 15) == 0) {
+          const int pg = 2 * r + lane;
+          ghi = fmax(B - w0 * (ldexp(1.0, pg) - 1.0), Wcut);
+          glo = fmax(B - w0 * (ldexp(1.0, pg + 1) - 1.0), Wcut);
+        }
+        const double hi = __shfl_sync(0xffffffffu, ghi, pnl & 31), lo = __shfl_sync(0xffffffffu, glo, pnl & 31);
+        const double last_lo = __shfl_sync(0xffffffffu, glo, (2 * r + 1) & 31);
         double Jl = 0.0;
         Pl = 0.0;
         if (hi > lo) {
@@ -530,7 +548,6 @@ __device__ inline void current_density_warp(const Consts &C, const Tables &T, do
         const double rJ = warp_sum_d(Jl), rP = warp_sum_d(Pl);
         J += rJ;
         P += rP;
-        const double last_lo = fmax(B - w0 * (ldexp(1.0, 2 * r + 2) - 1.0), Wcut);
         nev += 32;
         if (last_lo == Wcut) break;
         if (fabs(rJ) <= 1e-18 * fabs(J) && fabs(rP) <= 1e-18 * fabs(P)) break;

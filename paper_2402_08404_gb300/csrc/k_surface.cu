@@ -450,10 +450,12 @@ int stage_emit(pic_t *h) {
       ++h->nlaunch;
       { KtScope kt_(h, kidEmitSurrogate, (double)fc.n); k_emit_surrogate<<<grid_for(fc.n), kThreads, 0, h->stream>>>(a); }
       ++h->nlaunch;
+      // one warp per block: the queued faces (a few thousand, each a long FP64-bound chain) then
+      // spread over the SMs one warp at a time rather than four
       if (fast)
-        { KtScope kt_(h, kidEmitFallback, (double)fc.n); k_emit_fallback<true><<<h->nsm * 8, 128, 0, h->stream>>>(a); }
+        { KtScope kt_(h, kidEmitFallback, (double)fc.n); k_emit_fallback<true><<<h->nsm * 32, 32, 0, h->stream>>>(a); }
       else
-        { KtScope kt_(h, kidEmitFallback, (double)fc.n); k_emit_fallback<false><<<h->nsm * 8, 128, 0, h->stream>>>(a); }
+        { KtScope kt_(h, kidEmitFallback, (double)fc.n); k_emit_fallback<false><<<h->nsm * 32, 32, 0, h->stream>>>(a); }
     } else {
       ++h->nlaunch;
       const int blocks = (int)std::min<int64_t>((fc.n + 3) / 4, (int64_t)h->nsm * 16);
